@@ -1,0 +1,659 @@
+/*
+ * RACIPE oracle: a plain, slow, FP64 CPU statement of what the RACIPE
+ * ensemble path computes.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the library's product path links,
+ * loads or calls this file; only the test-suite, the smoke check and the
+ * CPU-baseline leg of the benchmark do.  It shares no code, header, table
+ * or constant generator with the CUDA library: every formula below is
+ * restated from the paper (GRiNS, arXiv 2503.18356) and from the published
+ * definitions of the numerical methods it names.
+ *
+ * Contents (each function cites the passage it follows):
+ *   - Philox4x64-10 counter-based generator (Salmon et al., SC'11), the one
+ *     random source of the sampler; pinned against numpy's Philox.
+ *   - Shifted Hill function, Eq. 2, and the RACIPE node equation, Eq. 1.
+ *   - Parameter and initial-condition sampling, Sec. 2.1.2 and Table 1,
+ *     including the inverse-range inhibitory fold change and the
+ *     half-functional threshold rule.
+ *   - Dormand-Prince 5(4) with FSAL and step-size control (Dormand & Prince
+ *     1980; Hairer, Norsett & Wanner, Solving ODEs I, Sec. II.4), run to the
+ *     steady-state condition of Sec. 2.1.3, with optional output at grid
+ *     times (Sec. 2.1.3, time series).
+ *   - Newton polish of a converged state (steady state = Eq. 1 equal to 0).
+ *   - Per-parameter-set steady-state dedupe (Sec. 3.1, multistability).
+ *
+ * Parity status: every function here is pinned by a CPU test against
+ * closed forms, library routines (numpy Philox, scipy DOP853, scipy
+ * quadrature) or brute force; none is "parity unpinned".
+ *
+ * Compiled with -O2 -ffp-contract=off: every floating-point expression is
+ * evaluated as written, one IEEE rounding per operation, no FMA.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------ */
+/* Status codes of one solve (outcome of one (parameter set, IC) pair)  */
+/* ------------------------------------------------------------------ */
+enum { ORC_CONVERGED = 0, ORC_TEND = 1, ORC_MAXSTEPS = 2, ORC_NONFINITE = 3,
+       ORC_POLISH_FAIL = 4 };
+
+/* ------------------------------------------------------------------ */
+/* Philox4x64-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers:  */
+/* as easy as 1, 2, 3", SC'11).  Ten rounds of the 4-word Philox S-box  */
+/* with the published multipliers and Weyl key increments.              */
+/* ------------------------------------------------------------------ */
+void orc_philox4x64_10(const uint64_t ctr_in[4], const uint64_t key_in[2],
+                       uint64_t out[4])
+{
+    const uint64_t mult0 = 0xD2E7470EE14C6C93ULL;
+    const uint64_t mult1 = 0xCA5A826395121157ULL;
+    const uint64_t weyl0 = 0x9E3779B97F4A7C15ULL;  /* golden ratio */
+    const uint64_t weyl1 = 0xBB67AE8584CAA73BULL;  /* sqrt(3) - 1 */
+    uint64_t x0 = ctr_in[0], x1 = ctr_in[1], x2 = ctr_in[2], x3 = ctr_in[3];
+    uint64_t k0 = key_in[0], k1 = key_in[1];
+    for (int round = 0; round < 10; ++round) {
+        unsigned __int128 p0 = (unsigned __int128)mult0 * x0;
+        unsigned __int128 p1 = (unsigned __int128)mult1 * x2;
+        uint64_t hi0 = (uint64_t)(p0 >> 64), lo0 = (uint64_t)p0;
+        uint64_t hi1 = (uint64_t)(p1 >> 64), lo1 = (uint64_t)p1;
+        uint64_t y0 = hi1 ^ x1 ^ k0;
+        uint64_t y1 = lo1;
+        uint64_t y2 = hi0 ^ x3 ^ k1;
+        uint64_t y3 = lo0;
+        x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+        k0 += weyl0;
+        k1 += weyl1;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* Draw number d of the stream (key, c0): word d%4 of the block with
+ * counter (c0, d/4, 0, 0). */
+static uint64_t draw64(uint64_t key0, uint64_t key1, uint64_t c0, uint64_t d)
+{
+    uint64_t ctr[4] = { c0, d / 4, 0, 0 };
+    uint64_t key[2] = { key0, key1 };
+    uint64_t out[4];
+    orc_philox4x64_10(ctr, key, out);
+    return out[d % 4];
+}
+
+/* Uniform double in [0, 1) from the top 53 bits. */
+double orc_u01(uint64_t r) { return (double)(r >> 11) * 0x1.0p-53; }
+
+/* Uniform integer in [lo, hi] from the top 32 bits (multiply-shift). */
+int32_t orc_uint_range(uint64_t r, int32_t lo, int32_t hi)
+{
+    uint64_t span = (uint64_t)(int64_t)(hi - lo + 1);
+    return lo + (int32_t)(((r >> 32) * span) >> 32);
+}
+
+/* Stream keys (second key word; the first is the user's seed). */
+#define ORC_TAG_PARAMS 0x52414349504550ULL  /* "RACIPEP" */
+#define ORC_TAG_ICS    0x52414349504549ULL  /* "RACIPEI" */
+#define ORC_KEY_MEDIAN 0x48414C4646554E43ULL /* "HALFFUNC", fixed */
+
+/* ------------------------------------------------------------------ */
+/* Parameter ranges, Table 1 (defaults set by orc_default_ranges).      */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    double G_min, G_max;           /* production rate */
+    double k_min, k_max;           /* degradation rate */
+    double lam_act_min, lam_act_max; /* activating fold change (>= 1) */
+    double lam_inh_min, lam_inh_max; /* inhibiting fold change (<= 1) */
+    int32_t n_min, n_max;          /* Hill coefficient, integer */
+    double thr_lo, thr_hi;         /* half-functional factors */
+    int32_t median_samples;        /* samples per median estimate */
+    int32_t median_mode;           /* 0 = per in-degree class, 1 = unregulated */
+} orc_ranges;
+
+void orc_default_ranges(orc_ranges *r)
+{
+    r->G_min = 1.0;   r->G_max = 100.0;
+    r->k_min = 0.1;   r->k_max = 1.0;
+    r->lam_act_min = 1.0;  r->lam_act_max = 100.0;
+    r->lam_inh_min = 0.01; r->lam_inh_max = 1.0;
+    r->n_min = 1; r->n_max = 6;
+    r->thr_lo = 0.02; r->thr_hi = 1.98;
+    r->median_samples = 10000;
+    r->median_mode = 0;
+}
+
+/* Affine map of a unit draw onto [lo, hi]: lo + (hi - lo) * u. */
+static double affine(double lo, double hi, double u) { return lo + (hi - lo) * u; }
+
+/* Activating fold change: uniform on [lam_act_min, lam_act_max] (Table 1). */
+static double lam_activating(const orc_ranges *r, double u)
+{
+    return affine(r->lam_act_min, r->lam_act_max, u);
+}
+
+/* Inhibiting fold change, Sec. 2.1.2: drawn uniformly in the inverse range
+ * [1/max, 1/min] and then inverted. */
+static double lam_inhibiting(const orc_ranges *r, double u)
+{
+    double v_lo = 1.0 / r->lam_inh_max;
+    double v_hi = 1.0 / r->lam_inh_min;
+    return 1.0 / affine(v_lo, v_hi, u);
+}
+
+/* ------------------------------------------------------------------ */
+/* Shifted Hill function, Eq. 2, written exactly as printed:            */
+/*   H = B0^n / (B0^n + B^n) + lambda * B^n / (B0^n + B^n).             */
+/* B is an expression level; negative values (which the model never    */
+/* produces) are read as 0.                                            */
+/* ------------------------------------------------------------------ */
+double orc_shifted_hill(double B, double B0, double n, double lam)
+{
+    if (B < 0.0) B = 0.0;
+    double b0n = pow(B0, n);
+    double bn = pow(B, n);
+    return b0n / (b0n + bn) + lam * bn / (b0n + bn);
+}
+
+/* One edge's factor in Eq. 1: H/lambda for an activating edge, H for an
+ * inhibiting one. */
+static double edge_factor(int sign, double B, double T, double n, double lam)
+{
+    double h = orc_shifted_hill(B, T, n, lam);
+    return sign > 0 ? h / lam : h;
+}
+
+/* ------------------------------------------------------------------ */
+/* Network (signed, directed edge list, Sec. 2.1.1).                    */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    int32_t n_nodes, n_edges;
+    const int32_t *src, *dst;
+    const int8_t *sign;            /* +1 activation, -1 inhibition */
+} orc_net;
+
+/* One parameter set, 2N + 3E values (Sec. 2.1.2). */
+typedef struct {
+    const double *G, *k;           /* [N] */
+    const double *T, *lam;         /* [E] */
+    const int32_t *n;              /* [E] */
+} orc_params;
+
+/* Eq. 1: f_i(x) = G_i * prod_{e into i} factor_e(x_src(e)) - k_i * x_i. */
+void orc_rhs(const orc_net *net, const orc_params *p, const double *x, double *f)
+{
+    int N = net->n_nodes;
+    for (int i = 0; i < N; ++i) f[i] = p->G[i];
+    for (int e = 0; e < net->n_edges; ++e) {
+        int s = net->src[e], t = net->dst[e];
+        f[t] = f[t] * edge_factor(net->sign[e], x[s], p->T[e], (double)p->n[e], p->lam[e]);
+    }
+    for (int i = 0; i < N; ++i) f[i] = f[i] - p->k[i] * x[i];
+}
+
+/* Steady-state residual: rho(x) = max_i |f_i| / (G_i / k_i). */
+static double residual_rho(int N, const orc_params *p, const double *f)
+{
+    double rho = 0.0;
+    for (int i = 0; i < N; ++i) {
+        double r = fabs(f[i]) / (p->G[i] / p->k[i]);
+        if (!(r <= rho)) rho = r;   /* NaN propagates */
+    }
+    return rho;
+}
+
+double orc_rho(const orc_net *net, const orc_params *p, const double *x)
+{
+    double f[1024];
+    if (net->n_nodes > 1024) return NAN;
+    orc_rhs(net, p, x, f);
+    return residual_rho(net->n_nodes, p, f);
+}
+
+/* ------------------------------------------------------------------ */
+/* Half-functional rule (Table 1 threshold row; Sec. 2.1.2).            */
+/* The threshold of an edge out of node j is U[thr_lo, thr_hi] times    */
+/* the median steady-state level M_j of node j.  For an unregulated j   */
+/* the steady state is G/k, so M0 = median(G/k).  For a j with `a`      */
+/* activating and `b` inhibiting inputs, the level is simulated from    */
+/* its regulation: (G/k) * prod over inputs of the edge factor, each    */
+/* input at an unregulated level G'/k', with its threshold drawn from   */
+/* U[thr_lo, thr_hi] * M0 and n, lambda from Table 1.  The median over  */
+/* `median_samples` seeded samples is M(a, b).  Draw layout of sample   */
+/* s: 0 -> G, 1 -> k, then per input m (activating ones first) the five */
+/* draws 2+5m .. 6+5m -> G', k', threshold, lambda, n.                  */
+/* ------------------------------------------------------------------ */
+static int cmp_double(const void *a, const void *b)
+{
+    double x = *(const double *)a, y = *(const double *)b;
+    return (x > y) - (x < y);
+}
+
+static double median_of(double *v, int K)
+{
+    qsort(v, (size_t)K, sizeof(double), cmp_double);
+    if (K % 2 == 1) return v[K / 2];
+    return (v[K / 2 - 1] + v[K / 2]) / 2.0;
+}
+
+/* Fills out[0..K) with the samples of class (a, b) given M0 (unused for
+ * a = b = 0).  Exposed for the tests. */
+void orc_median_samples(int32_t a, int32_t b, const orc_ranges *r, double M0,
+                        double *out)
+{
+    int K = r->median_samples;
+    uint64_t key1 = ((uint64_t)(uint32_t)a << 32) | (uint64_t)(uint32_t)b;
+    for (int s = 0; s < K; ++s) {
+        double G = affine(r->G_min, r->G_max, orc_u01(draw64(ORC_KEY_MEDIAN, key1, (uint64_t)s, 0)));
+        double k = affine(r->k_min, r->k_max, orc_u01(draw64(ORC_KEY_MEDIAN, key1, (uint64_t)s, 1)));
+        double level = G / k;
+        for (int m = 0; m < a + b; ++m) {
+            uint64_t d = 2 + 5 * (uint64_t)m;
+            double Gs = affine(r->G_min, r->G_max, orc_u01(draw64(ORC_KEY_MEDIAN, key1, (uint64_t)s, d + 0)));
+            double ks = affine(r->k_min, r->k_max, orc_u01(draw64(ORC_KEY_MEDIAN, key1, (uint64_t)s, d + 1)));
+            double T = affine(r->thr_lo, r->thr_hi, orc_u01(draw64(ORC_KEY_MEDIAN, key1, (uint64_t)s, d + 2))) * M0;
+            double ul = orc_u01(draw64(ORC_KEY_MEDIAN, key1, (uint64_t)s, d + 3));
+            int32_t n = orc_uint_range(draw64(ORC_KEY_MEDIAN, key1, (uint64_t)s, d + 4), r->n_min, r->n_max);
+            int sign = m < a ? +1 : -1;
+            double lam = sign > 0 ? lam_activating(r, ul) : lam_inhibiting(r, ul);
+            level = level * edge_factor(sign, Gs / ks, T, (double)n, lam);
+        }
+        out[s] = level;
+    }
+}
+
+double orc_median(int32_t a, int32_t b, const orc_ranges *r)
+{
+    int K = r->median_samples;
+    double *v = (double *)malloc(sizeof(double) * (size_t)K);
+    if (!v) return NAN;
+    orc_median_samples(0, 0, r, 0.0, v);
+    double M0 = median_of(v, K);
+    double M = M0;
+    if ((a != 0 || b != 0) && r->median_mode == 0) {
+        orc_median_samples(a, b, r, M0, v);
+        M = median_of(v, K);
+    }
+    free(v);
+    return M;
+}
+
+/* ------------------------------------------------------------------ */
+/* Sampling, Sec. 2.1.2 and Table 1.  Parameter set s uses the stream  */
+/* key (seed, TAG_PARAMS), counter word 0 = s, draws:                   */
+/*   [0, N)        G_i          [N, 2N)        k_i                      */
+/*   [2N, 2N+E)    threshold_e  [2N+E, 2N+2E)  lambda_e                 */
+/*   [2N+2E, 2N+3E) n_e                                                 */
+/* IC number c uses key (seed, TAG_ICS), counter word 0 = c, draw i ->  */
+/* the unit level u_{c,i}; the initial condition of node i under set s  */
+/* is u_{c,i} * G_i / k_i (Sec. 2.1.2, between a node's minimum 0 and   */
+/* maximum G/k; the same unit ICs are used for every set, Sec. 3.1).    */
+/* ------------------------------------------------------------------ */
+void orc_sample_params(const orc_net *net, const orc_ranges *r, uint64_t seed,
+                       int64_t set0, int64_t n_sets,
+                       double *G, double *k, double *T, double *lam, int32_t *n)
+{
+    int N = net->n_nodes, E = net->n_edges;
+    /* Median per source node, from its in-degree class. */
+    double *Msrc = (double *)malloc(sizeof(double) * (size_t)N);
+    for (int j = 0; j < N; ++j) {
+        int a = 0, b = 0;
+        for (int e = 0; e < E; ++e)
+            if (net->dst[e] == j) { if (net->sign[e] > 0) ++a; else ++b; }
+        Msrc[j] = orc_median(a, b, r);
+    }
+    for (int64_t s = 0; s < n_sets; ++s) {
+        uint64_t c0 = (uint64_t)(set0 + s);
+        double *Gs = G + s * N, *ks = k + s * N, *Ts = T + s * E, *ls = lam + s * E;
+        int32_t *ns = n + s * E;
+        for (int i = 0; i < N; ++i) {
+            Gs[i] = affine(r->G_min, r->G_max, orc_u01(draw64(seed, ORC_TAG_PARAMS, c0, (uint64_t)i)));
+            ks[i] = affine(r->k_min, r->k_max, orc_u01(draw64(seed, ORC_TAG_PARAMS, c0, (uint64_t)(N + i))));
+        }
+        for (int e = 0; e < E; ++e) {
+            double ut = orc_u01(draw64(seed, ORC_TAG_PARAMS, c0, (uint64_t)(2 * N + e)));
+            double ul = orc_u01(draw64(seed, ORC_TAG_PARAMS, c0, (uint64_t)(2 * N + E + e)));
+            uint64_t rn = draw64(seed, ORC_TAG_PARAMS, c0, (uint64_t)(2 * N + 2 * E + e));
+            Ts[e] = affine(r->thr_lo, r->thr_hi, ut) * Msrc[net->src[e]];
+            ls[e] = net->sign[e] > 0 ? lam_activating(r, ul) : lam_inhibiting(r, ul);
+            ns[e] = orc_uint_range(rn, r->n_min, r->n_max);
+        }
+    }
+    free(Msrc);
+}
+
+void orc_sample_ics(int32_t n_nodes, uint64_t seed, int32_t n_ics, double *u)
+{
+    for (int c = 0; c < n_ics; ++c)
+        for (int i = 0; i < n_nodes; ++i)
+            u[(int64_t)c * n_nodes + i] = orc_u01(draw64(seed, ORC_TAG_ICS, (uint64_t)c, (uint64_t)i));
+}
+
+/* ------------------------------------------------------------------ */
+/* Dormand-Prince 5(4) (Dormand & Prince 1980, "A family of embedded    */
+/* Runge-Kutta formulae"), seven stages, first-same-as-last.            */
+/* ------------------------------------------------------------------ */
+static const double DP_C[7] = { 0.0, 1.0 / 5.0, 3.0 / 10.0, 4.0 / 5.0, 8.0 / 9.0, 1.0, 1.0 };
+static const double DP_A[7][6] = {
+    { 0 },
+    { 1.0 / 5.0 },
+    { 3.0 / 40.0, 9.0 / 40.0 },
+    { 44.0 / 45.0, -56.0 / 15.0, 32.0 / 9.0 },
+    { 19372.0 / 6561.0, -25360.0 / 2187.0, 64448.0 / 6561.0, -212.0 / 729.0 },
+    { 9017.0 / 3168.0, -355.0 / 33.0, 46732.0 / 5247.0, 49.0 / 176.0, -5103.0 / 18656.0 },
+    { 35.0 / 384.0, 0.0, 500.0 / 1113.0, 125.0 / 192.0, -2187.0 / 6784.0, 11.0 / 84.0 },
+};
+/* 5th-order weights (equal to the last row of A) and embedded 4th order. */
+static const double DP_B5[7] = { 35.0 / 384.0, 0.0, 500.0 / 1113.0, 125.0 / 192.0,
+                                 -2187.0 / 6784.0, 11.0 / 84.0, 0.0 };
+static const double DP_B4[7] = { 5179.0 / 57600.0, 0.0, 7571.0 / 16695.0, 393.0 / 640.0,
+                                 -92097.0 / 339200.0, 187.0 / 2100.0, 1.0 / 40.0 };
+
+typedef struct {
+    double rtol, atol, t0, t_end, ss_tol;
+    int64_t max_steps;
+    const double *t_grid;          /* NULL: no time series */
+    int32_t n_t;
+    double h_fixed;                /* > 0: fixed step, no control, no steady-state stop */
+} orc_opts;
+
+typedef struct {
+    int32_t status;
+    double t_final;
+    int64_t n_attempts, n_accepted;
+} orc_result;
+
+#define ORC_NMAX 256
+
+/* One DP5 step of size h from (y, k1 = f(y)); fills k[0..6], y5, y4. */
+static void dp5_step(const orc_net *net, const orc_params *p, const double *y, double h,
+                     double k[7][ORC_NMAX], double *y5, double *y4)
+{
+    int N = net->n_nodes;
+    double z[ORC_NMAX];
+    for (int s = 1; s < 7; ++s) {
+        for (int i = 0; i < N; ++i) {
+            double acc = 0.0;
+            for (int j = 0; j < s; ++j) acc = acc + DP_A[s][j] * k[j][i];
+            z[i] = y[i] + h * acc;
+        }
+        orc_rhs(net, p, z, k[s]);
+    }
+    for (int i = 0; i < N; ++i) {
+        double a5 = 0.0, a4 = 0.0;
+        for (int j = 0; j < 7; ++j) { a5 = a5 + DP_B5[j] * k[j][i]; a4 = a4 + DP_B4[j] * k[j][i]; }
+        y5[i] = y[i] + h * a5;
+        y4[i] = y[i] + h * a4;
+    }
+}
+
+static double rms_scaled(int N, const double *v, const double *y, const double *y2,
+                         double atol, double rtol)
+{
+    double s = 0.0;
+    for (int i = 0; i < N; ++i) {
+        double m = fabs(y[i]);
+        if (y2 && fabs(y2[i]) > m) m = fabs(y2[i]);
+        double q = v[i] / (atol + rtol * m);
+        s = s + q * q;
+    }
+    return sqrt(s / N);
+}
+
+static int all_finite(int N, const double *v)
+{
+    for (int i = 0; i < N; ++i) if (!isfinite(v[i])) return 0;
+    return 1;
+}
+
+/* Integrates Eq. 1 from x0 at t0 until the steady-state condition
+ * (Sec. 2.1.3) rho(f(y)) < ss_tol holds at an accepted step, or t_end is
+ * reached, or max_steps attempts are spent.  With a time grid, steps are
+ * shortened to land on every grid time and the state there is written to
+ * series[g * N + i]; grid times after termination get the final state.
+ * With h_fixed > 0 the method runs with that fixed step to t_end (used to
+ * measure its order). */
+orc_result orc_solve(const orc_net *net, const orc_params *p, const double *x0,
+                     const orc_opts *o, double *x_out, double *series)
+{
+    int N = net->n_nodes;
+    orc_result res = { ORC_TEND, o->t0, 0, 0 };
+    double y[ORC_NMAX], y5[ORC_NMAX], y4[ORC_NMAX], err[ORC_NMAX];
+    double k[7][ORC_NMAX];
+    memcpy(y, x0, sizeof(double) * N);
+    double t = o->t0;
+    int g = 0;                     /* next grid index */
+    while (series && g < o->n_t && o->t_grid[g] <= t) {
+        memcpy(series + (int64_t)g * N, y, sizeof(double) * N); ++g;
+    }
+    orc_rhs(net, p, y, k[0]);
+    int fixed = o->h_fixed > 0.0;
+    if (!fixed && residual_rho(N, p, k[0]) < o->ss_tol) {
+        res.status = ORC_CONVERGED;
+        goto finish;
+    }
+    double h;
+    if (fixed) {
+        h = o->h_fixed;
+    } else {
+        /* Starting step (Hairer, Norsett & Wanner, Sec. II.4). */
+        double d0 = rms_scaled(N, y, y, NULL, o->atol, o->rtol);
+        double d1 = rms_scaled(N, k[0], y, NULL, o->atol, o->rtol);
+        double h0 = (d0 < 1e-5 || d1 < 1e-5) ? 1e-6 : 0.01 * d0 / d1;
+        double y1[ORC_NMAX], f1[ORC_NMAX], df[ORC_NMAX];
+        for (int i = 0; i < N; ++i) y1[i] = y[i] + h0 * k[0][i];
+        orc_rhs(net, p, y1, f1);
+        for (int i = 0; i < N; ++i) df[i] = f1[i] - k[0][i];
+        double d2 = rms_scaled(N, df, y, NULL, o->atol, o->rtol) / h0;
+        double dm = d1 > d2 ? d1 : d2;
+        double h1 = dm <= 1e-15 ? fmax(1e-6, h0 * 1e-3) : pow(0.01 / dm, 1.0 / 5.0);
+        h = fmin(100.0 * h0, h1);
+    }
+    double span = o->t_end - o->t0;
+    if (h > span) h = span;
+    int rejected = 0;
+    for (;;) {
+        if (t >= o->t_end) { res.status = ORC_TEND; break; }
+        if (res.n_attempts >= o->max_steps) { res.status = ORC_MAXSTEPS; break; }
+        /* Land exactly on the next grid time or on t_end. */
+        double h_try = h;
+        double t_stop = o->t_end;
+        int to_grid = 0;
+        if (series && g < o->n_t && o->t_grid[g] < t_stop) { t_stop = o->t_grid[g]; to_grid = 1; }
+        int clipped = 0;
+        if (t + h_try >= t_stop) { h_try = t_stop - t; clipped = 1; }
+        dp5_step(net, p, y, h_try, k, y5, y4);
+        res.n_attempts++;
+        for (int i = 0; i < N; ++i) err[i] = y5[i] - y4[i];
+        if (!all_finite(N, y5) || !all_finite(N, k[6])) { res.status = ORC_NONFINITE; break; }
+        double en = fixed ? 0.0 : rms_scaled(N, err, y, y5, o->atol, o->rtol);
+        if (!isfinite(en)) { res.status = ORC_NONFINITE; break; }
+        if (en < 1.0) {
+            res.n_accepted++;
+            t = clipped ? t_stop : t + h_try;
+            memcpy(y, y5, sizeof(double) * N);
+            memcpy(k[0], k[6], sizeof(double) * N);   /* first same as last */
+            if (clipped && to_grid) {
+                while (g < o->n_t && o->t_grid[g] <= t) {
+                    memcpy(series + (int64_t)g * N, y, sizeof(double) * N); ++g;
+                }
+            }
+            if (!fixed && residual_rho(N, p, k[0]) < o->ss_tol) { res.status = ORC_CONVERGED; break; }
+            if (!fixed) {
+                /* Step-size controller: safety 0.9, factor in [0.2, 10],
+                 * no growth right after a rejected attempt. */
+                double fac = en == 0.0 ? 10.0 : 0.9 * pow(en, -1.0 / 5.0);
+                if (fac > 10.0) fac = 10.0;
+                if (rejected && fac > 1.0) fac = 1.0;
+                h = h_try * fac;
+            }
+            rejected = 0;
+        } else {
+            double fac = 0.9 * pow(en, -1.0 / 5.0);
+            if (fac < 0.2) fac = 0.2;
+            h = h_try * fac;
+            rejected = 1;
+        }
+        if (!fixed && h < 1e-14 * (fabs(t) > 1.0 ? fabs(t) : 1.0)) { res.status = ORC_NONFINITE; break; }
+    }
+finish:
+    res.t_final = t;
+    memcpy(x_out, y, sizeof(double) * N);
+    while (series && g < o->n_t) {
+        memcpy(series + (int64_t)g * N, y, sizeof(double) * N); ++g;
+    }
+    return res;
+}
+
+/* ------------------------------------------------------------------ */
+/* Newton polish.  A steady state is a zero of Eq. 1.  From the state   */
+/* the integrator stopped at, Newton iterations x <- x + d with         */
+/* J d = -f(x), J by central differences, solved by Gaussian            */
+/* elimination with partial pivoting, until rho(x) < tol.               */
+/* Returns 0 when rho < tol, 1 when max_iter is spent, 2 if J singular. */
+/* ------------------------------------------------------------------ */
+static int lu_solve(int N, double *A, double *b)
+{
+    for (int c = 0; c < N; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < N; ++r) if (fabs(A[r * N + c]) > fabs(A[piv * N + c])) piv = r;
+        if (A[piv * N + c] == 0.0) return 2;
+        if (piv != c) {
+            for (int j = 0; j < N; ++j) { double tmp = A[c * N + j]; A[c * N + j] = A[piv * N + j]; A[piv * N + j] = tmp; }
+            double tb = b[c]; b[c] = b[piv]; b[piv] = tb;
+        }
+        for (int r = c + 1; r < N; ++r) {
+            double m = A[r * N + c] / A[c * N + c];
+            for (int j = c; j < N; ++j) A[r * N + j] = A[r * N + j] - m * A[c * N + j];
+            b[r] = b[r] - m * b[c];
+        }
+    }
+    for (int r = N - 1; r >= 0; --r) {
+        double s = b[r];
+        for (int j = r + 1; j < N; ++j) s = s - A[r * N + j] * b[j];
+        b[r] = s / A[r * N + r];
+    }
+    return 0;
+}
+
+int32_t orc_polish(const orc_net *net, const orc_params *p, double *x, double tol,
+                   int32_t max_iter, double *rho_out, double *step_out)
+{
+    int N = net->n_nodes;
+    double f[ORC_NMAX], fp[ORC_NMAX], fm[ORC_NMAX], xp[ORC_NMAX];
+    double *J = (double *)malloc(sizeof(double) * (size_t)N * N);
+    int32_t rc = 1;
+    double last_step = 0.0;
+    for (int it = 0; it <= max_iter; ++it) {
+        orc_rhs(net, p, x, f);
+        double rho = residual_rho(N, p, f);
+        if (rho_out) *rho_out = rho;
+        if (rho < tol) { rc = 0; break; }
+        if (it == max_iter) break;
+        for (int j = 0; j < N; ++j) {
+            double scale = fabs(x[j]) > 1e-6 * p->G[j] / p->k[j] ? fabs(x[j]) : 1e-6 * p->G[j] / p->k[j];
+            double dx = 6e-6 * scale;
+            memcpy(xp, x, sizeof(double) * N);
+            xp[j] = x[j] + dx; orc_rhs(net, p, xp, fp);
+            xp[j] = x[j] - dx; orc_rhs(net, p, xp, fm);
+            for (int i = 0; i < N; ++i) J[i * N + j] = (fp[i] - fm[i]) / (2.0 * dx);
+        }
+        for (int i = 0; i < N; ++i) f[i] = -f[i];
+        if (lu_solve(N, J, f) != 0) { rc = 2; break; }
+        last_step = 0.0;
+        for (int i = 0; i < N; ++i) {
+            x[i] = x[i] + f[i];
+            double s = fabs(f[i]) / (p->G[i] / p->k[i]);
+            if (s > last_step) last_step = s;
+        }
+    }
+    if (step_out) *step_out = last_step;
+    free(J);
+    return rc;
+}
+
+/* ------------------------------------------------------------------ */
+/* Steady-state dedupe for one parameter set (Sec. 3.1: the             */
+/* multistability of a set is its number of unique steady states over   */
+/* its initial conditions).  States are compared after G/k              */
+/* normalisation (Sec. 2.1.3), v_i = (x_i * k_i) / G_i.  In IC order,   */
+/* each converged state joins the first representative r with           */
+/* max_i |v_i - r_i| <= tol, or becomes a new representative.           */
+/* state_id = representative index, -1 for solves that did not converge.*/
+/* Returns the number of representatives.                               */
+/* ------------------------------------------------------------------ */
+int32_t orc_dedupe(int32_t N, int32_t n_ics, const double *states, const uint8_t *status,
+                   const double *G, const double *k, double tol, int32_t *state_id)
+{
+    int32_t n_rep = 0;
+    int32_t *rep_ic = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n_ics > 0 ? n_ics : 1));
+    for (int c = 0; c < n_ics; ++c) {
+        state_id[c] = -1;
+        if (status[c] != ORC_CONVERGED) continue;
+        const double *x = states + (int64_t)c * N;
+        int joined = -1;
+        for (int r = 0; r < n_rep && joined < 0; ++r) {
+            const double *xr = states + (int64_t)rep_ic[r] * N;
+            double dmax = 0.0;
+            for (int i = 0; i < N; ++i) {
+                double v = (x[i] * k[i]) / G[i];
+                double vr = (xr[i] * k[i]) / G[i];
+                double d = fabs(v - vr);
+                if (d > dmax) dmax = d;
+            }
+            if (dmax <= tol) joined = r;
+        }
+        if (joined < 0) { rep_ic[n_rep] = c; joined = n_rep; ++n_rep; }
+        state_id[c] = joined;
+    }
+    free(rep_ic);
+    return n_rep;
+}
+
+/* ------------------------------------------------------------------ */
+/* Whole path for a range of parameter sets: for every (set, IC) solve, */
+/* optionally polish converged states, then dedupe each set.            */
+/* Arrays are indexed by the set's position in the range.               */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    int32_t polish;                /* 1: Newton polish of converged states */
+    double polish_tol;             /* rho target of the polish */
+    int32_t polish_iters;
+    double dedupe_tol;
+} orc_path_opts;
+
+void orc_run_sets(const orc_net *net, const double *G, const double *k, const double *T,
+                  const double *lam, const int32_t *n, int64_t n_sets,
+                  const double *ic_unit, int32_t n_ics, const orc_opts *o,
+                  const orc_path_opts *po,
+                  double *states, uint8_t *status, double *t_final, int64_t *n_attempts,
+                  double *series, int32_t *state_id, int32_t *n_unique)
+{
+    int N = net->n_nodes, E = net->n_edges;
+    double x0[ORC_NMAX];
+    for (int64_t s = 0; s < n_sets; ++s) {
+        orc_params p = { G + s * N, k + s * N, T + s * E, lam + s * E, n + s * E };
+        for (int c = 0; c < n_ics; ++c) {
+            int64_t idx = s * n_ics + c;
+            for (int i = 0; i < N; ++i) x0[i] = (ic_unit[(int64_t)c * N + i] * p.G[i]) / p.k[i];
+            double *xo = states + idx * N;
+            double *sr = series ? series + idx * (int64_t)o->n_t * N : NULL;
+            orc_result r = orc_solve(net, &p, x0, o, xo, sr);
+            if (r.status == ORC_CONVERGED && po->polish) {
+                double xp[ORC_NMAX];
+                memcpy(xp, xo, sizeof(double) * N);
+                double rho, stp;
+                if (orc_polish(net, &p, xp, po->polish_tol, po->polish_iters, &rho, &stp) == 0)
+                    memcpy(xo, xp, sizeof(double) * N);
+                else
+                    r.status = ORC_POLISH_FAIL;
+            }
+            status[idx] = (uint8_t)r.status;
+            if (t_final) t_final[idx] = r.t_final;
+            if (n_attempts) n_attempts[idx] = r.n_attempts;
+        }
+        if (state_id && n_unique)
+            n_unique[s] = orc_dedupe(N, n_ics, states + s * n_ics * (int64_t)N, status + s * n_ics,
+                                     p.G, p.k, po->dedupe_tol, state_id + s * n_ics);
+    }
+}

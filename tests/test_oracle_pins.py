@@ -1,0 +1,427 @@
+"""Pins of the CPU oracle to facts outside itself.
+
+Each test ties one oracle function to something the paper or mathematics
+fixes: library routines (numpy's Philox, scipy's RK45 / DOP853, scipy
+quadrature), closed forms, special values of Eq. 2, invariants of Eq. 1,
+brute force on tiny inputs, and the printed ranges of Table 1.  A plausible
+slip in the oracle (a dropped term, a wrong sign, index or coefficient)
+fails at least one of these.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import integrate, optimize, stats
+
+import oracle as O
+from paper_2503_18356_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def table1():
+    rows = {}
+    for line in open(os.path.join(GOLDEN, "table1_default_ranges.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        name, lo, hi = line.split()
+        rows[name] = (float(lo), float(hi))
+    return rows
+
+
+def model_rhs(net, G, k, T, lam, n):
+    """Eq. 1 with Eq. 2 in the algebraic form lam + (1 - lam) / (1 + (B/B0)^n),
+    used to drive scipy's integrators (independent of the oracle's code)."""
+    src, dst, sign = net.src, net.dst, net.sign
+
+    def f(t, x):
+        xb = np.maximum(x[src], 0.0)
+        H = lam + (1.0 - lam) / (1.0 + (xb / T) ** n)
+        fac = np.where(sign > 0, H / lam, H)
+        prod = np.ones(net.n_nodes)
+        np.multiply.at(prod, dst, fac)
+        return G * prod - k * x
+    return f
+
+
+def handmade(net, G, k, T, lam, n):
+    return O.ParamSet(np.array([G], float), np.array([k], float), np.array([T], float),
+                      np.array([lam], float), np.array([n], np.int32))
+
+
+# ------------------------------------------------------------------ Philox
+def test_philox_matches_numpy():
+    rng = np.random.default_rng(7)
+    for _ in range(200):
+        key = rng.integers(0, 2**64, size=2, dtype=np.uint64)
+        ctr = rng.integers(0, 2**64, size=4, dtype=np.uint64)
+        ctr[0] = max(int(ctr[0]), 1)
+        mine = O.philox4x64_10(ctr, key)
+        prev = ctr.copy()
+        prev[0] = np.uint64(int(ctr[0]) - 1)   # numpy increments before drawing
+        ref = np.random.Philox(key=key, counter=prev).random_raw(4)
+        assert np.array_equal(mine, ref)
+
+
+def test_unit_maps():
+    assert O.u01(0) == 0.0
+    assert O.u01(2**64 - 1) == 1.0 - 2.0**-53
+    assert O.u01(1 << 63) == 0.5
+    # multiply-shift integer map covers {lo..hi} with equal-width bins
+    hits = [O.uint_range((h << 32), 1, 6) for h in np.linspace(0, 2**32 - 1, 6000).astype(np.uint64)]
+    vals, counts = np.unique(hits, return_counts=True)
+    assert list(vals) == [1, 2, 3, 4, 5, 6]
+    assert counts.min() >= 990 and counts.max() <= 1010
+
+
+# ------------------------------------------------------------------ Eq. 2
+@pytest.mark.parametrize("lam", [0.01, 0.3, 1.0, 2.5, 100.0])
+@pytest.mark.parametrize("n", [1, 2, 3, 6])
+def test_shifted_hill_special_values(lam, n):
+    B0 = 3.7
+    assert O.shifted_hill(0.0, B0, n, lam) == pytest.approx(1.0, rel=1e-15)
+    assert O.shifted_hill(B0, B0, n, lam) == pytest.approx((1.0 + lam) / 2.0, rel=1e-14)
+    assert O.shifted_hill(1e40 * B0, B0, n, lam) == pytest.approx(lam, rel=1e-14)
+    # algebraic identity H = lam + (1 - lam) / (1 + (B/B0)^n)
+    for B in [0.1, 1.0, 2.0, 5.5, 40.0]:
+        ref = lam + (1.0 - lam) / (1.0 + (B / B0) ** n)
+        assert O.shifted_hill(B, B0, n, lam) == pytest.approx(ref, rel=1e-13)
+
+
+def test_shifted_hill_monotone():
+    B = np.linspace(0, 50, 200)
+    inh = [O.shifted_hill(b, 5.0, 3, 0.1) for b in B]
+    act = [O.shifted_hill(b, 5.0, 3, 10.0) for b in B]
+    assert np.all(np.diff(inh) <= 0) and np.all(np.diff(act) >= 0)
+
+
+# ------------------------------------------------------------------ Eq. 1
+def test_rhs_closed_forms():
+    # one node, no inputs: f = G - k x
+    one = O.Network(1, [], [], [])
+    p = O.ParamSet(np.array([[40.0]]), np.array([[0.5]]), np.zeros((1, 0)),
+                   np.zeros((1, 0)), np.zeros((1, 0), np.int32))
+    assert O.rhs(one, p, [10.0])[0] == pytest.approx(40.0 - 5.0, rel=1e-15)
+    # cascade A -> B at x_A = T: f_B = G_B (1 + lam) / (2 lam) - k_B x_B
+    for sign, lam in [(+1, 7.0), (-1, 0.2)]:
+        net = O.Network(*W.cascade(sign).edges())
+        p = handmade(net, [10.0, 30.0], [1.0, 0.25], [4.0], [lam], [3])
+        f = O.rhs(net, p, [4.0, 2.0])
+        H = (1.0 + lam) / 2.0
+        expect = 30.0 * (H / lam if sign > 0 else H) - 0.25 * 2.0
+        assert f[0] == pytest.approx(10.0 - 4.0, rel=1e-15)
+        assert f[1] == pytest.approx(expect, rel=1e-14)
+
+
+def test_rhs_product_of_inputs():
+    # TSSA node 0 has inputs: B -| A and A -> A.  At x_B = 0 the inhibiting
+    # factor is 1; at x_A = 0 the activating factor is 1/lam.
+    net = O.Network(*W.toggle_switch_self_activation().edges())
+    lam = [0.05, 0.07, 4.0, 9.0]
+    p = handmade(net, [20.0, 30.0], [0.5, 0.8], [3.0, 2.0, 5.0, 6.0], lam, [2, 3, 4, 5])
+    f = O.rhs(net, p, [0.0, 0.0])
+    assert f[0] == pytest.approx(20.0 / 4.0, rel=1e-14)
+    assert f[1] == pytest.approx(30.0 / 9.0, rel=1e-14)
+
+
+# ------------------------------------------------------------------ sampler
+def test_sampler_ranges_match_table1():
+    t1 = table1()
+    net = O.Network(*W.random_network(5, 6, 14, 7, 2).edges())
+    p = O.sample_params(net, 11, 3000)
+    act = net.sign > 0
+    assert p.G.min() >= t1["production_G"][0] and p.G.max() <= t1["production_G"][1]
+    assert p.k.min() >= t1["degradation_k"][0] and p.k.max() <= t1["degradation_k"][1]
+    la, li = p.lam[:, act], p.lam[:, ~act]
+    assert la.min() >= t1["fold_activation"][0] and la.max() <= t1["fold_activation"][1]
+    assert li.min() >= t1["fold_inhibition"][0] and li.max() <= t1["fold_inhibition"][1]
+    assert set(np.unique(p.n)) == set(range(int(t1["hill_n"][0]), int(t1["hill_n"][1]) + 1))
+    M = np.array([O.median(int(((net.dst == j) & (net.sign > 0)).sum()),
+                           int(((net.dst == j) & (net.sign < 0)).sum())) for j in range(6)])
+    ratio = p.T / M[net.src][None, :]
+    lo, hi = t1["threshold_factor"]
+    assert ratio.min() >= lo and ratio.max() <= hi
+    assert ratio.min() < lo + 0.01 and ratio.max() > hi - 0.01
+
+
+def test_sampler_distributions():
+    t1 = table1()
+    net = O.Network(*W.random_network(9, 4, 8, 4, 0).edges())
+    p = O.sample_params(net, 23, 5000)
+    lo, hi = t1["production_G"]
+    assert stats.kstest(p.G.ravel(), stats.uniform(lo, hi - lo).cdf).pvalue > 1e-4
+    lo, hi = t1["degradation_k"]
+    assert stats.kstest(p.k.ravel(), stats.uniform(lo, hi - lo).cdf).pvalue > 1e-4
+    act = net.sign > 0
+    lo, hi = t1["fold_activation"]
+    assert stats.kstest(p.lam[:, act].ravel(), stats.uniform(lo, hi - lo).cdf).pvalue > 1e-4
+    # inverse-range rule: 1/lam uniform on [1/max, 1/min] (Sec. 2.1.2)
+    lo, hi = t1["fold_inhibition"]
+    inv = 1.0 / p.lam[:, ~act].ravel()
+    assert stats.kstest(inv, stats.uniform(1 / hi, 1 / lo - 1 / hi).cdf).pvalue > 1e-4
+    # the paper's "0.02" is the centre (median) of the inverted draw: 1/50.5
+    centre = t1["inhibitory_fold_centre"][0]
+    assert np.median(p.lam[:, ~act]) == pytest.approx(centre, abs=0.0015)
+    counts = np.bincount(p.n.ravel(), minlength=7)[1:]
+    assert stats.chisquare(counts).pvalue > 1e-4
+
+
+def test_sampler_draw_layout_from_numpy_philox():
+    """Set s, draw d comes from Philox block (s, d // 4) word d % 4 under the
+    key (seed, params tag): recomputed here with numpy's Philox."""
+    tag = 0x52414349504550
+    net = O.Network(*W.random_network(3, 3, 5, 2, 1).edges())
+    N, E = 3, 5
+    seed, s = 99, 17
+    p = O.sample_params(net, seed, 1, set0=s)
+
+    def draw(d):
+        ctr = np.array([s - 1, d // 4, 0, 0], dtype=np.uint64)
+        key = np.array([seed, tag], dtype=np.uint64)
+        return int(np.random.Philox(key=key, counter=ctr).random_raw(4)[d % 4])
+
+    u = lambda d: (draw(d) >> 11) * 2.0**-53
+    assert p.G[0, 1] == 1.0 + 99.0 * u(1)
+    assert p.k[0, 2] == 0.1 + (1.0 - 0.1) * u(N + 2)
+    e_inh = int(np.where(net.sign < 0)[0][0])
+    assert p.lam[0, e_inh] == 1.0 / (1.0 + (1.0 / 0.01 - 1.0) * u(2 * N + E + e_inh))
+    assert p.n[0, 4] == 1 + (((draw(2 * N + 2 * E + 4) >> 32) * 6) >> 32)
+    # counter-based: a set drawn alone equals the same set drawn in a batch
+    batch = O.sample_params(net, seed, 20)
+    assert np.array_equal(batch.T[s], p.T[0]) and np.array_equal(batch.n[s], p.n[0])
+
+
+def test_ic_layout_from_numpy_philox():
+    tag = 0x52414349504549
+    u = O.sample_ics(5, 42, 3)
+    ctr = np.array([2 - 1, 0, 0, 0], dtype=np.uint64)
+    key = np.array([42, tag], dtype=np.uint64)
+    r = np.random.Philox(key=key, counter=ctr).random_raw(4)
+    assert u[2, 3] == (int(r[3]) >> 11) * 2.0**-53
+    assert u.min() >= 0.0 and u.max() < 1.0
+
+
+# ------------------------------------------------------- half-functional rule
+def test_unregulated_median_closed_form():
+    """M0 = median of G/k, G ~ U[1,100], k ~ U[0.1,1]: solved by quadrature."""
+    def cdf(m):
+        f = lambda k: np.clip((m * k - 1.0) / 99.0, 0.0, 1.0) / 0.9
+        return integrate.quad(f, 0.1, 1.0, points=[1.0 / m, 100.0 / m], limit=200)[0]
+    m_true = optimize.brentq(lambda m: cdf(m) - 0.5, 1.0, 1000.0, xtol=1e-12)
+    eps = 1e-3
+    dens = (cdf(m_true + eps) - cdf(m_true - eps)) / (2 * eps)
+    se = 1.0 / (2.0 * dens * math.sqrt(10000))
+    assert abs(O.median(0, 0) - m_true) < 5 * se
+
+
+@pytest.mark.parametrize("a,b", [(1, 0), (0, 1), (2, 1)])
+def test_regulated_median_monte_carlo(a, b):
+    """The regulated class's samples follow the distribution of
+    (G/k) * prod factor(G'/k'; T = U[.02,1.98] M0, n, lam) drawn with numpy."""
+    M0 = O.median(0, 0)
+    mine = O.median_samples(a, b, M0=M0)
+    rng = np.random.default_rng(123)
+    K = 200_000
+    lvl = rng.uniform(1, 100, K) / rng.uniform(0.1, 1, K)
+    for m in range(a + b):
+        src = rng.uniform(1, 100, K) / rng.uniform(0.1, 1, K)
+        T = rng.uniform(0.02, 1.98, K) * M0
+        n = rng.integers(1, 7, K)
+        if m < a:
+            lam = rng.uniform(1, 100, K)
+            fac = (lam + (1 - lam) / (1 + (src / T) ** n)) / lam
+        else:
+            lam = 1.0 / rng.uniform(1, 100, K)
+            fac = lam + (1 - lam) / (1 + (src / T) ** n)
+        lvl = lvl * fac
+    assert stats.ks_2samp(mine, lvl).pvalue > 1e-4
+    assert O.median(a, b) == pytest.approx(np.median(lvl), rel=0.05)
+
+
+# ------------------------------------------------------------------ DP5
+def rand_params(net, seed):
+    rng = np.random.default_rng(seed)
+    N, E = net.n_nodes, net.n_edges
+    lam = np.where(net.sign > 0, rng.uniform(1, 10, E), rng.uniform(0.05, 1, E))
+    return handmade(net, rng.uniform(5, 50, N), rng.uniform(0.2, 1, N),
+                    rng.uniform(3, 30, E), lam, rng.integers(1, 5, E))
+
+
+def test_single_node_closed_form_series():
+    one = O.Network(1, [], [], [])
+    G, k, x0 = 37.0, 0.3, 2.0
+    p = O.ParamSet(np.array([[G]]), np.array([[k]]), np.zeros((1, 0)), np.zeros((1, 0)),
+                   np.zeros((1, 0), np.int32))
+    grid = np.linspace(0, 20, 41)
+    r = O.solve(one, p, [x0], t_end=20.0, ss_tol=0.0, t_grid=grid)
+    exact = G / k + (x0 - G / k) * np.exp(-k * grid)
+    assert np.max(np.abs(r["series"][:, 0] - exact) / exact) < 1e-9
+    assert r["status"] == O.TEND
+
+
+def test_single_step_matches_scipy_rk45():
+    """One Dormand-Prince step equals scipy's RK45 step (same tableau)."""
+    net = O.Network(*W.random_network(4, 3, 6, 3, 1).edges())
+    p = rand_params(net, 4)
+    f = model_rhs(net, p.G[0], p.k[0], p.T[0], p.lam[0], p.n[0])
+    x0 = np.array([3.0, 20.0, 9.0])
+    h = 0.05
+    r = O.solve(net, p, x0, t_end=h, h_fixed=h)
+    s = integrate.RK45(f, 0.0, x0, 10.0, first_step=h, rtol=1e-3, atol=1e-6)
+    s.step()
+    assert s.t == pytest.approx(h, rel=1e-15)
+    assert np.allclose(r["x"], s.y, rtol=1e-13, atol=0)
+
+
+def test_adaptive_sequence_matches_scipy_rk45():
+    """Same error estimate, norm, controller and starting step as scipy RK45:
+    the accepted-step counts agree and the end states agree."""
+    net = O.Network(*W.random_network(8, 3, 6, 3, 0).edges())
+    p = rand_params(net, 8)
+    f = model_rhs(net, p.G[0], p.k[0], p.T[0], p.lam[0], p.n[0])
+    x0 = np.array([1.0, 30.0, 5.0])
+    for rtol, atol in [(1e-4, 1e-7), (1e-6, 1e-9)]:
+        r = O.solve(net, p, x0, t_end=3.0, ss_tol=0.0, rtol=rtol, atol=atol)
+        sol = integrate.solve_ivp(f, (0, 3.0), x0, method="RK45", rtol=rtol, atol=atol)
+        n_scipy = sol.t.size - 1
+        assert abs(r["n_accepted"] - n_scipy) <= max(2, 0.05 * n_scipy)
+        assert np.allclose(r["x"], sol.y[:, -1], rtol=50 * rtol)
+
+
+def test_fixed_step_order_five():
+    net = O.Network(*W.toggle_switch_self_activation().edges())
+    p = rand_params(net, 3)
+    f = model_rhs(net, p.G[0], p.k[0], p.T[0], p.lam[0], p.n[0])
+    x0 = np.array([2.0, 15.0])
+    ref = integrate.solve_ivp(f, (0, 1.0), x0, method="DOP853", rtol=1e-13, atol=1e-13).y[:, -1]
+    errs = [np.max(np.abs(O.solve(net, p, x0, t_end=1.0, h_fixed=h)["x"] - ref)) for h in (0.1, 0.05, 0.025)]
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert all(4.5 < q < 5.6 for q in orders), orders
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_trajectory_vs_dop853_and_rk4(seed):
+    n = 1 + seed % 3
+    n_edges = {1: 1, 2: 2, 3: 4}[n]
+    net = O.Network(*W.random_network(seed, n, n_edges, min(1, n_edges - 1), 1).edges())
+    p = rand_params(net, seed)
+    f = model_rhs(net, p.G[0], p.k[0], p.T[0], p.lam[0], p.n[0])
+    x0 = np.linspace(1.0, 20.0, n)
+    grid = np.linspace(0, 2.0, 9)
+    r = O.solve(net, p, x0, t_end=2.0, ss_tol=0.0, t_grid=grid)
+    ref = integrate.solve_ivp(f, (0, 2.0), x0, method="DOP853", rtol=1e-13, atol=1e-12,
+                              t_eval=grid).y.T
+    assert np.max(np.abs(r["series"] - ref) / np.abs(ref)) < 1e-8
+    # brute-force classical RK4, h = 1e-4
+    x, h = x0.copy(), 1e-4
+    for _ in range(20000):
+        a = f(0, x); b = f(0, x + h / 2 * a); c = f(0, x + h / 2 * b); d = f(0, x + h * c)
+        x = x + h / 6 * (a + 2 * b + 2 * c + d)
+    assert np.max(np.abs(r["series"][-1] - x) / np.abs(x)) < 1e-9
+
+
+def test_invariants_positive_and_bounded():
+    net = O.Network(*W.random_network(12, 5, 10, 5, 0).edges())
+    p = O.sample_params(net, 5, 30)
+    u = O.sample_ics(5, 5, 4)
+    grid = np.linspace(0, 50, 51)
+    for s in range(30):
+        Gk = p.G[s] / p.k[s]
+        for c in range(4):
+            r = O.solve(net, p, u[c] * Gk, s=s, rtol=1e-8, atol=1e-11, t_end=50.0,
+                        ss_tol=0.0, t_grid=grid)
+            assert np.all(r["series"] > 0)
+            assert np.all(r["series"] <= Gk * (1 + 1e-9))
+
+
+def test_steady_state_stop_and_cascade_closed_form():
+    for sign, lam in [(+1, 6.0), (-1, 0.05)]:
+        net = O.Network(*W.cascade(sign).edges())
+        p = handmade(net, [12.0, 40.0], [0.4, 0.8], [9.0], [lam], [4])
+        r = O.solve(net, p, [1.0, 1.0], ss_tol=1e-6)
+        assert r["status"] == O.CONVERGED and r["t_final"] < 200.0
+        assert O.rho(net, p, r["x"]) < 1e-6
+        pl = O.polish(net, p, r["x"])
+        A = 12.0 / 0.4
+        H = O.shifted_hill(A, 9.0, 4, lam)
+        B = 40.0 / 0.8 * (H / lam if sign > 0 else H)
+        assert pl["rc"] == 0 and pl["rho"] < 1e-13
+        assert pl["x"] == pytest.approx([A, B], rel=1e-12)
+
+
+def test_polish_reaches_long_time_limit():
+    net = O.Network(*W.random_network(21, 4, 7, 3, 1).edges())
+    p = rand_params(net, 21)
+    f = model_rhs(net, p.G[0], p.k[0], p.T[0], p.lam[0], p.n[0])
+    x0 = np.array([2.0, 8.0, 30.0, 1.0])
+    r = O.solve(net, p, x0, ss_tol=1e-6, t_end=500.0)
+    assert r["status"] == O.CONVERGED
+    pl = O.polish(net, p, r["x"])
+    ref = integrate.solve_ivp(f, (0, 400.0), x0, method="DOP853", rtol=1e-13, atol=1e-13).y[:, -1]
+    assert pl["rc"] == 0
+    assert np.allclose(pl["x"], ref, rtol=1e-9)
+    assert not np.allclose(r["x"], ref, rtol=1e-12)   # the polish did something
+
+
+def test_symmetric_toggle_switch_bistable():
+    net = O.Network(*W.toggle_switch().edges())
+    p = handmade(net, [50.0, 50.0], [1.0, 1.0], [10.0, 10.0], [0.01, 0.01], [4, 4])
+    a = O.polish(net, p, O.solve(net, p, [40.0, 1.0])["x"])["x"]
+    b = O.polish(net, p, O.solve(net, p, [1.0, 40.0])["x"])["x"]
+    assert a[0] == pytest.approx(b[1], rel=1e-10) and a[1] == pytest.approx(b[0], rel=1e-10)
+    assert a[0] > 10 * a[1]
+
+
+# ------------------------------------------------------------------ dedupe
+def brute_dedupe(states, status, G, k, tol):
+    v = states * k / G
+    reps, ids = [], []
+    for c in range(len(states)):
+        if status[c] != 0:
+            ids.append(-1)
+            continue
+        hit = [r for r, rc in enumerate(reps) if np.max(np.abs(v[c] - v[rc])) <= tol]
+        if hit:
+            ids.append(hit[0])
+        else:
+            reps.append(c)
+            ids.append(len(reps) - 1)
+    return np.array(ids), len(reps)
+
+
+def test_dedupe_brute_force_and_properties():
+    rng = np.random.default_rng(0)
+    for trial in range(300):
+        N, I = rng.integers(1, 5), rng.integers(1, 12)
+        G, k = rng.uniform(1, 100, N), rng.uniform(0.1, 1, N)
+        centres = rng.uniform(0, 1, (3, N))
+        v = centres[rng.integers(0, 3, I)] + rng.normal(0, 0.004, (I, N))
+        states = v * G / k
+        status = (rng.uniform(size=I) < 0.15).astype(np.uint8)
+        sid, nu = O.dedupe(states, status, G, k, tol=1e-2)
+        bid, bnu = brute_dedupe(states, status, G, k, 1e-2)
+        assert nu == bnu and np.array_equal(sid, bid)
+        vv = states * k / G
+        reps = [np.where(sid == r)[0][0] for r in range(nu)]
+        for c in range(I):
+            if sid[c] >= 0:
+                assert np.max(np.abs(vv[c] - vv[reps[sid[c]]])) <= 1e-2
+        for a in range(nu):
+            for b in range(a):
+                assert np.max(np.abs(vv[reps[a]] - vv[reps[b]])) > 1e-2
+
+
+def test_dedupe_ties_and_first_representative():
+    G = np.array([1.0, 1.0]); k = np.array([1.0, 1.0])
+    tol = 2.0**-7
+    states = np.array([[0.25, 0.5], [0.25 + tol, 0.5], [0.25 + 2 * tol, 0.5],
+                       [0.25 + tol, 0.5 + tol]])
+    sid, nu = O.dedupe(states, np.zeros(4, np.uint8), G, k, tol=tol)
+    assert list(sid) == [0, 0, 1, 0] and nu == 2
+    # a state within tol of two representatives joins the first
+    states = np.array([[0.0, 0.0], [0.0, 2 * tol], [0.0, tol]])
+    sid, nu = O.dedupe(states, np.zeros(3, np.uint8), G, k, tol=tol)
+    assert list(sid) == [0, 1, 0] and nu == 2
+    sid, nu = O.dedupe(states, np.array([1, 0, 0], np.uint8), G, k, tol=tol)
+    assert list(sid) == [-1, 0, 0] and nu == 1
