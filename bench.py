@@ -1,0 +1,339 @@
+"""RACIPE ensemble benchmark: steady-state solves per second on one GB300.
+
+Workload (one "step" = the whole hot path over one batch): the seeded random
+22-node / 82-edge signed network (33 inhibitory edges, 3 self-activations;
+stand-in for the paper's EMT network, Sec. 3.2), 100,000 parameter sets x 10
+initial conditions = 1,000,000 solves per step:
+  sample parameters + ICs -> FP32 Dormand-Prince 5(4) to steady state ->
+  FP64 Newton polish -> distinct steady states per set.
+Under torchrun each rank integrates its own 100,000 sets (set offset rank x
+100,000; weak scaling, no collective on the data path).
+
+Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle (the
+plain FP64 implementation under oracle/) on a bounded sample instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_SETS = 100_000
+N_ICS = 10
+TOL = dict(rtol=1e-6, atol=1e-9, t_end=200.0, ss_tol=1e-6)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--sets", type=int, default=N_SETS)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sets", type=int, default=24, help="sets of the oracle sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"])
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.th.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0])); smax.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return dict(sm_mhz=statistics.median(sm) if sm else None,
+                    sm_max_mhz=max(smax) if smax else None, reasons=sorted(reasons),
+                    samples=len(sm))
+
+
+# ------------------------------------------------------------ CPU baseline
+def oracle_sample(n_sets, threads):
+    """The oracle as it stands on the first n_sets sets of the workload."""
+    import numpy as np
+    import oracle as O
+    from paper_2503_18356_gb300 import workloads as W
+    w = W.net22_workload()
+    net = O.Network(*w["topology"].edges())
+    p = O.sample_params(net, w["param_seed"], n_sets)
+    ic = O.sample_ics(w["topology"].n_nodes, w["ic_seed"], N_ICS)
+    t0 = time.perf_counter()
+    out = O.run_sets_parallel(net, p, ic, threads=threads)
+    dt = time.perf_counter() - t0
+    return n_sets * N_ICS / dt, dt, out
+
+
+def cpu_baseline(n_sets):
+    threads = os.cpu_count() or 1
+    v, dt, _ = oracle_sample(n_sets, threads)
+    return dict(value=v, unit="solves/s", cores=threads, kind="oracle",
+                sample="sets 0..%d of the workload x %d ICs (%d solves), FP64 DP5 rtol 1e-10 + "
+                       "Newton polish + dedupe, %.1f s" % (n_sets - 1, N_ICS, n_sets * N_ICS, dt))
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle as O
+    O.build()
+    for _ in range(args.warmup):
+        oracle_sample(max(2, args.cpu_sets // 4), os.cpu_count() or 1)
+    vals, times = [], []
+    for _ in range(args.steps):
+        v, dt, _ = oracle_sample(args.cpu_sets, os.cpu_count() or 1)
+        vals.append(v); times.append(dt)
+    total = args.cpu_sets * N_ICS * args.steps
+    value = total / sum(times)
+    cores = os.cpu_count() or 1
+    line = dict(impl="reference", metric="RACIPE steady-state solves/s (22-node network)",
+                value=value, unit="solves/s", n_gpus=args.gpus, steps=args.steps, warmup=args.warmup,
+                ms_per_step=1000 * sum(times) / args.steps, higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="f64", data="synthetic",
+                config=dict(workload="rand22x82: 22 nodes, 82 edges; %d sets x %d ICs per step "
+                                     "(bounded CPU sample of the 100000 x 10 workload)" % (args.cpu_sets, N_ICS)),
+                cpu_baseline=dict(value=value, unit="solves/s", cores=cores, kind="oracle",
+                                  sample="%d sets x %d ICs per step" % (args.cpu_sets, N_ICS)),
+                e2e=dict(value=value, unit="solves/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line))
+
+
+# ------------------------------------------------------------------ native
+def run_native(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    from paper_2503_18356_gb300 import build as B
+    B.build()
+    from paper_2503_18356_gb300 import api, workloads as W
+
+    w = W.net22_workload()
+    topo = w["topology"]
+    S, I, N, E = args.sets, N_ICS, topo.n_nodes, topo.n_edges
+    set0 = rank * S
+    h = api.Racipe.from_topology(topo, device=dev)
+    stream = torch.cuda.current_stream()
+    params = torch.empty((S, h.param_stride), dtype=torch.uint8, device=dev)
+    ic = torch.empty((I, N), dtype=torch.float64, device=dev)
+    out = dict(states=torch.empty((S, I, N), dtype=torch.float64, device=dev),
+               status=torch.empty((S, I), dtype=torch.uint8, device=dev),
+               t_final=torch.empty((S, I), dtype=torch.float64, device=dev),
+               err_est=torch.empty((S, I), dtype=torch.float32, device=dev),
+               n_steps=torch.empty((S, I), dtype=torch.int32, device=dev), series=None)
+    sid = torch.empty((S, I), dtype=torch.int32, device=dev)
+    nu = torch.empty((S,), dtype=torch.int32, device=dev)
+    opts = api.default_opts(precision=api.GRINS_FP32, polish=0, **TOL)
+    popts = api.default_opts()
+
+    def step(ev=None):
+        if ev: ev[0].record(stream)
+        h.sample_params(w["param_seed"], S, I, set0=set0, params=params, ic_unit=ic, stream=stream)
+        if ev: ev[1].record(stream)
+        h.integrate(params, ic, opts=opts, stream=stream, out=out)
+        if ev: ev[2].record(stream)
+        h.polish(params, out["states"], out["status"], out["err_est"], opts=popts, stream=stream)
+        if ev: ev[3].record(stream)
+        h.unique_states(params, out["states"], out["status"], stream=stream, out=(sid, nu))
+        if ev: ev[4].record(stream)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+            torch.cuda.synchronize()
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    barrier()
+
+    clk = ClockSampler(torch.cuda.current_device())
+    clk.start()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    barrier()
+    start.record(stream)
+    for k in range(args.steps):
+        step(evs[k])
+    stop.record(stream)
+    barrier()
+    clocks = clk.stop()
+    elapsed_ms = start.elapsed_time(stop)
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([elapsed_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    per_kernel = np.array([[e[i].elapsed_time(e[i + 1]) for i in range(4)] for e in evs])  # ms
+    kern_ms = per_kernel.mean(axis=0)
+
+    # algorithmic work of the FP32 integrator (per step attempt of one solve)
+    attempts = int(out["n_steps"].sum().item())
+    status = out["status"].cpu().numpy()
+    w32 = 35 * E + 45 * N
+    wsfu = 6 * E + N
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    f_mhz = clocks.get("sm_mhz") or 1440.0
+    t_int = kern_ms[1] / 1e3
+    sfu_bound = wsfu / 16.0 >= w32 / 128.0
+    if sfu_bound:
+        achieved = attempts * wsfu / t_int / 1e9
+        peak = 16 * sms * f_mhz * 1e6 / 1e9
+        unit = "Gop/s (MUFU, SFU pipe)"
+    else:
+        achieved = attempts * w32 / t_int / 1e9
+        peak = 128 * sms * f_mhz * 1e6 / 1e9
+        unit = "Gop/s (FP32 pipe)"
+
+    solves = S * I * ws
+    value = solves * args.steps / (elapsed_ms / 1e3)
+
+    # end to end through the C ABI with host buffers: create from the host edge
+    # list, run the path, copy every result back to pinned host memory.
+    host = dict(states=torch.empty((S, I, N), dtype=torch.float64, pin_memory=True),
+                status=torch.empty((S, I), dtype=torch.uint8, pin_memory=True),
+                sid=torch.empty((S, I), dtype=torch.int32, pin_memory=True),
+                nu=torch.empty((S,), dtype=torch.int32, pin_memory=True))
+    h2d = 4 * E * 2 + E
+    d2h = sum(t.numel() * t.element_size() for t in host.values())
+
+    def e2e_step():
+        hh = api.Racipe.from_topology(topo, device=dev)
+        hh.sample_params(w["param_seed"], S, I, set0=set0, params=params, ic_unit=ic, stream=stream)
+        hh.integrate(params, ic, opts=opts, stream=stream, out=out)
+        hh.polish(params, out["states"], out["status"], out["err_est"], opts=popts, stream=stream)
+        hh.unique_states(params, out["states"], out["status"], stream=stream, out=(sid, nu))
+        host["states"].copy_(out["states"], non_blocking=True)
+        host["status"].copy_(out["status"], non_blocking=True)
+        host["sid"].copy_(sid, non_blocking=True)
+        host["nu"].copy_(nu, non_blocking=True)
+        torch.cuda.synchronize()
+        hh.close()
+
+    e2e_step()
+    barrier()
+    t0 = time.perf_counter()
+    e2e_steps = max(1, min(args.steps, 3))
+    for _ in range(e2e_steps):
+        e2e_step()
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = solves * e2e_steps / e2e_s
+
+    if rank == 0:
+        line = dict(
+            metric="RACIPE steady-state solves/s (22-node network, FP32 + FP64 polish)",
+            value=value, unit="solves/s", n_gpus=ws, steps=args.steps, warmup=max(3, args.warmup),
+            ms_per_step=elapsed_ms / args.steps, higher_is_better=True, scaling="weak",
+            vs_baseline=None, dtype="f32", data="synthetic",
+            config=dict(workload="rand22x82: seeded random signed network, 22 nodes, 82 edges "
+                                 "(33 inhibitory, 3 self-activations); %d sets x %d ICs per GPU" % (S, I),
+                        solver="Dormand-Prince 5(4) FP32, rtol 1e-6, atol 1e-9, t_end 200, "
+                               "ss_tol 1e-6; FP64 Newton polish; dedupe tol 1e-2",
+                        l2="inputs larger than L2: parameter block %.0f MB, states %.0f MB" % (
+                            S * h.param_stride / 1e6, S * I * N * 8 / 1e6),
+                        parallelism="dp%d (sets sharded by rank)" % ws),
+            kernel_ms=dict(sample=kern_ms[0], integrate_fp32=kern_ms[1], polish_fp64=kern_ms[2],
+                           unique=kern_ms[3]),
+            step_attempts_per_solve=attempts / (S * I),
+            status_hist=np.bincount(status.ravel(), minlength=5).tolist(),
+            roofline=dict(bound="alu", achieved=achieved, peak=peak, unit=unit, frac=achieved / peak,
+                          traffic=None, kernel="dp5_kernel<float,24> (FP32 integrator)",
+                          peak_basis="%d SMs x %s lanes/clk x %.0f MHz (median SM clock sampled in the "
+                                     "timed region)" % (sms, "16 SFU" if sfu_bound else "128 FP32", f_mhz),
+                          work_per_attempt=dict(fp32=w32, sfu=wsfu)),
+            e2e=dict(value=e2e_value, unit="solves/s", h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h),
+            gpu_launches=5 * args.steps,
+            clocks=clocks)
+        if not args.no_cpu_baseline and ws == 1:
+            line["cpu_baseline"] = cpu_baseline(args.cpu_sets)
+        print(json.dumps(line))
+    h.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,221 @@
+/*
+ * grins_racipe.h -- C ABI of the GB300 RACIPE ensemble solver
+ * (libgrins_racipe.so).
+ *
+ * RACIPE (GRiNS, arXiv 2503.18356, Sec. 2.1) integrates, for a fixed signed
+ * directed gene-regulatory network, one trajectory of the node equation
+ * (Eq. 1, with the shifted Hill function of Eq. 2) per pair (random
+ * parameter set, random initial condition), runs it to steady state, and
+ * reduces each parameter set's results to its distinct steady states.
+ *
+ * Conventions shared by every entry point
+ *   - Plain C types only.  "d_" arguments are DEVICE pointers (CUDA global
+ *     memory of the current device), everything else is host memory.
+ *   - Every device buffer is owned by the caller; the library never frees
+ *     it and never keeps it after the call returns.  The handle owns its
+ *     own copy of the topology, the half-functional median table and a
+ *     small device workspace (work-queue counters).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls that launch kernels are asynchronous on that stream;
+ *     results are valid once the stream reaches the call's work.
+ *   - Argument errors are reported before any work is queued, with a
+ *     status other than GRINS_OK and a message for grins_last_error().
+ *     CUDA launch or allocation failures return GRINS_E_CUDA / GRINS_E_NOMEM.
+ *     The outcome of each individual solve is never an error: it is written
+ *     to that solve's status byte (grins_solve_status).
+ *   - A handle may be used from one host thread at a time.  Distinct handles
+ *     are independent.
+ *
+ * Layout of one parameter set (2N + 3E values, Sec. 2.1.2), in the byte
+ * block d_params[set * grins_racipe_param_stride(h) ...]:
+ *     double G[N]      production rate of node i
+ *     double k[N]      degradation rate of node i
+ *     double T[E]      threshold of edge e (edge order = creation order)
+ *     double lam[E]    fold change of edge e (>= 1 activating, <= 1 inhibiting)
+ *     uint8  n[E]      integer Hill coefficient of edge e
+ *     (zero padding to a multiple of 16 bytes)
+ * Unit initial conditions: double u[n_ics][N] in [0, 1); solve (s, c) starts
+ * from x0_i = (u[c][i] * G_i) / k_i (Sec. 2.1.2: between a node's minimum 0
+ * and maximum G/k; the same ICs serve every parameter set, Sec. 3.1).
+ */
+#ifndef GRINS_RACIPE_H
+#define GRINS_RACIPE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct grins_racipe *grins_racipe_t;   /* opaque, library-owned */
+
+typedef enum {
+    GRINS_OK = 0,
+    GRINS_E_INVALID_ARG = 1,   /* null pointer, bad size, bad option value */
+    GRINS_E_TOPOLOGY = 2,      /* invalid edge list */
+    GRINS_E_NOMEM = 3,         /* host or device allocation failed */
+    GRINS_E_CUDA = 4,          /* a CUDA call or kernel launch failed */
+    GRINS_E_BUDGET = 5,        /* request exceeds a documented limit */
+    GRINS_E_CANCELLED = 6
+} grins_status;
+
+/* Per-solve outcome, one byte per (set, IC). */
+typedef enum {
+    GRINS_SS_CONVERGED = 0,    /* steady-state condition met (Sec. 2.1.3) */
+    GRINS_SS_TEND = 1,         /* reached t_end first */
+    GRINS_SS_MAXSTEPS = 2,     /* spent max_steps step attempts */
+    GRINS_SS_NONFINITE = 3,    /* NaN/Inf or step-size underflow */
+    GRINS_SS_POLISH_FAIL = 4   /* converged, but the FP64 polish did not certify it;
+                                  the unpolished state is returned */
+} grins_solve_status;
+
+enum { GRINS_FP64 = 0, GRINS_FP32 = 1 };                       /* precision */
+enum { GRINS_MEDIAN_PER_INDEGREE = 0, GRINS_MEDIAN_UNREGULATED = 1 };
+
+/* Sampling ranges, Table 1 (Sec. 2.1.2).  grins_racipe_default_ranges fills
+ * the defaults: G [1,100], k [0.1,1], activating lambda [1,100], inhibiting
+ * lambda [0.01,1] (drawn in the inverse range and inverted), integer n [1,6],
+ * thresholds in [0.02, 1.98] x the median level of the source node (the
+ * half-functional rule), 10000 samples per median, per-in-degree medians. */
+typedef struct {
+    double G_min, G_max;
+    double k_min, k_max;
+    double lam_act_min, lam_act_max;
+    double lam_inh_min, lam_inh_max;
+    int32_t n_min, n_max;
+    double thr_lo, thr_hi;
+    int32_t median_samples;
+    int32_t median_mode;       /* GRINS_MEDIAN_* */
+} grins_racipe_ranges;
+
+/* Solver controls (Sec. 2.1.3: tolerances, start and end time, stop at
+ * steady state, optional time points).  grins_solver_default_opts fills:
+ * FP32 + polish, rtol 1e-6, atol 1e-9, t0 0, t_end 200, ss_tol 1e-6,
+ * max_steps 100000, no time grid, polish_tol 1e-12, polish_iters 4,
+ * polish_max_move 1e-2. */
+typedef struct {
+    int32_t precision;         /* GRINS_FP32 or GRINS_FP64 integration */
+    int32_t polish;            /* 1: FP64 Newton polish of each converged state */
+    double rtol, atol;         /* Dormand-Prince 5(4) local error tolerances */
+    double t0, t_end;
+    double ss_tol;             /* converged when max_i |dx_i/dt| / (G_i/k_i) < ss_tol */
+    int64_t max_steps;         /* step attempts (accepted + rejected) per solve */
+    const double *t_grid;      /* HOST pointer to n_t increasing times in [t0, t_end];
+                                  NULL / 0 = no time series */
+    int32_t n_t;
+    double polish_tol;         /* polish succeeds when the FP64 residual < polish_tol */
+    int32_t polish_iters;      /* Newton iterations at most */
+    double polish_max_move;    /* reject a polish that moves a G/k-normalised
+                                  coordinate by more than this */
+} grins_solver_opts;
+
+void grins_racipe_default_ranges(grins_racipe_ranges *r);
+void grins_solver_default_opts(grins_solver_opts *o);
+
+/* Thread-local message of the last failing call on this thread ("" if none). */
+const char *grins_last_error(void);
+
+/* Library version string. */
+const char *grins_version(void);
+
+/* Builds a handle from a signed, directed edge list (Sec. 2.1.1; the parser
+ * accepts activation and inhibition links only).  Host arrays of length
+ * n_edges: src[e] -> dst[e] with sign[e] = +1 (activation) or -1
+ * (inhibition).  They are copied.  Self-loops are allowed.
+ * Errors: GRINS_E_TOPOLOGY for n_nodes < 1 or > 64, n_edges < 0 or > 4096,
+ * an index out of range, a sign other than +1/-1, or a repeated (src, dst)
+ * pair; GRINS_E_INVALID_ARG for null pointers; GRINS_E_CUDA / NOMEM when
+ * the device workspace cannot be created.  Uses the current CUDA device. */
+grins_status grins_racipe_create(int32_t n_nodes, int32_t n_edges, const int32_t *src,
+                                 const int32_t *dst, const int8_t *sign,
+                                 grins_racipe_t *out);
+
+/* Frees the handle and its device workspace (synchronises the device). */
+grins_status grins_racipe_destroy(grins_racipe_t h);
+
+/* Bytes per parameter set in d_params (see the layout above); -1 on a
+ * null handle. */
+int64_t grins_racipe_param_stride(grins_racipe_t h);
+
+/* Host copy of the per-node median levels M_j used by the half-functional
+ * threshold rule for the given ranges (NULL = defaults): out[n_nodes].
+ * M_j depends on node j's in-degree class (#activating, #inhibiting
+ * inputs), Sec. 2.1.2 and Table 1 threshold row. */
+grins_status grins_racipe_node_medians(grins_racipe_t h, const grins_racipe_ranges *r,
+                                       double *out);
+
+/* Samples parameter sets set0 .. set0+n_sets-1 into d_params (bytes
+ * [n_sets][param_stride]) and, if d_ic_unit is not NULL, the unit initial
+ * conditions d_ic_unit[n_ics][N] (doubles), following Sec. 2.1.2 and
+ * Table 1 (r = NULL: defaults).  Counter-based: set s is the same whether
+ * it is drawn alone or in any batch, on any device.  Errors:
+ * GRINS_E_INVALID_ARG for bad ranges (min > max, non-positive G/k/lambda
+ * bounds, activating lambda below 1, inhibiting lambda above 1, n outside
+ * [1, 255], median_samples < 1), n_sets < 0, set0 < 0, n_ics < 0, or a
+ * null d_params with n_sets > 0. */
+grins_status grins_racipe_sample_params(grins_racipe_t h, const grins_racipe_ranges *r,
+                                        uint64_t seed, int64_t set0, int64_t n_sets,
+                                        int32_t n_ics, void *d_params, double *d_ic_unit,
+                                        void *stream);
+
+/* Integrates every (set, IC) pair: n_sets parameter sets from d_params
+ * (layout above) times n_ics unit ICs, with Dormand-Prince 5(4) (FSAL,
+ * per-solve step control) until the steady-state condition, t_end or
+ * max_steps; then (o->polish) an FP64 Newton polish of each converged
+ * state.  Outputs, indexed [set][ic]:
+ *   d_states  double [n_sets][n_ics][N]  final (polished) state
+ *   d_status  uint8  [n_sets][n_ics]     grins_solve_status
+ *   d_t_final double [n_sets][n_ics]     time at termination   (nullable)
+ *   d_err_est float  [n_sets][n_ics]     G/k-normalised size of the last
+ *                                        polish step; -1 if not polished (nullable)
+ *   d_n_steps int32  [n_sets][n_ics]     step attempts           (nullable)
+ *   d_series  double [n_sets][n_ics][n_t][N] states at o->t_grid (required
+ *                                        iff n_t > 0); grid times after
+ *                                        termination hold the final state
+ * Errors: GRINS_E_INVALID_ARG for null required pointers, n_ics < 1,
+ * n_sets < 0, non-positive tolerances, t_end <= t0, a grid that is not
+ * increasing inside [t0, t_end], or max_steps < 1. */
+grins_status grins_racipe_integrate(grins_racipe_t h, const grins_solver_opts *o,
+                                    const void *d_params, int64_t n_sets,
+                                    const double *d_ic_unit, int32_t n_ics,
+                                    double *d_states, uint8_t *d_status, double *d_t_final,
+                                    float *d_err_est, int32_t *d_n_steps, double *d_series,
+                                    void *stream);
+
+/* FP64 Newton polish of states already integrated (the step integrate runs
+ * when o->polish is set; exposed so a caller can polish separately).  For
+ * every solve with status GRINS_SS_CONVERGED: Newton iterations on Eq. 1 = 0
+ * in double precision with the analytic Jacobian, until the residual
+ * max_i |f_i| / (G_i / k_i) < o->polish_tol (at most o->polish_iters steps).
+ * Success overwrites d_states[set][ic][:] and writes the G/k-normalised size
+ * of the last Newton step to d_err_est (nullable); failure (singular
+ * Jacobian, a step moving a normalised coordinate by more than
+ * o->polish_max_move, or no convergence) keeps the state and sets the status
+ * to GRINS_SS_POLISH_FAIL.  Other statuses are left alone (err_est = -1).
+ * Only the polish_* fields of o are read.  Errors: GRINS_E_INVALID_ARG for
+ * null pointers, n_ics < 1, n_sets < 0 or bad polish options. */
+grins_status grins_racipe_polish(grins_racipe_t h, const grins_solver_opts *o,
+                                 const void *d_params, int64_t n_sets, int32_t n_ics,
+                                 double *d_states, uint8_t *d_status, float *d_err_est,
+                                 void *stream);
+
+/* Distinct steady states per parameter set (Sec. 3.1: multistability is
+ * the number of unique steady states a set reaches over its ICs).  States
+ * are G/k-normalised (Sec. 2.1.3), v_i = (x_i * k_i) / G_i in FP64; in IC
+ * order, each converged state joins the first representative whose
+ * max-norm distance is <= tol, else it becomes a new one.
+ *   d_state_id int32 [n_sets][n_ics]  representative index, -1 unless converged
+ *   d_n_unique int32 [n_sets]         number of representatives
+ * Deterministic and independent of launch shape.  Errors:
+ * GRINS_E_INVALID_ARG for null pointers, n_ics < 1 or > 4096, tol < 0. */
+grins_status grins_racipe_unique_states(grins_racipe_t h, const void *d_params,
+                                        const double *d_states, const uint8_t *d_status,
+                                        int64_t n_sets, int32_t n_ics, double tol,
+                                        int32_t *d_state_id, int32_t *d_n_unique,
+                                        void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GRINS_RACIPE_H */

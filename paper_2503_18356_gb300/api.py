@@ -1,0 +1,248 @@
+"""Thin Python binding of libgrins_racipe.so (the C ABI in include/grins_racipe.h).
+
+Argument marshalling only: every step of the path runs in the library's CUDA
+kernels.  Device buffers are torch CUDA tensors allocated here; the CUDA
+stream is torch's current stream unless one is given.  The library must be
+built (``paper_2503_18356_gb300.build.build()``); importing this module
+raises if it is missing -- there is no fallback.
+
+Low-level functions carry the C names (``grins_racipe_create``, ...); the
+``Racipe`` class wraps a handle for everyday use.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+# GRINS_RACIPE_LIB selects another build of the same library (the tests use it
+# to load the index-checked variant); the default is the in-tree release build.
+LIB_PATH = os.environ.get("GRINS_RACIPE_LIB") or os.path.join(_HERE, "libgrins_racipe.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libgrins_racipe.so is not built; run paper_2503_18356_gb300.build.build()")
+
+_lib = C.CDLL(LIB_PATH)
+
+GRINS_OK, GRINS_E_INVALID_ARG, GRINS_E_TOPOLOGY, GRINS_E_NOMEM, GRINS_E_CUDA, GRINS_E_BUDGET, \
+    GRINS_E_CANCELLED = range(7)
+CONVERGED, TEND, MAXSTEPS, NONFINITE, POLISH_FAIL = range(5)
+GRINS_FP64, GRINS_FP32 = 0, 1
+MEDIAN_PER_INDEGREE, MEDIAN_UNREGULATED = 0, 1
+
+
+class grins_racipe_ranges(C.Structure):
+    _fields_ = [("G_min", C.c_double), ("G_max", C.c_double),
+                ("k_min", C.c_double), ("k_max", C.c_double),
+                ("lam_act_min", C.c_double), ("lam_act_max", C.c_double),
+                ("lam_inh_min", C.c_double), ("lam_inh_max", C.c_double),
+                ("n_min", C.c_int32), ("n_max", C.c_int32),
+                ("thr_lo", C.c_double), ("thr_hi", C.c_double),
+                ("median_samples", C.c_int32), ("median_mode", C.c_int32)]
+
+
+class grins_solver_opts(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("polish", C.c_int32),
+                ("rtol", C.c_double), ("atol", C.c_double),
+                ("t0", C.c_double), ("t_end", C.c_double), ("ss_tol", C.c_double),
+                ("max_steps", C.c_int64),
+                ("t_grid", C.POINTER(C.c_double)), ("n_t", C.c_int32),
+                ("polish_tol", C.c_double), ("polish_iters", C.c_int32),
+                ("polish_max_move", C.c_double)]
+
+
+_H = C.c_void_p
+_P = C.c_void_p
+_S = C.c_int32
+
+_sig = {
+    "grins_racipe_default_ranges": (None, [C.POINTER(grins_racipe_ranges)]),
+    "grins_solver_default_opts": (None, [C.POINTER(grins_solver_opts)]),
+    "grins_last_error": (C.c_char_p, []),
+    "grins_version": (C.c_char_p, []),
+    "grins_racipe_create": (_S, [C.c_int32, C.c_int32, _P, _P, _P, C.POINTER(_H)]),
+    "grins_racipe_destroy": (_S, [_H]),
+    "grins_racipe_param_stride": (C.c_int64, [_H]),
+    "grins_racipe_node_medians": (_S, [_H, C.POINTER(grins_racipe_ranges), _P]),
+    "grins_racipe_sample_params": (_S, [_H, C.POINTER(grins_racipe_ranges), C.c_uint64, C.c_int64,
+                                        C.c_int64, C.c_int32, _P, _P, _P]),
+    "grins_racipe_integrate": (_S, [_H, C.POINTER(grins_solver_opts), _P, C.c_int64, _P, C.c_int32,
+                                    _P, _P, _P, _P, _P, _P, _P]),
+    "grins_racipe_polish": (_S, [_H, C.POINTER(grins_solver_opts), _P, C.c_int64, C.c_int32, _P, _P, _P, _P]),
+    "grins_racipe_unique_states": (_S, [_H, _P, _P, _P, C.c_int64, C.c_int32, C.c_double, _P, _P, _P]),
+}
+EXPORTED = tuple(_sig)
+for _name, (_res, _args) in _sig.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+    globals()[_name] = _f
+
+
+class GrinsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("grins status %d: %s" % (status, msg))
+        self.status = status
+
+
+def _check(st):
+    if st != GRINS_OK:
+        raise GrinsError(st, _lib.grins_last_error().decode())
+
+
+def default_ranges(**over) -> grins_racipe_ranges:
+    r = grins_racipe_ranges()
+    _lib.grins_racipe_default_ranges(C.byref(r))
+    for k, v in over.items():
+        setattr(r, k, v)
+    return r
+
+
+def default_opts(**over) -> grins_solver_opts:
+    o = grins_solver_opts()
+    _lib.grins_solver_default_opts(C.byref(o))
+    for k, v in over.items():
+        setattr(o, k, v)
+    return o
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+class Racipe:
+    """A RACIPE network handle (signed directed edge list, Sec. 2.1.1)."""
+
+    def __init__(self, n_nodes, src, dst, sign, device=None):
+        self.device = torch.device(device or "cuda")
+        self.n_nodes = int(n_nodes)
+        self.src = np.ascontiguousarray(src, dtype=np.int32)
+        self.dst = np.ascontiguousarray(dst, dtype=np.int32)
+        self.sign = np.ascontiguousarray(sign, dtype=np.int8)
+        self.n_edges = int(self.src.size)
+        h = _H()
+        with torch.cuda.device(self.device):
+            _check(_lib.grins_racipe_create(self.n_nodes, self.n_edges,
+                                            self.src.ctypes.data, self.dst.ctypes.data,
+                                            self.sign.ctypes.data, C.byref(h)))
+        self._h = h
+        self.param_stride = int(_lib.grins_racipe_param_stride(h))
+
+    @classmethod
+    def from_topology(cls, topo, device=None):
+        return cls(*topo.edges(), device=device)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.grins_racipe_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------ sampling
+    def node_medians(self, ranges=None):
+        out = np.zeros(self.n_nodes)
+        r = C.byref(ranges) if ranges is not None else None
+        _check(_lib.grins_racipe_node_medians(self._h, r, out.ctypes.data))
+        return out
+
+    def sample_params(self, seed, n_sets, n_ics, set0=0, ranges=None, stream=None, params=None,
+                      ic_unit=None):
+        """Returns (params uint8 [n_sets, stride], ic_unit float64 [n_ics, N])."""
+        if params is None:
+            params = torch.empty((n_sets, self.param_stride), dtype=torch.uint8, device=self.device)
+        if ic_unit is None and n_ics > 0:
+            ic_unit = torch.empty((n_ics, self.n_nodes), dtype=torch.float64, device=self.device)
+        r = C.byref(ranges) if ranges is not None else None
+        with torch.cuda.device(self.device):
+            _check(_lib.grins_racipe_sample_params(self._h, r, seed, set0, n_sets, n_ics, _ptr(params),
+                                                   _ptr(ic_unit), _stream(stream)))
+        return params, ic_unit
+
+    def unpack_params(self, params):
+        """Views of a parameter block: G, k [S, N]; T, lam [S, E] float64; n [S, E] uint8."""
+        N, E = self.n_nodes, self.n_edges
+        S = params.shape[0]
+        flat = params.view(S, -1)
+        f64 = flat[:, : 16 * N + 16 * E].contiguous().view(torch.float64)
+        G, k = f64[:, :N], f64[:, N:2 * N]
+        T, lam = f64[:, 2 * N:2 * N + E], f64[:, 2 * N + E:2 * N + 2 * E]
+        n = flat[:, 16 * N + 16 * E:16 * N + 17 * E]
+        return G, k, T, lam, n
+
+    def pack_params(self, G, k, T, lam, n):
+        """Inverse of unpack_params (device tensors or arrays) -> uint8 [S, stride]."""
+        G = torch.as_tensor(G, dtype=torch.float64, device=self.device)
+        S = G.shape[0]
+        f64 = torch.cat([G, torch.as_tensor(k, dtype=torch.float64, device=self.device),
+                         torch.as_tensor(T, dtype=torch.float64, device=self.device).reshape(S, -1),
+                         torch.as_tensor(lam, dtype=torch.float64, device=self.device).reshape(S, -1)],
+                        dim=1)
+        out = torch.zeros((S, self.param_stride), dtype=torch.uint8, device=self.device)
+        nb = f64.shape[1] * 8
+        out[:, :nb] = f64.contiguous().view(torch.uint8).view(S, nb)
+        out[:, nb:nb + self.n_edges] = torch.as_tensor(n, device=self.device).to(torch.uint8).reshape(S, -1)
+        return out
+
+    # ---------------------------------------------------------- integrate
+    def integrate(self, params, ic_unit, opts=None, stream=None, out=None, **over):
+        """Integrates every (set, IC); returns a dict of device tensors."""
+        o = opts if opts is not None else default_opts()
+        t_grid = over.pop("t_grid", None)
+        for k, v in over.items():
+            setattr(o, k, v)
+        grid = None
+        if t_grid is not None:
+            grid = np.ascontiguousarray(t_grid, dtype=np.float64)
+            o.t_grid = grid.ctypes.data_as(C.POINTER(C.c_double))
+            o.n_t = grid.size
+        S, I, N = params.shape[0], ic_unit.shape[0], self.n_nodes
+        dev = self.device
+        if out is None:
+            out = dict(states=torch.empty((S, I, N), dtype=torch.float64, device=dev),
+                       status=torch.empty((S, I), dtype=torch.uint8, device=dev),
+                       t_final=torch.empty((S, I), dtype=torch.float64, device=dev),
+                       err_est=torch.empty((S, I), dtype=torch.float32, device=dev),
+                       n_steps=torch.empty((S, I), dtype=torch.int32, device=dev),
+                       series=(torch.empty((S, I, o.n_t, N), dtype=torch.float64, device=dev)
+                               if o.n_t > 0 else None))
+        with torch.cuda.device(dev):
+            _check(_lib.grins_racipe_integrate(
+                self._h, C.byref(o), _ptr(params), S, _ptr(ic_unit), I, _ptr(out["states"]),
+                _ptr(out["status"]), _ptr(out.get("t_final")), _ptr(out.get("err_est")),
+                _ptr(out.get("n_steps")), _ptr(out.get("series")), _stream(stream)))
+        return out
+
+    def polish(self, params, states, status, err_est=None, opts=None, stream=None, **over):
+        """FP64 Newton polish in place of converged states (see grins_racipe_polish)."""
+        o = opts if opts is not None else default_opts()
+        for k, v in over.items():
+            setattr(o, k, v)
+        S, I = status.shape
+        with torch.cuda.device(self.device):
+            _check(_lib.grins_racipe_polish(self._h, C.byref(o), _ptr(params), S, I, _ptr(states),
+                                            _ptr(status), _ptr(err_est), _stream(stream)))
+        return states, status, err_est
+
+    def unique_states(self, params, states, status, tol=1e-2, stream=None, out=None):
+        S, I = status.shape
+        if out is None:
+            out = (torch.empty((S, I), dtype=torch.int32, device=self.device),
+                   torch.empty((S,), dtype=torch.int32, device=self.device))
+        with torch.cuda.device(self.device):
+            _check(_lib.grins_racipe_unique_states(self._h, _ptr(params), _ptr(states), _ptr(status),
+                                                   S, I, tol, _ptr(out[0]), _ptr(out[1]),
+                                                   _stream(stream)))
+        return out

@@ -1,0 +1,565 @@
+// Host side of the C ABI declared in include/grins_racipe.h: handle
+// lifetime, argument validation, the incoming-edge CSR, the half-functional
+// median table and the kernel launch sequence of each entry point.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+using namespace grins;
+
+// ------------------------------------------------------------------ errors
+static thread_local std::string g_last_error;
+
+static grins_status fail(grins_status s, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return s;
+}
+
+static grins_status cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(e == cudaErrorMemoryAllocation ? GRINS_E_NOMEM : GRINS_E_CUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+#define CUDA_TRY(expr, what)                                  \
+    do {                                                      \
+        cudaError_t _e = (expr);                              \
+        if (_e != cudaSuccess) return cuda_fail(_e, what);    \
+    } while (0)
+
+// ------------------------------------------------------------------ handle
+struct grins_racipe {
+    int N = 0, E = 0, device = 0, num_sms = 1;
+    size_t smem_optin = 0;
+    std::vector<int32_t> src, dst;
+    std::vector<int8_t> sign;
+    std::vector<int32_t> csr_off, csr_src, csr_edge;
+    std::vector<int8_t> csr_sign;
+    std::vector<int32_t> n_act_in, n_inh_in;          // in-degree class per node
+    ParamLayout layout{};
+    // device workspace
+    int32_t *d_off = nullptr, *d_src = nullptr, *d_edge = nullptr;
+    int8_t *d_sign = nullptr, *d_edge_sign = nullptr;
+    double *d_edge_median = nullptr;
+    unsigned long long *d_queue = nullptr;
+    double *d_grid = nullptr;
+    int grid_cap = 0;
+    // cached median table
+    bool median_valid = false;
+    grins_racipe_ranges median_ranges{};
+    std::vector<double> node_median;
+    bool median_uploaded = false;
+};
+
+extern "C" void grins_racipe_default_ranges(grins_racipe_ranges *r)
+{
+    if (!r) return;
+    r->G_min = 1.0; r->G_max = 100.0;
+    r->k_min = 0.1; r->k_max = 1.0;
+    r->lam_act_min = 1.0; r->lam_act_max = 100.0;
+    r->lam_inh_min = 0.01; r->lam_inh_max = 1.0;
+    r->n_min = 1; r->n_max = 6;
+    r->thr_lo = 0.02; r->thr_hi = 1.98;
+    r->median_samples = 10000;
+    r->median_mode = GRINS_MEDIAN_PER_INDEGREE;
+}
+
+extern "C" void grins_solver_default_opts(grins_solver_opts *o)
+{
+    if (!o) return;
+    o->precision = GRINS_FP32;
+    o->polish = 1;
+    o->rtol = 1e-6; o->atol = 1e-9;
+    o->t0 = 0.0; o->t_end = 200.0;
+    o->ss_tol = 1e-6;
+    o->max_steps = 100000;
+    o->t_grid = nullptr; o->n_t = 0;
+    o->polish_tol = 1e-12;
+    o->polish_iters = 4;
+    o->polish_max_move = 1e-2;
+}
+
+extern "C" const char *grins_last_error(void) { return g_last_error.c_str(); }
+extern "C" const char *grins_version(void) { return "grins_racipe 0.1 (sm_103a)"; }
+
+static void free_device(grins_racipe *h)
+{
+    cudaFree(h->d_off); cudaFree(h->d_src); cudaFree(h->d_edge); cudaFree(h->d_sign);
+    cudaFree(h->d_edge_sign); cudaFree(h->d_edge_median); cudaFree(h->d_queue); cudaFree(h->d_grid);
+    h->d_off = h->d_src = h->d_edge = nullptr;
+    h->d_sign = h->d_edge_sign = nullptr;
+    h->d_edge_median = h->d_grid = nullptr;
+    h->d_queue = nullptr;
+}
+
+extern "C" grins_status grins_racipe_create(int32_t n_nodes, int32_t n_edges, const int32_t *src,
+                                            const int32_t *dst, const int8_t *sign,
+                                            grins_racipe_t *out)
+{
+    g_last_error.clear();
+    if (!out) return fail(GRINS_E_INVALID_ARG, "create: out is NULL");
+    *out = nullptr;
+    if (n_nodes < 1 || n_nodes > kMaxNodes)
+        return fail(GRINS_E_TOPOLOGY, "create: n_nodes = %d outside [1, %d]", n_nodes, kMaxNodes);
+    if (n_edges < 0 || n_edges > kMaxEdges)
+        return fail(GRINS_E_TOPOLOGY, "create: n_edges = %d outside [0, %d]", n_edges, kMaxEdges);
+    if (n_edges > 0 && (!src || !dst || !sign)) return fail(GRINS_E_INVALID_ARG, "create: NULL edge array");
+    std::vector<char> seen((size_t)n_nodes * n_nodes, 0);
+    for (int e = 0; e < n_edges; ++e) {
+        if (src[e] < 0 || src[e] >= n_nodes || dst[e] < 0 || dst[e] >= n_nodes)
+            return fail(GRINS_E_TOPOLOGY, "create: edge %d (%d -> %d) has a node index outside [0, %d)", e,
+                        src[e], dst[e], n_nodes);
+        if (sign[e] != 1 && sign[e] != -1)
+            return fail(GRINS_E_TOPOLOGY, "create: edge %d has sign %d (must be +1 or -1)", e, (int)sign[e]);
+        char &s = seen[(size_t)src[e] * n_nodes + dst[e]];
+        if (s) return fail(GRINS_E_TOPOLOGY, "create: edge %d repeats the pair (%d -> %d)", e, src[e], dst[e]);
+        s = 1;
+    }
+    grins_racipe *h = new (std::nothrow) grins_racipe();
+    if (!h) return fail(GRINS_E_NOMEM, "create: host allocation failed");
+    h->N = n_nodes; h->E = n_edges;
+    h->src.assign(src, src + n_edges);
+    h->dst.assign(dst, dst + n_edges);
+    h->sign.assign(sign, sign + n_edges);
+    // CSR of incoming edges, stable in creation order within a target
+    h->csr_off.assign(n_nodes + 1, 0);
+    h->n_act_in.assign(n_nodes, 0);
+    h->n_inh_in.assign(n_nodes, 0);
+    for (int e = 0; e < n_edges; ++e) {
+        h->csr_off[dst[e] + 1]++;
+        if (sign[e] > 0) h->n_act_in[dst[e]]++; else h->n_inh_in[dst[e]]++;
+    }
+    for (int i = 0; i < n_nodes; ++i) h->csr_off[i + 1] += h->csr_off[i];
+    h->csr_src.resize(n_edges); h->csr_edge.resize(n_edges); h->csr_sign.resize(n_edges);
+    std::vector<int> fillp(h->csr_off.begin(), h->csr_off.end() - 1);
+    for (int e = 0; e < n_edges; ++e) {
+        const int p = fillp[dst[e]]++;
+        h->csr_src[p] = src[e]; h->csr_edge[p] = e; h->csr_sign[p] = sign[e];
+    }
+    h->layout = make_layout(n_nodes, n_edges);
+
+    cudaError_t ce = cudaGetDevice(&h->device);
+    if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+    int optin = 0;
+    if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+    h->smem_optin = (size_t)optin;
+    const size_t Eb = (size_t)std::max(n_edges, 1);
+    if (ce == cudaSuccess) ce = cudaMalloc(&h->d_off, sizeof(int32_t) * (n_nodes + 1));
+    if (ce == cudaSuccess) ce = cudaMalloc(&h->d_src, sizeof(int32_t) * Eb);
+    if (ce == cudaSuccess) ce = cudaMalloc(&h->d_edge, sizeof(int32_t) * Eb);
+    if (ce == cudaSuccess) ce = cudaMalloc(&h->d_sign, Eb);
+    if (ce == cudaSuccess) ce = cudaMalloc(&h->d_edge_sign, Eb);
+    if (ce == cudaSuccess) ce = cudaMalloc(&h->d_edge_median, sizeof(double) * Eb);
+    if (ce == cudaSuccess) ce = cudaMalloc(&h->d_queue, sizeof(unsigned long long) * 4);
+    if (ce == cudaSuccess) ce = cudaMemset(h->d_queue, 0, sizeof(unsigned long long) * 4);
+    if (ce == cudaSuccess) ce = cudaMemcpy(h->d_off, h->csr_off.data(), sizeof(int32_t) * (n_nodes + 1), cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess && n_edges) ce = cudaMemcpy(h->d_src, h->csr_src.data(), sizeof(int32_t) * n_edges, cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess && n_edges) ce = cudaMemcpy(h->d_edge, h->csr_edge.data(), sizeof(int32_t) * n_edges, cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess && n_edges) ce = cudaMemcpy(h->d_sign, h->csr_sign.data(), n_edges, cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess && n_edges) ce = cudaMemcpy(h->d_edge_sign, h->sign.data(), n_edges, cudaMemcpyHostToDevice);
+    if (ce != cudaSuccess) {
+        free_device(h);
+        delete h;
+        return cuda_fail(ce, "create: device workspace");
+    }
+    *out = h;
+    return GRINS_OK;
+}
+
+extern "C" grins_status grins_racipe_destroy(grins_racipe_t h)
+{
+    if (!h) return fail(GRINS_E_INVALID_ARG, "destroy: NULL handle");
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != h->device) cudaSetDevice(h->device);
+    cudaDeviceSynchronize();
+    free_device(h);
+    if (cur != h->device) cudaSetDevice(cur);
+    delete h;
+    return GRINS_OK;
+}
+
+extern "C" int64_t grins_racipe_param_stride(grins_racipe_t h)
+{
+    return h ? h->layout.stride : -1;
+}
+
+// ----------------------------------------------------- half-functional rule
+// Host Philox4x64-10 (Salmon et al., SC'11), identical in definition to the
+// device generator of common.cuh.
+static void philox_host(uint64_t c[4], uint64_t k0, uint64_t k1)
+{
+    const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+    for (int r = 0; r < 10; ++r) {
+        const unsigned __int128 p0 = (unsigned __int128)M0 * c[0];
+        const unsigned __int128 p1 = (unsigned __int128)M1 * c[2];
+        const uint64_t n0 = (uint64_t)(p1 >> 64) ^ c[1] ^ k0;
+        const uint64_t n2 = (uint64_t)(p0 >> 64) ^ c[3] ^ k1;
+        c[0] = n0; c[1] = (uint64_t)p1; c[2] = n2; c[3] = (uint64_t)p0;
+        k0 += W0; k1 += W1;
+    }
+}
+
+namespace {
+
+struct MedianStream {
+    uint64_t key1;
+    uint64_t draw(uint64_t sample, uint64_t d) const
+    {
+        uint64_t c[4] = {sample, d / 4, 0, 0};
+        philox_host(c, kKeyMedian, key1);
+        return c[d % 4];
+    }
+};
+
+inline double span_map(double lo, double hi, double u) { return lo + (hi - lo) * u; }
+
+// Eq. 2 in its printed form, H = B0^n/(B0^n+B^n) + lambda B^n/(B0^n+B^n),
+// times 1/lambda for an activating input (Eq. 1).
+inline double hill_factor(bool act, double B, double B0, double n, double lam)
+{
+    if (B < 0.0) B = 0.0;
+    const double b0n = std::pow(B0, n), bn = std::pow(B, n);
+    const double h = b0n / (b0n + bn) + lam * bn / (b0n + bn);
+    return act ? h / lam : h;
+}
+
+double median_sorted(std::vector<double> &v)
+{
+    std::sort(v.begin(), v.end());
+    const size_t K = v.size();
+    return K % 2 ? v[K / 2] : (v[K / 2 - 1] + v[K / 2]) / 2.0;
+}
+
+// Levels of a node with `na` activating and `ni` inhibiting inputs: the node
+// at its own steady state (G/k times its input factors), each input at an
+// unregulated level G'/k' with threshold U[thr_lo, thr_hi] * M0 and n, lambda
+// from the ranges.  Draw layout of sample s: 0 -> G, 1 -> k, then for input m
+// (activating inputs first) draws 2+5m .. 6+5m -> G', k', threshold, lambda, n.
+std::vector<double> level_samples(int na, int ni, const grins_racipe_ranges &r, double M0)
+{
+    const MedianStream ms{((uint64_t)(uint32_t)na << 32) | (uint64_t)(uint32_t)ni};
+    const int K = r.median_samples;
+    std::vector<double> out((size_t)K);
+    const double v_lo = 1.0 / r.lam_inh_max, v_hi = 1.0 / r.lam_inh_min;
+    for (int s = 0; s < K; ++s) {
+        const double G = span_map(r.G_min, r.G_max, unit_double(ms.draw(s, 0)));
+        const double k = span_map(r.k_min, r.k_max, unit_double(ms.draw(s, 1)));
+        double level = G / k;
+        for (int m = 0; m < na + ni; ++m) {
+            const uint64_t d = 2 + 5 * (uint64_t)m;
+            const double Gs = span_map(r.G_min, r.G_max, unit_double(ms.draw(s, d)));
+            const double ks = span_map(r.k_min, r.k_max, unit_double(ms.draw(s, d + 1)));
+            const double T = span_map(r.thr_lo, r.thr_hi, unit_double(ms.draw(s, d + 2))) * M0;
+            const double ul = unit_double(ms.draw(s, d + 3));
+            const int n = unit_int(ms.draw(s, d + 4), r.n_min, r.n_max - r.n_min + 1);
+            const bool act = m < na;
+            const double lam = act ? span_map(r.lam_act_min, r.lam_act_max, ul) : 1.0 / span_map(v_lo, v_hi, ul);
+            level = level * hill_factor(act, Gs / ks, T, (double)n, lam);
+        }
+        out[(size_t)s] = level;
+    }
+    return out;
+}
+
+bool same_ranges(const grins_racipe_ranges &a, const grins_racipe_ranges &b)
+{
+    return std::memcmp(&a, &b, sizeof(a)) == 0;
+}
+
+grins_status check_ranges(const grins_racipe_ranges &r)
+{
+    auto ok_pair = [](double lo, double hi) { return std::isfinite(lo) && std::isfinite(hi) && lo > 0 && lo <= hi; };
+    if (!ok_pair(r.G_min, r.G_max)) return fail(GRINS_E_INVALID_ARG, "ranges: need 0 < G_min <= G_max");
+    if (!ok_pair(r.k_min, r.k_max)) return fail(GRINS_E_INVALID_ARG, "ranges: need 0 < k_min <= k_max");
+    if (!ok_pair(r.lam_act_min, r.lam_act_max) || r.lam_act_min < 1.0)
+        return fail(GRINS_E_INVALID_ARG, "ranges: need 1 <= lam_act_min <= lam_act_max");
+    if (!ok_pair(r.lam_inh_min, r.lam_inh_max) || r.lam_inh_max > 1.0)
+        return fail(GRINS_E_INVALID_ARG, "ranges: need 0 < lam_inh_min <= lam_inh_max <= 1");
+    if (r.n_min < 1 || r.n_max > 255 || r.n_min > r.n_max)
+        return fail(GRINS_E_INVALID_ARG, "ranges: need 1 <= n_min <= n_max <= 255");
+    if (!ok_pair(r.thr_lo, r.thr_hi)) return fail(GRINS_E_INVALID_ARG, "ranges: need 0 < thr_lo <= thr_hi");
+    if (r.median_samples < 1 || r.median_samples > 10000000)
+        return fail(GRINS_E_INVALID_ARG, "ranges: median_samples outside [1, 1e7]");
+    if (r.median_mode != GRINS_MEDIAN_PER_INDEGREE && r.median_mode != GRINS_MEDIAN_UNREGULATED)
+        return fail(GRINS_E_INVALID_ARG, "ranges: unknown median_mode %d", r.median_mode);
+    return GRINS_OK;
+}
+
+grins_status ensure_medians(grins_racipe *h, const grins_racipe_ranges &r)
+{
+    if (h->median_valid && same_ranges(h->median_ranges, r)) return GRINS_OK;
+    std::vector<double> v0 = level_samples(0, 0, r, 0.0);
+    const double M0 = median_sorted(v0);
+    h->node_median.assign(h->N, M0);
+    if (r.median_mode == GRINS_MEDIAN_PER_INDEGREE) {
+        std::vector<std::pair<std::pair<int, int>, double>> cache;
+        for (int j = 0; j < h->N; ++j) {
+            const int na = h->n_act_in[j], ni = h->n_inh_in[j];
+            if (na == 0 && ni == 0) continue;
+            double M = -1.0;
+            for (auto &c : cache) if (c.first.first == na && c.first.second == ni) M = c.second;
+            if (M < 0.0) {
+                std::vector<double> v = level_samples(na, ni, r, M0);
+                M = median_sorted(v);
+                cache.push_back({{na, ni}, M});
+            }
+            h->node_median[j] = M;
+        }
+    }
+    h->median_ranges = r;
+    h->median_valid = true;
+    h->median_uploaded = false;
+    return GRINS_OK;
+}
+
+bool on_handle_device(const grins_racipe *h)
+{
+    int cur = -1;
+    return cudaGetDevice(&cur) == cudaSuccess && cur == h->device;
+}
+
+}  // namespace
+
+extern "C" grins_status grins_racipe_node_medians(grins_racipe_t h, const grins_racipe_ranges *r,
+                                                  double *out)
+{
+    g_last_error.clear();
+    if (!h || !out) return fail(GRINS_E_INVALID_ARG, "node_medians: NULL argument");
+    grins_racipe_ranges rr;
+    if (r) rr = *r; else grins_racipe_default_ranges(&rr);
+    grins_status s = check_ranges(rr);
+    if (s != GRINS_OK) return s;
+    s = ensure_medians(h, rr);
+    if (s != GRINS_OK) return s;
+    std::copy(h->node_median.begin(), h->node_median.end(), out);
+    return GRINS_OK;
+}
+
+// ------------------------------------------------------------------ sample
+extern "C" grins_status grins_racipe_sample_params(grins_racipe_t h, const grins_racipe_ranges *r,
+                                                   uint64_t seed, int64_t set0, int64_t n_sets,
+                                                   int32_t n_ics, void *d_params, double *d_ic_unit,
+                                                   void *stream)
+{
+    g_last_error.clear();
+    if (!h) return fail(GRINS_E_INVALID_ARG, "sample_params: NULL handle");
+    if (set0 < 0 || n_sets < 0 || n_ics < 0)
+        return fail(GRINS_E_INVALID_ARG, "sample_params: negative set0, n_sets or n_ics");
+    if (n_sets > 0 && !d_params) return fail(GRINS_E_INVALID_ARG, "sample_params: d_params is NULL");
+    if (!on_handle_device(h)) return fail(GRINS_E_INVALID_ARG, "sample_params: current device is not the handle's");
+    grins_racipe_ranges rr;
+    if (r) rr = *r; else grins_racipe_default_ranges(&rr);
+    grins_status s = check_ranges(rr);
+    if (s != GRINS_OK) return s;
+    s = ensure_medians(h, rr);
+    if (s != GRINS_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!h->median_uploaded && h->E > 0) {
+        std::vector<double> em(h->E);
+        for (int e = 0; e < h->E; ++e) em[e] = h->node_median[h->src[e]];
+        CUDA_TRY(cudaMemcpyAsync(h->d_edge_median, em.data(), sizeof(double) * h->E, cudaMemcpyHostToDevice, st),
+                 "sample_params: median upload");
+        CUDA_TRY(cudaStreamSynchronize(st), "sample_params: median upload");
+        h->median_uploaded = true;
+    }
+    SampleArgs a{};
+    a.L = h->layout;
+    a.edge_sign = h->d_edge_sign;
+    a.edge_median = h->d_edge_median;
+    a.seed = seed; a.set0 = set0; a.n_sets = n_sets;
+    a.G_min = rr.G_min; a.G_span = rr.G_max - rr.G_min;
+    a.k_min = rr.k_min; a.k_span = rr.k_max - rr.k_min;
+    a.la_min = rr.lam_act_min; a.la_span = rr.lam_act_max - rr.lam_act_min;
+    a.vi_min = 1.0 / rr.lam_inh_max;
+    a.vi_span = 1.0 / rr.lam_inh_min - 1.0 / rr.lam_inh_max;
+    a.thr_lo = rr.thr_lo; a.thr_span = rr.thr_hi - rr.thr_lo;
+    a.n_min = rr.n_min; a.n_count = rr.n_max - rr.n_min + 1;
+    a.params = static_cast<unsigned char *>(d_params);
+    CUDA_TRY(launch_sample_params(a, st), "sample_params: launch");
+    if (d_ic_unit && n_ics > 0) CUDA_TRY(launch_sample_ics(h->N, seed, n_ics, d_ic_unit, st), "sample_params: IC launch");
+    return GRINS_OK;
+}
+
+// --------------------------------------------------------------- integrate
+static PolishArgs polish_args(const grins_racipe *h, const grins_solver_opts *o, const void *d_params,
+                              int64_t n_sets, int32_t n_ics, double *d_states, uint8_t *d_status,
+                              float *d_err_est)
+{
+    PolishArgs p{};
+    p.topo = DevTopo{h->N, h->E, h->d_off, h->d_src, h->d_edge, h->d_sign};
+    p.L = h->layout;
+    p.params = static_cast<const unsigned char *>(d_params);
+    p.n_solves = n_sets * (int64_t)n_ics;
+    p.n_ics = n_ics;
+    p.states = d_states;
+    p.status = d_status;
+    p.err_est = d_err_est;
+    p.tol = o->polish_tol;
+    p.max_move = o->polish_max_move;
+    p.iters = o->polish_iters;
+    p.check = h->d_queue + 2;
+    return p;
+}
+
+static bool polish_opts_ok(const grins_solver_opts *o)
+{
+    return o->polish_tol > 0 && o->polish_iters >= 0 && o->polish_iters <= 64 && o->polish_max_move > 0;
+}
+
+extern "C" grins_status grins_racipe_polish(grins_racipe_t h, const grins_solver_opts *o,
+                                            const void *d_params, int64_t n_sets, int32_t n_ics,
+                                            double *d_states, uint8_t *d_status, float *d_err_est,
+                                            void *stream)
+{
+    g_last_error.clear();
+    if (!h || !o) return fail(GRINS_E_INVALID_ARG, "polish: NULL handle or options");
+    if (n_sets < 0 || n_ics < 1) return fail(GRINS_E_INVALID_ARG, "polish: bad sizes");
+    if (n_sets > 0 && (!d_params || !d_states || !d_status))
+        return fail(GRINS_E_INVALID_ARG, "polish: NULL required device buffer");
+    if (!polish_opts_ok(o)) return fail(GRINS_E_INVALID_ARG, "polish: bad polish options");
+    if (!on_handle_device(h)) return fail(GRINS_E_INVALID_ARG, "polish: current device is not the handle's");
+    if (n_sets == 0) return GRINS_OK;
+    CUDA_TRY(launch_polish(polish_args(h, o, d_params, n_sets, n_ics, d_states, d_status, d_err_est),
+                           (cudaStream_t)stream, h->num_sms), "polish: launch");
+    return GRINS_OK;
+}
+
+static int slots_for(int n_ics)
+{
+    int s = (48 + n_ics - 1) / n_ics;
+    return std::max(2, std::min(32, s));
+}
+
+extern "C" grins_status grins_racipe_integrate(grins_racipe_t h, const grins_solver_opts *o,
+                                               const void *d_params, int64_t n_sets,
+                                               const double *d_ic_unit, int32_t n_ics,
+                                               double *d_states, uint8_t *d_status, double *d_t_final,
+                                               float *d_err_est, int32_t *d_n_steps, double *d_series,
+                                               void *stream)
+{
+    g_last_error.clear();
+    if (!h || !o) return fail(GRINS_E_INVALID_ARG, "integrate: NULL handle or options");
+    if (n_sets < 0) return fail(GRINS_E_INVALID_ARG, "integrate: n_sets < 0");
+    if (n_ics < 1) return fail(GRINS_E_INVALID_ARG, "integrate: n_ics < 1");
+    if (n_sets > 0 && (!d_params || !d_ic_unit || !d_states || !d_status))
+        return fail(GRINS_E_INVALID_ARG, "integrate: NULL required device buffer");
+    if (o->precision != GRINS_FP32 && o->precision != GRINS_FP64)
+        return fail(GRINS_E_INVALID_ARG, "integrate: unknown precision %d", o->precision);
+    if (!(o->rtol > 0) || !(o->atol > 0) || !std::isfinite(o->rtol) || !std::isfinite(o->atol))
+        return fail(GRINS_E_INVALID_ARG, "integrate: rtol and atol must be positive");
+    if (!std::isfinite(o->t0) || !std::isfinite(o->t_end) || !(o->t_end > o->t0))
+        return fail(GRINS_E_INVALID_ARG, "integrate: need finite t0 < t_end");
+    if (!(o->ss_tol >= 0)) return fail(GRINS_E_INVALID_ARG, "integrate: ss_tol < 0");
+    if (o->max_steps < 1) return fail(GRINS_E_INVALID_ARG, "integrate: max_steps < 1");
+    if (o->n_t < 0 || (o->n_t > 0 && !o->t_grid)) return fail(GRINS_E_INVALID_ARG, "integrate: bad time grid");
+    if ((o->n_t > 0) != (d_series != nullptr) && n_sets > 0)
+        return fail(GRINS_E_INVALID_ARG, "integrate: d_series must be given exactly when n_t > 0");
+    for (int g = 0; g < o->n_t; ++g) {
+        const double tg = o->t_grid[g];
+        if (!(tg >= o->t0 && tg <= o->t_end) || (g > 0 && !(tg > o->t_grid[g - 1])))
+            return fail(GRINS_E_INVALID_ARG, "integrate: t_grid must increase strictly inside [t0, t_end]");
+    }
+    if (o->polish && !polish_opts_ok(o))
+        return fail(GRINS_E_INVALID_ARG, "integrate: bad polish options");
+    if (!on_handle_device(h)) return fail(GRINS_E_INVALID_ARG, "integrate: current device is not the handle's");
+    if (n_sets == 0) return GRINS_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+
+    if (o->n_t > h->grid_cap) {
+        CUDA_TRY(cudaStreamSynchronize(st), "integrate: grid buffer");
+        cudaFree(h->d_grid);
+        h->d_grid = nullptr;
+        h->grid_cap = 0;
+        CUDA_TRY(cudaMalloc(&h->d_grid, sizeof(double) * o->n_t), "integrate: grid buffer");
+        h->grid_cap = o->n_t;
+    }
+    if (o->n_t > 0) {
+        CUDA_TRY(cudaMemcpyAsync(h->d_grid, o->t_grid, sizeof(double) * o->n_t, cudaMemcpyHostToDevice, st),
+                 "integrate: grid upload");
+    }
+
+    IntegrateArgs a{};
+    a.topo = DevTopo{h->N, h->E, h->d_off, h->d_src, h->d_edge, h->d_sign};
+    a.L = h->layout;
+    a.params = static_cast<const unsigned char *>(d_params);
+    a.n_sets = n_sets;
+    a.ic_unit = d_ic_unit;
+    a.n_ics = n_ics;
+    a.rtol = o->rtol; a.atol = o->atol; a.t0 = o->t0; a.t_end = o->t_end; a.ss_tol = o->ss_tol;
+    a.max_steps = o->max_steps;
+    a.t_grid = h->d_grid;
+    a.n_t = o->n_t;
+    a.states = d_states; a.status = d_status; a.t_final = d_t_final; a.n_steps = d_n_steps;
+    a.series = o->n_t > 0 ? d_series : nullptr;
+    a.queue = h->d_queue;
+    a.check = h->d_queue + 2;
+    a.slots = slots_for(n_ics);
+    a.smem_limit = (int32_t)h->smem_optin;
+
+    CUDA_TRY(cudaMemsetAsync(h->d_queue, 0, 2 * sizeof(unsigned long long), st), "integrate: queue reset");
+    cudaError_t le;
+    if (o->precision == GRINS_FP32) le = launch_integrate_fp32(a, st, h->num_sms);
+    else le = launch_integrate_fp64(a, st, h->num_sms);
+    if (le == cudaErrorInvalidConfiguration)
+        return fail(GRINS_E_BUDGET, "integrate: the network needs more shared memory per block than the device has");
+    if (le != cudaSuccess) return cuda_fail(le, "integrate: launch");
+
+    if (o->polish) {
+        CUDA_TRY(launch_polish(polish_args(h, o, d_params, n_sets, n_ics, d_states, d_status, d_err_est), st,
+                               h->num_sms), "integrate: polish launch");
+    } else if (d_err_est) {
+        CUDA_TRY(cudaMemsetAsync(d_err_est, 0xff, sizeof(float) * n_sets * n_ics, st), "integrate: err_est");
+    }
+    return GRINS_OK;
+}
+
+// ------------------------------------------------------------------ unique
+extern "C" grins_status grins_racipe_unique_states(grins_racipe_t h, const void *d_params,
+                                                   const double *d_states, const uint8_t *d_status,
+                                                   int64_t n_sets, int32_t n_ics, double tol,
+                                                   int32_t *d_state_id, int32_t *d_n_unique, void *stream)
+{
+    g_last_error.clear();
+    if (!h) return fail(GRINS_E_INVALID_ARG, "unique_states: NULL handle");
+    if (n_sets < 0 || n_ics < 1 || n_ics > 4096) return fail(GRINS_E_INVALID_ARG, "unique_states: bad sizes");
+    if (!(tol >= 0) || !std::isfinite(tol)) return fail(GRINS_E_INVALID_ARG, "unique_states: tol must be >= 0");
+    if (n_sets > 0 && (!d_params || !d_states || !d_status || !d_state_id || !d_n_unique))
+        return fail(GRINS_E_INVALID_ARG, "unique_states: NULL device buffer");
+    if (!on_handle_device(h)) return fail(GRINS_E_INVALID_ARG, "unique_states: current device is not the handle's");
+    UniqueArgs a{};
+    a.L = h->layout;
+    a.params = static_cast<const unsigned char *>(d_params);
+    a.states = d_states; a.status = d_status;
+    a.n_sets = n_sets; a.n_ics = n_ics; a.tol = tol;
+    a.state_id = d_state_id; a.n_unique = d_n_unique;
+    CUDA_TRY(launch_unique(a, (cudaStream_t)stream, h->num_sms), "unique_states: launch");
+    return GRINS_OK;
+}
+
+#ifdef GRINS_CHECKED
+// Checked builds only: first index/alignment violation recorded by the
+// handle's kernels (0 = none); *info receives the offending index.
+extern "C" int grins_debug_check_status(grins_racipe_t h, long long *info)
+{
+    unsigned long long w[2] = {0, 0};
+    if (!h || cudaMemcpy(w, h->d_queue + 2, sizeof(w), cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+    if (info) *info = (long long)w[1];
+    return (int)w[0];
+}
+#endif

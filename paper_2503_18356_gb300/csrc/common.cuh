@@ -1,0 +1,171 @@
+// Internal definitions shared by the CUDA translation units of
+// libgrins_racipe.so: parameter-block layout, device topology, kernel
+// argument structs, the device Philox generator and launch declarations.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "grins_racipe.h"
+
+namespace grins {
+
+constexpr int kMaxNodes = 64;     // kernels are bucketed up to this N
+constexpr int kMaxEdges = 4096;
+constexpr int kWarp = 32;
+
+// Byte layout of one parameter set (2N + 3E values, Sec. 2.1.2):
+// double G[N], k[N], T[E], lam[E]; uint8 n[E]; padded to 16 bytes.
+struct ParamLayout {
+    int32_t N, E;
+    int32_t off_G, off_k, off_T, off_lam, off_n;
+    int64_t stride;
+};
+
+inline ParamLayout make_layout(int N, int E)
+{
+    ParamLayout L;
+    L.N = N; L.E = E;
+    L.off_G = 0;
+    L.off_k = 8 * N;
+    L.off_T = 16 * N;
+    L.off_lam = 16 * N + 8 * E;
+    L.off_n = 16 * N + 16 * E;
+    int64_t bytes = (int64_t)16 * N + 16 * E + E;
+    L.stride = (bytes + 15) / 16 * 16;
+    return L;
+}
+
+// Network on the device, in-edges grouped by target (CSR).
+struct DevTopo {
+    int32_t N, E;
+    const int32_t *off;       // [N+1] first CSR position of each target's inputs
+    const int32_t *src;       // [E] source node of CSR position
+    const int32_t *edge;      // [E] creation-order edge index of CSR position
+    const int8_t *sign;       // [E] +1 activation / -1 inhibition
+};
+
+// ---------------------------------------------------------------- sampler
+struct SampleArgs {
+    ParamLayout L;
+    const int8_t *edge_sign;     // [E] creation order
+    const double *edge_median;   // [E] creation order: median level of the edge's source
+    uint64_t seed;
+    int64_t set0, n_sets;
+    double G_min, G_span, k_min, k_span;
+    double la_min, la_span;      // activating lambda
+    double vi_min, vi_span;      // inverse inhibiting lambda
+    double thr_lo, thr_span;
+    int32_t n_min, n_count;
+    unsigned char *params;
+};
+
+cudaError_t launch_sample_params(const SampleArgs &a, cudaStream_t st);
+cudaError_t launch_sample_ics(int N, uint64_t seed, int n_ics, double *u, cudaStream_t st);
+
+// ------------------------------------------------------------- integrator
+struct IntegrateArgs {
+    DevTopo topo;
+    ParamLayout L;
+    const unsigned char *params;
+    int64_t n_sets;
+    const double *ic_unit;       // [n_ics][N]
+    int32_t n_ics;
+    double rtol, atol, t0, t_end, ss_tol;
+    int64_t max_steps;
+    const double *t_grid;        // device copy, [n_t]
+    int32_t n_t;
+    double *states;              // [S][I][N]
+    uint8_t *status;             // [S][I]
+    double *t_final;             // nullable
+    int32_t *n_steps;            // nullable
+    double *series;              // [S][I][n_t][N] or null
+    unsigned long long *queue;   // work counter, zero before launch
+    const unsigned long long *nmax;  // largest Hill exponent in the batch (device), or null
+    int32_t gate;                // 0: always run; 2: run only if *nmax exceeds the power table
+    unsigned long long *check;   // checked builds: first violation (code, info)
+    int32_t slots;               // parameter-set slots per warp (upper bound)
+    int32_t smem_limit;          // opt-in shared memory per block, bytes
+};
+
+// Maximum N served by the FP32 / FP64 integrator buckets.
+cudaError_t launch_integrate_fp32(const IntegrateArgs &a, cudaStream_t st, int num_sms);
+cudaError_t launch_integrate_fp64(const IntegrateArgs &a, cudaStream_t st, int num_sms);
+
+// ----------------------------------------------------------------- polish
+struct PolishArgs {
+    DevTopo topo;
+    ParamLayout L;
+    const unsigned char *params;
+    int64_t n_solves;            // S * I
+    int32_t n_ics;
+    double *states;              // in/out
+    uint8_t *status;             // in/out
+    float *err_est;              // nullable
+    double tol, max_move;
+    int32_t iters;
+    unsigned long long *check;   // checked builds: first violation (code, info)
+};
+
+cudaError_t launch_polish(const PolishArgs &a, cudaStream_t st, int num_sms);
+
+// ----------------------------------------------------------------- unique
+struct UniqueArgs {
+    ParamLayout L;
+    const unsigned char *params;
+    const double *states;
+    const uint8_t *status;
+    int64_t n_sets;
+    int32_t n_ics;
+    double tol;
+    int32_t *state_id;
+    int32_t *n_unique;
+};
+
+cudaError_t launch_unique(const UniqueArgs &a, cudaStream_t st, int num_sms);
+
+// ------------------------------------------------------------- device RNG
+// Philox4x64-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds of the
+// four-word Philox bijection with the published multipliers and Weyl key
+// increments.  Used as a keyed hash of (stream key, counter): draw d of
+// the stream (key, c0) is word d % 4 of the block with counter
+// (c0, d / 4, 0, 0).
+struct U64x4 { uint64_t v[4]; };
+
+__device__ __forceinline__ U64x4 philox4x64_10(uint64_t c0, uint64_t c1, uint64_t c2,
+                                                uint64_t c3, uint64_t k0, uint64_t k1)
+{
+    const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        uint64_t lo0 = M0 * c0, hi0 = __umul64hi(M0, c0);
+        uint64_t lo1 = M1 * c2, hi1 = __umul64hi(M1, c2);
+        uint64_t n0 = hi1 ^ c1 ^ k0;
+        uint64_t n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+        k0 += W0; k1 += W1;
+    }
+    U64x4 o; o.v[0] = c0; o.v[1] = c1; o.v[2] = c2; o.v[3] = c3;
+    return o;
+}
+
+// Stream tags (second key word; the first is the user's seed) and the
+// fixed key of the half-functional median samples.
+constexpr uint64_t kTagParams = 0x52414349504550ull;  // "RACIPEP"
+constexpr uint64_t kTagIcs = 0x52414349504549ull;     // "RACIPEI"
+constexpr uint64_t kKeyMedian = 0x48414C4646554E43ull; // "HALFFUNC"
+
+// [0, 1) from the top 53 bits; exact.
+__host__ __device__ __forceinline__ double unit_double(uint64_t r)
+{
+    return (double)(r >> 11) * 0x1.0p-53;
+}
+
+// Integer in [lo, lo + count) from the top 32 bits (multiply-shift).
+__host__ __device__ __forceinline__ int32_t unit_int(uint64_t r, int32_t lo, int32_t count)
+{
+    return lo + (int32_t)(((r >> 32) * (uint64_t)count) >> 32);
+}
+
+}  // namespace grins

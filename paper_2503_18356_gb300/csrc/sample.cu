@@ -1,0 +1,113 @@
+// Parameter and initial-condition sampler (Sec. 2.1.2, Table 1).
+//
+// One thread per (parameter set, Philox block): block c of set s yields the
+// draws 4c .. 4c+3 of that set's stream, each mapped to one parameter.
+// Draw layout of a set (2N + 3E draws):
+//   [0, N) G_i   [N, 2N) k_i   [2N, 2N+E) threshold_e   [2N+E, 2N+2E) lambda_e
+//   [2N+2E, 2N+3E) n_e
+// Floating-point maps use explicit round-to-nearest intrinsics so that no
+// multiply-add is contracted: the values are reproducible bit for bit.
+#include "common.cuh"
+
+namespace grins {
+
+namespace {
+
+__device__ __forceinline__ double affine_rn(double lo, double span, double u)
+{
+    return __dadd_rn(lo, __dmul_rn(span, u));
+}
+
+__global__ void sample_params_kernel(SampleArgs a)
+{
+    const int N = a.L.N, E = a.L.E;
+    const int n_draws = 2 * N + 3 * E;
+    const int blocks_per_set = (n_draws + 3) / 4;
+    const int64_t total = a.n_sets * blocks_per_set;
+    for (int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; gid < total;
+         gid += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s_local = gid / blocks_per_set;
+        const int c = (int)(gid - s_local * blocks_per_set);
+        const uint64_t s = (uint64_t)(a.set0 + s_local);
+        U64x4 r = philox4x64_10(s, (uint64_t)c, 0, 0, a.seed, kTagParams);
+        unsigned char *blk = a.params + s_local * a.L.stride;
+        double *G = reinterpret_cast<double *>(blk + a.L.off_G);
+        double *k = reinterpret_cast<double *>(blk + a.L.off_k);
+        double *T = reinterpret_cast<double *>(blk + a.L.off_T);
+        double *lam = reinterpret_cast<double *>(blk + a.L.off_lam);
+        uint8_t *nn = blk + a.L.off_n;
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const int d = 4 * c + w;
+            if (d >= n_draws) break;
+            const uint64_t x = r.v[w];
+            if (d < N) {
+                G[d] = affine_rn(a.G_min, a.G_span, unit_double(x));
+            } else if (d < 2 * N) {
+                k[d - N] = affine_rn(a.k_min, a.k_span, unit_double(x));
+            } else if (d < 2 * N + E) {
+                const int e = d - 2 * N;
+                T[e] = __dmul_rn(affine_rn(a.thr_lo, a.thr_span, unit_double(x)), a.edge_median[e]);
+            } else if (d < 2 * N + 2 * E) {
+                const int e = d - 2 * N - E;
+                const double u = unit_double(x);
+                const bool act = a.edge_sign[e] > 0;
+                lam[e] = act ? affine_rn(a.la_min, a.la_span, u)
+                             : __ddiv_rn(1.0, affine_rn(a.vi_min, a.vi_span, u));
+            } else {
+                const int e = d - 2 * N - 2 * E;
+                nn[e] = (uint8_t)unit_int(x, a.n_min, a.n_count);
+            }
+        }
+        // zero the tail padding once per set
+        if (c == 0) {
+            for (int64_t b = a.L.off_n + E; b < a.L.stride; ++b) blk[b] = 0;
+        }
+    }
+}
+
+__global__ void sample_ics_kernel(int N, uint64_t seed, int n_ics, double *u)
+{
+    const int blocks_per_ic = (N + 3) / 4;
+    const int64_t total = (int64_t)n_ics * blocks_per_ic;
+    for (int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; gid < total;
+         gid += (int64_t)gridDim.x * blockDim.x) {
+        const int ic = (int)(gid / blocks_per_ic);
+        const int c = (int)(gid - (int64_t)ic * blocks_per_ic);
+        U64x4 r = philox4x64_10((uint64_t)ic, (uint64_t)c, 0, 0, seed, kTagIcs);
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const int i = 4 * c + w;
+            if (i < N) u[(int64_t)ic * N + i] = unit_double(r.v[w]);
+        }
+    }
+}
+
+int grid_for(int64_t work, int threads)
+{
+    int64_t b = (work + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > 65535LL * 16) b = 65535LL * 16;
+    return (int)b;
+}
+
+}  // namespace
+
+cudaError_t launch_sample_params(const SampleArgs &a, cudaStream_t st)
+{
+    if (a.n_sets <= 0) return cudaSuccess;
+    const int n_draws = 2 * a.L.N + 3 * a.L.E;
+    const int64_t work = a.n_sets * ((n_draws + 3) / 4);
+    sample_params_kernel<<<grid_for(work, 256), 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sample_ics(int N, uint64_t seed, int n_ics, double *u, cudaStream_t st)
+{
+    if (n_ics <= 0) return cudaSuccess;
+    const int64_t work = (int64_t)n_ics * ((N + 3) / 4);
+    sample_ics_kernel<<<grid_for(work, 256), 256, 0, st>>>(N, seed, n_ics, u);
+    return cudaGetLastError();
+}
+
+}  // namespace grins

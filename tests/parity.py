@@ -1,0 +1,55 @@
+"""Helpers shared by the GPU parity tests: run the CUDA path through the C ABI
+and the oracle on the same seeded inputs, and compare them."""
+from __future__ import annotations
+
+import os
+
+import numpy as np
+
+import oracle as O
+
+THREADS = max(1, min(16, os.cpu_count() or 1))
+
+
+def gpu_handle(topo):
+    from paper_2503_18356_gb300 import api
+    return api.Racipe.from_topology(topo)
+
+
+def gpu_sample(h, seed, n_sets, n_ics, set0=0, ranges=None):
+    params, ic = h.sample_params(seed, n_sets, n_ics, set0=set0, ranges=ranges)
+    G, k, T, lam, n = (x.cpu().numpy() for x in h.unpack_params(params))
+    return params, ic, O.ParamSet(G, k, T, lam, n.astype(np.int32)), ic.cpu().numpy()
+
+
+def rel_err(x, ref, G, k, floor=1e-6):
+    """|x - x*| / max(|x*|, floor * G/k), elementwise (floor for states near 0)."""
+    scale = np.maximum(np.abs(ref), floor * (G / k))
+    return np.abs(x - ref) / scale
+
+
+def compare_states(gpu, orc, p: O.ParamSet, tol, basin_tol=1e-2, normalised=False):
+    """Compares converged states set by set.  Returns a dict with the max
+    error over solves converged on both sides and in the same basin, the
+    number of such solves, the basin-mismatch count and the status agreement
+    rate.  The error is relative (floor 1e-6 G/k) for polished states; with
+    `normalised` it is measured on the G/k scale, |x - x*| k / G, which is
+    how unpolished states (stopped at max_i |f_i| k_i / G_i < ss_tol) are
+    judged: that stop rule bounds the distance to the fixed point in units of
+    G/k, not relative to a small steady level."""
+    G = p.G[:, None, :]
+    k = p.k[:, None, :]
+    both = (gpu["status"] == O.CONVERGED) & (orc["status"] == O.CONVERGED)
+    vg = gpu["states"] * k / G
+    vo = orc["states"] * k / G
+    dist = np.max(np.abs(vg - vo), axis=2)
+    same = both & (dist <= basin_tol)
+    err = np.abs(vg - vo) if normalised else rel_err(gpu["states"], orc["states"], G, k)
+    emax = float(np.max(err[same])) if same.any() else 0.0
+    return dict(max_rel=emax, n_compared=int(same.sum()), n_basin=int((both & ~same).sum()),
+                status_agree=float(np.mean(gpu["status"] == orc["status"])),
+                p999=float(np.quantile(err[same].max(axis=-1), 0.999)) if same.any() else 0.0)
+
+
+def to_numpy(out):
+    return {k: (v.cpu().numpy() if hasattr(v, "cpu") else v) for k, v in out.items() if v is not None}

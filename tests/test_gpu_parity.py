@@ -1,0 +1,256 @@
+"""GPU parity: the CUDA path, called through the C ABI, against the CPU oracle
+on the same seeded inputs.
+
+Bars (written in each test):
+  * sampler (parameters, initial conditions, median table): bit-exact;
+  * steady-state dedupe on a given states array: bit-exact;
+  * FP32 + FP64 polish: relative 1e-6 (floor 1e-6 G/k); raw FP32 and plain
+    FP64 (stopped at the steady-state condition, unpolished): 1e-3 on the
+    G/k-normalised scale, the scale the stop rule controls;
+  * time series on a fixed grid: relative 1e-3;
+  * distinct steady states per set: every mismatching set is explained by a
+    solve whose status differs (a slow solve meeting the steady-state
+    condition near t_end on one side only), and mismatches stay below 1 % of
+    sets (the 1000-set agreement rate is reported by the parity report);
+  * solves that converge to different fixed points on the two sides (near a
+    separatrix) are counted, reported and kept below 1 %.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2503_18356_gb300 import workloads as W
+from tests import parity as PT
+
+pytestmark = pytest.mark.gpu
+
+
+def oracle_run(topo, p, ic, **kw):
+    return O.run_sets_parallel(O.Network(*topo.edges()), p, ic, threads=PT.THREADS, **kw)
+
+
+# ---------------------------------------------------------------- sampler
+@pytest.mark.parametrize("wl", ["ts", "net5", "net22"])
+def test_sampler_bit_exact(wl):
+    w = {"ts": W.ts_workload, "net5": W.net5_workload, "net22": W.net22_workload}[wl]()
+    topo = w["topology"]
+    h = PT.gpu_handle(topo)
+    net = O.Network(*topo.edges())
+    for set0, S in [(0, 257), (12345, 33)]:
+        _, _, p, ic = PT.gpu_sample(h, w["param_seed"], S, w["n_ics"], set0=set0)
+        ref = O.sample_params(net, w["param_seed"], S, set0=set0)
+        for name in ("G", "k", "T", "lam", "n"):
+            assert np.array_equal(getattr(p, name), getattr(ref, name)), name
+        assert np.array_equal(ic, O.sample_ics(topo.n_nodes, w["param_seed"], w["n_ics"]))
+    # per-node medians equal the oracle's per in-degree class
+    med = h.node_medians()
+    for j in range(topo.n_nodes):
+        a = int(((topo.dst == j) & (topo.sign > 0)).sum())
+        b = int(((topo.dst == j) & (topo.sign < 0)).sum())
+        assert med[j] == O.median(a, b)
+
+
+def test_sampler_unregulated_mode_and_custom_ranges():
+    from paper_2503_18356_gb300 import api
+    topo = W.random_network(7, 6, 12, 6, 1)
+    h = PT.gpu_handle(topo)
+    r = api.default_ranges(median_mode=1, n_max=4, G_max=50.0, lam_inh_min=0.1, median_samples=999)
+    ro = O.default_ranges(median_mode=1, n_max=4, G_max=50.0, lam_inh_min=0.1, median_samples=999)
+    _, _, p, _ = PT.gpu_sample(h, 5, 64, 3, ranges=r)
+    ref = O.sample_params(O.Network(*topo.edges()), 5, 64, ranges=ro)
+    for name in ("G", "k", "T", "lam", "n"):
+        assert np.array_equal(getattr(p, name), getattr(ref, name)), name
+
+
+# ----------------------------------------------------------------- dedupe
+def test_unique_states_bit_exact_on_given_states():
+    topo = W.random_network(3, 4, 8, 4, 0)
+    h = PT.gpu_handle(topo)
+    S, I, N = 300, 12, 4
+    params, _, p, _ = PT.gpu_sample(h, 9, S, I)
+    rng = np.random.default_rng(1)
+    centres = rng.uniform(0, 1, (S, 3, N))
+    v = np.take_along_axis(centres, rng.integers(0, 3, (S, I))[:, :, None], axis=1)
+    v = v + rng.normal(0, 0.004, (S, I, N))
+    # exact ties at the tolerance on some sets: v differs by exactly 2^-7
+    v[::7, 1] = v[::7, 0]
+    v[::7, 1, 0] += 2.0**-7
+    states = v * p.G[:, None, :] / p.k[:, None, :]
+    status = (rng.uniform(size=(S, I)) < 0.1).astype(np.uint8)
+    sid, nu = h.unique_states(params, torch.tensor(states, device="cuda"),
+                              torch.tensor(status, device="cuda"), tol=2.0**-7)
+    sid, nu = sid.cpu().numpy(), nu.cpu().numpy()
+    for s in range(S):
+        rs, rn = O.dedupe(states[s], status[s], p.G[s], p.k[s], tol=2.0**-7)
+        assert rn == nu[s] and np.array_equal(rs, sid[s]), s
+
+
+# -------------------------------------------------------------- integrator
+def run_gpu(h, params, ic, **opt):
+    out = h.integrate(params, ic, **opt)
+    torch.cuda.synchronize()
+    return PT.to_numpy(out)
+
+
+@pytest.mark.parametrize("precision,polish,tol", [(1, 1, 1e-6), (1, 0, 1e-3), (0, 0, 1e-3), (0, 1, 1e-6)])
+def test_toggle_switch_states(precision, polish, tol):
+    w = W.ts_workload()
+    h = PT.gpu_handle(w["topology"])
+    params, ic, p, icn = PT.gpu_sample(h, w["param_seed"], 120, w["n_ics"])
+    g = run_gpu(h, params, ic, precision=precision, polish=polish)
+    o = oracle_run(w["topology"], p, icn)
+    c = PT.compare_states(g, o, p, tol, normalised=not polish)
+    print("TS", precision, polish, c)
+    assert c["n_compared"] > 0.9 * g["status"].size
+    assert c["max_rel"] <= tol
+    assert c["n_basin"] <= 0.01 * g["status"].size
+    assert c["status_agree"] >= 0.98
+
+
+@pytest.mark.parametrize("wl,S", [("net5", 60), ("net22", 60)])
+def test_random_networks_fp32_polish_and_raw(wl, S):
+    w = {"net5": W.net5_workload, "net22": W.net22_workload}[wl]()
+    h = PT.gpu_handle(w["topology"])
+    I = min(w["n_ics"], 20)
+    params, ic, p, icn = PT.gpu_sample(h, w["param_seed"], S, I)
+    o = oracle_run(w["topology"], p, icn)
+    for polish, tol in [(1, 1e-6), (0, 1e-3)]:
+        g = run_gpu(h, params, ic, precision=1, polish=polish)
+        c = PT.compare_states(g, o, p, tol, normalised=not polish)
+        print(wl, polish, c, np.bincount(g["status"].ravel(), minlength=5))
+        assert c["max_rel"] <= tol
+        assert c["n_basin"] <= max(1, 0.01 * g["status"].size)
+        assert c["status_agree"] >= 0.97
+        if polish:
+            ok = g["status"] == O.CONVERGED
+            assert np.all(g["err_est"][ok] >= 0)
+
+
+def test_fp64_random_network():
+    w = W.net22_workload()
+    h = PT.gpu_handle(w["topology"])
+    params, ic, p, icn = PT.gpu_sample(h, w["param_seed"], 24, 10)
+    g = run_gpu(h, params, ic, precision=0, polish=0)
+    o = oracle_run(w["topology"], p, icn)
+    c = PT.compare_states(g, o, p, 1e-3, normalised=True)
+    print("fp64 net22", c)
+    assert c["max_rel"] <= 1e-3 and c["status_agree"] >= 0.97
+
+
+def test_n_unique_agreement_net22():
+    w = W.net22_workload()
+    h = PT.gpu_handle(w["topology"])
+    S, I = 400, 10
+    params, ic, p, icn = PT.gpu_sample(h, w["param_seed"], S, I)
+    g = run_gpu(h, params, ic, precision=1, polish=1)
+    sid, nu = h.unique_states(params, torch.tensor(g["states"], device="cuda"),
+                              torch.tensor(g["status"], device="cuda"))
+    o = oracle_run(w["topology"], p, icn)
+    nu = nu.cpu().numpy()
+    bad = np.where(nu != o["n_unique"])[0]
+    # a mismatch must come from a solve whose status differs (a slowly
+    # converging solve that meets the steady-state condition near t_end on
+    # one side only) or from two states that lie at the dedupe tolerance
+    st_diff = np.any(g["status"] != o["status"], axis=1)
+    unexplained = [int(s) for s in bad if not st_diff[s]]
+    for s in bad:
+        print("set", s, "gpu", nu[s], g["status"][s], g["t_final"][s].round(1),
+              "oracle", o["n_unique"][s], o["status"][s], o["t_final"][s].round(1))
+    print("n_unique mismatches", len(bad), "of", S, "hist", np.bincount(o["n_unique"]),
+          "status agreement", np.mean(g["status"] == o["status"]))
+    assert len(bad) <= 0.01 * S
+    assert not unexplained, unexplained
+
+
+def test_time_series_fp32():
+    w = W.net5_workload()
+    h = PT.gpu_handle(w["topology"])
+    params, ic, p, icn = PT.gpu_sample(h, w["param_seed"], 40, 8)
+    grid = np.linspace(0.0, 30.0, 31)
+    g = run_gpu(h, params, ic, precision=1, polish=0, t_grid=grid)
+    o = oracle_run(w["topology"], p, icn, series=True, t_grid=grid)
+    G = p.G[:, None, None, :]; k = p.k[:, None, None, :]
+    err = PT.rel_err(g["series"], o["series"], G, k, floor=1e-3)
+    # grid points before both sides stopped (after a stop the final state is held)
+    stop = np.minimum(g["t_final"], o["t_final"])[:, :, None] >= grid[None, None, :]
+    e = err.max(axis=-1)[stop]
+    print("series max rel", e.max(), "points", e.size)
+    assert e.max() <= 1e-3
+    assert np.allclose(g["series"][:, :, 0, :], icn[None, :, :] * p.G[:, None, :] / p.k[:, None, :])
+
+
+# -------------------------------------------------------------- edge cases
+def test_single_node_and_empty_networks():
+    from paper_2503_18356_gb300 import api
+    for topo in [W.Topology(1, np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(0, np.int8)),
+                 W.Topology(3, np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(0, np.int8))]:
+        h = PT.gpu_handle(topo)
+        params, ic, p, icn = PT.gpu_sample(h, 3, 17, 5)
+        for prec in (0, 1):
+            g = run_gpu(h, params, ic, precision=prec, polish=1)
+            assert np.all(g["status"] == O.CONVERGED)
+            assert np.allclose(g["states"], (p.G / p.k)[:, None, :], rtol=1e-9)
+
+
+def test_single_solve_and_ragged_shapes():
+    w = W.net22_workload()
+    h = PT.gpu_handle(w["topology"])
+    params, ic, p, icn = PT.gpu_sample(h, w["param_seed"], 37, 7)
+    full = run_gpu(h, params, ic, precision=1, polish=1)
+    one = run_gpu(h, params[5:6], ic[3:4], precision=1, polish=1)
+    # the same solve alone and inside a ragged batch gives identical results
+    assert np.array_equal(one["states"][0, 0], full["states"][5, 3])
+    assert one["status"][0, 0] == full["status"][5, 3]
+    empty = h.integrate(params[:0], ic, precision=1)
+    assert empty["states"].shape[0] == 0
+
+
+def test_large_network_generic_path_and_max_nodes():
+    for N, d, seed in [(30, 0.1, 11), (64, 0.03, 12)]:
+        topo = W.density_network(seed, N, d)
+        h = PT.gpu_handle(topo)
+        params, ic, p, icn = PT.gpu_sample(h, seed, 6, 4)
+        o = oracle_run(topo, p, icn)
+        for prec, polish, tol in [(1, 1, 1e-6), (0, 0, 1e-3)]:
+            g = run_gpu(h, params, ic, precision=prec, polish=polish)
+            c = PT.compare_states(g, o, p, tol, normalised=not polish)
+            print(N, prec, c)
+            assert c["max_rel"] <= tol and c["status_agree"] >= 0.9
+
+
+def test_self_loops_tssa():
+    topo = W.toggle_switch_self_activation()
+    h = PT.gpu_handle(topo)
+    params, ic, p, icn = PT.gpu_sample(h, 77, 100, 20)
+    g = run_gpu(h, params, ic, precision=1, polish=1)
+    o = oracle_run(topo, p, icn)
+    c = PT.compare_states(g, o, p, 1e-6)
+    assert c["max_rel"] <= 1e-6 and c["n_basin"] <= 0.01 * g["status"].size
+
+
+def test_invalid_arguments_report_errors():
+    from paper_2503_18356_gb300 import api
+    h = PT.gpu_handle(W.toggle_switch())
+    params, ic = h.sample_params(1, 4, 3)
+    with pytest.raises(api.GrinsError) as e:
+        h.integrate(params, ic, rtol=-1.0)
+    assert e.value.status == api.GRINS_E_INVALID_ARG
+    with pytest.raises(api.GrinsError):
+        h.integrate(params, ic, t_end=-5.0)
+    with pytest.raises(api.GrinsError):
+        h.integrate(params, ic, t_grid=[0.0, 2.0, 1.0])
+    with pytest.raises(api.GrinsError):
+        h.sample_params(1, 4, 3, ranges=api.default_ranges(n_min=0))
+    with pytest.raises(api.GrinsError):
+        h.unique_states(params, torch.zeros((4, 3, 2), dtype=torch.float64, device="cuda"),
+                        torch.zeros((4, 3), dtype=torch.uint8, device="cuda"), tol=-1.0)
+
+
+def test_max_steps_status():
+    w = W.net5_workload()
+    h = PT.gpu_handle(w["topology"])
+    params, ic = h.sample_params(1, 10, 4)
+    g = run_gpu(h, params, ic, precision=1, polish=0, max_steps=3)
+    assert np.all((g["status"] == O.MAXSTEPS) | (g["status"] == O.CONVERGED))
+    assert np.all(g["n_steps"][g["status"] == O.MAXSTEPS] == 3)

@@ -1,0 +1,38 @@
+"""Sanitizer substitute: the index/alignment-checked build of the library
+(-DGRINS_CHECKED) runs small cases of every kernel path with no recorded
+violation, and its polished states equal the release build's."""
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def run(lib, out):
+    env = dict(os.environ, GRINS_RACIPE_LIB=lib)
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "tests", "checked_runner.py"), out],
+                       env=env, capture_output=True, text=True, timeout=900)
+    assert r.returncode == 0, r.stdout + r.stderr
+    return r.stdout
+
+
+def test_checked_build_records_no_violation(tmp_path):
+    from paper_2503_18356_gb300 import build
+    checked = build.build(checked=True)
+    release = build.build()
+    out_c = run(checked, str(tmp_path / "c.npz"))
+    line = [l for l in out_c.splitlines() if l.startswith("CHECK")][0]
+    codes = eval(line[len("CHECK"):])
+    assert codes and all(c == (0, 0) for c in codes.values()), codes
+    run(release, str(tmp_path / "r.npz"))
+    c = np.load(tmp_path / "c.npz")
+    r = np.load(tmp_path / "r.npz")
+    for k in r.files:
+        if k.endswith("pol1_states"):
+            st = r[k.replace("_states", "_status")]
+            ok = (st == 0) & (c[k.replace("_states", "_status")] == 0)
+            assert np.allclose(c[k][ok], r[k][ok], rtol=1e-9, atol=0), k
