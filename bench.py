@@ -39,7 +39,7 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--sets", type=int, default=N_SETS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sets", type=int, default=24, help="sets of the oracle sample")
+    ap.add_argument("--cpu-sets", type=int, default=160, help="sets of the oracle sample")
     return ap.parse_args()
 
 
@@ -65,7 +65,7 @@ class ClockSampler:
 
     def start(self):
         try:
-            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", self.index, "--query-gpu=" + self.Q,
                                           "--format=csv,noheader,nounits", "-lms", "200"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.th = threading.Thread(target=self._read, daemon=True)
@@ -213,7 +213,9 @@ def run_native(args):
         step()
     barrier()
 
-    clk = ClockSampler(torch.cuda.current_device())
+    props = torch.cuda.get_device_properties(dev)
+    uuid = str(getattr(props, "uuid", "") or "")
+    clk = ClockSampler(("GPU-" + uuid) if uuid and not uuid.startswith("GPU-") else (uuid or str(dev.index)))
     clk.start()
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
     start = torch.cuda.Event(enable_timing=True)
@@ -239,7 +241,6 @@ def run_native(args):
     status = out["status"].cpu().numpy()
     w32 = 35 * E + 45 * N
     wsfu = 6 * E + N
-    props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
     f_mhz = clocks.get("sm_mhz") or 1440.0
     t_int = kern_ms[1] / 1e3
