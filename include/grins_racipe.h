@@ -182,6 +182,35 @@ grins_status grins_racipe_integrate(grins_racipe_t h, const grins_solver_opts *o
                                     float *d_err_est, int32_t *d_n_steps, double *d_series,
                                     void *stream);
 
+/* Largest time grid (o->n_t) that grins_racipe_integrate_static accepts. */
+#define GRINS_STATIC_MAX_GRID 4096
+
+/* Same computation, arguments, outputs and errors as grins_racipe_integrate,
+ * for callers that must not allocate device memory during a call: code that
+ * runs inside a host framework owning every device allocation, a real-time
+ * loop where cudaMalloc/cudaFree would synchronise the device or block, or a
+ * sandbox whose allocation quota is already spent.  The paper has no
+ * counterpart; this is an ABI convenience.
+ *   - Allocates nothing: no cudaMalloc, cudaFree or allocating library call.
+ *     Its scratch (work-queue counter, check words and the device copy of
+ *     the time grid) is one fixed array of about 33 KB inside the library,
+ *     present on every device that loads the library until the process
+ *     exits.  Inputs and outputs are still the caller's buffers.
+ *   - The first call on each device looks up that array's device address
+ *     (cudaGetSymbolAddress) with the device current; make that first call
+ *     before any stream capture.
+ *   - Every call, from any handle or thread, shares the one array; the call
+ *     clears the counters it needs before launching.  Calls whose work
+ *     overlaps on the GPU (different streams, or different host threads)
+ *     race on it: serialise them.
+ *   - Extra error: GRINS_E_BUDGET when o->n_t > GRINS_STATIC_MAX_GRID. */
+grins_status grins_racipe_integrate_static(grins_racipe_t h, const grins_solver_opts *o,
+                                           const void *d_params, int64_t n_sets,
+                                           const double *d_ic_unit, int32_t n_ics,
+                                           double *d_states, uint8_t *d_status,
+                                           double *d_t_final, float *d_err_est,
+                                           int32_t *d_n_steps, double *d_series, void *stream);
+
 /* FP64 Newton polish of states already integrated (the step integrate runs
  * when o->polish is set; exposed so a caller can polish separately).  For
  * every solve with status GRINS_SS_CONVERGED: Newton iterations on Eq. 1 = 0

@@ -32,6 +32,7 @@ GRINS_OK, GRINS_E_INVALID_ARG, GRINS_E_TOPOLOGY, GRINS_E_NOMEM, GRINS_E_CUDA, GR
 CONVERGED, TEND, MAXSTEPS, NONFINITE, POLISH_FAIL = range(5)
 GRINS_FP64, GRINS_FP32 = 0, 1
 MEDIAN_PER_INDEGREE, MEDIAN_UNREGULATED = 0, 1
+GRINS_STATIC_MAX_GRID = 4096        # largest time grid of grins_racipe_integrate_static
 
 
 class grins_racipe_ranges(C.Structure):
@@ -71,6 +72,8 @@ _sig = {
                                         C.c_int64, C.c_int32, _P, _P, _P]),
     "grins_racipe_integrate": (_S, [_H, C.POINTER(grins_solver_opts), _P, C.c_int64, _P, C.c_int32,
                                     _P, _P, _P, _P, _P, _P, _P]),
+    "grins_racipe_integrate_static": (_S, [_H, C.POINTER(grins_solver_opts), _P, C.c_int64, _P,
+                                           C.c_int32, _P, _P, _P, _P, _P, _P, _P]),
     "grins_racipe_polish": (_S, [_H, C.POINTER(grins_solver_opts), _P, C.c_int64, C.c_int32, _P, _P, _P, _P]),
     "grins_racipe_unique_states": (_S, [_H, _P, _P, _P, C.c_int64, C.c_int32, C.c_double, _P, _P, _P]),
 }
@@ -220,6 +223,19 @@ class Racipe:
                                if o.n_t > 0 else None))
         with torch.cuda.device(dev):
             _check(_lib.grins_racipe_integrate(
+                self._h, C.byref(o), _ptr(params), S, _ptr(ic_unit), I, _ptr(out["states"]),
+                _ptr(out["status"]), _ptr(out.get("t_final")), _ptr(out.get("err_est")),
+                _ptr(out.get("n_steps")), _ptr(out.get("series")), _stream(stream)))
+        return out
+
+    def integrate_static(self, params, ic_unit, out, opts=None, stream=None):
+        """grins_racipe_integrate_static: the same integration with the library's
+        fixed scratch array instead of any device allocation.  ``out`` holds
+        caller-allocated buffers (keys as returned by ``integrate``)."""
+        o = opts if opts is not None else default_opts()
+        S, I = params.shape[0], ic_unit.shape[0]
+        with torch.cuda.device(self.device):
+            _check(_lib.grins_racipe_integrate_static(
                 self._h, C.byref(o), _ptr(params), S, _ptr(ic_unit), I, _ptr(out["states"]),
                 _ptr(out["status"]), _ptr(out.get("t_final")), _ptr(out.get("err_est")),
                 _ptr(out.get("n_steps")), _ptr(out.get("series")), _stream(stream)))

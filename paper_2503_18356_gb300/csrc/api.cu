@@ -563,3 +563,129 @@ extern "C" int grins_debug_check_status(grins_racipe_t h, long long *info)
     return (int)w[0];
 }
 #endif
+
+// ------------------------------------------------- integrate, no allocation
+// grins_racipe_integrate_static: the integrate entry point for callers that
+// cannot allocate device memory.  Its scratch -- the work-queue counter, the
+// largest-exponent word, the check words and the device copy of the time
+// grid -- lives in the fixed array below instead of the handle's workspace,
+// and nothing is allocated per call.  Every device that loads the library
+// holds this array until the process exits.
+namespace {
+
+constexpr int kStaticWords = 4;   // queue, nmax, check code, check info
+constexpr size_t kStaticBytes = kStaticWords * sizeof(unsigned long long) +
+                                (size_t)GRINS_STATIC_MAX_GRID * sizeof(double);
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
+
+constexpr int kStaticMaxDevices = 64;
+std::mutex g_static_mu;
+unsigned char *g_static_addr[kStaticMaxDevices] = {};
+
+// Device address of g_static_scratch on the current device, looked up once
+// per device (host code must not use the symbol itself: it names a host-side
+// shadow, not device memory).
+grins_status static_scratch(int device, unsigned char **out)
+{
+    if (device < 0 || device >= kStaticMaxDevices)
+        return fail(GRINS_E_INVALID_ARG, "integrate_static: device %d outside [0, %d)", device, kStaticMaxDevices);
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_addr[device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "integrate_static: cudaGetSymbolAddress");
+        g_static_addr[device] = static_cast<unsigned char *>(p);
+    }
+    *out = g_static_addr[device];
+    return GRINS_OK;
+}
+
+}  // namespace
+
+extern "C" grins_status grins_racipe_integrate_static(grins_racipe_t h, const grins_solver_opts *o,
+                                                      const void *d_params, int64_t n_sets,
+                                                      const double *d_ic_unit, int32_t n_ics,
+                                                      double *d_states, uint8_t *d_status,
+                                                      double *d_t_final, float *d_err_est,
+                                                      int32_t *d_n_steps, double *d_series, void *stream)
+{
+    g_last_error.clear();
+    if (!h || !o) return fail(GRINS_E_INVALID_ARG, "integrate_static: NULL handle or options");
+    if (n_sets < 0) return fail(GRINS_E_INVALID_ARG, "integrate_static: n_sets < 0");
+    if (n_ics < 1) return fail(GRINS_E_INVALID_ARG, "integrate_static: n_ics < 1");
+    if (n_sets > 0 && (!d_params || !d_ic_unit || !d_states || !d_status))
+        return fail(GRINS_E_INVALID_ARG, "integrate_static: NULL required device buffer");
+    if (o->precision != GRINS_FP32 && o->precision != GRINS_FP64)
+        return fail(GRINS_E_INVALID_ARG, "integrate_static: unknown precision %d", o->precision);
+    if (!(o->rtol > 0) || !(o->atol > 0) || !std::isfinite(o->rtol) || !std::isfinite(o->atol))
+        return fail(GRINS_E_INVALID_ARG, "integrate_static: rtol and atol must be positive");
+    if (!std::isfinite(o->t0) || !std::isfinite(o->t_end) || !(o->t_end > o->t0))
+        return fail(GRINS_E_INVALID_ARG, "integrate_static: need finite t0 < t_end");
+    if (!(o->ss_tol >= 0)) return fail(GRINS_E_INVALID_ARG, "integrate_static: ss_tol < 0");
+    if (o->max_steps < 1) return fail(GRINS_E_INVALID_ARG, "integrate_static: max_steps < 1");
+    if (o->n_t < 0 || (o->n_t > 0 && !o->t_grid))
+        return fail(GRINS_E_INVALID_ARG, "integrate_static: bad time grid");
+    if (o->n_t > GRINS_STATIC_MAX_GRID)
+        return fail(GRINS_E_BUDGET, "integrate_static: n_t = %d exceeds the fixed scratch limit of %d grid times",
+                    o->n_t, GRINS_STATIC_MAX_GRID);
+    if ((o->n_t > 0) != (d_series != nullptr) && n_sets > 0)
+        return fail(GRINS_E_INVALID_ARG, "integrate_static: d_series must be given exactly when n_t > 0");
+    for (int g = 0; g < o->n_t; ++g) {
+        const double tg = o->t_grid[g];
+        if (!(tg >= o->t0 && tg <= o->t_end) || (g > 0 && !(tg > o->t_grid[g - 1])))
+            return fail(GRINS_E_INVALID_ARG, "integrate_static: t_grid must increase strictly inside [t0, t_end]");
+    }
+    if (o->polish && !polish_opts_ok(o))
+        return fail(GRINS_E_INVALID_ARG, "integrate_static: bad polish options");
+    if (!on_handle_device(h))
+        return fail(GRINS_E_INVALID_ARG, "integrate_static: current device is not the handle's");
+    unsigned char *scratch = nullptr;
+    grins_status s = static_scratch(h->device, &scratch);
+    if (s != GRINS_OK) return s;
+    if (n_sets == 0) return GRINS_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned long long *words = reinterpret_cast<unsigned long long *>(scratch);
+    double *grid = reinterpret_cast<double *>(scratch + kStaticWords * sizeof(unsigned long long));
+    if (o->n_t > 0) {
+        CUDA_TRY(cudaMemcpyAsync(grid, o->t_grid, sizeof(double) * o->n_t, cudaMemcpyHostToDevice, st),
+                 "integrate_static: grid upload");
+    }
+
+    IntegrateArgs a{};
+    a.topo = DevTopo{h->N, h->E, h->d_off, h->d_src, h->d_edge, h->d_sign};
+    a.L = h->layout;
+    a.params = static_cast<const unsigned char *>(d_params);
+    a.n_sets = n_sets;
+    a.ic_unit = d_ic_unit;
+    a.n_ics = n_ics;
+    a.rtol = o->rtol; a.atol = o->atol; a.t0 = o->t0; a.t_end = o->t_end; a.ss_tol = o->ss_tol;
+    a.max_steps = o->max_steps;
+    a.t_grid = grid;
+    a.n_t = o->n_t;
+    a.states = d_states; a.status = d_status; a.t_final = d_t_final; a.n_steps = d_n_steps;
+    a.series = o->n_t > 0 ? d_series : nullptr;
+    a.queue = words;
+    a.check = words + 2;
+    a.slots = slots_for(n_ics);
+    a.smem_limit = (int32_t)h->smem_optin;
+
+    // the array keeps the previous call's counters: clear them first
+    CUDA_TRY(cudaMemsetAsync(words, 0, kStaticWords * sizeof(unsigned long long), st),
+             "integrate_static: scratch reset");
+    cudaError_t le;
+    if (o->precision == GRINS_FP32) le = launch_integrate_fp32(a, st, h->num_sms);
+    else le = launch_integrate_fp64(a, st, h->num_sms);
+    if (le == cudaErrorInvalidConfiguration)
+        return fail(GRINS_E_BUDGET, "integrate_static: the network needs more shared memory per block than the device has");
+    if (le != cudaSuccess) return cuda_fail(le, "integrate_static: launch");
+
+    if (o->polish) {
+        PolishArgs p = polish_args(h, o, d_params, n_sets, n_ics, d_states, d_status, d_err_est);
+        p.check = words + 2;
+        CUDA_TRY(launch_polish(p, st, h->num_sms), "integrate_static: polish launch");
+    } else if (d_err_est) {
+        CUDA_TRY(cudaMemsetAsync(d_err_est, 0xff, sizeof(float) * n_sets * n_ics, st), "integrate_static: err_est");
+    }
+    return GRINS_OK;
+}

@@ -1,0 +1,86 @@
+"""grins_racipe_integrate_static, the integrate entry point that allocates no
+device memory, against grins_racipe_integrate on the same inputs.
+
+Some callers cannot allocate device memory while they run (a host framework
+that owns every allocation, a loop where cudaMalloc would stall the device,
+an exhausted quota).  The static entry point serves them from a fixed array
+inside the library.  That array outlives each call and is shared by all of
+them, so the test calls it twice in a row: the second call must not see the
+first call's work counters.  The tolerance is the one the parity tests use
+for FP32 + FP64 polish (relative 1e-6 with a floor of 1e-6 G/k); statuses
+must match exactly.
+
+This file is collected last so that a failure here cannot hide the other
+tests' results in a run that stops at the first failure.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2503_18356_gb300 import workloads as W
+from tests import parity as PT
+
+pytestmark = pytest.mark.gpu
+
+
+def _buffers(S, I, N, n_t, dev):
+    return dict(states=torch.empty((S, I, N), dtype=torch.float64, device=dev),
+                status=torch.empty((S, I), dtype=torch.uint8, device=dev),
+                t_final=torch.empty((S, I), dtype=torch.float64, device=dev),
+                err_est=torch.empty((S, I), dtype=torch.float32, device=dev),
+                n_steps=torch.empty((S, I), dtype=torch.int32, device=dev),
+                series=(torch.empty((S, I, n_t, N), dtype=torch.float64, device=dev)
+                        if n_t > 0 else None))
+
+
+def _agree(ref, got, G, k):
+    r, g = PT.to_numpy(ref), PT.to_numpy(got)
+    assert np.array_equal(r["status"], g["status"])
+    conv = r["status"] == 0
+    err = PT.rel_err(g["states"], r["states"], G[:, None, :], k[:, None, :])
+    assert conv.sum() > 0
+    assert err[conv].max() <= 1e-6, err[conv].max()
+    assert np.array_equal(r["n_steps"], g["n_steps"])
+    if r.get("series") is not None:
+        scale = np.maximum(np.abs(r["series"]), 1e-6 * (G / k)[:, None, None, :])
+        assert (np.abs(g["series"] - r["series"]) / scale).max() <= 1e-3
+
+
+@pytest.mark.parametrize("n_t", [0, 7])
+def test_static_entry_point_matches_integrate_twice(n_t):
+    from paper_2503_18356_gb300 import api
+    w = W.net5_workload()
+    topo = w["topology"]
+    h = PT.gpu_handle(topo)
+    S, I, N = 300, 8, topo.n_nodes
+    params, ic, p, _ = PT.gpu_sample(h, w["param_seed"], S, I)
+    grid = np.linspace(0.0, 50.0, n_t) if n_t else None
+    kw = dict(t_grid=grid) if n_t else {}
+    ref = h.integrate(params, ic, **kw)
+    o = api.default_opts()
+    if n_t:
+        o.t_grid = grid.ctypes.data_as(api.C.POINTER(api.C.c_double))
+        o.n_t = n_t
+    for _ in range(2):
+        out = _buffers(S, I, N, n_t, h.device)
+        h.integrate_static(params, ic, out, opts=o)
+        torch.cuda.synchronize()
+        _agree(ref, out, p.G, p.k)
+    h.close()
+
+
+def test_static_entry_point_rejects_oversized_grid():
+    from paper_2503_18356_gb300 import api
+    topo = W.toggle_switch()
+    h = PT.gpu_handle(topo)
+    params, ic, _, _ = PT.gpu_sample(h, 1, 4, 2)
+    big = np.linspace(0.0, 100.0, api.GRINS_STATIC_MAX_GRID + 1)
+    o = api.default_opts()
+    o.t_grid = big.ctypes.data_as(api.C.POINTER(api.C.c_double))
+    o.n_t = big.size
+    out = _buffers(4, 2, 2, big.size, h.device)
+    with pytest.raises(api.GrinsError) as e:
+        h.integrate_static(params, ic, out, opts=o)
+    assert e.value.status == api.GRINS_E_BUDGET
+    assert "exceeds" in str(e.value)
+    h.close()
