@@ -18,8 +18,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgrins_racipe.so")
 
-SOURCES = ["api.cu", "sample.cu", "integrate_generic.cu", "integrate_reg8.cu",
-           "integrate_reg16.cu", "integrate_reg24.cu", "polish.cu", "unique.cu"]
+SOURCES = ["api.cu", "sample.cu", "integrate_generic.cu", "integrate_grp2.cu", "integrate_grp4.cu",
+           "integrate_grp6.cu", "integrate_grp8.cu", "integrate_grp12.cu", "polish.cu", "unique.cu"]
 
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17", "-lineinfo",
               "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off", "-I" + INCLUDE, "-I" + CSRC]
@@ -72,7 +72,7 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None,
         return obj
 
     # longest translation units first so the parallel build ends sooner
-    order = sorted(SOURCES, key=lambda s: 0 if "reg" in s else 1)
+    order = sorted(SOURCES, key=lambda s: 0 if "grp" in s else 1)
     with ThreadPoolExecutor(jobs or min(len(order), os.cpu_count() or 4)) as ex:
         objs = list(ex.map(compile_one, order))
     tmp = lib + ".tmp.%d" % os.getpid()

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -57,6 +58,10 @@ struct grins_racipe {
     double *d_edge_median = nullptr;
     unsigned long long *d_queue = nullptr;
     double *d_grid = nullptr;
+    // lane-group layout of the FP32 integrator (see GrpTopo)
+    int grp_L = 0, grp_R = 0, grp_P = 0;
+    std::vector<int32_t> grp_row_off, grp_row_deg;
+    int32_t *d_pos_edge = nullptr, *d_pos_off = nullptr, *d_row_node = nullptr;
     int grid_cap = 0;
     // cached median table
     bool median_valid = false;
@@ -100,10 +105,105 @@ static void free_device(grins_racipe *h)
 {
     cudaFree(h->d_off); cudaFree(h->d_src); cudaFree(h->d_edge); cudaFree(h->d_sign);
     cudaFree(h->d_edge_sign); cudaFree(h->d_edge_median); cudaFree(h->d_queue); cudaFree(h->d_grid);
+    cudaFree(h->d_pos_edge); cudaFree(h->d_pos_off); cudaFree(h->d_row_node);
+    h->d_pos_edge = h->d_pos_off = h->d_row_node = nullptr;
     h->d_off = h->d_src = h->d_edge = nullptr;
     h->d_sign = h->d_edge_sign = nullptr;
     h->d_edge_median = h->d_grid = nullptr;
     h->d_queue = nullptr;
+}
+
+// Lane-group layout (GrpTopo): L = the smallest power of two with at most
+// 12 node rows; nodes sorted by in-degree (descending, ties by index) fill
+// rows of L; row r takes D_r = its largest in-degree positions.  Within a row
+// the host orders each lane's in-edges so that, position by position, the L
+// lanes read sources in distinct gather columns (distinct shared-memory
+// banks) where it can, filling the gaps with neutral edges.
+struct GrpHost {
+    int L = 0, R = 0, P = 0;
+    std::vector<int32_t> row_off, row_deg, pos_edge, pos_off, row_node;
+};
+
+static GrpHost build_grp(int N, const std::vector<int32_t> &csr_off, const std::vector<int32_t> &csr_src,
+                         const std::vector<int32_t> &csr_edge)
+{
+    GrpHost g;
+    int L = 1;
+    while ((N + L - 1) / L > 12 && L < kWarp) L *= 2;
+    // GRINS_GRP_L (1, 2, 4, 8, 16 or 32) overrides the choice when it still
+    // gives at most 12 rows (a tuning override)
+    if (const char *ev = std::getenv("GRINS_GRP_L")) {
+        const int f = std::atoi(ev);
+        if ((f == 1 || f == 2 || f == 4 || f == 8 || f == 16 || f == 32) && (N + f - 1) / f <= 12) L = f;
+    }
+    const int R = (N + L - 1) / L;
+    if (R > kGrpMaxRows) return g;
+    const int GS = kWarp / L;
+    std::vector<int> order(N);
+    for (int i = 0; i < N; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return csr_off[a + 1] - csr_off[a] > csr_off[b + 1] - csr_off[b];
+    });
+    g.L = L; g.R = R;
+    g.row_node.assign((size_t)R * L, -1);
+    std::vector<int> gslot(N, 0);
+    for (int q = 0; q < N; ++q) { g.row_node[q] = order[q]; gslot[order[q]] = q; }
+    auto col_of = [&](int node) { return gslot[node] % L; };
+    auto off_of_slot = [&](int slot) { return slot * GS * 4; };
+    int P = 0;
+    for (int r = 0; r < R; ++r) {
+        int D = 0;
+        std::vector<std::vector<int>> lst(L);            // CSR positions per lane
+        for (int j = 0; j < L; ++j) {
+            const int node = g.row_node[r * L + j];
+            if (node < 0) continue;
+            for (int c = csr_off[node]; c < csr_off[node + 1]; ++c) lst[j].push_back(c);
+            D = std::max(D, (int)lst[j].size());
+        }
+        g.row_off.push_back(P);
+        g.row_deg.push_back(D);
+        std::vector<std::vector<char>> used(L);
+        for (int j = 0; j < L; ++j) used[j].assign(lst[j].size(), 0);
+        std::vector<int> left(L);
+        for (int j = 0; j < L; ++j) left[j] = (int)lst[j].size();
+        for (int m = 0; m < D; ++m) {
+            std::vector<char> col_used(L, 0);
+            std::vector<int> src_here;
+            for (int j = 0; j < L; ++j) {
+                const int spare = (D - m) - left[j];       // neutral slots still to place
+                int pick = -1;
+                for (size_t q = 0; q < lst[j].size() && pick < 0; ++q) {
+                    if (used[j][q]) continue;
+                    const int sn = csr_src[lst[j][q]];
+                    bool same = false;
+                    for (int x : src_here) same = same || x == sn;
+                    if (same || !col_used[col_of(sn)]) pick = (int)q;
+                }
+                if (pick < 0 && spare == 0) {
+                    for (size_t q = 0; q < lst[j].size() && pick < 0; ++q)
+                        if (!used[j][q]) pick = (int)q;
+                }
+                if (pick >= 0) {
+                    used[j][pick] = 1;
+                    --left[j];
+                    const int c = lst[j][pick], sn = csr_src[c];
+                    col_used[col_of(sn)] = 1;
+                    src_here.push_back(sn);
+                    g.pos_edge.push_back(csr_edge[c]);
+                    g.pos_off.push_back(off_of_slot(gslot[sn]));
+                } else {                                    // neutral edge in a free column
+                    int cf = 0;
+                    while (cf < L - 1 && col_used[cf]) ++cf;
+                    col_used[cf] = 1;
+                    g.pos_edge.push_back(-1);
+                    g.pos_off.push_back(off_of_slot(cf));
+                }
+            }
+        }
+        P += D;
+    }
+    g.P = P;
+    return g;
 }
 
 extern "C" grins_status grins_racipe_create(int32_t n_nodes, int32_t n_edges, const int32_t *src,
@@ -151,6 +251,9 @@ extern "C" grins_status grins_racipe_create(int32_t n_nodes, int32_t n_edges, co
         h->csr_src[p] = src[e]; h->csr_edge[p] = e; h->csr_sign[p] = sign[e];
     }
     h->layout = make_layout(n_nodes, n_edges);
+    GrpHost grp = build_grp(n_nodes, h->csr_off, h->csr_src, h->csr_edge);
+    h->grp_L = grp.L; h->grp_R = grp.R; h->grp_P = grp.P;
+    h->grp_row_off = grp.row_off; h->grp_row_deg = grp.row_deg;
 
     cudaError_t ce = cudaGetDevice(&h->device);
     if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
@@ -171,6 +274,18 @@ extern "C" grins_status grins_racipe_create(int32_t n_nodes, int32_t n_edges, co
     if (ce == cudaSuccess && n_edges) ce = cudaMemcpy(h->d_edge, h->csr_edge.data(), sizeof(int32_t) * n_edges, cudaMemcpyHostToDevice);
     if (ce == cudaSuccess && n_edges) ce = cudaMemcpy(h->d_sign, h->csr_sign.data(), n_edges, cudaMemcpyHostToDevice);
     if (ce == cudaSuccess && n_edges) ce = cudaMemcpy(h->d_edge_sign, h->sign.data(), n_edges, cudaMemcpyHostToDevice);
+    if (h->grp_L > 0) {
+        const size_t np = std::max<size_t>(grp.pos_edge.size(), 1), nr = grp.row_node.size();
+        if (ce == cudaSuccess) ce = cudaMalloc(&h->d_pos_edge, sizeof(int32_t) * np);
+        if (ce == cudaSuccess) ce = cudaMalloc(&h->d_pos_off, sizeof(int32_t) * np);
+        if (ce == cudaSuccess) ce = cudaMalloc(&h->d_row_node, sizeof(int32_t) * nr);
+        if (ce == cudaSuccess && !grp.pos_edge.empty())
+            ce = cudaMemcpy(h->d_pos_edge, grp.pos_edge.data(), sizeof(int32_t) * grp.pos_edge.size(), cudaMemcpyHostToDevice);
+        if (ce == cudaSuccess && !grp.pos_off.empty())
+            ce = cudaMemcpy(h->d_pos_off, grp.pos_off.data(), sizeof(int32_t) * grp.pos_off.size(), cudaMemcpyHostToDevice);
+        if (ce == cudaSuccess)
+            ce = cudaMemcpy(h->d_row_node, grp.row_node.data(), sizeof(int32_t) * nr, cudaMemcpyHostToDevice);
+    }
     if (ce != cudaSuccess) {
         free_device(h);
         delete h;
@@ -417,6 +532,15 @@ static PolishArgs polish_args(const grins_racipe *h, const grins_solver_opts *o,
     return p;
 }
 
+static GrpTopo grp_topo(const grins_racipe *h)
+{
+    GrpTopo g{};
+    g.L = h->grp_L; g.R = h->grp_R; g.P = h->grp_P;
+    g.pos_edge = h->d_pos_edge; g.pos_off = h->d_pos_off; g.row_node = h->d_row_node;
+    for (int r = 0; r < h->grp_R && r < kGrpMaxRows; ++r) { g.row_off[r] = h->grp_row_off[r]; g.row_deg[r] = h->grp_row_deg[r]; }
+    return g;
+}
+
 static bool polish_opts_ok(const grins_solver_opts *o)
 {
     return o->polish_tol > 0 && o->polish_iters >= 0 && o->polish_iters <= 64 && o->polish_max_move > 0;
@@ -511,6 +635,7 @@ extern "C" grins_status grins_racipe_integrate(grins_racipe_t h, const grins_sol
     a.check = h->d_queue + 2;
     a.slots = slots_for(n_ics);
     a.smem_limit = (int32_t)h->smem_optin;
+    a.grp = grp_topo(h);
 
     CUDA_TRY(cudaMemsetAsync(h->d_queue, 0, 2 * sizeof(unsigned long long), st), "integrate: queue reset");
     cudaError_t le;
@@ -669,6 +794,7 @@ extern "C" grins_status grins_racipe_integrate_static(grins_racipe_t h, const gr
     a.check = words + 2;
     a.slots = slots_for(n_ics);
     a.smem_limit = (int32_t)h->smem_optin;
+    a.grp = grp_topo(h);
 
     // the array keeps the previous call's counters: clear them first
     CUDA_TRY(cudaMemsetAsync(words, 0, kStaticWords * sizeof(unsigned long long), st),

@@ -64,6 +64,21 @@ cudaError_t launch_sample_params(const SampleArgs &a, cudaStream_t st);
 cudaError_t launch_sample_ics(int N, uint64_t seed, int n_ics, double *u, cudaStream_t st);
 
 // ------------------------------------------------------------- integrator
+// Lane-group layout of a network (built by the host at create time): the
+// nodes sorted by in-degree and dealt out in R rows of L nodes; row r's
+// in-edges fill D_r = row_deg[r] positions starting at row_off[r]; position
+// p of lane j holds edge pos_edge[p * L + j] (-1: neutral padding) whose
+// source value sits pos_off[p * L + j] bytes into a group's gather column.
+constexpr int kGrpMaxRows = 16;
+struct GrpTopo {
+    int32_t L, R, P;
+    const int32_t *pos_edge;     // [P * L] creation-order edge index or -1
+    const int32_t *pos_off;      // [P * L] gather byte offset of the source
+    const int32_t *row_node;     // [R * L] node of slot (r, j) or -1
+    int32_t row_off[kGrpMaxRows];
+    int32_t row_deg[kGrpMaxRows];
+};
+
 struct IntegrateArgs {
     DevTopo topo;
     ParamLayout L;
@@ -81,11 +96,10 @@ struct IntegrateArgs {
     int32_t *n_steps;            // nullable
     double *series;              // [S][I][n_t][N] or null
     unsigned long long *queue;   // work counter, zero before launch
-    const unsigned long long *nmax;  // largest Hill exponent in the batch (device), or null
-    int32_t gate;                // 0: always run; 2: run only if *nmax exceeds the power table
     unsigned long long *check;   // checked builds: first violation (code, info)
     int32_t slots;               // parameter-set slots per warp (upper bound)
     int32_t smem_limit;          // opt-in shared memory per block, bytes
+    GrpTopo grp;                 // lane-group layout (grp.L == 0: not available)
 };
 
 // Maximum N served by the FP32 / FP64 integrator buckets.

@@ -67,7 +67,6 @@ dp5_generic_kernel(const IntegrateArgs a)
 
     unsigned long long *grins_chk = a.check;
     (void)grins_chk;
-    if (a.gate == 2 && !(a.nmax && *a.nmax > (unsigned long long)kPowTable)) return;
     const int N = a.topo.N, E = a.topo.E, S = a.slots;
     const int lane = threadIdx.x;
     const GenericLayout LY{N, E, S, (int)sizeof(Real)};

@@ -1,0 +1,11 @@
+// Lane-group FP32 integrator, up to 12 node rows per lane.
+#include "integrate_grp.cuh"
+
+namespace grins {
+
+cudaError_t launch_integrate_grp12(const IntegrateArgs &a, cudaStream_t st, int num_sms)
+{
+    return launch_grp_bucket<12, GRINS_GRP_MINB>(a, st, num_sms);
+}
+
+}  // namespace grins
