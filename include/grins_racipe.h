@@ -182,6 +182,14 @@ grins_status grins_racipe_integrate(grins_racipe_t h, const grins_solver_opts *o
                                     float *d_err_est, int32_t *d_n_steps, double *d_series,
                                     void *stream);
 
+/* Which FP32 integrator kernel the handle's integrate calls use, as text:
+ * the lane-group layout (lanes per solve L, node rows R, edge positions P)
+ * and whether the kernel specialised to this network at run time (NVRTC)
+ * is in use, or why not (before the first FP32 integrate call it reports
+ * that nothing has been compiled yet).  The string is owned by the handle
+ * and valid until the next call on it. */
+const char *grins_racipe_integrator(grins_racipe_t h);
+
 /* Largest time grid (o->n_t) that grins_racipe_integrate_static accepts. */
 #define GRINS_STATIC_MAX_GRID 4096
 

@@ -67,6 +67,7 @@ _sig = {
     "grins_racipe_create": (_S, [C.c_int32, C.c_int32, _P, _P, _P, C.POINTER(_H)]),
     "grins_racipe_destroy": (_S, [_H]),
     "grins_racipe_param_stride": (C.c_int64, [_H]),
+    "grins_racipe_integrator": (C.c_char_p, [_H]),
     "grins_racipe_node_medians": (_S, [_H, C.POINTER(grins_racipe_ranges), _P]),
     "grins_racipe_sample_params": (_S, [_H, C.POINTER(grins_racipe_ranges), C.c_uint64, C.c_int64,
                                         C.c_int64, C.c_int32, _P, _P, _P]),
@@ -142,6 +143,10 @@ class Racipe:
     @classmethod
     def from_topology(cls, topo, device=None):
         return cls(*topo.edges(), device=device)
+
+    def integrator(self) -> str:
+        """Which FP32 integrator kernel this handle uses (grins_racipe_integrator)."""
+        return _lib.grins_racipe_integrator(self._h).decode()
 
     def close(self):
         if getattr(self, "_h", None):

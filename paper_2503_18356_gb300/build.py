@@ -19,7 +19,32 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgrins_racipe.so")
 
 SOURCES = ["api.cu", "sample.cu", "integrate_generic.cu", "integrate_grp2.cu", "integrate_grp4.cu",
-           "integrate_grp6.cu", "integrate_grp8.cu", "integrate_grp12.cu", "polish.cu", "unique.cu"]
+           "integrate_grp6.cu", "integrate_grp8.cu", "integrate_grp12.cu", "polish.cu", "unique.cu",
+           "jit.cu"]
+
+# Sources the run-time compile of the lane-group kernel needs (jit.cu embeds
+# them as string literals): (include name, path).
+JIT_SOURCES = [("grins_racipe.h", os.path.join(INCLUDE, "grins_racipe.h")),
+               ("common.cuh", os.path.join(CSRC, "common.cuh")),
+               ("integrate.cuh", os.path.join(CSRC, "integrate.cuh")),
+               ("integrate_grp.cuh", os.path.join(CSRC, "integrate_grp.cuh"))]
+
+
+def write_jit_sources(bdir):
+    """jit_sources.inc: the JIT_SOURCES files as C++ raw string literals."""
+    parts = []
+    for name, path in JIT_SOURCES:
+        text = open(path).read()
+        assert ")GRINSJIT\"" not in text
+        parts.append('R"GRINSJIT(' + text + ')GRINSJIT"')
+    inc = ("static const int kJitSourceCount = %d;\n" % len(JIT_SOURCES)
+           + "static const char *const kJitSourceNames[] = {"
+           + ", ".join('"%s"' % n for n, _ in JIT_SOURCES) + "};\n"
+           + "static const char *const kJitSources[] = {\n" + ",\n".join(parts) + "};\n")
+    path = os.path.join(bdir, "jit_sources.inc")
+    if not os.path.exists(path) or open(path).read() != inc:
+        with open(path, "w") as f:
+            f.write(inc)
 
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17", "-lineinfo",
               "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off", "-I" + INCLUDE, "-I" + CSRC]
@@ -57,7 +82,8 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None,
     bdir = BUILD + ("_checked" if checked else "")
     os.makedirs(bdir, exist_ok=True)
     nvcc = _nvcc()
-    flags = NVCC_FLAGS + (["-DGRINS_CHECKED"] if checked else [])
+    write_jit_sources(bdir)
+    flags = NVCC_FLAGS + ["-I" + bdir] + (["-DGRINS_CHECKED"] if checked else [])
 
     def compile_one(src):
         obj = os.path.join(bdir, os.path.splitext(src)[0] + ".o")
@@ -77,7 +103,7 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None,
         objs = list(ex.map(compile_one, order))
     tmp = lib + ".tmp.%d" % os.getpid()
     subprocess.check_call([nvcc, "-shared", "-gencode", "arch=compute_103a,code=sm_103a",
-                           "-o", tmp] + objs)
+                           "-o", tmp] + objs + ["-ldl"])
     os.replace(tmp, lib)
     return lib
 

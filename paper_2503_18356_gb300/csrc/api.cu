@@ -62,6 +62,9 @@ struct grins_racipe {
     int grp_L = 0, grp_R = 0, grp_P = 0;
     std::vector<int32_t> grp_row_off, grp_row_deg;
     int32_t *d_pos_edge = nullptr, *d_pos_off = nullptr, *d_row_node = nullptr;
+    std::string jit_why = "not compiled yet";          // why no run-time compiled kernel is used
+    bool jit_used = false;
+    std::string info;                                  // grins_racipe_integrator text
     int grid_cap = 0;
     // cached median table
     bool median_valid = false;
@@ -306,6 +309,20 @@ extern "C" grins_status grins_racipe_destroy(grins_racipe_t h)
     if (cur != h->device) cudaSetDevice(cur);
     delete h;
     return GRINS_OK;
+}
+
+extern "C" const char *grins_racipe_integrator(grins_racipe_t h)
+{
+    if (!h) return "";
+    char buf[160];
+    if (h->grp_L > 0)
+        std::snprintf(buf, sizeof(buf), "lane-group DP5(4), L=%d lanes per solve, R=%d node rows, P=%d edge positions",
+                      h->grp_L, h->grp_R, h->grp_P);
+    else
+        std::snprintf(buf, sizeof(buf), "generic shared-memory DP5(4) (no lane-group layout)");
+    h->info = buf;
+    if (h->grp_L > 0) h->info += h->jit_used ? "; compiled for this network at run time" : "; run-time layout (" + h->jit_why + ")";
+    return h->info.c_str();
 }
 
 extern "C" int64_t grins_racipe_param_stride(grins_racipe_t h)
@@ -636,6 +653,10 @@ extern "C" grins_status grins_racipe_integrate(grins_racipe_t h, const grins_sol
     a.slots = slots_for(n_ics);
     a.smem_limit = (int32_t)h->smem_optin;
     a.grp = grp_topo(h);
+    if (o->precision == GRINS_FP32) {
+        a.grp_jit = grp_jit_kernel(a.grp, &h->jit_why);
+        h->jit_used = a.grp_jit != nullptr;
+    }
 
     CUDA_TRY(cudaMemsetAsync(h->d_queue, 0, 2 * sizeof(unsigned long long), st), "integrate: queue reset");
     cudaError_t le;
@@ -795,6 +816,7 @@ extern "C" grins_status grins_racipe_integrate_static(grins_racipe_t h, const gr
     a.slots = slots_for(n_ics);
     a.smem_limit = (int32_t)h->smem_optin;
     a.grp = grp_topo(h);
+    a.grp_jit = grp_jit_lookup(a.grp);   // only a kernel an earlier call already loaded
 
     // the array keeps the previous call's counters: clear them first
     CUDA_TRY(cudaMemsetAsync(words, 0, kStaticWords * sizeof(unsigned long long), st),

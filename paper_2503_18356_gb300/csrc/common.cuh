@@ -3,8 +3,11 @@
 // argument structs, the device Philox generator and launch declarations.
 #pragma once
 
+#ifndef __CUDACC_RTC__
 #include <cstdint>
+#include <string>
 #include <cuda_runtime.h>
+#endif
 
 #include "grins_racipe.h"
 
@@ -22,7 +25,7 @@ struct ParamLayout {
     int64_t stride;
 };
 
-inline ParamLayout make_layout(int N, int E)
+__host__ __device__ inline ParamLayout make_layout(int N, int E)
 {
     ParamLayout L;
     L.N = N; L.E = E;
@@ -60,8 +63,10 @@ struct SampleArgs {
     unsigned char *params;
 };
 
+#ifndef __CUDACC_RTC__
 cudaError_t launch_sample_params(const SampleArgs &a, cudaStream_t st);
 cudaError_t launch_sample_ics(int N, uint64_t seed, int n_ics, double *u, cudaStream_t st);
+#endif
 
 // ------------------------------------------------------------- integrator
 // Lane-group layout of a network (built by the host at create time): the
@@ -100,11 +105,19 @@ struct IntegrateArgs {
     int32_t slots;               // parameter-set slots per warp (upper bound)
     int32_t smem_limit;          // opt-in shared memory per block, bytes
     GrpTopo grp;                 // lane-group layout (grp.L == 0: not available)
+    const void *grp_jit;         // host: kernel compiled for this layout, or null
 };
 
 // Maximum N served by the FP32 / FP64 integrator buckets.
+#ifndef __CUDACC_RTC__
+// Run-time compiled lane-group kernel for one layout (jit.cu): compiled on
+// first use (grp_jit_kernel) or only looked up (grp_jit_lookup).
+const void *grp_jit_kernel(const GrpTopo &g, std::string *why);
+const void *grp_jit_lookup(const GrpTopo &g);
+cudaError_t launch_grp_jit(const void *kern, const IntegrateArgs &a, cudaStream_t st, int num_sms);
 cudaError_t launch_integrate_fp32(const IntegrateArgs &a, cudaStream_t st, int num_sms);
 cudaError_t launch_integrate_fp64(const IntegrateArgs &a, cudaStream_t st, int num_sms);
+#endif
 
 // ----------------------------------------------------------------- polish
 struct PolishArgs {
@@ -121,7 +134,9 @@ struct PolishArgs {
     unsigned long long *check;   // checked builds: first violation (code, info)
 };
 
+#ifndef __CUDACC_RTC__
 cudaError_t launch_polish(const PolishArgs &a, cudaStream_t st, int num_sms);
+#endif
 
 // ----------------------------------------------------------------- unique
 struct UniqueArgs {
@@ -136,7 +151,9 @@ struct UniqueArgs {
     int32_t *n_unique;
 };
 
+#ifndef __CUDACC_RTC__
 cudaError_t launch_unique(const UniqueArgs &a, cudaStream_t st, int num_sms);
+#endif
 
 // ------------------------------------------------------------- device RNG
 // Philox4x64-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds of the

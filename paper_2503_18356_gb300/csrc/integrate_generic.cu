@@ -28,6 +28,10 @@ cudaError_t launch_integrate_fp32(const IntegrateArgs &a, cudaStream_t st, int n
         s = s < 1 ? 1 : (s > 16 ? 16 : s);
         b.slots = s * ndom;
         cudaError_t e;
+        if (a.grp_jit) {
+            e = launch_grp_jit(a.grp_jit, b, st, num_sms);
+            if (e != cudaErrorInvalidConfiguration) return e;
+        }
         if (a.grp.R <= 2) e = launch_integrate_grp2(b, st, num_sms);
         else if (a.grp.R <= 4) e = launch_integrate_grp4(b, st, num_sms);
         else if (a.grp.R <= 6) e = launch_integrate_grp6(b, st, num_sms);

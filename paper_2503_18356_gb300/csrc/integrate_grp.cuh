@@ -10,7 +10,9 @@
 // parameter set.  p = 2^t with t = n log2(B) - n log2(T): log2 of every
 // stage value once per node, one FMA and one ex2 per edge.  Numerators and
 // denominators are multiplied in chunks of four edges (p clamped to 2^30 so a
-// chunk cannot overflow) and divided once per chunk.
+// chunk cannot overflow) and divided once per chunk.  A row's edges are
+// processed as one straight-line block (up to eight at a time) so their
+// dependent shared loads and ex2 latencies overlap.
 //
 // Execution model (one GPU, persistent grid, warps independent):
 //   * a solve (parameter set x initial condition) is spread over a group of
@@ -92,26 +94,108 @@ __device__ __forceinline__ bool grp_all(bool v, int L)
     return x != 0;
 }
 
-// One edge position: multiplies (p + u) into num and (1 + p) into den,
+// One edge position: the factor's numerator p + u and denominator 1 + p,
 // p = 2^min(n log2 x_src - n log2 T, 30).
-__device__ __forceinline__ void grp_edge(const float4 *ed, const unsigned char *gcol, int pi,
-                                         float &num, float &den, unsigned long long *grins_chk,
-                                         int lim_pi, int lim_off)
+struct GrpCtx {
+    const float4 *ed;            // this lane's column of the slot's edge records
+    const unsigned char *gcol;   // this group's column of the gather buffer
+    int L, lim_pi, lim_off;
+    unsigned long long *grins_chk;
+};
+
+__device__ __forceinline__ void grp_edge(const GrpCtx &c, int pi, float &num, float &den)
 {
-    (void)grins_chk; (void)lim_pi; (void)lim_off;
-    if (!GRINS_OK_IDX(pi >= 0 && pi < lim_pi, 32, pi)) pi = 0;
-    const float4 e = ed[pi];
+    unsigned long long *grins_chk = c.grins_chk;
+    (void)grins_chk;
+    if (!GRINS_OK_IDX(pi >= 0 && pi < c.lim_pi, 32, pi)) pi = 0;
+    const float4 e = c.ed[pi];
     int off = __float_as_int(e.w);
-    if (!GRINS_OK_IDX(off >= 0 && off < lim_off && (off & 3) == 0, 33, off)) off = 0;
-    const float ls = *reinterpret_cast<const float *>(gcol + off);
+    if (!GRINS_OK_IDX(off >= 0 && off < c.lim_off && (off & 3) == 0, 33, off)) off = 0;
+    const float ls = *reinterpret_cast<const float *>(c.gcol + off);
     const float pw = ex2_approx(fminf(fmaf(e.x, ls, e.y), 30.0f));
-    num *= pw + e.z;
-    den = fmaf(den, pw, den);
+    num = pw + e.z;
+    den = 1.0f + pw;
 }
 
-template <int NPL, int WARPS, int MINB>
-__global__ void __launch_bounds__(WARPS * kWarp, MINB)
-dp5_grp_kernel(const IntegrateArgs a)
+// Product over the D positions of a row starting at record index pi (D is
+// the same for every lane of the warp).
+//  * Compile-time layout (the kernel compiled at run time for one network,
+//    GRINS_GRP_CT): D is a constant, the loop unrolls into one straight-line
+//    block per row and rows follow each other without branches.
+//  * Run-time layout: chunks of four in a loop, then the remainder.
+// One division per four factors keeps the partial products finite.
+#ifdef GRINS_GRP_CT
+template <int D>
+__device__ __forceinline__ float grp_row_ct(const GrpCtx &c, int pi)
+{
+    float prod = 1.0f;
+#pragma unroll
+    for (int m = 0; m < D; m += 4) {
+        float num = 1.0f, den = 1.0f;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (m + q < D) {
+                float nq, dq;
+                grp_edge(c, pi + (m + q) * c.L, nq, dq);
+                num *= nq;
+                den *= dq;
+            }
+        }
+        prod *= __fdividef(num, den);
+    }
+    return prod;
+}
+
+// Rows r, r+1, ... of the compile-time layout (GrpRowCt<r>::off / ::deg and
+// kGrpCtRows come from the generated prelude of the run-time compile):
+// z[r] <- G'_r prod_r - k_r z[r].
+template <int r, int NPL>
+__device__ __forceinline__ void grp_rows_ct(const GrpCtx &c, const float4 *nd, float (&z)[NPL])
+{
+    if constexpr (r < kGrpCtRows && r < NPL) {
+        const float prod = grp_row_ct<GrpRowCt<r>::deg>(c, GrpRowCt<r>::off * c.L);
+        const float4 nr = nd[r * c.L];
+        z[r] = fmaf(nr.x, prod, -nr.y * z[r]);
+        grp_rows_ct<r + 1, NPL>(c, nd, z);
+    }
+}
+#endif
+
+__device__ __forceinline__ float grp_row_rt(const GrpCtx &c, int pi, int D)
+{
+    const int pend = pi + D * c.L;
+    float prod = 1.0f;
+#pragma unroll 1
+    for (; pi + 4 * c.L <= pend; pi += 4 * c.L) {
+        float num = 1.0f, den = 1.0f;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float nq, dq;
+            grp_edge(c, pi + q * c.L, nq, dq);
+            num *= nq;
+            den *= dq;
+        }
+        prod *= __fdividef(num, den);
+    }
+    if (pi < pend) {
+        float num = 1.0f, den = 1.0f;
+#pragma unroll 1
+        for (; pi < pend; pi += c.L) {
+            float nq, dq;
+            grp_edge(c, pi, nq, dq);
+            num *= nq;
+            den *= dq;
+        }
+        prod *= __fdividef(num, den);
+    }
+    return prod;
+}
+
+// Body of the lane-group kernel.  NPL: node rows per lane (register arrays);
+// LC, RC: lanes per group and rows when fixed at compile time (0: read from
+// the launch arguments).
+template <int NPL, int WARPS, int LC, int RC>
+__device__ __forceinline__ void grp_body(const IntegrateArgs &a)
 {
     constexpr unsigned FULL = 0xffffffffu;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -119,7 +203,7 @@ dp5_grp_kernel(const IntegrateArgs a)
     (void)grins_chk;
 
     const GrpTopo &gt = a.grp;
-    const int N = a.topo.N, L = gt.L, R = gt.R, P = gt.P, S = a.slots;
+    const int N = a.topo.N, L = LC ? LC : gt.L, R = RC ? RC : gt.R, P = gt.P, S = a.slots;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int GS = kWarp / L;                    // groups per warp
     const int g = lane / L, j = lane - g * L;    // group, lane within group
@@ -175,35 +259,26 @@ dp5_grp_kernel(const IntegrateArgs a)
         for (int r = 0; r < NPL; ++r)
             if (r < R) gb[r * kWarp + col] = lg2_approx(fmaxf(z[r], 0.0f));
         __syncwarp();
-        const float4 *ed = reinterpret_cast<const float4 *>(sp) + j;
+        GrpCtx c;
+        c.ed = reinterpret_cast<const float4 *>(sp) + j;
+        c.gcol = reinterpret_cast<const unsigned char *>(gb) + 4 * g;
+        c.L = L;
+        c.lim_pi = P * L;
+        c.lim_off = R * kWarp * 4;
+        c.grins_chk = grins_chk;
         const float4 *nd = reinterpret_cast<const float4 *>(sp + LY.edge_bytes()) + j;
-        const unsigned char *gcol = reinterpret_cast<const unsigned char *>(gb) + 4 * g;
-        const int lim_pi = P * L, lim_off = R * kWarp * 4;
+#ifdef GRINS_GRP_CT
+        grp_rows_ct<0, NPL>(c, nd, z);
+#else
 #pragma unroll
         for (int r = 0; r < NPL; ++r) {
             if (r < R) {
-                int pi = gt.row_off[r] * L;
-                const int pend = pi + gt.row_deg[r] * L;
-                float prod = 1.0f;
-#pragma unroll 1
-                for (; pi + 4 * L <= pend; pi += 4 * L) {
-                    float num = 1.0f, den = 1.0f;
-                    grp_edge(ed, gcol, pi, num, den, grins_chk, lim_pi, lim_off);
-                    grp_edge(ed, gcol, pi + L, num, den, grins_chk, lim_pi, lim_off);
-                    grp_edge(ed, gcol, pi + 2 * L, num, den, grins_chk, lim_pi, lim_off);
-                    grp_edge(ed, gcol, pi + 3 * L, num, den, grins_chk, lim_pi, lim_off);
-                    prod *= __fdividef(num, den);
-                }
-                if (pi < pend) {
-                    float num = 1.0f, den = 1.0f;
-#pragma unroll 1
-                    for (; pi < pend; pi += L) grp_edge(ed, gcol, pi, num, den, grins_chk, lim_pi, lim_off);
-                    prod *= __fdividef(num, den);
-                }
+                const float prod = grp_row_rt(c, gt.row_off[r] * L, gt.row_deg[r]);
                 const float4 nr = nd[r * L];
                 z[r] = fmaf(nr.x, prod, -nr.y * z[r]);
             }
         }
+#endif
     };
 
     // parameter set `set` -> slot `s` (whole warp)
@@ -540,6 +615,14 @@ dp5_grp_kernel(const IntegrateArgs a)
     }
 }
 
+#ifndef __CUDACC_RTC__
+template <int NPL, int WARPS, int MINB>
+__global__ void __launch_bounds__(WARPS * kWarp, MINB)
+dp5_grp_kernel(const IntegrateArgs a)
+{
+    grp_body<NPL, WARPS, 0, 0>(a);
+}
+
 template <int NPL, int MINB>
 cudaError_t launch_grp_bucket(const IntegrateArgs &a, cudaStream_t st, int num_sms)
 {
@@ -566,5 +649,6 @@ cudaError_t launch_grp_bucket(const IntegrateArgs &a, cudaStream_t st, int num_s
     kern<<<(unsigned)blocks, WARPS * kWarp, smem, st>>>(b);
     return cudaGetLastError();
 }
+#endif  // __CUDACC_RTC__
 
 }  // namespace grins

@@ -1,0 +1,225 @@
+// Run-time specialisation of the lane-group FP32 integrator for one network.
+//
+// The lane-group kernel (integrate_grp.cuh) reads its row layout (node rows
+// per lane, positions per row) from the launch arguments, so every row costs
+// a loop with run-time bounds.  For a fixed network the layout is known when
+// the handle is created; this file compiles the same kernel source with
+// NVRTC for sm_103a with the layout as compile-time constants (every row one
+// straight-line block, register arrays sized to the row count), loads the
+// cubin with the CUDA runtime's library API and launches it.  Compiled
+// kernels are cached per process by their source text, so handles of the
+// same network share one compile.
+//
+// libnvrtc is opened with dlopen: a machine without it, or a failed compile,
+// leaves the run-time-layout kernel in charge (GRINS_JIT=0 forces that).
+#include <dlfcn.h>
+
+#include <cstdio>
+#include <cstdlib>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include <nvrtc.h>
+
+#include "integrate_grp.cuh"
+
+namespace grins {
+
+namespace {
+
+// Kernel sources embedded at build time (jit_sources.inc, generated by
+// build.py from the files of this folder and include/).
+#include "jit_sources.inc"
+
+// C integer types for the run-time compile (grins_racipe.h includes
+// <stdint.h>, which NVRTC does not ship).
+const char *const kStdintStandIn =
+    "#pragma once\n"
+    "typedef signed char int8_t; typedef unsigned char uint8_t;\n"
+    "typedef short int16_t; typedef unsigned short uint16_t;\n"
+    "typedef int int32_t; typedef unsigned int uint32_t;\n"
+    "typedef long long int64_t; typedef unsigned long long uint64_t;\n"
+    "typedef unsigned long long uintptr_t;\n";
+
+struct NvrtcApi {
+    bool ok = false;
+    std::string why;
+    decltype(&nvrtcCreateProgram) create = nullptr;
+    decltype(&nvrtcCompileProgram) compile = nullptr;
+    decltype(&nvrtcGetProgramLogSize) log_size = nullptr;
+    decltype(&nvrtcGetProgramLog) log = nullptr;
+    decltype(&nvrtcGetCUBINSize) cubin_size = nullptr;
+    decltype(&nvrtcGetCUBIN) cubin = nullptr;
+    decltype(&nvrtcDestroyProgram) destroy = nullptr;
+    decltype(&nvrtcGetErrorString) err = nullptr;
+};
+
+NvrtcApi &nvrtc()
+{
+    static NvrtcApi api;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        const char *names[] = {"libnvrtc.so.13", "libnvrtc.so", "/usr/local/cuda/lib64/libnvrtc.so.13",
+                               "/usr/local/cuda/lib64/libnvrtc.so"};
+        void *h = nullptr;
+        for (const char *n : names)
+            if ((h = dlopen(n, RTLD_NOW | RTLD_LOCAL))) break;
+        if (!h) { api.why = "libnvrtc not found"; return; }
+        api.create = reinterpret_cast<decltype(api.create)>(dlsym(h, "nvrtcCreateProgram"));
+        api.compile = reinterpret_cast<decltype(api.compile)>(dlsym(h, "nvrtcCompileProgram"));
+        api.log_size = reinterpret_cast<decltype(api.log_size)>(dlsym(h, "nvrtcGetProgramLogSize"));
+        api.log = reinterpret_cast<decltype(api.log)>(dlsym(h, "nvrtcGetProgramLog"));
+        api.cubin_size = reinterpret_cast<decltype(api.cubin_size)>(dlsym(h, "nvrtcGetCUBINSize"));
+        api.cubin = reinterpret_cast<decltype(api.cubin)>(dlsym(h, "nvrtcGetCUBIN"));
+        api.destroy = reinterpret_cast<decltype(api.destroy)>(dlsym(h, "nvrtcDestroyProgram"));
+        api.err = reinterpret_cast<decltype(api.err)>(dlsym(h, "nvrtcGetErrorString"));
+        api.ok = api.create && api.compile && api.log_size && api.log && api.cubin_size && api.cubin &&
+                 api.destroy && api.err;
+        if (!api.ok) api.why = "libnvrtc lacks an expected symbol";
+    });
+    return api;
+}
+
+constexpr int kJitWarps = 4;
+
+struct JitEntry {
+    bool ok = false;
+    std::string why;
+    cudaLibrary_t lib = nullptr;
+    cudaKernel_t kern = nullptr;
+};
+
+std::mutex g_jit_mu;
+std::map<std::string, std::shared_ptr<JitEntry>> g_jit_cache;
+
+// Generated prelude + kernel wrapper for one layout.
+std::string jit_main(const GrpTopo &g, int minb)
+{
+    std::string s;
+    char buf[256];
+    s += "#define GRINS_GRP_CT 1\n";
+#ifdef GRINS_CHECKED
+    s += "#define GRINS_CHECKED 1\n";
+#endif
+    s += "#include \"common.cuh\"\nnamespace grins {\n";
+    std::snprintf(buf, sizeof(buf), "constexpr int kGrpCtRows = %d;\n", g.R);
+    s += buf;
+    s += "template <int r> struct GrpRowCt { static constexpr int off = 0, deg = 0; };\n";
+    for (int r = 0; r < g.R; ++r) {
+        std::snprintf(buf, sizeof(buf),
+                      "template <> struct GrpRowCt<%d> { static constexpr int off = %d, deg = %d; };\n", r,
+                      g.row_off[r], g.row_deg[r]);
+        s += buf;
+    }
+    s += "}\n#include \"integrate_grp.cuh\"\n";
+    std::snprintf(buf, sizeof(buf),
+                  "extern \"C\" __global__ void __launch_bounds__(%d, %d) grins_grp_ct(const grins::IntegrateArgs a)\n"
+                  "{\n    grins::grp_body<%d, %d, %d, %d>(a);\n}\n",
+                  kJitWarps * kWarp, minb, g.R, kJitWarps, g.L, g.R);
+    s += buf;
+    return s;
+}
+
+std::shared_ptr<JitEntry> jit_compile(const std::string &src)
+{
+    auto e = std::make_shared<JitEntry>();
+    NvrtcApi &api = nvrtc();
+    if (!api.ok) { e->why = api.why; return e; }
+    std::vector<const char *> hdr_src, hdr_name;
+    for (int i = 0; i < kJitSourceCount; ++i) {
+        hdr_src.push_back(kJitSources[i]);
+        hdr_name.push_back(kJitSourceNames[i]);
+    }
+    hdr_src.push_back(kStdintStandIn);
+    hdr_name.push_back("stdint.h");
+    nvrtcProgram prog = nullptr;
+    nvrtcResult r = api.create(&prog, src.c_str(), "grins_grp_ct.cu", (int)hdr_src.size(), hdr_src.data(),
+                               hdr_name.data());
+    if (r != NVRTC_SUCCESS) { e->why = std::string("nvrtcCreateProgram: ") + api.err(r); return e; }
+    const char *opts[] = {"--gpu-architecture=sm_103a", "--std=c++17", "-lineinfo", "-default-device"};
+    r = api.compile(prog, 4, opts);
+    if (r != NVRTC_SUCCESS) {
+        size_t n = 0;
+        api.log_size(prog, &n);
+        std::string log(n, '\0');
+        if (n) api.log(prog, &log[0]);
+        e->why = std::string("nvrtcCompileProgram: ") + api.err(r) + "\n" + log;
+        api.destroy(&prog);
+        return e;
+    }
+    size_t n = 0;
+    api.cubin_size(prog, &n);
+    std::vector<char> cubin(n);
+    api.cubin(prog, cubin.data());
+    api.destroy(&prog);
+    cudaError_t ce = cudaLibraryLoadData(&e->lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+    if (ce == cudaSuccess) ce = cudaLibraryGetKernel(&e->kern, e->lib, "grins_grp_ct");
+    if (ce != cudaSuccess) { e->why = std::string("loading the compiled kernel: ") + cudaGetErrorString(ce); return e; }
+    e->ok = true;
+    return e;
+}
+
+}  // namespace
+
+// The compiled kernel for layout g (compiling it on first use), or null
+// with the reason in *why.
+const void *grp_jit_kernel(const GrpTopo &g, std::string *why)
+{
+    const char *ev = std::getenv("GRINS_JIT");
+    if (ev && ev[0] == '0') { if (why) *why = "disabled by GRINS_JIT=0"; return nullptr; }
+    if (g.L <= 0 || g.R <= 0 || g.R > 12) { if (why) *why = "no lane-group layout"; return nullptr; }
+    const std::string src = jit_main(g, GRINS_GRP_MINB);
+    std::shared_ptr<JitEntry> e;
+    {
+        std::lock_guard<std::mutex> lock(g_jit_mu);
+        auto it = g_jit_cache.find(src);
+        if (it == g_jit_cache.end()) it = g_jit_cache.emplace(src, jit_compile(src)).first;
+        e = it->second;
+    }
+    if (!e->ok) { if (why) *why = e->why; return nullptr; }
+    return reinterpret_cast<const void *>(e->kern);
+}
+
+// The compiled kernel for layout g if an earlier call compiled it; never
+// compiles or loads anything.
+const void *grp_jit_lookup(const GrpTopo &g)
+{
+    const char *ev = std::getenv("GRINS_JIT");
+    if ((ev && ev[0] == '0') || g.L <= 0 || g.R <= 0 || g.R > 12) return nullptr;
+    const std::string src = jit_main(g, GRINS_GRP_MINB);
+    std::lock_guard<std::mutex> lock(g_jit_mu);
+    auto it = g_jit_cache.find(src);
+    if (it == g_jit_cache.end() || !it->second->ok) return nullptr;
+    return reinterpret_cast<const void *>(it->second->kern);
+}
+
+cudaError_t launch_grp_jit(const void *kern, const IntegrateArgs &a, cudaStream_t st, int num_sms)
+{
+    IntegrateArgs b = a;
+    const int ndom = b.grp.L <= 16 ? 2 : 1;
+    GrpLayout LY{b.grp.L, b.grp.R, b.grp.P, b.slots};
+    while (kJitWarps * LY.warp_bytes() > b.smem_limit && LY.S > ndom) LY.S = (b.slots -= ndom);
+    const int smem = kJitWarps * LY.warp_bytes();
+    if (smem > b.smem_limit) return cudaErrorInvalidConfiguration;
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (err != cudaSuccess) return err;
+    int per_sm = 0;
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kJitWarps * kWarp, smem);
+    if (err != cudaSuccess) return err;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int groups = kWarp / b.grp.L;
+    const long long work_warps = (b.n_sets * b.n_ics + groups - 1) / groups + 1;
+    long long blocks = (long long)num_sms * per_sm;
+    const long long need = (work_warps + kJitWarps - 1) / kJitWarps;
+    if (blocks > need) blocks = need;
+    if (blocks < 1) blocks = 1;
+    void *args[] = {&b};
+    err = cudaLaunchKernel(kern, dim3((unsigned)blocks), dim3(kJitWarps * kWarp), args, (size_t)smem, st);
+    if (err != cudaSuccess) return err;
+    return cudaGetLastError();
+}
+
+}  // namespace grins
