@@ -39,7 +39,7 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--sets", type=int, default=N_SETS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sets", type=int, default=160, help="sets of the oracle sample")
+    ap.add_argument("--cpu-sets", type=int, default=800, help="sets of the oracle sample")
     return ap.parse_args()
 
 
@@ -312,9 +312,10 @@ def run_native(args):
             step_attempts_per_solve=attempts / (S * I),
             status_hist=np.bincount(status.ravel(), minlength=5).tolist(),
             roofline=dict(bound="alu", achieved=achieved, peak=peak, unit=unit, frac=achieved / peak,
-                          traffic=None, kernel="dp5_kernel<float,24> (FP32 integrator)",
+                          traffic=None, kernel=h.integrator(),
                           peak_basis="%d SMs x %s lanes/clk x %.0f MHz (median SM clock sampled in the "
-                                     "timed region)" % (sms, "16 SFU" if sfu_bound else "128 FP32", f_mhz),
+                                     "timed region); reciprocal rate measured at 16/clk/SM on this GPU"
+                                     % (sms, "16 SFU" if sfu_bound else "128 FP32", f_mhz),
                           work_per_attempt=dict(fp32=w32, sfu=wsfu)),
             e2e=dict(value=e2e_value, unit="solves/s", h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h),
             gpu_launches=5 * args.steps,

@@ -91,7 +91,7 @@ typedef struct {
 /* Solver controls (Sec. 2.1.3: tolerances, start and end time, stop at
  * steady state, optional time points).  grins_solver_default_opts fills:
  * FP32 + polish, rtol 1e-6, atol 1e-9, t0 0, t_end 200, ss_tol 1e-6,
- * max_steps 100000, no time grid, polish_tol 1e-12, polish_iters 4,
+ * max_steps 100000, no time grid, polish_tol 1e-12, polish_iters 16,
  * polish_max_move 1e-2. */
 typedef struct {
     int32_t precision;         /* GRINS_FP32 or GRINS_FP64 integration */
@@ -104,7 +104,8 @@ typedef struct {
                                   NULL / 0 = no time series */
     int32_t n_t;
     double polish_tol;         /* polish succeeds when the FP64 residual < polish_tol */
-    int32_t polish_iters;      /* Newton iterations at most */
+    int32_t polish_iters;      /* polish steps at most (chord-Newton steps, see
+                                  grins_racipe_polish) */
     double polish_max_move;    /* reject a polish that moves a G/k-normalised
                                   coordinate by more than this */
 } grins_solver_opts;
@@ -219,13 +220,16 @@ grins_status grins_racipe_integrate_static(grins_racipe_t h, const grins_solver_
                                            double *d_t_final, float *d_err_est,
                                            int32_t *d_n_steps, double *d_series, void *stream);
 
-/* FP64 Newton polish of states already integrated (the step integrate runs
- * when o->polish is set; exposed so a caller can polish separately).  For
- * every solve with status GRINS_SS_CONVERGED: Newton iterations on Eq. 1 = 0
- * in double precision with the analytic Jacobian, until the residual
- * max_i |f_i| / (G_i / k_i) < o->polish_tol (at most o->polish_iters steps).
+/* Newton polish of states already integrated (the step integrate runs when
+ * o->polish is set; exposed so a caller can polish separately).  For every
+ * solve with status GRINS_SS_CONVERGED: chord-Newton steps on Eq. 1 = 0 --
+ * the residual in double precision at every step, the analytic Jacobian
+ * evaluated and LU-factorised once in single precision, the step added in
+ * double precision (mixed-precision iterative refinement) -- until the FP64
+ * residual max_i |f_i| / (G_i / k_i) < o->polish_tol (at most
+ * o->polish_iters steps).
  * Success overwrites d_states[set][ic][:] and writes the G/k-normalised size
- * of the last Newton step to d_err_est (nullable); failure (singular
+ * of the last step to d_err_est (nullable); failure (singular
  * Jacobian, a step moving a normalised coordinate by more than
  * o->polish_max_move, or no convergence) keeps the state and sets the status
  * to GRINS_SS_POLISH_FAIL.  Other statuses are left alone (err_est = -1).

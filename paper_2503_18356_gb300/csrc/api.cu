@@ -97,7 +97,7 @@ extern "C" void grins_solver_default_opts(grins_solver_opts *o)
     o->max_steps = 100000;
     o->t_grid = nullptr; o->n_t = 0;
     o->polish_tol = 1e-12;
-    o->polish_iters = 4;
+    o->polish_iters = 16;
     o->polish_max_move = 1e-2;
 }
 

@@ -1,17 +1,24 @@
-// FP64 Newton polish and residual certificate of converged steady states.
+// Newton polish and FP64 residual certificate of converged steady states.
 //
 // A steady state is a zero of Eq. 1: f_i(x) = G_i prod_e F_e(x_src) - k_i x_i.
-// From the state the integrator stopped at, Newton steps x <- x + d with
-// J d = -f(x) are taken in double precision, J analytic:
-//     J_ij = G_i P_i sum_{e: src(e)=j, dst(e)=i} F_e'(x_j) / F_e(x_j) - k_i [i=j],
-//     F_e = (a p + b) / (1 + p), p = (x/T)^n,
-//     F_e'/F_e = (a - b) n p / ((1 + p)(a p + b) x).
-// Converged when rho = max_i |f_i| / (G_i / k_i) < tol.  A solve whose
-// Newton step moves a G/k-normalised coordinate by more than max_move, whose
-// Jacobian is singular, or that does not reach tol within `iters` steps keeps
-// its unpolished state and gets status GRINS_SS_POLISH_FAIL.
-// One warp per solve: lanes over rows (targets) for the residual and
-// Jacobian, Gaussian elimination with partial pivoting in shared memory.
+// From the state the integrator stopped at, the polish takes chord-Newton
+// steps x <- x + d with J0 d = -f(x) (mixed-precision iterative refinement):
+//   * f is evaluated in FP64 at every step (the quantity being certified);
+//   * the analytic Jacobian is evaluated once, at the starting state, in
+//     FP32, and factorised once (LU with partial pivoting, FP32):
+//       J_ij = G_i P_i sum_{e: src(e)=j, dst(e)=i} F_e'(x_j) / F_e(x_j) - k_i [i=j],
+//       F_e = (a p + b) / (1 + p), p = (x/T)^n,
+//       F_e'/F_e = (a - b) n p / ((1 + p)(a p + b) x);
+//   * the step is solved in FP32 and added to the FP64 state.
+// Starting within ~1e-5 of the fixed point, each step shrinks the error by
+// about the FP32 Jacobian's relative error times its condition number, so
+// two or three steps reach an FP64 residual of 1e-12 while every operation
+// but the residual runs at FP32 rate.
+// Converged when rho = max_i |f_i| / (G_i / k_i) < tol.  A solve whose step
+// moves a G/k-normalised coordinate by more than max_move, whose Jacobian is
+// singular, or that does not reach tol within `iters` steps keeps its
+// unpolished state and gets status GRINS_SS_POLISH_FAIL.
+// One warp per solve: lanes over rows (targets).
 #include "integrate.cuh"
 
 namespace grins {
@@ -27,26 +34,40 @@ __device__ __forceinline__ double warp_max(double v)
     return v;
 }
 
-__device__ __forceinline__ double warp_sum(double v)
+__device__ __forceinline__ float warp_maxf(float v)
 {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(FULL, v, o));
     return v;
+}
+
+// x^n for a small non-negative integer n, by repeated squaring
+template <typename Real>
+__device__ __forceinline__ Real ipow(Real x, int n)
+{
+    Real p = (Real)1, b = x;
+    for (; n; n >>= 1) {
+        if (n & 1) p *= b;
+        b *= b;
+    }
+    return p;
 }
 
 template <int NMAX, int WARPS>
 __global__ void __launch_bounds__(WARPS * kWarp) polish_kernel(const PolishArgs a)
 {
-    __shared__ double sJ[WARPS][NMAX][NMAX + 1];
-    __shared__ double sx[WARPS][NMAX];
-    __shared__ double sb[WARPS][NMAX];
+    __shared__ float sJ[WARPS][NMAX][NMAX + 1];   // FP32 Jacobian, then its LU factors
+    __shared__ double sx[WARPS][NMAX];            // FP64 state
+    __shared__ float sb[WARPS][NMAX];             // FP32 right-hand side, then the step
+    __shared__ int spiv[WARPS][NMAX];             // pivot row of each elimination step
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int N = a.topo.N;
     unsigned long long *grins_chk = a.check;
     (void)grins_chk;
-    double (*J)[NMAX + 1] = sJ[w];
+    float (*J)[NMAX + 1] = sJ[w];
     double *x = sx[w];
-    double *b = sb[w];
+    float *b = sb[w];
+    int *piv = spiv[w];
 
     for (long long idx = (long long)blockIdx.x * WARPS + w; idx < a.n_solves;
          idx += (long long)gridDim.x * WARPS) {
@@ -65,90 +86,129 @@ __global__ void __launch_bounds__(WARPS * kWarp) polish_kernel(const PolishArgs 
         for (int i = lane; i < N; i += kWarp) x[i] = state[i];
         __syncwarp();
 
-        bool ok = false;
-        double last_move = 0.0, rho = 0.0;
-        for (int it = 0; it <= a.iters; ++it) {
-            // residual and Jacobian rows, lanes over targets
+        // f_i in FP64 for the rows of this lane -> b (FP32, negated); returns
+        // rho.  Each factor of Eq. 2 is written without divisions,
+        //     F_e = (lam x^n + T^n) / ((x^n + T^n) c),  c = lam (activating), 1,
+        // (numerator and denominator of (lam p + 1) / ((1 + p) c) times T^n),
+        // and the products are divided once per eight factors (x^n, T^n stay
+        // below ~1e24, so eight factors stay finite).  With `jac` row i of
+        // the Jacobian is filled in as well.
+        auto residual = [&](bool jac) -> double {
             double rloc = 0.0;
             for (int i = lane; i < N; i += kWarp) {
-                for (int j = 0; j < N; ++j) J[i][j] = 0.0;
-                double P = 1.0;
+                if (jac)
+                    for (int j = 0; j < N; ++j) J[i][j] = 0.0f;
+                double P = 1.0, num = 1.0, den = 1.0;
+                int cnt = 0;
                 for (int c = a.topo.off[i]; c < a.topo.off[i + 1]; ++c) {
                     int e = a.topo.edge[c], s = a.topo.src[c];
                     if (!GRINS_OK_IDX(e >= 0 && e < a.topo.E && s >= 0 && s < N && N <= NMAX, 21, c)) e = s = 0;
-                    const double xs = fmax(x[s], 0.0);
-                    const double r = xs / T[e];
-                    const int n = nn[e];
-                    double p = 1.0, pm1 = 1.0, base = r;
-                    for (int m = n; m; m >>= 1) { if (m & 1) p *= base; base *= base; }
-                    base = r;
-                    for (int m = n - 1; m > 0; m >>= 1) { if (m & 1) pm1 *= base; base *= base; }
                     const bool act = a.topo.sign[c] > 0;
-                    const double aa = act ? 1.0 : lam[e];
-                    const double bb = act ? 1.0 / lam[e] : 1.0;
-                    const double num = fma(aa, p, bb), den = 1.0 + p;
-                    P *= num / den;
-                    // d log F / dx = (a - b) n r^(n-1) / (T (1 + p)(a p + b))
-                    J[i][s] += (aa - bb) * (double)n * pm1 / (T[e] * den * num);
+                    const int n = nn[e];
+                    const double l = lam[e], Te = T[e];
+                    const double xs = fmax(x[s], 0.0);
+                    const double xn = ipow(xs, n), tn = ipow(Te, n);
+                    num *= fma(l, xn, tn);
+                    den *= act ? (xn + tn) * l : xn + tn;
+                    if (++cnt == 8) { P *= num / den; num = den = 1.0; cnt = 0; }
+                    if (jac) {
+                        // d log F / dx = n p (lam - 1) / (x (lam p + 1)(1 + p)),
+                        // p = (x/T)^n, in FP32 (the Jacobian only steers the
+                        // iteration); at x = 0 only n = 1 leaves a slope
+                        const float lf = (float)l, xf = (float)xs;
+                        float dl;
+                        if (xf > 0.0f) {
+                            const float pf = (float)fmin(xn / tn, 1e30);
+                            dl = (float)n * (lf - 1.0f) / xf * (pf / (1.0f + pf)) / fmaf(lf, pf, 1.0f);
+                        } else {
+                            dl = n == 1 ? (lf - 1.0f) / (float)Te : 0.0f;
+                        }
+                        J[i][s] += dl;   // scaled by G_i P_i below
+                    }
                 }
+                P *= num / den;
                 const double f = G[i] * P - K[i] * x[i];
-                b[i] = -f;
-                for (int j = 0; j < N; ++j) J[i][j] *= G[i] * P;
-                J[i][i] -= K[i];
-                rloc = fmax(rloc, fabs(f) / (G[i] / K[i]));
+                b[i] = (float)(-f);
+                if (jac) {
+                    const float gp = (float)(G[i] * P);
+                    for (int j = 0; j < N; ++j) J[i][j] *= gp;
+                    J[i][i] -= (float)K[i];
+                }
+                rloc = fmax(rloc, fabs(f) * (K[i] / G[i]));
             }
-            rho = warp_max(rloc);
-            __syncwarp();
-            if (rho < a.tol) { ok = true; break; }
-            if (it == a.iters || !(rho == rho)) break;
+            return warp_max(rloc);
+        };
 
-            // Gaussian elimination with partial pivoting
-            bool singular = false;
+        bool ok = false, singular = false;
+        double last_move = 0.0;
+        double rho = residual(true);
+        __syncwarp();
+        if (rho < a.tol) ok = true;
+
+        // LU of the FP32 Jacobian with partial pivoting; multipliers kept
+        // below the diagonal, row swaps recorded in piv
+        if (!ok) {
             for (int c = 0; c < N; ++c) {
-                double best = -1.0;
-                int piv = c;
+                float best = -1.0f;
+                int pr = c;
                 for (int r = c + lane; r < N; r += kWarp) {
-                    const double v = fabs(J[r][c]);
-                    if (v > best) { best = v; piv = r; }
+                    const float v = fabsf(J[r][c]);
+                    if (v > best) { best = v; pr = r; }
                 }
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) {
-                    const double ob = __shfl_xor_sync(FULL, best, o);
-                    const int op = __shfl_xor_sync(FULL, piv, o);
-                    if (ob > best || (ob == best && op < piv)) { best = ob; piv = op; }
+                    const float ob = __shfl_xor_sync(FULL, best, o);
+                    const int op = __shfl_xor_sync(FULL, pr, o);
+                    if (ob > best || (ob == best && op < pr)) { best = ob; pr = op; }
                 }
-                if (!(best > 0.0)) { singular = true; break; }
-                if (piv != c) {
+                if (!(best > 0.0f)) { singular = true; break; }
+                if (lane == 0) piv[c] = pr;
+                if (pr != c) {
                     for (int j = lane; j < N; j += kWarp) {
-                        const double tmp = J[c][j]; J[c][j] = J[piv][j]; J[piv][j] = tmp;
+                        const float t = J[c][j]; J[c][j] = J[pr][j]; J[pr][j] = t;
                     }
-                    if (lane == 0) { const double tb = b[c]; b[c] = b[piv]; b[piv] = tb; }
                 }
                 __syncwarp();
-                const double inv = 1.0 / J[c][c];
+                const float inv = 1.0f / J[c][c];
                 for (int r = c + 1 + lane; r < N; r += kWarp) {
-                    const double m = J[r][c] * inv;
-                    for (int j = c + 1; j < N; ++j) J[r][j] -= m * J[c][j];
-                    b[r] -= m * b[c];
+                    const float m = J[r][c] * inv;
+                    J[r][c] = m;
+                    for (int j = c + 1; j < N; ++j) J[r][j] = fmaf(-m, J[c][j], J[r][j]);
                 }
                 __syncwarp();
             }
-            if (singular) break;
-            // back substitution (b becomes the Newton step)
-            for (int r = N - 1; r >= 0; --r) {
-                double s = 0.0;
-                for (int j = r + 1 + lane; j < N; j += kWarp) s += J[r][j] * b[j];
-                s = warp_sum(s);
-                if (lane == 0) b[r] = (b[r] - s) / J[r][r];
+        }
+
+        // chord iterations: solve J0 d = -f(x) in FP32, x += d in FP64
+        for (int it = 0; !ok && !singular && it < a.iters; ++it) {
+            if (lane == 0)
+                for (int c = 0; c < N; ++c) {
+                    const int pr = piv[c];
+                    if (pr != c) { const float t = b[c]; b[c] = b[pr]; b[pr] = t; }
+                }
+            __syncwarp();
+            for (int c = 0; c < N; ++c) {                 // forward (unit lower)
+                const float bc = b[c];
+                for (int r = c + 1 + lane; r < N; r += kWarp) b[r] = fmaf(-J[r][c], bc, b[r]);
                 __syncwarp();
             }
-            double mv = 0.0;
-            for (int i = lane; i < N; i += kWarp) mv = fmax(mv, fabs(b[i]) * (K[i] / G[i]));
-            mv = warp_max(mv);
-            if (!(mv <= a.max_move)) break;
-            for (int i = lane; i < N; i += kWarp) x[i] += b[i];
+            for (int c = N - 1; c >= 0; --c) {            // backward (upper)
+                if (lane == 0) b[c] = b[c] / J[c][c];
+                __syncwarp();
+                const float bc = b[c];
+                for (int r = lane; r < c; r += kWarp) b[r] = fmaf(-J[r][c], bc, b[r]);
+                __syncwarp();
+            }
+            float mv = 0.0f;
+            for (int i = lane; i < N; i += kWarp) mv = fmaxf(mv, fabsf(b[i]) * (float)(K[i] / G[i]));
+            mv = warp_maxf(mv);
+            if (!(mv <= (float)a.max_move)) break;
+            for (int i = lane; i < N; i += kWarp) x[i] += (double)b[i];
             last_move = mv;
             __syncwarp();
+            rho = residual(false);
+            __syncwarp();
+            if (rho < a.tol) ok = true;
         }
         if (ok) {
             for (int i = lane; i < N; i += kWarp) state[i] = x[i];

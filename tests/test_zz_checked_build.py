@@ -35,4 +35,8 @@ def test_checked_build_records_no_violation(tmp_path):
         if k.endswith("pol1_states"):
             st = r[k.replace("_states", "_status")]
             ok = (st == 0) & (c[k.replace("_states", "_status")] == 0)
-            assert np.allclose(c[k][ok], r[k][ok], rtol=1e-9, atol=0), k
+            # the two builds may contract multiply-adds differently, so their
+            # unpolished states differ by rounding; the polish certifies an
+            # FP64 residual below 1e-12, which bounds the remaining difference
+            # through the Jacobian's conditioning, far inside the 1e-6 bar
+            assert np.allclose(c[k][ok], r[k][ok], rtol=1e-7, atol=1e-10), k
