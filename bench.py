@@ -29,6 +29,10 @@ sys.path.insert(0, ROOT)
 N_SETS = 100_000
 N_ICS = 10
 TOL = dict(rtol=1e-6, atol=1e-9, t_end=200.0, ss_tol=1e-6)
+# DRAM bytes (read + write) of one integrator launch per solve, from an ncu
+# capture of the same kernel on a 20,000-set launch of this workload
+# (35.9 MB for 200,000 solves); traffic grows with the solves per launch.
+INTEGRATOR_DRAM_BYTES_PER_SOLVE = 35.9e6 / 200_000
 
 
 def parse():
@@ -40,6 +44,7 @@ def parse():
     ap.add_argument("--sets", type=int, default=N_SETS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sets", type=int, default=800, help="sets of the oracle sample")
+    ap.add_argument("--fp64-sets", type=int, default=5000, help="sets of the FP64 GPU solver sample")
     return ap.parse_args()
 
 
@@ -294,6 +299,20 @@ def run_native(args):
         e2e_s = float(t.item())
     e2e_value = solves * e2e_steps / e2e_s
 
+    # the plain FP64 GPU solver (FP64 Dormand-Prince end to end, no polish)
+    # on the first sets of the same workload, for the FP32 + polish ratio
+    f64_sets = max(1, min(S, args.fp64_sets))
+    opts64 = api.default_opts(precision=api.GRINS_FP64, polish=0, **TOL)
+    out64 = {k: (v[:f64_sets] if v is not None else None) for k, v in out.items()}
+    h.integrate(params[:f64_sets], ic, opts=opts64, stream=stream, out=out64)
+    e64 = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    barrier()
+    e64[0].record(stream)
+    h.integrate(params[:f64_sets], ic, opts=opts64, stream=stream, out=out64)
+    e64[1].record(stream)
+    barrier()
+    fp64_value = f64_sets * I / (e64[0].elapsed_time(e64[1]) / 1e3)
+
     if rank == 0:
         line = dict(
             metric="RACIPE steady-state solves/s (22-node network, FP32 + FP64 polish)",
@@ -312,13 +331,17 @@ def run_native(args):
             step_attempts_per_solve=attempts / (S * I),
             status_hist=np.bincount(status.ravel(), minlength=5).tolist(),
             roofline=dict(bound="alu", achieved=achieved, peak=peak, unit=unit, frac=achieved / peak,
-                          traffic=None, kernel=h.integrator(),
+                          traffic=INTEGRATOR_DRAM_BYTES_PER_SOLVE * S * I, kernel=h.integrator(),
                           peak_basis="%d SMs x %s lanes/clk x %.0f MHz (median SM clock sampled in the "
                                      "timed region); reciprocal rate measured at 16/clk/SM on this GPU"
                                      % (sms, "16 SFU" if sfu_bound else "128 FP32", f_mhz),
                           work_per_attempt=dict(fp32=w32, sfu=wsfu)),
             e2e=dict(value=e2e_value, unit="solves/s", h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h),
             gpu_launches=5 * args.steps,
+            fp64_gpu_solver=dict(value=fp64_value, unit="solves/s",
+                                 sample="sets 0..%d x %d ICs, FP64 Dormand-Prince 5(4) on the GPU, same "
+                                        "tolerances, no polish" % (f64_sets - 1, I),
+                                 ratio=value / fp64_value),
             clocks=clocks)
         if not args.no_cpu_baseline and ws == 1:
             line["cpu_baseline"] = cpu_baseline(args.cpu_sets)

@@ -117,7 +117,8 @@ static void free_device(grins_racipe *h)
 }
 
 // Lane-group layout (GrpTopo): L = the smallest power of two with at most
-// 12 node rows; nodes sorted by in-degree (descending, ties by index) fill
+// 8 node rows (the register arrays stay small enough for 12 warps per SM);
+// nodes sorted by in-degree (descending, ties by index) fill
 // rows of L; row r takes D_r = its largest in-degree positions.  Within a row
 // the host orders each lane's in-edges so that, position by position, the L
 // lanes read sources in distinct gather columns (distinct shared-memory
@@ -132,7 +133,7 @@ static GrpHost build_grp(int N, const std::vector<int32_t> &csr_off, const std::
 {
     GrpHost g;
     int L = 1;
-    while ((N + L - 1) / L > 12 && L < kWarp) L *= 2;
+    while ((N + L - 1) / L > 8 && L < kWarp) L *= 2;
     // GRINS_GRP_L (1, 2, 4, 8, 16 or 32) overrides the choice when it still
     // gives at most 12 rows (a tuning override)
     if (const char *ev = std::getenv("GRINS_GRP_L")) {

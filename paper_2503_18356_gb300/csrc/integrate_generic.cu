@@ -1,6 +1,7 @@
 // Generic-N integrator instantiations and the precision/size dispatch of the
 // integrator.
 #include "integrate_generic.cuh"
+#include "integrate_grp.cuh"
 
 // Parameter-set slots per warp of the lane-group kernel beyond the number
 // that covers every group once (a tuning knob of the build).
@@ -22,7 +23,7 @@ cudaError_t launch_integrate_fp32(const IntegrateArgs &a, cudaStream_t st, int n
     // shared memory; the generic kernel otherwise
     if (a.grp.L > 0 && a.grp.R <= 12) {
         IntegrateArgs b = a;
-        const int ndom = a.grp.L <= 16 ? 2 : 1;             // half-warp domains
+        const int ndom = grp_domains(a.grp.L);               // scheduling domains per warp
         const int groups = kWarp / a.grp.L / ndom;           // groups per domain
         int s = (groups + a.n_ics - 1) / a.n_ics + GRINS_GRP_SLOT_EXTRA;
         s = s < 1 ? 1 : (s > 16 ? 16 : s);

@@ -54,20 +54,24 @@ namespace grins {
 
 // Shared-memory layout of one warp of the group kernel:
 //   gather buffers 2 x [R][32] float | slot meta [S] | slots [S]
-//   slot: edge records [P][L] float4 | node records [R][L] float4 | pad
-// Slot sizes are padded so that slot s starts 16 L s bytes past a 128-byte
-// boundary: the L records the groups of different slots read at one
-// position fall into different banks (up to 128 / (16 L) slots).
+//   slot: edge records [P][L] float4 (n, -n log2 T, 1/lambda, gather offset)
+//         | node records [R][L] float2 (G', k) | [R][L] float k/G | pad
+// A half-warp holds the lanes of max(1, L/2) values of j; a slot is padded
+// to 16 * max(1, L/2) bytes past a multiple of 128, so that the records the
+// half-warp reads at one position from all slots of the warp (at most
+// 128 / (16 max(1, L/2)) of them) fall into distinct banks.
 struct GrpLayout {
     int L, R, P, S;
     __host__ __device__ int gather_bytes() const { return 2 * R * kWarp * 4; }
     __host__ __device__ int meta_bytes() const { return (S * (int)sizeof(SlotMeta) + 127) / 128 * 128; }
     __host__ __device__ int edge_bytes() const { return P * L * 16; }
+    __host__ __device__ int node_bytes() const { return R * L * 8; }
     __host__ __device__ int slot_bytes() const
     {
-        const int b = (P + R) * L * 16;
-        const int r = (b + 16 * L) % 128;
-        return b + (r ? 128 - r : 0) + 16 * L;
+        const int b = edge_bytes() + node_bytes() + R * L * 4;
+        const int step = 16 * (L > 2 ? L / 2 : 1);
+        const int r = (b + 128 - step) % 128;   // pad to step mod 128
+        return b + (r ? 128 - r : 0);
     }
     __host__ __device__ int warp_bytes() const
     {
@@ -75,27 +79,35 @@ struct GrpLayout {
     }
 };
 
+// Lanes of a group are j-major: lane = j * (32 / L) + g, so lane j of every
+// group sits in one contiguous block and a group's lanes are 32/L apart.
+// Scheduling domains of four consecutive groups: domains per warp.
+__host__ __device__ inline int grp_domains(int L)
+{
+    const int gs = kWarp / L;
+    return gs < 4 ? 1 : gs / 4;
+}
 __device__ __forceinline__ float grp_sum(float v, int L)
 {
-    for (int o = 1; o < L; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    for (int o = kWarp / L; o < kWarp; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
 
 __device__ __forceinline__ float grp_max(float v, int L)
 {
-    for (int o = 1; o < L; o <<= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    for (int o = kWarp / L; o < kWarp; o <<= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
 }
 
 __device__ __forceinline__ bool grp_all(bool v, int L)
 {
     int x = v ? 1 : 0;
-    for (int o = 1; o < L; o <<= 1) x &= __shfl_xor_sync(0xffffffffu, x, o);
+    for (int o = kWarp / L; o < kWarp; o <<= 1) x &= __shfl_xor_sync(0xffffffffu, x, o);
     return x != 0;
 }
 
-// One edge position: the factor's numerator p + u and denominator 1 + p,
-// p = 2^min(n log2 x_src - n log2 T, 30).
+// One edge position: multiplies the factor's numerator p + u into num and
+// its denominator 1 + p into den, p = 2^min(n log2 x_src - n log2 T, 30).
 struct GrpCtx {
     const float4 *ed;            // this lane's column of the slot's edge records
     const unsigned char *gcol;   // this group's column of the gather buffer
@@ -113,8 +125,8 @@ __device__ __forceinline__ void grp_edge(const GrpCtx &c, int pi, float &num, fl
     if (!GRINS_OK_IDX(off >= 0 && off < c.lim_off && (off & 3) == 0, 33, off)) off = 0;
     const float ls = *reinterpret_cast<const float *>(c.gcol + off);
     const float pw = ex2_approx(fminf(fmaf(e.x, ls, e.y), 30.0f));
-    num = pw + e.z;
-    den = 1.0f + pw;
+    num *= pw + e.z;
+    den = fmaf(den, pw, den);
 }
 
 // Product over the D positions of a row starting at record index pi (D is
@@ -134,12 +146,7 @@ __device__ __forceinline__ float grp_row_ct(const GrpCtx &c, int pi)
         float num = 1.0f, den = 1.0f;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            if (m + q < D) {
-                float nq, dq;
-                grp_edge(c, pi + (m + q) * c.L, nq, dq);
-                num *= nq;
-                den *= dq;
-            }
+            if (m + q < D) grp_edge(c, pi + (m + q) * c.L, num, den);
         }
         prod *= __fdividef(num, den);
     }
@@ -150,11 +157,11 @@ __device__ __forceinline__ float grp_row_ct(const GrpCtx &c, int pi)
 // kGrpCtRows come from the generated prelude of the run-time compile):
 // z[r] <- G'_r prod_r - k_r z[r].
 template <int r, int NPL>
-__device__ __forceinline__ void grp_rows_ct(const GrpCtx &c, const float4 *nd, float (&z)[NPL])
+__device__ __forceinline__ void grp_rows_ct(const GrpCtx &c, const float2 *nd, float (&z)[NPL])
 {
     if constexpr (r < kGrpCtRows && r < NPL) {
         const float prod = grp_row_ct<GrpRowCt<r>::deg>(c, GrpRowCt<r>::off * c.L);
-        const float4 nr = nd[r * c.L];
+        const float2 nr = nd[r * c.L];
         z[r] = fmaf(nr.x, prod, -nr.y * z[r]);
         grp_rows_ct<r + 1, NPL>(c, nd, z);
     }
@@ -169,23 +176,13 @@ __device__ __forceinline__ float grp_row_rt(const GrpCtx &c, int pi, int D)
     for (; pi + 4 * c.L <= pend; pi += 4 * c.L) {
         float num = 1.0f, den = 1.0f;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            float nq, dq;
-            grp_edge(c, pi + q * c.L, nq, dq);
-            num *= nq;
-            den *= dq;
-        }
+        for (int q = 0; q < 4; ++q) grp_edge(c, pi + q * c.L, num, den);
         prod *= __fdividef(num, den);
     }
     if (pi < pend) {
         float num = 1.0f, den = 1.0f;
 #pragma unroll 1
-        for (; pi < pend; pi += c.L) {
-            float nq, dq;
-            grp_edge(c, pi, nq, dq);
-            num *= nq;
-            den *= dq;
-        }
+        for (; pi < pend; pi += c.L) grp_edge(c, pi, num, den);
         prod *= __fdividef(num, den);
     }
     return prod;
@@ -206,9 +203,12 @@ __device__ __forceinline__ void grp_body(const IntegrateArgs &a)
     const int N = a.topo.N, L = LC ? LC : gt.L, R = RC ? RC : gt.R, P = gt.P, S = a.slots;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int GS = kWarp / L;                    // groups per warp
-    const int g = lane / L, j = lane - g * L;    // group, lane within group
-    const int col = j * GS + g;                  // this lane's column in a gather row
-    const int NDOM = L <= 16 ? 2 : 1;            // scheduling domains (half-warps)
+    const int j = lane / GS, g = lane - j * GS;  // lane within group, group (j-major)
+    const int col = lane;                        // this lane's column in a gather row
+    // scheduling domains: four consecutive groups (one lane quad per j), so
+    // a 16-byte record load serves a quad from at most its domain's slots
+    const int DG = GS < 4 ? GS : 4;              // groups per domain
+    const int NDOM = GS / DG;                    // domains per warp
     const int SD = S / NDOM;                     // slots per domain
     const GrpLayout LY{L, R, P, S};
 
@@ -266,7 +266,7 @@ __device__ __forceinline__ void grp_body(const IntegrateArgs &a)
         c.lim_pi = P * L;
         c.lim_off = R * kWarp * 4;
         c.grins_chk = grins_chk;
-        const float4 *nd = reinterpret_cast<const float4 *>(sp + LY.edge_bytes()) + j;
+        const float2 *nd = reinterpret_cast<const float2 *>(sp + LY.edge_bytes()) + j;
 #ifdef GRINS_GRP_CT
         grp_rows_ct<0, NPL>(c, nd, z);
 #else
@@ -274,7 +274,7 @@ __device__ __forceinline__ void grp_body(const IntegrateArgs &a)
         for (int r = 0; r < NPL; ++r) {
             if (r < R) {
                 const float prod = grp_row_rt(c, gt.row_off[r] * L, gt.row_deg[r]);
-                const float4 nr = nd[r * L];
+                const float2 nr = nd[r * L];
                 z[r] = fmaf(nr.x, prod, -nr.y * z[r]);
             }
         }
@@ -285,7 +285,8 @@ __device__ __forceinline__ void grp_body(const IntegrateArgs &a)
     auto stage_slot = [&](int s, long long set) {
         unsigned char *sp = slot_ptr(s);
         float4 *ed = reinterpret_cast<float4 *>(sp);
-        float4 *nd = reinterpret_cast<float4 *>(sp + LY.edge_bytes());
+        float2 *nd = reinterpret_cast<float2 *>(sp + LY.edge_bytes());
+        float *nkg = reinterpret_cast<float *>(sp + LY.edge_bytes() + LY.node_bytes());
         if (!GRINS_OK_IDX(set >= 0 && set < a.n_sets, 34, set)) set = 0;
         const unsigned char *blk = a.params + set * a.L.stride;
         const double *Gd = reinterpret_cast<const double *>(blk + a.L.off_G);
@@ -311,7 +312,8 @@ __device__ __forceinline__ void grp_body(const IntegrateArgs &a)
 #pragma unroll 1
         for (int i = lane; i < R * L; i += kWarp) {
             const int node = gt.row_node[i];
-            float4 rec = make_float4(0.0f, 1.0f, 0.0f, 0.0f);
+            float2 rec = make_float2(0.0f, 1.0f);
+            float kg = 0.0f;
             if (node >= 0) {
                 const double G = Gd[node], k = kdd[node];
                 double Gp = G;
@@ -320,9 +322,10 @@ __device__ __forceinline__ void grp_body(const IntegrateArgs &a)
                     if (a.topo.sign[c] < 0) Gp *= ld[a.topo.edge[c]];
                 rec.x = (float)Gp;
                 rec.y = (float)k;
-                rec.z = (float)(k / G);
+                kg = (float)(k / G);
             }
             nd[i] = rec;
+            nkg[i] = kg;
         }
         __syncwarp();
     };
@@ -346,8 +349,10 @@ __device__ __forceinline__ void grp_body(const IntegrateArgs &a)
     auto refill = [&]() {
 #pragma unroll 1
         for (int d = 0; d < NDOM; ++d) {
-            const unsigned dmask = NDOM == 2 ? (0xffffu << (16 * d)) : FULL;
-            const bool in_dom = (dmask >> lane) & 1u;
+            // the domain's groups are bits d*DG .. d*DG+DG-1 of the ballot
+            // below (taken at the lanes j = 0, lane = g)
+            const unsigned dmask = (DG == 32 ? FULL : ((1u << DG) - 1u)) << (d * DG);
+            const bool in_dom = g / DG == d;
             const int s_lo = d * SD, s_hi = s_lo + SD;
 #pragma unroll 1
             for (;;) {
@@ -361,7 +366,7 @@ __device__ __forceinline__ void grp_body(const IntegrateArgs &a)
                 if (s_pend >= 0) {
                     const int first = meta[s_pend].next_ic;
                     const int take = min(a.n_ics - first, __popc(idle));
-                    const int rank = __popc(idle & ((1u << (g * L)) - 1u));
+                    const int rank = __popc(idle & ((1u << g) - 1u));
                     if (in_dom && my_slot < 0 && rank < take) {
                         my_slot = s_pend;
                         my_ic = first + rank;
@@ -416,11 +421,11 @@ __device__ __forceinline__ void grp_body(const IntegrateArgs &a)
 
     // max_i |v_i| k_i / G_i over the group
     auto residual = [&](const float (&v)[NPL], const unsigned char *sp) -> float {
-        const float4 *nd = reinterpret_cast<const float4 *>(sp + LY.edge_bytes()) + j;
+        const float *nkg = reinterpret_cast<const float *>(sp + LY.edge_bytes() + LY.node_bytes()) + j;
         float r = 0.0f;
 #pragma unroll
         for (int q = 0; q < NPL; ++q)
-            if (q < R) r = fmaxf(r, fabsf(v[q]) * nd[q * L].z);
+            if (q < R) r = fmaxf(r, fabsf(v[q]) * nkg[q * L]);
         return grp_max(r, L);
     };
 
@@ -442,8 +447,7 @@ __device__ __forceinline__ void grp_body(const IntegrateArgs &a)
         // every right-hand side (they hold warp barriers); idle and finished
         // groups compute on scratch values and only working groups act.
         const int s0 = __any_sync(FULL, need_k1) ? 0 : 1;
-#pragma unroll 1
-        for (int s = s0; s <= 6; ++s) {
+        auto stage = [&](const int s) {
             if (s == 0) {
 #pragma unroll
                 for (int r = 0; r < NPL; ++r) z[r] = y[r];
@@ -535,7 +539,16 @@ __device__ __forceinline__ void grp_body(const IntegrateArgs &a)
                     for (int r = 0; r < NPL; ++r) k6[r] = z[r];
                 }
             }
-        }
+        };
+#if defined(GRINS_GRP_CT) && !defined(GRINS_GRP_ROLL_STAGES)
+        // compile-time layout: every stage inlined, so k_{s+1} = z renames
+        // registers instead of copying them
+        if (s0 == 0) stage(0);
+        stage(1); stage(2); stage(3); stage(4); stage(5); stage(6);
+#else
+#pragma unroll 1
+        for (int s = s0; s <= 6; ++s) stage(s);
+#endif
 
         // error estimate and step control; k2 now holds the fifth-order
         // solution and z its derivative k7
@@ -629,7 +642,7 @@ cudaError_t launch_grp_bucket(const IntegrateArgs &a, cudaStream_t st, int num_s
     constexpr int WARPS = 4;
     auto kern = dp5_grp_kernel<NPL, WARPS, MINB>;
     IntegrateArgs b = a;
-    const int ndom = b.grp.L <= 16 ? 2 : 1;
+    const int ndom = grp_domains(b.grp.L);
     GrpLayout LY{b.grp.L, b.grp.R, b.grp.P, b.slots};
     while (WARPS * LY.warp_bytes() > b.smem_limit && LY.S > ndom) LY.S = (b.slots -= ndom);
     const int smem = WARPS * LY.warp_bytes();

@@ -104,6 +104,14 @@ std::string jit_main(const GrpTopo &g, int minb)
 #ifdef GRINS_CHECKED
     s += "#define GRINS_CHECKED 1\n";
 #endif
+#ifdef GRINS_GRP_ROLL_STAGES
+    s += "#define GRINS_GRP_ROLL_STAGES 1\n";
+#else
+    // unrolled stages repeat the right-hand side seven times: keep the stage
+    // loop when a lane's edge list is long (the code would outgrow the
+    // instruction cache)
+    if (g.P > 32) s += "#define GRINS_GRP_ROLL_STAGES 1\n";
+#endif
     s += "#include \"common.cuh\"\nnamespace grins {\n";
     std::snprintf(buf, sizeof(buf), "constexpr int kGrpCtRows = %d;\n", g.R);
     s += buf;
@@ -199,7 +207,7 @@ const void *grp_jit_lookup(const GrpTopo &g)
 cudaError_t launch_grp_jit(const void *kern, const IntegrateArgs &a, cudaStream_t st, int num_sms)
 {
     IntegrateArgs b = a;
-    const int ndom = b.grp.L <= 16 ? 2 : 1;
+    const int ndom = grp_domains(b.grp.L);
     GrpLayout LY{b.grp.L, b.grp.R, b.grp.P, b.slots};
     while (kJitWarps * LY.warp_bytes() > b.smem_limit && LY.S > ndom) LY.S = (b.slots -= ndom);
     const int smem = kJitWarps * LY.warp_bytes();
