@@ -91,7 +91,7 @@ typedef struct {
 /* Solver controls (Sec. 2.1.3: tolerances, start and end time, stop at
  * steady state, optional time points).  grins_solver_default_opts fills:
  * FP32 + polish, rtol 1e-6, atol 1e-9, t0 0, t_end 200, ss_tol 1e-6,
- * max_steps 100000, no time grid, polish_tol 1e-12, polish_iters 16,
+ * max_steps 100000, no time grid, polish_tol 1e-13, polish_iters 16,
  * polish_max_move 1e-2. */
 typedef struct {
     int32_t precision;         /* GRINS_FP32 or GRINS_FP64 integration */
@@ -190,6 +190,57 @@ grins_status grins_racipe_integrate(grins_racipe_t h, const grins_solver_opts *o
  * that nothing has been compiled yet).  The string is owned by the handle
  * and valid until the next call on it. */
 const char *grins_racipe_integrator(grins_racipe_t h);
+
+/* ----------------------------------------------------------------- plans
+ * Batched form of the path (the production "batching" form of the hot
+ * path; the paper's simulator runs one network per call): many networks of
+ * uneven node and edge counts and uneven ensemble sizes are integrated in
+ * one persistent launch of the FP32 lane-group kernel -- each warp visits
+ * the jobs in turn and takes parameter sets from each job's work counter --
+ * followed by each job's FP64 polish (o->polish) and dedupe.  The work is
+ * captured once into a CUDA graph; grins_racipe_plan_run replays it. */
+typedef struct grins_racipe_plan *grins_racipe_plan_t;   /* opaque, library-owned */
+
+/* One job of a plan: a network handle and its device buffers, laid out as
+ * for grins_racipe_integrate and grins_racipe_unique_states. */
+typedef struct {
+    grins_racipe_t net;          /* the network (must outlive the plan) */
+    const void *d_params;        /* [n_sets][param_stride] bytes */
+    int64_t n_sets;
+    const double *d_ic_unit;     /* [n_ics][N] unit initial conditions */
+    int32_t n_ics;
+    double *d_states;            /* [n_sets][n_ics][N] */
+    uint8_t *d_status;           /* [n_sets][n_ics] */
+    double *d_t_final;           /* [n_sets][n_ics], nullable */
+    int32_t *d_n_steps;          /* [n_sets][n_ics], nullable */
+    float *d_err_est;            /* [n_sets][n_ics], nullable */
+    int32_t *d_state_id;         /* [n_sets][n_ics] dedupe output, nullable */
+    int32_t *d_n_unique;         /* [n_sets] dedupe output; both or neither */
+    double dedupe_tol;           /* max-norm tolerance of the dedupe (G/k scale) */
+} grins_racipe_job;
+
+/* Builds a plan for n_jobs jobs with the solver options o (FP32, no time
+ * grid).  With autotune != 0 the block size (2 or 4 warps) and the number
+ * of parameter-set slots per scheduling domain are chosen by timing each
+ * candidate on the first sixteenth of every job's sets (this runs kernels
+ * on `stream` and writes to the jobs' output buffers).  The jobs' buffers
+ * must stay valid for the plan's lifetime; their contents are read when the
+ * plan runs.  Errors: GRINS_E_INVALID_ARG for bad options or jobs (networks
+ * on another device, missing buffers, precision other than FP32, a time
+ * grid); GRINS_E_BUDGET when a network has no lane-group layout of at most
+ * 8 node rows or the jobs do not fit in shared memory. */
+grins_status grins_racipe_plan_create(const grins_solver_opts *o, const grins_racipe_job *jobs,
+                                      int32_t n_jobs, int32_t autotune, void *stream,
+                                      grins_racipe_plan_t *out);
+
+/* Replays the plan's graph on `stream` (asynchronous). */
+grins_status grins_racipe_plan_run(grins_racipe_plan_t p, void *stream);
+
+/* The chosen configuration and the autotuner's timings, as text. */
+const char *grins_racipe_plan_info(grins_racipe_plan_t p);
+
+/* Frees the plan (synchronises the device). */
+grins_status grins_racipe_plan_destroy(grins_racipe_plan_t p);
 
 /* Largest time grid (o->n_t) that grins_racipe_integrate_static accepts. */
 #define GRINS_STATIC_MAX_GRID 4096

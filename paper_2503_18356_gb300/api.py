@@ -55,6 +55,14 @@ class grins_solver_opts(C.Structure):
                 ("polish_max_move", C.c_double)]
 
 
+class grins_racipe_job(C.Structure):
+    _fields_ = [("net", C.c_void_p), ("d_params", C.c_void_p), ("n_sets", C.c_int64),
+                ("d_ic_unit", C.c_void_p), ("n_ics", C.c_int32),
+                ("d_states", C.c_void_p), ("d_status", C.c_void_p), ("d_t_final", C.c_void_p),
+                ("d_n_steps", C.c_void_p), ("d_err_est", C.c_void_p), ("d_state_id", C.c_void_p),
+                ("d_n_unique", C.c_void_p), ("dedupe_tol", C.c_double)]
+
+
 _H = C.c_void_p
 _P = C.c_void_p
 _S = C.c_int32
@@ -75,6 +83,11 @@ _sig = {
                                     _P, _P, _P, _P, _P, _P, _P]),
     "grins_racipe_integrate_static": (_S, [_H, C.POINTER(grins_solver_opts), _P, C.c_int64, _P,
                                            C.c_int32, _P, _P, _P, _P, _P, _P, _P]),
+    "grins_racipe_plan_create": (_S, [C.POINTER(grins_solver_opts), C.POINTER(grins_racipe_job), C.c_int32,
+                                      C.c_int32, _P, C.POINTER(_H)]),
+    "grins_racipe_plan_run": (_S, [_H, _P]),
+    "grins_racipe_plan_info": (C.c_char_p, [_H]),
+    "grins_racipe_plan_destroy": (_S, [_H]),
     "grins_racipe_polish": (_S, [_H, C.POINTER(grins_solver_opts), _P, C.c_int64, C.c_int32, _P, _P, _P, _P]),
     "grins_racipe_unique_states": (_S, [_H, _P, _P, _P, C.c_int64, C.c_int32, C.c_double, _P, _P, _P]),
 }
@@ -267,3 +280,62 @@ class Racipe:
                                                    S, I, tol, _ptr(out[0]), _ptr(out[1]),
                                                    _stream(stream)))
         return out
+
+
+class Plan:
+    """A batched launch over many networks (grins_racipe_plan_*).
+
+    ``jobs``: list of dicts with keys net (a Racipe), params, ic_unit and,
+    optionally, out (buffers as returned by ``Racipe.integrate``; allocated
+    here when absent), dedupe (bool, default True) and dedupe_tol.  The
+    buffers live as long as the plan."""
+
+    def __init__(self, jobs, opts=None, autotune=True, stream=None):
+        self.opts = opts if opts is not None else default_opts()
+        self.jobs = []
+        arr = (grins_racipe_job * len(jobs))()
+        for b, jb in enumerate(jobs):
+            net, params, ic = jb["net"], jb["params"], jb["ic_unit"]
+            S, I, N = params.shape[0], ic.shape[0], net.n_nodes
+            dev = net.device
+            out = jb.get("out") or dict(
+                states=torch.empty((S, I, N), dtype=torch.float64, device=dev),
+                status=torch.empty((S, I), dtype=torch.uint8, device=dev),
+                t_final=torch.empty((S, I), dtype=torch.float64, device=dev),
+                err_est=torch.empty((S, I), dtype=torch.float32, device=dev),
+                n_steps=torch.empty((S, I), dtype=torch.int32, device=dev))
+            if jb.get("dedupe", True):
+                out.setdefault("state_id", torch.empty((S, I), dtype=torch.int32, device=dev))
+                out.setdefault("n_unique", torch.empty((S,), dtype=torch.int32, device=dev))
+            self.jobs.append(dict(net=net, params=params, ic_unit=ic, out=out))
+            arr[b] = grins_racipe_job(net._h.value, params.data_ptr(), S, ic.data_ptr(), I,
+                                      out["states"].data_ptr(), out["status"].data_ptr(),
+                                      out["t_final"].data_ptr() if out.get("t_final") is not None else None,
+                                      out["n_steps"].data_ptr() if out.get("n_steps") is not None else None,
+                                      out["err_est"].data_ptr() if out.get("err_est") is not None else None,
+                                      out["state_id"].data_ptr() if out.get("state_id") is not None else None,
+                                      out["n_unique"].data_ptr() if out.get("n_unique") is not None else None,
+                                      float(jb.get("dedupe_tol", 1e-2)))
+        self._arr = arr
+        h = _H()
+        _check(_lib.grins_racipe_plan_create(C.byref(self.opts), arr, len(jobs), 1 if autotune else 0,
+                                             _stream(stream), C.byref(h)))
+        self._p = h
+
+    def run(self, stream=None):
+        _check(_lib.grins_racipe_plan_run(self._p, _stream(stream)))
+        return self.jobs
+
+    def info(self) -> str:
+        return _lib.grins_racipe_plan_info(self._p).decode()
+
+    def close(self):
+        if getattr(self, "_p", None):
+            _lib.grins_racipe_plan_destroy(self._p)
+            self._p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

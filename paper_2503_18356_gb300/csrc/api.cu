@@ -12,7 +12,7 @@
 #include <string>
 #include <vector>
 
-#include "common.cuh"
+#include "integrate_grp.cuh"
 
 using namespace grins;
 
@@ -96,7 +96,7 @@ extern "C" void grins_solver_default_opts(grins_solver_opts *o)
     o->ss_tol = 1e-6;
     o->max_steps = 100000;
     o->t_grid = nullptr; o->n_t = 0;
-    o->polish_tol = 1e-12;
+    o->polish_tol = 1e-13;
     o->polish_iters = 16;
     o->polish_max_move = 1e-2;
 }
@@ -696,6 +696,267 @@ extern "C" grins_status grins_racipe_unique_states(grins_racipe_t h, const void 
     a.n_sets = n_sets; a.n_ics = n_ics; a.tol = tol;
     a.state_id = d_state_id; a.n_unique = d_n_unique;
     CUDA_TRY(launch_unique(a, (cudaStream_t)stream, h->num_sms), "unique_states: launch");
+    return GRINS_OK;
+}
+
+// ------------------------------------------------------------------- plans
+// A plan integrates many networks (jobs) in one batched launch of the
+// lane-group kernel, followed by each job's polish and dedupe, all captured
+// once into a CUDA graph that grins_racipe_plan_run replays.
+struct grins_racipe_plan {
+    int device = 0, num_sms = 1, smem_limit = 0;
+    grins_solver_opts opts{};
+    std::vector<grins_racipe_job> jobs;
+    std::vector<IntegrateArgs> args;
+    IntegrateArgs *d_args = nullptr;
+    double *d_cum = nullptr;
+    unsigned long long *d_counters = nullptr;   // per job: queue, spare, check code, check info
+    BatchArgs batch{};
+    int warps = 4, slot_extra = 1;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::string info;
+};
+
+static void plan_free(grins_racipe_plan *p)
+{
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+    cudaFree(p->d_args); cudaFree(p->d_cum); cudaFree(p->d_counters);
+    p->exec = nullptr; p->graph = nullptr; p->cap_stream = nullptr;
+    p->d_args = nullptr; p->d_cum = nullptr; p->d_counters = nullptr;
+}
+
+// Per-job integrator arguments for a slot rule (extra slots per domain) and,
+// when `sample` > 1, only the first 1/sample of each job's sets.
+static void plan_args(grins_racipe_plan *p, int slot_extra, int sample)
+{
+    p->args.assign(p->jobs.size(), IntegrateArgs{});
+    int wb = 0;
+    for (size_t b = 0; b < p->jobs.size(); ++b) {
+        const grins_racipe_job &j = p->jobs[b];
+        const grins_racipe *h = j.net;
+        const grins_solver_opts *o = &p->opts;
+        IntegrateArgs &a = p->args[b];
+        a.topo = DevTopo{h->N, h->E, h->d_off, h->d_src, h->d_edge, h->d_sign};
+        a.L = h->layout;
+        a.params = static_cast<const unsigned char *>(j.d_params);
+        a.n_sets = sample > 1 ? (j.n_sets + sample - 1) / sample : j.n_sets;
+        a.ic_unit = j.d_ic_unit;
+        a.n_ics = j.n_ics;
+        a.rtol = o->rtol; a.atol = o->atol; a.t0 = o->t0; a.t_end = o->t_end; a.ss_tol = o->ss_tol;
+        a.max_steps = o->max_steps;
+        a.t_grid = nullptr;
+        a.n_t = 0;
+        a.states = j.d_states; a.status = j.d_status; a.t_final = j.d_t_final; a.n_steps = j.d_n_steps;
+        a.series = nullptr;
+        a.queue = p->d_counters + 4 * b;
+        a.check = p->d_counters + 4 * b + 2;
+        a.smem_limit = p->smem_limit;
+        a.grp = grp_topo(h);
+        a.grp_jit = nullptr;
+        const int ndom = grp_domains(a.grp.L);
+        const int groups = kWarp / a.grp.L / ndom;
+        int sd = (groups + j.n_ics - 1) / j.n_ics + slot_extra;
+        sd = std::max(1, std::min(16, sd));
+        a.slots = sd * ndom;
+        wb = std::max(wb, GrpLayout{a.grp.L, a.grp.R, a.grp.P, a.slots}.warp_bytes());
+    }
+    p->batch.warp_bytes = wb;
+}
+
+static grins_status plan_upload(grins_racipe_plan *p, cudaStream_t st)
+{
+    CUDA_TRY(cudaMemcpyAsync(p->d_args, p->args.data(), sizeof(IntegrateArgs) * p->args.size(),
+                             cudaMemcpyHostToDevice, st), "plan: argument upload");
+    CUDA_TRY(cudaStreamSynchronize(st), "plan: argument upload");
+    return GRINS_OK;
+}
+
+// The plan's work on stream st: reset the counters, the batched integration,
+// then per job the polish and the dedupe.
+static grins_status plan_enqueue(grins_racipe_plan *p, cudaStream_t st, bool integrate_only)
+{
+    CUDA_TRY(cudaMemsetAsync(p->d_counters, 0, sizeof(unsigned long long) * 4 * p->jobs.size(), st),
+             "plan: counter reset");
+    cudaError_t e = launch_integrate_batch(p->batch, p->warps, st, p->num_sms, p->smem_limit);
+    if (e == cudaErrorInvalidConfiguration)
+        return fail(GRINS_E_BUDGET, "plan: the jobs need more shared memory per block than the device has");
+    if (e != cudaSuccess) return cuda_fail(e, "plan: batched launch");
+    if (integrate_only) return GRINS_OK;
+    for (size_t b = 0; b < p->jobs.size(); ++b) {
+        const grins_racipe_job &j = p->jobs[b];
+        if (j.n_sets == 0) continue;
+        if (p->opts.polish) {
+            PolishArgs pa = polish_args(j.net, &p->opts, j.d_params, j.n_sets, j.n_ics, j.d_states, j.d_status,
+                                        j.d_err_est);
+            pa.check = p->d_counters + 4 * b + 2;
+            CUDA_TRY(launch_polish(pa, st, p->num_sms), "plan: polish launch");
+        } else if (j.d_err_est) {
+            CUDA_TRY(cudaMemsetAsync(j.d_err_est, 0xff, sizeof(float) * j.n_sets * j.n_ics, st), "plan: err_est");
+        }
+        if (j.d_state_id) {
+            UniqueArgs u{};
+            u.L = j.net->layout;
+            u.params = static_cast<const unsigned char *>(j.d_params);
+            u.states = j.d_states; u.status = j.d_status;
+            u.n_sets = j.n_sets; u.n_ics = j.n_ics; u.tol = j.dedupe_tol;
+            u.state_id = j.d_state_id; u.n_unique = j.d_n_unique;
+            CUDA_TRY(launch_unique(u, st, p->num_sms), "plan: dedupe launch");
+        }
+    }
+    return GRINS_OK;
+}
+
+extern "C" grins_status grins_racipe_plan_create(const grins_solver_opts *o, const grins_racipe_job *jobs,
+                                                 int32_t n_jobs, int32_t autotune, void *stream,
+                                                 grins_racipe_plan_t *out)
+{
+    g_last_error.clear();
+    if (!o || !out || (n_jobs > 0 && !jobs)) return fail(GRINS_E_INVALID_ARG, "plan_create: NULL argument");
+    *out = nullptr;
+    if (n_jobs < 1) return fail(GRINS_E_INVALID_ARG, "plan_create: n_jobs < 1");
+    if (o->precision != GRINS_FP32) return fail(GRINS_E_INVALID_ARG, "plan_create: plans integrate in FP32");
+    if (!(o->rtol > 0) || !(o->atol > 0) || !std::isfinite(o->rtol) || !std::isfinite(o->atol))
+        return fail(GRINS_E_INVALID_ARG, "plan_create: rtol and atol must be positive");
+    if (!std::isfinite(o->t0) || !std::isfinite(o->t_end) || !(o->t_end > o->t0))
+        return fail(GRINS_E_INVALID_ARG, "plan_create: need finite t0 < t_end");
+    if (!(o->ss_tol >= 0) || o->max_steps < 1) return fail(GRINS_E_INVALID_ARG, "plan_create: bad ss_tol or max_steps");
+    if (o->n_t != 0) return fail(GRINS_E_INVALID_ARG, "plan_create: plans do not write time series");
+    if (o->polish && !polish_opts_ok(o)) return fail(GRINS_E_INVALID_ARG, "plan_create: bad polish options");
+    int dev = -1;
+    CUDA_TRY(cudaGetDevice(&dev), "plan_create: current device");
+    for (int b = 0; b < n_jobs; ++b) {
+        const grins_racipe_job &j = jobs[b];
+        if (!j.net) return fail(GRINS_E_INVALID_ARG, "plan_create: job %d has no network", b);
+        if (j.net->device != dev) return fail(GRINS_E_INVALID_ARG, "plan_create: job %d's network is on another device", b);
+        if (j.n_sets < 0 || j.n_ics < 1) return fail(GRINS_E_INVALID_ARG, "plan_create: job %d has bad sizes", b);
+        if (j.n_sets > 0 && (!j.d_params || !j.d_ic_unit || !j.d_states || !j.d_status))
+            return fail(GRINS_E_INVALID_ARG, "plan_create: job %d lacks a required device buffer", b);
+        if ((j.d_state_id == nullptr) != (j.d_n_unique == nullptr))
+            return fail(GRINS_E_INVALID_ARG, "plan_create: job %d: give both dedupe outputs or neither", b);
+        if (j.d_state_id && (!(j.dedupe_tol >= 0) || !std::isfinite(j.dedupe_tol) || j.n_ics > 4096))
+            return fail(GRINS_E_INVALID_ARG, "plan_create: job %d: bad dedupe tolerance or n_ics", b);
+        if (j.net->grp_L <= 0 || j.net->grp_R > 8)
+            return fail(GRINS_E_BUDGET, "plan_create: job %d's network has no lane-group layout of at most 8 rows", b);
+    }
+    grins_racipe_plan *p = new (std::nothrow) grins_racipe_plan();
+    if (!p) return fail(GRINS_E_NOMEM, "plan_create: host allocation failed");
+    p->device = dev;
+    p->num_sms = jobs[0].net->num_sms;
+    p->smem_limit = (int)jobs[0].net->smem_optin;
+    p->opts = *o;
+    p->jobs.assign(jobs, jobs + n_jobs);
+    // share of the work per job ~ solves x (edges + nodes)
+    std::vector<double> cum(n_jobs);
+    double tot = 0.0;
+    for (int b = 0; b < n_jobs; ++b) {
+        tot += (double)jobs[b].n_sets * jobs[b].n_ics * (jobs[b].net->E + jobs[b].net->N);
+        cum[b] = tot;
+    }
+    for (int b = 0; b < n_jobs; ++b) cum[b] = tot > 0 ? cum[b] / tot : (b + 1.0) / n_jobs;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t ce = cudaMalloc(&p->d_args, sizeof(IntegrateArgs) * n_jobs);
+    if (ce == cudaSuccess) ce = cudaMalloc(&p->d_cum, sizeof(double) * n_jobs);
+    if (ce == cudaSuccess) ce = cudaMalloc(&p->d_counters, sizeof(unsigned long long) * 4 * n_jobs);
+    if (ce == cudaSuccess) ce = cudaMemcpy(p->d_cum, cum.data(), sizeof(double) * n_jobs, cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking);
+    if (ce != cudaSuccess) { plan_free(p); delete p; return cuda_fail(ce, "plan_create: device buffers"); }
+    p->batch.jobs = p->d_args;
+    p->batch.cum_work = p->d_cum;
+    p->batch.n_jobs = n_jobs;
+
+    // autotuner: block size (warps per block) x slots per scheduling domain,
+    // each timed on the first sixteenth of every job's sets
+    char buf[512];
+    std::string tried;
+    if (autotune) {
+        float best = -1.0f;
+        int bw = 4, bx = 1;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        for (int w : {2, 4}) {
+            for (int x : {1, 2}) {
+                plan_args(p, x, 16);
+                p->warps = w;
+                grins_status s = plan_upload(p, st);
+                if (s != GRINS_OK) { plan_free(p); delete p; return s; }
+                cudaEventRecord(e0, st);
+                s = plan_enqueue(p, st, true);
+                cudaEventRecord(e1, st);
+                if (s == GRINS_OK && cudaEventSynchronize(e1) == cudaSuccess) {
+                    float ms = 0.0f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    std::snprintf(buf, sizeof(buf), "%s%d warps/%d extra slots: %.3f ms", tried.empty() ? "" : "; ",
+                                  w, x, ms);
+                    tried += buf;
+                    if (best < 0 || ms < best) { best = ms; bw = w; bx = x; }
+                } else if (s != GRINS_E_BUDGET) {
+                    cudaEventDestroy(e0); cudaEventDestroy(e1);
+                    plan_free(p); delete p;
+                    return s != GRINS_OK ? s : fail(GRINS_E_CUDA, "plan_create: autotune run failed");
+                }
+                g_last_error.clear();
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (best < 0) { plan_free(p); delete p; return fail(GRINS_E_BUDGET, "plan_create: no configuration fits"); }
+        p->warps = bw;
+        p->slot_extra = bx;
+    }
+    plan_args(p, p->slot_extra, 1);
+    grins_status s = plan_upload(p, st);
+    if (s != GRINS_OK) { plan_free(p); delete p; return s; }
+
+    // capture the plan's work once into a graph
+    ce = cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeRelaxed);
+    if (ce != cudaSuccess) { plan_free(p); delete p; return cuda_fail(ce, "plan_create: graph capture"); }
+    s = plan_enqueue(p, p->cap_stream, false);
+    cudaGraph_t g = nullptr;
+    ce = cudaStreamEndCapture(p->cap_stream, &g);
+    p->graph = g;
+    if (s != GRINS_OK) { plan_free(p); delete p; return s; }
+    if (ce == cudaSuccess) ce = cudaGraphInstantiate(&p->exec, p->graph, 0);
+    if (ce != cudaSuccess) { plan_free(p); delete p; return cuda_fail(ce, "plan_create: graph instantiation"); }
+    std::snprintf(buf, sizeof(buf), "batched lane-group DP5(4), %d jobs, %d warps per block, %d extra slots per "
+                  "domain, %d-byte warp region%s", n_jobs, p->warps, p->slot_extra, p->batch.warp_bytes,
+                  autotune ? "; autotuned: " : "");
+    p->info = buf;
+    p->info += tried;
+    *out = p;
+    return GRINS_OK;
+}
+
+extern "C" grins_status grins_racipe_plan_run(grins_racipe_plan_t p, void *stream)
+{
+    g_last_error.clear();
+    if (!p) return fail(GRINS_E_INVALID_ARG, "plan_run: NULL plan");
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != p->device)
+        return fail(GRINS_E_INVALID_ARG, "plan_run: current device is not the plan's");
+    CUDA_TRY(cudaGraphLaunch(p->exec, (cudaStream_t)stream), "plan_run: graph launch");
+    return GRINS_OK;
+}
+
+extern "C" const char *grins_racipe_plan_info(grins_racipe_plan_t p)
+{
+    return p ? p->info.c_str() : "";
+}
+
+extern "C" grins_status grins_racipe_plan_destroy(grins_racipe_plan_t p)
+{
+    if (!p) return fail(GRINS_E_INVALID_ARG, "plan_destroy: NULL plan");
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != p->device) cudaSetDevice(p->device);
+    cudaDeviceSynchronize();
+    plan_free(p);
+    if (cur != p->device) cudaSetDevice(cur);
+    delete p;
     return GRINS_OK;
 }
 

@@ -108,6 +108,16 @@ struct IntegrateArgs {
     const void *grp_jit;         // host: kernel compiled for this layout, or null
 };
 
+// Jobs of one batched launch (a plan): per-job arguments as for a single
+// network (device array), the cumulative share of work up to each job, and
+// the shared-memory bytes each warp's integration region takes.
+struct BatchArgs {
+    const IntegrateArgs *jobs;   // [n_jobs], device
+    const double *cum_work;      // [n_jobs], device: cumulative work fraction
+    int32_t n_jobs;
+    int32_t warp_bytes;          // max over jobs of the per-warp layout (multiple of 128)
+};
+
 // Maximum N served by the FP32 / FP64 integrator buckets.
 #ifndef __CUDACC_RTC__
 // Run-time compiled lane-group kernel for one layout (jit.cu): compiled on
@@ -116,6 +126,11 @@ const void *grp_jit_kernel(const GrpTopo &g, std::string *why);
 const void *grp_jit_lookup(const GrpTopo &g);
 cudaError_t launch_grp_jit(const void *kern, const IntegrateArgs &a, cudaStream_t st, int num_sms);
 cudaError_t launch_integrate_fp32(const IntegrateArgs &a, cudaStream_t st, int num_sms);
+// Batched lane-group launch with `warps` warps per block (2 or 4); smem =
+// dynamic shared memory per block.  Returns cudaErrorInvalidConfiguration
+// when it does not fit.
+cudaError_t launch_integrate_batch(const BatchArgs &b, int warps, cudaStream_t st, int num_sms,
+                                   int smem_limit);
 cudaError_t launch_integrate_fp64(const IntegrateArgs &a, cudaStream_t st, int num_sms);
 #endif
 

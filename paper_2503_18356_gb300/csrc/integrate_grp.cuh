@@ -192,10 +192,9 @@ __device__ __forceinline__ float grp_row_rt(const GrpCtx &c, int pi, int D)
 // LC, RC: lanes per group and rows when fixed at compile time (0: read from
 // the launch arguments).
 template <int NPL, int WARPS, int LC, int RC>
-__device__ __forceinline__ void grp_body(const IntegrateArgs &a)
+__device__ __forceinline__ void grp_body(const IntegrateArgs &a, unsigned char *wbase)
 {
     constexpr unsigned FULL = 0xffffffffu;
-    extern __shared__ __align__(128) unsigned char smem[];
     unsigned long long *grins_chk = a.check;
     (void)grins_chk;
 
@@ -212,7 +211,7 @@ __device__ __forceinline__ void grp_body(const IntegrateArgs &a)
     const int SD = S / NDOM;                     // slots per domain
     const GrpLayout LY{L, R, P, S};
 
-    unsigned char *wbase = smem + warp * LY.warp_bytes();
+    (void)warp;
     float *gbuf = reinterpret_cast<float *>(wbase);
     SlotMeta *meta = reinterpret_cast<SlotMeta *>(wbase + LY.gather_bytes());
     unsigned char *slot_base = wbase + LY.gather_bytes() + LY.meta_bytes();
@@ -628,7 +627,50 @@ __device__ __forceinline__ void grp_body(const IntegrateArgs &a)
     }
 }
 
+// Single network: warp w of the block owns bytes [w * warp_bytes, ...) of
+// the block's dynamic shared memory.
+template <int NPL, int WARPS, int LC, int RC>
+__device__ __forceinline__ void grp_body(const IntegrateArgs &a)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    const GrpLayout LY{LC ? LC : a.grp.L, RC ? RC : a.grp.R, a.grp.P, a.slots};
+    grp_body<NPL, WARPS, LC, RC>(a, smem + (threadIdx.x >> 5) * LY.warp_bytes());
+}
+
 #ifndef __CUDACC_RTC__
+// Many networks in one launch (a plan, grins_racipe_plan_create): warp w
+// starts on the job where its share of the total work falls and then visits
+// every job in turn, integrating sets from that job's work counter until it
+// is exhausted.  The job's arguments are copied into the warp's shared
+// memory (after its fixed-size integration region) so the body reads them
+// with broadcast loads.
+template <int NPL, int WARPS, int MINB>
+__global__ void __launch_bounds__(WARPS * kWarp, MINB)
+dp5_grp_batch_kernel(const BatchArgs b)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int region = b.warp_bytes + (int)((sizeof(IntegrateArgs) + 127) / 128 * 128);
+    unsigned char *wbase = smem + warp * region;
+    IntegrateArgs *ja = reinterpret_cast<IntegrateArgs *>(wbase + b.warp_bytes);
+    const double share = ((double)(blockIdx.x * WARPS + warp) + 0.5) / ((double)gridDim.x * WARPS);
+    int b0 = 0;
+    while (b0 + 1 < b.n_jobs && b.cum_work[b0] <= share) ++b0;
+    for (int k = 0; k < b.n_jobs; ++k) {
+        const int jb = (b0 + k) % b.n_jobs;
+        const unsigned *src = reinterpret_cast<const unsigned *>(b.jobs + jb);
+        unsigned *dst = reinterpret_cast<unsigned *>(ja);
+        for (int i = lane; i < (int)(sizeof(IntegrateArgs) / 4); i += kWarp) dst[i] = src[i];
+        __syncwarp();
+        // one warp-uniform decision: skip a job whose sets are all handed out
+        unsigned long long q = 0;
+        if (lane == 0) q = *reinterpret_cast<volatile unsigned long long *>(ja->queue);
+        q = __shfl_sync(0xffffffffu, q, 0);
+        if (q < (unsigned long long)ja->n_sets) grp_body<NPL, WARPS, 0, 0>(*ja, wbase);
+        __syncwarp();
+    }
+}
+
 template <int NPL, int WARPS, int MINB>
 __global__ void __launch_bounds__(WARPS * kWarp, MINB)
 dp5_grp_kernel(const IntegrateArgs a)

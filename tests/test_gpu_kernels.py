@@ -1,0 +1,62 @@
+"""The FP32 integrator's kernel variants, each through the C ABI against the
+CPU oracle on the same seeded inputs:
+
+  * lane-group layouts with 2, 4 and 8 lanes per solve (GRINS_GRP_L), which
+    change the node rows, the edge positions and the lane mapping;
+  * the kernel compiled for the network at run time (the default) and the
+    run-time-layout kernel (GRINS_JIT=0).
+
+Bars as in test_gpu_parity.py: FP32 + FP64 polish relative 1e-6 (floor
+1e-6 G/k); raw FP32 1e-3 on the G/k scale.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2503_18356_gb300 import workloads as W
+from tests import parity as PT
+
+pytestmark = pytest.mark.gpu
+
+
+def _check(h, params, ic, p, o):
+    for polish, tol in [(1, 1e-6), (0, 1e-3)]:
+        g = PT.to_numpy(h.integrate(params, ic, precision=1, polish=polish))
+        torch.cuda.synchronize()
+        c = PT.compare_states(g, o, p, tol, normalised=not polish)
+        print(h.integrator(), polish, c)
+        assert c["max_rel"] <= tol
+        assert c["n_basin"] <= max(1, 0.01 * g["status"].size)
+        assert c["status_agree"] >= 0.97
+
+
+@pytest.mark.parametrize("L", [2, 4, 8])
+def test_lane_group_layouts_match_oracle(L, monkeypatch):
+    monkeypatch.setenv("GRINS_GRP_L", str(L))
+    w = W.net22_workload()
+    topo = w["topology"]
+    h = PT.gpu_handle(topo)
+    params, ic, p, icn = PT.gpu_sample(h, w["param_seed"], 40, 10)
+    o = O.run_sets_parallel(O.Network(*topo.edges()), p, icn, threads=PT.THREADS)
+    _check(h, params, ic, p, o)
+    assert "L=%d lanes" % L in h.integrator()
+    h.close()
+
+
+@pytest.mark.parametrize("jit", ["1", "0"])
+@pytest.mark.parametrize("wl", ["ts", "net5", "net22"])
+def test_compiled_and_runtime_layout_kernels(jit, wl, monkeypatch):
+    monkeypatch.setenv("GRINS_JIT", jit)
+    w = {"ts": W.ts_workload, "net5": W.net5_workload, "net22": W.net22_workload}[wl]()
+    topo = w["topology"]
+    h = PT.gpu_handle(topo)
+    params, ic, p, icn = PT.gpu_sample(h, w["param_seed"], 40, min(w["n_ics"], 10))
+    o = O.run_sets_parallel(O.Network(*topo.edges()), p, icn, threads=PT.THREADS)
+    _check(h, params, ic, p, o)
+    info = h.integrator()
+    if jit == "1":
+        assert "compiled for this network at run time" in info, info
+    else:
+        assert "run-time layout" in info, info
+    h.close()
