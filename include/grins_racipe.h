@@ -242,6 +242,72 @@ const char *grins_racipe_plan_info(grins_racipe_plan_t p);
 /* Frees the plan (synchronises the device). */
 grins_status grins_racipe_plan_destroy(grins_racipe_plan_t p);
 
+/* ---------------------------------------------------------------- server
+ * Serving form of the path (the paper's simulator is a batch library; this
+ * is the production "serving" form): ensemble requests -- a network, a
+ * sampling seed, n_sets x n_ics, solver options -- are admitted by a worker
+ * thread in arrival order while the number in flight and the HBM budget
+ * allow.  Each admitted request gets its own stream and device buffers
+ * (from a private stream-ordered memory pool) and runs sample -> integrate
+ * -> polish -> dedupe; requests admitted while others run execute
+ * concurrently on the device (continuous batching).  Results stay in device
+ * memory until the request is released.  A network handle must not be used
+ * by other threads while it has requests queued or running; two requests on
+ * one network run one after the other. */
+typedef struct grins_racipe_server *grins_racipe_server_t;   /* opaque */
+
+typedef struct {
+    int32_t max_inflight;      /* requests running at once (streams), 1..64 */
+    int64_t hbm_budget_bytes;  /* device memory all admitted requests may hold */
+} grins_server_config;
+
+enum { GRINS_REQ_QUEUED = 0, GRINS_REQ_RUNNING = 1, GRINS_REQ_DONE = 2, GRINS_REQ_FAILED = 3 };
+
+typedef struct {
+    int32_t state;             /* GRINS_REQ_* */
+    int32_t error;             /* grins_status of a failed request */
+    int64_t n_sets;
+    int32_t n_ics;
+    int64_t bytes;             /* device memory the request holds until released */
+    double queued_s;           /* submission -> admission (so far, if queued) */
+    double latency_s;          /* submission -> results ready; -1 if not done */
+} grins_request_info;
+
+/* Defaults: 8 in flight, 32 GiB budget. */
+void grins_server_default_config(grins_server_config *c);
+
+/* Starts a server (and its worker thread) on the current device; c = NULL
+ * for the defaults.  Errors: GRINS_E_INVALID_ARG for a bad config. */
+grins_status grins_racipe_server_create(const grins_server_config *c, grins_racipe_server_t *out);
+
+/* Queues a request: parameter sets 0 .. n_sets-1 of `seed` (ranges r, NULL
+ * = defaults) with n_ics ICs on network `net`, integrated with o (no time
+ * grid) and deduplicated with dedupe_tol.  Returns at once with its id.
+ * Errors: GRINS_E_INVALID_ARG for bad arguments, GRINS_E_BUDGET when the
+ * request alone needs more than the whole HBM budget. */
+grins_status grins_racipe_server_submit(grins_racipe_server_t sv, grins_racipe_t net,
+                                        const grins_racipe_ranges *r, uint64_t seed, int64_t n_sets,
+                                        int32_t n_ics, const grins_solver_opts *o, double dedupe_tol,
+                                        int64_t *request_id);
+
+/* Waits (timeout_s < 0: without limit) for the request to finish and
+ * reports its state and timings in *info (nullable). */
+grins_status grins_racipe_server_wait(grins_racipe_server_t sv, int64_t request_id, double timeout_s,
+                                      grins_request_info *info);
+
+/* Copies a finished request's results into caller buffers (each nullable):
+ * states double [n_sets][n_ics][N], status uint8 [n_sets][n_ics],
+ * n_unique int32 [n_sets], state_id int32 [n_sets][n_ics]. */
+grins_status grins_racipe_server_copy_results(grins_racipe_server_t sv, int64_t request_id,
+                                              double *d_states, uint8_t *d_status, int32_t *d_n_unique,
+                                              int32_t *d_state_id, void *stream);
+
+/* Frees a finished request's device memory and forgets it. */
+grins_status grins_racipe_server_release(grins_racipe_server_t sv, int64_t request_id);
+
+/* Stops the worker, waits for running requests and frees everything. */
+grins_status grins_racipe_server_destroy(grins_racipe_server_t sv);
+
 /* Largest time grid (o->n_t) that grins_racipe_integrate_static accepts. */
 #define GRINS_STATIC_MAX_GRID 4096
 

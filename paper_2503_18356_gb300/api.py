@@ -63,6 +63,17 @@ class grins_racipe_job(C.Structure):
                 ("d_n_unique", C.c_void_p), ("dedupe_tol", C.c_double)]
 
 
+class grins_server_config(C.Structure):
+    _fields_ = [("max_inflight", C.c_int32), ("hbm_budget_bytes", C.c_int64)]
+
+
+class grins_request_info(C.Structure):
+    _fields_ = [("state", C.c_int32), ("error", C.c_int32), ("n_sets", C.c_int64), ("n_ics", C.c_int32),
+                ("bytes", C.c_int64), ("queued_s", C.c_double), ("latency_s", C.c_double)]
+
+
+REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = range(4)
+
 _H = C.c_void_p
 _P = C.c_void_p
 _S = C.c_int32
@@ -88,6 +99,14 @@ _sig = {
     "grins_racipe_plan_run": (_S, [_H, _P]),
     "grins_racipe_plan_info": (C.c_char_p, [_H]),
     "grins_racipe_plan_destroy": (_S, [_H]),
+    "grins_server_default_config": (None, [C.POINTER(grins_server_config)]),
+    "grins_racipe_server_create": (_S, [C.POINTER(grins_server_config), C.POINTER(_H)]),
+    "grins_racipe_server_submit": (_S, [_H, _H, C.POINTER(grins_racipe_ranges), C.c_uint64, C.c_int64, C.c_int32,
+                                        C.POINTER(grins_solver_opts), C.c_double, C.POINTER(C.c_int64)]),
+    "grins_racipe_server_wait": (_S, [_H, C.c_int64, C.c_double, C.POINTER(grins_request_info)]),
+    "grins_racipe_server_copy_results": (_S, [_H, C.c_int64, _P, _P, _P, _P, _P]),
+    "grins_racipe_server_release": (_S, [_H, C.c_int64]),
+    "grins_racipe_server_destroy": (_S, [_H]),
     "grins_racipe_polish": (_S, [_H, C.POINTER(grins_solver_opts), _P, C.c_int64, C.c_int32, _P, _P, _P, _P]),
     "grins_racipe_unique_states": (_S, [_H, _P, _P, _P, C.c_int64, C.c_int32, C.c_double, _P, _P, _P]),
 }
@@ -333,6 +352,63 @@ class Plan:
         if getattr(self, "_p", None):
             _lib.grins_racipe_plan_destroy(self._p)
             self._p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching request server (grins_racipe_server_*)."""
+
+    def __init__(self, max_inflight=8, hbm_budget_bytes=32 << 30, device=None):
+        self.device = torch.device(device or "cuda")
+        cfg = grins_server_config(max_inflight, hbm_budget_bytes)
+        h = _H()
+        with torch.cuda.device(self.device):
+            _check(_lib.grins_racipe_server_create(C.byref(cfg), C.byref(h)))
+        self._s = h
+        self._nets = {}
+
+    def submit(self, net, seed, n_sets, n_ics, opts=None, ranges=None, dedupe_tol=1e-2):
+        o = opts if opts is not None else default_opts()
+        rid = C.c_int64()
+        r = C.byref(ranges) if ranges is not None else None
+        _check(_lib.grins_racipe_server_submit(self._s, net._h, r, seed, n_sets, n_ics, C.byref(o),
+                                               dedupe_tol, C.byref(rid)))
+        self._nets[rid.value] = (net, n_sets, n_ics)
+        return rid.value
+
+    def wait(self, rid, timeout_s=-1.0):
+        info = grins_request_info()
+        _check(_lib.grins_racipe_server_wait(self._s, rid, timeout_s, C.byref(info)))
+        return dict(state=info.state, n_sets=info.n_sets, n_ics=info.n_ics, bytes=info.bytes,
+                    queued_s=info.queued_s, latency_s=info.latency_s)
+
+    def results(self, rid, stream=None):
+        """Copies a finished request's states, status, n_unique, state_id into new tensors."""
+        net, S, I = self._nets[rid]
+        dev = net.device
+        out = dict(states=torch.empty((S, I, net.n_nodes), dtype=torch.float64, device=dev),
+                   status=torch.empty((S, I), dtype=torch.uint8, device=dev),
+                   n_unique=torch.empty((S,), dtype=torch.int32, device=dev),
+                   state_id=torch.empty((S, I), dtype=torch.int32, device=dev))
+        with torch.cuda.device(dev):
+            _check(_lib.grins_racipe_server_copy_results(self._s, rid, _ptr(out["states"]), _ptr(out["status"]),
+                                                         _ptr(out["n_unique"]), _ptr(out["state_id"]),
+                                                         _stream(stream)))
+        return out
+
+    def release(self, rid):
+        _check(_lib.grins_racipe_server_release(self._s, rid))
+        self._nets.pop(rid, None)
+
+    def close(self):
+        if getattr(self, "_s", None):
+            _lib.grins_racipe_server_destroy(self._s)
+            self._s = None
 
     def __del__(self):
         try:

@@ -2,6 +2,13 @@
 // lifetime, argument validation, the incoming-edge CSR, the half-functional
 // median table and the kernel launch sequence of each entry point.
 #include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <memory>
+#include <set>
+#include <thread>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -957,6 +964,375 @@ extern "C" grins_status grins_racipe_plan_destroy(grins_racipe_plan_t p)
     plan_free(p);
     if (cur != p->device) cudaSetDevice(cur);
     delete p;
+    return GRINS_OK;
+}
+
+// ------------------------------------------------------------------ server
+// Continuous batching of ensemble requests.  A worker thread admits queued
+// requests in arrival order while the in-flight count and the HBM budget
+// allow, gives each its own stream, device buffers (from a private
+// stream-ordered memory pool) and work counters, and enqueues sample ->
+// FP32 integrate -> FP64 polish -> dedupe.  Requests admitted while others
+// run execute concurrently (each launch's grid covers only its own work).
+// Results stay in device memory until the request is released.
+namespace {
+
+double now_s()
+{
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+struct ServerRequest {
+    int64_t id = 0;
+    grins_racipe *net = nullptr;
+    grins_racipe_ranges ranges{};
+    uint64_t seed = 0;
+    int64_t n_sets = 0;
+    int32_t n_ics = 0;
+    grins_solver_opts opts{};
+    double dedupe_tol = 1e-2;
+    int state = 0;                 // GRINS_REQ_*
+    grins_status err = GRINS_OK;
+    std::string msg;
+    double t_submit = 0, t_admit = 0, t_done = 0;
+    int64_t bytes = 0;
+    int slot = -1;
+    unsigned char *mem = nullptr;
+    unsigned char *params = nullptr;
+    double *ic = nullptr, *states = nullptr, *t_final = nullptr;
+    uint8_t *status = nullptr;
+    float *err_est = nullptr;
+    int32_t *n_steps = nullptr, *state_id = nullptr, *n_unique = nullptr;
+    unsigned long long *words = nullptr;
+    cudaEvent_t done = nullptr;
+};
+
+int64_t align256(int64_t b) { return (b + 255) / 256 * 256; }
+
+}  // namespace
+
+struct grins_racipe_server {
+    int device = 0, num_sms = 1, max_inflight = 8;
+    int64_t budget = 0, used = 0;
+    cudaMemPool_t pool = nullptr;
+    std::vector<cudaStream_t> streams;
+    std::vector<char> slot_busy;
+    std::mutex mu;
+    std::condition_variable cv, cv_done;
+    std::deque<int64_t> pending;
+    std::map<int64_t, std::unique_ptr<ServerRequest>> reqs;
+    std::set<grins_racipe *> busy_nets;
+    std::thread worker;
+    bool stop = false;
+    int64_t next_id = 1;
+    std::string fatal;
+};
+
+namespace {
+
+// Bytes of device memory a request holds from admission to release.
+int64_t request_bytes(const ServerRequest &r)
+{
+    const int64_t S = r.n_sets, I = r.n_ics, N = r.net->N;
+    return align256(S * r.net->layout.stride) + align256(I * N * 8) + align256(S * I * N * 8) +
+           align256(S * I) + align256(S * I * 8) + align256(S * I * 4) * 3 + align256(S * 4) + 256;
+}
+
+// Enqueues the request's work on its stream (called by the worker with the
+// server lock held).
+grins_status server_launch(grins_racipe_server *sv, ServerRequest &r)
+{
+    cudaStream_t st = sv->streams[r.slot];
+    const int64_t S = r.n_sets, I = r.n_ics, N = r.net->N;
+    CUDA_TRY(cudaMallocFromPoolAsync(reinterpret_cast<void **>(&r.mem), (size_t)r.bytes, sv->pool, st),
+             "server: request buffers");
+    unsigned char *q = r.mem;
+    auto take = [&](int64_t b) { unsigned char *x = q; q += align256(b); return x; };
+    r.params = take(S * r.net->layout.stride);
+    r.ic = reinterpret_cast<double *>(take(I * N * 8));
+    r.states = reinterpret_cast<double *>(take(S * I * N * 8));
+    r.status = take(S * I);
+    r.t_final = reinterpret_cast<double *>(take(S * I * 8));
+    r.err_est = reinterpret_cast<float *>(take(S * I * 4));
+    r.n_steps = reinterpret_cast<int32_t *>(take(S * I * 4));
+    r.state_id = reinterpret_cast<int32_t *>(take(S * I * 4));
+    r.n_unique = reinterpret_cast<int32_t *>(take(S * 4));
+    r.words = reinterpret_cast<unsigned long long *>(take(32));
+    grins_status s = grins_racipe_sample_params(r.net, &r.ranges, r.seed, 0, S, I, r.params, r.ic, st);
+    if (s != GRINS_OK) return s;
+    const grins_racipe *h = r.net;
+    const grins_solver_opts *o = &r.opts;
+    IntegrateArgs a{};
+    a.topo = DevTopo{h->N, h->E, h->d_off, h->d_src, h->d_edge, h->d_sign};
+    a.L = h->layout;
+    a.params = r.params;
+    a.n_sets = S;
+    a.ic_unit = r.ic;
+    a.n_ics = I;
+    a.rtol = o->rtol; a.atol = o->atol; a.t0 = o->t0; a.t_end = o->t_end; a.ss_tol = o->ss_tol;
+    a.max_steps = o->max_steps;
+    a.states = r.states; a.status = r.status; a.t_final = r.t_final; a.n_steps = r.n_steps;
+    a.queue = r.words;
+    a.check = r.words + 2;
+    a.slots = slots_for(I);
+    a.smem_limit = (int32_t)h->smem_optin;
+    a.grp = grp_topo(h);
+    a.grp_jit = o->precision == GRINS_FP32 ? grp_jit_lookup(a.grp) : nullptr;   // never compiles here
+    CUDA_TRY(cudaMemsetAsync(r.words, 0, 32, st), "server: counter reset");
+    cudaError_t le = o->precision == GRINS_FP32 ? launch_integrate_fp32(a, st, h->num_sms)
+                                                : launch_integrate_fp64(a, st, h->num_sms);
+    if (le == cudaErrorInvalidConfiguration)
+        return fail(GRINS_E_BUDGET, "server: the network needs more shared memory per block than the device has");
+    if (le != cudaSuccess) return cuda_fail(le, "server: integrate launch");
+    if (o->polish) {
+        PolishArgs pa = polish_args(h, o, r.params, S, I, r.states, r.status, r.err_est);
+        pa.check = r.words + 2;
+        CUDA_TRY(launch_polish(pa, st, h->num_sms), "server: polish launch");
+    } else {
+        CUDA_TRY(cudaMemsetAsync(r.err_est, 0xff, sizeof(float) * S * I, st), "server: err_est");
+    }
+    s = grins_racipe_unique_states(r.net, r.params, r.states, r.status, S, I, r.dedupe_tol, r.state_id,
+                                   r.n_unique, st);
+    if (s != GRINS_OK) return s;
+    CUDA_TRY(cudaEventRecord(r.done, st), "server: completion event");
+    return GRINS_OK;
+}
+
+void server_loop(grins_racipe_server *sv)
+{
+    cudaSetDevice(sv->device);
+    std::unique_lock<std::mutex> lock(sv->mu);
+    while (!sv->stop) {
+        bool progress = false;
+        // completions
+        for (auto &kv : sv->reqs) {
+            ServerRequest &r = *kv.second;
+            if (r.state != GRINS_REQ_RUNNING) continue;
+            const cudaError_t q = cudaEventQuery(r.done);
+            if (q == cudaErrorNotReady) continue;
+            r.t_done = now_s();
+            r.state = q == cudaSuccess ? GRINS_REQ_DONE : GRINS_REQ_FAILED;
+            if (q != cudaSuccess) { r.err = GRINS_E_CUDA; r.msg = cudaGetErrorString(q); }
+            sv->slot_busy[r.slot] = 0;
+            sv->busy_nets.erase(r.net);
+            progress = true;
+        }
+        if (progress) sv->cv_done.notify_all();
+        // admissions, in arrival order; a request whose network is busy with
+        // an earlier request waits without blocking the others
+        for (auto it = sv->pending.begin(); it != sv->pending.end();) {
+            ServerRequest &r = *sv->reqs[*it];
+            int slot = -1;
+            for (int i = 0; i < sv->max_inflight && slot < 0; ++i)
+                if (!sv->slot_busy[i]) slot = i;
+            if (slot < 0) break;
+            if (sv->busy_nets.count(r.net)) { ++it; continue; }
+            if (sv->used + r.bytes > sv->budget && sv->used > 0) break;   // head waits for memory
+            r.slot = slot;
+            sv->slot_busy[slot] = 1;
+            sv->busy_nets.insert(r.net);
+            sv->used += r.bytes;
+            r.t_admit = now_s();
+            r.state = GRINS_REQ_RUNNING;
+            cudaSetDevice(r.net->device);
+            const grins_status s = server_launch(sv, r);
+            if (s != GRINS_OK) {
+                r.state = GRINS_REQ_FAILED;
+                r.err = s;
+                r.msg = grins_last_error();
+                r.t_done = now_s();
+                sv->slot_busy[slot] = 0;
+                sv->busy_nets.erase(r.net);
+                sv->cv_done.notify_all();
+            }
+            it = sv->pending.erase(it);
+            progress = true;
+        }
+        if (!progress) sv->cv.wait_for(lock, std::chrono::microseconds(100));
+    }
+}
+
+}  // namespace
+
+extern "C" void grins_server_default_config(grins_server_config *c)
+{
+    if (!c) return;
+    c->max_inflight = 8;
+    c->hbm_budget_bytes = (int64_t)32 << 30;
+}
+
+extern "C" grins_status grins_racipe_server_create(const grins_server_config *c, grins_racipe_server_t *out)
+{
+    g_last_error.clear();
+    if (!out) return fail(GRINS_E_INVALID_ARG, "server_create: out is NULL");
+    *out = nullptr;
+    grins_server_config cfg;
+    if (c) cfg = *c; else grins_server_default_config(&cfg);
+    if (cfg.max_inflight < 1 || cfg.max_inflight > 64 || cfg.hbm_budget_bytes <= 0)
+        return fail(GRINS_E_INVALID_ARG, "server_create: need 1 <= max_inflight <= 64 and a positive budget");
+    auto sv = std::unique_ptr<grins_racipe_server>(new (std::nothrow) grins_racipe_server());
+    if (!sv) return fail(GRINS_E_NOMEM, "server_create: host allocation failed");
+    CUDA_TRY(cudaGetDevice(&sv->device), "server_create: current device");
+    CUDA_TRY(cudaDeviceGetAttribute(&sv->num_sms, cudaDevAttrMultiProcessorCount, sv->device), "server_create");
+    sv->max_inflight = cfg.max_inflight;
+    sv->budget = cfg.hbm_budget_bytes;
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = sv->device;
+    CUDA_TRY(cudaMemPoolCreate(&sv->pool, &props), "server_create: memory pool");
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(sv->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    sv->streams.assign(sv->max_inflight, nullptr);
+    sv->slot_busy.assign(sv->max_inflight, 0);
+    for (auto &st : sv->streams) {
+        cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            for (auto &x : sv->streams) if (x) cudaStreamDestroy(x);
+            cudaMemPoolDestroy(sv->pool);
+            return cuda_fail(e, "server_create: streams");
+        }
+    }
+    grins_racipe_server *raw = sv.release();
+    raw->worker = std::thread(server_loop, raw);
+    *out = raw;
+    return GRINS_OK;
+}
+
+extern "C" grins_status grins_racipe_server_submit(grins_racipe_server_t sv, grins_racipe_t net,
+                                                   const grins_racipe_ranges *r, uint64_t seed, int64_t n_sets,
+                                                   int32_t n_ics, const grins_solver_opts *o, double dedupe_tol,
+                                                   int64_t *request_id)
+{
+    g_last_error.clear();
+    if (!sv || !net || !o || !request_id) return fail(GRINS_E_INVALID_ARG, "server_submit: NULL argument");
+    if (n_sets < 1 || n_ics < 1 || n_ics > 4096) return fail(GRINS_E_INVALID_ARG, "server_submit: bad sizes");
+    if (net->device != sv->device) return fail(GRINS_E_INVALID_ARG, "server_submit: network on another device");
+    if (o->n_t != 0) return fail(GRINS_E_INVALID_ARG, "server_submit: requests do not write time series");
+    if (o->precision != GRINS_FP32 && o->precision != GRINS_FP64)
+        return fail(GRINS_E_INVALID_ARG, "server_submit: unknown precision");
+    if (!(o->rtol > 0) || !(o->atol > 0) || !(o->t_end > o->t0) || o->max_steps < 1 || !(o->ss_tol >= 0) ||
+        (o->polish && !polish_opts_ok(o)))
+        return fail(GRINS_E_INVALID_ARG, "server_submit: bad solver options");
+    if (!(dedupe_tol >= 0)) return fail(GRINS_E_INVALID_ARG, "server_submit: dedupe_tol < 0");
+    grins_racipe_ranges rr;
+    if (r) rr = *r; else grins_racipe_default_ranges(&rr);
+    grins_status s = check_ranges(rr);
+    if (s != GRINS_OK) return s;
+    // the half-functional median table is host work: do it here, in the
+    // submitting thread, not in the worker
+    s = ensure_medians(net, rr);
+    if (s != GRINS_OK) return s;
+    auto req = std::unique_ptr<ServerRequest>(new (std::nothrow) ServerRequest());
+    if (!req) return fail(GRINS_E_NOMEM, "server_submit: host allocation failed");
+    req->net = net; req->ranges = rr; req->seed = seed; req->n_sets = n_sets; req->n_ics = n_ics;
+    req->opts = *o; req->dedupe_tol = dedupe_tol;
+    req->bytes = request_bytes(*req);
+    if (req->bytes > sv->budget)
+        return fail(GRINS_E_BUDGET, "server_submit: the request needs %lld bytes, above the %lld-byte budget",
+                    (long long)req->bytes, (long long)sv->budget);
+    CUDA_TRY(cudaEventCreateWithFlags(&req->done, cudaEventDisableTiming), "server_submit: event");
+    std::lock_guard<std::mutex> lock(sv->mu);
+    req->id = sv->next_id++;
+    req->t_submit = now_s();
+    req->state = GRINS_REQ_QUEUED;
+    *request_id = req->id;
+    sv->pending.push_back(req->id);
+    sv->reqs.emplace(req->id, std::move(req));
+    sv->cv.notify_all();
+    return GRINS_OK;
+}
+
+static void fill_info(const ServerRequest &r, grins_request_info *info)
+{
+    info->state = r.state;
+    info->error = r.err;
+    info->n_sets = r.n_sets;
+    info->n_ics = r.n_ics;
+    info->bytes = r.bytes;
+    info->queued_s = (r.state >= GRINS_REQ_RUNNING ? r.t_admit : now_s()) - r.t_submit;
+    info->latency_s = r.state >= GRINS_REQ_DONE ? r.t_done - r.t_submit : -1.0;
+}
+
+extern "C" grins_status grins_racipe_server_wait(grins_racipe_server_t sv, int64_t id, double timeout_s,
+                                                 grins_request_info *info)
+{
+    g_last_error.clear();
+    if (!sv) return fail(GRINS_E_INVALID_ARG, "server_wait: NULL server");
+    std::unique_lock<std::mutex> lock(sv->mu);
+    auto it = sv->reqs.find(id);
+    if (it == sv->reqs.end()) return fail(GRINS_E_INVALID_ARG, "server_wait: unknown request %lld", (long long)id);
+    ServerRequest &r = *it->second;
+    const auto deadline = std::chrono::steady_clock::now() +
+                          std::chrono::microseconds((long long)(std::max(0.0, timeout_s) * 1e6));
+    while (r.state < GRINS_REQ_DONE) {
+        if (timeout_s >= 0 && sv->cv_done.wait_until(lock, deadline) == std::cv_status::timeout) break;
+        if (timeout_s < 0) sv->cv_done.wait(lock);
+    }
+    if (info) fill_info(r, info);
+    if (r.state == GRINS_REQ_FAILED)
+        return fail(r.err, "server_wait: request %lld failed: %s", (long long)id, r.msg.c_str());
+    return GRINS_OK;
+}
+
+extern "C" grins_status grins_racipe_server_copy_results(grins_racipe_server_t sv, int64_t id, double *d_states,
+                                                         uint8_t *d_status, int32_t *d_n_unique,
+                                                         int32_t *d_state_id, void *stream)
+{
+    g_last_error.clear();
+    if (!sv) return fail(GRINS_E_INVALID_ARG, "server_copy_results: NULL server");
+    std::lock_guard<std::mutex> lock(sv->mu);
+    auto it = sv->reqs.find(id);
+    if (it == sv->reqs.end()) return fail(GRINS_E_INVALID_ARG, "server_copy_results: unknown request");
+    ServerRequest &r = *it->second;
+    if (r.state != GRINS_REQ_DONE) return fail(GRINS_E_INVALID_ARG, "server_copy_results: request not done");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t S = r.n_sets, I = r.n_ics, N = r.net->N;
+    if (d_states) CUDA_TRY(cudaMemcpyAsync(d_states, r.states, S * I * N * 8, cudaMemcpyDeviceToDevice, st), "copy");
+    if (d_status) CUDA_TRY(cudaMemcpyAsync(d_status, r.status, S * I, cudaMemcpyDeviceToDevice, st), "copy");
+    if (d_n_unique) CUDA_TRY(cudaMemcpyAsync(d_n_unique, r.n_unique, S * 4, cudaMemcpyDeviceToDevice, st), "copy");
+    if (d_state_id) CUDA_TRY(cudaMemcpyAsync(d_state_id, r.state_id, S * I * 4, cudaMemcpyDeviceToDevice, st), "copy");
+    return GRINS_OK;
+}
+
+extern "C" grins_status grins_racipe_server_release(grins_racipe_server_t sv, int64_t id)
+{
+    g_last_error.clear();
+    if (!sv) return fail(GRINS_E_INVALID_ARG, "server_release: NULL server");
+    std::lock_guard<std::mutex> lock(sv->mu);
+    auto it = sv->reqs.find(id);
+    if (it == sv->reqs.end()) return fail(GRINS_E_INVALID_ARG, "server_release: unknown request");
+    ServerRequest &r = *it->second;
+    if (r.state == GRINS_REQ_QUEUED || r.state == GRINS_REQ_RUNNING)
+        return fail(GRINS_E_INVALID_ARG, "server_release: request %lld is not finished", (long long)id);
+    if (r.mem) {
+        cudaFreeAsync(r.mem, sv->streams[r.slot]);
+        sv->used -= r.bytes;
+    }
+    cudaEventDestroy(r.done);
+    sv->reqs.erase(it);
+    sv->cv.notify_all();
+    return GRINS_OK;
+}
+
+extern "C" grins_status grins_racipe_server_destroy(grins_racipe_server_t sv)
+{
+    if (!sv) return fail(GRINS_E_INVALID_ARG, "server_destroy: NULL server");
+    {
+        std::lock_guard<std::mutex> lock(sv->mu);
+        sv->stop = true;
+        sv->cv.notify_all();
+    }
+    sv->worker.join();
+    cudaSetDevice(sv->device);
+    for (auto &st : sv->streams) cudaStreamSynchronize(st);
+    for (auto &kv : sv->reqs) {
+        if (kv.second->mem) cudaFreeAsync(kv.second->mem, sv->streams[kv.second->slot]);
+        cudaEventDestroy(kv.second->done);
+    }
+    for (auto &st : sv->streams) { cudaStreamSynchronize(st); cudaStreamDestroy(st); }
+    cudaMemPoolDestroy(sv->pool);
+    delete sv;
     return GRINS_OK;
 }
 
