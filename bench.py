@@ -30,9 +30,10 @@ N_SETS = 100_000
 N_ICS = 10
 TOL = dict(rtol=1e-6, atol=1e-9, t_end=200.0, ss_tol=1e-6)
 # DRAM bytes (read + write) of one integrator launch per solve, from an ncu
-# capture of the same kernel on a 20,000-set launch of this workload
-# (35.9 MB for 200,000 solves); traffic grows with the solves per launch.
-INTEGRATOR_DRAM_BYTES_PER_SOLVE = 35.9e6 / 200_000
+# capture of the same kernel on a 20,000-set launch of this workload;
+# traffic grows with the solves per launch.  None while no capture of the
+# current kernel exists.
+INTEGRATOR_DRAM_BYTES_PER_SOLVE = None
 
 
 def parse():
@@ -331,7 +332,8 @@ def run_native(args):
             step_attempts_per_solve=attempts / (S * I),
             status_hist=np.bincount(status.ravel(), minlength=5).tolist(),
             roofline=dict(bound="alu", achieved=achieved, peak=peak, unit=unit, frac=achieved / peak,
-                          traffic=INTEGRATOR_DRAM_BYTES_PER_SOLVE * S * I, kernel=h.integrator(),
+                          traffic=(INTEGRATOR_DRAM_BYTES_PER_SOLVE * S * I
+                                   if INTEGRATOR_DRAM_BYTES_PER_SOLVE else None), kernel=h.integrator(),
                           peak_basis="%d SMs x %s lanes/clk x %.0f MHz (median SM clock sampled in the "
                                      "timed region); reciprocal rate measured at 16/clk/SM on this GPU"
                                      % (sms, "16 SFU" if sfu_bound else "128 FP32", f_mhz),

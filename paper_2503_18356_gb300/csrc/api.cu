@@ -50,6 +50,26 @@ static grins_status cuda_fail(cudaError_t e, const char *what)
     } while (0)
 
 // ------------------------------------------------------------------ handle
+// A lane-group layout on the device (host copy of the row table).
+struct GrpDev {
+    int L = 0, R = 0, P = 0;
+    std::vector<int32_t> row_off, row_deg;
+    int32_t *d_pos_edge = nullptr, *d_pos_off = nullptr, *d_row_node = nullptr;
+    void free_device()
+    {
+        cudaFree(d_pos_edge); cudaFree(d_pos_off); cudaFree(d_row_node);
+        d_pos_edge = d_pos_off = d_row_node = nullptr;
+    }
+    GrpTopo topo() const
+    {
+        GrpTopo g{};
+        g.L = L; g.R = R; g.P = P;
+        g.pos_edge = d_pos_edge; g.pos_off = d_pos_off; g.row_node = d_row_node;
+        for (int r = 0; r < R && r < kGrpMaxRows; ++r) { g.row_off[r] = row_off[r]; g.row_deg[r] = row_deg[r]; }
+        return g;
+    }
+};
+
 struct grins_racipe {
     int N = 0, E = 0, device = 0, num_sms = 1;
     size_t smem_optin = 0;
@@ -65,12 +85,13 @@ struct grins_racipe {
     double *d_edge_median = nullptr;
     unsigned long long *d_queue = nullptr;
     double *d_grid = nullptr;
-    // lane-group layout of the FP32 integrator (see GrpTopo)
-    int grp_L = 0, grp_R = 0, grp_P = 0;
-    std::vector<int32_t> grp_row_off, grp_row_deg;
-    int32_t *d_pos_edge = nullptr, *d_pos_off = nullptr, *d_row_node = nullptr;
+    // lane-group layouts of the FP32 integrator (see GrpTopo): for the
+    // shared-record kernels (run-time layout, batched plans) and for the
+    // register-record kernel compiled at run time
+    GrpDev grp, rr;
     std::string jit_why = "not compiled yet";          // why no run-time compiled kernel is used
     bool jit_used = false;
+    int used_L = 0, used_R = 0, used_P = 0;            // layout of the last FP32 launch
     std::string info;                                  // grins_racipe_integrator text
     int grid_cap = 0;
     // cached median table
@@ -115,38 +136,29 @@ static void free_device(grins_racipe *h)
 {
     cudaFree(h->d_off); cudaFree(h->d_src); cudaFree(h->d_edge); cudaFree(h->d_sign);
     cudaFree(h->d_edge_sign); cudaFree(h->d_edge_median); cudaFree(h->d_queue); cudaFree(h->d_grid);
-    cudaFree(h->d_pos_edge); cudaFree(h->d_pos_off); cudaFree(h->d_row_node);
-    h->d_pos_edge = h->d_pos_off = h->d_row_node = nullptr;
+    h->grp.free_device();
+    h->rr.free_device();
     h->d_off = h->d_src = h->d_edge = nullptr;
     h->d_sign = h->d_edge_sign = nullptr;
     h->d_edge_median = h->d_grid = nullptr;
     h->d_queue = nullptr;
 }
 
-// Lane-group layout (GrpTopo): L = the smallest power of two with at most
-// 8 node rows (the register arrays stay small enough for 12 warps per SM);
-// nodes sorted by in-degree (descending, ties by index) fill
-// rows of L; row r takes D_r = its largest in-degree positions.  Within a row
-// the host orders each lane's in-edges so that, position by position, the L
-// lanes read sources in distinct gather columns (distinct shared-memory
-// banks) where it can, filling the gaps with neutral edges.
+// Lane-group layout (GrpTopo) with L lanes per solve: nodes sorted by
+// in-degree (descending, ties by index) fill rows of L; row r takes D_r = its
+// largest in-degree positions.  Within a row the host orders each lane's
+// in-edges so that, position by position, the L lanes read sources in
+// distinct gather columns (distinct shared-memory banks) where it can,
+// filling the gaps with neutral edges.
 struct GrpHost {
     int L = 0, R = 0, P = 0;
     std::vector<int32_t> row_off, row_deg, pos_edge, pos_off, row_node;
 };
 
-static GrpHost build_grp(int N, const std::vector<int32_t> &csr_off, const std::vector<int32_t> &csr_src,
+static GrpHost build_grp(int N, int L, const std::vector<int32_t> &csr_off, const std::vector<int32_t> &csr_src,
                          const std::vector<int32_t> &csr_edge)
 {
     GrpHost g;
-    int L = 1;
-    while ((N + L - 1) / L > 8 && L < kWarp) L *= 2;
-    // GRINS_GRP_L (1, 2, 4, 8, 16 or 32) overrides the choice when it still
-    // gives at most 12 rows (a tuning override)
-    if (const char *ev = std::getenv("GRINS_GRP_L")) {
-        const int f = std::atoi(ev);
-        if ((f == 1 || f == 2 || f == 4 || f == 8 || f == 16 || f == 32) && (N + f - 1) / f <= 12) L = f;
-    }
     const int R = (N + L - 1) / L;
     if (R > kGrpMaxRows) return g;
     const int GS = kWarp / L;
@@ -161,6 +173,74 @@ static GrpHost build_grp(int N, const std::vector<int32_t> &csr_off, const std::
     for (int q = 0; q < N; ++q) { g.row_node[q] = order[q]; gslot[order[q]] = q; }
     auto col_of = [&](int node) { return gslot[node] % L; };
     auto off_of_slot = [&](int slot) { return slot * GS * 4; };
+    // Order of one row's edges: position by position, each lane (in lane
+    // order) takes its first unplaced edge whose source column no other
+    // source at this position uses (or whose source another lane already
+    // reads), else -- when it has no neutral slot left -- its first unplaced
+    // edge; a lane with nothing to place reads a neutral edge at the address
+    // of the position's first real source (a broadcast, no extra wavefront).
+    // Returns the position count weighted by wavefronts (the largest number
+    // of distinct sources sharing a column at each position).
+    int trials = 64;
+    if (const char *ev = std::getenv("GRINS_GRP_ORDER_TRIALS")) trials = std::max(1, std::atoi(ev));
+    auto order_row = [&](const std::vector<std::vector<int>> &lst0, int D, uint64_t seed,
+                         std::vector<int32_t> &E, std::vector<int32_t> &O) -> int {
+        uint64_t st = seed * 0x9E3779B97F4A7C15ull + 0x632BE59BD9B4E019ull;
+        auto next = [&]() {      // splitmix64
+            uint64_t z = (st += 0x9E3779B97F4A7C15ull);
+            z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+            z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+            return z ^ (z >> 31);
+        };
+        std::vector<std::vector<int>> lst = lst0;
+        std::vector<int> lanes(L);
+        for (int j = 0; j < L; ++j) lanes[j] = j;
+        if (seed) {
+            for (int i = L - 1; i > 0; --i) std::swap(lanes[i], lanes[next() % (uint64_t)(i + 1)]);
+            for (auto &v : lst)
+                for (int i = (int)v.size() - 1; i > 0; --i) std::swap(v[i], v[next() % (uint64_t)(i + 1)]);
+        }
+        std::vector<std::vector<char>> used(L);
+        std::vector<int> left(L);
+        for (int j = 0; j < L; ++j) { used[j].assign(lst[j].size(), 0); left[j] = (int)lst[j].size(); }
+        E.assign((size_t)D * L, -1);
+        O.assign((size_t)D * L, 0);
+        int score = 0;
+        for (int m = 0; m < D; ++m) {
+            std::vector<int> col_cnt(L, 0);
+            std::vector<int> src_here;
+            std::vector<int> neutral;
+            for (int jj = 0; jj < L; ++jj) {
+                const int j = lanes[jj];
+                const int spare = (D - m) - left[j];       // neutral slots still to place
+                int pick = -1;
+                for (size_t q = 0; q < lst[j].size() && pick < 0; ++q) {
+                    if (used[j][q]) continue;
+                    const int sn = csr_src[lst[j][q]];
+                    bool same = false;
+                    for (int x : src_here) same = same || x == sn;
+                    if (same || col_cnt[col_of(sn)] == 0) pick = (int)q;
+                }
+                if (pick < 0 && spare == 0) {
+                    for (size_t q = 0; q < lst[j].size() && pick < 0; ++q)
+                        if (!used[j][q]) pick = (int)q;
+                }
+                if (pick < 0) { neutral.push_back(j); continue; }
+                used[j][pick] = 1;
+                --left[j];
+                const int c = lst[j][pick], sn = csr_src[c];
+                bool seen = false;
+                for (int x : src_here) seen = seen || x == sn;
+                if (!seen) { src_here.push_back(sn); col_cnt[col_of(sn)]++; }
+                E[(size_t)m * L + j] = csr_edge[c];
+                O[(size_t)m * L + j] = off_of_slot(gslot[sn]);
+            }
+            const int nof = src_here.empty() ? 0 : off_of_slot(gslot[src_here[0]]);
+            for (int j : neutral) { E[(size_t)m * L + j] = -1; O[(size_t)m * L + j] = nof; }
+            score += std::max(1, *std::max_element(col_cnt.begin(), col_cnt.end()));
+        }
+        return score;
+    };
     int P = 0;
     for (int r = 0; r < R; ++r) {
         int D = 0;
@@ -173,48 +253,85 @@ static GrpHost build_grp(int N, const std::vector<int32_t> &csr_off, const std::
         }
         g.row_off.push_back(P);
         g.row_deg.push_back(D);
-        std::vector<std::vector<char>> used(L);
-        for (int j = 0; j < L; ++j) used[j].assign(lst[j].size(), 0);
-        std::vector<int> left(L);
-        for (int j = 0; j < L; ++j) left[j] = (int)lst[j].size();
-        for (int m = 0; m < D; ++m) {
-            std::vector<char> col_used(L, 0);
-            std::vector<int> src_here;
-            for (int j = 0; j < L; ++j) {
-                const int spare = (D - m) - left[j];       // neutral slots still to place
-                int pick = -1;
-                for (size_t q = 0; q < lst[j].size() && pick < 0; ++q) {
-                    if (used[j][q]) continue;
-                    const int sn = csr_src[lst[j][q]];
-                    bool same = false;
-                    for (int x : src_here) same = same || x == sn;
-                    if (same || !col_used[col_of(sn)]) pick = (int)q;
-                }
-                if (pick < 0 && spare == 0) {
-                    for (size_t q = 0; q < lst[j].size() && pick < 0; ++q)
-                        if (!used[j][q]) pick = (int)q;
-                }
-                if (pick >= 0) {
-                    used[j][pick] = 1;
-                    --left[j];
-                    const int c = lst[j][pick], sn = csr_src[c];
-                    col_used[col_of(sn)] = 1;
-                    src_here.push_back(sn);
-                    g.pos_edge.push_back(csr_edge[c]);
-                    g.pos_off.push_back(off_of_slot(gslot[sn]));
-                } else {                                    // neutral edge in a free column
-                    int cf = 0;
-                    while (cf < L - 1 && col_used[cf]) ++cf;
-                    col_used[cf] = 1;
-                    g.pos_edge.push_back(-1);
-                    g.pos_off.push_back(off_of_slot(cf));
-                }
-            }
+        // trial 0 is the plain greedy order; later trials shuffle the lane
+        // order and each lane's candidate order; the order with the fewest
+        // shared-memory wavefronts wins
+        std::vector<int32_t> best_e, best_o, e, o;
+        int best = -1;
+        for (int trial = 0; trial < trials; ++trial) {
+            const int sc = order_row(lst, D, (uint64_t)trial, e, o);
+            if (best < 0 || sc < best) { best = sc; best_e.swap(e); best_o.swap(o); }
         }
+        g.pos_edge.insert(g.pos_edge.end(), best_e.begin(), best_e.end());
+        g.pos_off.insert(g.pos_off.end(), best_o.begin(), best_o.end());
         P += D;
     }
     g.P = P;
     return g;
+}
+
+// GRINS_GRP_L (1, 2, 4, 8, 16 or 32): lanes per solve for both layouts when
+// it gives at most 12 rows (a tuning override); 0 when unset.
+static int grp_l_override(int N)
+{
+    if (const char *ev = std::getenv("GRINS_GRP_L")) {
+        const int f = std::atoi(ev);
+        if ((f == 1 || f == 2 || f == 4 || f == 8 || f == 16 || f == 32) && (N + f - 1) / f <= 12) return f;
+    }
+    return 0;
+}
+
+// Shared-record kernels: the smallest power of two L with at most 8 node
+// rows (their register arrays stay small enough for 12 warps per SM).
+static GrpHost choose_grp_shared(int N, const std::vector<int32_t> &off, const std::vector<int32_t> &src,
+                                 const std::vector<int32_t> &edge)
+{
+    int L = 1;
+    while ((N + L - 1) / L > 8 && L < kWarp) L *= 2;
+    if (const int f = grp_l_override(N)) L = f;
+    if ((N + L - 1) / L > kGrpMaxRows) return GrpHost{};
+    return build_grp(N, L, off, src, edge);
+}
+
+// Register-record kernel: a lane holds about 4 registers per edge position
+// and 11 per row on top of ~40.  The smallest power of two L (at most 12
+// rows) whose estimate allows 3 resident blocks of 4 warps per SM (168
+// registers), else 2 (255); none when no L fits.
+static GrpHost choose_grp_registers(int N, const std::vector<int32_t> &off, const std::vector<int32_t> &src,
+                                    const std::vector<int32_t> &edge)
+{
+    auto est = [](const GrpHost &g) { return 4 * g.P + 11 * g.R + 40; };
+    if (const int f = grp_l_override(N)) {
+        GrpHost g = build_grp(N, f, off, src, edge);
+        return est(g) <= 255 ? g : GrpHost{};
+    }
+    for (int limit : {168, 255}) {
+        for (int L = 1; L <= kWarp; L *= 2) {
+            if ((N + L - 1) / L > 12) continue;
+            GrpHost g = build_grp(N, L, off, src, edge);
+            if (est(g) <= limit) return g;
+        }
+    }
+    return GrpHost{};
+}
+
+// Copies layout g to the device into d.
+static cudaError_t upload_grp(const GrpHost &g, GrpDev &d)
+{
+    d.L = g.L; d.R = g.R; d.P = g.P;
+    d.row_off = g.row_off; d.row_deg = g.row_deg;
+    if (g.L <= 0) return cudaSuccess;
+    const size_t np = std::max<size_t>(g.pos_edge.size(), 1), nr = g.row_node.size();
+    cudaError_t ce = cudaMalloc(&d.d_pos_edge, sizeof(int32_t) * np);
+    if (ce == cudaSuccess) ce = cudaMalloc(&d.d_pos_off, sizeof(int32_t) * np);
+    if (ce == cudaSuccess) ce = cudaMalloc(&d.d_row_node, sizeof(int32_t) * nr);
+    if (ce == cudaSuccess && !g.pos_edge.empty())
+        ce = cudaMemcpy(d.d_pos_edge, g.pos_edge.data(), sizeof(int32_t) * g.pos_edge.size(), cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess && !g.pos_off.empty())
+        ce = cudaMemcpy(d.d_pos_off, g.pos_off.data(), sizeof(int32_t) * g.pos_off.size(), cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess)
+        ce = cudaMemcpy(d.d_row_node, g.row_node.data(), sizeof(int32_t) * nr, cudaMemcpyHostToDevice);
+    return ce;
 }
 
 extern "C" grins_status grins_racipe_create(int32_t n_nodes, int32_t n_edges, const int32_t *src,
@@ -262,9 +379,8 @@ extern "C" grins_status grins_racipe_create(int32_t n_nodes, int32_t n_edges, co
         h->csr_src[p] = src[e]; h->csr_edge[p] = e; h->csr_sign[p] = sign[e];
     }
     h->layout = make_layout(n_nodes, n_edges);
-    GrpHost grp = build_grp(n_nodes, h->csr_off, h->csr_src, h->csr_edge);
-    h->grp_L = grp.L; h->grp_R = grp.R; h->grp_P = grp.P;
-    h->grp_row_off = grp.row_off; h->grp_row_deg = grp.row_deg;
+    const GrpHost grp = choose_grp_shared(n_nodes, h->csr_off, h->csr_src, h->csr_edge);
+    const GrpHost grr = choose_grp_registers(n_nodes, h->csr_off, h->csr_src, h->csr_edge);
 
     cudaError_t ce = cudaGetDevice(&h->device);
     if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
@@ -285,18 +401,8 @@ extern "C" grins_status grins_racipe_create(int32_t n_nodes, int32_t n_edges, co
     if (ce == cudaSuccess && n_edges) ce = cudaMemcpy(h->d_edge, h->csr_edge.data(), sizeof(int32_t) * n_edges, cudaMemcpyHostToDevice);
     if (ce == cudaSuccess && n_edges) ce = cudaMemcpy(h->d_sign, h->csr_sign.data(), n_edges, cudaMemcpyHostToDevice);
     if (ce == cudaSuccess && n_edges) ce = cudaMemcpy(h->d_edge_sign, h->sign.data(), n_edges, cudaMemcpyHostToDevice);
-    if (h->grp_L > 0) {
-        const size_t np = std::max<size_t>(grp.pos_edge.size(), 1), nr = grp.row_node.size();
-        if (ce == cudaSuccess) ce = cudaMalloc(&h->d_pos_edge, sizeof(int32_t) * np);
-        if (ce == cudaSuccess) ce = cudaMalloc(&h->d_pos_off, sizeof(int32_t) * np);
-        if (ce == cudaSuccess) ce = cudaMalloc(&h->d_row_node, sizeof(int32_t) * nr);
-        if (ce == cudaSuccess && !grp.pos_edge.empty())
-            ce = cudaMemcpy(h->d_pos_edge, grp.pos_edge.data(), sizeof(int32_t) * grp.pos_edge.size(), cudaMemcpyHostToDevice);
-        if (ce == cudaSuccess && !grp.pos_off.empty())
-            ce = cudaMemcpy(h->d_pos_off, grp.pos_off.data(), sizeof(int32_t) * grp.pos_off.size(), cudaMemcpyHostToDevice);
-        if (ce == cudaSuccess)
-            ce = cudaMemcpy(h->d_row_node, grp.row_node.data(), sizeof(int32_t) * nr, cudaMemcpyHostToDevice);
-    }
+    if (ce == cudaSuccess) ce = upload_grp(grp, h->grp);
+    if (ce == cudaSuccess) ce = upload_grp(grr, h->rr);
     if (ce != cudaSuccess) {
         free_device(h);
         delete h;
@@ -323,13 +429,16 @@ extern "C" const char *grins_racipe_integrator(grins_racipe_t h)
 {
     if (!h) return "";
     char buf[160];
-    if (h->grp_L > 0)
+    const bool ran = h->used_L > 0;
+    const int L = ran ? h->used_L : h->grp.L, R = ran ? h->used_R : h->grp.R, P = ran ? h->used_P : h->grp.P;
+    if (L > 0)
         std::snprintf(buf, sizeof(buf), "lane-group DP5(4), L=%d lanes per solve, R=%d node rows, P=%d edge positions",
-                      h->grp_L, h->grp_R, h->grp_P);
+                      L, R, P);
     else
         std::snprintf(buf, sizeof(buf), "generic shared-memory DP5(4) (no lane-group layout)");
     h->info = buf;
-    if (h->grp_L > 0) h->info += h->jit_used ? "; compiled for this network at run time" : "; run-time layout (" + h->jit_why + ")";
+    if (L > 0) h->info += h->jit_used ? "; compiled for this network at run time (" + h->jit_why + ")"
+                              : "; run-time layout (" + h->jit_why + ")";
     return h->info.c_str();
 }
 
@@ -557,13 +666,30 @@ static PolishArgs polish_args(const grins_racipe *h, const grins_solver_opts *o,
     return p;
 }
 
-static GrpTopo grp_topo(const grins_racipe *h)
+static GrpTopo grp_topo(const grins_racipe *h) { return h->grp.topo(); }
+
+// The FP32 lane-group kernel for h: sets a->grp and a->grp_jit to the
+// kernel compiled for this network -- records in registers when the
+// register layout exists, else records in shared memory (GRINS_JIT_KIND=grp
+// asks for the latter) -- or leaves the run-time-layout kernel (grp_jit
+// null).  compile = false only looks up kernels an earlier call compiled.
+static void pick_fp32_kernel(const grins_racipe *h, IntegrateArgs *a, bool compile, std::string *why)
 {
-    GrpTopo g{};
-    g.L = h->grp_L; g.R = h->grp_R; g.P = h->grp_P;
-    g.pos_edge = h->d_pos_edge; g.pos_off = h->d_pos_off; g.row_node = h->d_row_node;
-    for (int r = 0; r < h->grp_R && r < kGrpMaxRows; ++r) { g.row_off[r] = h->grp_row_off[r]; g.row_deg[r] = h->grp_row_deg[r]; }
-    return g;
+    a->grp = h->grp.topo();
+    a->grp_jit = nullptr;
+    const char *ev = std::getenv("GRINS_JIT_KIND");
+    const bool want_shared = ev && std::string(ev) == "grp";
+    std::string w;
+    if (!want_shared && h->rr.L > 0) {
+        const GrpTopo g = h->rr.topo();
+        const void *k = compile ? grp_jit_kernel(g, kJitRegisters, &w) : grp_jit_lookup(g, kJitRegisters);
+        if (k) { a->grp = g; a->grp_jit = k; if (why) *why = w; return; }
+    }
+    if (h->grp.L > 0) {
+        const void *k = compile ? grp_jit_kernel(a->grp, kJitShared, &w) : grp_jit_lookup(a->grp, kJitShared);
+        if (k) a->grp_jit = k;
+    }
+    if (why) *why = w;
 }
 
 static bool polish_opts_ok(const grins_solver_opts *o)
@@ -662,8 +788,9 @@ extern "C" grins_status grins_racipe_integrate(grins_racipe_t h, const grins_sol
     a.smem_limit = (int32_t)h->smem_optin;
     a.grp = grp_topo(h);
     if (o->precision == GRINS_FP32) {
-        a.grp_jit = grp_jit_kernel(a.grp, &h->jit_why);
+        pick_fp32_kernel(h, &a, true, &h->jit_why);
         h->jit_used = a.grp_jit != nullptr;
+        h->used_L = a.grp.L; h->used_R = a.grp.R; h->used_P = a.grp.P;
     }
 
     CUDA_TRY(cudaMemsetAsync(h->d_queue, 0, 2 * sizeof(unsigned long long), st), "integrate: queue reset");
@@ -846,7 +973,7 @@ extern "C" grins_status grins_racipe_plan_create(const grins_solver_opts *o, con
             return fail(GRINS_E_INVALID_ARG, "plan_create: job %d: give both dedupe outputs or neither", b);
         if (j.d_state_id && (!(j.dedupe_tol >= 0) || !std::isfinite(j.dedupe_tol) || j.n_ics > 4096))
             return fail(GRINS_E_INVALID_ARG, "plan_create: job %d: bad dedupe tolerance or n_ics", b);
-        if (j.net->grp_L <= 0 || j.net->grp_R > 8)
+        if (j.net->grp.L <= 0 || j.net->grp.R > 8)
             return fail(GRINS_E_BUDGET, "plan_create: job %d's network has no lane-group layout of at most 8 rows", b);
     }
     grins_racipe_plan *p = new (std::nothrow) grins_racipe_plan();
@@ -1077,7 +1204,7 @@ grins_status server_launch(grins_racipe_server *sv, ServerRequest &r)
     a.slots = slots_for(I);
     a.smem_limit = (int32_t)h->smem_optin;
     a.grp = grp_topo(h);
-    a.grp_jit = o->precision == GRINS_FP32 ? grp_jit_lookup(a.grp) : nullptr;   // never compiles here
+    if (o->precision == GRINS_FP32) pick_fp32_kernel(h, &a, false, nullptr);   // never compiles here
     CUDA_TRY(cudaMemsetAsync(r.words, 0, 32, st), "server: counter reset");
     cudaError_t le = o->precision == GRINS_FP32 ? launch_integrate_fp32(a, st, h->num_sms)
                                                 : launch_integrate_fp64(a, st, h->num_sms);
@@ -1454,7 +1581,7 @@ extern "C" grins_status grins_racipe_integrate_static(grins_racipe_t h, const gr
     a.slots = slots_for(n_ics);
     a.smem_limit = (int32_t)h->smem_optin;
     a.grp = grp_topo(h);
-    a.grp_jit = grp_jit_lookup(a.grp);   // only a kernel an earlier call already loaded
+    if (o->precision == GRINS_FP32) pick_fp32_kernel(h, &a, false, nullptr);   // only kernels an earlier call loaded
 
     // the array keeps the previous call's counters: clear them first
     CUDA_TRY(cudaMemsetAsync(words, 0, kStaticWords * sizeof(unsigned long long), st),

@@ -121,9 +121,12 @@ struct BatchArgs {
 // Maximum N served by the FP32 / FP64 integrator buckets.
 #ifndef __CUDACC_RTC__
 // Run-time compiled lane-group kernel for one layout (jit.cu): compiled on
-// first use (grp_jit_kernel) or only looked up (grp_jit_lookup).
-const void *grp_jit_kernel(const GrpTopo &g, std::string *why);
-const void *grp_jit_lookup(const GrpTopo &g);
+// first use (grp_jit_kernel) or only looked up (grp_jit_lookup); kind is
+// kJitRegisters (records in registers) or kJitShared (records in shared
+// memory).  The returned pointer is an opaque handle for launch_grp_jit.
+enum JitKind { kJitShared = 0, kJitRegisters = 1 };
+const void *grp_jit_kernel(const GrpTopo &g, int kind, std::string *why);
+const void *grp_jit_lookup(const GrpTopo &g, int kind);
 cudaError_t launch_grp_jit(const void *kern, const IntegrateArgs &a, cudaStream_t st, int num_sms);
 cudaError_t launch_integrate_fp32(const IntegrateArgs &a, cudaStream_t st, int num_sms);
 // Batched lane-group launch with `warps` warps per block (2 or 4); smem =

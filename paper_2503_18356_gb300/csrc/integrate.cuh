@@ -44,6 +44,17 @@ __device__ __forceinline__ float ex2_approx(float x)
     return y;
 }
 
+// a / b as a times the approximate reciprocal of b (one MUFU.RCP, no range
+// handling): for |b| in [2^-126, 2^126], relative error within a few ulp.
+// The integrators' divisors stay inside that range (chunk denominators in
+// [1, 2^121], error scales >= atol).
+__device__ __forceinline__ float div_approx(float a, float b)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(b));
+    return a * r;
+}
+
 // ------------------------------------------------------------------------
 // Checked mode (-DGRINS_CHECKED): every computed shared/global index of the
 // integrator and polish kernels is range- and alignment-checked; the first

@@ -79,6 +79,10 @@ struct GrpLayout {
     }
 };
 
+// Dynamic shared memory of one warp of the register-record kernel
+// (integrate_rr.cuh): two gather buffers [rows][32] float.
+__host__ __device__ constexpr int rr_warp_bytes(int rows) { return 2 * rows * kWarp * 4; }
+
 // Lanes of a group are j-major: lane = j * (32 / L) + g, so lane j of every
 // group sits in one contiguous block and a group's lanes are 32/L apart.
 // Scheduling domains of four consecutive groups: domains per warp.
@@ -148,7 +152,7 @@ __device__ __forceinline__ float grp_row_ct(const GrpCtx &c, int pi)
         for (int q = 0; q < 4; ++q) {
             if (m + q < D) grp_edge(c, pi + (m + q) * c.L, num, den);
         }
-        prod *= __fdividef(num, den);
+        prod *= div_approx(num, den);
     }
     return prod;
 }
@@ -177,13 +181,13 @@ __device__ __forceinline__ float grp_row_rt(const GrpCtx &c, int pi, int D)
         float num = 1.0f, den = 1.0f;
 #pragma unroll
         for (int q = 0; q < 4; ++q) grp_edge(c, pi + q * c.L, num, den);
-        prod *= __fdividef(num, den);
+        prod *= div_approx(num, den);
     }
     if (pi < pend) {
         float num = 1.0f, den = 1.0f;
 #pragma unroll 1
         for (; pi < pend; pi += c.L) grp_edge(c, pi, num, den);
-        prod *= __fdividef(num, den);
+        prod *= div_approx(num, den);
     }
     return prod;
 }
@@ -559,7 +563,7 @@ __device__ __forceinline__ void grp_body(const IntegrateArgs &a, unsigned char *
                 const float err = hh * ((float)dp::e1 * k1[r] + (float)dp::e3 * k3[r] + (float)dp::e4 * k4[r] +
                                         (float)dp::e5 * k5[r] + (float)dp::e6 * k6[r] + (float)dp::e7 * z[r]);
                 const float sc = atol + rtol * fmaxf(fabsf(y[r]), fabsf(k2[r]));
-                const float q = __fdividef(err, sc);
+                const float q = div_approx(err, sc);
                 en += q * q;
                 finite = finite && isfinite(z[r]) && isfinite(k2[r]);
             }

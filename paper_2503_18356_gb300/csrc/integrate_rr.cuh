@@ -1,0 +1,488 @@
+// Lane-group FP32 Dormand-Prince 5(4) integrator with the parameter records
+// in registers, compiled at run time for one network's row layout.
+//
+// Model, lane mapping, gather buffer and step control are those of the
+// shared-memory-record kernel (integrate_grp.cuh; GRiNS Sec. 2.1.1, Eq. 1
+// and Eq. 2 written as products of w (p + u) / (1 + p), p = 2^t,
+// t = n log2 x_src - n log2 T).  What differs:
+//   * a lane keeps the records of its own edge positions in registers --
+//     n, -n log2 T and 1/lambda as FP32 pairs, and the shared-memory address
+//     of each position's source entry -- together with G', k and k/G of its
+//     rows, loaded when it starts a solve.  The edge loop then issues one
+//     shared load per edge (the source value) where the shared-record kernel
+//     issues two, one of them 16 bytes wide;
+//   * edges are taken two at a time with the packed FP32 pair instructions
+//     (fma/add/mul .f32x2 of sm_100 and later), each pair component carrying
+//     at most four factors (p <= 2^30) before its division;
+//   * work is handed out one solve at a time from a set-major counter, so
+//     no parameter-set slots are needed.
+// The rows (GrpRowCt<r>: position offset and degree; kGrpCtRows) are
+// compile-time constants generated for the network, and the stages of an
+// attempt are written out, so every register array is indexed by constants
+// and the gather buffer of each right-hand side is an immediate offset.
+#pragma once
+
+#include "integrate_grp.cuh"
+
+namespace grins {
+
+// Pair offset of row r: rows before it take ceil(deg / 2) pairs each.
+template <int r> struct RrQ {
+    static constexpr int off = RrQ<r - 1>::off + (GrpRowCt<r - 1>::deg + 1) / 2;
+};
+template <> struct RrQ<0> { static constexpr int off = 0; };
+
+constexpr int kRrP = GrpRowCt<kGrpCtRows - 1>::off + GrpRowCt<kGrpCtRows - 1>::deg;   // positions per lane
+constexpr int kRrQ = RrQ<kGrpCtRows>::off;                                              // pairs per lane
+constexpr int kRrPa = kRrP > 0 ? kRrP : 1;
+constexpr int kRrQa = kRrQ > 0 ? kRrQ : 1;
+
+__device__ __forceinline__ unsigned rr_smem_addr(const void *p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+// Gather-buffer accesses and the warp barrier as ordered inline PTX: the
+// buffer offset of a right-hand side is an immediate.
+template <int OFF>
+__device__ __forceinline__ float rr_lds(unsigned addr)
+{
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1+%2];" : "=f"(v) : "r"(addr), "n"(OFF));
+    return v;
+}
+
+template <int OFF>
+__device__ __forceinline__ void rr_sts(unsigned addr, float v)
+{
+    asm volatile("st.shared.f32 [%0+%1], %2;" ::"r"(addr), "n"(OFF), "f"(v) : "memory");
+}
+
+__device__ __forceinline__ void rr_syncwarp()
+{
+    asm volatile("bar.warp.sync %0;" ::"r"(0xffffffffu) : "memory");
+}
+
+template <int NPL>
+struct RrRecs {
+    unsigned ga[kRrPa];                    // shared address of each position's source entry (buffer 0)
+    float2 n[kRrQa], c[kRrQa], u[kRrQa];   // n, -n log2 T, 1/lambda, two positions per pair
+    float Gp[NPL], k[NPL], kg[NPL];        // G' = G prod_inh lambda, k, k/G of this lane's rows
+};
+
+// Positions P, P+1 (record pair Q) into (num, den); FIRST starts the chunk.
+template <int BO, int P, int Q, bool FIRST, int NPL>
+__device__ __forceinline__ void rr_pair(const RrRecs<NPL> &q, float2 &num, float2 &den)
+{
+    const float2 s = make_float2(rr_lds<BO>(q.ga[P]), rr_lds<BO>(q.ga[P + 1]));
+    const float2 t = __ffma2_rn(q.n[Q], s, q.c[Q]);
+    const float2 pw = make_float2(ex2_approx(fminf(t.x, 30.0f)), ex2_approx(fminf(t.y, 30.0f)));
+    const float2 a = __fadd2_rn(pw, q.u[Q]);
+    if constexpr (FIRST) {
+        num = a;
+        den = __fadd2_rn(pw, make_float2(1.0f, 1.0f));
+    } else {
+        num = __fmul2_rn(num, a);
+        den = __ffma2_rn(den, pw, den);
+    }
+}
+
+// Position P alone (component x of record pair Q).
+template <int BO, int P, int Q, bool FIRST, int NPL>
+__device__ __forceinline__ void rr_single(const RrRecs<NPL> &q, float &num, float &den)
+{
+    const float s = rr_lds<BO>(q.ga[P]);
+    const float pw = ex2_approx(fminf(fmaf(q.n[Q].x, s, q.c[Q].x), 30.0f));
+    if constexpr (FIRST) {
+        num = pw + q.u[Q].x;
+        den = pw + 1.0f;
+    } else {
+        num *= pw + q.u[Q].x;
+        den = fmaf(den, pw, den);
+    }
+}
+
+template <int BO, int P0, int Q0, int I, int NP, int NPL>
+__device__ __forceinline__ void rr_pairs(const RrRecs<NPL> &q, float2 &num, float2 &den)
+{
+    if constexpr (I < NP) {
+        rr_pair<BO, P0 + 2 * I, Q0 + I, I == 0, NPL>(q, num, den);
+        rr_pairs<BO, P0, Q0, I + 1, NP, NPL>(q, num, den);
+    }
+}
+
+// NP (1..4) pairs from position P0 / pair Q0, plus the row's last (odd)
+// position when TAIL: the product of their factors.  Up to four factors in
+// all share one division; more keep the two components apart (each holds at
+// most four) and divide each.
+template <int BO, int P0, int Q0, int NP, bool TAIL, int NPL>
+__device__ __forceinline__ float rr_chunk(const RrRecs<NPL> &q)
+{
+    float2 num, den;
+    rr_pairs<BO, P0, Q0, 0, NP, NPL>(q, num, den);
+    if constexpr (TAIL) rr_single<BO, P0 + 2 * NP, Q0 + NP, false, NPL>(q, num.x, den.x);
+    if constexpr (2 * NP + (TAIL ? 1 : 0) <= 4)
+        return div_approx(num.x * num.y, den.x * den.y);
+    else
+        return div_approx(num.x, den.x) * div_approx(num.y, den.y);
+}
+
+// Product over a row of NP pairs (+ TAIL) in chunks of four pairs; the odd
+// position joins the last chunk when it has room, else forms its own.
+template <int BO, int P0, int Q0, int NP, bool TAIL, int C, int NPL>
+__device__ __forceinline__ float rr_row_prod(const RrRecs<NPL> &q)
+{
+    constexpr int first = 4 * C;
+    if constexpr (first >= NP) {
+        if constexpr (TAIL && NP % 4 == 0) {
+            float num, den;
+            rr_single<BO, P0 + 2 * NP, Q0 + NP, true, NPL>(q, num, den);
+            return div_approx(num, den);
+        } else {
+            return 1.0f;
+        }
+    } else {
+        constexpr int np = NP - first < 4 ? NP - first : 4;
+        constexpr bool tail_here = TAIL && first + np >= NP && np < 4;
+        const float f = rr_chunk<BO, P0 + 2 * first, Q0 + first, np, tail_here, NPL>(q);
+        if constexpr (first + 4 >= NP && !(TAIL && NP % 4 == 0))
+            return f;
+        else
+            return f * rr_row_prod<BO, P0, Q0, NP, TAIL, C + 1, NPL>(q);
+    }
+}
+
+// z[r] <- G'_r prod_r - k_r z[r] for rows r, r+1, ...
+template <int BO, int r, int NPL>
+__device__ __forceinline__ void rr_rows(const RrRecs<NPL> &q, float (&z)[NPL])
+{
+    if constexpr (r < kGrpCtRows && r < NPL) {
+        constexpr int D = GrpRowCt<r>::deg;
+        const float prod = rr_row_prod<BO, GrpRowCt<r>::off, RrQ<r>::off, D / 2, (D & 1) != 0, 0, NPL>(q);
+        z[r] = fmaf(q.Gp[r], prod, -q.k[r] * z[r]);
+        rr_rows<BO, r + 1, NPL>(q, z);
+    }
+}
+
+// log2 of this lane's stage values into its column of the buffer at BO
+template <int BO, int r, int NPL>
+__device__ __forceinline__ void rr_put(const float (&z)[NPL], unsigned own)
+{
+    if constexpr (r < kGrpCtRows && r < NPL) {
+        rr_sts<BO + r * kWarp * 4>(own, lg2_approx(fmaxf(z[r], 0.0f)));
+        rr_put<BO, r + 1, NPL>(z, own);
+    }
+}
+
+// z <- Eq. 1 at the stage input z through gather buffer B (0 or 1)
+template <int B, int NPL>
+__device__ __forceinline__ void rr_rhs(const RrRecs<NPL> &q, float (&z)[NPL], unsigned own)
+{
+    constexpr int BO = B * NPL * kWarp * 4;
+    rr_put<BO, 0, NPL>(z, own);
+    rr_syncwarp();
+    rr_rows<BO, 0, NPL>(q, z);
+}
+
+// Records of row r (positions d = 0 .. deg-1) from parameter block blk.
+template <int r, int NPL, int L>
+__device__ __forceinline__ void rr_load_rows(RrRecs<NPL> &q, const IntegrateArgs &a, const unsigned char *blk, int j)
+{
+    if constexpr (r < kGrpCtRows && r < NPL) {
+        constexpr int D = GrpRowCt<r>::deg, P0 = GrpRowCt<r>::off, Q0 = RrQ<r>::off;
+        const double *Td = reinterpret_cast<const double *>(blk + a.L.off_T);
+        const double *ld = reinterpret_cast<const double *>(blk + a.L.off_lam);
+        const uint8_t *nn = blk + a.L.off_n;
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            const int e = a.grp.pos_edge[(P0 + d) * L + j];
+            float n = 1.0f, c = -100.0f, u = 1.0f;     // neutral: (p + 1) / (1 + p) = 1
+            if (e >= 0) {
+                n = (float)nn[e];
+                c = -n * log2f((float)Td[e]);
+                u = __frcp_rn((float)ld[e]);
+            }
+            if (d & 1) { q.n[Q0 + d / 2].y = n; q.c[Q0 + d / 2].y = c; q.u[Q0 + d / 2].y = u; }
+            else       { q.n[Q0 + d / 2].x = n; q.c[Q0 + d / 2].x = c; q.u[Q0 + d / 2].x = u; }
+        }
+        rr_load_rows<r + 1, NPL, L>(q, a, blk, j);
+    }
+}
+
+// Body of the register-record kernel: NPL rows, WARPS warps per block, L
+// lanes per solve.
+template <int NPL, int WARPS, int L>
+__device__ __forceinline__ void rr_body(const IntegrateArgs &a)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    constexpr unsigned FULL = 0xffffffffu;
+    constexpr int GS = kWarp / L;                // groups per warp
+    unsigned long long *grins_chk = a.check;
+    (void)grins_chk;
+    const int N = a.topo.N;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int j = lane / GS, g = lane - j * GS;  // lane within group, group (j-major)
+
+    float *gbuf = reinterpret_cast<float *>(smem) + warp * 2 * NPL * kWarp;
+    const unsigned base = rr_smem_addr(gbuf);
+    const unsigned own = base + 4 * lane;
+#pragma unroll 1
+    for (int i = lane; i < 2 * NPL * kWarp; i += kWarp) gbuf[i] = 0.0f;
+
+    RrRecs<NPL> q;
+#pragma unroll
+    for (int p = 0; p < kRrPa; ++p) {
+        int off = p < kRrP ? a.grp.pos_off[p * L + j] : 0;
+        if (!GRINS_OK_IDX(off >= 0 && off < NPL * kWarp * 4 && (off & 3) == 0, 33, off)) off = 0;
+        q.ga[p] = base + off + 4 * g;
+    }
+#pragma unroll
+    for (int i = 0; i < kRrQa; ++i) {
+        q.n[i] = make_float2(1.0f, 1.0f);
+        q.c[i] = make_float2(-100.0f, -100.0f);
+        q.u[i] = make_float2(1.0f, 1.0f);
+    }
+#pragma unroll
+    for (int r = 0; r < NPL; ++r) { q.Gp[r] = 0.0f; q.k[r] = 1.0f; q.kg[r] = 0.0f; }
+    rr_syncwarp();
+
+    const float rtol = (float)a.rtol, atol = (float)a.atol;
+    const float ss_tol = (float)a.ss_tol;
+    const float t_end = (float)a.t_end;
+    const float invN = 1.0f / (float)N;
+    const long long total = a.n_sets * (long long)a.n_ics;
+
+    long long my_set = 0;
+    int my_ic = 0;
+    bool working = false, exhausted = false;
+    float t = 0.0f, h = 0.0f;
+    int steps = 0, gidx = 0;
+    bool need_k1 = false, rejected = false;
+    float y[NPL], k1[NPL], k2[NPL], k3[NPL], k4[NPL], k5[NPL], k6[NPL], z[NPL];
+#pragma unroll
+    for (int r = 0; r < NPL; ++r) y[r] = k1[r] = k2[r] = k3[r] = k4[r] = k5[r] = k6[r] = z[r] = 0.0f;
+
+    auto write_series = [&](int gi) {
+        double *dst = a.series + ((my_set * a.n_ics + my_ic) * (long long)a.n_t + gi) * N;
+#pragma unroll
+        for (int r = 0; r < NPL; ++r) {
+            const int node = a.grp.row_node[r * L + j];
+            if (node >= 0) dst[node] = (double)y[r];
+        }
+    };
+
+    // item it = set * n_ics + ic -> this lane's records, rows and state
+    auto start = [&](long long it) {
+        if (!GRINS_OK_IDX(it >= 0 && it < total, 35, it)) it = 0;
+        my_set = it / a.n_ics;
+        my_ic = (int)(it - my_set * a.n_ics);
+        const unsigned char *blk = a.params + my_set * a.L.stride;
+        const double *Gd = reinterpret_cast<const double *>(blk + a.L.off_G);
+        const double *kdd = reinterpret_cast<const double *>(blk + a.L.off_k);
+        const double *ld = reinterpret_cast<const double *>(blk + a.L.off_lam);
+        const double *u0 = a.ic_unit + (long long)my_ic * N;
+        rr_load_rows<0, NPL, L>(q, a, blk, j);
+#pragma unroll
+        for (int r = 0; r < NPL; ++r) {
+            const int node = a.grp.row_node[r * L + j];
+            q.Gp[r] = 0.0f; q.k[r] = 1.0f; q.kg[r] = 0.0f; y[r] = 0.0f;
+            if (node >= 0) {
+                const double G = Gd[node], k = kdd[node];
+                double Gp = G;
+#pragma unroll 1
+                for (int c = a.topo.off[node]; c < a.topo.off[node + 1]; ++c)
+                    if (a.topo.sign[c] < 0) Gp *= ld[a.topo.edge[c]];
+                q.Gp[r] = (float)Gp;
+                q.k[r] = (float)k;
+                q.kg[r] = (float)(k / G);
+                y[r] = __fdividef((float)u0[node] * (float)G, (float)k);
+            }
+        }
+        t = (float)a.t0;
+        steps = 0;
+        gidx = 0;
+        need_k1 = true;
+        rejected = false;
+        working = true;
+#pragma unroll 1
+        while (gidx < a.n_t && a.t_grid[gidx] <= a.t0) { write_series(gidx); ++gidx; }
+    };
+
+    // idle groups take the next solves; one counter update per warp
+    auto fetch = [&]() {
+        const bool want = !working && !exhausted;
+        const unsigned m = __ballot_sync(FULL, want && j == 0);   // bit g: group g
+        if (m == 0) return;
+        unsigned long long b0 = 0;
+        if (lane == 0) b0 = atomicAdd(a.queue, (unsigned long long)__popc(m));
+        b0 = __shfl_sync(FULL, b0, 0);
+        if (want) {
+            const long long it = (long long)b0 + __popc(m & ((1u << g) - 1u));
+            if (it < total) start(it);
+            else exhausted = true;
+        }
+    };
+
+    auto residual = [&](const float (&v)[NPL]) -> float {
+        float r = 0.0f;
+#pragma unroll
+        for (int i = 0; i < NPL; ++i) r = fmaxf(r, fabsf(v[i]) * q.kg[i]);
+        return grp_max(r, L);
+    };
+
+    fetch();
+
+#pragma unroll 1
+    for (;;) {
+        if (!__any_sync(FULL, working)) break;
+        bool done = false;
+        uint8_t st_code = GRINS_SS_TEND;
+
+        // first derivative and starting step of freshly started solves
+        // (only when some group has one); idle and finished groups compute on
+        // scratch values throughout and only working groups act
+        if (__any_sync(FULL, need_k1)) {
+            rr_syncwarp();                        // buffer 1 was read by the last stage
+#pragma unroll
+            for (int r = 0; r < NPL; ++r) z[r] = y[r];
+            rr_rhs<1>(q, z, own);
+            float d0 = 0.0f, d1 = 0.0f;
+            bool fin = true;
+#pragma unroll
+            for (int r = 0; r < NPL; ++r) {
+                fin = fin && isfinite(z[r]);
+                const float isc = __fdividef(1.0f, atol + rtol * fabsf(y[r]));
+                d0 += (y[r] * isc) * (y[r] * isc);
+                d1 += (z[r] * isc) * (z[r] * isc);
+            }
+            d0 = sqrtf(grp_sum(d0, L) * invN);
+            d1 = sqrtf(grp_sum(d1, L) * invN);
+            fin = grp_all(fin, L);
+            const float res = residual(z);
+            if (need_k1) {
+                need_k1 = false;
+#pragma unroll
+                for (int r = 0; r < NPL; ++r) k1[r] = z[r];
+                h = (d0 < 1e-5f || d1 < 1e-5f) ? 1e-6f : 0.01f * d0 / d1;
+                h = fminf(h, (float)(a.t_end - a.t0));
+                if (!fin) { done = true; st_code = GRINS_SS_NONFINITE; }
+                else if (res < ss_tol) { done = true; st_code = GRINS_SS_CONVERGED; }
+            }
+        }
+
+        float t_stop = t_end;
+        bool to_grid = false, clipped = false;
+        if (gidx < a.n_t && (float)a.t_grid[gidx] < t_stop) { t_stop = (float)a.t_grid[gidx]; to_grid = true; }
+        float hh = h;
+        if (t + hh >= t_stop) { hh = t_stop - t; clipped = true; }
+
+#pragma unroll
+        for (int r = 0; r < NPL; ++r) z[r] = y[r] + hh * ((float)dp::a21 * k1[r]);
+        rr_rhs<0>(q, z, own);
+#pragma unroll
+        for (int r = 0; r < NPL; ++r) {
+            k2[r] = z[r];
+            z[r] = y[r] + hh * ((float)dp::a31 * k1[r] + (float)dp::a32 * k2[r]);
+        }
+        rr_rhs<1>(q, z, own);
+#pragma unroll
+        for (int r = 0; r < NPL; ++r) {
+            k3[r] = z[r];
+            z[r] = y[r] + hh * ((float)dp::a41 * k1[r] + (float)dp::a42 * k2[r] + (float)dp::a43 * k3[r]);
+        }
+        rr_rhs<0>(q, z, own);
+#pragma unroll
+        for (int r = 0; r < NPL; ++r) {
+            k4[r] = z[r];
+            z[r] = y[r] + hh * ((float)dp::a51 * k1[r] + (float)dp::a52 * k2[r] + (float)dp::a53 * k3[r] +
+                                (float)dp::a54 * k4[r]);
+        }
+        rr_rhs<1>(q, z, own);
+#pragma unroll
+        for (int r = 0; r < NPL; ++r) {
+            k5[r] = z[r];
+            z[r] = y[r] + hh * ((float)dp::a61 * k1[r] + (float)dp::a62 * k2[r] + (float)dp::a63 * k3[r] +
+                                (float)dp::a64 * k4[r] + (float)dp::a65 * k5[r]);
+        }
+        rr_rhs<0>(q, z, own);
+#pragma unroll
+        for (int r = 0; r < NPL; ++r) {
+            k6[r] = z[r];
+            // fifth-order solution in k2 (no later stage reads k2)
+            k2[r] = y[r] + hh * ((float)dp::b1 * k1[r] + (float)dp::b3 * k3[r] + (float)dp::b4 * k4[r] +
+                                 (float)dp::b5 * k5[r] + (float)dp::b6 * k6[r]);
+            z[r] = k2[r];
+        }
+        rr_rhs<1>(q, z, own);                     // z = k7
+
+        float en = 0.0f;
+        bool finite = true;
+#pragma unroll
+        for (int r = 0; r < NPL; ++r) {
+            const float err = hh * ((float)dp::e1 * k1[r] + (float)dp::e3 * k3[r] + (float)dp::e4 * k4[r] +
+                                    (float)dp::e5 * k5[r] + (float)dp::e6 * k6[r] + (float)dp::e7 * z[r]);
+            const float sc = atol + rtol * fmaxf(fabsf(y[r]), fabsf(k2[r]));
+            const float qq = div_approx(err, sc);
+            en += qq * qq;
+            finite = finite && isfinite(z[r]) && isfinite(k2[r]);
+        }
+        en = grp_sum(en, L) * invN;               // squared RMS error norm
+        finite = grp_all(finite, L);
+        const float res = residual(z);
+
+        if (working && !done) {
+            ++steps;
+            if (!finite || !isfinite(en)) {
+                done = true; st_code = GRINS_SS_NONFINITE;
+            } else if (en < 1.0f) {
+                const float t_new = clipped ? t_stop : t + hh;
+                if (!(t_new > t)) { done = true; st_code = GRINS_SS_NONFINITE; }
+                t = t_new;
+#pragma unroll
+                for (int r = 0; r < NPL; ++r) { y[r] = k2[r]; k1[r] = z[r]; }
+                if (clipped && to_grid) {
+#pragma unroll 1
+                    while (gidx < a.n_t && (float)a.t_grid[gidx] <= t) { write_series(gidx); ++gidx; }
+                }
+                // controller 0.9 err^(-1/5), err = sqrt(en)
+                float fac = en == 0.0f ? 10.0f : 0.9f * ex2_approx(-0.1f * lg2_approx(en));
+                fac = fminf(fac, 10.0f);
+                if (rejected) fac = fminf(fac, 1.0f);
+                h = hh * fac;
+                rejected = false;
+                if (!done) {
+                    if (res < ss_tol) { done = true; st_code = GRINS_SS_CONVERGED; }
+                    else if (t >= t_end) { done = true; st_code = GRINS_SS_TEND; }
+                }
+            } else {
+                h = hh * fmaxf(0.9f * ex2_approx(-0.1f * lg2_approx(en)), 0.2f);
+                rejected = true;
+            }
+            if (!done && steps >= a.max_steps) { done = true; st_code = GRINS_SS_MAXSTEPS; }
+        }
+
+        if (__any_sync(FULL, done)) {
+            if (done) {
+                long long idx = my_set * a.n_ics + my_ic;
+                if (!GRINS_OK_IDX(idx >= 0 && idx < total, 35, idx)) idx = 0;
+                double *dst = a.states + idx * N;
+#pragma unroll
+                for (int r = 0; r < NPL; ++r) {
+                    const int node = a.grp.row_node[r * L + j];
+                    if (node >= 0) dst[node] = (double)y[r];
+                }
+                if (j == 0) {
+                    a.status[idx] = st_code;
+                    if (a.t_final) a.t_final[idx] = (double)t;
+                    if (a.n_steps) a.n_steps[idx] = steps;
+                }
+#pragma unroll 1
+                while (gidx < a.n_t) { write_series(gidx); ++gidx; }
+                working = false;
+            }
+            fetch();
+        }
+    }
+}
+
+}  // namespace grins

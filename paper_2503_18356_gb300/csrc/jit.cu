@@ -3,12 +3,16 @@
 // The lane-group kernel (integrate_grp.cuh) reads its row layout (node rows
 // per lane, positions per row) from the launch arguments, so every row costs
 // a loop with run-time bounds.  For a fixed network the layout is known when
-// the handle is created; this file compiles the same kernel source with
-// NVRTC for sm_103a with the layout as compile-time constants (every row one
-// straight-line block, register arrays sized to the row count), loads the
-// cubin with the CUDA runtime's library API and launches it.  Compiled
-// kernels are cached per process by their source text, so handles of the
-// same network share one compile.
+// the handle is created; this file compiles a kernel with the layout as
+// compile-time constants with NVRTC for sm_103a, loads the cubin with the
+// CUDA runtime's library API and launches it.  Two kernels can be compiled:
+//   * register records (integrate_rr.cuh, the default): every lane keeps its
+//     edge records in registers, one shared load per edge;
+//   * shared records (integrate_grp.cuh with the layout fixed): the same
+//     source as the run-time-layout kernel, used when the register records
+//     would not fit (a lane with many edge positions) or on request.
+// Compiled kernels are cached per process by their source text, so handles
+// of the same network share one compile.
 //
 // libnvrtc is opened with dlopen: a machine without it, or a failed compile,
 // leaves the run-time-layout kernel in charge (GRINS_JIT=0 forces that).
@@ -88,6 +92,8 @@ constexpr int kJitWarps = 4;
 struct JitEntry {
     bool ok = false;
     std::string why;
+    int kind = kJitShared;
+    int spill_bytes = 0;
     cudaLibrary_t lib = nullptr;
     cudaKernel_t kern = nullptr;
 };
@@ -96,7 +102,7 @@ std::mutex g_jit_mu;
 std::map<std::string, std::shared_ptr<JitEntry>> g_jit_cache;
 
 // Generated prelude + kernel wrapper for one layout.
-std::string jit_main(const GrpTopo &g, int minb)
+std::string jit_main(const GrpTopo &g, int kind, int minb)
 {
     std::string s;
     char buf[256];
@@ -104,14 +110,16 @@ std::string jit_main(const GrpTopo &g, int minb)
 #ifdef GRINS_CHECKED
     s += "#define GRINS_CHECKED 1\n";
 #endif
+    if (kind == kJitShared) {
 #ifdef GRINS_GRP_ROLL_STAGES
-    s += "#define GRINS_GRP_ROLL_STAGES 1\n";
+        s += "#define GRINS_GRP_ROLL_STAGES 1\n";
 #else
-    // unrolled stages repeat the right-hand side seven times: keep the stage
-    // loop when a lane's edge list is long (the code would outgrow the
-    // instruction cache)
-    if (g.P > 32) s += "#define GRINS_GRP_ROLL_STAGES 1\n";
+        // unrolled stages repeat the right-hand side seven times: keep the
+        // stage loop when a lane's edge list is long (the code would outgrow
+        // the instruction cache)
+        if (g.P > 32) s += "#define GRINS_GRP_ROLL_STAGES 1\n";
 #endif
+    }
     s += "#include \"common.cuh\"\nnamespace grins {\n";
     std::snprintf(buf, sizeof(buf), "constexpr int kGrpCtRows = %d;\n", g.R);
     s += buf;
@@ -122,13 +130,34 @@ std::string jit_main(const GrpTopo &g, int minb)
                       g.row_off[r], g.row_deg[r]);
         s += buf;
     }
-    s += "}\n#include \"integrate_grp.cuh\"\n";
-    std::snprintf(buf, sizeof(buf),
-                  "extern \"C\" __global__ void __launch_bounds__(%d, %d) grins_grp_ct(const grins::IntegrateArgs a)\n"
-                  "{\n    grins::grp_body<%d, %d, %d, %d>(a);\n}\n",
-                  kJitWarps * kWarp, minb, g.R, kJitWarps, g.L, g.R);
+    if (kind == kJitRegisters) {
+        s += "}\n#include \"integrate_rr.cuh\"\n";
+        std::snprintf(buf, sizeof(buf),
+                      "extern \"C\" __global__ void __launch_bounds__(%d, %d) grins_grp_ct(const grins::IntegrateArgs a)\n"
+                      "{\n    grins::rr_body<%d, %d, %d>(a);\n}\n",
+                      kJitWarps * kWarp, minb, g.R, kJitWarps, g.L);
+    } else {
+        s += "}\n#include \"integrate_grp.cuh\"\n";
+        std::snprintf(buf, sizeof(buf),
+                      "extern \"C\" __global__ void __launch_bounds__(%d, %d) grins_grp_ct(const grins::IntegrateArgs a)\n"
+                      "{\n    grins::grp_body<%d, %d, %d, %d>(a);\n}\n",
+                      kJitWarps * kWarp, minb, g.R, kJitWarps, g.L, g.R);
+    }
     s += buf;
     return s;
+}
+
+// Spill bytes reported by ptxas in a compile log ("N bytes spill stores").
+int log_spill_bytes(const std::string &log)
+{
+    int total = 0;
+    for (size_t p = log.find(" bytes spill stores"); p != std::string::npos;
+         p = log.find(" bytes spill stores", p + 1)) {
+        size_t b = p;
+        while (b > 0 && log[b - 1] >= '0' && log[b - 1] <= '9') --b;
+        if (b < p) total += std::atoi(log.substr(b, p - b).c_str());
+    }
+    return total;
 }
 
 std::shared_ptr<JitEntry> jit_compile(const std::string &src)
@@ -147,18 +176,20 @@ std::shared_ptr<JitEntry> jit_compile(const std::string &src)
     nvrtcResult r = api.create(&prog, src.c_str(), "grins_grp_ct.cu", (int)hdr_src.size(), hdr_src.data(),
                                hdr_name.data());
     if (r != NVRTC_SUCCESS) { e->why = std::string("nvrtcCreateProgram: ") + api.err(r); return e; }
-    const char *opts[] = {"--gpu-architecture=sm_103a", "--std=c++17", "-lineinfo", "-default-device"};
-    r = api.compile(prog, 4, opts);
+    const char *opts[] = {"--gpu-architecture=sm_103a", "--std=c++17", "-lineinfo", "-default-device",
+                          "--ptxas-options=-v"};
+    r = api.compile(prog, 5, opts);
+    size_t n = 0;
+    api.log_size(prog, &n);
+    std::string log(n, '\0');
+    if (n) api.log(prog, &log[0]);
     if (r != NVRTC_SUCCESS) {
-        size_t n = 0;
-        api.log_size(prog, &n);
-        std::string log(n, '\0');
-        if (n) api.log(prog, &log[0]);
         e->why = std::string("nvrtcCompileProgram: ") + api.err(r) + "\n" + log;
         api.destroy(&prog);
         return e;
     }
-    size_t n = 0;
+    e->spill_bytes = log_spill_bytes(log);
+    n = 0;
     api.cubin_size(prog, &n);
     std::vector<char> cubin(n);
     api.cubin(prog, cubin.data());
@@ -170,48 +201,88 @@ std::shared_ptr<JitEntry> jit_compile(const std::string &src)
     return e;
 }
 
+// Minimum resident blocks per SM for a kernel of this kind and layout: for
+// register records from the estimate of a lane's registers (about 4 per edge
+// position and 11 per row on top of ~40; ptxas usually fits a little more
+// than the estimate, and a spilling compile is retried with one block
+// fewer).  GRINS_JIT_MINB overrides it (a tuning knob).
+int jit_minb(const GrpTopo &g, int kind)
+{
+    const int est = 4 * g.P + 11 * g.R + 40;
+    int minb = kind == kJitRegisters ? (est <= 144 ? 4 : (est <= 176 ? 3 : 2)) : GRINS_GRP_MINB;
+    if (const char *ev = std::getenv("GRINS_JIT_MINB")) {
+        const int m = std::atoi(ev);
+        if (m >= 1 && m <= 8) minb = m;
+    }
+    return minb;
+}
+
+std::shared_ptr<JitEntry> jit_get(const GrpTopo &g, int kind, bool compile)
+{
+    int minb = jit_minb(g, kind);
+    std::lock_guard<std::mutex> lock(g_jit_mu);
+    for (;;) {
+        const std::string src = jit_main(g, kind, minb);
+        auto it = g_jit_cache.find(src);
+        if (it == g_jit_cache.end()) {
+            if (!compile) return nullptr;
+            auto e = jit_compile(src);
+            e->kind = kind;
+            it = g_jit_cache.emplace(src, e).first;
+        }
+        std::shared_ptr<JitEntry> e = it->second;
+        // a register-record kernel that spills gets another try with fewer
+        // resident blocks (more registers per thread)
+        if (e->ok && kind == kJitRegisters && e->spill_bytes > 0 && minb > 1 && !std::getenv("GRINS_JIT_MINB")) {
+            --minb;
+            continue;
+        }
+        return e;
+    }
+}
+
 }  // namespace
 
 // The compiled kernel for layout g (compiling it on first use), or null
-// with the reason in *why.
-const void *grp_jit_kernel(const GrpTopo &g, std::string *why)
+// with the reason in *why.  The pointer is an opaque handle for
+// launch_grp_jit.
+const void *grp_jit_kernel(const GrpTopo &g, int kind, std::string *why)
 {
     const char *ev = std::getenv("GRINS_JIT");
     if (ev && ev[0] == '0') { if (why) *why = "disabled by GRINS_JIT=0"; return nullptr; }
     if (g.L <= 0 || g.R <= 0 || g.R > 12) { if (why) *why = "no lane-group layout"; return nullptr; }
-    const std::string src = jit_main(g, GRINS_GRP_MINB);
-    std::shared_ptr<JitEntry> e;
-    {
-        std::lock_guard<std::mutex> lock(g_jit_mu);
-        auto it = g_jit_cache.find(src);
-        if (it == g_jit_cache.end()) it = g_jit_cache.emplace(src, jit_compile(src)).first;
-        e = it->second;
-    }
+    std::shared_ptr<JitEntry> e = jit_get(g, kind, true);
     if (!e->ok) { if (why) *why = e->why; return nullptr; }
-    return reinterpret_cast<const void *>(e->kern);
+    if (why) *why = e->kind == kJitRegisters ? "records in registers" : "records in shared memory";
+    return e.get();
 }
 
 // The compiled kernel for layout g if an earlier call compiled it; never
 // compiles or loads anything.
-const void *grp_jit_lookup(const GrpTopo &g)
+const void *grp_jit_lookup(const GrpTopo &g, int kind)
 {
     const char *ev = std::getenv("GRINS_JIT");
     if ((ev && ev[0] == '0') || g.L <= 0 || g.R <= 0 || g.R > 12) return nullptr;
-    const std::string src = jit_main(g, GRINS_GRP_MINB);
-    std::lock_guard<std::mutex> lock(g_jit_mu);
-    auto it = g_jit_cache.find(src);
-    if (it == g_jit_cache.end() || !it->second->ok) return nullptr;
-    return reinterpret_cast<const void *>(it->second->kern);
+    std::shared_ptr<JitEntry> e = jit_get(g, kind, false);
+    if (!e || !e->ok) return nullptr;
+    return e.get();
 }
 
-cudaError_t launch_grp_jit(const void *kern, const IntegrateArgs &a, cudaStream_t st, int num_sms)
+cudaError_t launch_grp_jit(const void *handle, const IntegrateArgs &a, cudaStream_t st, int num_sms)
 {
+    const JitEntry *je = static_cast<const JitEntry *>(handle);
     IntegrateArgs b = a;
-    const int ndom = grp_domains(b.grp.L);
-    GrpLayout LY{b.grp.L, b.grp.R, b.grp.P, b.slots};
-    while (kJitWarps * LY.warp_bytes() > b.smem_limit && LY.S > ndom) LY.S = (b.slots -= ndom);
-    const int smem = kJitWarps * LY.warp_bytes();
+    int smem = 0;
+    if (je->kind == kJitRegisters) {
+        smem = kJitWarps * rr_warp_bytes(b.grp.R);
+    } else {
+        const int ndom = grp_domains(b.grp.L);
+        GrpLayout LY{b.grp.L, b.grp.R, b.grp.P, b.slots};
+        while (kJitWarps * LY.warp_bytes() > b.smem_limit && LY.S > ndom) LY.S = (b.slots -= ndom);
+        smem = kJitWarps * LY.warp_bytes();
+    }
     if (smem > b.smem_limit) return cudaErrorInvalidConfiguration;
+    const void *kern = reinterpret_cast<const void *>(je->kern);
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (err != cudaSuccess) return err;
     int per_sm = 0;

@@ -3,8 +3,9 @@ CPU oracle on the same seeded inputs:
 
   * lane-group layouts with 2, 4 and 8 lanes per solve (GRINS_GRP_L), which
     change the node rows, the edge positions and the lane mapping;
-  * the kernel compiled for the network at run time (the default) and the
-    run-time-layout kernel (GRINS_JIT=0).
+  * the kernels compiled for the network at run time -- records in
+    registers (the default) and records in shared memory (GRINS_JIT_KIND)
+    -- and the run-time-layout kernel (GRINS_JIT=0).
 
 Bars as in test_gpu_parity.py: FP32 + FP64 polish relative 1e-6 (floor
 1e-6 G/k); raw FP32 1e-3 on the G/k scale.
@@ -44,10 +45,13 @@ def test_lane_group_layouts_match_oracle(L, monkeypatch):
     h.close()
 
 
-@pytest.mark.parametrize("jit", ["1", "0"])
+@pytest.mark.parametrize("jit", ["rr", "grp", "0"])
 @pytest.mark.parametrize("wl", ["ts", "net5", "net22"])
 def test_compiled_and_runtime_layout_kernels(jit, wl, monkeypatch):
-    monkeypatch.setenv("GRINS_JIT", jit)
+    if jit == "0":
+        monkeypatch.setenv("GRINS_JIT", "0")
+    else:
+        monkeypatch.setenv("GRINS_JIT_KIND", jit)
     w = {"ts": W.ts_workload, "net5": W.net5_workload, "net22": W.net22_workload}[wl]()
     topo = w["topology"]
     h = PT.gpu_handle(topo)
@@ -55,8 +59,10 @@ def test_compiled_and_runtime_layout_kernels(jit, wl, monkeypatch):
     o = O.run_sets_parallel(O.Network(*topo.edges()), p, icn, threads=PT.THREADS)
     _check(h, params, ic, p, o)
     info = h.integrator()
-    if jit == "1":
-        assert "compiled for this network at run time" in info, info
-    else:
+    if jit == "0":
         assert "run-time layout" in info, info
+    else:
+        assert "compiled for this network at run time" in info, info
+        kind = "registers" if jit == "rr" else "shared memory"
+        assert "records in " + kind in info, info
     h.close()
