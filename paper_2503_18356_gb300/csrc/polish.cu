@@ -18,7 +18,22 @@
 // moves a G/k-normalised coordinate by more than max_move, whose Jacobian is
 // singular, or that does not reach tol within `iters` steps keeps its
 // unpolished state and gets status GRINS_SS_POLISH_FAIL.
-// One warp per solve: lanes over rows (targets).
+//
+// FP64 runs at a small fraction of the FP32 rate on this GPU (a warp's FP64
+// instruction occupies the SM's FP64 pipe for about 16 cycles), so the
+// residual is arranged to issue few FP64 warp instructions, each with most
+// lanes busy.  One warp per solve:
+//   * once per solve, lanes over edges (CSR order) tabulate T^n, lambda and
+//     the edge's source, exponent and sign in shared memory;
+//   * per residual, lanes over nodes tabulate x^1 .. x^6, lanes over edges
+//     form each factor's numerator lambda x^n + T^n and denominator
+//     (x^n + T^n) c (c = lambda for activating edges, 1 otherwise), and lanes
+//     over rows (targets) multiply their factors and form f_i;
+//   * the Jacobian is filled edge by edge in FP32; the LU runs in shared
+//     memory, the substitutions with the right-hand side in registers (one
+//     row per lane, values passed by shuffles).
+#include <climits>
+
 #include "integrate.cuh"
 
 namespace grins {
@@ -26,13 +41,7 @@ namespace grins {
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
-
-__device__ __forceinline__ double warp_max(double v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(FULL, v, o));
-    return v;
-}
+constexpr int kPow = 6;          // x^1 .. x^6 tabulated per node
 
 __device__ __forceinline__ float warp_maxf(float v)
 {
@@ -40,6 +49,10 @@ __device__ __forceinline__ float warp_maxf(float v)
     for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(FULL, v, o));
     return v;
 }
+
+// NaN -> +inf, so that the warp maxima of rho and of the step (fmaxf drops
+// NaN operands) see a non-finite residual or step
+__device__ __forceinline__ float nan_to_inf(float v) { return v == v ? v : __int_as_float(0x7f800000); }
 
 // x^n for a small non-negative integer n, by repeated squaring
 template <typename Real>
@@ -53,21 +66,44 @@ __device__ __forceinline__ Real ipow(Real x, int n)
     return p;
 }
 
+// Bytes of the per-warp edge tables for E edges: FP64 T^n, lambda, factor
+// numerator and denominator; int (src << 9 | act << 8 | n) and target row;
+// FP32 (T, lambda).
+__host__ __device__ constexpr long long polish_edge_bytes(int E)
+{
+    return (long long)(E > 0 ? E : 1) * (4 * 8 + 2 * 4 + 8);
+}
+
 template <int NMAX, int WARPS>
 __global__ void __launch_bounds__(WARPS * kWarp) polish_kernel(const PolishArgs a)
 {
+    constexpr int RPL = NMAX > kWarp ? NMAX / kWarp : 1;   // rows per lane
     __shared__ float sJ[WARPS][NMAX][NMAX + 1];   // FP32 Jacobian, then its LU factors
     __shared__ double sx[WARPS][NMAX];            // FP64 state
-    __shared__ float sb[WARPS][NMAX];             // FP32 right-hand side, then the step
+    __shared__ double sxp[WARPS][kPow][NMAX];     // x^1 .. x^6 per node
+    __shared__ float sgp[WARPS][NMAX];            // G_i P_i at the starting state
     __shared__ int spiv[WARPS][NMAX];             // pivot row of each elimination step
+    __shared__ int sperm[WARPS][NMAX];            // row permutation of the LU
+    extern __shared__ __align__(16) unsigned char dsm[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int N = a.topo.N;
+    const int N = a.topo.N, E = a.topo.E;
     unsigned long long *grins_chk = a.check;
     (void)grins_chk;
     float (*J)[NMAX + 1] = sJ[w];
     double *x = sx[w];
-    float *b = sb[w];
+    double (*xp)[NMAX] = sxp[w];
+    float *gp = sgp[w];
     int *piv = spiv[w];
+    int *perm = sperm[w];
+    const int Eb = E > 0 ? E : 1;
+    unsigned char *eb = dsm + (long long)w * polish_edge_bytes(E);
+    double *tn_e = reinterpret_cast<double *>(eb);
+    double *lam_e = tn_e + Eb;
+    double *num_e = lam_e + Eb;
+    double *den_e = num_e + Eb;
+    int *code_e = reinterpret_cast<int *>(den_e + Eb);
+    int *row_e = code_e + Eb;
+    float2 *tl_e = reinterpret_cast<float2 *>(row_e + Eb);
 
     for (long long idx = (long long)blockIdx.x * WARPS + w; idx < a.n_solves;
          idx += (long long)gridDim.x * WARPS) {
@@ -84,69 +120,123 @@ __global__ void __launch_bounds__(WARPS * kWarp) polish_kernel(const PolishArgs 
         const uint8_t *nn = blk + a.L.off_n;
         double *state = a.states + idx * N;
         for (int i = lane; i < N; i += kWarp) x[i] = state[i];
+
+        // edge tables (lanes over CSR positions) and row constants
+        for (int c = lane; c < E; c += kWarp) {
+            int e = a.topo.edge[c], s = a.topo.src[c];
+            if (!GRINS_OK_IDX(e >= 0 && e < E && s >= 0 && s < N && N <= NMAX, 21, c)) e = s = 0;
+            const int n = nn[e];
+            const double Te = T[e], l = lam[e];
+            tn_e[c] = ipow(Te, n);
+            lam_e[c] = l;
+            code_e[c] = (s << 9) | (a.topo.sign[c] > 0 ? 256 : 0) | n;
+            tl_e[c] = make_float2((float)Te, (float)l);
+        }
+        double Gr[RPL], Kr[RPL];
+        float kg[RPL];
+#pragma unroll
+        for (int k = 0; k < RPL; ++k) {
+            const int i = lane + kWarp * k;
+            Gr[k] = 1.0; Kr[k] = 0.0; kg[k] = 0.0f;
+            if (i < N) {
+                Gr[k] = G[i]; Kr[k] = K[i];
+                kg[k] = (float)(Kr[k] / Gr[k]);
+                for (int c = a.topo.off[i]; c < a.topo.off[i + 1]; ++c) row_e[c] = i;
+            }
+        }
         __syncwarp();
 
-        // f_i in FP64 for the rows of this lane -> b (FP32, negated); returns
+        // f in FP64 -> b = -f (FP32, one entry per row of this lane); returns
         // rho.  Each factor of Eq. 2 is written without divisions,
         //     F_e = (lam x^n + T^n) / ((x^n + T^n) c),  c = lam (activating), 1,
         // (numerator and denominator of (lam p + 1) / ((1 + p) c) times T^n),
-        // and the products are divided once per eight factors (x^n, T^n stay
-        // below ~1e24, so eight factors stay finite).  With `jac` row i of
-        // the Jacobian is filled in as well.
-        auto residual = [&](bool jac) -> double {
-            double rloc = 0.0;
+        // and a row's products are divided once per eight factors (x^n, T^n
+        // stay below ~1e24, so eight factors stay finite).  With `jac` the
+        // FP32 Jacobian is filled in as well.
+        float b[RPL];
+        auto residual = [&](bool jac) -> float {
             for (int i = lane; i < N; i += kWarp) {
-                if (jac)
-                    for (int j = 0; j < N; ++j) J[i][j] = 0.0f;
-                double P = 1.0, num = 1.0, den = 1.0;
-                int cnt = 0;
-                for (int c = a.topo.off[i]; c < a.topo.off[i + 1]; ++c) {
-                    int e = a.topo.edge[c], s = a.topo.src[c];
-                    if (!GRINS_OK_IDX(e >= 0 && e < a.topo.E && s >= 0 && s < N && N <= NMAX, 21, c)) e = s = 0;
-                    const bool act = a.topo.sign[c] > 0;
-                    const int n = nn[e];
-                    const double l = lam[e], Te = T[e];
-                    const double xs = fmax(x[s], 0.0);
-                    const double xn = ipow(xs, n), tn = ipow(Te, n);
-                    num *= fma(l, xn, tn);
-                    den *= act ? (xn + tn) * l : xn + tn;
-                    if (++cnt == 8) { P *= num / den; num = den = 1.0; cnt = 0; }
-                    if (jac) {
-                        // d log F / dx = n p (lam - 1) / (x (lam p + 1)(1 + p)),
-                        // p = (x/T)^n, in FP32 (the Jacobian only steers the
-                        // iteration); at x = 0 only n = 1 leaves a slope
-                        const float lf = (float)l, xf = (float)xs;
-                        float dl;
-                        if (xf > 0.0f) {
-                            const float pf = (float)fmin(xn / tn, 1e30);
-                            dl = (float)n * (lf - 1.0f) / xf * (pf / (1.0f + pf)) / fmaf(lf, pf, 1.0f);
-                        } else {
-                            dl = n == 1 ? (lf - 1.0f) / (float)Te : 0.0f;
-                        }
-                        J[i][s] += dl;   // scaled by G_i P_i below
-                    }
-                }
-                P *= num / den;
-                const double f = G[i] * P - K[i] * x[i];
-                b[i] = (float)(-f);
-                if (jac) {
-                    const float gp = (float)(G[i] * P);
-                    for (int j = 0; j < N; ++j) J[i][j] *= gp;
-                    J[i][i] -= (float)K[i];
-                }
-                rloc = fmax(rloc, fabs(f) * (K[i] / G[i]));
+                const double v = fmax(x[i], 0.0);
+                const double v2 = v * v, v4 = v2 * v2;
+                xp[0][i] = v; xp[1][i] = v2; xp[2][i] = v2 * v;
+                xp[3][i] = v4; xp[4][i] = v4 * v; xp[5][i] = v2 * v4;
             }
-            return warp_max(rloc);
+            __syncwarp();
+            for (int c = lane; c < E; c += kWarp) {
+                const int code = code_e[c], s = code >> 9, n = code & 255;
+                const double xn = (n >= 1 && n <= kPow) ? xp[n - 1][s] : ipow(fmax(x[s], 0.0), n);
+                const double tn = tn_e[c], l = lam_e[c];
+                num_e[c] = fma(l, xn, tn);
+                den_e[c] = (xn + tn) * ((code & 256) ? l : 1.0);
+            }
+            __syncwarp();
+            float rloc = 0.0f;
+#pragma unroll
+            for (int k = 0; k < RPL; ++k) {
+                const int i = lane + kWarp * k;
+                b[k] = 0.0f;
+                if (i < N) {
+                    double P = 1.0, nu = 1.0, de = 1.0;
+                    int cnt = 0;
+                    for (int c = a.topo.off[i]; c < a.topo.off[i + 1]; ++c) {
+                        nu *= num_e[c];
+                        de *= den_e[c];
+                        if (++cnt == 8) { P *= nu / de; nu = de = 1.0; cnt = 0; }
+                    }
+                    P *= nu / de;
+                    const double gpi = Gr[k] * P;
+                    const double f = gpi - Kr[k] * x[i];
+                    b[k] = (float)(-f);
+                    if (jac) gp[i] = (float)gpi;
+                    rloc = fmaxf(rloc, nan_to_inf(fabsf(b[k]) * kg[k]));
+                }
+            }
+            if (jac) {
+                // J_is = G_i P_i dlog F_e / dx_s for the edge e = (s -> i)
+                // (one edge per pair), then J_ii -= k_i.  dlog F / dx =
+                // n p (lam - 1) / (x (lam p + 1)(1 + p)), p = (x/T)^n, in
+                // FP32 (the Jacobian only steers the iteration); at x = 0
+                // only n = 1 leaves a slope.
+#pragma unroll
+                for (int k = 0; k < RPL; ++k) {
+                    const int i = lane + kWarp * k;
+                    if (i < N)
+                        for (int j = 0; j < N; ++j) J[i][j] = 0.0f;
+                }
+                __syncwarp();
+                for (int c = lane; c < E; c += kWarp) {
+                    const int code = code_e[c], s = code >> 9, n = code & 255, i = row_e[c];
+                    const float2 tl = tl_e[c];
+                    const float xf = (float)fmax(x[s], 0.0);
+                    float dl;
+                    if (xf > 0.0f) {
+                        const float pf = fminf(ipow(xf * div_approx(1.0f, tl.x), n), 1e30f);
+                        dl = (float)n * (tl.y - 1.0f) * pf * div_approx(1.0f, xf * (1.0f + pf)) *
+                             div_approx(1.0f, fmaf(tl.y, pf, 1.0f));
+                    } else {
+                        dl = n == 1 ? (tl.y - 1.0f) * div_approx(1.0f, tl.x) : 0.0f;
+                    }
+                    J[i][s] = gp[i] * dl;
+                }
+                __syncwarp();
+#pragma unroll
+                for (int k = 0; k < RPL; ++k) {
+                    const int i = lane + kWarp * k;
+                    if (i < N) J[i][i] -= (float)Kr[k];
+                }
+            }
+            return warp_maxf(rloc);
         };
 
         bool ok = false, singular = false;
-        double last_move = 0.0;
-        double rho = residual(true);
+        float last_move = 0.0f;
+        float rho = residual(true);
         __syncwarp();
-        if (rho < a.tol) ok = true;
+        if ((double)rho < a.tol) ok = true;
 
         // LU of the FP32 Jacobian with partial pivoting; multipliers kept
-        // below the diagonal, row swaps recorded in piv
+        // below the diagonal, reciprocals of the pivots on it, and the row
+        // swaps composed into perm ((P b)_r = b_perm[r])
         if (!ok) {
             for (int c = 0; c < N; ++c) {
                 float best = -1.0f;
@@ -155,13 +245,11 @@ __global__ void __launch_bounds__(WARPS * kWarp) polish_kernel(const PolishArgs 
                     const float v = fabsf(J[r][c]);
                     if (v > best) { best = v; pr = r; }
                 }
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    const float ob = __shfl_xor_sync(FULL, best, o);
-                    const int op = __shfl_xor_sync(FULL, pr, o);
-                    if (ob > best || (ob == best && op < pr)) { best = ob; pr = op; }
-                }
-                if (!(best > 0.0f)) { singular = true; break; }
+                // largest magnitude over the warp, lowest row among equals
+                const unsigned key = best >= 0.0f ? __float_as_uint(best) + 1u : 0u;
+                const unsigned mx = __reduce_max_sync(FULL, key);
+                pr = __reduce_min_sync(FULL, key == mx ? pr : INT_MAX);
+                if (mx <= 1u) { singular = true; break; }     // no candidate, or only zeros
                 if (lane == 0) piv[c] = pr;
                 if (pr != c) {
                     for (int j = lane; j < N; j += kWarp) {
@@ -177,42 +265,86 @@ __global__ void __launch_bounds__(WARPS * kWarp) polish_kernel(const PolishArgs 
                 }
                 __syncwarp();
             }
+            if (!singular) {
+                for (int c = lane; c < N; c += kWarp) J[c][c] = 1.0f / J[c][c];
+                if (lane == 0) {
+                    // the swaps in order applied to the identity
+                    for (int c = 0; c < N; ++c) perm[c] = c;
+                    for (int c = 0; c < N; ++c) {
+                        const int p = piv[c];
+                        const int t = perm[c]; perm[c] = perm[p]; perm[p] = t;
+                    }
+                }
+                __syncwarp();
+            }
         }
+
+        // b of row r (warp-uniform r) from the lane holding it
+        auto row_value = [&](int r) -> float {
+            float v = b[0];
+#pragma unroll
+            for (int k = 1; k < RPL; ++k)
+                if (r >= kWarp * k) v = b[k];
+            return __shfl_sync(FULL, v, r & (kWarp - 1));
+        };
 
         // chord iterations: solve J0 d = -f(x) in FP32, x += d in FP64
         for (int it = 0; !ok && !singular && it < a.iters; ++it) {
-            if (lane == 0)
-                for (int c = 0; c < N; ++c) {
-                    const int pr = piv[c];
-                    if (pr != c) { const float t = b[c]; b[c] = b[pr]; b[pr] = t; }
+            // b <- P b
+            float pb[RPL];
+#pragma unroll
+            for (int k = 0; k < RPL; ++k) {
+                const int i = lane + kWarp * k;
+                const int p = i < N ? perm[i] : 0;
+                float v = 0.0f;
+#pragma unroll
+                for (int q = 0; q < RPL; ++q) {
+                    const float t = __shfl_sync(FULL, b[q], p & (kWarp - 1));
+                    if (p >> 5 == q) v = t;
                 }
-            __syncwarp();
-            for (int c = 0; c < N; ++c) {                 // forward (unit lower)
-                const float bc = b[c];
-                for (int r = c + 1 + lane; r < N; r += kWarp) b[r] = fmaf(-J[r][c], bc, b[r]);
-                __syncwarp();
+                pb[k] = v;
             }
-            for (int c = N - 1; c >= 0; --c) {            // backward (upper)
-                if (lane == 0) b[c] = b[c] / J[c][c];
-                __syncwarp();
-                const float bc = b[c];
-                for (int r = lane; r < c; r += kWarp) b[r] = fmaf(-J[r][c], bc, b[r]);
-                __syncwarp();
+#pragma unroll
+            for (int k = 0; k < RPL; ++k) b[k] = pb[k];
+            for (int c = 0; c < N; ++c) {                 // forward (unit lower)
+                const float bc = row_value(c);
+#pragma unroll
+                for (int k = 0; k < RPL; ++k) {
+                    const int i = lane + kWarp * k;
+                    if (i > c && i < N) b[k] = fmaf(-J[i][c], bc, b[k]);
+                }
+            }
+            for (int c = N - 1; c >= 0; --c) {            // backward (upper, reciprocal diagonal)
+#pragma unroll
+                for (int k = 0; k < RPL; ++k)
+                    if (lane + kWarp * k == c) b[k] *= J[c][c];
+                const float bc = row_value(c);
+#pragma unroll
+                for (int k = 0; k < RPL; ++k) {
+                    const int i = lane + kWarp * k;
+                    if (i < c) b[k] = fmaf(-J[i][c], bc, b[k]);
+                }
             }
             float mv = 0.0f;
-            for (int i = lane; i < N; i += kWarp) mv = fmaxf(mv, fabsf(b[i]) * (float)(K[i] / G[i]));
+#pragma unroll
+            for (int k = 0; k < RPL; ++k)
+                if (lane + kWarp * k < N) mv = fmaxf(mv, nan_to_inf(fabsf(b[k]) * kg[k]));
             mv = warp_maxf(mv);
             if (!(mv <= (float)a.max_move)) break;
-            for (int i = lane; i < N; i += kWarp) x[i] += (double)b[i];
+#pragma unroll
+            for (int k = 0; k < RPL; ++k) {
+                const int i = lane + kWarp * k;
+                if (i < N) x[i] += (double)b[k];
+            }
             last_move = mv;
             __syncwarp();
             rho = residual(false);
             __syncwarp();
-            if (rho < a.tol) ok = true;
+            if ((double)rho < a.tol) ok = true;
         }
         if (ok) {
             for (int i = lane; i < N; i += kWarp) state[i] = x[i];
-            if (lane == 0 && a.err_est) a.err_est[idx] = (float)(last_move > 0.0 ? last_move : rho);
+            if (lane == 0 && a.err_est) a.err_est[idx] = last_move > 0.0f ? last_move : rho;
         } else {
             if (lane == 0) {
                 a.status[idx] = GRINS_SS_POLISH_FAIL;
@@ -227,15 +359,26 @@ template <int NMAX, int WARPS>
 cudaError_t launch_bucket(const PolishArgs &a, cudaStream_t st, int num_sms)
 {
     auto kern = polish_kernel<NMAX, WARPS>;
+    const long long dyn = WARPS * polish_edge_bytes(a.topo.E);
+    int dev = 0, optin = 0;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err == cudaSuccess) err = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (err != cudaSuccess) return err;
+    cudaFuncAttributes fa;
+    err = cudaFuncGetAttributes(&fa, kern);
+    if (err != cudaSuccess) return err;
+    if (dyn + (long long)fa.sharedSizeBytes > optin) return cudaErrorInvalidConfiguration;
+    err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (err != cudaSuccess) return err;
     int per_sm = 0;
-    cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WARPS * kWarp, 0);
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WARPS * kWarp, (size_t)dyn);
     if (err != cudaSuccess) return err;
     if (per_sm < 1) per_sm = 1;
     long long blocks = (long long)num_sms * per_sm;
     const long long need = (a.n_solves + WARPS - 1) / WARPS;
     if (blocks > need) blocks = need;
     if (blocks < 1) blocks = 1;
-    kern<<<(unsigned)blocks, WARPS * kWarp, 0, st>>>(a);
+    kern<<<(unsigned)blocks, WARPS * kWarp, (size_t)dyn, st>>>(a);
     return cudaGetLastError();
 }
 
