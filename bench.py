@@ -30,10 +30,10 @@ N_SETS = 100_000
 N_ICS = 10
 TOL = dict(rtol=1e-6, atol=1e-9, t_end=200.0, ss_tol=1e-6)
 # DRAM bytes (read + write) of one integrator launch per solve, from an ncu
-# capture of the same kernel on a 20,000-set launch of this workload;
-# traffic grows with the solves per launch.  None while no capture of the
-# current kernel exists.
-INTEGRATOR_DRAM_BYTES_PER_SOLVE = None
+# capture of the same kernel on a 20,000-set launch of this workload
+# (35.28 MB read + 1.16 MB written for 200,000 solves); traffic grows with
+# the solves per launch.  None while no capture of the current kernel exists.
+INTEGRATOR_DRAM_BYTES_PER_SOLVE = 36.44e6 / 200_000
 
 
 def parse():
@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sets", type=int, default=800, help="sets of the oracle sample")
     ap.add_argument("--fp64-sets", type=int, default=5000, help="sets of the FP64 GPU solver sample")
+    ap.add_argument("--serve-seconds", type=float, default=6.0,
+                    help="length of the Poisson request stream of the serving measurement (0: skip)")
+    ap.add_argument("--serve-rate", type=float, default=20.0, help="requests per second of that stream")
     return ap.parse_args()
 
 
@@ -159,6 +162,62 @@ def run_reference(args):
                                   sample="%d sets x %d ICs per step" % (args.cpu_sets, N_ICS)),
                 e2e=dict(value=value, unit="solves/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line))
+
+
+# ------------------------------------------------------------------ serving
+def serving_measurement(dev, seconds, rate):
+    """Request server under the Poisson stream of ensemble requests (networks
+    of 2-60 nodes, density 0.05-0.3, 1k-50k sets x 1-20 ICs, FP32 + FP64
+    polish + dedupe): requests are submitted at their arrival times, a second
+    thread waits for each and releases it.  Latency = submission -> results
+    ready on the device (the server's own clock); solves/s = all solves of the
+    stream / wall time from the first arrival to the last completion."""
+    import threading as th
+    import numpy as np
+    from paper_2503_18356_gb300 import api, workloads as W
+
+    stream = W.serving_stream(rate_hz=rate, duration_s=seconds)
+    nets = [api.Racipe.from_topology(r["topology"], device=dev) for r in stream]
+    sv = api.Server(max_inflight=16, hbm_budget_bytes=64 << 30, device=dev)
+    w = W.net5_workload()                          # warm-up request (not timed)
+    wnet = api.Racipe.from_topology(w["topology"], device=dev)
+    rid = sv.submit(wnet, 1, 100, 2)
+    sv.wait(rid)
+    sv.release(rid)
+    ids = [None] * len(stream)
+    infos = [None] * len(stream)
+    ready = th.Semaphore(0)
+
+    def releaser():
+        for k in range(len(stream)):
+            ready.acquire()
+            infos[k] = sv.wait(ids[k])
+            sv.release(ids[k])
+
+    t = th.Thread(target=releaser)
+    t.start()
+    solves = 0
+    start = time.perf_counter()
+    for k, r in enumerate(stream):
+        dt = r["arrival_s"] - (time.perf_counter() - start)
+        if dt > 0:
+            time.sleep(dt)
+        ids[k] = sv.submit(nets[k], r["param_seed"], r["n_sets"], r["n_ics"])
+        solves += r["n_sets"] * r["n_ics"]
+        ready.release()
+    t.join()
+    wall = time.perf_counter() - start
+    sv.close()
+    lat = np.array([x["latency_s"] for x in infos]) * 1e3
+    que = np.array([x["queued_s"] for x in infos]) * 1e3
+    return dict(requests=len(stream), rate_hz=rate, stream_s=seconds, wall_s=wall, solves=solves,
+                solves_per_s=solves / wall, p50_ms=float(np.percentile(lat, 50)),
+                p99_ms=float(np.percentile(lat, 99)), max_ms=float(lat.max()),
+                queued_p50_ms=float(np.percentile(que, 50)), queued_p99_ms=float(np.percentile(que, 99)),
+                failed=int(sum(x["state"] != api.REQ_DONE for x in infos)),
+                workload="Poisson stream at %g req/s for %g s: seeded random signed networks of 2-60 nodes, "
+                         "density 0.05-0.3, 1k-50k sets x 1-20 ICs each, FP32 + FP64 polish + dedupe; "
+                         "admitted by HBM budget (64 GB), up to 16 in flight" % (rate, seconds))
 
 
 # ------------------------------------------------------------------ native
@@ -345,6 +404,8 @@ def run_native(args):
                                         "tolerances, no polish" % (f64_sets - 1, I),
                                  ratio=value / fp64_value),
             clocks=clocks)
+        if args.serve_seconds > 0 and ws == 1:
+            line["serving"] = serving_measurement(dev, args.serve_seconds, args.serve_rate)
         if not args.no_cpu_baseline and ws == 1:
             line["cpu_baseline"] = cpu_baseline(args.cpu_sets)
         print(json.dumps(line))
