@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=6.0,
                     help="length of the Poisson request stream of the serving measurement (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=20.0, help="requests per second of that stream")
+    ap.add_argument("--batch-reps", type=int, default=3,
+                    help="timed replays of the batched 64-network plan (0: skip)")
     return ap.parse_args()
 
 
@@ -162,6 +164,43 @@ def run_reference(args):
                                   sample="%d sets x %d ICs per step" % (args.cpu_sets, N_ICS)),
                 e2e=dict(value=value, unit="solves/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line))
+
+
+# ------------------------------------------------------------------ batched
+def batched_measurement(dev, reps):
+    """One plan over the 64 uneven networks of the batched workload (2-40
+    nodes, density 0.1-0.3, 100-10k sets log-uniform, 10 ICs each): one
+    persistent integrator launch, then each job's polish and dedupe, captured
+    in a CUDA graph and autotuned at creation (untimed).  Timed: `reps`
+    replays of the graph after one warm-up replay, CUDA events on the
+    stream."""
+    import torch
+    from paper_2503_18356_gb300 import api, workloads as W
+
+    jobs = []
+    solves = 0
+    for wl in W.batched_workload(64):
+        h = api.Racipe.from_topology(wl["topology"], device=dev)
+        params, ic = h.sample_params(wl["param_seed"], wl["n_sets"], wl["n_ics"])
+        jobs.append(dict(net=h, params=params, ic_unit=ic))
+        solves += wl["n_sets"] * wl["n_ics"]
+    stream = torch.cuda.current_stream()
+    plan = api.Plan(jobs, stream=stream)
+    plan.run(stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        plan.run(stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    info = plan.info()
+    plan.close()
+    return dict(networks=len(jobs), solves=solves, ms_per_replay=ms, solves_per_s=solves / (ms / 1e3),
+                plan=info, reps=reps,
+                workload="64 seeded random signed networks of 2-40 nodes, density 0.1-0.3, 100-10k sets "
+                         "(log-uniform) x 10 ICs, FP32 + FP64 polish + dedupe, one CUDA-graph replay")
 
 
 # ------------------------------------------------------------------ serving
@@ -404,6 +443,8 @@ def run_native(args):
                                         "tolerances, no polish" % (f64_sets - 1, I),
                                  ratio=value / fp64_value),
             clocks=clocks)
+        if args.batch_reps > 0 and ws == 1:
+            line["batched"] = batched_measurement(dev, args.batch_reps)
         if args.serve_seconds > 0 and ws == 1:
             line["serving"] = serving_measurement(dev, args.serve_seconds, args.serve_rate)
         if not args.no_cpu_baseline and ws == 1:

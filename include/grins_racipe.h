@@ -259,6 +259,18 @@ typedef struct grins_racipe_server *grins_racipe_server_t;   /* opaque */
 typedef struct {
     int32_t max_inflight;      /* requests running at once (streams), 1..64 */
     int64_t hbm_budget_bytes;  /* device memory all admitted requests may hold */
+    /* Run-time compiled integrator (FP32 requests).  jit = 1: a request whose
+     * work n_sets * n_ics * n_edges is at least jit_min_work starts, at
+     * submission, a background compile of the integrator for its network
+     * (unless one exists) and is admitted once the compile is done, or after
+     * jit_max_wait_s, whichever comes first; it then runs the compiled kernel
+     * if ready.  Smaller requests, and every request with jit = 0, run the
+     * run-time-layout kernel unless an earlier call compiled one for the
+     * network.  A request waiting for its compile does not hold back later
+     * requests. */
+    int32_t jit;
+    double jit_min_work;
+    double jit_max_wait_s;
 } grins_server_config;
 
 enum { GRINS_REQ_QUEUED = 0, GRINS_REQ_RUNNING = 1, GRINS_REQ_DONE = 2, GRINS_REQ_FAILED = 3 };
@@ -273,7 +285,8 @@ typedef struct {
     double latency_s;          /* submission -> results ready; -1 if not done */
 } grins_request_info;
 
-/* Defaults: 8 in flight, 32 GiB budget. */
+/* Defaults: 8 in flight, 32 GiB budget, jit = 1, jit_min_work = 2e6,
+ * jit_max_wait_s = 3. */
 void grins_server_default_config(grins_server_config *c);
 
 /* Starts a server (and its worker thread) on the current device; c = NULL

@@ -64,7 +64,8 @@ class grins_racipe_job(C.Structure):
 
 
 class grins_server_config(C.Structure):
-    _fields_ = [("max_inflight", C.c_int32), ("hbm_budget_bytes", C.c_int64)]
+    _fields_ = [("max_inflight", C.c_int32), ("hbm_budget_bytes", C.c_int64), ("jit", C.c_int32),
+                ("jit_min_work", C.c_double), ("jit_max_wait_s", C.c_double)]
 
 
 class grins_request_info(C.Structure):
@@ -363,9 +364,16 @@ class Plan:
 class Server:
     """Continuous-batching request server (grins_racipe_server_*)."""
 
-    def __init__(self, max_inflight=8, hbm_budget_bytes=32 << 30, device=None):
+    def __init__(self, max_inflight=8, hbm_budget_bytes=32 << 30, device=None, jit=True, jit_min_work=None,
+                 jit_max_wait_s=None):
         self.device = torch.device(device or "cuda")
-        cfg = grins_server_config(max_inflight, hbm_budget_bytes)
+        cfg = grins_server_config()
+        _lib.grins_server_default_config(C.byref(cfg))
+        cfg.max_inflight, cfg.hbm_budget_bytes, cfg.jit = max_inflight, hbm_budget_bytes, 1 if jit else 0
+        if jit_min_work is not None:
+            cfg.jit_min_work = jit_min_work
+        if jit_max_wait_s is not None:
+            cfg.jit_max_wait_s = jit_max_wait_s
         h = _H()
         with torch.cuda.device(self.device):
             _check(_lib.grins_racipe_server_create(C.byref(cfg), C.byref(h)))

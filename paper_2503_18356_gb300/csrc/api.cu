@@ -1124,6 +1124,9 @@ struct ServerRequest {
     double t_submit = 0, t_admit = 0, t_done = 0;
     int64_t bytes = 0;
     int slot = -1;
+    bool jit_wait = false;         // admitted once its compile is done (or jit_max_wait_s passed)
+    GrpTopo jit_topo{};
+    int jit_kind = 0;
     unsigned char *mem = nullptr;
     unsigned char *params = nullptr;
     double *ic = nullptr, *states = nullptr, *t_final = nullptr;
@@ -1141,6 +1144,8 @@ int64_t align256(int64_t b) { return (b + 255) / 256 * 256; }
 struct grins_racipe_server {
     int device = 0, num_sms = 1, max_inflight = 8;
     int64_t budget = 0, used = 0;
+    bool jit = true;
+    double jit_min_work = 2e6, jit_max_wait_s = 3.0;
     cudaMemPool_t pool = nullptr;
     std::vector<cudaStream_t> streams;
     std::vector<char> slot_busy;
@@ -1254,6 +1259,13 @@ void server_loop(grins_racipe_server *sv)
                 if (!sv->slot_busy[i]) slot = i;
             if (slot < 0) break;
             if (sv->busy_nets.count(r.net)) { ++it; continue; }
+            if (r.jit_wait) {
+                if (grp_jit_prefetch(r.jit_topo, r.jit_kind) == 0 && now_s() - r.t_submit < sv->jit_max_wait_s) {
+                    ++it;
+                    continue;
+                }
+                r.jit_wait = false;
+            }
             if (sv->used + r.bytes > sv->budget && sv->used > 0) break;   // head waits for memory
             r.slot = slot;
             sv->slot_busy[slot] = 1;
@@ -1286,6 +1298,9 @@ extern "C" void grins_server_default_config(grins_server_config *c)
     if (!c) return;
     c->max_inflight = 8;
     c->hbm_budget_bytes = (int64_t)32 << 30;
+    c->jit = 1;
+    c->jit_min_work = 2e6;
+    c->jit_max_wait_s = 3.0;
 }
 
 extern "C" grins_status grins_racipe_server_create(const grins_server_config *c, grins_racipe_server_t *out)
@@ -1297,12 +1312,17 @@ extern "C" grins_status grins_racipe_server_create(const grins_server_config *c,
     if (c) cfg = *c; else grins_server_default_config(&cfg);
     if (cfg.max_inflight < 1 || cfg.max_inflight > 64 || cfg.hbm_budget_bytes <= 0)
         return fail(GRINS_E_INVALID_ARG, "server_create: need 1 <= max_inflight <= 64 and a positive budget");
+    if (!(cfg.jit_min_work >= 0) || !(cfg.jit_max_wait_s >= 0))
+        return fail(GRINS_E_INVALID_ARG, "server_create: jit_min_work and jit_max_wait_s must be >= 0");
     auto sv = std::unique_ptr<grins_racipe_server>(new (std::nothrow) grins_racipe_server());
     if (!sv) return fail(GRINS_E_NOMEM, "server_create: host allocation failed");
     CUDA_TRY(cudaGetDevice(&sv->device), "server_create: current device");
     CUDA_TRY(cudaDeviceGetAttribute(&sv->num_sms, cudaDevAttrMultiProcessorCount, sv->device), "server_create");
     sv->max_inflight = cfg.max_inflight;
     sv->budget = cfg.hbm_budget_bytes;
+    sv->jit = cfg.jit != 0;
+    sv->jit_min_work = cfg.jit_min_work;
+    sv->jit_max_wait_s = cfg.jit_max_wait_s;
     cudaMemPoolProps props{};
     props.allocType = cudaMemAllocationTypePinned;
     props.location.type = cudaMemLocationTypeDevice;
@@ -1358,6 +1378,18 @@ extern "C" grins_status grins_racipe_server_submit(grins_racipe_server_t sv, gri
     if (req->bytes > sv->budget)
         return fail(GRINS_E_BUDGET, "server_submit: the request needs %lld bytes, above the %lld-byte budget",
                     (long long)req->bytes, (long long)sv->budget);
+    // large FP32 requests start the compile of their network's integrator
+    // now, so that it overlaps the queueing; the worker admits them once it
+    // is done (the kernel the integrate call would pick: records in
+    // registers when that layout exists, else records in shared memory)
+    if (sv->jit && o->precision == GRINS_FP32 &&
+        (double)n_sets * n_ics * std::max(net->E, 1) >= sv->jit_min_work) {
+        const char *ev = std::getenv("GRINS_JIT_KIND");
+        const bool want_shared = ev && std::string(ev) == "grp";
+        if (!want_shared && net->rr.L > 0) { req->jit_topo = net->rr.topo(); req->jit_kind = kJitRegisters; }
+        else { req->jit_topo = net->grp.topo(); req->jit_kind = kJitShared; }
+        req->jit_wait = grp_jit_prefetch(req->jit_topo, req->jit_kind) == 0;
+    }
     CUDA_TRY(cudaEventCreateWithFlags(&req->done, cudaEventDisableTiming), "server_submit: event");
     std::lock_guard<std::mutex> lock(sv->mu);
     req->id = sv->next_id++;

@@ -127,6 +127,9 @@ struct BatchArgs {
 enum JitKind { kJitShared = 0, kJitRegisters = 1 };
 const void *grp_jit_kernel(const GrpTopo &g, int kind, std::string *why);
 const void *grp_jit_lookup(const GrpTopo &g, int kind);
+// Starts (once) a background compile for layout g: 1 ready, 0 compiling, -1
+// failed or unavailable.
+int grp_jit_prefetch(const GrpTopo &g, int kind);
 cudaError_t launch_grp_jit(const void *kern, const IntegrateArgs &a, cudaStream_t st, int num_sms);
 cudaError_t launch_integrate_fp32(const IntegrateArgs &a, cudaStream_t st, int num_sms);
 // Batched lane-group launch with `warps` warps per block (2 or 4); smem =

@@ -18,12 +18,17 @@
 // leaves the run-time-layout kernel in charge (GRINS_JIT=0 forces that).
 #include <dlfcn.h>
 
+#include <atomic>
+#include <condition_variable>
 #include <cstdio>
 #include <cstdlib>
+#include <deque>
+#include <functional>
 #include <map>
 #include <memory>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include <nvrtc.h>
@@ -89,17 +94,75 @@ NvrtcApi &nvrtc()
 
 constexpr int kJitWarps = 4;
 
+// One cache entry: a kernel for one (layout, kind), compiled once per
+// process, in the calling thread or in the background pool.
 struct JitEntry {
-    bool ok = false;
+    std::atomic<int> state{0};   // 0 compiling, 1 ready, -1 failed
     std::string why;
     int kind = kJitShared;
+    cudaLibrary_t lib = nullptr;
+    cudaKernel_t kern = nullptr;
+};
+
+// Result of one NVRTC compile and load.
+struct JitBuild {
+    bool ok = false;
+    std::string why;
     int spill_bytes = 0;
     cudaLibrary_t lib = nullptr;
     cudaKernel_t kern = nullptr;
 };
 
-std::mutex g_jit_mu;
-std::map<std::string, std::shared_ptr<JitEntry>> g_jit_cache;
+// Cache and background pool.  Both are created once and never destroyed:
+// a pool thread may still be compiling when the process exits.
+struct JitCache {
+    std::mutex mu;
+    std::condition_variable cv;            // an entry left the compiling state
+    std::map<std::string, std::shared_ptr<JitEntry>> map;
+};
+JitCache &jit_cache()
+{
+    static JitCache *c = new JitCache();
+    return *c;
+}
+
+struct JitPool {
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<std::function<void()>> tasks;
+    int threads = 0;
+};
+JitPool &jit_pool()
+{
+    static JitPool *p = new JitPool();
+    return *p;
+}
+
+// Runs f on a pool thread; the pool grows to (cores - 2) threads, at least
+// one, as tasks arrive.
+void jit_pool_push(std::function<void()> f)
+{
+    JitPool &p = jit_pool();
+    std::lock_guard<std::mutex> lock(p.mu);
+    p.tasks.push_back(std::move(f));
+    const int cores = (int)std::thread::hardware_concurrency();
+    const int cap = cores > 3 ? cores - 2 : 1;
+    if (p.threads < cap && (int)p.tasks.size() > 0) {
+        ++p.threads;
+        std::thread([&p] {
+            std::unique_lock<std::mutex> l(p.mu);
+            for (;;) {
+                p.cv.wait(l, [&p] { return !p.tasks.empty(); });
+                std::function<void()> t = std::move(p.tasks.front());
+                p.tasks.pop_front();
+                l.unlock();
+                t();
+                l.lock();
+            }
+        }).detach();
+    }
+    p.cv.notify_one();
+}
 
 // Generated prelude + kernel wrapper for one layout.
 std::string jit_main(const GrpTopo &g, int kind, int minb)
@@ -160,11 +223,12 @@ int log_spill_bytes(const std::string &log)
     return total;
 }
 
-std::shared_ptr<JitEntry> jit_compile(const std::string &src)
+JitBuild jit_compile(const std::string &src)
 {
-    auto e = std::make_shared<JitEntry>();
+    JitBuild b;
+    JitBuild *e = &b;
     NvrtcApi &api = nvrtc();
-    if (!api.ok) { e->why = api.why; return e; }
+    if (!api.ok) { e->why = api.why; return b; }
     std::vector<const char *> hdr_src, hdr_name;
     for (int i = 0; i < kJitSourceCount; ++i) {
         hdr_src.push_back(kJitSources[i]);
@@ -175,7 +239,7 @@ std::shared_ptr<JitEntry> jit_compile(const std::string &src)
     nvrtcProgram prog = nullptr;
     nvrtcResult r = api.create(&prog, src.c_str(), "grins_grp_ct.cu", (int)hdr_src.size(), hdr_src.data(),
                                hdr_name.data());
-    if (r != NVRTC_SUCCESS) { e->why = std::string("nvrtcCreateProgram: ") + api.err(r); return e; }
+    if (r != NVRTC_SUCCESS) { e->why = std::string("nvrtcCreateProgram: ") + api.err(r); return b; }
     const char *opts[] = {"--gpu-architecture=sm_103a", "--std=c++17", "-lineinfo", "-default-device",
                           "--ptxas-options=-v"};
     r = api.compile(prog, 5, opts);
@@ -186,7 +250,7 @@ std::shared_ptr<JitEntry> jit_compile(const std::string &src)
     if (r != NVRTC_SUCCESS) {
         e->why = std::string("nvrtcCompileProgram: ") + api.err(r) + "\n" + log;
         api.destroy(&prog);
-        return e;
+        return b;
     }
     e->spill_bytes = log_spill_bytes(log);
     n = 0;
@@ -196,9 +260,9 @@ std::shared_ptr<JitEntry> jit_compile(const std::string &src)
     api.destroy(&prog);
     cudaError_t ce = cudaLibraryLoadData(&e->lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
     if (ce == cudaSuccess) ce = cudaLibraryGetKernel(&e->kern, e->lib, "grins_grp_ct");
-    if (ce != cudaSuccess) { e->why = std::string("loading the compiled kernel: ") + cudaGetErrorString(ce); return e; }
+    if (ce != cudaSuccess) { e->why = std::string("loading the compiled kernel: ") + cudaGetErrorString(ce); return b; }
     e->ok = true;
-    return e;
+    return b;
 }
 
 // Minimum resident blocks per SM for a kernel of this kind and layout: for
@@ -217,28 +281,72 @@ int jit_minb(const GrpTopo &g, int kind)
     return minb;
 }
 
-std::shared_ptr<JitEntry> jit_get(const GrpTopo &g, int kind, bool compile)
+// Compiles the kernel for (g, kind) into e on device dev: from the block
+// count of the register estimate, one block fewer while a register-record
+// compile spills.  Wakes every thread waiting for an entry.
+void jit_build_entry(JitEntry &e, const GrpTopo &g, int kind, int dev)
 {
+    cudaSetDevice(dev);
     int minb = jit_minb(g, kind);
-    std::lock_guard<std::mutex> lock(g_jit_mu);
+    JitBuild b;
     for (;;) {
-        const std::string src = jit_main(g, kind, minb);
-        auto it = g_jit_cache.find(src);
-        if (it == g_jit_cache.end()) {
-            if (!compile) return nullptr;
-            auto e = jit_compile(src);
-            e->kind = kind;
-            it = g_jit_cache.emplace(src, e).first;
-        }
-        std::shared_ptr<JitEntry> e = it->second;
-        // a register-record kernel that spills gets another try with fewer
-        // resident blocks (more registers per thread)
-        if (e->ok && kind == kJitRegisters && e->spill_bytes > 0 && minb > 1 && !std::getenv("GRINS_JIT_MINB")) {
+        b = jit_compile(jit_main(g, kind, minb));
+        if (b.ok && kind == kJitRegisters && b.spill_bytes > 0 && minb > 1 && !std::getenv("GRINS_JIT_MINB")) {
+            cudaLibraryUnload(b.lib);
             --minb;
             continue;
         }
+        break;
+    }
+    JitCache &c = jit_cache();
+    {
+        std::lock_guard<std::mutex> lock(c.mu);
+        e.why = b.why;
+        e.lib = b.lib;
+        e.kern = b.kern;
+        e.state.store(b.ok ? 1 : -1);
+    }
+    c.cv.notify_all();
+}
+
+enum JitMode { kLookup = 0, kCompileHere = 1, kCompileAsync = 2 };
+
+// The cache entry for (g, kind), keyed by the source text of its first
+// compile.  kLookup: null when absent; kCompileHere: compiles in this
+// thread when absent and waits for a compile in flight; kCompileAsync:
+// queues a background compile when absent and returns at once.
+std::shared_ptr<JitEntry> jit_get(const GrpTopo &g, int kind, int mode)
+{
+    const std::string key = jit_main(g, kind, jit_minb(g, kind));
+    JitCache &c = jit_cache();
+    std::unique_lock<std::mutex> lock(c.mu);
+    auto it = c.map.find(key);
+    if (it == c.map.end()) {
+        if (mode == kLookup) return nullptr;
+        auto e = std::make_shared<JitEntry>();
+        e->kind = kind;
+        c.map.emplace(key, e);
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (mode == kCompileHere) {
+            lock.unlock();
+            jit_build_entry(*e, g, kind, dev);
+        } else {
+            jit_pool_push([e, g, kind, dev] { jit_build_entry(*e, g, kind, dev); });
+        }
         return e;
     }
+    std::shared_ptr<JitEntry> e = it->second;
+    if (mode == kCompileHere) c.cv.wait(lock, [&e] { return e->state.load() != 0; });
+    return e;
+}
+
+bool jit_enabled(const GrpTopo &g, std::string *why)
+{
+    const char *ev = std::getenv("GRINS_JIT");
+    if (ev && ev[0] == '0') { if (why) *why = "disabled by GRINS_JIT=0"; return false; }
+    if (g.L <= 0 || g.R <= 0 || g.R > 12) { if (why) *why = "no lane-group layout"; return false; }
+    return true;
 }
 
 }  // namespace
@@ -248,29 +356,36 @@ std::shared_ptr<JitEntry> jit_get(const GrpTopo &g, int kind, bool compile)
 // launch_grp_jit.
 const void *grp_jit_kernel(const GrpTopo &g, int kind, std::string *why)
 {
-    const char *ev = std::getenv("GRINS_JIT");
-    if (ev && ev[0] == '0') { if (why) *why = "disabled by GRINS_JIT=0"; return nullptr; }
-    if (g.L <= 0 || g.R <= 0 || g.R > 12) { if (why) *why = "no lane-group layout"; return nullptr; }
-    std::shared_ptr<JitEntry> e = jit_get(g, kind, true);
-    if (!e->ok) { if (why) *why = e->why; return nullptr; }
+    if (!jit_enabled(g, why)) return nullptr;
+    std::shared_ptr<JitEntry> e = jit_get(g, kind, kCompileHere);
+    if (e->state.load() != 1) { if (why) *why = e->why; return nullptr; }
     if (why) *why = e->kind == kJitRegisters ? "records in registers" : "records in shared memory";
     return e.get();
 }
 
 // The compiled kernel for layout g if an earlier call compiled it; never
-// compiles or loads anything.
+// compiles, loads or waits.
 const void *grp_jit_lookup(const GrpTopo &g, int kind)
 {
-    const char *ev = std::getenv("GRINS_JIT");
-    if ((ev && ev[0] == '0') || g.L <= 0 || g.R <= 0 || g.R > 12) return nullptr;
-    std::shared_ptr<JitEntry> e = jit_get(g, kind, false);
-    if (!e || !e->ok) return nullptr;
+    if (!jit_enabled(g, nullptr)) return nullptr;
+    std::shared_ptr<JitEntry> e = jit_get(g, kind, kLookup);
+    if (!e || e->state.load() != 1) return nullptr;
     return e.get();
+}
+
+// Starts (once) a background compile of the kernel for layout g and
+// returns its state: 1 ready, 0 compiling, -1 failed or run-time compiles
+// unavailable.
+int grp_jit_prefetch(const GrpTopo &g, int kind)
+{
+    if (!jit_enabled(g, nullptr)) return -1;
+    return jit_get(g, kind, kCompileAsync)->state.load();
 }
 
 cudaError_t launch_grp_jit(const void *handle, const IntegrateArgs &a, cudaStream_t st, int num_sms)
 {
     const JitEntry *je = static_cast<const JitEntry *>(handle);
+    if (je->state.load() != 1) return cudaErrorInvalidValue;
     IntegrateArgs b = a;
     int smem = 0;
     if (je->kind == kJitRegisters) {

@@ -28,15 +28,24 @@ def rel_err(x, ref, G, k, floor=1e-6):
     return np.abs(x - ref) / scale
 
 
-def compare_states(gpu, orc, p: O.ParamSet, tol, basin_tol=1e-2, normalised=False):
+def compare_states(gpu, orc, p: O.ParamSet, tol, basin_tol=None, normalised=False):
     """Compares converged states set by set.  Returns a dict with the max
-    error over solves converged on both sides and in the same basin, the
-    number of such solves, the basin-mismatch count and the status agreement
-    rate.  The error is relative (floor 1e-6 G/k) for polished states; with
-    `normalised` it is measured on the G/k scale, |x - x*| k / G, which is
-    how unpolished states (stopped at max_i |f_i| k_i / G_i < ss_tol) are
-    judged: that stop rule bounds the distance to the fixed point in units of
-    G/k, not relative to a small steady level."""
+    error over solves converged on both sides and at the same fixed point,
+    the number of such solves, the count of solves that reached different
+    fixed points and the status agreement rate.  The error is relative
+    (floor 1e-6 G/k) for polished states; with `normalised` it is measured on
+    the G/k scale, |x - x*| k / G, which is how unpolished states (stopped at
+    max_i |f_i| k_i / G_i < ss_tol) are judged: that stop rule bounds the
+    distance to the fixed point in units of G/k, not relative to a small
+    steady level.
+
+    Same fixed point: G/k-normalised distance <= basin_tol, by default 1e-2
+    for unpolished states and 1e-5 for polished ones (fixed points to ~1e-12;
+    near a saddle-node bifurcation a stable node and its saddle can lie
+    1e-4 .. 1e-2 apart, and a solve that the two sides send to different
+    ones is a basin mismatch, not an accuracy error)."""
+    if basin_tol is None:
+        basin_tol = 1e-2 if normalised else 1e-5
     G = p.G[:, None, :]
     k = p.k[:, None, :]
     both = (gpu["status"] == O.CONVERGED) & (orc["status"] == O.CONVERGED)

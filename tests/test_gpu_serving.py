@@ -7,7 +7,8 @@ requests on one GPU.
   * admission respects the HBM budget, and a request larger than the whole
     budget is refused;
   * a served request agrees with the CPU oracle (FP32 + FP64 polish,
-    relative 1e-6 with a floor of 1e-6 G/k).
+    relative 1e-6 with a floor of 1e-6 G/k), on the run-time-layout kernel
+    and on kernels compiled in the background at submission.
 """
 import numpy as np
 import pytest
@@ -110,6 +111,7 @@ def test_served_request_matches_oracle():
     print(topo.n_nodes, topo.n_edges, c)
     assert c["max_rel"] <= 1e-6
     assert c["n_compared"] > 0
+    assert c["n_basin"] <= max(1, 0.01 * g["status"].size)
     # a status mismatch is a slow solve meeting the steady-state condition
     # before t_end on one side only (converged, possibly with a polish that
     # could not certify it, vs t_end), never a non-finite or step-limit stop
@@ -117,3 +119,43 @@ def test_served_request_matches_oracle():
     seen = set(g["status"][diff].tolist()) | set(o["status"][diff].tolist())
     assert seen <= {O.CONVERGED, O.TEND, O.POLISH_FAIL}, seen
     assert c["status_agree"] >= 0.9
+
+
+def test_requests_on_compiled_kernels():
+    """With jit_min_work = 0 every FP32 request starts a background compile of
+    its network's integrator at submission and is admitted once it is done:
+    results agree with the oracle as on the run-time-layout kernel, and a
+    second request on the same network finds the kernel compiled."""
+    from paper_2503_18356_gb300 import api
+    reqs = _requests(3, max_sets=24)[1:]
+    sv = api.Server(jit_min_work=0.0, jit_max_wait_s=60.0)
+    ids = [sv.submit(r["net"], r["seed"], r["S"], r["I"]) for r in reqs]
+    infos = [sv.wait(i) for i in ids]
+    assert all(x["state"] == api.REQ_DONE for x in infos), infos
+    res = [_np(sv.results(i)) for i in ids]
+    for i in ids:
+        sv.release(i)
+    r = reqs[0]
+    again = sv.submit(r["net"], r["seed"], r["S"], r["I"])
+    info2 = sv.wait(again)
+    g2 = _np(sv.results(again))
+    sv.release(again)
+    sv.close()
+    print("queued", [round(x["queued_s"], 3) for x in infos], "second", round(info2["queued_s"], 4))
+    assert info2["queued_s"] < infos[0]["queued_s"] + 0.5
+    for k in ("states", "status", "n_unique", "state_id"):
+        assert np.array_equal(res[0][k], g2[k]), k
+    for r, g in zip(reqs, res):
+        topo = r["topo"]
+        net = O.Network(*topo.edges())
+        p = O.sample_params(net, r["seed"], r["S"])
+        ic = O.sample_ics(topo.n_nodes, r["seed"], r["I"])
+        o = O.run_sets_parallel(net, p, ic, threads=PT.THREADS)
+        c = PT.compare_states(g, o, p, 1e-6)
+        print(topo.n_nodes, topo.n_edges, c)
+        assert c["max_rel"] <= 1e-6
+        assert c["n_compared"] > 0
+        assert c["n_basin"] <= max(1, 0.01 * g["status"].size)
+        diff = g["status"] != o["status"]
+        seen = set(g["status"][diff].tolist()) | set(o["status"][diff].tolist())
+        assert seen <= {O.CONVERGED, O.TEND, O.POLISH_FAIL}, seen
