@@ -220,10 +220,17 @@ typedef struct {
 } grins_racipe_job;
 
 /* Builds a plan for n_jobs jobs with the solver options o (FP32, no time
- * grid).  With autotune != 0 the block size (2 or 4 warps) and the number
- * of parameter-set slots per scheduling domain are chosen by timing each
- * candidate on the first sixteenth of every job's sets (this runs kernels
- * on `stream` and writes to the jobs' output buffers).  The jobs' buffers
+ * grid).  The integration runs in one of two forms:
+ *   * one persistent launch over all jobs (run-time-layout kernel);
+ *   * per job the integrator compiled for its network (NVRTC, compiled at
+ *     plan creation in parallel on host threads), each on one of up to 16
+ *     branches of the graph, so that jobs run concurrently.
+ * autotune = 0: the persistent launch with 4 warps per block and 1 extra
+ * slot per scheduling domain.  autotune = 1: the block size (2 or 4 warps),
+ * the slots per domain and the per-job form are each timed on the first
+ * sixteenth of every job's sets and the fastest kept (this runs kernels on
+ * `stream` and writes to the jobs' output buffers).  autotune = 2: the
+ * per-job form without timing.  The jobs' buffers
  * must stay valid for the plan's lifetime; their contents are read when the
  * plan runs.  Errors: GRINS_E_INVALID_ARG for bad options or jobs (networks
  * on another device, missing buffers, precision other than FP32, a time
@@ -286,7 +293,7 @@ typedef struct {
 } grins_request_info;
 
 /* Defaults: 8 in flight, 32 GiB budget, jit = 1, jit_min_work = 2e6,
- * jit_max_wait_s = 3. */
+ * jit_max_wait_s = 1. */
 void grins_server_default_config(grins_server_config *c);
 
 /* Starts a server (and its worker thread) on the current device; c = NULL

@@ -305,6 +305,10 @@ class Racipe:
 class Plan:
     """A batched launch over many networks (grins_racipe_plan_*).
 
+    ``autotune``: 0/False the persistent batched launch, 1/True time the
+    launch configurations and the per-network compiled kernels and keep the
+    fastest, 2 the per-network compiled kernels without timing.
+
     ``jobs``: list of dicts with keys net (a Racipe), params, ic_unit and,
     optionally, out (buffers as returned by ``Racipe.integrate``; allocated
     here when absent), dedupe (bool, default True) and dedupe_tol.  The
@@ -338,7 +342,7 @@ class Plan:
                                       float(jb.get("dedupe_tol", 1e-2)))
         self._arr = arr
         h = _H()
-        _check(_lib.grins_racipe_plan_create(C.byref(self.opts), arr, len(jobs), 1 if autotune else 0,
+        _check(_lib.grins_racipe_plan_create(C.byref(self.opts), arr, len(jobs), int(autotune),
                                              _stream(stream), C.byref(h)))
         self._p = h
 

@@ -258,7 +258,7 @@ static GrpHost build_grp(int N, int L, const std::vector<int32_t> &csr_off, cons
         // shared-memory wavefronts wins
         std::vector<int32_t> best_e, best_o, e, o;
         int best = -1;
-        for (int trial = 0; trial < trials; ++trial) {
+        for (int trial = 0; trial < trials && best != D; ++trial) {   // D: one wavefront per position
             const int sc = order_row(lst, D, (uint64_t)trial, e, o);
             if (best < 0 || sc < best) { best = sc; best_e.swap(e); best_o.swap(o); }
         }
@@ -293,6 +293,19 @@ static GrpHost choose_grp_shared(int N, const std::vector<int32_t> &off, const s
     return build_grp(N, L, off, src, edge);
 }
 
+// Positions per lane of the layout with L lanes: nodes sorted by
+// in-degree, each row of L taking its largest in-degree (no edge ordering
+// needed for the count).
+static int grp_positions(int N, int L, const std::vector<int32_t> &off)
+{
+    std::vector<int> deg(N);
+    for (int i = 0; i < N; ++i) deg[i] = off[i + 1] - off[i];
+    std::sort(deg.begin(), deg.end(), [](int a, int b) { return a > b; });
+    int P = 0;
+    for (int q = 0; q < N; q += L) P += deg[q];
+    return P;
+}
+
 // Register-record kernel: a lane holds about 4 registers per edge position
 // and 11 per row on top of ~40.  The smallest power of two L (at most 12
 // rows) whose estimate allows 3 resident blocks of 4 warps per SM (168
@@ -300,16 +313,12 @@ static GrpHost choose_grp_shared(int N, const std::vector<int32_t> &off, const s
 static GrpHost choose_grp_registers(int N, const std::vector<int32_t> &off, const std::vector<int32_t> &src,
                                     const std::vector<int32_t> &edge)
 {
-    auto est = [](const GrpHost &g) { return 4 * g.P + 11 * g.R + 40; };
-    if (const int f = grp_l_override(N)) {
-        GrpHost g = build_grp(N, f, off, src, edge);
-        return est(g) <= 255 ? g : GrpHost{};
-    }
+    auto est = [&](int L) { return 4 * grp_positions(N, L, off) + 11 * ((N + L - 1) / L) + 40; };
+    if (const int f = grp_l_override(N)) return est(f) <= 255 ? build_grp(N, f, off, src, edge) : GrpHost{};
     for (int limit : {168, 255}) {
         for (int L = 1; L <= kWarp; L *= 2) {
             if ((N + L - 1) / L > 12) continue;
-            GrpHost g = build_grp(N, L, off, src, edge);
-            if (est(g) <= limit) return g;
+            if (est(L) <= limit) return build_grp(N, L, off, src, edge);
         }
     }
     return GrpHost{};
@@ -550,25 +559,38 @@ grins_status check_ranges(const grins_racipe_ranges &r)
     return GRINS_OK;
 }
 
+// Median level of the in-degree class (na activating, ni inhibiting inputs)
+// under ranges r.  It depends on the class and the ranges only (the samples
+// use a fixed key), so it is computed once per process and shared by every
+// network; (0, 0) is the unregulated level, m0 the median the regulated
+// classes' sources are drawn around.
+double class_median(int na, int ni, const grins_racipe_ranges &r, double m0)
+{
+    struct Entry { grins_racipe_ranges r; int na, ni; double m; };
+    static std::mutex *mu = new std::mutex();
+    static std::vector<Entry> *tab = new std::vector<Entry>();
+    {
+        std::lock_guard<std::mutex> lock(*mu);
+        for (const Entry &e : *tab)
+            if (e.na == na && e.ni == ni && same_ranges(e.r, r)) return e.m;
+    }
+    std::vector<double> v = level_samples(na, ni, r, m0);
+    const double m = median_sorted(v);
+    std::lock_guard<std::mutex> lock(*mu);
+    tab->push_back(Entry{r, na, ni, m});
+    return m;
+}
+
 grins_status ensure_medians(grins_racipe *h, const grins_racipe_ranges &r)
 {
     if (h->median_valid && same_ranges(h->median_ranges, r)) return GRINS_OK;
-    std::vector<double> v0 = level_samples(0, 0, r, 0.0);
-    const double M0 = median_sorted(v0);
+    const double M0 = class_median(0, 0, r, 0.0);
     h->node_median.assign(h->N, M0);
     if (r.median_mode == GRINS_MEDIAN_PER_INDEGREE) {
-        std::vector<std::pair<std::pair<int, int>, double>> cache;
         for (int j = 0; j < h->N; ++j) {
             const int na = h->n_act_in[j], ni = h->n_inh_in[j];
             if (na == 0 && ni == 0) continue;
-            double M = -1.0;
-            for (auto &c : cache) if (c.first.first == na && c.first.second == ni) M = c.second;
-            if (M < 0.0) {
-                std::vector<double> v = level_samples(na, ni, r, M0);
-                M = median_sorted(v);
-                cache.push_back({{na, ni}, M});
-            }
-            h->node_median[j] = M;
+            h->node_median[j] = class_median(na, ni, r, M0);
         }
     }
     h->median_ranges = r;
@@ -847,6 +869,11 @@ struct grins_racipe_plan {
     unsigned long long *d_counters = nullptr;   // per job: queue, spare, check code, check info
     BatchArgs batch{};
     int warps = 4, slot_extra = 1;
+    int mode = 0;                          // 0: one persistent launch; 1: per-job compiled kernels on branches
+    std::vector<IntegrateArgs> jargs;      // mode 1: per-job arguments (compiled kernel and its layout)
+    std::vector<size_t> order;             // mode 1: jobs by decreasing work
+    std::vector<cudaStream_t> side;        // mode 1: branch streams
+    std::vector<cudaEvent_t> events;       // mode 1: fork event, then one join event per branch
     cudaStream_t cap_stream = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -858,6 +885,10 @@ static void plan_free(grins_racipe_plan *p)
     if (p->exec) cudaGraphExecDestroy(p->exec);
     if (p->graph) cudaGraphDestroy(p->graph);
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+    for (cudaStream_t x : p->side) cudaStreamDestroy(x);
+    for (cudaEvent_t x : p->events) cudaEventDestroy(x);
+    p->side.clear();
+    p->events.clear();
     cudaFree(p->d_args); cudaFree(p->d_cum); cudaFree(p->d_counters);
     p->exec = nullptr; p->graph = nullptr; p->cap_stream = nullptr;
     p->d_args = nullptr; p->d_cum = nullptr; p->d_counters = nullptr;
@@ -909,38 +940,104 @@ static grins_status plan_upload(grins_racipe_plan *p, cudaStream_t st)
     return GRINS_OK;
 }
 
-// The plan's work on stream st: reset the counters, the batched integration,
-// then per job the polish and the dedupe.
+// Polish and dedupe of job b on stream st.
+static grins_status plan_job_tail(grins_racipe_plan *p, size_t b, cudaStream_t st)
+{
+    const grins_racipe_job &j = p->jobs[b];
+    if (j.n_sets == 0) return GRINS_OK;
+    if (p->opts.polish) {
+        PolishArgs pa = polish_args(j.net, &p->opts, j.d_params, j.n_sets, j.n_ics, j.d_states, j.d_status,
+                                    j.d_err_est);
+        pa.check = p->d_counters + 4 * b + 2;
+        CUDA_TRY(launch_polish(pa, st, p->num_sms), "plan: polish launch");
+    } else if (j.d_err_est) {
+        CUDA_TRY(cudaMemsetAsync(j.d_err_est, 0xff, sizeof(float) * j.n_sets * j.n_ics, st), "plan: err_est");
+    }
+    if (j.d_state_id) {
+        UniqueArgs u{};
+        u.L = j.net->layout;
+        u.params = static_cast<const unsigned char *>(j.d_params);
+        u.states = j.d_states; u.status = j.d_status;
+        u.n_sets = j.n_sets; u.n_ics = j.n_ics; u.tol = j.dedupe_tol;
+        u.state_id = j.d_state_id; u.n_unique = j.d_n_unique;
+        CUDA_TRY(launch_unique(u, st, p->num_sms), "plan: dedupe launch");
+    }
+    return GRINS_OK;
+}
+
+// The plan's work on stream st: reset the counters, then either the
+// persistent batched integration followed by every job's polish and dedupe,
+// or, per job on a branch stream forked from st, its compiled integrator,
+// polish and dedupe, the branches joined back into st.
 static grins_status plan_enqueue(grins_racipe_plan *p, cudaStream_t st, bool integrate_only)
 {
     CUDA_TRY(cudaMemsetAsync(p->d_counters, 0, sizeof(unsigned long long) * 4 * p->jobs.size(), st),
              "plan: counter reset");
-    cudaError_t e = launch_integrate_batch(p->batch, p->warps, st, p->num_sms, p->smem_limit);
-    if (e == cudaErrorInvalidConfiguration)
-        return fail(GRINS_E_BUDGET, "plan: the jobs need more shared memory per block than the device has");
-    if (e != cudaSuccess) return cuda_fail(e, "plan: batched launch");
-    if (integrate_only) return GRINS_OK;
-    for (size_t b = 0; b < p->jobs.size(); ++b) {
-        const grins_racipe_job &j = p->jobs[b];
-        if (j.n_sets == 0) continue;
-        if (p->opts.polish) {
-            PolishArgs pa = polish_args(j.net, &p->opts, j.d_params, j.n_sets, j.n_ics, j.d_states, j.d_status,
-                                        j.d_err_est);
-            pa.check = p->d_counters + 4 * b + 2;
-            CUDA_TRY(launch_polish(pa, st, p->num_sms), "plan: polish launch");
-        } else if (j.d_err_est) {
-            CUDA_TRY(cudaMemsetAsync(j.d_err_est, 0xff, sizeof(float) * j.n_sets * j.n_ics, st), "plan: err_est");
+    if (p->mode == 0) {
+        cudaError_t e = launch_integrate_batch(p->batch, p->warps, st, p->num_sms, p->smem_limit);
+        if (e == cudaErrorInvalidConfiguration)
+            return fail(GRINS_E_BUDGET, "plan: the jobs need more shared memory per block than the device has");
+        if (e != cudaSuccess) return cuda_fail(e, "plan: batched launch");
+        if (integrate_only) return GRINS_OK;
+        for (size_t b = 0; b < p->jobs.size(); ++b) {
+            const grins_status s = plan_job_tail(p, b, st);
+            if (s != GRINS_OK) return s;
         }
-        if (j.d_state_id) {
-            UniqueArgs u{};
-            u.L = j.net->layout;
-            u.params = static_cast<const unsigned char *>(j.d_params);
-            u.states = j.d_states; u.status = j.d_status;
-            u.n_sets = j.n_sets; u.n_ics = j.n_ics; u.tol = j.dedupe_tol;
-            u.state_id = j.d_state_id; u.n_unique = j.d_n_unique;
-            CUDA_TRY(launch_unique(u, st, p->num_sms), "plan: dedupe launch");
+        return GRINS_OK;
+    }
+    const int K = (int)p->side.size();
+    CUDA_TRY(cudaEventRecord(p->events[0], st), "plan: fork");
+    for (int k = 0; k < K; ++k) CUDA_TRY(cudaStreamWaitEvent(p->side[k], p->events[0], 0), "plan: fork");
+    for (size_t q = 0; q < p->order.size(); ++q) {
+        const size_t b = p->order[q];
+        cudaStream_t sb = p->side[q % K];
+        if (p->jargs[b].n_sets > 0) {
+            const cudaError_t e = launch_integrate_fp32(p->jargs[b], sb, p->num_sms);
+            if (e == cudaErrorInvalidConfiguration)
+                return fail(GRINS_E_BUDGET, "plan: job %zu needs more shared memory per block than the device has", b);
+            if (e != cudaSuccess) return cuda_fail(e, "plan: job launch");
+        }
+        if (!integrate_only) {
+            const grins_status s = plan_job_tail(p, b, sb);
+            if (s != GRINS_OK) return s;
         }
     }
+    for (int k = 0; k < K; ++k) {
+        CUDA_TRY(cudaEventRecord(p->events[1 + k], p->side[k]), "plan: join");
+        CUDA_TRY(cudaStreamWaitEvent(st, p->events[1 + k], 0), "plan: join");
+    }
+    return GRINS_OK;
+}
+
+// Mode 1 setup: branch streams and events, the job order, and per-job
+// arguments (from p->args) with the kernel compiled for each job's network;
+// the compiles run in parallel on the host pool.
+static grins_status plan_setup_jobs(grins_racipe_plan *p)
+{
+    const size_t n = p->jobs.size();
+    if (p->side.empty()) {
+        const int K = (int)std::min<size_t>(16, n);
+        p->side.assign(K, nullptr);
+        p->events.assign(K + 1, nullptr);
+        for (auto &x : p->side) CUDA_TRY(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking), "plan: branch streams");
+        for (auto &x : p->events) CUDA_TRY(cudaEventCreateWithFlags(&x, cudaEventDisableTiming), "plan: events");
+        p->order.resize(n);
+        for (size_t b = 0; b < n; ++b) p->order[b] = b;
+        std::stable_sort(p->order.begin(), p->order.end(), [p](size_t x, size_t y) {
+            auto work = [p](size_t b) {
+                const grins_racipe_job &j = p->jobs[b];
+                return (double)j.n_sets * j.n_ics * (j.net->E + j.net->N);
+            };
+            return work(x) > work(y);
+        });
+        for (size_t b = 0; b < n; ++b) {          // start every compile before waiting for any
+            const grins_racipe *h = p->jobs[b].net;
+            if (h->rr.L > 0) grp_jit_prefetch(h->rr.topo(), kJitRegisters);
+            else grp_jit_prefetch(h->grp.topo(), kJitShared);
+        }
+    }
+    p->jargs = p->args;
+    for (size_t b = 0; b < n; ++b) pick_fp32_kernel(p->jobs[b].net, &p->jargs[b], true, nullptr);
     return GRINS_OK;
 }
 
@@ -1006,7 +1103,8 @@ extern "C" grins_status grins_racipe_plan_create(const grins_solver_opts *o, con
     // each timed on the first sixteenth of every job's sets
     char buf[512];
     std::string tried;
-    if (autotune) {
+    if (autotune < 0 || autotune > 2) { plan_free(p); delete p; return fail(GRINS_E_INVALID_ARG, "plan_create: autotune must be 0, 1 or 2"); }
+    if (autotune == 1) {
         float best = -1.0f;
         int bw = 4, bx = 1;
         cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1036,14 +1134,39 @@ extern "C" grins_status grins_racipe_plan_create(const grins_solver_opts *o, con
                 g_last_error.clear();
             }
         }
+        // the per-job form: every network's compiled kernel on graph branches
+        plan_args(p, 1, 16);
+        grins_status s = plan_setup_jobs(p);
+        if (s != GRINS_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); plan_free(p); delete p; return s; }
+        p->mode = 1;
+        cudaEventRecord(e0, st);
+        s = plan_enqueue(p, st, true);
+        cudaEventRecord(e1, st);
+        bool per_job = false;
+        if (s == GRINS_OK && cudaEventSynchronize(e1) == cudaSuccess) {
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            std::snprintf(buf, sizeof(buf), "; per-network compiled kernels: %.3f ms", ms);
+            tried += buf;
+            per_job = best < 0 || ms < best;
+        } else if (s != GRINS_E_BUDGET) {
+            cudaEventDestroy(e0); cudaEventDestroy(e1);
+            plan_free(p); delete p;
+            return s != GRINS_OK ? s : fail(GRINS_E_CUDA, "plan_create: autotune run failed");
+        }
+        g_last_error.clear();
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
-        if (best < 0) { plan_free(p); delete p; return fail(GRINS_E_BUDGET, "plan_create: no configuration fits"); }
+        if (best < 0 && !per_job) { plan_free(p); delete p; return fail(GRINS_E_BUDGET, "plan_create: no configuration fits"); }
+        p->mode = per_job ? 1 : 0;
         p->warps = bw;
         p->slot_extra = bx;
     }
+    if (autotune == 2) p->mode = 1;
     plan_args(p, p->slot_extra, 1);
-    grins_status s = plan_upload(p, st);
+    grins_status s = GRINS_OK;
+    if (p->mode == 1) s = plan_setup_jobs(p);
+    if (s == GRINS_OK) s = plan_upload(p, st);
     if (s != GRINS_OK) { plan_free(p); delete p; return s; }
 
     // capture the plan's work once into a graph
@@ -1056,9 +1179,13 @@ extern "C" grins_status grins_racipe_plan_create(const grins_solver_opts *o, con
     if (s != GRINS_OK) { plan_free(p); delete p; return s; }
     if (ce == cudaSuccess) ce = cudaGraphInstantiate(&p->exec, p->graph, 0);
     if (ce != cudaSuccess) { plan_free(p); delete p; return cuda_fail(ce, "plan_create: graph instantiation"); }
-    std::snprintf(buf, sizeof(buf), "batched lane-group DP5(4), %d jobs, %d warps per block, %d extra slots per "
-                  "domain, %d-byte warp region%s", n_jobs, p->warps, p->slot_extra, p->batch.warp_bytes,
-                  autotune ? "; autotuned: " : "");
+    if (p->mode == 1)
+        std::snprintf(buf, sizeof(buf), "per-network compiled lane-group DP5(4) kernels, %d jobs on %d graph "
+                      "branches%s", n_jobs, (int)p->side.size(), autotune == 1 ? "; autotuned: " : "");
+    else
+        std::snprintf(buf, sizeof(buf), "batched lane-group DP5(4), %d jobs, %d warps per block, %d extra slots "
+                      "per domain, %d-byte warp region%s", n_jobs, p->warps, p->slot_extra, p->batch.warp_bytes,
+                      autotune == 1 ? "; autotuned: " : "");
     p->info = buf;
     p->info += tried;
     *out = p;
@@ -1145,7 +1272,7 @@ struct grins_racipe_server {
     int device = 0, num_sms = 1, max_inflight = 8;
     int64_t budget = 0, used = 0;
     bool jit = true;
-    double jit_min_work = 2e6, jit_max_wait_s = 3.0;
+    double jit_min_work = 2e6, jit_max_wait_s = 1.0;
     cudaMemPool_t pool = nullptr;
     std::vector<cudaStream_t> streams;
     std::vector<char> slot_busy;
@@ -1300,7 +1427,7 @@ extern "C" void grins_server_default_config(grins_server_config *c)
     c->hbm_budget_bytes = (int64_t)32 << 30;
     c->jit = 1;
     c->jit_min_work = 2e6;
-    c->jit_max_wait_s = 3.0;
+    c->jit_max_wait_s = 1.0;
 }
 
 extern "C" grins_status grins_racipe_server_create(const grins_server_config *c, grins_racipe_server_t *out)

@@ -1,6 +1,7 @@
 """Batched launch (grins_racipe_plan_*): many uneven networks in one
-persistent launch under a captured CUDA graph, checked job by job against
-the CPU oracle and against the single-network path.
+persistent launch, or each on its own compiled kernel on a graph branch,
+under a captured CUDA graph, checked job by job against the CPU oracle and
+against the single-network path.
 
 Bars as in test_gpu_parity.py: FP32 + FP64 polish relative 1e-6 (floor
 1e-6 G/k) against the oracle; distinct-state counts equal the oracle's
@@ -35,13 +36,17 @@ def _np(out):
     return {k: v.cpu().numpy() for k, v in out.items() if v is not None}
 
 
-def test_plan_matches_oracle_and_replays_exactly():
+@pytest.mark.parametrize("autotune", [1, 2])
+def test_plan_matches_oracle_and_replays_exactly(autotune):
     from paper_2503_18356_gb300 import api
     jobs = _jobs(8, 48)
-    plan = api.Plan(jobs)
+    plan = api.Plan(jobs, autotune=autotune)
     info = plan.info()
     print(info)
-    assert "autotuned" in info
+    if autotune == 1:
+        assert "autotuned" in info and "per-network compiled kernels:" in info
+    else:
+        assert "per-network compiled" in info
     res1 = [_np(j["out"]) for j in plan.run()]
     torch.cuda.synchronize()
     res2 = [_np(j["out"]) for j in plan.run()]
