@@ -287,12 +287,12 @@ def run_native(args):
 
     from paper_2503_18356_gb300 import build as B
     B.build()
-    from paper_2503_18356_gb300 import api, workloads as W
+    from paper_2503_18356_gb300 import api, shard, workloads as W
 
     w = W.net22_workload()
     topo = w["topology"]
     S, I, N, E = args.sets, N_ICS, topo.n_nodes, topo.n_edges
-    set0 = rank * S
+    set0, _ = shard.rank_sets(S, rank)
     h = api.Racipe.from_topology(topo, device=dev)
     stream = torch.cuda.current_stream()
     params = torch.empty((S, h.param_stride), dtype=torch.uint8, device=dev)
@@ -343,12 +343,7 @@ def run_native(args):
     stop.record(stream)
     barrier()
     clocks = clk.stop()
-    elapsed_ms = start.elapsed_time(stop)
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([elapsed_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms = shard.max_over_ranks(start.elapsed_time(stop), dev)
     per_kernel = np.array([[e[i].elapsed_time(e[i + 1]) for i in range(4)] for e in evs])  # ms
     kern_ms = per_kernel.mean(axis=0)
 
@@ -402,12 +397,7 @@ def run_native(args):
     for _ in range(e2e_steps):
         e2e_step()
     barrier()
-    e2e_s = time.perf_counter() - t0
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = shard.max_over_ranks(time.perf_counter() - t0, dev)
     e2e_value = solves * e2e_steps / e2e_s
 
     # the plain FP64 GPU solver (FP64 Dormand-Prince end to end, no polish)
