@@ -132,11 +132,45 @@ def oracle_sample(n_sets, threads):
 
 
 def cpu_baseline(n_sets):
+    """The timed oracle sample; also returns the oracle's results."""
     threads = os.cpu_count() or 1
-    v, dt, _ = oracle_sample(n_sets, threads)
+    v, dt, out = oracle_sample(n_sets, threads)
     return dict(value=v, unit="solves/s", cores=threads, kind="oracle",
                 sample="sets 0..%d of the workload x %d ICs (%d solves), FP64 DP5 rtol 1e-10 + "
-                       "Newton polish + dedupe, %.1f s" % (n_sets - 1, N_ICS, n_sets * N_ICS, dt))
+                       "Newton polish + dedupe, %.1f s" % (n_sets - 1, N_ICS, n_sets * N_ICS, dt)), out
+
+
+def parity_figures(gpu, orc, G, k):
+    """Per-result error of the GPU path against the oracle on the same sets:
+    raw FP32 states on the G/k scale, polished states relative (floor
+    1e-6 G/k), over solves converged on both sides at the same fixed point
+    (G/k-normalised distance <= 1e-2 raw, 1e-5 polished); the basin-mismatch
+    rate (both converged, different fixed points), the status agreement and
+    the share of sets with the same number of distinct steady states."""
+    import numpy as np
+    G = G[:, None, :]
+    k = k[:, None, :]
+    vo = orc["states"] * k / G
+    res = {}
+    for name, states, status, tol in (("fp32_raw", gpu["raw_states"], gpu["raw_status"], 1e-2),
+                                      ("fp32_polish", gpu["states"], gpu["status"], 1e-5)):
+        both = (status == 0) & (orc["status"] == 0)
+        vg = states * k / G
+        dist = np.abs(vg - vo).max(axis=2)
+        same = both & (dist <= tol)
+        if name == "fp32_raw":
+            err = np.abs(vg - vo).max(axis=2)
+        else:
+            err = (np.abs(states - orc["states"]) / np.maximum(np.abs(orc["states"]), 1e-6 * G)).max(axis=2)
+        e = err[same]
+        res[name] = dict(max=float(e.max()) if e.size else None,
+                         p999=float(np.quantile(e, 0.999)) if e.size else None,
+                         compared=int(same.sum()), basin_mismatch_rate=float((both & ~same).mean()),
+                         status_agree=float((status == orc["status"]).mean()))
+    res["fp32_polish"]["error"] = "relative, floor 1e-6 G/k"
+    res["fp32_raw"]["error"] = "G/k-normalised"
+    res["n_unique_agree"] = float((gpu["n_unique"] == orc["n_unique"]).mean())
+    return res
 
 
 def run_reference(args):
@@ -345,6 +379,20 @@ def run_native(args):
     clocks = clk.stop()
     elapsed_ms = shard.max_over_ranks(start.elapsed_time(stop), dev)
     per_kernel = np.array([[e[i].elapsed_time(e[i + 1]) for i in range(4)] for e in evs])  # ms
+
+    # the first sets of one more (untimed) step, raw and polished, for the
+    # per-result comparison with the oracle
+    snap = None
+    if rank == 0 and not args.no_cpu_baseline and ws == 1:
+        P = min(S, args.cpu_sets)
+        h.sample_params(w["param_seed"], S, I, set0=set0, params=params, ic_unit=ic, stream=stream)
+        h.integrate(params, ic, opts=opts, stream=stream, out=out)
+        snap = dict(raw_states=out["states"][:P].cpu().numpy(), raw_status=out["status"][:P].cpu().numpy())
+        h.polish(params, out["states"], out["status"], out["err_est"], opts=popts, stream=stream)
+        h.unique_states(params, out["states"], out["status"], stream=stream, out=(sid, nu))
+        G, k = (x[:P].cpu().numpy() for x in h.unpack_params(params[:P])[:2])
+        snap.update(states=out["states"][:P].cpu().numpy(), status=out["status"][:P].cpu().numpy(),
+                    n_unique=nu[:P].cpu().numpy(), G=G, k=k)
     kern_ms = per_kernel.mean(axis=0)
 
     # algorithmic work of the FP32 integrator (per step attempt of one solve)
@@ -450,7 +498,11 @@ def run_native(args):
         if args.serve_seconds > 0 and ws == 1:
             line["serving"] = serving_measurement(dev, args.serve_seconds, args.serve_rate)
         if not args.no_cpu_baseline and ws == 1:
-            line["cpu_baseline"] = cpu_baseline(args.cpu_sets)
+            line["cpu_baseline"], orc = cpu_baseline(args.cpu_sets)
+            P = snap["G"].shape[0]
+            orc = {kk: (v[:P] if hasattr(v, "shape") else v) for kk, v in orc.items()}
+            line["parity"] = dict(sets=P, solves=P * I, against="the oracle (FP64 CPU, rtol 1e-10, Newton "
+                                  "polish) on the same sets", **parity_figures(snap, orc, snap["G"], snap["k"]))
         print(json.dumps(line))
     h.close()
     if ws > 1:
