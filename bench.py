@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--sets", type=int, default=N_SETS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sets", type=int, default=800, help="sets of the oracle sample")
+    ap.add_argument("--cpu-sets", type=int, default=1000, help="sets of the oracle sample (sets 0..n-1)")
     ap.add_argument("--fp64-sets", type=int, default=5000, help="sets of the FP64 GPU solver sample")
     ap.add_argument("--serve-seconds", type=float, default=6.0,
                     help="length of the Poisson request stream of the serving measurement (0: skip)")

@@ -92,7 +92,7 @@ typedef struct {
  * steady state, optional time points).  grins_solver_default_opts fills:
  * FP32 + polish, rtol 1e-6, atol 1e-9, t0 0, t_end 200, ss_tol 1e-6,
  * max_steps 100000, no time grid, polish_tol 1e-13, polish_iters 16,
- * polish_max_move 1e-2. */
+ * polish_max_move 1e-2, ss_tighten 0.3. */
 typedef struct {
     int32_t precision;         /* GRINS_FP32 or GRINS_FP64 integration */
     int32_t polish;            /* 1: FP64 Newton polish of each converged state */
@@ -108,6 +108,11 @@ typedef struct {
                                   grins_racipe_polish) */
     double polish_max_move;    /* reject a polish that moves a G/k-normalised
                                   coordinate by more than this */
+    double ss_tighten;         /* once a solve's residual max_i |dx_i/dt| / (G_i/k_i) is
+                                  below 10 ss_tol, its error tolerances are scaled by
+                                  this factor (0 < ss_tighten <= 1; 1 = never): with
+                                  ss_tol near rtol, the integrator's own error level
+                                  would otherwise sit at the steady-state threshold */
 } grins_solver_opts;
 
 void grins_racipe_default_ranges(grins_racipe_ranges *r);

@@ -52,7 +52,7 @@ class grins_solver_opts(C.Structure):
                 ("max_steps", C.c_int64),
                 ("t_grid", C.POINTER(C.c_double)), ("n_t", C.c_int32),
                 ("polish_tol", C.c_double), ("polish_iters", C.c_int32),
-                ("polish_max_move", C.c_double)]
+                ("polish_max_move", C.c_double), ("ss_tighten", C.c_double)]
 
 
 class grins_racipe_job(C.Structure):

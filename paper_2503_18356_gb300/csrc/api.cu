@@ -127,6 +127,7 @@ extern "C" void grins_solver_default_opts(grins_solver_opts *o)
     o->polish_tol = 1e-13;
     o->polish_iters = 16;
     o->polish_max_move = 1e-2;
+    o->ss_tighten = 0.3;
 }
 
 extern "C" const char *grins_last_error(void) { return g_last_error.c_str(); }
@@ -690,6 +691,15 @@ static PolishArgs polish_args(const grins_racipe *h, const grins_solver_opts *o,
 
 static GrpTopo grp_topo(const grins_racipe *h) { return h->grp.topo(); }
 
+// Tolerance tightening near steady state: below a residual of 10 ss_tol the
+// squared error norm is scaled by 1 / ss_tighten^2 (tolerances times
+// ss_tighten).
+static void set_tighten(IntegrateArgs *a, const grins_solver_opts *o)
+{
+    a->ss_near = 10.0 * o->ss_tol;
+    a->ss_gain = 1.0 / (o->ss_tighten * o->ss_tighten);
+}
+
 // The FP32 lane-group kernel for h: sets a->grp and a->grp_jit to the
 // kernel compiled for this network -- records in registers when the
 // register layout exists, else records in shared memory (GRINS_JIT_KIND=grp
@@ -763,6 +773,7 @@ extern "C" grins_status grins_racipe_integrate(grins_racipe_t h, const grins_sol
     if (!std::isfinite(o->t0) || !std::isfinite(o->t_end) || !(o->t_end > o->t0))
         return fail(GRINS_E_INVALID_ARG, "integrate: need finite t0 < t_end");
     if (!(o->ss_tol >= 0)) return fail(GRINS_E_INVALID_ARG, "integrate: ss_tol < 0");
+    if (!(o->ss_tighten > 0 && o->ss_tighten <= 1)) return fail(GRINS_E_INVALID_ARG, "integrate: need 0 < ss_tighten <= 1");
     if (o->max_steps < 1) return fail(GRINS_E_INVALID_ARG, "integrate: max_steps < 1");
     if (o->n_t < 0 || (o->n_t > 0 && !o->t_grid)) return fail(GRINS_E_INVALID_ARG, "integrate: bad time grid");
     if ((o->n_t > 0) != (d_series != nullptr) && n_sets > 0)
@@ -799,6 +810,7 @@ extern "C" grins_status grins_racipe_integrate(grins_racipe_t h, const grins_sol
     a.ic_unit = d_ic_unit;
     a.n_ics = n_ics;
     a.rtol = o->rtol; a.atol = o->atol; a.t0 = o->t0; a.t_end = o->t_end; a.ss_tol = o->ss_tol;
+    set_tighten(&a, o);
     a.max_steps = o->max_steps;
     a.t_grid = h->d_grid;
     a.n_t = o->n_t;
@@ -912,6 +924,7 @@ static void plan_args(grins_racipe_plan *p, int slot_extra, int sample)
         a.ic_unit = j.d_ic_unit;
         a.n_ics = j.n_ics;
         a.rtol = o->rtol; a.atol = o->atol; a.t0 = o->t0; a.t_end = o->t_end; a.ss_tol = o->ss_tol;
+    set_tighten(&a, o);
         a.max_steps = o->max_steps;
         a.t_grid = nullptr;
         a.n_t = 0;
@@ -1055,6 +1068,7 @@ extern "C" grins_status grins_racipe_plan_create(const grins_solver_opts *o, con
     if (!std::isfinite(o->t0) || !std::isfinite(o->t_end) || !(o->t_end > o->t0))
         return fail(GRINS_E_INVALID_ARG, "plan_create: need finite t0 < t_end");
     if (!(o->ss_tol >= 0) || o->max_steps < 1) return fail(GRINS_E_INVALID_ARG, "plan_create: bad ss_tol or max_steps");
+    if (!(o->ss_tighten > 0 && o->ss_tighten <= 1)) return fail(GRINS_E_INVALID_ARG, "plan_create: need 0 < ss_tighten <= 1");
     if (o->n_t != 0) return fail(GRINS_E_INVALID_ARG, "plan_create: plans do not write time series");
     if (o->polish && !polish_opts_ok(o)) return fail(GRINS_E_INVALID_ARG, "plan_create: bad polish options");
     int dev = -1;
@@ -1329,6 +1343,7 @@ grins_status server_launch(grins_racipe_server *sv, ServerRequest &r)
     a.ic_unit = r.ic;
     a.n_ics = I;
     a.rtol = o->rtol; a.atol = o->atol; a.t0 = o->t0; a.t_end = o->t_end; a.ss_tol = o->ss_tol;
+    set_tighten(&a, o);
     a.max_steps = o->max_steps;
     a.states = r.states; a.status = r.status; a.t_final = r.t_final; a.n_steps = r.n_steps;
     a.queue = r.words;
@@ -1486,6 +1501,7 @@ extern "C" grins_status grins_racipe_server_submit(grins_racipe_server_t sv, gri
     if (o->precision != GRINS_FP32 && o->precision != GRINS_FP64)
         return fail(GRINS_E_INVALID_ARG, "server_submit: unknown precision");
     if (!(o->rtol > 0) || !(o->atol > 0) || !(o->t_end > o->t0) || o->max_steps < 1 || !(o->ss_tol >= 0) ||
+        !(o->ss_tighten > 0 && o->ss_tighten <= 1) ||
         (o->polish && !polish_opts_ok(o)))
         return fail(GRINS_E_INVALID_ARG, "server_submit: bad solver options");
     if (!(dedupe_tol >= 0)) return fail(GRINS_E_INVALID_ARG, "server_submit: dedupe_tol < 0");
@@ -1693,6 +1709,8 @@ extern "C" grins_status grins_racipe_integrate_static(grins_racipe_t h, const gr
     if (!std::isfinite(o->t0) || !std::isfinite(o->t_end) || !(o->t_end > o->t0))
         return fail(GRINS_E_INVALID_ARG, "integrate_static: need finite t0 < t_end");
     if (!(o->ss_tol >= 0)) return fail(GRINS_E_INVALID_ARG, "integrate_static: ss_tol < 0");
+    if (!(o->ss_tighten > 0 && o->ss_tighten <= 1))
+        return fail(GRINS_E_INVALID_ARG, "integrate_static: need 0 < ss_tighten <= 1");
     if (o->max_steps < 1) return fail(GRINS_E_INVALID_ARG, "integrate_static: max_steps < 1");
     if (o->n_t < 0 || (o->n_t > 0 && !o->t_grid))
         return fail(GRINS_E_INVALID_ARG, "integrate_static: bad time grid");
@@ -1730,6 +1748,7 @@ extern "C" grins_status grins_racipe_integrate_static(grins_racipe_t h, const gr
     a.ic_unit = d_ic_unit;
     a.n_ics = n_ics;
     a.rtol = o->rtol; a.atol = o->atol; a.t0 = o->t0; a.t_end = o->t_end; a.ss_tol = o->ss_tol;
+    set_tighten(&a, o);
     a.max_steps = o->max_steps;
     a.t_grid = grid;
     a.n_t = o->n_t;

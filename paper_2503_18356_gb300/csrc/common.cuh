@@ -92,6 +92,8 @@ struct IntegrateArgs {
     const double *ic_unit;       // [n_ics][N]
     int32_t n_ics;
     double rtol, atol, t0, t_end, ss_tol;
+    double ss_near;              // residual below which the tolerances tighten (10 ss_tol)
+    double ss_gain;              // factor on the squared error norm there (1 / ss_tighten^2)
     int64_t max_steps;
     const double *t_grid;        // device copy, [n_t]
     int32_t n_t;

@@ -99,6 +99,7 @@ dp5_generic_kernel(const IntegrateArgs a)
     Real t = 0, h = 0;
     int steps = 0, gidx = 0, yb = 0, kb1 = 2;
     bool need_k1 = false, rejected = false, exhausted = false;
+    bool near = false;                 // residual below ss_near: tolerances tightened
 
     auto slot_ptr = [&](int s) -> unsigned char * {
         if (!GRINS_OK_IDX(s >= 0 && s < S, 13, s)) s = 0;
@@ -177,7 +178,7 @@ dp5_generic_kernel(const IntegrateArgs a)
                     for (int i = 0; i < N; ++i) V(yb, i) = (Real)((u[i] * Gd[i]) / kdd[i]);
                     t = (Real)a.t0;
                     steps = 0; gidx = 0;
-                    need_k1 = true; rejected = false;
+                    need_k1 = true; rejected = false; near = false;
                     if (a.n_t > 0) {
                         while (gidx < a.n_t && a.t_grid[gidx] <= a.t0) { write_series(gidx); ++gidx; }
                     }
@@ -283,6 +284,7 @@ dp5_generic_kernel(const IntegrateArgs a)
                 finite = finite && isfinite(z) && isfinite(k7);
             }
             en *= invN;
+            if (near) en *= (Real)a.ss_gain;
             ++steps;
             if (!finite || !isfinite(en)) {
                 done = true; st_code = GRINS_SS_NONFINITE;
@@ -301,7 +303,9 @@ dp5_generic_kernel(const IntegrateArgs a)
                 h = hh * fac;
                 rejected = false;
                 if (!done) {
-                    if (residual(kb1, sp) < ss_tol) { done = true; st_code = GRINS_SS_CONVERGED; }
+                    const Real res = residual(kb1, sp);
+                    near = res < (Real)a.ss_near;
+                    if (res < ss_tol) { done = true; st_code = GRINS_SS_CONVERGED; }
                     else if (t >= t_end) { done = true; st_code = GRINS_SS_TEND; }
                 }
             } else {

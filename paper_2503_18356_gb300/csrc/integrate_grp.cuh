@@ -240,6 +240,8 @@ __device__ __forceinline__ void grp_body(const IntegrateArgs &a, unsigned char *
     long long my_set = 0;
     float t = 0.0f, h = 0.0f;
     int steps = 0, gidx = 0, buf = 0;
+    bool near = false;               // residual below ss_near: tolerances tightened
+    const float ss_near = (float)a.ss_near, ss_gain = (float)a.ss_gain;
     bool need_k1 = false, rejected = false, exhausted = false;
     // y: state; k1..k6: stage derivatives; z: stage input, overwritten by
     // the right-hand side.  The last stage input (the fifth-order solution)
@@ -391,6 +393,7 @@ __device__ __forceinline__ void grp_body(const IntegrateArgs &a, unsigned char *
                         gidx = 0;
                         need_k1 = true;
                         rejected = false;
+                        near = false;
 #pragma unroll 1
                         while (gidx < a.n_t && a.t_grid[gidx] <= a.t0) { write_series(gidx); ++gidx; }
                     }
@@ -569,6 +572,7 @@ __device__ __forceinline__ void grp_body(const IntegrateArgs &a, unsigned char *
             }
         }
         en = grp_sum(en, L) * invN;                   // squared RMS error norm
+        if (near) en *= ss_gain;
         finite = grp_all(finite, L);
         const float res = residual(z, sp);
 
@@ -592,6 +596,7 @@ __device__ __forceinline__ void grp_body(const IntegrateArgs &a, unsigned char *
                 if (rejected) fac = fminf(fac, 1.0f);
                 h = hh * fac;
                 rejected = false;
+                near = res < ss_near;
                 if (!done) {
                     if (res < ss_tol) { done = true; st_code = GRINS_SS_CONVERGED; }
                     else if (t >= t_end) { done = true; st_code = GRINS_SS_TEND; }

@@ -257,6 +257,8 @@ __device__ __forceinline__ void rr_body(const IntegrateArgs &a)
     bool working = false, exhausted = false;
     float t = 0.0f, h = 0.0f;
     int steps = 0, gidx = 0;
+    bool near = false;               // residual below ss_near: tolerances tightened
+    const float ss_near = (float)a.ss_near, ss_gain = (float)a.ss_gain;
     bool need_k1 = false, rejected = false;
     float y[NPL], k1[NPL], k2[NPL], k3[NPL], k4[NPL], k5[NPL], k6[NPL], z[NPL];
 #pragma unroll
@@ -303,6 +305,7 @@ __device__ __forceinline__ void rr_body(const IntegrateArgs &a)
         gidx = 0;
         need_k1 = true;
         rejected = false;
+        near = false;
         working = true;
 #pragma unroll 1
         while (gidx < a.n_t && a.t_grid[gidx] <= a.t0) { write_series(gidx); ++gidx; }
@@ -426,7 +429,8 @@ __device__ __forceinline__ void rr_body(const IntegrateArgs &a)
             en += qq * qq;
             finite = finite && isfinite(z[r]) && isfinite(k2[r]);
         }
-        en = grp_sum(en, L) * invN;               // squared RMS error norm
+        en = grp_sum(en, L) * invN;                   // squared RMS error norm
+        if (near) en *= ss_gain;
         finite = grp_all(finite, L);
         const float res = residual(z);
 
@@ -450,6 +454,7 @@ __device__ __forceinline__ void rr_body(const IntegrateArgs &a)
                 if (rejected) fac = fminf(fac, 1.0f);
                 h = hh * fac;
                 rejected = false;
+                near = res < ss_near;
                 if (!done) {
                     if (res < ss_tol) { done = true; st_code = GRINS_SS_CONVERGED; }
                     else if (t >= t_end) { done = true; st_code = GRINS_SS_TEND; }
