@@ -104,7 +104,9 @@ struct JitEntry {
     cudaKernel_t kern = nullptr;
 };
 
-// Result of one NVRTC compile and load.
+// Result of one NVRTC compile and load (the compile log's spill count
+// decides whether a register-record kernel is compiled again with fewer
+// resident blocks).
 struct JitBuild {
     bool ok = false;
     std::string why;
@@ -226,9 +228,8 @@ int log_spill_bytes(const std::string &log)
 JitBuild jit_compile(const std::string &src)
 {
     JitBuild b;
-    JitBuild *e = &b;
     NvrtcApi &api = nvrtc();
-    if (!api.ok) { e->why = api.why; return b; }
+    if (!api.ok) { b.why = api.why; return b; }
     std::vector<const char *> hdr_src, hdr_name;
     for (int i = 0; i < kJitSourceCount; ++i) {
         hdr_src.push_back(kJitSources[i]);
@@ -239,7 +240,7 @@ JitBuild jit_compile(const std::string &src)
     nvrtcProgram prog = nullptr;
     nvrtcResult r = api.create(&prog, src.c_str(), "grins_grp_ct.cu", (int)hdr_src.size(), hdr_src.data(),
                                hdr_name.data());
-    if (r != NVRTC_SUCCESS) { e->why = std::string("nvrtcCreateProgram: ") + api.err(r); return b; }
+    if (r != NVRTC_SUCCESS) { b.why = std::string("nvrtcCreateProgram: ") + api.err(r); return b; }
     const char *opts[] = {"--gpu-architecture=sm_103a", "--std=c++17", "-lineinfo", "-default-device",
                           "--ptxas-options=-v"};
     r = api.compile(prog, 5, opts);
@@ -248,20 +249,20 @@ JitBuild jit_compile(const std::string &src)
     std::string log(n, '\0');
     if (n) api.log(prog, &log[0]);
     if (r != NVRTC_SUCCESS) {
-        e->why = std::string("nvrtcCompileProgram: ") + api.err(r) + "\n" + log;
+        b.why = std::string("nvrtcCompileProgram: ") + api.err(r) + "\n" + log;
         api.destroy(&prog);
         return b;
     }
-    e->spill_bytes = log_spill_bytes(log);
+    b.spill_bytes = log_spill_bytes(log);
     n = 0;
     api.cubin_size(prog, &n);
     std::vector<char> cubin(n);
     api.cubin(prog, cubin.data());
     api.destroy(&prog);
-    cudaError_t ce = cudaLibraryLoadData(&e->lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
-    if (ce == cudaSuccess) ce = cudaLibraryGetKernel(&e->kern, e->lib, "grins_grp_ct");
-    if (ce != cudaSuccess) { e->why = std::string("loading the compiled kernel: ") + cudaGetErrorString(ce); return b; }
-    e->ok = true;
+    cudaError_t ce = cudaLibraryLoadData(&b.lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+    if (ce == cudaSuccess) ce = cudaLibraryGetKernel(&b.kern, b.lib, "grins_grp_ct");
+    if (ce != cudaSuccess) { b.why = std::string("loading the compiled kernel: ") + cudaGetErrorString(ce); return b; }
+    b.ok = true;
     return b;
 }
 
