@@ -26,6 +26,9 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+# the headline metric, the same string on both arms (the reference arm times
+# the oracle on a bounded sample of the same workload)
+METRIC = "RACIPE steady-state solves/s (22-node network, FP32 + FP64 polish)"
 N_SETS = 100_000
 N_ICS = 10
 TOL = dict(rtol=1e-6, atol=1e-9, t_end=200.0, ss_tol=1e-6)
@@ -188,7 +191,7 @@ def run_reference(args):
     total = args.cpu_sets * N_ICS * args.steps
     value = total / sum(times)
     cores = os.cpu_count() or 1
-    line = dict(impl="reference", metric="RACIPE steady-state solves/s (22-node network)",
+    line = dict(impl="reference", metric=METRIC,
                 value=value, unit="solves/s", n_gpus=args.gpus, steps=args.steps, warmup=args.warmup,
                 ms_per_step=1000 * sum(times) / args.steps, higher_is_better=True, scaling="weak",
                 vs_baseline=None, dtype="f64", data="synthetic",
@@ -464,7 +467,7 @@ def run_native(args):
 
     if rank == 0:
         line = dict(
-            metric="RACIPE steady-state solves/s (22-node network, FP32 + FP64 polish)",
+            metric=METRIC,
             value=value, unit="solves/s", n_gpus=ws, steps=args.steps, warmup=max(3, args.warmup),
             ms_per_step=elapsed_ms / args.steps, higher_is_better=True, scaling="weak",
             vs_baseline=None, dtype="f32", data="synthetic",
