@@ -691,6 +691,23 @@ static PolishArgs polish_args(const grins_racipe *h, const grins_solver_opts *o,
 
 static GrpTopo grp_topo(const grins_racipe *h) { return h->grp.topo(); }
 
+// The FP64 integrator for h: the register-record kernel compiled for this
+// network in FP64 (power-table edge terms) when the register layout exists,
+// else the generic FP64 kernel (grp_jit null).  compile = false only looks
+// up a kernel an earlier call compiled.
+static void pick_fp64_kernel(const grins_racipe *h, IntegrateArgs *a, bool compile, std::string *why)
+{
+    a->grp = h->grp.topo();
+    a->grp_jit = nullptr;
+    std::string w = h->rr.L > 0 ? "" : "no register layout";
+    if (h->rr.L > 0) {
+        const GrpTopo g = h->rr.topo();
+        const void *k = compile ? grp_jit_kernel(g, kJitRegisters64, &w) : grp_jit_lookup(g, kJitRegisters64);
+        if (k) { a->grp = g; a->grp_jit = k; }
+    }
+    if (why) *why = w;
+}
+
 // Tolerance tightening near steady state: below a residual of 10 ss_tol the
 // squared error norm is scaled by 1 / ss_tighten^2 (tolerances times
 // ss_tighten).
@@ -821,11 +838,10 @@ extern "C" grins_status grins_racipe_integrate(grins_racipe_t h, const grins_sol
     a.slots = slots_for(n_ics);
     a.smem_limit = (int32_t)h->smem_optin;
     a.grp = grp_topo(h);
-    if (o->precision == GRINS_FP32) {
-        pick_fp32_kernel(h, &a, true, &h->jit_why);
-        h->jit_used = a.grp_jit != nullptr;
-        h->used_L = a.grp.L; h->used_R = a.grp.R; h->used_P = a.grp.P;
-    }
+    if (o->precision == GRINS_FP32) pick_fp32_kernel(h, &a, true, &h->jit_why);
+    else pick_fp64_kernel(h, &a, true, &h->jit_why);
+    h->jit_used = a.grp_jit != nullptr;
+    h->used_L = a.grp.L; h->used_R = a.grp.R; h->used_P = a.grp.P;
 
     CUDA_TRY(cudaMemsetAsync(h->d_queue, 0, 2 * sizeof(unsigned long long), st), "integrate: queue reset");
     cudaError_t le;
@@ -1352,6 +1368,7 @@ grins_status server_launch(grins_racipe_server *sv, ServerRequest &r)
     a.smem_limit = (int32_t)h->smem_optin;
     a.grp = grp_topo(h);
     if (o->precision == GRINS_FP32) pick_fp32_kernel(h, &a, false, nullptr);   // never compiles here
+    else pick_fp64_kernel(h, &a, false, nullptr);
     CUDA_TRY(cudaMemsetAsync(r.words, 0, 32, st), "server: counter reset");
     cudaError_t le = o->precision == GRINS_FP32 ? launch_integrate_fp32(a, st, h->num_sms)
                                                 : launch_integrate_fp64(a, st, h->num_sms);
@@ -1525,12 +1542,16 @@ extern "C" grins_status grins_racipe_server_submit(grins_racipe_server_t sv, gri
     // now, so that it overlaps the queueing; the worker admits them once it
     // is done (the kernel the integrate call would pick: records in
     // registers when that layout exists, else records in shared memory)
-    if (sv->jit && o->precision == GRINS_FP32 &&
-        (double)n_sets * n_ics * std::max(net->E, 1) >= sv->jit_min_work) {
+    if (sv->jit && (double)n_sets * n_ics * std::max(net->E, 1) >= sv->jit_min_work) {
         const char *ev = std::getenv("GRINS_JIT_KIND");
         const bool want_shared = ev && std::string(ev) == "grp";
-        if (!want_shared && net->rr.L > 0) { req->jit_topo = net->rr.topo(); req->jit_kind = kJitRegisters; }
-        else { req->jit_topo = net->grp.topo(); req->jit_kind = kJitShared; }
+        if (o->precision == GRINS_FP64) {
+            if (net->rr.L > 0) { req->jit_topo = net->rr.topo(); req->jit_kind = kJitRegisters64; }
+        } else if (!want_shared && net->rr.L > 0) {
+            req->jit_topo = net->rr.topo(); req->jit_kind = kJitRegisters;
+        } else {
+            req->jit_topo = net->grp.topo(); req->jit_kind = kJitShared;
+        }
         req->jit_wait = grp_jit_prefetch(req->jit_topo, req->jit_kind) == 0;
     }
     CUDA_TRY(cudaEventCreateWithFlags(&req->done, cudaEventDisableTiming), "server_submit: event");
@@ -1760,6 +1781,7 @@ extern "C" grins_status grins_racipe_integrate_static(grins_racipe_t h, const gr
     a.smem_limit = (int32_t)h->smem_optin;
     a.grp = grp_topo(h);
     if (o->precision == GRINS_FP32) pick_fp32_kernel(h, &a, false, nullptr);   // only kernels an earlier call loaded
+    else pick_fp64_kernel(h, &a, false, nullptr);
 
     // the array keeps the previous call's counters: clear them first
     CUDA_TRY(cudaMemsetAsync(words, 0, kStaticWords * sizeof(unsigned long long), st),

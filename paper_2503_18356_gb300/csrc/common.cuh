@@ -126,7 +126,7 @@ struct BatchArgs {
 // first use (grp_jit_kernel) or only looked up (grp_jit_lookup); kind is
 // kJitRegisters (records in registers) or kJitShared (records in shared
 // memory).  The returned pointer is an opaque handle for launch_grp_jit.
-enum JitKind { kJitShared = 0, kJitRegisters = 1 };
+enum JitKind { kJitShared = 0, kJitRegisters = 1, kJitRegisters64 = 2 };
 const void *grp_jit_kernel(const GrpTopo &g, int kind, std::string *why);
 const void *grp_jit_lookup(const GrpTopo &g, int kind);
 // Starts (once) a background compile for layout g: 1 ready, 0 compiling, -1

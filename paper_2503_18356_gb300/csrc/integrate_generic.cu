@@ -45,6 +45,12 @@ cudaError_t launch_integrate_fp32(const IntegrateArgs &a, cudaStream_t st, int n
 
 cudaError_t launch_integrate_fp64(const IntegrateArgs &a, cudaStream_t st, int num_sms)
 {
+    // the FP64 register-record kernel compiled for this network when there
+    // is one; the generic kernel otherwise
+    if (a.grp_jit) {
+        const cudaError_t e = launch_grp_jit(a.grp_jit, a, st, num_sms);
+        if (e != cudaErrorInvalidConfiguration) return e;
+    }
     return launch_dp5_generic<double>(a, st, num_sms);
 }
 

@@ -80,8 +80,12 @@ struct GrpLayout {
 };
 
 // Dynamic shared memory of one warp of the register-record kernel
-// (integrate_rr.cuh): two gather buffers [rows][32] float.
-__host__ __device__ constexpr int rr_warp_bytes(int rows) { return 2 * rows * kWarp * 4; }
+// (integrate_rr.cuh): two gather buffers [planes][rows][32] entries of el
+// bytes (FP32: 1 plane of log2 x; FP64: 6 planes x .. x^6).
+__host__ __device__ constexpr int rr_warp_bytes(int rows, int planes, int el)
+{
+    return 2 * planes * rows * kWarp * el;
+}
 
 // Lanes of a group are j-major: lane = j * (32 / L) + g, so lane j of every
 // group sits in one contiguous block and a group's lanes are 32/L apart.

@@ -20,6 +20,13 @@
 // compile-time constants generated for the network, and the stages of an
 // attempt are written out, so every register array is indexed by constants
 // and the gather buffer of each right-hand side is an immediate offset.
+//
+// FP64 instantiation (the plain FP64 GPU solver): the same body with double
+// states and records; its edge term is exact rather than log-domain -- the
+// gather buffer holds x, x^2 .. x^6 of every stage value and an edge forms
+// p = x^n (1/T)^n with one multiply (n <= 6, Table 1; an edge with a larger
+// n makes its solve non-finite), numerators and denominators divided once
+// per eight factors.
 #pragma once
 
 #include "integrate_grp.cuh"
@@ -184,9 +191,153 @@ __device__ __forceinline__ void rr_rhs(const RrRecs<NPL> &q, float (&z)[NPL], un
     rr_rows<BO, 0, NPL>(q, z);
 }
 
+// ------------------------------------------------------------------ FP64
+constexpr int kRr64Pow = 6;                   // planes x .. x^6 of the FP64 gather buffer
+
+template <int OFF>
+__device__ __forceinline__ double rr_lds64(unsigned addr)
+{
+    double v;
+    asm volatile("ld.shared.f64 %0, [%1+%2];" : "=d"(v) : "r"(addr), "n"(OFF));
+    return v;
+}
+
+template <int OFF>
+__device__ __forceinline__ void rr_sts64(unsigned addr, double v)
+{
+    asm volatile("st.shared.f64 [%0+%1], %2;" ::"r"(addr), "n"(OFF), "d"(v) : "memory");
+}
+
+template <int NPL>
+struct RrRecs64 {
+    unsigned ga[kRrPa];                 // shared address of each position's x^n entry (buffer 0)
+    double itn[kRrPa], u[kRrPa];        // (1/T)^n, 1/lambda (neutral: 0, 1)
+    double Gp[NPL], k[NPL], kg[NPL];
+};
+
+// Product of the D factors of a row from position P0, one division per
+// eight factors (p <= 2^120, so eight stay finite).
+template <int BO, int P0, int D, int I, int NPL>
+__device__ __forceinline__ void rr64_acc(const RrRecs64<NPL> &q, double &prod, double &num, double &den)
+{
+    if constexpr (I < D) {
+        const double p = fmin(rr_lds64<BO>(q.ga[P0 + I]) * q.itn[P0 + I], 0x1.0p120);
+        num *= p + q.u[P0 + I];
+        den = fma(den, p, den);
+        if constexpr (I % 8 == 7) { prod *= num / den; num = 1.0; den = 1.0; }
+        rr64_acc<BO, P0, D, I + 1, NPL>(q, prod, num, den);
+    }
+}
+
+template <int BO, int r, int NPL>
+__device__ __forceinline__ void rr64_rows(const RrRecs64<NPL> &q, double (&z)[NPL])
+{
+    if constexpr (r < kGrpCtRows && r < NPL) {
+        constexpr int D = GrpRowCt<r>::deg;
+        double prod = 1.0, num = 1.0, den = 1.0;
+        rr64_acc<BO, GrpRowCt<r>::off, D, 0, NPL>(q, prod, num, den);
+        if constexpr (D % 8 != 0) prod *= num / den;
+        z[r] = fma(q.Gp[r], prod, -q.k[r] * z[r]);
+        rr64_rows<BO, r + 1, NPL>(q, z);
+    }
+}
+
+// x .. x^6 of this lane's stage values (x clamped to [0, 1e6]) into plane q
+// of its column of the buffer at BO
+template <int BO, int r, int NPL>
+__device__ __forceinline__ void rr64_put(const double (&z)[NPL], unsigned own)
+{
+    if constexpr (r < kGrpCtRows && r < NPL) {
+        constexpr int PL = NPL * kWarp * 8, RO = r * kWarp * 8;
+        const double x = fmin(fmax(z[r], 0.0), 1e6);
+        const double x2 = x * x, x4 = x2 * x2;
+        rr_sts64<BO + RO>(own, x);
+        rr_sts64<BO + PL + RO>(own, x2);
+        rr_sts64<BO + 2 * PL + RO>(own, x2 * x);
+        rr_sts64<BO + 3 * PL + RO>(own, x4);
+        rr_sts64<BO + 4 * PL + RO>(own, x4 * x);
+        rr_sts64<BO + 5 * PL + RO>(own, x2 * x4);
+        rr64_put<BO, r + 1, NPL>(z, own);
+    }
+}
+
+template <int B, int NPL>
+__device__ __forceinline__ void rr_rhs(const RrRecs64<NPL> &q, double (&z)[NPL], unsigned own)
+{
+    constexpr int BO = B * kRr64Pow * NPL * kWarp * 8;
+    rr64_put<BO, 0, NPL>(z, own);
+    rr_syncwarp();
+    rr64_rows<BO, 0, NPL>(q, z);
+}
+
+// FP64 records of row r from parameter block blk; col = this group's column
+// address of plane 0 in buffer 0.
+template <int r, int NPL, int L>
+__device__ __forceinline__ void rr_load_rows(RrRecs64<NPL> &q, const IntegrateArgs &a, const unsigned char *blk,
+                                             int j, unsigned col)
+{
+    if constexpr (r < kGrpCtRows && r < NPL) {
+        constexpr int D = GrpRowCt<r>::deg, P0 = GrpRowCt<r>::off;
+        const double *Td = reinterpret_cast<const double *>(blk + a.L.off_T);
+        const double *ld = reinterpret_cast<const double *>(blk + a.L.off_lam);
+        const uint8_t *nn = blk + a.L.off_n;
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            const int e = a.grp.pos_edge[(P0 + d) * L + j];
+            double itn = 0.0, u = 1.0;
+            int plane = 0;
+            if (e >= 0) {
+                const int ne = nn[e];
+                const double it = 1.0 / Td[e];
+                double pn = it;
+#pragma unroll 1
+                for (int m = 1; m < ne; ++m) pn *= it;
+                const bool ok = ne >= 1 && ne <= kRr64Pow;
+                itn = ok ? fmin(pn, 1e30) : __longlong_as_double(0x7ff8000000000000ll);
+                plane = ok ? ne - 1 : 0;
+                u = 1.0 / ld[e];
+            }
+            q.itn[P0 + d] = itn;
+            q.u[P0 + d] = u;
+            q.ga[P0 + d] = col + 2 * a.grp.pos_off[(P0 + d) * L + j] + plane * (NPL * kWarp * 8);
+        }
+        rr_load_rows<r + 1, NPL, L>(q, a, blk, j, col);
+    }
+}
+
+// ------------------------------------------------------------ by precision
+template <typename Real, int NPL> struct RrSel { using Recs = RrRecs<NPL>; static constexpr int planes = 1; };
+template <int NPL> struct RrSel<double, NPL> { using Recs = RrRecs64<NPL>; static constexpr int planes = kRr64Pow; };
+
+__device__ __forceinline__ float rr_div(float a, float b) { return div_approx(a, b); }
+__device__ __forceinline__ double rr_div(double a, double b) { return a / b; }
+__device__ __forceinline__ float rr_abs(float a) { return fabsf(a); }
+__device__ __forceinline__ double rr_abs(double a) { return fabs(a); }
+__device__ __forceinline__ float rr_max(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double rr_max(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ float rr_min(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double rr_min(double a, double b) { return fmin(a, b); }
+__device__ __forceinline__ float rr_sqrt(float a) { return sqrtf(a); }
+__device__ __forceinline__ double rr_sqrt(double a) { return sqrt(a); }
+
+template <typename Real>
+__device__ __forceinline__ Real rr_gsum(Real v, int L)
+{
+    for (int o = kWarp / L; o < kWarp; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <typename Real>
+__device__ __forceinline__ Real rr_gmax(Real v, int L)
+{
+    for (int o = kWarp / L; o < kWarp; o <<= 1) v = rr_max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
 // Records of row r (positions d = 0 .. deg-1) from parameter block blk.
 template <int r, int NPL, int L>
-__device__ __forceinline__ void rr_load_rows(RrRecs<NPL> &q, const IntegrateArgs &a, const unsigned char *blk, int j)
+__device__ __forceinline__ void rr_load_rows(RrRecs<NPL> &q, const IntegrateArgs &a, const unsigned char *blk, int j,
+                                             unsigned)
 {
     if constexpr (r < kGrpCtRows && r < NPL) {
         constexpr int D = GrpRowCt<r>::deg, P0 = GrpRowCt<r>::off, Q0 = RrQ<r>::off;
@@ -205,15 +356,19 @@ __device__ __forceinline__ void rr_load_rows(RrRecs<NPL> &q, const IntegrateArgs
             if (d & 1) { q.n[Q0 + d / 2].y = n; q.c[Q0 + d / 2].y = c; q.u[Q0 + d / 2].y = u; }
             else       { q.n[Q0 + d / 2].x = n; q.c[Q0 + d / 2].x = c; q.u[Q0 + d / 2].x = u; }
         }
-        rr_load_rows<r + 1, NPL, L>(q, a, blk, j);
+        rr_load_rows<r + 1, NPL, L>(q, a, blk, j, 0u);
     }
 }
 
 // Body of the register-record kernel: NPL rows, WARPS warps per block, L
-// lanes per solve.
-template <int NPL, int WARPS, int L>
+// lanes per solve, Real = float (log-domain edge terms) or double (power
+// table).
+template <int NPL, int WARPS, int L, typename Real = float>
 __device__ __forceinline__ void rr_body(const IntegrateArgs &a)
 {
+    constexpr bool F64 = sizeof(Real) == 8;
+    constexpr int EL = (int)sizeof(Real);                 // bytes per gather entry
+    constexpr int PLN = RrSel<Real, NPL>::planes;
     extern __shared__ __align__(128) unsigned char smem[];
     constexpr unsigned FULL = 0xffffffffu;
     constexpr int GS = kWarp / L;                // groups per warp
@@ -223,46 +378,51 @@ __device__ __forceinline__ void rr_body(const IntegrateArgs &a)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int j = lane / GS, g = lane - j * GS;  // lane within group, group (j-major)
 
-    float *gbuf = reinterpret_cast<float *>(smem) + warp * 2 * NPL * kWarp;
+    float *gbuf = reinterpret_cast<float *>(smem) + warp * (2 * PLN * NPL * kWarp * EL / 4);
     const unsigned base = rr_smem_addr(gbuf);
-    const unsigned own = base + 4 * lane;
+    const unsigned own = base + EL * lane;
 #pragma unroll 1
-    for (int i = lane; i < 2 * NPL * kWarp; i += kWarp) gbuf[i] = 0.0f;
+    for (int i = lane; i < 2 * PLN * NPL * kWarp * EL / 4; i += kWarp) gbuf[i] = 0.0f;
 
-    RrRecs<NPL> q;
+    typename RrSel<Real, NPL>::Recs q;
 #pragma unroll
     for (int p = 0; p < kRrPa; ++p) {
         int off = p < kRrP ? a.grp.pos_off[p * L + j] : 0;
         if (!GRINS_OK_IDX(off >= 0 && off < NPL * kWarp * 4 && (off & 3) == 0, 33, off)) off = 0;
-        q.ga[p] = base + off + 4 * g;
+        q.ga[p] = base + (EL / 4) * off + EL * g;
+    }
+    if constexpr (F64) {
+#pragma unroll
+        for (int p = 0; p < kRrPa; ++p) { q.itn[p] = 0.0; q.u[p] = 1.0; }
+    } else {
+#pragma unroll
+        for (int i = 0; i < kRrQa; ++i) {
+            q.n[i] = make_float2(1.0f, 1.0f);
+            q.c[i] = make_float2(-100.0f, -100.0f);
+            q.u[i] = make_float2(1.0f, 1.0f);
+        }
     }
 #pragma unroll
-    for (int i = 0; i < kRrQa; ++i) {
-        q.n[i] = make_float2(1.0f, 1.0f);
-        q.c[i] = make_float2(-100.0f, -100.0f);
-        q.u[i] = make_float2(1.0f, 1.0f);
-    }
-#pragma unroll
-    for (int r = 0; r < NPL; ++r) { q.Gp[r] = 0.0f; q.k[r] = 1.0f; q.kg[r] = 0.0f; }
+    for (int r = 0; r < NPL; ++r) { q.Gp[r] = 0; q.k[r] = 1; q.kg[r] = 0; }
     rr_syncwarp();
 
-    const float rtol = (float)a.rtol, atol = (float)a.atol;
-    const float ss_tol = (float)a.ss_tol;
-    const float t_end = (float)a.t_end;
-    const float invN = 1.0f / (float)N;
+    const Real rtol = (Real)a.rtol, atol = (Real)a.atol;
+    const Real ss_tol = (Real)a.ss_tol;
+    const Real t_end = (Real)a.t_end;
+    const Real invN = (Real)1 / (Real)N;
     const long long total = a.n_sets * (long long)a.n_ics;
 
     long long my_set = 0;
     int my_ic = 0;
     bool working = false, exhausted = false;
-    float t = 0.0f, h = 0.0f;
+    Real t = 0, h = 0;
     int steps = 0, gidx = 0;
     bool near = false;               // residual below ss_near: tolerances tightened
-    const float ss_near = (float)a.ss_near, ss_gain = (float)a.ss_gain;
+    const Real ss_near = (Real)a.ss_near, ss_gain = (Real)a.ss_gain;
     bool need_k1 = false, rejected = false;
-    float y[NPL], k1[NPL], k2[NPL], k3[NPL], k4[NPL], k5[NPL], k6[NPL], z[NPL];
+    Real y[NPL], k1[NPL], k2[NPL], k3[NPL], k4[NPL], k5[NPL], k6[NPL], z[NPL];
 #pragma unroll
-    for (int r = 0; r < NPL; ++r) y[r] = k1[r] = k2[r] = k3[r] = k4[r] = k5[r] = k6[r] = z[r] = 0.0f;
+    for (int r = 0; r < NPL; ++r) y[r] = k1[r] = k2[r] = k3[r] = k4[r] = k5[r] = k6[r] = z[r] = 0;
 
     auto write_series = [&](int gi) {
         double *dst = a.series + ((my_set * a.n_ics + my_ic) * (long long)a.n_t + gi) * N;
@@ -283,24 +443,25 @@ __device__ __forceinline__ void rr_body(const IntegrateArgs &a)
         const double *kdd = reinterpret_cast<const double *>(blk + a.L.off_k);
         const double *ld = reinterpret_cast<const double *>(blk + a.L.off_lam);
         const double *u0 = a.ic_unit + (long long)my_ic * N;
-        rr_load_rows<0, NPL, L>(q, a, blk, j);
+        rr_load_rows<0, NPL, L>(q, a, blk, j, base + EL * g);
 #pragma unroll
         for (int r = 0; r < NPL; ++r) {
             const int node = a.grp.row_node[r * L + j];
-            q.Gp[r] = 0.0f; q.k[r] = 1.0f; q.kg[r] = 0.0f; y[r] = 0.0f;
+            q.Gp[r] = 0; q.k[r] = 1; q.kg[r] = 0; y[r] = 0;
             if (node >= 0) {
                 const double G = Gd[node], k = kdd[node];
                 double Gp = G;
 #pragma unroll 1
                 for (int c = a.topo.off[node]; c < a.topo.off[node + 1]; ++c)
                     if (a.topo.sign[c] < 0) Gp *= ld[a.topo.edge[c]];
-                q.Gp[r] = (float)Gp;
-                q.k[r] = (float)k;
-                q.kg[r] = (float)(k / G);
-                y[r] = __fdividef((float)u0[node] * (float)G, (float)k);
+                q.Gp[r] = (Real)Gp;
+                q.k[r] = (Real)k;
+                q.kg[r] = (Real)(k / G);
+                if constexpr (F64) y[r] = u0[node] * G / k;
+                else y[r] = __fdividef((float)u0[node] * (float)G, (float)k);
             }
         }
-        t = (float)a.t0;
+        t = (Real)a.t0;
         steps = 0;
         gidx = 0;
         need_k1 = true;
@@ -326,11 +487,11 @@ __device__ __forceinline__ void rr_body(const IntegrateArgs &a)
         }
     };
 
-    auto residual = [&](const float (&v)[NPL]) -> float {
-        float r = 0.0f;
+    auto residual = [&](const Real (&v)[NPL]) -> Real {
+        Real r = 0;
 #pragma unroll
-        for (int i = 0; i < NPL; ++i) r = fmaxf(r, fabsf(v[i]) * q.kg[i]);
-        return grp_max(r, L);
+        for (int i = 0; i < NPL; ++i) r = rr_max(r, rr_abs(v[i]) * q.kg[i]);
+        return rr_gmax(r, L);
     };
 
     fetch();
@@ -349,110 +510,111 @@ __device__ __forceinline__ void rr_body(const IntegrateArgs &a)
 #pragma unroll
             for (int r = 0; r < NPL; ++r) z[r] = y[r];
             rr_rhs<1>(q, z, own);
-            float d0 = 0.0f, d1 = 0.0f;
+            Real d0 = 0, d1 = 0;
             bool fin = true;
 #pragma unroll
             for (int r = 0; r < NPL; ++r) {
                 fin = fin && isfinite(z[r]);
-                const float isc = __fdividef(1.0f, atol + rtol * fabsf(y[r]));
+                const Real isc = rr_div((Real)1, atol + rtol * rr_abs(y[r]));
                 d0 += (y[r] * isc) * (y[r] * isc);
                 d1 += (z[r] * isc) * (z[r] * isc);
             }
-            d0 = sqrtf(grp_sum(d0, L) * invN);
-            d1 = sqrtf(grp_sum(d1, L) * invN);
+            d0 = rr_sqrt(rr_gsum(d0, L) * invN);
+            d1 = rr_sqrt(rr_gsum(d1, L) * invN);
             fin = grp_all(fin, L);
-            const float res = residual(z);
+            const Real res = residual(z);
             if (need_k1) {
                 need_k1 = false;
 #pragma unroll
                 for (int r = 0; r < NPL; ++r) k1[r] = z[r];
-                h = (d0 < 1e-5f || d1 < 1e-5f) ? 1e-6f : 0.01f * d0 / d1;
-                h = fminf(h, (float)(a.t_end - a.t0));
+                h = (d0 < (Real)1e-5 || d1 < (Real)1e-5) ? (Real)1e-6 : (Real)0.01 * d0 / d1;
+                h = rr_min(h, (Real)(a.t_end - a.t0));
                 if (!fin) { done = true; st_code = GRINS_SS_NONFINITE; }
                 else if (res < ss_tol) { done = true; st_code = GRINS_SS_CONVERGED; }
             }
         }
 
-        float t_stop = t_end;
+        Real t_stop = t_end;
         bool to_grid = false, clipped = false;
-        if (gidx < a.n_t && (float)a.t_grid[gidx] < t_stop) { t_stop = (float)a.t_grid[gidx]; to_grid = true; }
-        float hh = h;
+        if (gidx < a.n_t && (Real)a.t_grid[gidx] < t_stop) { t_stop = (Real)a.t_grid[gidx]; to_grid = true; }
+        Real hh = h;
         if (t + hh >= t_stop) { hh = t_stop - t; clipped = true; }
 
 #pragma unroll
-        for (int r = 0; r < NPL; ++r) z[r] = y[r] + hh * ((float)dp::a21 * k1[r]);
+        for (int r = 0; r < NPL; ++r) z[r] = y[r] + hh * ((Real)dp::a21 * k1[r]);
         rr_rhs<0>(q, z, own);
 #pragma unroll
         for (int r = 0; r < NPL; ++r) {
             k2[r] = z[r];
-            z[r] = y[r] + hh * ((float)dp::a31 * k1[r] + (float)dp::a32 * k2[r]);
+            z[r] = y[r] + hh * ((Real)dp::a31 * k1[r] + (Real)dp::a32 * k2[r]);
         }
         rr_rhs<1>(q, z, own);
 #pragma unroll
         for (int r = 0; r < NPL; ++r) {
             k3[r] = z[r];
-            z[r] = y[r] + hh * ((float)dp::a41 * k1[r] + (float)dp::a42 * k2[r] + (float)dp::a43 * k3[r]);
+            z[r] = y[r] + hh * ((Real)dp::a41 * k1[r] + (Real)dp::a42 * k2[r] + (Real)dp::a43 * k3[r]);
         }
         rr_rhs<0>(q, z, own);
 #pragma unroll
         for (int r = 0; r < NPL; ++r) {
             k4[r] = z[r];
-            z[r] = y[r] + hh * ((float)dp::a51 * k1[r] + (float)dp::a52 * k2[r] + (float)dp::a53 * k3[r] +
-                                (float)dp::a54 * k4[r]);
+            z[r] = y[r] + hh * ((Real)dp::a51 * k1[r] + (Real)dp::a52 * k2[r] + (Real)dp::a53 * k3[r] +
+                                (Real)dp::a54 * k4[r]);
         }
         rr_rhs<1>(q, z, own);
 #pragma unroll
         for (int r = 0; r < NPL; ++r) {
             k5[r] = z[r];
-            z[r] = y[r] + hh * ((float)dp::a61 * k1[r] + (float)dp::a62 * k2[r] + (float)dp::a63 * k3[r] +
-                                (float)dp::a64 * k4[r] + (float)dp::a65 * k5[r]);
+            z[r] = y[r] + hh * ((Real)dp::a61 * k1[r] + (Real)dp::a62 * k2[r] + (Real)dp::a63 * k3[r] +
+                                (Real)dp::a64 * k4[r] + (Real)dp::a65 * k5[r]);
         }
         rr_rhs<0>(q, z, own);
 #pragma unroll
         for (int r = 0; r < NPL; ++r) {
             k6[r] = z[r];
             // fifth-order solution in k2 (no later stage reads k2)
-            k2[r] = y[r] + hh * ((float)dp::b1 * k1[r] + (float)dp::b3 * k3[r] + (float)dp::b4 * k4[r] +
-                                 (float)dp::b5 * k5[r] + (float)dp::b6 * k6[r]);
+            k2[r] = y[r] + hh * ((Real)dp::b1 * k1[r] + (Real)dp::b3 * k3[r] + (Real)dp::b4 * k4[r] +
+                                 (Real)dp::b5 * k5[r] + (Real)dp::b6 * k6[r]);
             z[r] = k2[r];
         }
         rr_rhs<1>(q, z, own);                     // z = k7
 
-        float en = 0.0f;
+        Real en = 0;
         bool finite = true;
 #pragma unroll
         for (int r = 0; r < NPL; ++r) {
-            const float err = hh * ((float)dp::e1 * k1[r] + (float)dp::e3 * k3[r] + (float)dp::e4 * k4[r] +
-                                    (float)dp::e5 * k5[r] + (float)dp::e6 * k6[r] + (float)dp::e7 * z[r]);
-            const float sc = atol + rtol * fmaxf(fabsf(y[r]), fabsf(k2[r]));
-            const float qq = div_approx(err, sc);
+            const Real err = hh * ((Real)dp::e1 * k1[r] + (Real)dp::e3 * k3[r] + (Real)dp::e4 * k4[r] +
+                                    (Real)dp::e5 * k5[r] + (Real)dp::e6 * k6[r] + (Real)dp::e7 * z[r]);
+            const Real sc = atol + rtol * rr_max(rr_abs(y[r]), rr_abs(k2[r]));
+            const Real qq = rr_div(err, sc);
             en += qq * qq;
             finite = finite && isfinite(z[r]) && isfinite(k2[r]);
         }
-        en = grp_sum(en, L) * invN;                   // squared RMS error norm
+        en = rr_gsum(en, L) * invN;                   // squared RMS error norm
         if (near) en *= ss_gain;
         finite = grp_all(finite, L);
-        const float res = residual(z);
+        const Real res = residual(z);
 
         if (working && !done) {
             ++steps;
             if (!finite || !isfinite(en)) {
                 done = true; st_code = GRINS_SS_NONFINITE;
             } else if (en < 1.0f) {
-                const float t_new = clipped ? t_stop : t + hh;
+                const Real t_new = clipped ? t_stop : t + hh;
                 if (!(t_new > t)) { done = true; st_code = GRINS_SS_NONFINITE; }
                 t = t_new;
 #pragma unroll
                 for (int r = 0; r < NPL; ++r) { y[r] = k2[r]; k1[r] = z[r]; }
                 if (clipped && to_grid) {
 #pragma unroll 1
-                    while (gidx < a.n_t && (float)a.t_grid[gidx] <= t) { write_series(gidx); ++gidx; }
+                    while (gidx < a.n_t && (Real)a.t_grid[gidx] <= t) { write_series(gidx); ++gidx; }
                 }
                 // controller 0.9 err^(-1/5), err = sqrt(en)
-                float fac = en == 0.0f ? 10.0f : 0.9f * ex2_approx(-0.1f * lg2_approx(en));
+                const float enf = (float)en;
+                float fac = enf == 0.0f ? 10.0f : 0.9f * ex2_approx(-0.1f * lg2_approx(enf));
                 fac = fminf(fac, 10.0f);
                 if (rejected) fac = fminf(fac, 1.0f);
-                h = hh * fac;
+                h = hh * (Real)fac;
                 rejected = false;
                 near = res < ss_near;
                 if (!done) {
@@ -460,7 +622,7 @@ __device__ __forceinline__ void rr_body(const IntegrateArgs &a)
                     else if (t >= t_end) { done = true; st_code = GRINS_SS_TEND; }
                 }
             } else {
-                h = hh * fmaxf(0.9f * ex2_approx(-0.1f * lg2_approx(en)), 0.2f);
+                h = hh * (Real)fmaxf(0.9f * ex2_approx(-0.1f * lg2_approx((float)en)), 0.2f);
                 rejected = true;
             }
             if (!done && steps >= a.max_steps) { done = true; st_code = GRINS_SS_MAXSTEPS; }

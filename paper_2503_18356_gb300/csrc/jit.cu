@@ -195,12 +195,12 @@ std::string jit_main(const GrpTopo &g, int kind, int minb)
                       g.row_off[r], g.row_deg[r]);
         s += buf;
     }
-    if (kind == kJitRegisters) {
+    if (kind == kJitRegisters || kind == kJitRegisters64) {
         s += "}\n#include \"integrate_rr.cuh\"\n";
         std::snprintf(buf, sizeof(buf),
                       "extern \"C\" __global__ void __launch_bounds__(%d, %d) grins_grp_ct(const grins::IntegrateArgs a)\n"
-                      "{\n    grins::rr_body<%d, %d, %d>(a);\n}\n",
-                      kJitWarps * kWarp, minb, g.R, kJitWarps, g.L);
+                      "{\n    grins::rr_body<%d, %d, %d, %s>(a);\n}\n",
+                      kJitWarps * kWarp, minb, g.R, kJitWarps, g.L, kind == kJitRegisters64 ? "double" : "float");
     } else {
         s += "}\n#include \"integrate_grp.cuh\"\n";
         std::snprintf(buf, sizeof(buf),
@@ -275,6 +275,10 @@ int jit_minb(const GrpTopo &g, int kind)
 {
     const int est = 4 * g.P + 11 * g.R + 40;
     int minb = kind == kJitRegisters ? (est <= 144 ? 4 : (est <= 176 ? 3 : 2)) : GRINS_GRP_MINB;
+    if (kind == kJitRegisters64) {          // 2 registers per value, 5 per position
+        const int est64 = 5 * g.P + 22 * g.R + 60;
+        minb = est64 <= 128 ? 4 : (est64 <= 168 ? 3 : 2);
+    }
     if (const char *ev = std::getenv("GRINS_JIT_MINB")) {
         const int m = std::atoi(ev);
         if (m >= 1 && m <= 8) minb = m;
@@ -292,7 +296,7 @@ void jit_build_entry(JitEntry &e, const GrpTopo &g, int kind, int dev)
     JitBuild b;
     for (;;) {
         b = jit_compile(jit_main(g, kind, minb));
-        if (b.ok && kind == kJitRegisters && b.spill_bytes > 0 && minb > 1 && !std::getenv("GRINS_JIT_MINB")) {
+        if (b.ok && kind != kJitShared && b.spill_bytes > 0 && minb > 1 && !std::getenv("GRINS_JIT_MINB")) {
             cudaLibraryUnload(b.lib);
             --minb;
             continue;
@@ -360,7 +364,9 @@ const void *grp_jit_kernel(const GrpTopo &g, int kind, std::string *why)
     if (!jit_enabled(g, why)) return nullptr;
     std::shared_ptr<JitEntry> e = jit_get(g, kind, kCompileHere);
     if (e->state.load() != 1) { if (why) *why = e->why; return nullptr; }
-    if (why) *why = e->kind == kJitRegisters ? "records in registers" : "records in shared memory";
+    if (why)
+        *why = e->kind == kJitRegisters64 ? "FP64, records in registers"
+                                          : (e->kind == kJitRegisters ? "records in registers" : "records in shared memory");
     return e.get();
 }
 
@@ -389,8 +395,8 @@ cudaError_t launch_grp_jit(const void *handle, const IntegrateArgs &a, cudaStrea
     if (je->state.load() != 1) return cudaErrorInvalidValue;
     IntegrateArgs b = a;
     int smem = 0;
-    if (je->kind == kJitRegisters) {
-        smem = kJitWarps * rr_warp_bytes(b.grp.R);
+    if (je->kind == kJitRegisters || je->kind == kJitRegisters64) {
+        smem = je->kind == kJitRegisters ? kJitWarps * rr_warp_bytes(b.grp.R, 1, 4) : kJitWarps * rr_warp_bytes(b.grp.R, 6, 8);
     } else {
         const int ndom = grp_domains(b.grp.L);
         GrpLayout LY{b.grp.L, b.grp.R, b.grp.P, b.slots};

@@ -66,3 +66,28 @@ def test_compiled_and_runtime_layout_kernels(jit, wl, monkeypatch):
         kind = "registers" if jit == "rr" else "shared memory"
         assert "records in " + kind in info, info
     h.close()
+
+
+@pytest.mark.parametrize("jit", ["1", "0"])
+@pytest.mark.parametrize("wl", ["ts", "net5", "net22"])
+def test_fp64_compiled_and_generic_kernels(jit, wl, monkeypatch):
+    """The plain FP64 solver: the register-record kernel compiled in FP64
+    (exact power-table edge terms) and the generic FP64 kernel, raw states
+    against the oracle on the G/k scale (1e-3, as for FP32)."""
+    monkeypatch.setenv("GRINS_JIT", jit)
+    w = {"ts": W.ts_workload, "net5": W.net5_workload, "net22": W.net22_workload}[wl]()
+    topo = w["topology"]
+    h = PT.gpu_handle(topo)
+    params, ic, p, icn = PT.gpu_sample(h, w["param_seed"], 40, min(w["n_ics"], 10))
+    o = O.run_sets_parallel(O.Network(*topo.edges()), p, icn, threads=PT.THREADS)
+    g = PT.to_numpy(h.integrate(params, ic, precision=0, polish=0))
+    torch.cuda.synchronize()
+    c = PT.compare_states(g, o, p, 1e-3, normalised=True)
+    info = h.integrator()
+    print(info, c)
+    assert c["max_rel"] <= 1e-3
+    assert c["n_basin"] <= max(1, 0.01 * g["status"].size)
+    assert c["status_agree"] >= 0.97
+    if jit == "1":
+        assert "FP64, records in registers" in info, info
+    h.close()
