@@ -53,19 +53,23 @@ static grins_status cuda_fail(cudaError_t e, const char *what)
 // A lane-group layout on the device (host copy of the row table).
 struct GrpDev {
     int L = 0, R = 0, P = 0;
-    std::vector<int32_t> row_off, row_deg;
-    int32_t *d_pos_edge = nullptr, *d_pos_off = nullptr, *d_row_node = nullptr;
+    std::vector<int32_t> row_off, row_deg, link_to;
+    int32_t *d_pos_edge = nullptr, *d_pos_off = nullptr, *d_row_node = nullptr, *d_row_link = nullptr;
     void free_device()
     {
-        cudaFree(d_pos_edge); cudaFree(d_pos_off); cudaFree(d_row_node);
-        d_pos_edge = d_pos_off = d_row_node = nullptr;
+        cudaFree(d_pos_edge); cudaFree(d_pos_off); cudaFree(d_row_node); cudaFree(d_row_link);
+        d_pos_edge = d_pos_off = d_row_node = d_row_link = nullptr;
     }
     GrpTopo topo() const
     {
         GrpTopo g{};
         g.L = L; g.R = R; g.P = P;
-        g.pos_edge = d_pos_edge; g.pos_off = d_pos_off; g.row_node = d_row_node;
-        for (int r = 0; r < R && r < kGrpMaxRows; ++r) { g.row_off[r] = row_off[r]; g.row_deg[r] = row_deg[r]; }
+        g.pos_edge = d_pos_edge; g.pos_off = d_pos_off; g.row_node = d_row_node; g.row_link = d_row_link;
+        for (int r = 0; r < R && r < kGrpMaxRows; ++r) {
+            g.row_off[r] = row_off[r];
+            g.row_deg[r] = row_deg[r];
+            g.link_to[r] = r < (int)link_to.size() ? link_to[r] : -1;
+        }
         return g;
     }
 };
@@ -154,10 +158,12 @@ static void free_device(grins_racipe *h)
 struct GrpHost {
     int L = 0, R = 0, P = 0;
     std::vector<int32_t> row_off, row_deg, pos_edge, pos_off, row_node;
+    std::vector<int32_t> row_link;      // [R * L]: 1 where slot (r, j) continues slot (link_to[r], j)
+    std::vector<int32_t> link_to;       // [R]: the row a row's continuations multiply into, or -1
 };
 
 static GrpHost build_grp(int N, int L, const std::vector<int32_t> &csr_off, const std::vector<int32_t> &csr_src,
-                         const std::vector<int32_t> &csr_edge)
+                         const std::vector<int32_t> &csr_edge, bool split = false)
 {
     GrpHost g;
     const int R = (N + L - 1) / L;
@@ -170,8 +176,41 @@ static GrpHost build_grp(int N, int L, const std::vector<int32_t> &csr_off, cons
     });
     g.L = L; g.R = R;
     g.row_node.assign((size_t)R * L, -1);
+    g.row_link.assign((size_t)R * L, 0);
+    g.link_to.assign(R, -1);
     std::vector<int> gslot(N, 0);
     for (int q = 0; q < N; ++q) { g.row_node[q] = order[q]; gslot[order[q]] = q; }
+    // in-edges (CSR positions) handled by each slot
+    std::vector<std::vector<int>> slot_lst((size_t)R * L);
+    for (int q = 0; q < N; ++q)
+        for (int c = csr_off[order[q]]; c < csr_off[order[q] + 1]; ++c) slot_lst[q].push_back(c);
+    // Splitting (register-record layouts): while the widest node of row 0 is
+    // alone in needing its row's width and a last-row slot is free, move it
+    // to that slot's lane and hand the edges beyond the row's next width to
+    // the free slot (a continuation: its partial product multiplies into
+    // the node's own), if they fit the last row's width.
+    if (split && R >= 2) {
+        for (int js = 0; js < L; ++js) {
+            const int spare = (R - 1) * L + js;
+            if (g.row_node[spare] >= 0 || !slot_lst[spare].empty()) continue;
+            int jmax = 0;
+            for (int j = 1; j < L; ++j)
+                if (slot_lst[j].size() > slot_lst[jmax].size()) jmax = j;
+            size_t d1 = 0, dlast = 0;
+            for (int j = 0; j < L; ++j) if (j != jmax) d1 = std::max(d1, slot_lst[j].size());
+            for (int j = 0; j < L; ++j) dlast = std::max(dlast, slot_lst[(R - 1) * L + j].size());
+            const size_t dmax = slot_lst[jmax].size();
+            if (dmax <= d1 || dmax - d1 > dlast) break;
+            std::swap(g.row_node[jmax], g.row_node[js]);
+            std::swap(slot_lst[jmax], slot_lst[js]);
+            if (g.row_node[jmax] >= 0) gslot[g.row_node[jmax]] = jmax;
+            gslot[g.row_node[js]] = js;
+            slot_lst[spare].assign(slot_lst[js].begin() + d1, slot_lst[js].end());
+            slot_lst[js].resize(d1);
+            g.row_link[spare] = 1;
+            g.link_to[R - 1] = 0;
+        }
+    }
     auto col_of = [&](int node) { return gslot[node] % L; };
     auto off_of_slot = [&](int slot) { return slot * GS * 4; };
     // Order of one row's edges: position by position, each lane (in lane
@@ -247,9 +286,7 @@ static GrpHost build_grp(int N, int L, const std::vector<int32_t> &csr_off, cons
         int D = 0;
         std::vector<std::vector<int>> lst(L);            // CSR positions per lane
         for (int j = 0; j < L; ++j) {
-            const int node = g.row_node[r * L + j];
-            if (node < 0) continue;
-            for (int c = csr_off[node]; c < csr_off[node + 1]; ++c) lst[j].push_back(c);
+            lst[j] = slot_lst[(size_t)r * L + j];
             D = std::max(D, (int)lst[j].size());
         }
         g.row_off.push_back(P);
@@ -315,11 +352,11 @@ static GrpHost choose_grp_registers(int N, const std::vector<int32_t> &off, cons
                                     const std::vector<int32_t> &edge)
 {
     auto est = [&](int L) { return 4 * grp_positions(N, L, off) + 11 * ((N + L - 1) / L) + 40; };
-    if (const int f = grp_l_override(N)) return est(f) <= 255 ? build_grp(N, f, off, src, edge) : GrpHost{};
+    if (const int f = grp_l_override(N)) return est(f) <= 255 ? build_grp(N, f, off, src, edge, true) : GrpHost{};
     for (int limit : {168, 255}) {
         for (int L = 1; L <= kWarp; L *= 2) {
             if ((N + L - 1) / L > 12) continue;
-            if (est(L) <= limit) return build_grp(N, L, off, src, edge);
+            if (est(L) <= limit) return build_grp(N, L, off, src, edge, true);
         }
     }
     return GrpHost{};
@@ -329,7 +366,7 @@ static GrpHost choose_grp_registers(int N, const std::vector<int32_t> &off, cons
 static cudaError_t upload_grp(const GrpHost &g, GrpDev &d)
 {
     d.L = g.L; d.R = g.R; d.P = g.P;
-    d.row_off = g.row_off; d.row_deg = g.row_deg;
+    d.row_off = g.row_off; d.row_deg = g.row_deg; d.link_to = g.link_to;
     if (g.L <= 0) return cudaSuccess;
     const size_t np = std::max<size_t>(g.pos_edge.size(), 1), nr = g.row_node.size();
     cudaError_t ce = cudaMalloc(&d.d_pos_edge, sizeof(int32_t) * np);
@@ -341,6 +378,9 @@ static cudaError_t upload_grp(const GrpHost &g, GrpDev &d)
         ce = cudaMemcpy(d.d_pos_off, g.pos_off.data(), sizeof(int32_t) * g.pos_off.size(), cudaMemcpyHostToDevice);
     if (ce == cudaSuccess)
         ce = cudaMemcpy(d.d_row_node, g.row_node.data(), sizeof(int32_t) * nr, cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess) ce = cudaMalloc(&d.d_row_link, sizeof(int32_t) * nr);
+    if (ce == cudaSuccess)
+        ce = cudaMemcpy(d.d_row_link, g.row_link.data(), sizeof(int32_t) * nr, cudaMemcpyHostToDevice);
     return ce;
 }
 

@@ -80,8 +80,10 @@ struct GrpTopo {
     const int32_t *pos_edge;     // [P * L] creation-order edge index or -1
     const int32_t *pos_off;      // [P * L] gather byte offset of the source
     const int32_t *row_node;     // [R * L] node of slot (r, j) or -1
+    const int32_t *row_link;     // [R * L] 1: slot (r, j) continues slot (link_to[r], j)
     int32_t row_off[kGrpMaxRows];
     int32_t row_deg[kGrpMaxRows];
+    int32_t link_to[kGrpMaxRows];  // row a row's continuation products multiply into, -1 none
 };
 
 struct IntegrateArgs {

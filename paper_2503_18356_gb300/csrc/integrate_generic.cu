@@ -21,6 +21,16 @@ cudaError_t launch_integrate_fp32(const IntegrateArgs &a, cudaStream_t st, int n
 {
     // lane-group kernel when the network has a layout and its slots fit in
     // shared memory; the generic kernel otherwise
+    // (a layout with continuation rows is only for the register-record kernel)
+    bool links = false;
+    for (int r = 0; r < a.grp.R && r < kGrpMaxRows; ++r) links = links || a.grp.link_to[r] >= 0;
+    if (a.grp.L > 0 && a.grp.R <= 12 && links) {
+        if (a.grp_jit) {
+            const cudaError_t e = launch_grp_jit(a.grp_jit, a, st, num_sms);
+            if (e != cudaErrorInvalidConfiguration) return e;
+        }
+        return launch_dp5_generic<float>(a, st, num_sms);
+    }
     if (a.grp.L > 0 && a.grp.R <= 12) {
         IntegrateArgs b = a;
         const int ndom = grp_domains(a.grp.L);               // scheduling domains per warp

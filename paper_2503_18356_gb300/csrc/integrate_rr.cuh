@@ -159,16 +159,38 @@ __device__ __forceinline__ float rr_row_prod(const RrRecs<NPL> &q)
     }
 }
 
-// z[r] <- G'_r prod_r - k_r z[r] for rows r, r+1, ...
+__device__ __forceinline__ float rr_fma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double rr_fma(double a, double b, double c) { return fma(a, b, c); }
+
+// prod[r] <- the product of row r's factors, rows r, r+1, ...
 template <int BO, int r, int NPL>
-__device__ __forceinline__ void rr_rows(const RrRecs<NPL> &q, float (&z)[NPL])
+__device__ __forceinline__ void rr_prods(const RrRecs<NPL> &q, float (&prod)[NPL])
 {
     if constexpr (r < kGrpCtRows && r < NPL) {
         constexpr int D = GrpRowCt<r>::deg;
-        const float prod = rr_row_prod<BO, GrpRowCt<r>::off, RrQ<r>::off, D / 2, (D & 1) != 0, 0, NPL>(q);
-        z[r] = fmaf(q.Gp[r], prod, -q.k[r] * z[r]);
-        rr_rows<BO, r + 1, NPL>(q, z);
+        prod[r] = rr_row_prod<BO, GrpRowCt<r>::off, RrQ<r>::off, D / 2, (D & 1) != 0, 0, NPL>(q);
+        rr_prods<BO, r + 1, NPL>(q, prod);
     }
+}
+
+// Continuations: a lane whose slot in row r continues its slot in row
+// GrpRowCt<r>::link (lk[r]) multiplies its row-r partial product into it.
+template <int r, int NPL, typename Real>
+__device__ __forceinline__ void rr_links(const bool (&lk)[NPL], Real (&prod)[NPL])
+{
+    if constexpr (r < kGrpCtRows && r < NPL) {
+        constexpr int t = GrpRowCt<r>::link;
+        if constexpr (t >= 0 && t < NPL) prod[t] *= lk[r] ? prod[r] : (Real)1;
+        rr_links<r + 1, NPL, Real>(lk, prod);
+    }
+}
+
+// z[r] <- G'_r prod_r - k_r z[r]
+template <int NPL, typename Recs, typename Real>
+__device__ __forceinline__ void rr_update(const Recs &q, const Real (&prod)[NPL], Real (&z)[NPL])
+{
+#pragma unroll
+    for (int r = 0; r < NPL; ++r) z[r] = rr_fma(q.Gp[r], prod[r], -q.k[r] * z[r]);
 }
 
 // log2 of this lane's stage values into its column of the buffer at BO
@@ -183,12 +205,15 @@ __device__ __forceinline__ void rr_put(const float (&z)[NPL], unsigned own)
 
 // z <- Eq. 1 at the stage input z through gather buffer B (0 or 1)
 template <int B, int NPL>
-__device__ __forceinline__ void rr_rhs(const RrRecs<NPL> &q, float (&z)[NPL], unsigned own)
+__device__ __forceinline__ void rr_rhs(const RrRecs<NPL> &q, const bool (&lk)[NPL], float (&z)[NPL], unsigned own)
 {
     constexpr int BO = B * NPL * kWarp * 4;
     rr_put<BO, 0, NPL>(z, own);
     rr_syncwarp();
-    rr_rows<BO, 0, NPL>(q, z);
+    float prod[NPL];
+    rr_prods<BO, 0, NPL>(q, prod);
+    rr_links<0, NPL, float>(lk, prod);
+    rr_update<NPL>(q, prod, z);
 }
 
 // ------------------------------------------------------------------ FP64
@@ -230,15 +255,15 @@ __device__ __forceinline__ void rr64_acc(const RrRecs64<NPL> &q, double &prod, d
 }
 
 template <int BO, int r, int NPL>
-__device__ __forceinline__ void rr64_rows(const RrRecs64<NPL> &q, double (&z)[NPL])
+__device__ __forceinline__ void rr64_prods(const RrRecs64<NPL> &q, double (&prod)[NPL])
 {
     if constexpr (r < kGrpCtRows && r < NPL) {
         constexpr int D = GrpRowCt<r>::deg;
-        double prod = 1.0, num = 1.0, den = 1.0;
-        rr64_acc<BO, GrpRowCt<r>::off, D, 0, NPL>(q, prod, num, den);
-        if constexpr (D % 8 != 0) prod *= num / den;
-        z[r] = fma(q.Gp[r], prod, -q.k[r] * z[r]);
-        rr64_rows<BO, r + 1, NPL>(q, z);
+        double p = 1.0, num = 1.0, den = 1.0;
+        rr64_acc<BO, GrpRowCt<r>::off, D, 0, NPL>(q, p, num, den);
+        if constexpr (D % 8 != 0) p *= num / den;
+        prod[r] = p;
+        rr64_prods<BO, r + 1, NPL>(q, prod);
     }
 }
 
@@ -262,12 +287,15 @@ __device__ __forceinline__ void rr64_put(const double (&z)[NPL], unsigned own)
 }
 
 template <int B, int NPL>
-__device__ __forceinline__ void rr_rhs(const RrRecs64<NPL> &q, double (&z)[NPL], unsigned own)
+__device__ __forceinline__ void rr_rhs(const RrRecs64<NPL> &q, const bool (&lk)[NPL], double (&z)[NPL], unsigned own)
 {
     constexpr int BO = B * kRr64Pow * NPL * kWarp * 8;
     rr64_put<BO, 0, NPL>(z, own);
     rr_syncwarp();
-    rr64_rows<BO, 0, NPL>(q, z);
+    double prod[NPL];
+    rr64_prods<BO, 0, NPL>(q, prod);
+    rr_links<0, NPL, double>(lk, prod);
+    rr_update<NPL>(q, prod, z);
 }
 
 // FP64 records of row r from parameter block blk; col = this group's column
@@ -403,6 +431,9 @@ __device__ __forceinline__ void rr_body(const IntegrateArgs &a)
         }
     }
 #pragma unroll
+    bool lk[NPL];                     // continuation flags of this lane's slots
+#pragma unroll
+    for (int r = 0; r < NPL; ++r) lk[r] = a.grp.row_link != nullptr && a.grp.row_link[r * L + j] != 0;
     for (int r = 0; r < NPL; ++r) { q.Gp[r] = 0; q.k[r] = 1; q.kg[r] = 0; }
     rr_syncwarp();
 
@@ -509,7 +540,7 @@ __device__ __forceinline__ void rr_body(const IntegrateArgs &a)
             rr_syncwarp();                        // buffer 1 was read by the last stage
 #pragma unroll
             for (int r = 0; r < NPL; ++r) z[r] = y[r];
-            rr_rhs<1>(q, z, own);
+            rr_rhs<1>(q, lk, z, own);
             Real d0 = 0, d1 = 0;
             bool fin = true;
 #pragma unroll
@@ -542,33 +573,33 @@ __device__ __forceinline__ void rr_body(const IntegrateArgs &a)
 
 #pragma unroll
         for (int r = 0; r < NPL; ++r) z[r] = y[r] + hh * ((Real)dp::a21 * k1[r]);
-        rr_rhs<0>(q, z, own);
+        rr_rhs<0>(q, lk, z, own);
 #pragma unroll
         for (int r = 0; r < NPL; ++r) {
             k2[r] = z[r];
             z[r] = y[r] + hh * ((Real)dp::a31 * k1[r] + (Real)dp::a32 * k2[r]);
         }
-        rr_rhs<1>(q, z, own);
+        rr_rhs<1>(q, lk, z, own);
 #pragma unroll
         for (int r = 0; r < NPL; ++r) {
             k3[r] = z[r];
             z[r] = y[r] + hh * ((Real)dp::a41 * k1[r] + (Real)dp::a42 * k2[r] + (Real)dp::a43 * k3[r]);
         }
-        rr_rhs<0>(q, z, own);
+        rr_rhs<0>(q, lk, z, own);
 #pragma unroll
         for (int r = 0; r < NPL; ++r) {
             k4[r] = z[r];
             z[r] = y[r] + hh * ((Real)dp::a51 * k1[r] + (Real)dp::a52 * k2[r] + (Real)dp::a53 * k3[r] +
                                 (Real)dp::a54 * k4[r]);
         }
-        rr_rhs<1>(q, z, own);
+        rr_rhs<1>(q, lk, z, own);
 #pragma unroll
         for (int r = 0; r < NPL; ++r) {
             k5[r] = z[r];
             z[r] = y[r] + hh * ((Real)dp::a61 * k1[r] + (Real)dp::a62 * k2[r] + (Real)dp::a63 * k3[r] +
                                 (Real)dp::a64 * k4[r] + (Real)dp::a65 * k5[r]);
         }
-        rr_rhs<0>(q, z, own);
+        rr_rhs<0>(q, lk, z, own);
 #pragma unroll
         for (int r = 0; r < NPL; ++r) {
             k6[r] = z[r];
@@ -577,7 +608,7 @@ __device__ __forceinline__ void rr_body(const IntegrateArgs &a)
                                  (Real)dp::b5 * k5[r] + (Real)dp::b6 * k6[r]);
             z[r] = k2[r];
         }
-        rr_rhs<1>(q, z, own);                     // z = k7
+        rr_rhs<1>(q, lk, z, own);                     // z = k7
 
         Real en = 0;
         bool finite = true;

@@ -188,11 +188,11 @@ std::string jit_main(const GrpTopo &g, int kind, int minb)
     s += "#include \"common.cuh\"\nnamespace grins {\n";
     std::snprintf(buf, sizeof(buf), "constexpr int kGrpCtRows = %d;\n", g.R);
     s += buf;
-    s += "template <int r> struct GrpRowCt { static constexpr int off = 0, deg = 0; };\n";
+    s += "template <int r> struct GrpRowCt { static constexpr int off = 0, deg = 0, link = -1; };\n";
     for (int r = 0; r < g.R; ++r) {
         std::snprintf(buf, sizeof(buf),
-                      "template <> struct GrpRowCt<%d> { static constexpr int off = %d, deg = %d; };\n", r,
-                      g.row_off[r], g.row_deg[r]);
+                      "template <> struct GrpRowCt<%d> { static constexpr int off = %d, deg = %d, link = %d; };\n",
+                      r, g.row_off[r], g.row_deg[r], kind == kJitShared ? -1 : g.link_to[r]);
         s += buf;
     }
     if (kind == kJitRegisters || kind == kJitRegisters64) {
