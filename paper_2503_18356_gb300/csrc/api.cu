@@ -184,30 +184,56 @@ static GrpHost build_grp(int N, int L, const std::vector<int32_t> &csr_off, cons
     std::vector<std::vector<int>> slot_lst((size_t)R * L);
     for (int q = 0; q < N; ++q)
         for (int c = csr_off[order[q]]; c < csr_off[order[q] + 1]; ++c) slot_lst[q].push_back(c);
-    // Splitting (register-record layouts): while the widest node of row 0 is
-    // alone in needing its row's width and a last-row slot is free, move it
-    // to that slot's lane and hand the edges beyond the row's next width to
-    // the free slot (a continuation: its partial product multiplies into
-    // the node's own), if they fit the last row's width.
+    // Splitting (register-record layouts): row 0 may be cut to a width t
+    // below its widest node when every node wider than t can hand its edges
+    // beyond t to a free slot of the last row in its own lane (a
+    // continuation: the lane multiplies that partial product into the
+    // node's own).  t minimises t + the last row's width, and those nodes
+    // move to the free slots' lanes.
     if (split && R >= 2) {
-        for (int js = 0; js < L; ++js) {
-            const int spare = (R - 1) * L + js;
-            if (g.row_node[spare] >= 0 || !slot_lst[spare].empty()) continue;
-            int jmax = 0;
-            for (int j = 1; j < L; ++j)
-                if (slot_lst[j].size() > slot_lst[jmax].size()) jmax = j;
-            size_t d1 = 0, dlast = 0;
-            for (int j = 0; j < L; ++j) if (j != jmax) d1 = std::max(d1, slot_lst[j].size());
-            for (int j = 0; j < L; ++j) dlast = std::max(dlast, slot_lst[(R - 1) * L + j].size());
-            const size_t dmax = slot_lst[jmax].size();
-            if (dmax <= d1 || dmax - d1 > dlast) break;
-            std::swap(g.row_node[jmax], g.row_node[js]);
-            std::swap(slot_lst[jmax], slot_lst[js]);
-            if (g.row_node[jmax] >= 0) gslot[g.row_node[jmax]] = jmax;
-            gslot[g.row_node[js]] = js;
-            slot_lst[spare].assign(slot_lst[js].begin() + d1, slot_lst[js].end());
-            slot_lst[js].resize(d1);
-            g.row_link[spare] = 1;
+        std::vector<int> spare;
+        for (int j = 0; j < L; ++j)
+            if (g.row_node[(R - 1) * L + j] < 0) spare.push_back(j);
+        std::vector<int> d0(L);
+        int D0 = 0, Dl = 0;
+        for (int j = 0; j < L; ++j) { d0[j] = (int)slot_lst[j].size(); D0 = std::max(D0, d0[j]); }
+        for (int j = 0; j < L; ++j) Dl = std::max(Dl, (int)slot_lst[(R - 1) * L + j].size());
+        int best_t = D0, best_cost = D0 + Dl;
+        for (int t = D0 - 1; t >= 1; --t) {
+            int over = 0;
+            for (int j = 0; j < L; ++j) over += d0[j] > t;
+            if (over > (int)spare.size()) break;
+            const int cost = t + std::max(Dl, D0 - t);
+            if (cost < best_cost) { best_cost = cost; best_t = t; }
+        }
+        if (best_t < D0) {
+            // new row 0: the wide nodes in the free slots' lanes, the others
+            // in the remaining lanes in their order
+            std::vector<int> wide, rest;
+            for (int j = 0; j < L; ++j) (d0[j] > best_t ? wide : rest).push_back(j);
+            std::vector<int> lane_of(L, -1);      // old row-0 lane -> new lane
+            std::vector<char> taken(L, 0);
+            for (size_t k = 0; k < wide.size(); ++k) { lane_of[wide[k]] = spare[k]; taken[spare[k]] = 1; }
+            int nxt = 0;
+            for (int j : rest) {
+                while (taken[nxt]) ++nxt;
+                lane_of[j] = nxt;
+                taken[nxt] = 1;
+            }
+            std::vector<int32_t> node0(L);
+            std::vector<std::vector<int>> lst0(L);
+            for (int j = 0; j < L; ++j) { node0[lane_of[j]] = g.row_node[j]; lst0[lane_of[j]] = slot_lst[j]; }
+            for (int j = 0; j < L; ++j) {
+                g.row_node[j] = node0[j];
+                slot_lst[j] = lst0[j];
+                if (node0[j] >= 0) gslot[node0[j]] = j;
+            }
+            for (size_t k = 0; k < wide.size(); ++k) {
+                const int js = spare[k], cont = (R - 1) * L + js;
+                slot_lst[cont].assign(slot_lst[js].begin() + best_t, slot_lst[js].end());
+                slot_lst[js].resize(best_t);
+                g.row_link[cont] = 1;
+            }
             g.link_to[R - 1] = 0;
         }
     }
