@@ -192,8 +192,9 @@ grins_status grins_racipe_integrate(grins_racipe_t h, const grins_solver_opts *o
  * the lane-group layout (lanes per solve L, node rows R, edge positions P)
  * and whether the kernel specialised to this network at run time (NVRTC)
  * is in use, or why not (before the first FP32 integrate call it reports
- * that nothing has been compiled yet).  The string is owned by the handle
- * and valid until the next call on it. */
+ * that nothing has been compiled yet); after an FP64 integrate call, a
+ * second clause says which FP64 kernel ran.  The string is owned by the
+ * handle and valid until the next call on it. */
 const char *grins_racipe_integrator(grins_racipe_t h);
 
 /* ----------------------------------------------------------------- plans

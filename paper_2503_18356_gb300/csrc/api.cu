@@ -95,6 +95,8 @@ struct grins_racipe {
     GrpDev grp, rr;
     std::string jit_why = "not compiled yet";          // why no run-time compiled kernel is used
     bool jit_used = false;
+    std::string jit_why64;                             // the same for the last FP64 launch
+    bool jit_used64 = false, ran64 = false;
     int used_L = 0, used_R = 0, used_P = 0;            // layout of the last FP32 launch
     std::string info;                                  // grins_racipe_integrator text
     int grid_cap = 0;
@@ -515,6 +517,9 @@ extern "C" const char *grins_racipe_integrator(grins_racipe_t h)
     h->info = buf;
     if (L > 0) h->info += h->jit_used ? "; compiled for this network at run time (" + h->jit_why + ")"
                               : "; run-time layout (" + h->jit_why + ")";
+    if (h->ran64)
+        h->info += h->jit_used64 ? "; FP64 solver compiled for this network at run time (" + h->jit_why64 + ")"
+                                 : "; FP64 solver generic (" + h->jit_why64 + ")";
     return h->info.c_str();
 }
 
@@ -904,10 +909,16 @@ extern "C" grins_status grins_racipe_integrate(grins_racipe_t h, const grins_sol
     a.slots = slots_for(n_ics);
     a.smem_limit = (int32_t)h->smem_optin;
     a.grp = grp_topo(h);
-    if (o->precision == GRINS_FP32) pick_fp32_kernel(h, &a, true, &h->jit_why);
-    else pick_fp64_kernel(h, &a, true, &h->jit_why);
-    h->jit_used = a.grp_jit != nullptr;
-    h->used_L = a.grp.L; h->used_R = a.grp.R; h->used_P = a.grp.P;
+    if (o->precision == GRINS_FP32) {
+        // grins_racipe_integrator describes the FP32 kernel: only its launches record it
+        pick_fp32_kernel(h, &a, true, &h->jit_why);
+        h->jit_used = a.grp_jit != nullptr;
+        h->used_L = a.grp.L; h->used_R = a.grp.R; h->used_P = a.grp.P;
+    } else {
+        pick_fp64_kernel(h, &a, true, &h->jit_why64);
+        h->jit_used64 = a.grp_jit != nullptr;
+        h->ran64 = true;
+    }
 
     CUDA_TRY(cudaMemsetAsync(h->d_queue, 0, 2 * sizeof(unsigned long long), st), "integrate: queue reset");
     cudaError_t le;

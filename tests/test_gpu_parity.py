@@ -163,12 +163,15 @@ def test_n_unique_agreement_net22():
     assert not unexplained, unexplained
 
 
-def test_time_series_fp32():
+@pytest.mark.parametrize("precision", [1, 0])
+def test_time_series(precision):
+    """Time series on a fixed grid (FP32 and the plain FP64 solver), relative
+    1e-3 against the oracle's."""
     w = W.net5_workload()
     h = PT.gpu_handle(w["topology"])
     params, ic, p, icn = PT.gpu_sample(h, w["param_seed"], 40, 8)
     grid = np.linspace(0.0, 30.0, 31)
-    g = run_gpu(h, params, ic, precision=1, polish=0, t_grid=grid)
+    g = run_gpu(h, params, ic, precision=precision, polish=0, t_grid=grid)
     o = oracle_run(w["topology"], p, icn, series=True, t_grid=grid)
     G = p.G[:, None, None, :]; k = p.k[:, None, None, :]
     err = PT.rel_err(g["series"], o["series"], G, k, floor=1e-3)
