@@ -781,11 +781,14 @@ static void pick_fp64_kernel(const grins_racipe *h, IntegrateArgs *a, bool compi
 
 // Tolerance tightening near steady state: below a residual of 10 ss_tol the
 // squared error norm is scaled by 1 / ss_tighten^2 (tolerances times
-// ss_tighten).
+// ss_tighten).  Also fills the FP32 copies of the tolerance arguments, so
+// it follows the assignment of rtol, atol, t_end and ss_tol.
 static void set_tighten(IntegrateArgs *a, const grins_solver_opts *o)
 {
     a->ss_near = 10.0 * o->ss_tol;
     a->ss_gain = 1.0 / (o->ss_tighten * o->ss_tighten);
+    a->f_rtol = (float)a->rtol; a->f_atol = (float)a->atol; a->f_t_end = (float)a->t_end;
+    a->f_ss_tol = (float)a->ss_tol; a->f_ss_near = (float)a->ss_near; a->f_ss_gain = (float)a->ss_gain;
 }
 
 // The FP32 lane-group kernel for h: sets a->grp and a->grp_jit to the

@@ -96,6 +96,9 @@ struct IntegrateArgs {
     double rtol, atol, t0, t_end, ss_tol;
     double ss_near;              // residual below which the tolerances tighten (10 ss_tol)
     double ss_gain;              // factor on the squared error norm there (1 / ss_tighten^2)
+    // the same in FP32 (filled with them): FP32 kernels read these as
+    // constant operands instead of converting the doubles in the loop
+    float f_rtol, f_atol, f_t_end, f_ss_tol, f_ss_near, f_ss_gain;
     int64_t max_steps;
     const double *t_grid;        // device copy, [n_t]
     int32_t n_t;

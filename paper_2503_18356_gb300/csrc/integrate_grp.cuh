@@ -235,9 +235,9 @@ __device__ __forceinline__ void grp_body(const IntegrateArgs &a, unsigned char *
     for (int i = lane; i < 2 * R * kWarp; i += kWarp) gbuf[i] = 0.0f;
     __syncwarp();
 
-    const float rtol = (float)a.rtol, atol = (float)a.atol;
-    const float ss_tol = (float)a.ss_tol;
-    const float t_end = (float)a.t_end;
+    const float rtol = a.f_rtol, atol = a.f_atol;
+    const float ss_tol = a.f_ss_tol;
+    const float t_end = a.f_t_end;
     const float invN = 1.0f / (float)N;
 
     int my_slot = -1, my_ic = 0;
@@ -245,7 +245,7 @@ __device__ __forceinline__ void grp_body(const IntegrateArgs &a, unsigned char *
     float t = 0.0f, h = 0.0f;
     int steps = 0, gidx = 0, buf = 0;
     bool near = false;               // residual below ss_near: tolerances tightened
-    const float ss_near = (float)a.ss_near, ss_gain = (float)a.ss_gain;
+    const float ss_near = a.f_ss_near, ss_gain = a.f_ss_gain;
     bool need_k1 = false, rejected = false, exhausted = false;
     // y: state; k1..k6: stage derivatives; z: stage input, overwritten by
     // the right-hand side.  The last stage input (the fifth-order solution)
@@ -439,12 +439,20 @@ __device__ __forceinline__ void grp_body(const IntegrateArgs &a, unsigned char *
         return grp_max(r, L);
     };
 
+    // warp-wide: some group is working / has just been given a solve (they
+    // change only when a group finishes and the warp refills)
+    bool any_work = false, any_new = false;
+    auto refresh = [&]() {
+        any_work = __any_sync(FULL, my_slot >= 0);
+        any_new = __any_sync(FULL, need_k1);
+    };
     refill();
+    refresh();
 
 #pragma unroll 1
     for (;;) {
         const bool working = my_slot >= 0;
-        if (!__any_sync(FULL, working)) break;
+        if (!any_work) break;
         const unsigned char *sp = slot_ptr(working ? my_slot : 0);
         bool done = false;
         uint8_t st_code = GRINS_SS_TEND;
@@ -456,7 +464,8 @@ __device__ __forceinline__ void grp_body(const IntegrateArgs &a, unsigned char *
         // step attempt, f -> k2 .. k6, then k7 (kept in k2).  Every lane runs
         // every right-hand side (they hold warp barriers); idle and finished
         // groups compute on scratch values and only working groups act.
-        const int s0 = __any_sync(FULL, need_k1) ? 0 : 1;
+        const int s0 = any_new ? 0 : 1;
+        any_new = false;
         auto stage = [&](const int s) {
             if (s == 0) {
 #pragma unroll
@@ -561,9 +570,11 @@ __device__ __forceinline__ void grp_body(const IntegrateArgs &a, unsigned char *
 #endif
 
         // error estimate and step control; k2 now holds the fifth-order
-        // solution and z its derivative k7
+        // solution and z its derivative k7.  A non-finite stage derivative
+        // makes err non-finite -- through the error weights or through the
+        // later stages it feeds -- and with it the norm, the only finiteness
+        // test needed.
         float en = 0.0f;
-        bool finite = true;
 #pragma unroll
         for (int r = 0; r < NPL; ++r) {
             if (r < R) {
@@ -572,17 +583,15 @@ __device__ __forceinline__ void grp_body(const IntegrateArgs &a, unsigned char *
                 const float sc = atol + rtol * fmaxf(fabsf(y[r]), fabsf(k2[r]));
                 const float q = div_approx(err, sc);
                 en += q * q;
-                finite = finite && isfinite(z[r]) && isfinite(k2[r]);
             }
         }
         en = grp_sum(en, L) * invN;                   // squared RMS error norm
         if (near) en *= ss_gain;
-        finite = grp_all(finite, L);
         const float res = residual(z, sp);
 
         if (working && !done) {
             ++steps;
-            if (!finite || !isfinite(en)) {
+            if (!isfinite(en)) {
                 done = true; st_code = GRINS_SS_NONFINITE;
             } else if (en < 1.0f) {
                 const float t_new = clipped ? t_stop : t + hh;
@@ -636,6 +645,7 @@ __device__ __forceinline__ void grp_body(const IntegrateArgs &a, unsigned char *
             }
             __syncwarp();
             refill();
+            refresh();
         }
     }
 }

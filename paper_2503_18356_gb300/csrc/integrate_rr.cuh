@@ -348,6 +348,15 @@ __device__ __forceinline__ double rr_min(double a, double b) { return fmin(a, b)
 __device__ __forceinline__ float rr_sqrt(float a) { return sqrtf(a); }
 __device__ __forceinline__ double rr_sqrt(double a) { return sqrt(a); }
 
+// A tolerance argument in the kernel's precision (FP32 kernels read the
+// launcher's FP32 copy).
+template <typename Real>
+__device__ __forceinline__ Real rr_argr(double d, float f)
+{
+    if constexpr (sizeof(Real) == 4) return f;
+    else return d;
+}
+
 template <typename Real>
 __device__ __forceinline__ Real rr_gsum(Real v, int L)
 {
@@ -437,9 +446,9 @@ __device__ __forceinline__ void rr_body(const IntegrateArgs &a)
     for (int r = 0; r < NPL; ++r) { q.Gp[r] = 0; q.k[r] = 1; q.kg[r] = 0; }
     rr_syncwarp();
 
-    const Real rtol = (Real)a.rtol, atol = (Real)a.atol;
-    const Real ss_tol = (Real)a.ss_tol;
-    const Real t_end = (Real)a.t_end;
+    const Real rtol = rr_argr<Real>(a.rtol, a.f_rtol), atol = rr_argr<Real>(a.atol, a.f_atol);
+    const Real ss_tol = rr_argr<Real>(a.ss_tol, a.f_ss_tol);
+    const Real t_end = rr_argr<Real>(a.t_end, a.f_t_end);
     const Real invN = (Real)1 / (Real)N;
     const long long total = a.n_sets * (long long)a.n_ics;
 
@@ -449,7 +458,7 @@ __device__ __forceinline__ void rr_body(const IntegrateArgs &a)
     Real t = 0, h = 0;
     int steps = 0, gidx = 0;
     bool near = false;               // residual below ss_near: tolerances tightened
-    const Real ss_near = (Real)a.ss_near, ss_gain = (Real)a.ss_gain;
+    const Real ss_near = rr_argr<Real>(a.ss_near, a.f_ss_near), ss_gain = rr_argr<Real>(a.ss_gain, a.f_ss_gain);
     bool need_k1 = false, rejected = false;
     Real y[NPL], k1[NPL], k2[NPL], k3[NPL], k4[NPL], k5[NPL], k6[NPL], z[NPL];
 #pragma unroll
@@ -525,18 +534,27 @@ __device__ __forceinline__ void rr_body(const IntegrateArgs &a)
         return rr_gmax(r, L);
     };
 
+    // warp-wide: some group is working / has just started a solve (they
+    // change only when a group finishes and the warp fetches)
+    bool any_work = false, any_new = false;
+    auto refresh = [&]() {
+        any_work = __any_sync(FULL, working);
+        any_new = __any_sync(FULL, need_k1);
+    };
     fetch();
+    refresh();
 
 #pragma unroll 1
     for (;;) {
-        if (!__any_sync(FULL, working)) break;
+        if (!any_work) break;
         bool done = false;
         uint8_t st_code = GRINS_SS_TEND;
 
         // first derivative and starting step of freshly started solves
         // (only when some group has one); idle and finished groups compute on
         // scratch values throughout and only working groups act
-        if (__any_sync(FULL, need_k1)) {
+        if (any_new) {
+            any_new = false;
             rr_syncwarp();                        // buffer 1 was read by the last stage
 #pragma unroll
             for (int r = 0; r < NPL; ++r) z[r] = y[r];
@@ -610,8 +628,11 @@ __device__ __forceinline__ void rr_body(const IntegrateArgs &a)
         }
         rr_rhs<1>(q, lk, z, own);                     // z = k7
 
+        // A non-finite stage derivative makes err non-finite -- through the
+        // error weights or through the later stages it feeds -- and with it
+        // the norm, which is therefore the only finiteness test needed (the
+        // new state is finite whenever every stage derivative is).
         Real en = 0;
-        bool finite = true;
 #pragma unroll
         for (int r = 0; r < NPL; ++r) {
             const Real err = hh * ((Real)dp::e1 * k1[r] + (Real)dp::e3 * k3[r] + (Real)dp::e4 * k4[r] +
@@ -619,16 +640,14 @@ __device__ __forceinline__ void rr_body(const IntegrateArgs &a)
             const Real sc = atol + rtol * rr_max(rr_abs(y[r]), rr_abs(k2[r]));
             const Real qq = rr_div(err, sc);
             en += qq * qq;
-            finite = finite && isfinite(z[r]) && isfinite(k2[r]);
         }
         en = rr_gsum(en, L) * invN;                   // squared RMS error norm
         if (near) en *= ss_gain;
-        finite = grp_all(finite, L);
         const Real res = residual(z);
 
         if (working && !done) {
             ++steps;
-            if (!finite || !isfinite(en)) {
+            if (!isfinite(en)) {
                 done = true; st_code = GRINS_SS_NONFINITE;
             } else if (en < 1.0f) {
                 const Real t_new = clipped ? t_stop : t + hh;
@@ -679,6 +698,7 @@ __device__ __forceinline__ void rr_body(const IntegrateArgs &a)
                 working = false;
             }
             fetch();
+            refresh();
         }
     }
 }

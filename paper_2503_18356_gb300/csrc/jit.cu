@@ -92,7 +92,20 @@ NvrtcApi &nvrtc()
     return api;
 }
 
-constexpr int kJitWarps = 4;
+constexpr int kJitWarps = 4;         // warps per block of the shared-record kernel
+
+// Warps per block of a register-record kernel: 4, or GRINS_JIT_WARPS (1, 2,
+// 4 or 8; a tuning knob -- the kernel's warps are independent, so the block
+// size only sets the granularity of residency).
+int jit_warps(int kind)
+{
+    if (kind == kJitShared) return kJitWarps;
+    if (const char *ev = std::getenv("GRINS_JIT_WARPS")) {
+        const int w = std::atoi(ev);
+        if (w == 1 || w == 2 || w == 4 || w == 8) return w;
+    }
+    return kJitWarps;
+}
 
 // One cache entry: a kernel for one (layout, kind), compiled once per
 // process, in the calling thread or in the background pool.
@@ -100,6 +113,7 @@ struct JitEntry {
     std::atomic<int> state{0};   // 0 compiling, 1 ready, -1 failed
     std::string why;
     int kind = kJitShared;
+    int warps = kJitWarps;       // warps per block
     cudaLibrary_t lib = nullptr;
     cudaKernel_t kern = nullptr;
 };
@@ -167,7 +181,7 @@ void jit_pool_push(std::function<void()> f)
 }
 
 // Generated prelude + kernel wrapper for one layout.
-std::string jit_main(const GrpTopo &g, int kind, int minb)
+std::string jit_main(const GrpTopo &g, int kind, int minb, int warps)
 {
     std::string s;
     char buf[256];
@@ -200,7 +214,7 @@ std::string jit_main(const GrpTopo &g, int kind, int minb)
         std::snprintf(buf, sizeof(buf),
                       "extern \"C\" __global__ void __launch_bounds__(%d, %d) grins_grp_ct(const grins::IntegrateArgs a)\n"
                       "{\n    grins::rr_body<%d, %d, %d, %s>(a);\n}\n",
-                      kJitWarps * kWarp, minb, g.R, kJitWarps, g.L, kind == kJitRegisters64 ? "double" : "float");
+                      warps * kWarp, minb, g.R, warps, g.L, kind == kJitRegisters64 ? "double" : "float");
     } else {
         s += "}\n#include \"integrate_grp.cuh\"\n";
         std::snprintf(buf, sizeof(buf),
@@ -270,7 +284,8 @@ JitBuild jit_compile(const std::string &src)
 // register records from the estimate of a lane's registers (about 4 per edge
 // position and 11 per row on top of ~40; ptxas usually fits a little more
 // than the estimate, and a spilling compile is retried with one block
-// fewer).  GRINS_JIT_MINB overrides it (a tuning knob).
+// fewer).  Counted in blocks of 4 warps and scaled to the kernel's block
+// size; GRINS_JIT_MINB overrides it in blocks of that size (a tuning knob).
 int jit_minb(const GrpTopo &g, int kind)
 {
     const int est = 4 * g.P + 11 * g.R + 40;
@@ -279,9 +294,11 @@ int jit_minb(const GrpTopo &g, int kind)
         const int est64 = 5 * g.P + 22 * g.R + 60;
         minb = est64 <= 128 ? 4 : (est64 <= 168 ? 3 : 2);
     }
+    const int w = jit_warps(kind);
+    minb = std::max(1, minb * kJitWarps / w);
     if (const char *ev = std::getenv("GRINS_JIT_MINB")) {
         const int m = std::atoi(ev);
-        if (m >= 1 && m <= 8) minb = m;
+        if (m >= 1 && m * w <= 64) minb = m;
     }
     return minb;
 }
@@ -293,9 +310,10 @@ void jit_build_entry(JitEntry &e, const GrpTopo &g, int kind, int dev)
 {
     cudaSetDevice(dev);
     int minb = jit_minb(g, kind);
+    const int warps = jit_warps(kind);
     JitBuild b;
     for (;;) {
-        b = jit_compile(jit_main(g, kind, minb));
+        b = jit_compile(jit_main(g, kind, minb, warps));
         if (b.ok && kind != kJitShared && b.spill_bytes > 0 && minb > 1 && !std::getenv("GRINS_JIT_MINB")) {
             cudaLibraryUnload(b.lib);
             --minb;
@@ -307,6 +325,7 @@ void jit_build_entry(JitEntry &e, const GrpTopo &g, int kind, int dev)
     {
         std::lock_guard<std::mutex> lock(c.mu);
         e.why = b.why;
+        e.warps = warps;
         e.lib = b.lib;
         e.kern = b.kern;
         e.state.store(b.ok ? 1 : -1);
@@ -322,7 +341,7 @@ enum JitMode { kLookup = 0, kCompileHere = 1, kCompileAsync = 2 };
 // queues a background compile when absent and returns at once.
 std::shared_ptr<JitEntry> jit_get(const GrpTopo &g, int kind, int mode)
 {
-    const std::string key = jit_main(g, kind, jit_minb(g, kind));
+    const std::string key = jit_main(g, kind, jit_minb(g, kind), jit_warps(kind));
     JitCache &c = jit_cache();
     std::unique_lock<std::mutex> lock(c.mu);
     auto it = c.map.find(key);
@@ -394,9 +413,10 @@ cudaError_t launch_grp_jit(const void *handle, const IntegrateArgs &a, cudaStrea
     const JitEntry *je = static_cast<const JitEntry *>(handle);
     if (je->state.load() != 1) return cudaErrorInvalidValue;
     IntegrateArgs b = a;
+    const int W = je->warps;
     int smem = 0;
     if (je->kind == kJitRegisters || je->kind == kJitRegisters64) {
-        smem = je->kind == kJitRegisters ? kJitWarps * rr_warp_bytes(b.grp.R, 1, 4) : kJitWarps * rr_warp_bytes(b.grp.R, 6, 8);
+        smem = je->kind == kJitRegisters ? W * rr_warp_bytes(b.grp.R, 1, 4) : W * rr_warp_bytes(b.grp.R, 6, 8);
     } else {
         const int ndom = grp_domains(b.grp.L);
         GrpLayout LY{b.grp.L, b.grp.R, b.grp.P, b.slots};
@@ -408,17 +428,17 @@ cudaError_t launch_grp_jit(const void *handle, const IntegrateArgs &a, cudaStrea
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (err != cudaSuccess) return err;
     int per_sm = 0;
-    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kJitWarps * kWarp, smem);
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, W * kWarp, smem);
     if (err != cudaSuccess) return err;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     const int groups = kWarp / b.grp.L;
     const long long work_warps = (b.n_sets * b.n_ics + groups - 1) / groups + 1;
     long long blocks = (long long)num_sms * per_sm;
-    const long long need = (work_warps + kJitWarps - 1) / kJitWarps;
+    const long long need = (work_warps + W - 1) / W;
     if (blocks > need) blocks = need;
     if (blocks < 1) blocks = 1;
     void *args[] = {&b};
-    err = cudaLaunchKernel(kern, dim3((unsigned)blocks), dim3(kJitWarps * kWarp), args, (size_t)smem, st);
+    err = cudaLaunchKernel(kern, dim3((unsigned)blocks), dim3(W * kWarp), args, (size_t)smem, st);
     if (err != cudaSuccess) return err;
     return cudaGetLastError();
 }
