@@ -789,6 +789,7 @@ static void set_tighten(IntegrateArgs *a, const grins_solver_opts *o)
     a->ss_gain = 1.0 / (o->ss_tighten * o->ss_tighten);
     a->f_rtol = (float)a->rtol; a->f_atol = (float)a->atol; a->f_t_end = (float)a->t_end;
     a->f_ss_tol = (float)a->ss_tol; a->f_ss_near = (float)a->ss_near; a->f_ss_gain = (float)a->ss_gain;
+    a->max_steps32 = (int32_t)std::min<int64_t>(o->max_steps, INT32_MAX);
 }
 
 // The FP32 lane-group kernel for h: sets a->grp and a->grp_jit to the

@@ -100,6 +100,7 @@ struct IntegrateArgs {
     // constant operands instead of converting the doubles in the loop
     float f_rtol, f_atol, f_t_end, f_ss_tol, f_ss_near, f_ss_gain;
     int64_t max_steps;
+    int32_t max_steps32;         // max_steps clamped to the int32 range (filled with the copies above)
     const double *t_grid;        // device copy, [n_t]
     int32_t n_t;
     double *states;              // [S][I][N]

@@ -266,7 +266,7 @@ __device__ __forceinline__ void grp_body(const IntegrateArgs &a, unsigned char *
         buf ^= 1;
 #pragma unroll
         for (int r = 0; r < NPL; ++r)
-            if (r < R) gb[r * kWarp + col] = lg2_approx(fmaxf(z[r], 0.0f));
+            if (r < R) gb[r * kWarp + col] = lg2_approx(fabsf(z[r]));   // |z|: see rr_put
         __syncwarp();
         GrpCtx c;
         c.ed = reinterpret_cast<const float4 *>(sp) + j;
@@ -455,7 +455,7 @@ __device__ __forceinline__ void grp_body(const IntegrateArgs &a, unsigned char *
         if (!any_work) break;
         const unsigned char *sp = slot_ptr(working ? my_slot : 0);
         bool done = false;
-        uint8_t st_code = GRINS_SS_TEND;
+        int st_code = GRINS_SS_TEND;
         float t_stop = t_end, hh = 0.0f;
         bool to_grid = false, clipped = false;
 
@@ -591,6 +591,10 @@ __device__ __forceinline__ void grp_body(const IntegrateArgs &a, unsigned char *
 
         if (working && !done) {
             ++steps;
+            // controller 0.9 err^(-1/5), err = sqrt(en), evaluated once for
+            // accepted and rejected attempts (en = 0 gives +inf, which the
+            // growth limit clamps)
+            const float fr = 0.9f * ex2_approx(-0.1f * lg2_approx(en));
             if (!isfinite(en)) {
                 done = true; st_code = GRINS_SS_NONFINITE;
             } else if (en < 1.0f) {
@@ -603,11 +607,7 @@ __device__ __forceinline__ void grp_body(const IntegrateArgs &a, unsigned char *
 #pragma unroll 1
                     while (gidx < a.n_t && (float)a.t_grid[gidx] <= t) { write_series(gidx); ++gidx; }
                 }
-                // controller 0.9 err^(-1/5), err = sqrt(en)
-                float fac = en == 0.0f ? 10.0f : 0.9f * ex2_approx(-0.1f * lg2_approx(en));
-                fac = fminf(fac, 10.0f);
-                if (rejected) fac = fminf(fac, 1.0f);
-                h = hh * fac;
+                h = hh * fminf(fr, rejected ? 1.0f : 10.0f);   // no growth right after a rejection
                 rejected = false;
                 near = res < ss_near;
                 if (!done) {
@@ -615,10 +615,10 @@ __device__ __forceinline__ void grp_body(const IntegrateArgs &a, unsigned char *
                     else if (t >= t_end) { done = true; st_code = GRINS_SS_TEND; }
                 }
             } else {
-                h = hh * fmaxf(0.9f * ex2_approx(-0.1f * lg2_approx(en)), 0.2f);
+                h = hh * fmaxf(fr, 0.2f);
                 rejected = true;
             }
-            if (!done && steps >= a.max_steps) { done = true; st_code = GRINS_SS_MAXSTEPS; }
+            if (!done && steps >= a.max_steps32) { done = true; st_code = GRINS_SS_MAXSTEPS; }
         }
 
         if (__any_sync(FULL, done)) {
@@ -634,7 +634,7 @@ __device__ __forceinline__ void grp_body(const IntegrateArgs &a, unsigned char *
                     }
                 }
                 if (j == 0) {
-                    a.status[idx] = st_code;
+                    a.status[idx] = (uint8_t)st_code;
                     if (a.t_final) a.t_final[idx] = (double)t;
                     if (a.n_steps) a.n_steps[idx] = steps;
                 }

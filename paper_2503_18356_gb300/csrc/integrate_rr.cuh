@@ -77,17 +77,34 @@ struct RrRecs {
     float Gp[NPL], k[NPL], kg[NPL];        // G' = G prod_inh lambda, k, k/G of this lane's rows
 };
 
-// Positions P, P+1 (record pair Q) into (num, den); FIRST starts the chunk.
-template <int BO, int P, int Q, bool FIRST, int NPL>
+// A chunk of five or six factors shares one division: the y component of
+// its first pair carries an extra factor 2^-60 in numerator and denominator
+// alike (its record holds -n log2 T - 60 and 2^-60 / lambda), which keeps
+// both products of six factors of at most 2^30 + 1 within FP32 range.
+template <int r>
+__device__ constexpr bool rr_scaled_pair(int i)
+{
+    constexpr int D = GrpRowCt<r>::deg, NP = D / 2;
+    constexpr bool TAIL = (D & 1) != 0;
+    if (i % 4 != 0 || i >= NP) return false;
+    const int np = NP - i < 4 ? NP - i : 4;
+    const bool tail = TAIL && i + np >= NP && np < 4;
+    const int f = 2 * np + (tail ? 1 : 0);
+    return f >= 5 && f <= 6;
+}
+
+// Positions P, P+1 (record pair Q) into (num, den); FIRST starts the chunk,
+// SC: its y component is scaled by 2^-60 (rr_scaled_pair).
+template <int BO, int P, int Q, bool FIRST, bool SC, int NPL>
 __device__ __forceinline__ void rr_pair(const RrRecs<NPL> &q, float2 &num, float2 &den)
 {
     const float2 s = make_float2(rr_lds<BO>(q.ga[P]), rr_lds<BO>(q.ga[P + 1]));
     const float2 t = __ffma2_rn(q.n[Q], s, q.c[Q]);
-    const float2 pw = make_float2(ex2_approx(fminf(t.x, 30.0f)), ex2_approx(fminf(t.y, 30.0f)));
+    const float2 pw = make_float2(ex2_approx(fminf(t.x, 30.0f)), ex2_approx(fminf(t.y, SC ? -30.0f : 30.0f)));
     const float2 a = __fadd2_rn(pw, q.u[Q]);
     if constexpr (FIRST) {
         num = a;
-        den = __fadd2_rn(pw, make_float2(1.0f, 1.0f));
+        den = __fadd2_rn(pw, make_float2(1.0f, SC ? 0x1p-60f : 1.0f));
     } else {
         num = __fmul2_rn(num, a);
         den = __ffma2_rn(den, pw, den);
@@ -109,12 +126,12 @@ __device__ __forceinline__ void rr_single(const RrRecs<NPL> &q, float &num, floa
     }
 }
 
-template <int BO, int P0, int Q0, int I, int NP, int NPL>
+template <int BO, int P0, int Q0, int I, int NP, bool SC, int NPL>
 __device__ __forceinline__ void rr_pairs(const RrRecs<NPL> &q, float2 &num, float2 &den)
 {
     if constexpr (I < NP) {
-        rr_pair<BO, P0 + 2 * I, Q0 + I, I == 0, NPL>(q, num, den);
-        rr_pairs<BO, P0, Q0, I + 1, NP, NPL>(q, num, den);
+        rr_pair<BO, P0 + 2 * I, Q0 + I, I == 0, SC && I == 0, NPL>(q, num, den);
+        rr_pairs<BO, P0, Q0, I + 1, NP, SC, NPL>(q, num, den);
     }
 }
 
@@ -126,9 +143,10 @@ template <int BO, int P0, int Q0, int NP, bool TAIL, int NPL>
 __device__ __forceinline__ float rr_chunk(const RrRecs<NPL> &q)
 {
     float2 num, den;
-    rr_pairs<BO, P0, Q0, 0, NP, NPL>(q, num, den);
+    constexpr int F = 2 * NP + (TAIL ? 1 : 0);
+    rr_pairs<BO, P0, Q0, 0, NP, F >= 5 && F <= 6, NPL>(q, num, den);
     if constexpr (TAIL) rr_single<BO, P0 + 2 * NP, Q0 + NP, false, NPL>(q, num.x, den.x);
-    if constexpr (2 * NP + (TAIL ? 1 : 0) <= 4)
+    if constexpr (F <= 6)
         return div_approx(num.x * num.y, den.x * den.y);
     else
         return div_approx(num.x, den.x) * div_approx(num.y, den.y);
@@ -193,12 +211,18 @@ __device__ __forceinline__ void rr_update(const Recs &q, const Real (&prod)[NPL]
     for (int r = 0; r < NPL; ++r) z[r] = rr_fma(q.Gp[r], prod[r], -q.k[r] * z[r]);
 }
 
-// log2 of this lane's stage values into its column of the buffer at BO
+// log2 of this lane's stage values into its column of the buffer at BO.
+// The log-domain edge term reads a stage value through |z| (an operand
+// modifier of the log2, no instruction) where Eq. 2 reads a negative value
+// as 0: a small overshoot -delta << T below zero gives the same factor to
+// within (delta / T)^n, and the exact solution never goes below zero, so
+// only a stage far off the trajectory -- an inaccurate attempt -- sees a
+// difference.
 template <int BO, int r, int NPL>
 __device__ __forceinline__ void rr_put(const float (&z)[NPL], unsigned own)
 {
     if constexpr (r < kGrpCtRows && r < NPL) {
-        rr_sts<BO + r * kWarp * 4>(own, lg2_approx(fmaxf(z[r], 0.0f)));
+        rr_sts<BO + r * kWarp * 4>(own, lg2_approx(fabsf(z[r])));
         rr_put<BO, r + 1, NPL>(z, own);
     }
 }
@@ -390,10 +414,71 @@ __device__ __forceinline__ void rr_load_rows(RrRecs<NPL> &q, const IntegrateArgs
                 c = -n * log2f((float)Td[e]);
                 u = __frcp_rn((float)ld[e]);
             }
+            if ((d & 1) && rr_scaled_pair<r>(d / 2)) { c -= 60.0f; u *= 0x1p-60f; }
             if (d & 1) { q.n[Q0 + d / 2].y = n; q.c[Q0 + d / 2].y = c; q.u[Q0 + d / 2].y = u; }
             else       { q.n[Q0 + d / 2].x = n; q.c[Q0 + d / 2].x = c; q.u[Q0 + d / 2].x = u; }
         }
         rr_load_rows<r + 1, NPL, L>(q, a, blk, j, 0u);
+    }
+}
+
+// Stage combinations out[r] = (ADD_Y ? y[r] : 0) + hh (c1 k1[r] + c2 k2[r]
+// + ...), the sum taken left to right.  FP32 rows go two at a time through
+// the packed pair instructions (each component rounds as the scalar
+// operation would); an odd last row and FP64 rows go one at a time.
+template <int NPL>
+__device__ __forceinline__ void rr_acc2(float2 &s, int r, float c, const float (&k)[NPL])
+{
+    s = __ffma2_rn(make_float2(c, c), make_float2(k[r], k[r + 1]), s);
+}
+template <int NPL, typename... Ts>
+__device__ __forceinline__ void rr_acc2(float2 &s, int r, float c, const float (&k)[NPL], const Ts &...ts)
+{
+    rr_acc2<NPL>(s, r, c, k);
+    rr_acc2<NPL>(s, r, ts...);
+}
+template <int NPL, typename Real>
+__device__ __forceinline__ void rr_acc1(Real &s, int r, Real c, const Real (&k)[NPL])
+{
+    s = rr_fma(c, k[r], s);
+}
+template <int NPL, typename Real, typename... Ts>
+__device__ __forceinline__ void rr_acc1(Real &s, int r, Real c, const Real (&k)[NPL], const Ts &...ts)
+{
+    rr_acc1<NPL, Real>(s, r, c, k);
+    rr_acc1<NPL, Real>(s, r, ts...);
+}
+
+template <bool ADD_Y, int NPL, typename... Ts>
+__device__ __forceinline__ void rr_comb(float (&out)[NPL], const float (&y)[NPL], float hh, float c,
+                                        const float (&k)[NPL], const Ts &...ts)
+{
+#pragma unroll
+    for (int r = 0; r + 1 < NPL; r += 2) {
+        float2 s = __fmul2_rn(make_float2(c, c), make_float2(k[r], k[r + 1]));
+        if constexpr (sizeof...(Ts) > 0) rr_acc2<NPL>(s, r, ts...);
+        const float2 o = ADD_Y ? __ffma2_rn(make_float2(hh, hh), s, make_float2(y[r], y[r + 1]))
+                               : __fmul2_rn(make_float2(hh, hh), s);
+        out[r] = o.x;
+        out[r + 1] = o.y;
+    }
+    if constexpr (NPL % 2 == 1) {
+        constexpr int r = NPL - 1;
+        float s = c * k[r];
+        if constexpr (sizeof...(Ts) > 0) rr_acc1<NPL, float>(s, r, ts...);
+        out[r] = ADD_Y ? fmaf(hh, s, y[r]) : hh * s;
+    }
+}
+
+template <bool ADD_Y, int NPL, typename... Ts>
+__device__ __forceinline__ void rr_comb(double (&out)[NPL], const double (&y)[NPL], double hh, double c,
+                                        const double (&k)[NPL], const Ts &...ts)
+{
+#pragma unroll
+    for (int r = 0; r < NPL; ++r) {
+        double s = c * k[r];
+        if constexpr (sizeof...(Ts) > 0) rr_acc1<NPL, double>(s, r, ts...);
+        out[r] = ADD_Y ? fma(hh, s, y[r]) : hh * s;
     }
 }
 
@@ -548,7 +633,7 @@ __device__ __forceinline__ void rr_body(const IntegrateArgs &a)
     for (;;) {
         if (!any_work) break;
         bool done = false;
-        uint8_t st_code = GRINS_SS_TEND;
+        int st_code = GRINS_SS_TEND;
 
         // first derivative and starting step of freshly started solves
         // (only when some group has one); idle and finished groups compute on
@@ -589,54 +674,44 @@ __device__ __forceinline__ void rr_body(const IntegrateArgs &a)
         Real hh = h;
         if (t + hh >= t_stop) { hh = t_stop - t; clipped = true; }
 
-#pragma unroll
-        for (int r = 0; r < NPL; ++r) z[r] = y[r] + hh * ((Real)dp::a21 * k1[r]);
+        rr_comb<true>(z, y, hh, (Real)dp::a21, k1);
         rr_rhs<0>(q, lk, z, own);
 #pragma unroll
-        for (int r = 0; r < NPL; ++r) {
-            k2[r] = z[r];
-            z[r] = y[r] + hh * ((Real)dp::a31 * k1[r] + (Real)dp::a32 * k2[r]);
-        }
+        for (int r = 0; r < NPL; ++r) k2[r] = z[r];
+        rr_comb<true>(z, y, hh, (Real)dp::a31, k1, (Real)dp::a32, k2);
         rr_rhs<1>(q, lk, z, own);
 #pragma unroll
-        for (int r = 0; r < NPL; ++r) {
-            k3[r] = z[r];
-            z[r] = y[r] + hh * ((Real)dp::a41 * k1[r] + (Real)dp::a42 * k2[r] + (Real)dp::a43 * k3[r]);
-        }
+        for (int r = 0; r < NPL; ++r) k3[r] = z[r];
+        rr_comb<true>(z, y, hh, (Real)dp::a41, k1, (Real)dp::a42, k2, (Real)dp::a43, k3);
         rr_rhs<0>(q, lk, z, own);
 #pragma unroll
-        for (int r = 0; r < NPL; ++r) {
-            k4[r] = z[r];
-            z[r] = y[r] + hh * ((Real)dp::a51 * k1[r] + (Real)dp::a52 * k2[r] + (Real)dp::a53 * k3[r] +
-                                (Real)dp::a54 * k4[r]);
-        }
+        for (int r = 0; r < NPL; ++r) k4[r] = z[r];
+        rr_comb<true>(z, y, hh, (Real)dp::a51, k1, (Real)dp::a52, k2, (Real)dp::a53, k3, (Real)dp::a54, k4);
         rr_rhs<1>(q, lk, z, own);
 #pragma unroll
-        for (int r = 0; r < NPL; ++r) {
-            k5[r] = z[r];
-            z[r] = y[r] + hh * ((Real)dp::a61 * k1[r] + (Real)dp::a62 * k2[r] + (Real)dp::a63 * k3[r] +
-                                (Real)dp::a64 * k4[r] + (Real)dp::a65 * k5[r]);
-        }
+        for (int r = 0; r < NPL; ++r) k5[r] = z[r];
+        rr_comb<true>(z, y, hh, (Real)dp::a61, k1, (Real)dp::a62, k2, (Real)dp::a63, k3, (Real)dp::a64, k4,
+                      (Real)dp::a65, k5);
         rr_rhs<0>(q, lk, z, own);
 #pragma unroll
-        for (int r = 0; r < NPL; ++r) {
-            k6[r] = z[r];
-            // fifth-order solution in k2 (no later stage reads k2)
-            k2[r] = y[r] + hh * ((Real)dp::b1 * k1[r] + (Real)dp::b3 * k3[r] + (Real)dp::b4 * k4[r] +
-                                 (Real)dp::b5 * k5[r] + (Real)dp::b6 * k6[r]);
-            z[r] = k2[r];
-        }
+        for (int r = 0; r < NPL; ++r) k6[r] = z[r];
+        // fifth-order solution in k2 (no later stage reads k2)
+        rr_comb<true>(k2, y, hh, (Real)dp::b1, k1, (Real)dp::b3, k3, (Real)dp::b4, k4, (Real)dp::b5, k5,
+                      (Real)dp::b6, k6);
+#pragma unroll
+        for (int r = 0; r < NPL; ++r) z[r] = k2[r];
         rr_rhs<1>(q, lk, z, own);                     // z = k7
 
         // A non-finite stage derivative makes err non-finite -- through the
         // error weights or through the later stages it feeds -- and with it
         // the norm, which is therefore the only finiteness test needed (the
         // new state is finite whenever every stage derivative is).
-        Real en = 0;
+        Real en = 0, ev[NPL];
+        rr_comb<false>(ev, y, hh, (Real)dp::e1, k1, (Real)dp::e3, k3, (Real)dp::e4, k4, (Real)dp::e5, k5,
+                       (Real)dp::e6, k6, (Real)dp::e7, z);
 #pragma unroll
         for (int r = 0; r < NPL; ++r) {
-            const Real err = hh * ((Real)dp::e1 * k1[r] + (Real)dp::e3 * k3[r] + (Real)dp::e4 * k4[r] +
-                                    (Real)dp::e5 * k5[r] + (Real)dp::e6 * k6[r] + (Real)dp::e7 * z[r]);
+            const Real err = ev[r];
             const Real sc = atol + rtol * rr_max(rr_abs(y[r]), rr_abs(k2[r]));
             const Real qq = rr_div(err, sc);
             en += qq * qq;
@@ -645,38 +720,37 @@ __device__ __forceinline__ void rr_body(const IntegrateArgs &a)
         if (near) en *= ss_gain;
         const Real res = residual(z);
 
-        if (working && !done) {
+        // step control of the working groups: controller 0.9 err^(-1/5),
+        // err = sqrt(en), evaluated once (en = 0 gives +inf, which the growth
+        // limit clamps); growth at most 10, none right after a rejection,
+        // shrinking at most to 0.2
+        const bool act = working && !done;
+        const bool fin = isfinite(en);
+        const bool acc = act && fin && en < (Real)1;
+        const float fr = 0.9f * ex2_approx(-0.1f * lg2_approx((float)en));
+        const float fac = acc ? fminf(fr, rejected ? 1.0f : 10.0f) : fmaxf(fr, 0.2f);
+        const Real t_new = clipped ? t_stop : t + hh;
+        if (act) {
             ++steps;
-            if (!isfinite(en)) {
-                done = true; st_code = GRINS_SS_NONFINITE;
-            } else if (en < 1.0f) {
-                const Real t_new = clipped ? t_stop : t + hh;
-                if (!(t_new > t)) { done = true; st_code = GRINS_SS_NONFINITE; }
-                t = t_new;
-#pragma unroll
-                for (int r = 0; r < NPL; ++r) { y[r] = k2[r]; k1[r] = z[r]; }
-                if (clipped && to_grid) {
-#pragma unroll 1
-                    while (gidx < a.n_t && (Real)a.t_grid[gidx] <= t) { write_series(gidx); ++gidx; }
-                }
-                // controller 0.9 err^(-1/5), err = sqrt(en)
-                const float enf = (float)en;
-                float fac = enf == 0.0f ? 10.0f : 0.9f * ex2_approx(-0.1f * lg2_approx(enf));
-                fac = fminf(fac, 10.0f);
-                if (rejected) fac = fminf(fac, 1.0f);
-                h = hh * (Real)fac;
-                rejected = false;
-                near = res < ss_near;
-                if (!done) {
-                    if (res < ss_tol) { done = true; st_code = GRINS_SS_CONVERGED; }
-                    else if (t >= t_end) { done = true; st_code = GRINS_SS_TEND; }
-                }
-            } else {
-                h = hh * (Real)fmaxf(0.9f * ex2_approx(-0.1f * lg2_approx((float)en)), 0.2f);
-                rejected = true;
-            }
-            if (!done && steps >= a.max_steps) { done = true; st_code = GRINS_SS_MAXSTEPS; }
+            h = hh * (Real)fac;
+            rejected = !acc;
+            if (!fin || (acc && !(t_new > t))) { done = true; st_code = GRINS_SS_NONFINITE; }
         }
+        if (acc) {
+            t = t_new;
+#pragma unroll
+            for (int r = 0; r < NPL; ++r) { y[r] = k2[r]; k1[r] = z[r]; }
+            near = res < ss_near;
+            if (!done) {
+                if (res < ss_tol) { done = true; st_code = GRINS_SS_CONVERGED; }
+                else if (t >= t_end) { done = true; st_code = GRINS_SS_TEND; }
+            }
+            if (clipped && to_grid) {
+#pragma unroll 1
+                while (gidx < a.n_t && (Real)a.t_grid[gidx] <= t) { write_series(gidx); ++gidx; }
+            }
+        }
+        if (act && !done && steps >= a.max_steps32) { done = true; st_code = GRINS_SS_MAXSTEPS; }
 
         if (__any_sync(FULL, done)) {
             if (done) {
@@ -689,7 +763,7 @@ __device__ __forceinline__ void rr_body(const IntegrateArgs &a)
                     if (node >= 0) dst[node] = (double)y[r];
                 }
                 if (j == 0) {
-                    a.status[idx] = st_code;
+                    a.status[idx] = (uint8_t)st_code;
                     if (a.t_final) a.t_final[idx] = (double)t;
                     if (a.n_steps) a.n_steps[idx] = steps;
                 }

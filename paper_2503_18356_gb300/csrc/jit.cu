@@ -180,6 +180,19 @@ void jit_pool_push(std::function<void()> f)
     p.cv.notify_one();
 }
 
+// Register cap of a register-record kernel: 0 (residency from the block
+// count, __launch_bounds__), or GRINS_JIT_MAXNREG (64..255, __maxnreg__; a
+// tuning knob -- caps between the launch-bounds steps).
+int jit_maxnreg(int kind)
+{
+    if (kind == kJitShared) return 0;
+    if (const char *ev = std::getenv("GRINS_JIT_MAXNREG")) {
+        const int r = std::atoi(ev);
+        if (r >= 64 && r <= 255) return r;
+    }
+    return 0;
+}
+
 // Generated prelude + kernel wrapper for one layout.
 std::string jit_main(const GrpTopo &g, int kind, int minb, int warps)
 {
@@ -211,10 +224,13 @@ std::string jit_main(const GrpTopo &g, int kind, int minb, int warps)
     }
     if (kind == kJitRegisters || kind == kJitRegisters64) {
         s += "}\n#include \"integrate_rr.cuh\"\n";
+        char bounds[64];
+        if (const int mr = jit_maxnreg(kind)) std::snprintf(bounds, sizeof(bounds), "__maxnreg__(%d)", mr);
+        else std::snprintf(bounds, sizeof(bounds), "__launch_bounds__(%d, %d)", warps * kWarp, minb);
         std::snprintf(buf, sizeof(buf),
-                      "extern \"C\" __global__ void __launch_bounds__(%d, %d) grins_grp_ct(const grins::IntegrateArgs a)\n"
+                      "extern \"C\" __global__ void %s grins_grp_ct(const grins::IntegrateArgs a)\n"
                       "{\n    grins::rr_body<%d, %d, %d, %s>(a);\n}\n",
-                      warps * kWarp, minb, g.R, warps, g.L, kind == kJitRegisters64 ? "double" : "float");
+                      bounds, g.R, warps, g.L, kind == kJitRegisters64 ? "double" : "float");
     } else {
         s += "}\n#include \"integrate_grp.cuh\"\n";
         std::snprintf(buf, sizeof(buf),
@@ -314,7 +330,8 @@ void jit_build_entry(JitEntry &e, const GrpTopo &g, int kind, int dev)
     JitBuild b;
     for (;;) {
         b = jit_compile(jit_main(g, kind, minb, warps));
-        if (b.ok && kind != kJitShared && b.spill_bytes > 0 && minb > 1 && !std::getenv("GRINS_JIT_MINB")) {
+        if (b.ok && kind != kJitShared && b.spill_bytes > 0 && minb > 1 && !std::getenv("GRINS_JIT_MINB") &&
+            !jit_maxnreg(kind)) {
             cudaLibraryUnload(b.lib);
             --minb;
             continue;
