@@ -173,6 +173,10 @@ def parity_figures(gpu, orc, G, k):
     res["fp32_polish"]["error"] = "relative, floor 1e-6 G/k"
     res["fp32_raw"]["error"] = "G/k-normalised"
     res["n_unique_agree"] = float((gpu["n_unique"] == orc["n_unique"]).mean())
+    if "fp64_n_unique" in gpu:
+        # the same figures for the plain FP64 GPU solver at the same tolerances
+        res["fp64_solver"] = dict(status_agree=float((gpu["fp64_status"] == orc["status"]).mean()),
+                                  n_unique_agree=float((gpu["fp64_n_unique"] == orc["n_unique"]).mean()))
     return res
 
 
@@ -464,6 +468,14 @@ def run_native(args):
     e64[1].record(stream)
     barrier()
     fp64_value = f64_sets * I / (e64[0].elapsed_time(e64[1]) / 1e3)
+    if snap is not None and f64_sets >= snap["n_unique"].shape[0]:
+        # the plain FP64 solver's statuses and distinct-state counts on the
+        # oracle's sets (polished and deduplicated as the FP32 path is)
+        P = snap["n_unique"].shape[0]
+        o64 = {k: (v[:P] if v is not None else None) for k, v in out.items()}
+        h.polish(params[:P], o64["states"], o64["status"], o64["err_est"], opts=popts, stream=stream)
+        h.unique_states(params[:P], o64["states"], o64["status"], stream=stream, out=(sid[:P], nu[:P]))
+        snap.update(fp64_status=o64["status"].cpu().numpy(), fp64_n_unique=nu[:P].cpu().numpy())
 
     if rank == 0:
         line = dict(

@@ -127,6 +127,31 @@ def test_random_networks_fp32_polish_and_raw(wl, S):
             assert np.all(g["err_est"][ok] >= 0)
 
 
+@pytest.mark.parametrize("n", [6, 1])
+def test_dense_network_steep_hill_extreme_fold_changes(n):
+    """In-degrees 5-6 (rows whose six factors share one division), every
+    Hill coefficient n, fold changes spanning the full default ranges (down
+    to 1/100 for inhibition): FP32 polished and raw states against the
+    oracle with the usual bars, and no non-finite solve the oracle does not
+    also report."""
+    from paper_2503_18356_gb300 import api
+    topo = W.random_network(11, 8, 44, 22, 2)
+    h = PT.gpu_handle(topo)
+    r = api.default_ranges(n_min=n, n_max=n)
+    params, ic, p, icn = PT.gpu_sample(h, 7, 40, 10, ranges=r)
+    assert np.all(p.n == n)
+    o = O.run_sets_parallel(O.Network(*topo.edges()), p, icn, threads=PT.THREADS)
+    for polish, tol in [(1, 1e-6), (0, 1e-3)]:
+        g = run_gpu(h, params, ic, precision=1, polish=polish)
+        c = PT.compare_states(g, o, p, tol, normalised=not polish)
+        print(n, polish, h.integrator(), c, np.bincount(g["status"].ravel(), minlength=5))
+        assert c["n_compared"] >= 100            # steep Hill: many solves end at t_end on both sides
+        assert c["max_rel"] <= tol
+        assert c["n_basin"] <= max(1, 0.01 * g["status"].size)
+        assert c["status_agree"] >= 0.97
+        assert not np.any((g["status"] == O.NONFINITE) & (o["status"] != O.NONFINITE))
+
+
 def test_fp64_random_network():
     w = W.net22_workload()
     h = PT.gpu_handle(w["topology"])
