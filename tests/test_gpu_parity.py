@@ -86,6 +86,34 @@ def test_unique_states_bit_exact_on_given_states():
         assert rn == nu[s] and np.array_equal(rs, sid[s]), s
 
 
+@pytest.mark.parametrize("N,I,n_centres", [(64, 40, 40), (33, 16, 3)])
+def test_unique_states_bit_exact_wide_sets_and_nan(N, I, n_centres):
+    """Dedupe paths beyond the common case, bit-exact against the oracle:
+    more representatives than the kernel keeps in shared memory (64 nodes,
+    40 distinct states: ten fit), two coordinates per lane (33 and 64
+    nodes), and NaN coordinates (a NaN difference never raises the
+    maximum)."""
+    topo = W.random_network(5, N, 3 * N, N, 0)
+    h = PT.gpu_handle(topo)
+    S = 40
+    params, _, p, _ = PT.gpu_sample(h, 13, S, I)
+    rng = np.random.default_rng(2)
+    centres = rng.uniform(0, 1, (S, n_centres, N))
+    pick = np.tile(np.arange(I) % n_centres, (S, 1))
+    v = np.take_along_axis(centres, pick[:, :, None], axis=1) + rng.normal(0, 0.002, (S, I, N))
+    v[::5, 2, 7] = np.nan
+    v[::3, 0, :] = np.nan
+    states = v * p.G[:, None, :] / p.k[:, None, :]
+    status = (rng.uniform(size=(S, I)) < 0.1).astype(np.uint8)
+    sid, nu = h.unique_states(params, torch.tensor(states, device="cuda"),
+                              torch.tensor(status, device="cuda"), tol=1e-2)
+    sid, nu = sid.cpu().numpy(), nu.cpu().numpy()
+    for s in range(S):
+        rs, rn = O.dedupe(states[s], status[s], p.G[s], p.k[s], tol=1e-2)
+        assert rn == nu[s] and np.array_equal(rs, sid[s]), s
+    assert nu.max() > 10 or n_centres < 10
+
+
 # -------------------------------------------------------------- integrator
 def run_gpu(h, params, ic, **opt):
     out = h.integrate(params, ic, **opt)
