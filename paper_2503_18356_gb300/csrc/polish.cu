@@ -22,13 +22,17 @@
 // FP64 runs at a small fraction of the FP32 rate on this GPU (a warp's FP64
 // instruction occupies the SM's FP64 pipe for about 16 cycles), so the
 // residual is arranged to issue few FP64 warp instructions, each with most
-// lanes busy.  One warp per solve:
-//   * once per solve, lanes over edges (CSR order) tabulate T^n, lambda and
-//     the edge's source, exponent and sign in shared memory;
+// lanes busy.  A warp takes a work unit of one parameter set and up to
+// kUnitIcs of its initial conditions, and polishes the unit's converged
+// solves one after another:
+//   * once per unit, lanes over edges (CSR order) tabulate T^n and the
+//     numerator coefficients (a, b) below with the edge's source, exponent
+//     and sign in shared memory, lanes over nodes the row constants -- the
+//     parameters are the set's, shared by its ICs;
 //   * per residual, lanes over nodes tabulate x^1 .. x^6, lanes over edges
-//     form each factor's numerator lambda x^n + T^n and denominator
-//     (x^n + T^n) c (c = lambda for activating edges, 1 otherwise), and lanes
-//     over rows (targets) multiply their factors and form f_i;
+//     form each factor's numerator a x^n + b (one FMA) and denominator
+//     x^n + T^n (one add), and lanes over rows (targets) multiply their
+//     factors and form f_i;
 //   * the Jacobian is filled edge by edge in FP32; the LU runs in shared
 //     memory, the substitutions with the right-hand side in registers (one
 //     row per lane, values passed by shuffles).
@@ -42,6 +46,7 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int kPow = 6;          // x^1 .. x^6 tabulated per node
+constexpr int kUnitIcs = 4;      // initial conditions per work unit (measured: 1 / 4 / 16 -> 8.95 / 8.10 / 8.30 ms)
 
 __device__ __forceinline__ float warp_maxf(float v)
 {
@@ -66,12 +71,12 @@ __device__ __forceinline__ Real ipow(Real x, int n)
     return p;
 }
 
-// Bytes of the per-warp edge tables for E edges: FP64 T^n, lambda, factor
+// Bytes of the per-warp edge tables for E edges: FP64 T^n, a, b, factor
 // numerator and denominator; int (src << 9 | act << 8 | n) and target row;
 // FP32 (T, lambda).
 __host__ __device__ constexpr long long polish_edge_bytes(int E)
 {
-    return (long long)(E > 0 ? E : 1) * (4 * 8 + 2 * 4 + 8);
+    return (long long)(E > 0 ? E : 1) * (5 * 8 + 2 * 4 + 8);
 }
 
 template <int NMAX, int WARPS>
@@ -98,38 +103,49 @@ __global__ void __launch_bounds__(WARPS * kWarp) polish_kernel(const PolishArgs 
     const int Eb = E > 0 ? E : 1;
     unsigned char *eb = dsm + (long long)w * polish_edge_bytes(E);
     double *tn_e = reinterpret_cast<double *>(eb);
-    double *lam_e = tn_e + Eb;
-    double *num_e = lam_e + Eb;
+    double *a_e = tn_e + Eb;
+    double *b_e = a_e + Eb;
+    double *num_e = b_e + Eb;
     double *den_e = num_e + Eb;
     int *code_e = reinterpret_cast<int *>(den_e + Eb);
     int *row_e = code_e + Eb;
     float2 *tl_e = reinterpret_cast<float2 *>(row_e + Eb);
 
-    for (long long idx = (long long)blockIdx.x * WARPS + w; idx < a.n_solves;
-         idx += (long long)gridDim.x * WARPS) {
-        if (a.status[idx] != GRINS_SS_CONVERGED) {
-            if (lane == 0 && a.err_est) a.err_est[idx] = -1.0f;
-            continue;
+    // target row of every CSR position (the topology's, fixed)
+    for (int i = lane; i < N; i += kWarp)
+        for (int c = a.topo.off[i]; c < a.topo.off[i + 1]; ++c) row_e[c] = i;
+    const int upc = (a.n_ics + kUnitIcs - 1) / kUnitIcs;      // units per set
+    const long long n_units = a.n_ics > 0 ? a.n_solves / a.n_ics * upc : 0;
+    for (long long u = (long long)blockIdx.x * WARPS + w; u < n_units; u += (long long)gridDim.x * WARPS) {
+        const long long set = u / upc;
+        const int ic0 = (int)(u - set * upc) * kUnitIcs;
+        const int ic1 = min(ic0 + kUnitIcs, a.n_ics);
+        // a unit without converged solves needs no tables
+        bool any = false;
+        for (int ic = ic0 + lane; ic < ic1; ic += kWarp) {
+            const long long idx = set * a.n_ics + ic;
+            any = any || a.status[idx] == GRINS_SS_CONVERGED;
+            if (a.status[idx] != GRINS_SS_CONVERGED && a.err_est) a.err_est[idx] = -1.0f;
         }
-        const long long set = idx / a.n_ics;
+        if (!__any_sync(FULL, any)) continue;
         const unsigned char *blk = a.params + set * a.L.stride;
         const double *G = reinterpret_cast<const double *>(blk + a.L.off_G);
         const double *K = reinterpret_cast<const double *>(blk + a.L.off_k);
         const double *T = reinterpret_cast<const double *>(blk + a.L.off_T);
         const double *lam = reinterpret_cast<const double *>(blk + a.L.off_lam);
         const uint8_t *nn = blk + a.L.off_n;
-        double *state = a.states + idx * N;
-        for (int i = lane; i < N; i += kWarp) x[i] = state[i];
 
-        // edge tables (lanes over CSR positions) and row constants
+        // edge tables (lanes over CSR positions) and row constants of the set
         for (int c = lane; c < E; c += kWarp) {
             int e = a.topo.edge[c], s = a.topo.src[c];
             if (!GRINS_OK_IDX(e >= 0 && e < E && s >= 0 && s < N && N <= NMAX, 21, c)) e = s = 0;
             const int n = nn[e];
-            const double Te = T[e], l = lam[e];
-            tn_e[c] = ipow(Te, n);
-            lam_e[c] = l;
-            code_e[c] = (s << 9) | (a.topo.sign[c] > 0 ? 256 : 0) | n;
+            const bool act = a.topo.sign[c] > 0;
+            const double Te = T[e], l = lam[e], tn = ipow(Te, n);
+            tn_e[c] = tn;
+            a_e[c] = act ? 1.0 : l;
+            b_e[c] = act ? tn / l : tn;
+            code_e[c] = (s << 9) | (act ? 256 : 0) | n;
             tl_e[c] = make_float2((float)Te, (float)l);
         }
         double Gr[RPL], Kr[RPL];
@@ -141,217 +157,225 @@ __global__ void __launch_bounds__(WARPS * kWarp) polish_kernel(const PolishArgs 
             if (i < N) {
                 Gr[k] = G[i]; Kr[k] = K[i];
                 kg[k] = (float)(Kr[k] / Gr[k]);
-                for (int c = a.topo.off[i]; c < a.topo.off[i + 1]; ++c) row_e[c] = i;
             }
         }
         __syncwarp();
 
-        // f in FP64 -> b = -f (FP32, one entry per row of this lane); returns
-        // rho.  Each factor of Eq. 2 is written without divisions,
-        //     F_e = (lam x^n + T^n) / ((x^n + T^n) c),  c = lam (activating), 1,
-        // (numerator and denominator of (lam p + 1) / ((1 + p) c) times T^n),
-        // and a row's products are divided once per eight factors (x^n, T^n
-        // stay below ~1e24, so eight factors stay finite).  With `jac` the
-        // FP32 Jacobian is filled in as well.
-        float b[RPL];
-        auto residual = [&](bool jac) -> float {
-            for (int i = lane; i < N; i += kWarp) {
-                const double v = fmax(x[i], 0.0);
-                const double v2 = v * v, v4 = v2 * v2;
-                xp[0][i] = v; xp[1][i] = v2; xp[2][i] = v2 * v;
-                xp[3][i] = v4; xp[4][i] = v4 * v; xp[5][i] = v2 * v4;
-            }
+        for (int ic = ic0; ic < ic1; ++ic) {
+            const long long idx = set * a.n_ics + ic;
+            if (a.status[idx] != GRINS_SS_CONVERGED) continue;
+            double *state = a.states + idx * N;
+            for (int i = lane; i < N; i += kWarp) x[i] = state[i];
             __syncwarp();
-            for (int c = lane; c < E; c += kWarp) {
-                const int code = code_e[c], s = code >> 9, n = code & 255;
-                const double xn = (n >= 1 && n <= kPow) ? xp[n - 1][s] : ipow(fmax(x[s], 0.0), n);
-                const double tn = tn_e[c], l = lam_e[c];
-                num_e[c] = fma(l, xn, tn);
-                den_e[c] = (xn + tn) * ((code & 256) ? l : 1.0);
-            }
-            __syncwarp();
-            float rloc = 0.0f;
-#pragma unroll
-            for (int k = 0; k < RPL; ++k) {
-                const int i = lane + kWarp * k;
-                b[k] = 0.0f;
-                if (i < N) {
-                    double P = 1.0, nu = 1.0, de = 1.0;
-                    int cnt = 0;
-                    for (int c = a.topo.off[i]; c < a.topo.off[i + 1]; ++c) {
-                        nu *= num_e[c];
-                        de *= den_e[c];
-                        if (++cnt == 8) { P *= nu / de; nu = de = 1.0; cnt = 0; }
-                    }
-                    P *= nu / de;
-                    const double gpi = Gr[k] * P;
-                    const double f = gpi - Kr[k] * x[i];
-                    b[k] = (float)(-f);
-                    if (jac) gp[i] = (float)gpi;
-                    rloc = fmaxf(rloc, nan_to_inf(fabsf(b[k]) * kg[k]));
-                }
-            }
-            if (jac) {
-                // J_is = G_i P_i dlog F_e / dx_s for the edge e = (s -> i)
-                // (one edge per pair), then J_ii -= k_i.  dlog F / dx =
-                // n p (lam - 1) / (x (lam p + 1)(1 + p)), p = (x/T)^n, in
-                // FP32 (the Jacobian only steers the iteration); at x = 0
-                // only n = 1 leaves a slope.
-#pragma unroll
-                for (int k = 0; k < RPL; ++k) {
-                    const int i = lane + kWarp * k;
-                    if (i < N)
-                        for (int j = 0; j < N; ++j) J[i][j] = 0.0f;
+
+            // f in FP64 -> b = -f (FP32, one entry per row of this lane); returns
+            // rho.  Each factor of Eq. 2 is written without divisions,
+            //     F_e = (a x^n + b) / (x^n + T^n),
+            //     (a, b) = (1, T^n / lam) activating, (lam, T^n) inhibiting
+            // (numerator and denominator of (lam p + 1) / ((1 + p) c) times
+            // T^n / c, c = lam activating, 1 inhibiting), and a row's products
+            // are divided once per eight factors (x^n, T^n stay below ~1e24, so
+            // eight factors stay finite).  With `jac` the FP32 Jacobian is
+            // filled in as well.
+            float b[RPL];
+            auto residual = [&](bool jac) -> float {
+                for (int i = lane; i < N; i += kWarp) {
+                    const double v = fmax(x[i], 0.0);
+                    const double v2 = v * v, v4 = v2 * v2;
+                    xp[0][i] = v; xp[1][i] = v2; xp[2][i] = v2 * v;
+                    xp[3][i] = v4; xp[4][i] = v4 * v; xp[5][i] = v2 * v4;
                 }
                 __syncwarp();
                 for (int c = lane; c < E; c += kWarp) {
-                    const int code = code_e[c], s = code >> 9, n = code & 255, i = row_e[c];
-                    const float2 tl = tl_e[c];
-                    const float xf = (float)fmax(x[s], 0.0);
-                    float dl;
-                    if (xf > 0.0f) {
-                        const float pf = fminf(ipow(xf * div_approx(1.0f, tl.x), n), 1e30f);
-                        dl = (float)n * (tl.y - 1.0f) * pf * div_approx(1.0f, xf * (1.0f + pf)) *
-                             div_approx(1.0f, fmaf(tl.y, pf, 1.0f));
-                    } else {
-                        dl = n == 1 ? (tl.y - 1.0f) * div_approx(1.0f, tl.x) : 0.0f;
-                    }
-                    J[i][s] = gp[i] * dl;
+                    const int code = code_e[c], s = code >> 9, n = code & 255;
+                    const double xn = (n >= 1 && n <= kPow) ? xp[n - 1][s] : ipow(fmax(x[s], 0.0), n);
+                    num_e[c] = fma(a_e[c], xn, b_e[c]);
+                    den_e[c] = xn + tn_e[c];
                 }
                 __syncwarp();
+                float rloc = 0.0f;
 #pragma unroll
                 for (int k = 0; k < RPL; ++k) {
                     const int i = lane + kWarp * k;
-                    if (i < N) J[i][i] -= (float)Kr[k];
-                }
-            }
-            return warp_maxf(rloc);
-        };
-
-        bool ok = false, singular = false;
-        float last_move = 0.0f;
-        float rho = residual(true);
-        __syncwarp();
-        if ((double)rho < a.tol) ok = true;
-
-        // LU of the FP32 Jacobian with partial pivoting; multipliers kept
-        // below the diagonal, reciprocals of the pivots on it, and the row
-        // swaps composed into perm ((P b)_r = b_perm[r])
-        if (!ok) {
-            for (int c = 0; c < N; ++c) {
-                float best = -1.0f;
-                int pr = c;
-                for (int r = c + lane; r < N; r += kWarp) {
-                    const float v = fabsf(J[r][c]);
-                    if (v > best) { best = v; pr = r; }
-                }
-                // largest magnitude over the warp, lowest row among equals
-                const unsigned key = best >= 0.0f ? __float_as_uint(best) + 1u : 0u;
-                const unsigned mx = __reduce_max_sync(FULL, key);
-                pr = __reduce_min_sync(FULL, key == mx ? pr : INT_MAX);
-                if (mx <= 1u) { singular = true; break; }     // no candidate, or only zeros
-                if (lane == 0) piv[c] = pr;
-                if (pr != c) {
-                    for (int j = lane; j < N; j += kWarp) {
-                        const float t = J[c][j]; J[c][j] = J[pr][j]; J[pr][j] = t;
+                    b[k] = 0.0f;
+                    if (i < N) {
+                        double P = 1.0, nu = 1.0, de = 1.0;
+                        int cnt = 0;
+                        for (int c = a.topo.off[i]; c < a.topo.off[i + 1]; ++c) {
+                            nu *= num_e[c];
+                            de *= den_e[c];
+                            if (++cnt == 8) { P *= nu / de; nu = de = 1.0; cnt = 0; }
+                        }
+                        P *= nu / de;
+                        const double gpi = Gr[k] * P;
+                        const double f = gpi - Kr[k] * x[i];
+                        b[k] = (float)(-f);
+                        if (jac) gp[i] = (float)gpi;
+                        rloc = fmaxf(rloc, nan_to_inf(fabsf(b[k]) * kg[k]));
                     }
                 }
-                __syncwarp();
-                const float inv = 1.0f / J[c][c];
-                for (int r = c + 1 + lane; r < N; r += kWarp) {
-                    const float m = J[r][c] * inv;
-                    J[r][c] = m;
-                    for (int j = c + 1; j < N; ++j) J[r][j] = fmaf(-m, J[c][j], J[r][j]);
-                }
-                __syncwarp();
-            }
-            if (!singular) {
-                for (int c = lane; c < N; c += kWarp) J[c][c] = 1.0f / J[c][c];
-                if (lane == 0) {
-                    // the swaps in order applied to the identity
-                    for (int c = 0; c < N; ++c) perm[c] = c;
-                    for (int c = 0; c < N; ++c) {
-                        const int p = piv[c];
-                        const int t = perm[c]; perm[c] = perm[p]; perm[p] = t;
+                if (jac) {
+                    // J_is = G_i P_i dlog F_e / dx_s for the edge e = (s -> i)
+                    // (one edge per pair), then J_ii -= k_i.  dlog F / dx =
+                    // n p (lam - 1) / (x (lam p + 1)(1 + p)), p = (x/T)^n, in
+                    // FP32 (the Jacobian only steers the iteration); at x = 0
+                    // only n = 1 leaves a slope.
+#pragma unroll
+                    for (int k = 0; k < RPL; ++k) {
+                        const int i = lane + kWarp * k;
+                        if (i < N)
+                            for (int j = 0; j < N; ++j) J[i][j] = 0.0f;
+                    }
+                    __syncwarp();
+                    for (int c = lane; c < E; c += kWarp) {
+                        const int code = code_e[c], s = code >> 9, n = code & 255, i = row_e[c];
+                        const float2 tl = tl_e[c];
+                        const float xf = (float)fmax(x[s], 0.0);
+                        float dl;
+                        if (xf > 0.0f) {
+                            const float pf = fminf(ipow(xf * div_approx(1.0f, tl.x), n), 1e30f);
+                            dl = (float)n * (tl.y - 1.0f) * pf * div_approx(1.0f, xf * (1.0f + pf)) *
+                                 div_approx(1.0f, fmaf(tl.y, pf, 1.0f));
+                        } else {
+                            dl = n == 1 ? (tl.y - 1.0f) * div_approx(1.0f, tl.x) : 0.0f;
+                        }
+                        J[i][s] = gp[i] * dl;
+                    }
+                    __syncwarp();
+#pragma unroll
+                    for (int k = 0; k < RPL; ++k) {
+                        const int i = lane + kWarp * k;
+                        if (i < N) J[i][i] -= (float)Kr[k];
                     }
                 }
-                __syncwarp();
-            }
-        }
+                return warp_maxf(rloc);
+            };
 
-        // b of row r (warp-uniform r) from the lane holding it
-        auto row_value = [&](int r) -> float {
-            float v = b[0];
-#pragma unroll
-            for (int k = 1; k < RPL; ++k)
-                if (r >= kWarp * k) v = b[k];
-            return __shfl_sync(FULL, v, r & (kWarp - 1));
-        };
-
-        // chord iterations: solve J0 d = -f(x) in FP32, x += d in FP64
-        for (int it = 0; !ok && !singular && it < a.iters; ++it) {
-            // b <- P b
-            float pb[RPL];
-#pragma unroll
-            for (int k = 0; k < RPL; ++k) {
-                const int i = lane + kWarp * k;
-                const int p = i < N ? perm[i] : 0;
-                float v = 0.0f;
-#pragma unroll
-                for (int q = 0; q < RPL; ++q) {
-                    const float t = __shfl_sync(FULL, b[q], p & (kWarp - 1));
-                    if (p >> 5 == q) v = t;
-                }
-                pb[k] = v;
-            }
-#pragma unroll
-            for (int k = 0; k < RPL; ++k) b[k] = pb[k];
-            for (int c = 0; c < N; ++c) {                 // forward (unit lower)
-                const float bc = row_value(c);
-#pragma unroll
-                for (int k = 0; k < RPL; ++k) {
-                    const int i = lane + kWarp * k;
-                    if (i > c && i < N) b[k] = fmaf(-J[i][c], bc, b[k]);
-                }
-            }
-            for (int c = N - 1; c >= 0; --c) {            // backward (upper, reciprocal diagonal)
-#pragma unroll
-                for (int k = 0; k < RPL; ++k)
-                    if (lane + kWarp * k == c) b[k] *= J[c][c];
-                const float bc = row_value(c);
-#pragma unroll
-                for (int k = 0; k < RPL; ++k) {
-                    const int i = lane + kWarp * k;
-                    if (i < c) b[k] = fmaf(-J[i][c], bc, b[k]);
-                }
-            }
-            float mv = 0.0f;
-#pragma unroll
-            for (int k = 0; k < RPL; ++k)
-                if (lane + kWarp * k < N) mv = fmaxf(mv, nan_to_inf(fabsf(b[k]) * kg[k]));
-            mv = warp_maxf(mv);
-            if (!(mv <= (float)a.max_move)) break;
-#pragma unroll
-            for (int k = 0; k < RPL; ++k) {
-                const int i = lane + kWarp * k;
-                if (i < N) x[i] += (double)b[k];
-            }
-            last_move = mv;
-            __syncwarp();
-            rho = residual(false);
+            bool ok = false, singular = false;
+            float last_move = 0.0f;
+            float rho = residual(true);
             __syncwarp();
             if ((double)rho < a.tol) ok = true;
-        }
-        if (ok) {
-            for (int i = lane; i < N; i += kWarp) state[i] = x[i];
-            if (lane == 0 && a.err_est) a.err_est[idx] = last_move > 0.0f ? last_move : rho;
-        } else {
-            if (lane == 0) {
-                a.status[idx] = GRINS_SS_POLISH_FAIL;
-                if (a.err_est) a.err_est[idx] = -1.0f;
+
+            // LU of the FP32 Jacobian with partial pivoting; multipliers kept
+            // below the diagonal, reciprocals of the pivots on it, and the row
+            // swaps composed into perm ((P b)_r = b_perm[r])
+            if (!ok) {
+                for (int c = 0; c < N; ++c) {
+                    float best = -1.0f;
+                    int pr = c;
+                    for (int r = c + lane; r < N; r += kWarp) {
+                        const float v = fabsf(J[r][c]);
+                        if (v > best) { best = v; pr = r; }
+                    }
+                    // largest magnitude over the warp, lowest row among equals
+                    const unsigned key = best >= 0.0f ? __float_as_uint(best) + 1u : 0u;
+                    const unsigned mx = __reduce_max_sync(FULL, key);
+                    pr = __reduce_min_sync(FULL, key == mx ? pr : INT_MAX);
+                    if (mx <= 1u) { singular = true; break; }     // no candidate, or only zeros
+                    if (lane == 0) piv[c] = pr;
+                    if (pr != c) {
+                        for (int j = lane; j < N; j += kWarp) {
+                            const float t = J[c][j]; J[c][j] = J[pr][j]; J[pr][j] = t;
+                        }
+                    }
+                    __syncwarp();
+                    const float inv = 1.0f / J[c][c];
+                    for (int r = c + 1 + lane; r < N; r += kWarp) {
+                        const float m = J[r][c] * inv;
+                        J[r][c] = m;
+                        for (int j = c + 1; j < N; ++j) J[r][j] = fmaf(-m, J[c][j], J[r][j]);
+                    }
+                    __syncwarp();
+                }
+                if (!singular) {
+                    for (int c = lane; c < N; c += kWarp) J[c][c] = 1.0f / J[c][c];
+                    if (lane == 0) {
+                        // the swaps in order applied to the identity
+                        for (int c = 0; c < N; ++c) perm[c] = c;
+                        for (int c = 0; c < N; ++c) {
+                            const int p = piv[c];
+                            const int t = perm[c]; perm[c] = perm[p]; perm[p] = t;
+                        }
+                    }
+                    __syncwarp();
+                }
             }
+
+            // b of row r (warp-uniform r) from the lane holding it
+            auto row_value = [&](int r) -> float {
+                float v = b[0];
+#pragma unroll
+                for (int k = 1; k < RPL; ++k)
+                    if (r >= kWarp * k) v = b[k];
+                return __shfl_sync(FULL, v, r & (kWarp - 1));
+            };
+
+            // chord iterations: solve J0 d = -f(x) in FP32, x += d in FP64
+            for (int it = 0; !ok && !singular && it < a.iters; ++it) {
+                // b <- P b
+                float pb[RPL];
+#pragma unroll
+                for (int k = 0; k < RPL; ++k) {
+                    const int i = lane + kWarp * k;
+                    const int p = i < N ? perm[i] : 0;
+                    float v = 0.0f;
+#pragma unroll
+                    for (int q = 0; q < RPL; ++q) {
+                        const float t = __shfl_sync(FULL, b[q], p & (kWarp - 1));
+                        if (p >> 5 == q) v = t;
+                    }
+                    pb[k] = v;
+                }
+#pragma unroll
+                for (int k = 0; k < RPL; ++k) b[k] = pb[k];
+                for (int c = 0; c < N; ++c) {                 // forward (unit lower)
+                    const float bc = row_value(c);
+#pragma unroll
+                    for (int k = 0; k < RPL; ++k) {
+                        const int i = lane + kWarp * k;
+                        if (i > c && i < N) b[k] = fmaf(-J[i][c], bc, b[k]);
+                    }
+                }
+                for (int c = N - 1; c >= 0; --c) {            // backward (upper, reciprocal diagonal)
+#pragma unroll
+                    for (int k = 0; k < RPL; ++k)
+                        if (lane + kWarp * k == c) b[k] *= J[c][c];
+                    const float bc = row_value(c);
+#pragma unroll
+                    for (int k = 0; k < RPL; ++k) {
+                        const int i = lane + kWarp * k;
+                        if (i < c) b[k] = fmaf(-J[i][c], bc, b[k]);
+                    }
+                }
+                float mv = 0.0f;
+#pragma unroll
+                for (int k = 0; k < RPL; ++k)
+                    if (lane + kWarp * k < N) mv = fmaxf(mv, nan_to_inf(fabsf(b[k]) * kg[k]));
+                mv = warp_maxf(mv);
+                if (!(mv <= (float)a.max_move)) break;
+#pragma unroll
+                for (int k = 0; k < RPL; ++k) {
+                    const int i = lane + kWarp * k;
+                    if (i < N) x[i] += (double)b[k];
+                }
+                last_move = mv;
+                __syncwarp();
+                rho = residual(false);
+                __syncwarp();
+                if ((double)rho < a.tol) ok = true;
+            }
+            if (ok) {
+                for (int i = lane; i < N; i += kWarp) state[i] = x[i];
+                if (lane == 0 && a.err_est) a.err_est[idx] = last_move > 0.0f ? last_move : rho;
+            } else {
+                if (lane == 0) {
+                    a.status[idx] = GRINS_SS_POLISH_FAIL;
+                    if (a.err_est) a.err_est[idx] = -1.0f;
+                }
+            }
+            __syncwarp();
         }
-        __syncwarp();
     }
 }
 
@@ -375,7 +399,8 @@ cudaError_t launch_bucket(const PolishArgs &a, cudaStream_t st, int num_sms)
     if (err != cudaSuccess) return err;
     if (per_sm < 1) per_sm = 1;
     long long blocks = (long long)num_sms * per_sm;
-    const long long need = (a.n_solves + WARPS - 1) / WARPS;
+    const long long units = a.n_ics > 0 ? a.n_solves / a.n_ics * ((a.n_ics + kUnitIcs - 1) / kUnitIcs) : 0;
+    const long long need = (units + WARPS - 1) / WARPS;
     if (blocks > need) blocks = need;
     if (blocks < 1) blocks = 1;
     kern<<<(unsigned)blocks, WARPS * kWarp, (size_t)dyn, st>>>(a);
