@@ -13,6 +13,10 @@ Functions mirror the paper (GRiNS, arXiv 2503.18356):
                                            and time series (Sec. 2.1.3)
   * ``polish``                          -- Newton on Eq. 1 = 0
   * ``dedupe``                          -- unique steady states (Sec. 3.1)
+  * ``gk_histogram`` / ``level_boundaries`` / ``level_states``
+                                        -- levels of G/k-normalised expression,
+                                           state labels and multistability
+                                           (Sec. 2.1.3 analysis, Sec. 3.1)
   * ``run_sets`` / ``run_sets_parallel``-- the whole path over sets
 """
 from __future__ import annotations
@@ -114,6 +118,16 @@ def lib():
             l.orc_dedupe.argtypes = [C.c_int32, C.c_int32, P(C.c_double), P(C.c_uint8),
                                      P(C.c_double), P(C.c_double), C.c_double, P(C.c_int32)]
             l.orc_dedupe.restype = C.c_int32
+            l.orc_gk_bin.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int32]
+            l.orc_gk_bin.restype = C.c_int32
+            l.orc_gk_histogram.argtypes = [C.c_int32, C.c_int32, C.c_int64, P(C.c_double), P(C.c_uint8),
+                                           P(C.c_double), P(C.c_double), C.c_int32, P(C.c_uint64)]
+            l.orc_level_boundaries.argtypes = [P(C.c_uint64), C.c_int32, C.c_int32, C.c_int32, P(C.c_int32)]
+            l.orc_level_boundaries.restype = C.c_int32
+            l.orc_level_states.argtypes = [C.c_int32, C.c_int32, C.c_int64, P(C.c_double), P(C.c_uint8),
+                                           P(C.c_double), P(C.c_double), C.c_int32, P(C.c_int32), C.c_int32,
+                                           P(C.c_uint64), P(C.c_int32), P(C.c_uint64)]
+            l.orc_level_states.restype = C.c_int32
             l.orc_run_sets.argtypes = [P(Net), P(C.c_double), P(C.c_double), P(C.c_double),
                                        P(C.c_double), P(C.c_int32), C.c_int64, P(C.c_double),
                                        C.c_int32, P(Opts), P(PathOpts), P(C.c_double),
@@ -281,6 +295,50 @@ def dedupe(states, status, G, k, tol=1e-2):
     nu = lib().orc_dedupe(N, I, _p(st, C.c_double), _p(stat, C.c_uint8), _p(G, C.c_double),
                           _p(k, C.c_double), tol, _p(sid, C.c_int32))
     return sid, nu
+
+
+def gk_bin(x, k, G, n_bins):
+    """Bin of one normalised value (x k) / G among n_bins equal bins on [0, 1]."""
+    return lib().orc_gk_bin(float(x), float(k), float(G), int(n_bins))
+
+
+def gk_histogram(states, status, G, k, n_bins=100, counts=None):
+    """states [S, I, N], status [S, I], per-set G, k [S, N] -> counts [n_bins]
+    (added to ``counts`` when given)."""
+    st = _f64(states)
+    S, I, N = st.shape
+    stat = np.ascontiguousarray(status, dtype=np.uint8)
+    G = _f64(G); k = _f64(k)
+    out = np.zeros(n_bins, dtype=np.uint64) if counts is None else counts
+    lib().orc_gk_histogram(N, I, S, _p(st, C.c_double), _p(stat, C.c_uint8), _p(G, C.c_double),
+                           _p(k, C.c_double), n_bins, _p(out, C.c_uint64))
+    return out
+
+
+def level_boundaries(counts, m=4, max_b=3):
+    """Boundary bins of a histogram of normalised values (binomial smoothing
+    of half-width m, at most max_b valleys)."""
+    c = np.ascontiguousarray(counts, dtype=np.uint64)
+    out = np.zeros(max(1, max_b), dtype=np.int32)
+    n = lib().orc_level_boundaries(_p(c, C.c_uint64), c.size, m, max_b, _p(out, C.c_int32))
+    return out[:n].copy()
+
+
+def level_states(states, status, G, k, bounds, n_bins=100):
+    """-> (labels [S, I] uint64, n_states [S], multi_hist [I + 1]); None when
+    the levels of N nodes do not fit in 64 bits."""
+    st = _f64(states)
+    S, I, N = st.shape
+    stat = np.ascontiguousarray(status, dtype=np.uint8)
+    G = _f64(G); k = _f64(k)
+    b = np.ascontiguousarray(bounds, dtype=np.int32)
+    labels = np.zeros((S, I), dtype=np.uint64)
+    ns = np.zeros(S, dtype=np.int32)
+    mh = np.zeros(I + 1, dtype=np.uint64)
+    rc = lib().orc_level_states(N, I, S, _p(st, C.c_double), _p(stat, C.c_uint8), _p(G, C.c_double),
+                                _p(k, C.c_double), n_bins, _p(b, C.c_int32) if b.size else None, b.size,
+                                _p(labels, C.c_uint64), _p(ns, C.c_int32), _p(mh, C.c_uint64))
+    return None if rc != 0 else (labels, ns, mh)
 
 
 def run_sets(net: Network, p: ParamSet, ic_unit, polish=True, polish_tol=1e-13,

@@ -657,3 +657,138 @@ void orc_run_sets(const orc_net *net, const double *G, const double *k, const do
                                      p.G, p.k, po->dedupe_tol, state_id + s * n_ics);
     }
 }
+
+/* ------------------------------------------------------------------ */
+/* Levels of G/k-normalised expression (Sec. 2.1.3 analysis: nodes are  */
+/* coarse-grained into levels "based on the global distribution" of the */
+/* normalised values, a state is the concatenation of its nodes' levels,*/
+/* and a set's multistability is its number of distinct states; Sec.    */
+/* 3.1).  The paper does not say how the level boundaries are chosen;   */
+/* the reading taken here:                                              */
+/*   * v = (x k) / G of every node of every converged solve is put in   */
+/*     one of n_bins equal bins on [0, 1] (v below 0 in the first, v at */
+/*     or above 1 in the last) -- one histogram over all nodes and sets;*/
+/*   * the counts are smoothed with the binomial weights C(2m, j),      */
+/*     j = 0..2m, centred (zero outside the bins), in integers;         */
+/*   * a valley is a maximal run of equal smoothed counts with higher   */
+/*     counts on both sides; it is a boundary when twice its count is   */
+/*     at most the lower of the highest counts to its left and to its   */
+/*     right; its bin is the run's middle (lower middle for even runs); */
+/*     at most max_b boundaries are kept, the lowest valleys first      */
+/*     (ties: the lower bin), reported in bin order;                    */
+/*   * a value's level is the number of boundaries whose bin is below   */
+/*     its own; a solve's label packs its nodes' levels, node i in bits */
+/*     [i*w, i*w + w), w = bits for (boundaries + 1) levels; a solve    */
+/*     that did not converge has the label 2^64 - 1.                    */
+/* ------------------------------------------------------------------ */
+int32_t orc_gk_bin(double x, double k, double G, int32_t n_bins)
+{
+    double f = ((x * k) / G) * (double)n_bins;
+    if (!(f >= 0.0)) return 0;
+    if (f >= (double)n_bins) return n_bins - 1;
+    return (int32_t)f;
+}
+
+/* Adds the bins of n_sets sets of n_ics solves (states [S][I][N],      */
+/* status [S][I], per-set G and k [S][N]) to counts[n_bins].            */
+void orc_gk_histogram(int32_t N, int32_t n_ics, int64_t n_sets, const double *states,
+                      const uint8_t *status, const double *G, const double *k, int32_t n_bins,
+                      uint64_t *counts)
+{
+    for (int64_t s = 0; s < n_sets; ++s)
+        for (int c = 0; c < n_ics; ++c) {
+            if (status[s * n_ics + c] != ORC_CONVERGED) continue;
+            const double *x = states + (s * n_ics + c) * (int64_t)N;
+            for (int i = 0; i < N; ++i)
+                counts[orc_gk_bin(x[i], k[s * N + i], G[s * N + i], n_bins)] += 1;
+        }
+}
+
+static uint64_t binom(int n, int j)
+{
+    uint64_t r = 1;
+    for (int t = 1; t <= j; ++t) r = r * (uint64_t)(n - j + t) / (uint64_t)t;
+    return r;
+}
+
+/* Boundary bins of the histogram counts[n_bins] (reading above) into   */
+/* bins_out[<= max_b]; returns their number.                            */
+int32_t orc_level_boundaries(const uint64_t *counts, int32_t n_bins, int32_t m, int32_t max_b,
+                             int32_t *bins_out)
+{
+    if (n_bins < 3 || max_b < 1) return 0;
+    uint64_t *sm = (uint64_t *)calloc((size_t)n_bins, sizeof(uint64_t));
+    int32_t *cand = (int32_t *)malloc(sizeof(int32_t) * (size_t)n_bins);
+    uint64_t *cval = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)n_bins);
+    for (int b = 0; b < n_bins; ++b)
+        for (int j = 0; j <= 2 * m; ++j) {
+            int src = b + j - m;
+            if (src >= 0 && src < n_bins) sm[b] += binom(2 * m, j) * counts[src];
+        }
+    int nc = 0;
+    int b0 = 0;
+    while (b0 < n_bins) {
+        int b1 = b0;
+        while (b1 + 1 < n_bins && sm[b1 + 1] == sm[b0]) ++b1;      /* run [b0, b1] */
+        if (b0 > 0 && b1 < n_bins - 1 && sm[b0 - 1] > sm[b0] && sm[b1 + 1] > sm[b0]) {
+            uint64_t L = 0, R = 0;
+            for (int t = 0; t < b0; ++t) if (sm[t] > L) L = sm[t];
+            for (int t = b1 + 1; t < n_bins; ++t) if (sm[t] > R) R = sm[t];
+            if (2 * sm[b0] <= (L < R ? L : R)) { cand[nc] = (b0 + b1) / 2; cval[nc] = sm[b0]; ++nc; }
+        }
+        b0 = b1 + 1;
+    }
+    /* keep the max_b lowest valleys (ties: lower bin), then bin order */
+    int keep = nc < max_b ? nc : max_b;
+    for (int a = 0; a < keep; ++a) {          /* selection by (value, bin) */
+        int best = a;
+        for (int t = a + 1; t < nc; ++t)
+            if (cval[t] < cval[best] || (cval[t] == cval[best] && cand[t] < cand[best])) best = t;
+        int tb = cand[a]; cand[a] = cand[best]; cand[best] = tb;
+        uint64_t tv = cval[a]; cval[a] = cval[best]; cval[best] = tv;
+    }
+    for (int a = 1; a < keep; ++a)            /* insertion sort by bin */
+        for (int t = a; t > 0 && cand[t - 1] > cand[t]; --t) {
+            int tb = cand[t]; cand[t] = cand[t - 1]; cand[t - 1] = tb;
+        }
+    for (int a = 0; a < keep; ++a) bins_out[a] = cand[a];
+    free(sm); free(cand); free(cval);
+    return keep;
+}
+
+/* Labels [S][I] (reading above), distinct labels among each set's      */
+/* converged solves n_states[S], and multi_hist[k] += number of sets    */
+/* with k distinct states (k = 0..n_ics).  Returns 0, or -1 when N      */
+/* levels do not fit in 64 bits.                                        */
+int32_t orc_level_states(int32_t N, int32_t n_ics, int64_t n_sets, const double *states,
+                         const uint8_t *status, const double *G, const double *k, int32_t n_bins,
+                         const int32_t *bounds, int32_t n_b, uint64_t *labels, int32_t *n_states,
+                         uint64_t *multi_hist)
+{
+    int w = 0;
+    while ((1 << w) < n_b + 1) ++w;
+    if ((int64_t)N * w > 64) return -1;
+    for (int64_t s = 0; s < n_sets; ++s) {
+        int32_t distinct = 0;
+        for (int c = 0; c < n_ics; ++c) {
+            int64_t idx = s * n_ics + c;
+            if (status[idx] != ORC_CONVERGED) { labels[idx] = UINT64_MAX; continue; }
+            const double *x = states + idx * N;
+            uint64_t lab = 0;
+            for (int i = 0; i < N; ++i) {
+                int bin = orc_gk_bin(x[i], k[s * N + i], G[s * N + i], n_bins);
+                uint64_t lev = 0;
+                for (int t = 0; t < n_b; ++t) lev += bounds[t] < bin;
+                lab |= lev << (i * w);
+            }
+            labels[idx] = lab;
+            int seen = 0;
+            for (int c2 = 0; c2 < c && !seen; ++c2)
+                seen = status[s * n_ics + c2] == ORC_CONVERGED && labels[s * n_ics + c2] == lab;
+            if (!seen) ++distinct;
+        }
+        n_states[s] = distinct;
+        multi_hist[distinct] += 1;
+    }
+    return 0;
+}
