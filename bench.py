@@ -180,6 +180,45 @@ def parity_figures(gpu, orc, G, k):
     return res
 
 
+def levels_measurement(h, params, out, stream, dev, S, I, n_bins=100, reps=3):
+    """The levels row on the step's polished states: G/k histogram (device),
+    level boundaries (host), labels, distinct states per set and the
+    multistability histogram (device); CUDA-event times of the two device
+    passes, the boundaries found and the share of sets by number of states."""
+    import numpy as np
+    import torch
+    from paper_2503_18356_gb300 import api
+    cnt = torch.zeros((n_bins,), dtype=torch.int64, device=dev)
+    lab = torch.empty((S, I), dtype=torch.int64, device=dev)
+    nst = torch.empty((S,), dtype=torch.int32, device=dev)
+    mh = torch.zeros((I + 1,), dtype=torch.int64, device=dev)
+    t_hist, t_states = [], []
+    for r in range(reps + 1):                 # the first pass is a warm-up
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        cnt.zero_(); mh.zero_()
+        ev[0].record(stream)
+        h.gk_histogram(params, out["states"], out["status"], n_bins=n_bins, counts=cnt, stream=stream)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        bounds = api.level_boundaries(cnt.cpu().numpy().view(np.uint64), half_width=4, max_boundaries=3)
+        ev[2].record(stream)
+        h.level_states(params, out["states"], out["status"], bounds, n_bins=n_bins, stream=stream,
+                       out=(lab, nst, mh))
+        ev[3].record(stream)
+        torch.cuda.synchronize()
+        if r:
+            t_hist.append(ev[0].elapsed_time(ev[1])); t_states.append(ev[2].elapsed_time(ev[3]))
+    hist = mh.cpu().numpy()
+    ms = float(np.mean(t_hist) + np.mean(t_states))
+    return dict(ms_histogram=float(np.mean(t_hist)), ms_states=float(np.mean(t_states)),
+                solves_per_s=S * I / (ms / 1e3), n_bins=n_bins,
+                boundaries=[(b + 0.5) / n_bins for b in bounds],
+                share_of_sets_by_states={str(k): float(v) / S for k, v in enumerate(hist) if v},
+                reading="one G/k histogram over all nodes of all converged solves, binomial smoothing of "
+                        "half-width 4, modes merged by persistence (a boundary where the absorbed peak is at "
+                        "least twice the valley and 1/64 of the highest count), at most 3 boundaries")
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -401,6 +440,7 @@ def run_native(args):
         snap.update(states=out["states"][:P].cpu().numpy(), status=out["status"][:P].cpu().numpy(),
                     n_unique=nu[:P].cpu().numpy(), G=G, k=k)
     kern_ms = per_kernel.mean(axis=0)
+    levels = levels_measurement(h, params, out, stream, dev, S, I) if rank == 0 else None
 
     # algorithmic work of the FP32 integrator (per step attempt of one solve)
     attempts = int(out["n_steps"].sum().item())
@@ -508,6 +548,8 @@ def run_native(args):
                                         "tolerances, no polish" % (f64_sets - 1, I),
                                  ratio=value / fp64_value),
             clocks=clocks)
+        if levels is not None:
+            line["levels"] = levels
         if args.batch_reps > 0 and ws == 1:
             line["batched"] = batched_measurement(dev, args.batch_reps)
         if args.serve_seconds > 0 and ws == 1:

@@ -398,6 +398,80 @@ grins_status grins_racipe_unique_states(grins_racipe_t h, const void *d_params,
                                         int32_t *d_state_id, int32_t *d_n_unique,
                                         void *stream);
 
+/* ---------------------------------------------------------------- levels
+ * Levels of G/k-normalised expression, state labels and multistability
+ * (Sec. 2.1.3: "nodes can be discretised into levels based on the global
+ * distribution of normalised G/k values"; a state is the concatenation of
+ * its nodes' levels and a set's multistability its number of distinct
+ * states, Sec. 3.1).  The paper does not say how the boundaries between
+ * levels are chosen; the reading implemented here:
+ *   1. grins_racipe_gk_histogram: one histogram of v = (x_i k_i) / G_i (FP64)
+ *      over every node of every converged solve, n_bins equal bins on
+ *      [0, 1] -- bin floor(v n_bins), v below 0 in bin 0, at or above 1 in
+ *      the last bin;
+ *   2. grins_level_boundaries (host): the counts smoothed with the
+ *      binomial weights C(2m, j), j = 0..2m, m = half_width (integers,
+ *      zero beyond the ends); modes merged by persistence: maximal runs of
+ *      equal smoothed counts are peaks (higher than their neighbours; an
+ *      end run needs only its one neighbour lower) and valleys (lower than
+ *      both neighbours); valleys from the highest down (ties: lower bin
+ *      first) join the groups of peaks on their two sides, the group with
+ *      the lower highest peak (ties: the one on the right) is absorbed,
+ *      and the valley is a boundary when twice its count is at most that
+ *      peak and the peak is at least 1/64 of the highest smoothed count;
+ *      its bin is the run's middle (lower middle); at most max_boundaries
+ *      are kept, lowest valleys first (ties: lower bin), reported in
+ *      increasing bin order;
+ *   3. grins_racipe_level_states: a value's level is the number of
+ *      boundary bins below its bin; a solve's label packs its nodes'
+ *      levels, node i in bits [i w, i w + w), w the bits of (boundaries +
+ *      1) levels; per set, the number of distinct labels among its
+ *      converged solves, and a histogram of those numbers over sets.
+ * All three are exact (integer results, the FP64 normalisation rounded as
+ * written), independent of launch shape and batch split. */
+
+/* Adds the bins of the converged solves of n_sets sets to d_counts.
+ *   d_params  the sets' parameter block (as for grins_racipe_integrate)
+ *   d_states  double [n_sets][n_ics][N], d_status uint8 [n_sets][n_ics]
+ *   d_counts  uint64 [n_bins], device, caller-zeroed; accumulates, so
+ *             batches of sets add up to one histogram
+ * Asynchronous on stream.  Errors: GRINS_E_INVALID_ARG for a NULL handle or
+ * buffer, n_ics outside [1, 4096], n_bins outside [2, 4096]. */
+grins_status grins_racipe_gk_histogram(grins_racipe_t h, const void *d_params,
+                                       const double *d_states, const uint8_t *d_status,
+                                       int64_t n_sets, int32_t n_ics, int32_t n_bins,
+                                       unsigned long long *d_counts, void *stream);
+
+/* Level boundaries of a histogram (host memory in and out, no GPU).
+ *   h_counts  uint64 [n_bins]; half_width m >= 0 (0: no smoothing)
+ *   h_bins    int32 [max_boundaries], filled with *n_out boundary bins in
+ *             increasing order
+ * Errors: GRINS_E_INVALID_ARG for NULL pointers, n_bins outside [2, 4096],
+ * half_width outside [0, 8] (the smoothed counts stay exact in 64 bits up
+ * to 2^48 values), max_boundaries outside [1, 16]. */
+grins_status grins_level_boundaries(const unsigned long long *h_counts, int32_t n_bins,
+                                    int32_t half_width, int32_t max_boundaries, int32_t *h_bins,
+                                    int32_t *n_out);
+
+/* Level labels, distinct states per set and the multistability histogram.
+ *   h_bounds      int32 [n_bounds] boundary bins (host), increasing, in
+ *                 [0, n_bins); n_bounds in [0, 16]
+ *   d_labels      uint64 [n_sets][n_ics]: packed levels; 2^64 - 1 for a solve
+ *                 that did not converge
+ *   d_n_states    int32 [n_sets]: distinct labels among the set's converged
+ *                 solves
+ *   d_multi_hist  uint64 [n_ics + 1], caller-zeroed, accumulates: entry k
+ *                 counts the sets with k distinct states
+ * Asynchronous on stream.  Errors: GRINS_E_INVALID_ARG for a NULL handle or
+ * buffer, bad sizes or unordered boundaries; GRINS_E_BUDGET when N nodes'
+ * levels do not fit in 64 bits. */
+grins_status grins_racipe_level_states(grins_racipe_t h, const void *d_params,
+                                       const double *d_states, const uint8_t *d_status,
+                                       int64_t n_sets, int32_t n_ics, int32_t n_bins,
+                                       const int32_t *h_bounds, int32_t n_bounds,
+                                       unsigned long long *d_labels, int32_t *d_n_states,
+                                       unsigned long long *d_multi_hist, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -670,12 +670,17 @@ void orc_run_sets(const orc_net *net, const double *G, const double *k, const do
 /*     or above 1 in the last) -- one histogram over all nodes and sets;*/
 /*   * the counts are smoothed with the binomial weights C(2m, j),      */
 /*     j = 0..2m, centred (zero outside the bins), in integers;         */
-/*   * a valley is a maximal run of equal smoothed counts with higher   */
-/*     counts on both sides; it is a boundary when twice its count is   */
-/*     at most the lower of the highest counts to its left and to its   */
-/*     right; its bin is the run's middle (lower middle for even runs); */
-/*     at most max_b boundaries are kept, the lowest valleys first      */
-/*     (ties: the lower bin), reported in bin order;                    */
+/*   * modes are merged by persistence: runs of equal smoothed counts   */
+/*     are peaks (higher than their neighbours; an end run needs only   */
+/*     its one neighbour lower) and valleys (lower than both            */
+/*     neighbours); valleys are taken from the highest down (ties: the  */
+/*     lower bin first), each joining the two groups of modes beside    */
+/*     it; the group with the lower highest peak (ties: the one on the  */
+/*     right) is absorbed, and the valley is a boundary when twice its  */
+/*     count is at most that peak and the peak is at least 1/64 of the  */
+/*     histogram's highest count; its bin is the valley run's middle    */
+/*     (lower middle); at most max_b boundaries are kept, the lowest    */
+/*     valleys first (ties: the lower bin), reported in bin order;      */
 /*   * a value's level is the number of boundaries whose bin is below   */
 /*     its own; a solve's label packs its nodes' levels, node i in bits */
 /*     [i*w, i*w + w), w = bits for (boundaries + 1) levels; a solve    */
@@ -718,41 +723,79 @@ int32_t orc_level_boundaries(const uint64_t *counts, int32_t n_bins, int32_t m, 
 {
     if (n_bins < 3 || max_b < 1) return 0;
     uint64_t *sm = (uint64_t *)calloc((size_t)n_bins, sizeof(uint64_t));
-    int32_t *cand = (int32_t *)malloc(sizeof(int32_t) * (size_t)n_bins);
-    uint64_t *cval = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)n_bins);
     for (int b = 0; b < n_bins; ++b)
         for (int j = 0; j <= 2 * m; ++j) {
             int src = b + j - m;
             if (src >= 0 && src < n_bins) sm[b] += binom(2 * m, j) * counts[src];
         }
-    int nc = 0;
-    int b0 = 0;
-    while (b0 < n_bins) {
-        int b1 = b0;
-        while (b1 + 1 < n_bins && sm[b1 + 1] == sm[b0]) ++b1;      /* run [b0, b1] */
-        if (b0 > 0 && b1 < n_bins - 1 && sm[b0 - 1] > sm[b0] && sm[b1 + 1] > sm[b0]) {
-            uint64_t L = 0, R = 0;
-            for (int t = 0; t < b0; ++t) if (sm[t] > L) L = sm[t];
-            for (int t = b1 + 1; t < n_bins; ++t) if (sm[t] > R) R = sm[t];
-            if (2 * sm[b0] <= (L < R ? L : R)) { cand[nc] = (b0 + b1) / 2; cval[nc] = sm[b0]; ++nc; }
-        }
-        b0 = b1 + 1;
+    uint64_t top = 0;
+    for (int b = 0; b < n_bins; ++b) if (sm[b] > top) top = sm[b];
+    /* runs of equal counts: start, end, value, kind (1 peak, -1 valley) */
+    int nr = 0;
+    int *r0 = (int *)malloc(sizeof(int) * (size_t)n_bins), *r1 = (int *)malloc(sizeof(int) * (size_t)n_bins);
+    int *kind = (int *)malloc(sizeof(int) * (size_t)n_bins);
+    for (int b = 0; b < n_bins;) {
+        int e = b;
+        while (e + 1 < n_bins && sm[e + 1] == sm[b]) ++e;
+        r0[nr] = b; r1[nr] = e; ++nr;
+        b = e + 1;
     }
-    /* keep the max_b lowest valleys (ties: lower bin), then bin order */
+    for (int r = 0; r < nr; ++r) {
+        int lo_l = r > 0 && sm[r0[r - 1]] < sm[r0[r]], lo_r = r + 1 < nr && sm[r0[r + 1]] < sm[r0[r]];
+        int hi_l = r > 0 && sm[r0[r - 1]] > sm[r0[r]], hi_r = r + 1 < nr && sm[r0[r + 1]] > sm[r0[r]];
+        kind[r] = 0;
+        if ((lo_l || r == 0) && (lo_r || r == nr - 1) && nr > 1) kind[r] = 1;
+        if (hi_l && hi_r) kind[r] = -1;
+    }
+    /* groups of peaks: each peak run is a group (highest peak value and
+       its run index for ties); a valley joins the groups of the nearest
+       peaks on its two sides */
+    int *grp = (int *)malloc(sizeof(int) * (size_t)nr);      /* run -> group root (peaks only) */
+    uint64_t *gmax = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)nr);
+    int *gpos = (int *)malloc(sizeof(int) * (size_t)nr);
+    for (int r = 0; r < nr; ++r) { grp[r] = r; gmax[r] = sm[r0[r]]; gpos[r] = r; }
+    int nv = 0;
+    int *vr = (int *)malloc(sizeof(int) * (size_t)nr);
+    for (int r = 0; r < nr; ++r) if (kind[r] == -1) vr[nv++] = r;
+    /* valleys from the highest down, ties: lower bin first */
+    for (int a = 1; a < nv; ++a)
+        for (int t = a; t > 0; --t) {
+            uint64_t va = sm[r0[vr[t]]], vb = sm[r0[vr[t - 1]]];
+            if (va > vb || (va == vb && r0[vr[t]] < r0[vr[t - 1]])) { int x = vr[t]; vr[t] = vr[t - 1]; vr[t - 1] = x; }
+            else break;
+        }
+    int *cb = (int *)malloc(sizeof(int) * (size_t)(nv > 0 ? nv : 1));
+    uint64_t *cv = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(nv > 0 ? nv : 1));
+    int nc = 0;
+    for (int a = 0; a < nv; ++a) {
+        int v = vr[a];
+        int pl = v - 1, pr = v + 1;                 /* nearest peaks beside the valley */
+        while (kind[pl] != 1) --pl;
+        while (kind[pr] != 1) ++pr;
+        int gl = pl, gr = pr;
+        while (grp[gl] != gl) gl = grp[gl];
+        while (grp[gr] != gr) gr = grp[gr];
+        /* the absorbed group: the lower highest peak, ties the right one */
+        int young = gmax[gl] < gmax[gr] ? gl : (gmax[gr] < gmax[gl] ? gr : (gpos[gl] > gpos[gr] ? gl : gr));
+        int old = young == gl ? gr : gl;
+        uint64_t d = sm[r0[v]];
+        if (2 * d <= gmax[young] && 64 * gmax[young] >= top) { cb[nc] = (r0[v] + r1[v]) / 2; cv[nc] = d; ++nc; }
+        grp[young] = old;
+    }
     int keep = nc < max_b ? nc : max_b;
     for (int a = 0; a < keep; ++a) {          /* selection by (value, bin) */
         int best = a;
         for (int t = a + 1; t < nc; ++t)
-            if (cval[t] < cval[best] || (cval[t] == cval[best] && cand[t] < cand[best])) best = t;
-        int tb = cand[a]; cand[a] = cand[best]; cand[best] = tb;
-        uint64_t tv = cval[a]; cval[a] = cval[best]; cval[best] = tv;
+            if (cv[t] < cv[best] || (cv[t] == cv[best] && cb[t] < cb[best])) best = t;
+        int tb = cb[a]; cb[a] = cb[best]; cb[best] = tb;
+        uint64_t tv = cv[a]; cv[a] = cv[best]; cv[best] = tv;
     }
     for (int a = 1; a < keep; ++a)            /* insertion sort by bin */
-        for (int t = a; t > 0 && cand[t - 1] > cand[t]; --t) {
-            int tb = cand[t]; cand[t] = cand[t - 1]; cand[t - 1] = tb;
+        for (int t = a; t > 0 && cb[t - 1] > cb[t]; --t) {
+            int tb = cb[t]; cb[t] = cb[t - 1]; cb[t - 1] = tb;
         }
-    for (int a = 0; a < keep; ++a) bins_out[a] = cand[a];
-    free(sm); free(cand); free(cval);
+    for (int a = 0; a < keep; ++a) bins_out[a] = cb[a];
+    free(sm); free(r0); free(r1); free(kind); free(grp); free(gmax); free(gpos); free(vr); free(cb); free(cv);
     return keep;
 }
 

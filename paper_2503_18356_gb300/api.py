@@ -110,6 +110,11 @@ _sig = {
     "grins_racipe_server_destroy": (_S, [_H]),
     "grins_racipe_polish": (_S, [_H, C.POINTER(grins_solver_opts), _P, C.c_int64, C.c_int32, _P, _P, _P, _P]),
     "grins_racipe_unique_states": (_S, [_H, _P, _P, _P, C.c_int64, C.c_int32, C.c_double, _P, _P, _P]),
+    "grins_racipe_gk_histogram": (_S, [_H, _P, _P, _P, C.c_int64, C.c_int32, C.c_int32, _P, _P]),
+    "grins_level_boundaries": (_S, [C.POINTER(C.c_ulonglong), C.c_int32, C.c_int32, C.c_int32,
+                                    C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "grins_racipe_level_states": (_S, [_H, _P, _P, _P, C.c_int64, C.c_int32, C.c_int32, C.POINTER(C.c_int32),
+                                       C.c_int32, _P, _P, _P, _P]),
 }
 EXPORTED = tuple(_sig)
 for _name, (_res, _args) in _sig.items():
@@ -300,6 +305,45 @@ class Racipe:
                                                    S, I, tol, _ptr(out[0]), _ptr(out[1]),
                                                    _stream(stream)))
         return out
+
+
+    def gk_histogram(self, params, states, status, n_bins=100, counts=None, stream=None):
+        """Adds the bins of the converged solves' G/k-normalised values to
+        ``counts`` (uint64 [n_bins] on the device; zeros when None)."""
+        S, I = status.shape
+        if counts is None:
+            counts = torch.zeros((n_bins,), dtype=torch.int64, device=self.device)
+        with torch.cuda.device(self.device):
+            _check(_lib.grins_racipe_gk_histogram(self._h, _ptr(params), _ptr(states), _ptr(status), S, I,
+                                                  n_bins, _ptr(counts), _stream(stream)))
+        return counts
+
+    def level_states(self, params, states, status, bounds, n_bins=100, stream=None, out=None):
+        """-> (labels uint64 [S, I] as int64, n_states int32 [S], multi_hist
+        uint64 [I + 1] as int64, accumulated into ``out[2]`` when given)."""
+        S, I = status.shape
+        if out is None:
+            out = (torch.empty((S, I), dtype=torch.int64, device=self.device),
+                   torch.empty((S,), dtype=torch.int32, device=self.device),
+                   torch.zeros((I + 1,), dtype=torch.int64, device=self.device))
+        b = (C.c_int32 * max(1, len(bounds)))(*[int(x) for x in bounds])
+        with torch.cuda.device(self.device):
+            _check(_lib.grins_racipe_level_states(self._h, _ptr(params), _ptr(states), _ptr(status), S, I, n_bins,
+                                                  b, len(bounds), _ptr(out[0]), _ptr(out[1]), _ptr(out[2]),
+                                                  _stream(stream)))
+        return out
+
+
+def level_boundaries(counts, half_width=4, max_boundaries=3):
+    """Boundary bins of a histogram of normalised values (host; see
+    grins_level_boundaries)."""
+    import numpy as np
+    c = np.ascontiguousarray(np.asarray(counts).astype(np.uint64))
+    bins = (C.c_int32 * max_boundaries)()
+    n = C.c_int32(0)
+    _check(_lib.grins_level_boundaries(c.ctypes.data_as(C.POINTER(C.c_ulonglong)), c.size, half_width,
+                                       max_boundaries, bins, C.byref(n)))
+    return [bins[t] for t in range(n.value)]
 
 
 class Plan:

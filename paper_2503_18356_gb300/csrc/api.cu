@@ -964,6 +964,144 @@ extern "C" grins_status grins_racipe_unique_states(grins_racipe_t h, const void 
     return GRINS_OK;
 }
 
+// ------------------------------------------------------------------ levels
+static grins_status level_args(grins_racipe_t h, const char *who, const void *d_params, const double *d_states,
+                               const uint8_t *d_status, int64_t n_sets, int32_t n_ics, int32_t n_bins,
+                               LevelArgs *a)
+{
+    if (!h) return fail(GRINS_E_INVALID_ARG, "%s: NULL handle", who);
+    if (n_sets < 0 || n_ics < 1 || n_ics > 4096) return fail(GRINS_E_INVALID_ARG, "%s: bad sizes", who);
+    if (n_bins < 2 || n_bins > 4096) return fail(GRINS_E_INVALID_ARG, "%s: n_bins outside [2, 4096]", who);
+    if (n_sets > 0 && (!d_params || !d_states || !d_status))
+        return fail(GRINS_E_INVALID_ARG, "%s: NULL device buffer", who);
+    if (!on_handle_device(h)) return fail(GRINS_E_INVALID_ARG, "%s: current device is not the handle's", who);
+    *a = LevelArgs{};
+    a->L = h->layout;
+    a->params = static_cast<const unsigned char *>(d_params);
+    a->states = d_states; a->status = d_status;
+    a->n_sets = n_sets; a->n_ics = n_ics; a->n_bins = n_bins;
+    return GRINS_OK;
+}
+
+extern "C" grins_status grins_racipe_gk_histogram(grins_racipe_t h, const void *d_params, const double *d_states,
+                                                  const uint8_t *d_status, int64_t n_sets, int32_t n_ics,
+                                                  int32_t n_bins, unsigned long long *d_counts, void *stream)
+{
+    g_last_error.clear();
+    LevelArgs a;
+    const grins_status rc = level_args(h, "gk_histogram", d_params, d_states, d_status, n_sets, n_ics, n_bins, &a);
+    if (rc != GRINS_OK) return rc;
+    if (!d_counts) return fail(GRINS_E_INVALID_ARG, "gk_histogram: NULL counts");
+    a.counts = d_counts;
+    CUDA_TRY(launch_gk_histogram(a, (cudaStream_t)stream, h->num_sms), "gk_histogram: launch");
+    return GRINS_OK;
+}
+
+// Boundary bins of a histogram of normalised values: binomially smoothed
+// counts (Pascal's row 2m, exact in 64 bits), compressed into runs of equal
+// counts; peaks and valleys among the runs; valleys taken from the highest
+// down merge the groups of peaks on their two sides (union-find, each group
+// keeping its highest peak); a merge whose absorbed group's peak is at
+// least twice the valley and at least 1/64 of the highest count makes the
+// valley's middle bin a boundary; the lowest valleys are kept first.
+extern "C" grins_status grins_level_boundaries(const unsigned long long *h_counts, int32_t n_bins,
+                                               int32_t half_width, int32_t max_boundaries, int32_t *h_bins,
+                                               int32_t *n_out)
+{
+    g_last_error.clear();
+    if (!h_counts || !h_bins || !n_out) return fail(GRINS_E_INVALID_ARG, "level_boundaries: NULL pointer");
+    if (n_bins < 2 || n_bins > 4096) return fail(GRINS_E_INVALID_ARG, "level_boundaries: n_bins outside [2, 4096]");
+    if (half_width < 0 || half_width > 8)
+        return fail(GRINS_E_INVALID_ARG, "level_boundaries: half_width outside [0, 8]");
+    if (max_boundaries < 1 || max_boundaries > kMaxLevelBounds)
+        return fail(GRINS_E_INVALID_ARG, "level_boundaries: max_boundaries outside [1, %d]", kMaxLevelBounds);
+    const int B = n_bins, m = half_width;
+    std::vector<unsigned long long> wt(1, 1ull);                  // row 2m of Pascal's triangle
+    for (int r = 1; r <= 2 * m; ++r) {
+        std::vector<unsigned long long> nx(r + 1, 1ull);
+        for (int j = 1; j < r; ++j) nx[j] = wt[j - 1] + wt[j];
+        wt.swap(nx);
+    }
+    std::vector<unsigned long long> sm(B, 0ull);
+    for (int b = 0; b < B; ++b)
+        for (int j = -m; j <= m; ++j)
+            if (b + j >= 0 && b + j < B) sm[b] += wt[j + m] * h_counts[b + j];
+    const unsigned long long top = *std::max_element(sm.begin(), sm.end());
+    struct Run { int b0, b1; unsigned long long v; };
+    std::vector<Run> run;
+    for (int b = 0; b < B; ++b) {
+        if (!run.empty() && run.back().v == sm[b]) run.back().b1 = b;
+        else run.push_back({b, b, sm[b]});
+    }
+    const int R = (int)run.size();
+    std::vector<char> peak(R, 0);
+    std::vector<int> valleys;
+    for (int r = 0; r < R && R > 1; ++r) {
+        const bool below_l = r == 0 || run[r - 1].v < run[r].v, below_r = r == R - 1 || run[r + 1].v < run[r].v;
+        if (below_l && below_r) peak[r] = 1;
+        if (r > 0 && r < R - 1 && run[r - 1].v > run[r].v && run[r + 1].v > run[r].v) valleys.push_back(r);
+    }
+    std::vector<int> parent(R);
+    for (int r = 0; r < R; ++r) parent[r] = r;
+    auto root = [&](int r) { while (parent[r] != r) r = parent[r] = parent[parent[r]]; return r; };
+    std::vector<int> best(R);                                     // a group's highest peak run (first among equals)
+    for (int r = 0; r < R; ++r) best[r] = r;
+    std::sort(valleys.begin(), valleys.end(), [&](int a, int b) {
+        return run[a].v != run[b].v ? run[a].v > run[b].v : run[a].b0 < run[b].b0;
+    });
+    std::vector<std::pair<unsigned long long, int>> cut;          // (valley count, boundary bin)
+    for (int v : valleys) {
+        int pl = v - 1, pr = v + 1;
+        while (!peak[pl]) --pl;
+        while (!peak[pr]) ++pr;
+        const int gl = root(pl), gr = root(pr);
+        const unsigned long long hl = run[best[gl]].v, hr = run[best[gr]].v;
+        // absorbed: the lower highest peak; equal peaks: the one further right
+        const bool left_absorbed = hl < hr || (hl == hr && best[gl] > best[gr]);
+        const int young = left_absorbed ? gl : gr, old = left_absorbed ? gr : gl;
+        const unsigned long long h = run[best[young]].v, d = run[v].v;
+        if (2 * d <= h && 64 * h >= top) cut.push_back({d, (run[v].b0 + run[v].b1) / 2});
+        parent[young] = old;
+    }
+    std::sort(cut.begin(), cut.end());
+    if ((int)cut.size() > max_boundaries) cut.resize(max_boundaries);
+    std::vector<int> bins;
+    for (const auto &p : cut) bins.push_back(p.second);
+    std::sort(bins.begin(), bins.end());
+    for (size_t t = 0; t < bins.size(); ++t) h_bins[t] = bins[t];
+    *n_out = (int32_t)bins.size();
+    return GRINS_OK;
+}
+
+extern "C" grins_status grins_racipe_level_states(grins_racipe_t h, const void *d_params, const double *d_states,
+                                                  const uint8_t *d_status, int64_t n_sets, int32_t n_ics,
+                                                  int32_t n_bins, const int32_t *h_bounds, int32_t n_bounds,
+                                                  unsigned long long *d_labels, int32_t *d_n_states,
+                                                  unsigned long long *d_multi_hist, void *stream)
+{
+    g_last_error.clear();
+    LevelArgs a;
+    const grins_status rc = level_args(h, "level_states", d_params, d_states, d_status, n_sets, n_ics, n_bins, &a);
+    if (rc != GRINS_OK) return rc;
+    if (n_bounds < 0 || n_bounds > kMaxLevelBounds || (n_bounds > 0 && !h_bounds))
+        return fail(GRINS_E_INVALID_ARG, "level_states: n_bounds outside [0, %d] or NULL bounds", kMaxLevelBounds);
+    for (int t = 0; t < n_bounds; ++t)
+        if (h_bounds[t] < 0 || h_bounds[t] >= n_bins || (t > 0 && h_bounds[t] <= h_bounds[t - 1]))
+            return fail(GRINS_E_INVALID_ARG, "level_states: boundaries must increase within [0, n_bins)");
+    if (n_sets > 0 && (!d_labels || !d_n_states || !d_multi_hist))
+        return fail(GRINS_E_INVALID_ARG, "level_states: NULL output buffer");
+    int width = 0;
+    while ((1 << width) < n_bounds + 1) ++width;
+    if ((long long)h->N * width > 64)
+        return fail(GRINS_E_BUDGET, "level_states: %d nodes x %d bits exceed a 64-bit label", h->N, width);
+    a.n_bounds = n_bounds;
+    for (int t = 0; t < n_bounds; ++t) a.bounds[t] = h_bounds[t];
+    a.width = width;
+    a.labels = d_labels; a.n_states = d_n_states; a.multi_hist = d_multi_hist;
+    CUDA_TRY(launch_level_states(a, (cudaStream_t)stream, h->num_sms), "level_states: launch");
+    return GRINS_OK;
+}
+
 // ------------------------------------------------------------------- plans
 // A plan integrates many networks (jobs) in one batched launch of the
 // lane-group kernel, followed by each job's polish and dedupe, all captured

@@ -184,6 +184,30 @@ struct UniqueArgs {
 cudaError_t launch_unique(const UniqueArgs &a, cudaStream_t st, int num_sms);
 #endif
 
+// ----------------------------------------------------------------- levels
+constexpr int kMaxLevelBounds = 16;
+struct LevelArgs {
+    ParamLayout L;
+    const unsigned char *params;
+    const double *states;
+    const uint8_t *status;
+    int64_t n_sets;
+    int32_t n_ics;
+    int32_t n_bins;
+    unsigned long long *counts;          // gk histogram [n_bins], accumulated
+    int32_t n_bounds;                    // boundary bins, increasing
+    int32_t bounds[kMaxLevelBounds];
+    int32_t width;                       // label bits per node
+    unsigned long long *labels;          // [S][I]
+    int32_t *n_states;                   // [S]
+    unsigned long long *multi_hist;      // [I + 1], accumulated
+};
+
+#ifndef __CUDACC_RTC__
+cudaError_t launch_gk_histogram(const LevelArgs &a, cudaStream_t st, int num_sms);
+cudaError_t launch_level_states(const LevelArgs &a, cudaStream_t st, int num_sms);
+#endif
+
 // ------------------------------------------------------------- device RNG
 // Philox4x64-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds of the
 // four-word Philox bijection with the published multipliers and Weyl key

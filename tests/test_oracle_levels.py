@@ -4,10 +4,12 @@ inputs whose bins, valleys and labels are known by construction.
 
 The reading pinned here: one histogram of v = (x k) / G over all nodes of
 all converged solves, n_bins equal bins on [0, 1]; binomial smoothing of
-half-width m; a boundary at the middle of each valley (a run of equal
-smoothed counts with higher counts on both sides) whose count is at most
-half of the lower of the highest counts to its left and right; levels =
-boundaries below a value's bin; labels pack the levels node by node.
+half-width m; modes merged by persistence -- valleys (runs of equal
+smoothed counts lower than both neighbours) from the highest down, each
+absorbing the group of modes with the lower highest peak, a boundary (the
+run's middle) when twice the valley's count is at most that peak and the
+peak reaches 1/64 of the highest count; levels = boundaries below a
+value's bin; labels pack the levels node by node.
 """
 import numpy as np
 import pytest
@@ -168,3 +170,42 @@ def test_binomial_smoothing_weights():
     c[:] = 0
     c[40] = c[48] = 100
     assert list(O.level_boundaries(c, m=1)) == [44]
+
+
+def test_noisy_middle_gives_one_boundary_at_its_lowest_point():
+    # modes at bins 5-15 and 80-90; between them a sparse, wiggly region
+    # (peaks of 40-60, valleys of 25-35) whose lowest point is bin 51 (10):
+    # the wiggles are absorbed at valleys too high for them, the right mode
+    # at the lowest valley
+    c = np.zeros(100, dtype=np.uint64)
+    c[5:16] = 1000
+    c[80:91] = 500
+    mid = np.arange(20, 76)
+    c[20:76] = (45 + 12 * np.sin(mid * 1.3)).astype(np.uint64)
+    c[16:20] = [400, 200, 100, 60]                        # the modes' flanks
+    c[76:80] = [60, 100, 200, 400]
+    c[51] = 10
+    assert list(O.level_boundaries(c, m=0)) == [51]
+    # the rule with global side maxima alone would also cut at the wiggles
+    wiggle_valleys = [b for b in range(21, 75) if c[b] < c[b - 1] and c[b] < c[b + 1]]
+    assert len(wiggle_valleys) > 5
+
+
+def test_minimum_peak_height():
+    c = np.zeros(100, dtype=np.uint64)
+    c[8:13] = 10000
+    c[90] = 3                      # a stray count far in the tail: 3 < 10000 / 64
+    assert O.level_boundaries(c, m=0).size == 0
+    c[90] = 157                    # 64 * 157 >= 10000: a mode of its own
+    assert list(O.level_boundaries(c, m=0)) == [51]
+
+
+def test_equal_peaks_absorb_the_right_one():
+    # equal peaks at 10 and 40, a lower one at 70; valleys at 25 (count 1)
+    # and 55 (count 0): the valley at 25 joins the equal peaks (the right one
+    # is absorbed), the one at 55 the lower peak
+    c = np.zeros(80, dtype=np.uint64)
+    c[10] = c[40] = 100
+    c[70] = 60
+    c[11:40] = 1
+    assert list(O.level_boundaries(c, m=0)) == [25, 55]
