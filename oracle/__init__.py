@@ -76,7 +76,7 @@ class Opts(C.Structure):
     _fields_ = [("rtol", C.c_double), ("atol", C.c_double), ("t0", C.c_double),
                 ("t_end", C.c_double), ("ss_tol", C.c_double), ("max_steps", C.c_int64),
                 ("t_grid", C.POINTER(C.c_double)), ("n_t", C.c_int32),
-                ("h_fixed", C.c_double)]
+                ("h_fixed", C.c_double), ("method", C.c_int32)]
 
 
 class Result(C.Structure):
@@ -118,6 +118,7 @@ def lib():
             l.orc_dedupe.argtypes = [C.c_int32, C.c_int32, P(C.c_double), P(C.c_uint8),
                                      P(C.c_double), P(C.c_double), C.c_double, P(C.c_int32)]
             l.orc_dedupe.restype = C.c_int32
+            l.orc_tableau.argtypes = [C.c_int32, P(C.c_double), P(C.c_double), P(C.c_double), P(C.c_double)]
             l.orc_gk_bin.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int32]
             l.orc_gk_bin.restype = C.c_int32
             l.orc_gk_histogram.argtypes = [C.c_int32, C.c_int32, C.c_int64, P(C.c_double), P(C.c_uint8),
@@ -256,11 +257,21 @@ def sample_ics(n_nodes, seed, n_ics):
 
 
 def make_opts(rtol=1e-10, atol=1e-13, t0=0.0, t_end=200.0, ss_tol=1e-6, max_steps=10_000_000,
-              t_grid=None, h_fixed=0.0):
+              t_grid=None, h_fixed=0.0, method=0):
+    """method: 0 Dormand-Prince 5(4), 1 Tsitouras 5(4) (the paper's Tsit5)."""
     g = None if t_grid is None else _f64(t_grid)
     o = Opts(rtol, atol, t0, t_end, ss_tol, max_steps, _p(g, C.c_double),
-             0 if g is None else g.size, h_fixed)
+             0 if g is None else g.size, h_fixed, method)
     return o, g
+
+
+def tableau(method=0):
+    """(c [7], a [7, 7], b5 [7], b4 [7]) of a 5(4) pair (0 Dormand-Prince,
+    1 Tsitouras)."""
+    c, b5, b4 = np.zeros(7), np.zeros(7), np.zeros(7)
+    a = np.zeros((7, 7))
+    lib().orc_tableau(method, _p(c, C.c_double), _p(a, C.c_double), _p(b5, C.c_double), _p(b4, C.c_double))
+    return c, a, b5, b4
 
 
 def solve(net: Network, p: ParamSet, x0, s=0, **opt):

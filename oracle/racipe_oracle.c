@@ -349,12 +349,62 @@ static const double DP_B5[7] = { 35.0 / 384.0, 0.0, 500.0 / 1113.0, 125.0 / 192.
 static const double DP_B4[7] = { 5179.0 / 57600.0, 0.0, 7571.0 / 16695.0, 393.0 / 640.0,
                                  -92097.0 / 339200.0, 187.0 / 2100.0, 1.0 / 40.0 };
 
+/* ------------------------------------------------------------------ */
+/* Tsitouras 5(4) (Ch. Tsitouras 2011, "Runge-Kutta pairs of order 5(4) */
+/* satisfying only the first column simplifying assumption", Comput.    */
+/* Math. Appl. 62), seven stages, first-same-as-last: the paper's       */
+/* solver (diffrax Tsit5, Sec. 3.1).  The 5th-order weights are the last*/
+/* row of A; the embedded weights are written as b5 - (b5 - b4) with    */
+/* the published error coefficients b5 - b4.                            */
+/* ------------------------------------------------------------------ */
+static const double TS_C[7] = { 0.0, 0.161, 0.327, 0.9, 0.9800255409045097, 1.0, 1.0 };
+static const double TS_A[7][6] = {
+    { 0 },
+    { 0.161 },
+    { -0.008480655492356989, 0.335480655492357 },
+    { 2.897153057105493, -6.359448489975075, 4.3622954328695815 },
+    { 5.325864828439257, -11.748883564062828, 7.4955393428898365, -0.09249506636175525 },
+    { 5.86145544294642, -12.92096931784711, 8.159367898576159, -0.071584973281401, -0.028269050394068383 },
+    { 0.09646076681806523, 0.01, 0.4798896504144996, 1.379008574103742, -3.290069515436081,
+      2.324710524099774 },
+};
+static const double TS_B5[7] = { 0.09646076681806523, 0.01, 0.4798896504144996, 1.379008574103742,
+                                 -3.290069515436081, 2.324710524099774, 0.0 };
+static const double TS_B4[7] = {
+    0.09646076681806523 - -0.00178001105222577714, 0.01 - -0.0008164344596567469,
+    0.4798896504144996 - 0.007880878010261995, 1.379008574103742 - -0.1447110071732629,
+    -3.290069515436081 - 0.5823571654525552, 2.324710524099774 - -0.45808210592918697,
+    0.0 - 0.015151515151515152 };
+
+typedef struct {
+    const double *c, (*a)[6], *b5, *b4;
+} orc_tableau_t;
+
+static orc_tableau_t tableau_of(int32_t method)
+{
+    orc_tableau_t t = { DP_C, DP_A, DP_B5, DP_B4 };
+    if (method == 1) { t.c = TS_C; t.a = TS_A; t.b5 = TS_B5; t.b4 = TS_B4; }
+    return t;
+}
+
+/* The Butcher tableau of a method (0 Dormand-Prince, 1 Tsitouras) for   */
+/* tests: c[7], a[7][7] (row-major, zero above the diagonal), b5, b4.    */
+void orc_tableau(int32_t method, double *c, double *a, double *b5, double *b4)
+{
+    orc_tableau_t t = tableau_of(method);
+    for (int i = 0; i < 7; ++i) {
+        c[i] = t.c[i]; b5[i] = t.b5[i]; b4[i] = t.b4[i];
+        for (int j = 0; j < 7; ++j) a[i * 7 + j] = j < i && j < 6 ? t.a[i][j] : 0.0;
+    }
+}
+
 typedef struct {
     double rtol, atol, t0, t_end, ss_tol;
     int64_t max_steps;
     const double *t_grid;          /* NULL: no time series */
     int32_t n_t;
     double h_fixed;                /* > 0: fixed step, no control, no steady-state stop */
+    int32_t method;                /* 0 Dormand-Prince 5(4), 1 Tsitouras 5(4) */
 } orc_opts;
 
 typedef struct {
@@ -365,23 +415,24 @@ typedef struct {
 
 #define ORC_NMAX 256
 
-/* One DP5 step of size h from (y, k1 = f(y)); fills k[0..6], y5, y4. */
-static void dp5_step(const orc_net *net, const orc_params *p, const double *y, double h,
-                     double k[7][ORC_NMAX], double *y5, double *y4)
+/* One step of size h of the 5(4) pair t from (y, k1 = f(y)); fills      */
+/* k[0..6], y5, y4.                                                      */
+static void dp5_step(const orc_net *net, const orc_params *p, const orc_tableau_t *t, const double *y,
+                     double h, double k[7][ORC_NMAX], double *y5, double *y4)
 {
     int N = net->n_nodes;
     double z[ORC_NMAX];
     for (int s = 1; s < 7; ++s) {
         for (int i = 0; i < N; ++i) {
             double acc = 0.0;
-            for (int j = 0; j < s; ++j) acc = acc + DP_A[s][j] * k[j][i];
+            for (int j = 0; j < s; ++j) acc = acc + t->a[s][j] * k[j][i];
             z[i] = y[i] + h * acc;
         }
         orc_rhs(net, p, z, k[s]);
     }
     for (int i = 0; i < N; ++i) {
         double a5 = 0.0, a4 = 0.0;
-        for (int j = 0; j < 7; ++j) { a5 = a5 + DP_B5[j] * k[j][i]; a4 = a4 + DP_B4[j] * k[j][i]; }
+        for (int j = 0; j < 7; ++j) { a5 = a5 + t->b5[j] * k[j][i]; a4 = a4 + t->b4[j] * k[j][i]; }
         y5[i] = y[i] + h * a5;
         y4[i] = y[i] + h * a4;
     }
@@ -412,12 +463,14 @@ static int all_finite(int N, const double *v)
  * shortened to land on every grid time and the state there is written to
  * series[g * N + i]; grid times after termination get the final state.
  * With h_fixed > 0 the method runs with that fixed step to t_end (used to
- * measure its order). */
+ * measure its order).  o->method picks the 5(4) pair: 0 Dormand-Prince,
+ * 1 Tsitouras (the paper's solver); both take the step control above. */
 orc_result orc_solve(const orc_net *net, const orc_params *p, const double *x0,
                      const orc_opts *o, double *x_out, double *series)
 {
     int N = net->n_nodes;
     orc_result res = { ORC_TEND, o->t0, 0, 0 };
+    const orc_tableau_t tab = tableau_of(o->method);
     double y[ORC_NMAX], y5[ORC_NMAX], y4[ORC_NMAX], err[ORC_NMAX];
     double k[7][ORC_NMAX];
     memcpy(y, x0, sizeof(double) * N);
@@ -462,7 +515,7 @@ orc_result orc_solve(const orc_net *net, const orc_params *p, const double *x0,
         if (series && g < o->n_t && o->t_grid[g] < t_stop) { t_stop = o->t_grid[g]; to_grid = 1; }
         int clipped = 0;
         if (t + h_try >= t_stop) { h_try = t_stop - t; clipped = 1; }
-        dp5_step(net, p, y, h_try, k, y5, y4);
+        dp5_step(net, p, &tab, y, h_try, k, y5, y4);
         res.n_attempts++;
         for (int i = 0; i < N; ++i) err[i] = y5[i] - y4[i];
         if (!all_finite(N, y5) || !all_finite(N, k[6])) { res.status = ORC_NONFINITE; break; }

@@ -289,15 +289,64 @@ def test_adaptive_sequence_matches_scipy_rk45():
         assert np.allclose(r["x"], sol.y[:, -1], rtol=50 * rtol)
 
 
-def test_fixed_step_order_five():
+@pytest.mark.parametrize("method", [0, 1])
+def test_fixed_step_order_five(method):
     net = O.Network(*W.toggle_switch_self_activation().edges())
     p = rand_params(net, 3)
     f = model_rhs(net, p.G[0], p.k[0], p.T[0], p.lam[0], p.n[0])
     x0 = np.array([2.0, 15.0])
     ref = integrate.solve_ivp(f, (0, 1.0), x0, method="DOP853", rtol=1e-13, atol=1e-13).y[:, -1]
-    errs = [np.max(np.abs(O.solve(net, p, x0, t_end=1.0, h_fixed=h)["x"] - ref)) for h in (0.1, 0.05, 0.025)]
+    errs = [np.max(np.abs(O.solve(net, p, x0, t_end=1.0, h_fixed=h, method=method)["x"] - ref))
+            for h in (0.1, 0.05, 0.025)]
     orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
     assert all(4.5 < q < 5.6 for q in orders), orders
+
+
+def order_conditions(c, a, b):
+    """Residuals of the 17 order conditions up to order five (Butcher
+    trees) for weights b, plus the row-sum condition A 1 = c."""
+    e = np.ones(7)
+    Ac, Ac2, Ac3 = a @ c, a @ c ** 2, a @ c ** 3
+    AAc, AAc2 = a @ Ac, a @ Ac2
+    AAAc = a @ AAc
+    cond = [(b @ e, 1), (b @ c, 1 / 2), (b @ c ** 2, 1 / 3), (b @ Ac, 1 / 6),
+            (b @ c ** 3, 1 / 4), (b @ (c * Ac), 1 / 8), (b @ Ac2, 1 / 12), (b @ AAc, 1 / 24),
+            (b @ c ** 4, 1 / 5), (b @ (c ** 2 * Ac), 1 / 10), (b @ (c * Ac2), 1 / 15),
+            (b @ (c * AAc), 1 / 30), (b @ Ac ** 2, 1 / 20), (b @ Ac3, 1 / 20),
+            (b @ (a @ (c * Ac)), 1 / 40), (b @ AAc2, 1 / 60), (b @ AAAc, 1 / 120)]
+    return np.array([x - y for x, y in cond]), a @ e - c
+
+
+@pytest.mark.parametrize("method", [0, 1])
+def test_tableau_order_conditions(method):
+    """Both 5(4) pairs of the oracle (Dormand-Prince; Tsitouras, the paper's
+    Tsit5): the 5th-order weights meet all 17 conditions up to order five,
+    the embedded ones the 8 up to order four but not all of order five, the
+    rows of A sum to c, and the pair is first-same-as-last."""
+    c, a, b5, b4 = O.tableau(method)
+    r5, rows = order_conditions(c, a, b5)
+    r4, _ = order_conditions(c, a, b4)
+    assert np.max(np.abs(rows)) < 1e-14
+    assert np.max(np.abs(r5)) < 1e-14, r5
+    assert np.max(np.abs(r4[:8])) < 1e-14, r4
+    assert np.max(np.abs(r4[8:])) > 1e-4
+    assert np.array_equal(a[6, :6], b5[:6]) and b5[6] == 0.0
+
+
+def test_tsitouras_and_dormand_prince_agree():
+    """At tight tolerance both pairs reach the same trajectory, and at the
+    configured tolerance the same steady state."""
+    net = O.Network(*W.random_network(4, 5, 10, 4, 1).edges())
+    p = rand_params(net, 5)
+    x0 = np.linspace(2.0, 12.0, 5)
+    grid = np.linspace(0, 3.0, 7)
+    ra = O.solve(net, p, x0, t_end=3.0, ss_tol=0.0, t_grid=grid, rtol=1e-12, atol=1e-14)
+    rb = O.solve(net, p, x0, t_end=3.0, ss_tol=0.0, t_grid=grid, rtol=1e-12, atol=1e-14, method=1)
+    assert np.max(np.abs(ra["series"] - rb["series"]) / np.abs(ra["series"])) < 1e-9
+    sa = O.solve(net, p, x0, method=0)
+    sb = O.solve(net, p, x0, method=1)
+    assert sa["status"] == sb["status"] == O.CONVERGED
+    assert np.max(np.abs(sa["x"] - sb["x"]) * p.k[0] / p.G[0]) < 1e-5
 
 
 @pytest.mark.parametrize("seed", [1, 2, 3])
