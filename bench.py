@@ -219,6 +219,29 @@ def levels_measurement(h, params, out, stream, dev, S, I, n_bins=100, reps=3):
                         "least twice the valley and 1/64 of the highest count), at most 3 boundaries")
 
 
+def tsit5_measurement(h, params, ic, out, stream, S, I, reps=2):
+    """The paper's own 5(4) pair (Tsitouras, diffrax's Tsit5) on the same
+    workload and tolerances: FP32 integrate + FP64 polish, CUDA events."""
+    import numpy as np
+    import torch
+    from paper_2503_18356_gb300 import api
+    opts = api.default_opts(method=api.GRINS_METHOD_TSIT5, **TOL)
+    h.integrate(params, ic, opts=opts, stream=stream, out=out)       # compile and warm up
+    ts = []
+    for _ in range(reps):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record(stream)
+        h.integrate(params, ic, opts=opts, stream=stream, out=out)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        ts.append(ev[0].elapsed_time(ev[1]))
+    ms = float(np.mean(ts))
+    st = out["status"].cpu().numpy()
+    return dict(ms_integrate_polish=ms, solves_per_s=S * I / (ms / 1e3),
+                step_attempts_per_solve=float(out["n_steps"].float().mean().item()),
+                converged_share=float((st == 0).mean()), kernel=h.integrator())
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -440,11 +463,13 @@ def run_native(args):
         snap.update(states=out["states"][:P].cpu().numpy(), status=out["status"][:P].cpu().numpy(),
                     n_unique=nu[:P].cpu().numpy(), G=G, k=k)
     kern_ms = per_kernel.mean(axis=0)
-    levels = levels_measurement(h, params, out, stream, dev, S, I) if rank == 0 else None
-
-    # algorithmic work of the FP32 integrator (per step attempt of one solve)
+    # the timed step's step attempts and statuses, before later legs reuse the buffers
     attempts = int(out["n_steps"].sum().item())
     status = out["status"].cpu().numpy()
+    levels = levels_measurement(h, params, out, stream, dev, S, I) if rank == 0 else None
+    tsit5 = tsit5_measurement(h, params, ic, out, stream, S, I) if rank == 0 else None
+
+    # algorithmic work of the FP32 integrator (per step attempt of one solve)
     w32 = 35 * E + 45 * N
     wsfu = 6 * E + N
     sms = props.multi_processor_count
@@ -550,6 +575,8 @@ def run_native(args):
             clocks=clocks)
         if levels is not None:
             line["levels"] = levels
+        if tsit5 is not None:
+            line["tsit5"] = tsit5
         if args.batch_reps > 0 and ws == 1:
             line["batched"] = batched_measurement(dev, args.batch_reps)
         if args.serve_seconds > 0 and ws == 1:

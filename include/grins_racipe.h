@@ -70,6 +70,7 @@ typedef enum {
 } grins_solve_status;
 
 enum { GRINS_FP64 = 0, GRINS_FP32 = 1 };                       /* precision */
+enum { GRINS_METHOD_DOPRI5 = 0, GRINS_METHOD_TSIT5 = 1 };        /* 5(4) pair */
 enum { GRINS_MEDIAN_PER_INDEGREE = 0, GRINS_MEDIAN_UNREGULATED = 1 };
 
 /* Sampling ranges, Table 1 (Sec. 2.1.2).  grins_racipe_default_ranges fills
@@ -92,11 +93,11 @@ typedef struct {
  * steady state, optional time points).  grins_solver_default_opts fills:
  * FP32 + polish, rtol 1e-6, atol 1e-9, t0 0, t_end 200, ss_tol 1e-6,
  * max_steps 100000, no time grid, polish_tol 1e-13, polish_iters 16,
- * polish_max_move 1e-2, ss_tighten 0.3. */
+ * polish_max_move 1e-2, ss_tighten 0.3, method GRINS_METHOD_DOPRI5. */
 typedef struct {
     int32_t precision;         /* GRINS_FP32 or GRINS_FP64 integration */
     int32_t polish;            /* 1: FP64 Newton polish of each converged state */
-    double rtol, atol;         /* Dormand-Prince 5(4) local error tolerances */
+    double rtol, atol;         /* local error tolerances of the 5(4) pair */
     double t0, t_end;
     double ss_tol;             /* converged when max_i |dx_i/dt| / (G_i/k_i) < ss_tol */
     int64_t max_steps;         /* step attempts (accepted + rejected) per solve */
@@ -113,6 +114,15 @@ typedef struct {
                                   this factor (0 < ss_tighten <= 1; 1 = never): with
                                   ss_tol near rtol, the integrator's own error level
                                   would otherwise sit at the steady-state threshold */
+    int32_t method;            /* the embedded 5(4) pair: GRINS_METHOD_DOPRI5
+                                  (Dormand-Prince) or GRINS_METHOD_TSIT5 (Tsitouras
+                                  2011, the paper's Tsit5, Sec. 3.1); both take the
+                                  same step control and steady-state test.  Tsit5
+                                  runs on the kernels compiled for the network (FP32
+                                  and FP64 register records); calls without one --
+                                  no register layout, run-time compiles off -- and
+                                  plans and the server take Dormand-Prince only
+                                  (GRINS_E_INVALID_ARG otherwise) */
 } grins_solver_opts;
 
 void grins_racipe_default_ranges(grins_racipe_ranges *r);

@@ -31,6 +31,7 @@ GRINS_OK, GRINS_E_INVALID_ARG, GRINS_E_TOPOLOGY, GRINS_E_NOMEM, GRINS_E_CUDA, GR
     GRINS_E_CANCELLED = range(7)
 CONVERGED, TEND, MAXSTEPS, NONFINITE, POLISH_FAIL = range(5)
 GRINS_FP64, GRINS_FP32 = 0, 1
+GRINS_METHOD_DOPRI5, GRINS_METHOD_TSIT5 = 0, 1
 MEDIAN_PER_INDEGREE, MEDIAN_UNREGULATED = 0, 1
 GRINS_STATIC_MAX_GRID = 4096        # largest time grid of grins_racipe_integrate_static
 
@@ -52,7 +53,7 @@ class grins_solver_opts(C.Structure):
                 ("max_steps", C.c_int64),
                 ("t_grid", C.POINTER(C.c_double)), ("n_t", C.c_int32),
                 ("polish_tol", C.c_double), ("polish_iters", C.c_int32),
-                ("polish_max_move", C.c_double), ("ss_tighten", C.c_double)]
+                ("polish_max_move", C.c_double), ("ss_tighten", C.c_double), ("method", C.c_int32)]
 
 
 class grins_racipe_job(C.Structure):

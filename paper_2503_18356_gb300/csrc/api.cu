@@ -98,6 +98,7 @@ struct grins_racipe {
     std::string jit_why64;                             // the same for the last FP64 launch
     bool jit_used64 = false, ran64 = false;
     int used_L = 0, used_R = 0, used_P = 0;            // layout of the last FP32 launch
+    int used_method = 0;                               // and its 5(4) pair
     std::string info;                                  // grins_racipe_integrator text
     int grid_cap = 0;
     // cached median table
@@ -134,6 +135,7 @@ extern "C" void grins_solver_default_opts(grins_solver_opts *o)
     o->polish_iters = 16;
     o->polish_max_move = 1e-2;
     o->ss_tighten = 0.3;
+    o->method = GRINS_METHOD_DOPRI5;
 }
 
 extern "C" const char *grins_last_error(void) { return g_last_error.c_str(); }
@@ -510,8 +512,8 @@ extern "C" const char *grins_racipe_integrator(grins_racipe_t h)
     const bool ran = h->used_L > 0;
     const int L = ran ? h->used_L : h->grp.L, R = ran ? h->used_R : h->grp.R, P = ran ? h->used_P : h->grp.P;
     if (L > 0)
-        std::snprintf(buf, sizeof(buf), "lane-group DP5(4), L=%d lanes per solve, R=%d node rows, P=%d edge positions",
-                      L, R, P);
+        std::snprintf(buf, sizeof(buf), "lane-group %s, L=%d lanes per solve, R=%d node rows, P=%d edge positions",
+                      h->used_method == GRINS_METHOD_TSIT5 ? "Tsit5(4)" : "DP5(4)", L, R, P);
     else
         std::snprintf(buf, sizeof(buf), "generic shared-memory DP5(4) (no lane-group layout)");
     h->info = buf;
@@ -773,7 +775,8 @@ static void pick_fp64_kernel(const grins_racipe *h, IntegrateArgs *a, bool compi
     std::string w = h->rr.L > 0 ? "" : "no register layout";
     if (h->rr.L > 0) {
         const GrpTopo g = h->rr.topo();
-        const void *k = compile ? grp_jit_kernel(g, kJitRegisters64, &w) : grp_jit_lookup(g, kJitRegisters64);
+        const void *k = compile ? grp_jit_kernel(g, kJitRegisters64, &w, a->method)
+                                : grp_jit_lookup(g, kJitRegisters64, a->method);
         if (k) { a->grp = g; a->grp_jit = k; }
     }
     if (why) *why = w;
@@ -790,6 +793,7 @@ static void set_tighten(IntegrateArgs *a, const grins_solver_opts *o)
     a->f_rtol = (float)a->rtol; a->f_atol = (float)a->atol; a->f_t_end = (float)a->t_end;
     a->f_ss_tol = (float)a->ss_tol; a->f_ss_near = (float)a->ss_near; a->f_ss_gain = (float)a->ss_gain;
     a->max_steps32 = (int32_t)std::min<int64_t>(o->max_steps, INT32_MAX);
+    a->method = o->method;
 }
 
 // The FP32 lane-group kernel for h: sets a->grp and a->grp_jit to the
@@ -806,10 +810,11 @@ static void pick_fp32_kernel(const grins_racipe *h, IntegrateArgs *a, bool compi
     std::string w;
     if (!want_shared && h->rr.L > 0) {
         const GrpTopo g = h->rr.topo();
-        const void *k = compile ? grp_jit_kernel(g, kJitRegisters, &w) : grp_jit_lookup(g, kJitRegisters);
+        const void *k = compile ? grp_jit_kernel(g, kJitRegisters, &w, a->method)
+                                : grp_jit_lookup(g, kJitRegisters, a->method);
         if (k) { a->grp = g; a->grp_jit = k; if (why) *why = w; return; }
     }
-    if (h->grp.L > 0) {
+    if (h->grp.L > 0 && a->method == 0) {
         const void *k = compile ? grp_jit_kernel(a->grp, kJitShared, &w) : grp_jit_lookup(a->grp, kJitShared);
         if (k) a->grp_jit = k;
     }
@@ -866,6 +871,8 @@ extern "C" grins_status grins_racipe_integrate(grins_racipe_t h, const grins_sol
         return fail(GRINS_E_INVALID_ARG, "integrate: need finite t0 < t_end");
     if (!(o->ss_tol >= 0)) return fail(GRINS_E_INVALID_ARG, "integrate: ss_tol < 0");
     if (!(o->ss_tighten > 0 && o->ss_tighten <= 1)) return fail(GRINS_E_INVALID_ARG, "integrate: need 0 < ss_tighten <= 1");
+    if (o->method != GRINS_METHOD_DOPRI5 && o->method != GRINS_METHOD_TSIT5)
+        return fail(GRINS_E_INVALID_ARG, "integrate: unknown method %d", o->method);
     if (o->max_steps < 1) return fail(GRINS_E_INVALID_ARG, "integrate: max_steps < 1");
     if (o->n_t < 0 || (o->n_t > 0 && !o->t_grid)) return fail(GRINS_E_INVALID_ARG, "integrate: bad time grid");
     if ((o->n_t > 0) != (d_series != nullptr) && n_sets > 0)
@@ -918,11 +925,15 @@ extern "C" grins_status grins_racipe_integrate(grins_racipe_t h, const grins_sol
         pick_fp32_kernel(h, &a, true, &h->jit_why);
         h->jit_used = a.grp_jit != nullptr;
         h->used_L = a.grp.L; h->used_R = a.grp.R; h->used_P = a.grp.P;
+        h->used_method = a.method;
     } else {
         pick_fp64_kernel(h, &a, true, &h->jit_why64);
         h->jit_used64 = a.grp_jit != nullptr;
         h->ran64 = true;
     }
+    if (a.method != GRINS_METHOD_DOPRI5 && !a.grp_jit)
+        return fail(GRINS_E_INVALID_ARG, "integrate: the Tsitouras pair runs only on the kernel compiled for the "
+                    "network, which is not available here");
 
     CUDA_TRY(cudaMemsetAsync(h->d_queue, 0, 2 * sizeof(unsigned long long), st), "integrate: queue reset");
     cudaError_t le;
@@ -1304,6 +1315,7 @@ extern "C" grins_status grins_racipe_plan_create(const grins_solver_opts *o, con
         return fail(GRINS_E_INVALID_ARG, "plan_create: need finite t0 < t_end");
     if (!(o->ss_tol >= 0) || o->max_steps < 1) return fail(GRINS_E_INVALID_ARG, "plan_create: bad ss_tol or max_steps");
     if (!(o->ss_tighten > 0 && o->ss_tighten <= 1)) return fail(GRINS_E_INVALID_ARG, "plan_create: need 0 < ss_tighten <= 1");
+    if (o->method != GRINS_METHOD_DOPRI5) return fail(GRINS_E_INVALID_ARG, "plan_create: plans run Dormand-Prince only");
     if (o->n_t != 0) return fail(GRINS_E_INVALID_ARG, "plan_create: plans do not write time series");
     if (o->polish && !polish_opts_ok(o)) return fail(GRINS_E_INVALID_ARG, "plan_create: bad polish options");
     int dev = -1;
@@ -1740,6 +1752,8 @@ extern "C" grins_status grins_racipe_server_submit(grins_racipe_server_t sv, gri
         !(o->ss_tighten > 0 && o->ss_tighten <= 1) ||
         (o->polish && !polish_opts_ok(o)))
         return fail(GRINS_E_INVALID_ARG, "server_submit: bad solver options");
+    if (o->method != GRINS_METHOD_DOPRI5)
+        return fail(GRINS_E_INVALID_ARG, "server_submit: the server runs Dormand-Prince only");
     if (!(dedupe_tol >= 0)) return fail(GRINS_E_INVALID_ARG, "server_submit: dedupe_tol < 0");
     grins_racipe_ranges rr;
     if (r) rr = *r; else grins_racipe_default_ranges(&rr);
@@ -1951,6 +1965,8 @@ extern "C" grins_status grins_racipe_integrate_static(grins_racipe_t h, const gr
     if (!(o->ss_tol >= 0)) return fail(GRINS_E_INVALID_ARG, "integrate_static: ss_tol < 0");
     if (!(o->ss_tighten > 0 && o->ss_tighten <= 1))
         return fail(GRINS_E_INVALID_ARG, "integrate_static: need 0 < ss_tighten <= 1");
+    if (o->method != GRINS_METHOD_DOPRI5 && o->method != GRINS_METHOD_TSIT5)
+        return fail(GRINS_E_INVALID_ARG, "integrate_static: unknown method %d", o->method);
     if (o->max_steps < 1) return fail(GRINS_E_INVALID_ARG, "integrate_static: max_steps < 1");
     if (o->n_t < 0 || (o->n_t > 0 && !o->t_grid))
         return fail(GRINS_E_INVALID_ARG, "integrate_static: bad time grid");
@@ -2001,6 +2017,9 @@ extern "C" grins_status grins_racipe_integrate_static(grins_racipe_t h, const gr
     a.grp = grp_topo(h);
     if (o->precision == GRINS_FP32) pick_fp32_kernel(h, &a, false, nullptr);   // only kernels an earlier call loaded
     else pick_fp64_kernel(h, &a, false, nullptr);
+    if (a.method != GRINS_METHOD_DOPRI5 && !a.grp_jit)
+        return fail(GRINS_E_INVALID_ARG, "integrate_static: the Tsitouras pair needs the network's compiled kernel, "
+                    "loaded by an earlier grins_racipe_integrate call");
 
     // the array keeps the previous call's counters: clear them first
     CUDA_TRY(cudaMemsetAsync(words, 0, kStaticWords * sizeof(unsigned long long), st),

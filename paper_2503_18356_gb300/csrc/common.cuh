@@ -101,6 +101,7 @@ struct IntegrateArgs {
     float f_rtol, f_atol, f_t_end, f_ss_tol, f_ss_near, f_ss_gain;
     int64_t max_steps;
     int32_t max_steps32;         // max_steps clamped to the int32 range (filled with the copies above)
+    int32_t method;              // 5(4) pair: 0 Dormand-Prince, 1 Tsitouras (compiled kernels only)
     const double *t_grid;        // device copy, [n_t]
     int32_t n_t;
     double *states;              // [S][I][N]
@@ -133,11 +134,13 @@ struct BatchArgs {
 // kJitRegisters (records in registers) or kJitShared (records in shared
 // memory).  The returned pointer is an opaque handle for launch_grp_jit.
 enum JitKind { kJitShared = 0, kJitRegisters = 1, kJitRegisters64 = 2 };
-const void *grp_jit_kernel(const GrpTopo &g, int kind, std::string *why);
-const void *grp_jit_lookup(const GrpTopo &g, int kind);
+// method: the 5(4) pair of a register-record kernel (0 Dormand-Prince,
+// 1 Tsitouras); the shared-record kernel runs Dormand-Prince only.
+const void *grp_jit_kernel(const GrpTopo &g, int kind, std::string *why, int method = 0);
+const void *grp_jit_lookup(const GrpTopo &g, int kind, int method = 0);
 // Starts (once) a background compile for layout g: 1 ready, 0 compiling, -1
 // failed or unavailable.
-int grp_jit_prefetch(const GrpTopo &g, int kind);
+int grp_jit_prefetch(const GrpTopo &g, int kind, int method = 0);
 cudaError_t launch_grp_jit(const void *kern, const IntegrateArgs &a, cudaStream_t st, int num_sms);
 cudaError_t launch_integrate_fp32(const IntegrateArgs &a, cudaStream_t st, int num_sms);
 // Batched lane-group launch with `warps` warps per block (2 or 4); smem =

@@ -30,6 +30,25 @@ constexpr double e1 = 71.0 / 57600.0, e3 = -71.0 / 16695.0, e4 = 71.0 / 1920.0,
                  e5 = -17253.0 / 339200.0, e6 = 22.0 / 525.0, e7 = -1.0 / 40.0;
 }  // namespace dp
 
+// Tsitouras 5(4) (Ch. Tsitouras 2011, Comput. Math. Appl. 62; the paper's
+// Tsit5, Sec. 3.1): stage coefficients, 5th-order weights (the last row of
+// A, first-same-as-last) and error weights e = b5 - b4.  Unlike
+// Dormand-Prince, b2 and e2 are not zero.
+namespace ts {
+constexpr double a21 = 0.161;
+constexpr double a31 = -0.008480655492356989, a32 = 0.335480655492357;
+constexpr double a41 = 2.897153057105493, a42 = -6.359448489975075, a43 = 4.3622954328695815;
+constexpr double a51 = 5.325864828439257, a52 = -11.748883564062828, a53 = 7.4955393428898365,
+                 a54 = -0.09249506636175525;
+constexpr double a61 = 5.86145544294642, a62 = -12.92096931784711, a63 = 8.159367898576159,
+                 a64 = -0.071584973281401, a65 = -0.028269050394068383;
+constexpr double b1 = 0.09646076681806523, b2 = 0.01, b3 = 0.4798896504144996, b4 = 1.379008574103742,
+                 b5 = -3.290069515436081, b6 = 2.324710524099774;
+constexpr double e1 = -0.00178001105222577714, e2 = -0.0008164344596567469, e3 = 0.007880878010261995,
+                 e4 = -0.1447110071732629, e5 = 0.5823571654525552, e6 = -0.45808210592918697,
+                 e7 = 0.015151515151515152;
+}  // namespace ts
+
 __device__ __forceinline__ float lg2_approx(float x)
 {
     float y;

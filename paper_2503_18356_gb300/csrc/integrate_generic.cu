@@ -19,6 +19,8 @@ cudaError_t launch_integrate_grp12(const IntegrateArgs &a, cudaStream_t st, int 
 
 cudaError_t launch_integrate_fp32(const IntegrateArgs &a, cudaStream_t st, int num_sms)
 {
+    // the Tsitouras pair exists only in the kernels compiled for the network
+    if (a.method != 0) return a.grp_jit ? launch_grp_jit(a.grp_jit, a, st, num_sms) : cudaErrorNotSupported;
     // lane-group kernel when the network has a layout and its slots fit in
     // shared memory; the generic kernel otherwise
     // (a layout with continuation rows is only for the register-record kernel)
@@ -55,6 +57,7 @@ cudaError_t launch_integrate_fp32(const IntegrateArgs &a, cudaStream_t st, int n
 
 cudaError_t launch_integrate_fp64(const IntegrateArgs &a, cudaStream_t st, int num_sms)
 {
+    if (a.method != 0) return a.grp_jit ? launch_grp_jit(a.grp_jit, a, st, num_sms) : cudaErrorNotSupported;
     // the FP64 register-record kernel compiled for this network when there
     // is one; the generic kernel otherwise
     if (a.grp_jit) {

@@ -482,12 +482,33 @@ __device__ __forceinline__ void rr_comb(double (&out)[NPL], const double (&y)[NP
     }
 }
 
+// The 5(4) pair of the integrator: M = 0 Dormand-Prince (b2 = e2 = 0),
+// M = 1 Tsitouras (the paper's Tsit5).
+template <int M> struct RrTab;
+template <> struct RrTab<0> {
+    static constexpr double a21 = dp::a21, a31 = dp::a31, a32 = dp::a32, a41 = dp::a41, a42 = dp::a42,
+                            a43 = dp::a43, a51 = dp::a51, a52 = dp::a52, a53 = dp::a53, a54 = dp::a54,
+                            a61 = dp::a61, a62 = dp::a62, a63 = dp::a63, a64 = dp::a64, a65 = dp::a65;
+    static constexpr double b1 = dp::b1, b2 = 0.0, b3 = dp::b3, b4 = dp::b4, b5 = dp::b5, b6 = dp::b6;
+    static constexpr double e1 = dp::e1, e2 = 0.0, e3 = dp::e3, e4 = dp::e4, e5 = dp::e5, e6 = dp::e6,
+                            e7 = dp::e7;
+};
+template <> struct RrTab<1> {
+    static constexpr double a21 = ts::a21, a31 = ts::a31, a32 = ts::a32, a41 = ts::a41, a42 = ts::a42,
+                            a43 = ts::a43, a51 = ts::a51, a52 = ts::a52, a53 = ts::a53, a54 = ts::a54,
+                            a61 = ts::a61, a62 = ts::a62, a63 = ts::a63, a64 = ts::a64, a65 = ts::a65;
+    static constexpr double b1 = ts::b1, b2 = ts::b2, b3 = ts::b3, b4 = ts::b4, b5 = ts::b5, b6 = ts::b6;
+    static constexpr double e1 = ts::e1, e2 = ts::e2, e3 = ts::e3, e4 = ts::e4, e5 = ts::e5, e6 = ts::e6,
+                            e7 = ts::e7;
+};
+
 // Body of the register-record kernel: NPL rows, WARPS warps per block, L
 // lanes per solve, Real = float (log-domain edge terms) or double (power
-// table).
-template <int NPL, int WARPS, int L, typename Real = float>
+// table), M the 5(4) pair (RrTab).
+template <int NPL, int WARPS, int L, typename Real = float, int M = 0>
 __device__ __forceinline__ void rr_body(const IntegrateArgs &a)
 {
+    using T = RrTab<M>;
     constexpr bool F64 = sizeof(Real) == 8;
     constexpr int EL = (int)sizeof(Real);                 // bytes per gather entry
     constexpr int PLN = RrSel<Real, NPL>::planes;
@@ -674,41 +695,55 @@ __device__ __forceinline__ void rr_body(const IntegrateArgs &a)
         Real hh = h;
         if (t + hh >= t_stop) { hh = t_stop - t; clipped = true; }
 
-        rr_comb<true>(z, y, hh, (Real)dp::a21, k1);
+        rr_comb<true>(z, y, hh, (Real)T::a21, k1);
         rr_rhs<0>(q, lk, z, own);
 #pragma unroll
         for (int r = 0; r < NPL; ++r) k2[r] = z[r];
-        rr_comb<true>(z, y, hh, (Real)dp::a31, k1, (Real)dp::a32, k2);
+        rr_comb<true>(z, y, hh, (Real)T::a31, k1, (Real)T::a32, k2);
         rr_rhs<1>(q, lk, z, own);
 #pragma unroll
         for (int r = 0; r < NPL; ++r) k3[r] = z[r];
-        rr_comb<true>(z, y, hh, (Real)dp::a41, k1, (Real)dp::a42, k2, (Real)dp::a43, k3);
+        rr_comb<true>(z, y, hh, (Real)T::a41, k1, (Real)T::a42, k2, (Real)T::a43, k3);
         rr_rhs<0>(q, lk, z, own);
 #pragma unroll
         for (int r = 0; r < NPL; ++r) k4[r] = z[r];
-        rr_comb<true>(z, y, hh, (Real)dp::a51, k1, (Real)dp::a52, k2, (Real)dp::a53, k3, (Real)dp::a54, k4);
+        rr_comb<true>(z, y, hh, (Real)T::a51, k1, (Real)T::a52, k2, (Real)T::a53, k3, (Real)T::a54, k4);
         rr_rhs<1>(q, lk, z, own);
 #pragma unroll
         for (int r = 0; r < NPL; ++r) k5[r] = z[r];
-        rr_comb<true>(z, y, hh, (Real)dp::a61, k1, (Real)dp::a62, k2, (Real)dp::a63, k3, (Real)dp::a64, k4,
-                      (Real)dp::a65, k5);
+        rr_comb<true>(z, y, hh, (Real)T::a61, k1, (Real)T::a62, k2, (Real)T::a63, k3, (Real)T::a64, k4,
+                      (Real)T::a65, k5);
         rr_rhs<0>(q, lk, z, own);
 #pragma unroll
         for (int r = 0; r < NPL; ++r) k6[r] = z[r];
-        // fifth-order solution in k2 (no later stage reads k2)
-        rr_comb<true>(k2, y, hh, (Real)dp::b1, k1, (Real)dp::b3, k3, (Real)dp::b4, k4, (Real)dp::b5, k5,
-                      (Real)dp::b6, k6);
+        Real ev[NPL];                                 // error estimates
+        if constexpr (M == 0) {
+            // fifth-order solution in k2 (b2 = 0: no later stage reads k2)
+            rr_comb<true>(k2, y, hh, (Real)T::b1, k1, (Real)T::b3, k3, (Real)T::b4, k4, (Real)T::b5, k5,
+                          (Real)T::b6, k6);
 #pragma unroll
-        for (int r = 0; r < NPL; ++r) z[r] = k2[r];
-        rr_rhs<1>(q, lk, z, own);                     // z = k7
+            for (int r = 0; r < NPL; ++r) z[r] = k2[r];
+            rr_rhs<1>(q, lk, z, own);                 // z = k7
+            rr_comb<false>(ev, y, hh, (Real)T::e1, k1, (Real)T::e3, k3, (Real)T::e4, k4, (Real)T::e5, k5,
+                           (Real)T::e6, k6, (Real)T::e7, z);
+        } else {
+            Real yn[NPL];                             // fifth-order solution
+            rr_comb<true>(yn, y, hh, (Real)T::b1, k1, (Real)T::b2, k2, (Real)T::b3, k3, (Real)T::b4, k4,
+                          (Real)T::b5, k5, (Real)T::b6, k6);
+#pragma unroll
+            for (int r = 0; r < NPL; ++r) z[r] = yn[r];
+            rr_rhs<1>(q, lk, z, own);                 // z = k7
+            rr_comb<false>(ev, y, hh, (Real)T::e1, k1, (Real)T::e2, k2, (Real)T::e3, k3, (Real)T::e4, k4,
+                           (Real)T::e5, k5, (Real)T::e6, k6, (Real)T::e7, z);
+#pragma unroll
+            for (int r = 0; r < NPL; ++r) k2[r] = yn[r];   // the new state where the other pair keeps it
+        }
 
         // A non-finite stage derivative makes err non-finite -- through the
         // error weights or through the later stages it feeds -- and with it
         // the norm, which is therefore the only finiteness test needed (the
         // new state is finite whenever every stage derivative is).
-        Real en = 0, ev[NPL];
-        rr_comb<false>(ev, y, hh, (Real)dp::e1, k1, (Real)dp::e3, k3, (Real)dp::e4, k4, (Real)dp::e5, k5,
-                       (Real)dp::e6, k6, (Real)dp::e7, z);
+        Real en = 0;
 #pragma unroll
         for (int r = 0; r < NPL; ++r) {
             const Real err = ev[r];

@@ -194,7 +194,7 @@ int jit_maxnreg(int kind)
 }
 
 // Generated prelude + kernel wrapper for one layout.
-std::string jit_main(const GrpTopo &g, int kind, int minb, int warps)
+std::string jit_main(const GrpTopo &g, int kind, int minb, int warps, int method)
 {
     std::string s;
     char buf[256];
@@ -229,8 +229,8 @@ std::string jit_main(const GrpTopo &g, int kind, int minb, int warps)
         else std::snprintf(bounds, sizeof(bounds), "__launch_bounds__(%d, %d)", warps * kWarp, minb);
         std::snprintf(buf, sizeof(buf),
                       "extern \"C\" __global__ void %s grins_grp_ct(const grins::IntegrateArgs a)\n"
-                      "{\n    grins::rr_body<%d, %d, %d, %s>(a);\n}\n",
-                      bounds, g.R, warps, g.L, kind == kJitRegisters64 ? "double" : "float");
+                      "{\n    grins::rr_body<%d, %d, %d, %s, %d>(a);\n}\n",
+                      bounds, g.R, warps, g.L, kind == kJitRegisters64 ? "double" : "float", method);
     } else {
         s += "}\n#include \"integrate_grp.cuh\"\n";
         std::snprintf(buf, sizeof(buf),
@@ -322,14 +322,14 @@ int jit_minb(const GrpTopo &g, int kind)
 // Compiles the kernel for (g, kind) into e on device dev: from the block
 // count of the register estimate, one block fewer while a register-record
 // compile spills.  Wakes every thread waiting for an entry.
-void jit_build_entry(JitEntry &e, const GrpTopo &g, int kind, int dev)
+void jit_build_entry(JitEntry &e, const GrpTopo &g, int kind, int dev, int method)
 {
     cudaSetDevice(dev);
     int minb = jit_minb(g, kind);
     const int warps = jit_warps(kind);
     JitBuild b;
     for (;;) {
-        b = jit_compile(jit_main(g, kind, minb, warps));
+        b = jit_compile(jit_main(g, kind, minb, warps, method));
         if (b.ok && kind != kJitShared && b.spill_bytes > 0 && minb > 1 && !std::getenv("GRINS_JIT_MINB") &&
             !jit_maxnreg(kind)) {
             cudaLibraryUnload(b.lib);
@@ -356,9 +356,9 @@ enum JitMode { kLookup = 0, kCompileHere = 1, kCompileAsync = 2 };
 // compile.  kLookup: null when absent; kCompileHere: compiles in this
 // thread when absent and waits for a compile in flight; kCompileAsync:
 // queues a background compile when absent and returns at once.
-std::shared_ptr<JitEntry> jit_get(const GrpTopo &g, int kind, int mode)
+std::shared_ptr<JitEntry> jit_get(const GrpTopo &g, int kind, int mode, int method)
 {
-    const std::string key = jit_main(g, kind, jit_minb(g, kind), jit_warps(kind));
+    const std::string key = jit_main(g, kind, jit_minb(g, kind), jit_warps(kind), method);
     JitCache &c = jit_cache();
     std::unique_lock<std::mutex> lock(c.mu);
     auto it = c.map.find(key);
@@ -371,9 +371,9 @@ std::shared_ptr<JitEntry> jit_get(const GrpTopo &g, int kind, int mode)
         cudaGetDevice(&dev);
         if (mode == kCompileHere) {
             lock.unlock();
-            jit_build_entry(*e, g, kind, dev);
+            jit_build_entry(*e, g, kind, dev, method);
         } else {
-            jit_pool_push([e, g, kind, dev] { jit_build_entry(*e, g, kind, dev); });
+            jit_pool_push([e, g, kind, dev, method] { jit_build_entry(*e, g, kind, dev, method); });
         }
         return e;
     }
@@ -395,10 +395,14 @@ bool jit_enabled(const GrpTopo &g, std::string *why)
 // The compiled kernel for layout g (compiling it on first use), or null
 // with the reason in *why.  The pointer is an opaque handle for
 // launch_grp_jit.
-const void *grp_jit_kernel(const GrpTopo &g, int kind, std::string *why)
+const void *grp_jit_kernel(const GrpTopo &g, int kind, std::string *why, int method)
 {
     if (!jit_enabled(g, why)) return nullptr;
-    std::shared_ptr<JitEntry> e = jit_get(g, kind, kCompileHere);
+    if (method != 0 && kind == kJitShared) {
+        if (why) *why = "the shared-record kernel runs Dormand-Prince only";
+        return nullptr;
+    }
+    std::shared_ptr<JitEntry> e = jit_get(g, kind, kCompileHere, method);
     if (e->state.load() != 1) { if (why) *why = e->why; return nullptr; }
     if (why)
         *why = e->kind == kJitRegisters64 ? "FP64, records in registers"
@@ -408,10 +412,10 @@ const void *grp_jit_kernel(const GrpTopo &g, int kind, std::string *why)
 
 // The compiled kernel for layout g if an earlier call compiled it; never
 // compiles, loads or waits.
-const void *grp_jit_lookup(const GrpTopo &g, int kind)
+const void *grp_jit_lookup(const GrpTopo &g, int kind, int method)
 {
-    if (!jit_enabled(g, nullptr)) return nullptr;
-    std::shared_ptr<JitEntry> e = jit_get(g, kind, kLookup);
+    if (!jit_enabled(g, nullptr) || (method != 0 && kind == kJitShared)) return nullptr;
+    std::shared_ptr<JitEntry> e = jit_get(g, kind, kLookup, method);
     if (!e || e->state.load() != 1) return nullptr;
     return e.get();
 }
@@ -419,10 +423,10 @@ const void *grp_jit_lookup(const GrpTopo &g, int kind)
 // Starts (once) a background compile of the kernel for layout g and
 // returns its state: 1 ready, 0 compiling, -1 failed or run-time compiles
 // unavailable.
-int grp_jit_prefetch(const GrpTopo &g, int kind)
+int grp_jit_prefetch(const GrpTopo &g, int kind, int method)
 {
-    if (!jit_enabled(g, nullptr)) return -1;
-    return jit_get(g, kind, kCompileAsync)->state.load();
+    if (!jit_enabled(g, nullptr) || (method != 0 && kind == kJitShared)) return -1;
+    return jit_get(g, kind, kCompileAsync, method)->state.load();
 }
 
 cudaError_t launch_grp_jit(const void *handle, const IntegrateArgs &a, cudaStream_t st, int num_sms)
