@@ -13,6 +13,7 @@ Functions mirror the paper (GRiNS, arXiv 2503.18356):
                                            and time series (Sec. 2.1.3)
   * ``polish``                          -- Newton on Eq. 1 = 0
   * ``dedupe``                          -- unique steady states (Sec. 3.1)
+  * ``ising_run``                       -- Boolean Ising formalism (Sec. 2.2, Eq. 3)
   * ``gk_histogram`` / ``level_boundaries`` / ``level_states``
                                         -- levels of G/k-normalised expression,
                                            state labels and multistability
@@ -118,6 +119,9 @@ def lib():
             l.orc_dedupe.argtypes = [C.c_int32, C.c_int32, P(C.c_double), P(C.c_uint8),
                                      P(C.c_double), P(C.c_double), C.c_double, P(C.c_int32)]
             l.orc_dedupe.restype = C.c_int32
+            l.orc_ising_run.argtypes = [P(Net), C.c_int32, C.c_int32, C.c_uint64, C.c_int64, P(C.c_uint64),
+                                        C.c_int32, P(C.c_uint64), P(C.c_int32), P(C.c_uint8)]
+            l.orc_ising_run.restype = C.c_int32
             l.orc_tableau.argtypes = [C.c_int32, P(C.c_double), P(C.c_double), P(C.c_double), P(C.c_double)]
             l.orc_gk_bin.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int32]
             l.orc_gk_bin.restype = C.c_int32
@@ -350,6 +354,21 @@ def level_states(states, status, G, k, bounds, n_bins=100):
                                 _p(k, C.c_double), n_bins, _p(b, C.c_int32) if b.size else None, b.size,
                                 _p(labels, C.c_uint64), _p(ns, C.c_int32), _p(mh, C.c_uint64))
     return None if rc != 0 else (labels, ns, mh)
+
+
+def ising_run(net: Network, mode=0, seed=0, n_traj=1, init=None, max_steps=1000, enc01=False):
+    """Boolean Ising trajectories (Eq. 3) -> (final uint64 [n_traj], steps
+    int32, status uint8); mode 0 synchronous, 1 asynchronous; init: uint64
+    states (bit i = node i active) or None for random ones from seed."""
+    fin = np.zeros(n_traj, dtype=np.uint64)
+    stp = np.zeros(n_traj, dtype=np.int32)
+    st = np.zeros(n_traj, dtype=np.uint8)
+    ini = None if init is None else np.ascontiguousarray(init, dtype=np.uint64)
+    rc = lib().orc_ising_run(C.byref(net.c), mode, int(bool(enc01)), seed, n_traj,
+                             _p(ini, C.c_uint64), max_steps, _p(fin, C.c_uint64), _p(stp, C.c_int32),
+                             _p(st, C.c_uint8))
+    assert rc == 0
+    return fin, stp, st
 
 
 def run_sets(net: Network, p: ParamSet, ic_unit, polish=True, polish_tol=1e-13,

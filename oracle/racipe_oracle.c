@@ -888,3 +888,80 @@ int32_t orc_level_states(int32_t N, int32_t n_ics, int64_t n_sets, const double 
     }
     return 0;
 }
+
+/* ------------------------------------------------------------------ */
+/* Boolean Ising formalism (Sec. 2.2, Eq. 3): node i becomes active    */
+/* when sum_j J_ij s_j > 0, inactive when it is < 0, and keeps its      */
+/* state when it is 0; J_ij = +1 for an activating edge j -> i, -1 for  */
+/* an inhibiting one.  A state is a word of N bits, bit i set = node i  */
+/* active (s_i = +1); an inactive node counts as s_i = -1, or as 0 with */
+/* enc01 (the 0/1 encoding).  Synchronous mode updates every node at    */
+/* once; asynchronous mode updates one node per step, chosen uniformly  */
+/* (draw 1 + k of the stream (seed, ORC_TAG_ISING, trajectory) for step */
+/* k, orc_uint_range over [0, N-1]).  Initial states: given, or draw 0  */
+/* of the same stream masked to N bits.  A trajectory stops at a fixed  */
+/* point (no node would change: status CONVERGED, steps = updates       */
+/* applied before it) or after max_steps updates (status MAXSTEPS).     */
+/* ------------------------------------------------------------------ */
+#define ORC_TAG_ISING 0x4953494E47424FULL   /* "ISINGBO" */
+
+static int ising_field(const orc_net *net, int i, uint64_t s, int enc01)
+{
+    int h = 0;
+    for (int e = 0; e < net->n_edges; ++e) {
+        if (net->dst[e] != i) continue;
+        int sj = ((s >> net->src[e]) & 1ULL) ? 1 : (enc01 ? 0 : -1);
+        h += net->sign[e] * sj;
+    }
+    return h;
+}
+
+/* The state after updating node i of s. */
+static uint64_t ising_node(const orc_net *net, int i, uint64_t s, int enc01)
+{
+    int h = ising_field(net, i, s, enc01);
+    if (h > 0) return s | (1ULL << i);
+    if (h < 0) return s & ~(1ULL << i);
+    return s;
+}
+
+/* The state after updating every node of s at once. */
+static uint64_t ising_sync(const orc_net *net, uint64_t s, int enc01)
+{
+    uint64_t t = s;
+    for (int i = 0; i < net->n_nodes; ++i) {
+        uint64_t u = ising_node(net, i, s, enc01);
+        t = (t & ~(1ULL << i)) | (u & (1ULL << i));
+    }
+    return t;
+}
+
+/* Runs n_traj trajectories; mode 0 synchronous, 1 asynchronous.        */
+/* Returns 0, or -1 for more than 64 nodes.                             */
+int32_t orc_ising_run(const orc_net *net, int32_t mode, int32_t enc01, uint64_t seed, int64_t n_traj,
+                      const uint64_t *init, int32_t max_steps, uint64_t *final, int32_t *steps,
+                      uint8_t *status)
+{
+    int N = net->n_nodes;
+    if (N > 64) return -1;
+    uint64_t mask = N == 64 ? ~0ULL : ((1ULL << N) - 1ULL);
+    for (int64_t t = 0; t < n_traj; ++t) {
+        uint64_t s = init ? init[t] & mask : draw64(seed, ORC_TAG_ISING, (uint64_t)t, 0) & mask;
+        int32_t k = 0;
+        uint8_t st = ORC_MAXSTEPS;
+        for (;;) {
+            uint64_t next = ising_sync(net, s, enc01);
+            if (next == s) { st = ORC_CONVERGED; break; }
+            if (k >= max_steps) break;
+            if (mode == 0) {
+                s = next;
+            } else {
+                int i = orc_uint_range(draw64(seed, ORC_TAG_ISING, (uint64_t)t, 1 + (uint64_t)k), 0, N - 1);
+                s = ising_node(net, i, s, enc01);
+            }
+            ++k;
+        }
+        final[t] = s; steps[t] = k; status[t] = st;
+    }
+    return 0;
+}
