@@ -242,6 +242,38 @@ def tsit5_measurement(h, params, ic, out, stream, S, I, reps=2):
                 converged_share=float((st == 0).mean()), kernel=h.integrator())
 
 
+def ising_measurement(h, stream, N, n_traj=1_000_000, reps=3):
+    """The Boolean Ising formalism (Eq. 3) on the same network: random
+    initial states, synchronous and asynchronous modes, CUDA events."""
+    import numpy as np
+    import torch
+    from paper_2503_18356_gb300 import api
+    res = {}
+    for name, mode, max_steps in (("sync", api.GRINS_ISING_SYNC, 200), ("async", api.GRINS_ISING_ASYNC, 2000)):
+        out = h.ising_run(n_traj, mode=mode, seed=77, max_steps=max_steps, stream=stream)   # warm-up
+        ts = []
+        for _ in range(reps):
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            ev[0].record(stream)
+            h.ising_run(n_traj, mode=mode, seed=77, max_steps=max_steps, stream=stream, out=out)
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            ts.append(ev[0].elapsed_time(ev[1]))
+        ms = float(np.mean(ts))
+        fin = out[0].cpu().numpy()
+        steps = out[1].cpu().numpy().astype(np.int64)
+        conv = out[2].cpu().numpy() == 0
+        vals, cnt = np.unique(fin[conv], return_counts=True)
+        # node updates: every node of every synchronous step, one node an asynchronous step
+        updates = float(steps.sum() * (N if mode == api.GRINS_ISING_SYNC else 1))
+        res[name] = dict(ms=ms, trajectories_per_s=n_traj / (ms / 1e3), node_updates_per_s=updates / (ms / 1e3),
+                         max_steps=max_steps, converged_share=float(conv.mean()),
+                         distinct_fixed_points=int(vals.size),
+                         top_state_share=float(cnt.max() / conv.sum()) if cnt.size else 0.0)
+    res["trajectories"] = n_traj
+    return res
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -468,6 +500,7 @@ def run_native(args):
     status = out["status"].cpu().numpy()
     levels = levels_measurement(h, params, out, stream, dev, S, I) if rank == 0 else None
     tsit5 = tsit5_measurement(h, params, ic, out, stream, S, I) if rank == 0 else None
+    ising = ising_measurement(h, stream, N) if rank == 0 else None
 
     # algorithmic work of the FP32 integrator (per step attempt of one solve)
     w32 = 35 * E + 45 * N
@@ -577,6 +610,8 @@ def run_native(args):
             line["levels"] = levels
         if tsit5 is not None:
             line["tsit5"] = tsit5
+        if ising is not None:
+            line["ising"] = ising
         if args.batch_reps > 0 and ws == 1:
             line["batched"] = batched_measurement(dev, args.batch_reps)
         if args.serve_seconds > 0 and ws == 1:

@@ -482,6 +482,31 @@ grins_status grins_racipe_level_states(grins_racipe_t h, const void *d_params,
                                        unsigned long long *d_labels, int32_t *d_n_states,
                                        unsigned long long *d_multi_hist, void *stream);
 
+/* ----------------------------------------------------------------- Ising
+ * Boolean Ising formalism on the handle's network (Sec. 2.2, Eq. 3): node i
+ * turns on when sum_j J_ij s_j > 0, off when it is < 0, and keeps its
+ * state on a tie; J_ij = +1 for an activating edge j -> i, -1 for an
+ * inhibiting one.  A state is a 64-bit word, bit i set = node i on (s_i =
+ * +1); an off node counts as s_i = -1, or as 0 with enc01 (the 0/1
+ * encoding).  GRINS_ISING_SYNC updates every node at once,
+ * GRINS_ISING_ASYNC one node per step, chosen uniformly from the
+ * trajectory's counter-based stream: Philox4x64-10 with key (seed,
+ * 0x4953494E47424F), draw d = word d % 4 of the block with counter
+ * (trajectory, d / 4, 0, 0); step k takes draw 1 + k and the node
+ * ((draw >> 32) * N) >> 32.  A trajectory stops at a fixed point (no node
+ * would change: status GRINS_SS_CONVERGED, steps = updates applied before
+ * it) or after max_steps updates (GRINS_SS_MAXSTEPS).
+ *   d_init   uint64 [n_traj] initial states, or NULL: draw 0 of each
+ *            trajectory's stream, masked to N bits
+ *   d_final  uint64 [n_traj], d_steps int32 [n_traj], d_status uint8 [n_traj]
+ * Asynchronous on stream.  Errors: GRINS_E_INVALID_ARG for a NULL handle or
+ * output buffer, an unknown mode, n_traj < 0 or max_steps < 0. */
+enum { GRINS_ISING_SYNC = 0, GRINS_ISING_ASYNC = 1 };
+grins_status grins_ising_run(grins_racipe_t h, int32_t mode, int32_t enc01, uint64_t seed, int64_t n_traj,
+                             const unsigned long long *d_init, int32_t max_steps,
+                             unsigned long long *d_final, int32_t *d_steps, uint8_t *d_status,
+                             void *stream);
+
 #ifdef __cplusplus
 }
 #endif

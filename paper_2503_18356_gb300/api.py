@@ -32,6 +32,7 @@ GRINS_OK, GRINS_E_INVALID_ARG, GRINS_E_TOPOLOGY, GRINS_E_NOMEM, GRINS_E_CUDA, GR
 CONVERGED, TEND, MAXSTEPS, NONFINITE, POLISH_FAIL = range(5)
 GRINS_FP64, GRINS_FP32 = 0, 1
 GRINS_METHOD_DOPRI5, GRINS_METHOD_TSIT5 = 0, 1
+GRINS_ISING_SYNC, GRINS_ISING_ASYNC = 0, 1
 MEDIAN_PER_INDEGREE, MEDIAN_UNREGULATED = 0, 1
 GRINS_STATIC_MAX_GRID = 4096        # largest time grid of grins_racipe_integrate_static
 
@@ -116,6 +117,7 @@ _sig = {
                                     C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "grins_racipe_level_states": (_S, [_H, _P, _P, _P, C.c_int64, C.c_int32, C.c_int32, C.POINTER(C.c_int32),
                                        C.c_int32, _P, _P, _P, _P]),
+    "grins_ising_run": (_S, [_H, C.c_int32, C.c_int32, C.c_uint64, C.c_int64, _P, C.c_int32, _P, _P, _P, _P]),
 }
 EXPORTED = tuple(_sig)
 for _name, (_res, _args) in _sig.items():
@@ -318,6 +320,20 @@ class Racipe:
             _check(_lib.grins_racipe_gk_histogram(self._h, _ptr(params), _ptr(states), _ptr(status), S, I,
                                                   n_bins, _ptr(counts), _stream(stream)))
         return counts
+
+    def ising_run(self, n_traj, mode=GRINS_ISING_SYNC, seed=0, init=None, max_steps=1000, enc01=False,
+                  stream=None, out=None):
+        """Boolean Ising trajectories (grins_ising_run) -> (final states uint64
+        as int64 [n_traj], steps int32, status uint8); init: a device int64
+        tensor of states (bit i = node i on) or None for random ones."""
+        if out is None:
+            out = (torch.empty((n_traj,), dtype=torch.int64, device=self.device),
+                   torch.empty((n_traj,), dtype=torch.int32, device=self.device),
+                   torch.empty((n_traj,), dtype=torch.uint8, device=self.device))
+        with torch.cuda.device(self.device):
+            _check(_lib.grins_ising_run(self._h, mode, int(bool(enc01)), seed, n_traj, _ptr(init), max_steps,
+                                        _ptr(out[0]), _ptr(out[1]), _ptr(out[2]), _stream(stream)))
+        return out
 
     def level_states(self, params, states, status, bounds, n_bins=100, stream=None, out=None):
         """-> (labels uint64 [S, I] as int64, n_states int32 [S], multi_hist

@@ -1113,6 +1113,31 @@ extern "C" grins_status grins_racipe_level_states(grins_racipe_t h, const void *
     return GRINS_OK;
 }
 
+// ------------------------------------------------------------------- Ising
+extern "C" grins_status grins_ising_run(grins_racipe_t h, int32_t mode, int32_t enc01, uint64_t seed,
+                                        int64_t n_traj, const unsigned long long *d_init, int32_t max_steps,
+                                        unsigned long long *d_final, int32_t *d_steps, uint8_t *d_status,
+                                        void *stream)
+{
+    g_last_error.clear();
+    if (!h) return fail(GRINS_E_INVALID_ARG, "ising_run: NULL handle");
+    if (mode != GRINS_ISING_SYNC && mode != GRINS_ISING_ASYNC) return fail(GRINS_E_INVALID_ARG, "ising_run: unknown mode %d", mode);
+    if (n_traj < 0 || max_steps < 0) return fail(GRINS_E_INVALID_ARG, "ising_run: negative size");
+    if (n_traj > 0 && (!d_final || !d_steps || !d_status)) return fail(GRINS_E_INVALID_ARG, "ising_run: NULL output buffer");
+    if (!on_handle_device(h)) return fail(GRINS_E_INVALID_ARG, "ising_run: current device is not the handle's");
+    IsingArgs a{};
+    a.N = h->N; a.mode = mode; a.enc01 = enc01 ? 1 : 0; a.max_steps = max_steps;
+    a.seed = seed; a.n_traj = n_traj; a.init = d_init;
+    a.final_state = d_final; a.steps = d_steps; a.status = d_status;
+    for (int e = 0; e < h->E; ++e) {
+        const int i = h->dst[e];
+        if (h->sign[e] > 0) { a.act[i] |= 1ull << h->src[e]; ++a.n_act[i]; }
+        else { a.inh[i] |= 1ull << h->src[e]; ++a.n_inh[i]; }
+    }
+    CUDA_TRY(launch_ising(a, (cudaStream_t)stream, h->num_sms), "ising_run: launch");
+    return GRINS_OK;
+}
+
 // ------------------------------------------------------------------- plans
 // A plan integrates many networks (jobs) in one batched launch of the
 // lane-group kernel, followed by each job's polish and dedupe, all captured

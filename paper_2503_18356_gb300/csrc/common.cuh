@@ -211,6 +211,24 @@ cudaError_t launch_gk_histogram(const LevelArgs &a, cudaStream_t st, int num_sms
 cudaError_t launch_level_states(const LevelArgs &a, cudaStream_t st, int num_sms);
 #endif
 
+// ------------------------------------------------------------------ Ising
+struct IsingArgs {
+    int32_t N, mode, enc01, max_steps;
+    uint64_t seed;
+    int64_t n_traj;
+    const unsigned long long *init;      // [n_traj] or null: random from the seed
+    unsigned long long *final_state;     // [n_traj]
+    int32_t *steps;                      // [n_traj]
+    uint8_t *status;                     // [n_traj]
+    unsigned long long act[kMaxNodes];   // per node: bits of its activating sources
+    unsigned long long inh[kMaxNodes];   // and of its inhibiting ones
+    int32_t n_act[kMaxNodes], n_inh[kMaxNodes];
+};
+
+#ifndef __CUDACC_RTC__
+cudaError_t launch_ising(const IsingArgs &a, cudaStream_t st, int num_sms);
+#endif
+
 // ------------------------------------------------------------- device RNG
 // Philox4x64-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds of the
 // four-word Philox bijection with the published multipliers and Weyl key
