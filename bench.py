@@ -274,6 +274,29 @@ def ising_measurement(h, stream, N, n_traj=1_000_000, reps=3):
     return res
 
 
+def sampler_measurement(h, stream, S, reps=3):
+    """The parameter sampler of the workload under each distribution of
+    every continuous class (Table 1, log-uniform, normal, log-normal):
+    CUDA-event time of one call for all S sets (the medians are cached)."""
+    import numpy as np
+    import torch
+    from paper_2503_18356_gb300 import api
+    res = {}
+    for name, d in (("table1", 0), ("loguniform", 1), ("normal", 2), ("lognormal", 3)):
+        r = api.default_ranges(dist_G=d, dist_k=d, dist_lam_act=d, dist_lam_inh=d)
+        params, _ = h.sample_params(2000, S, 1, ranges=r, stream=stream)       # medians, warm-up
+        ts = []
+        for _ in range(reps):
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            ev[0].record(stream)
+            h.sample_params(2000, S, 1, ranges=r, stream=stream, params=params)
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            ts.append(ev[0].elapsed_time(ev[1]))
+        res[name] = dict(ms=float(np.mean(ts)), sets_per_s=S / (float(np.mean(ts)) / 1e3))
+    return res
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -501,6 +524,7 @@ def run_native(args):
     levels = levels_measurement(h, params, out, stream, dev, S, I) if rank == 0 else None
     tsit5 = tsit5_measurement(h, params, ic, out, stream, S, I) if rank == 0 else None
     ising = ising_measurement(h, stream, N) if rank == 0 else None
+    samplers = sampler_measurement(h, stream, S) if rank == 0 else None
 
     # algorithmic work of the FP32 integrator (per step attempt of one solve)
     w32 = 35 * E + 45 * N
@@ -612,6 +636,8 @@ def run_native(args):
             line["tsit5"] = tsit5
         if ising is not None:
             line["ising"] = ising
+        if samplers is not None:
+            line["samplers"] = samplers
         if args.batch_reps > 0 and ws == 1:
             line["batched"] = batched_measurement(dev, args.batch_reps)
         if args.serve_seconds > 0 and ws == 1:

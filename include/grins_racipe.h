@@ -72,6 +72,17 @@ typedef enum {
 enum { GRINS_FP64 = 0, GRINS_FP32 = 1 };                       /* precision */
 enum { GRINS_METHOD_DOPRI5 = 0, GRINS_METHOD_TSIT5 = 1 };        /* 5(4) pair */
 enum { GRINS_MEDIAN_PER_INDEGREE = 0, GRINS_MEDIAN_UNREGULATED = 1 };
+/* Distribution of a continuous parameter class over its [min, max] range
+ * (the paper's samplers besides Table 1's, Sec. 2.1.2):
+ *   GRINS_DIST_TABLE1      uniform; for the inhibiting fold change, uniform
+ *                          in the inverse range and inverted (the default)
+ *   GRINS_DIST_LOGUNIFORM  exp(U[log min, log max])
+ *   GRINS_DIST_NORMAL      mean (min + max) / 2, s.d. (max - min) / 6,
+ *                          clamped to [min, max]
+ *   GRINS_DIST_LOGNORMAL   the same in log space, then exp
+ * The normal deviate is Box-Muller on the draw's two 32-bit halves,
+ * u_hi, u_lo = (half + 1/2) 2^-32: sqrt(-2 log u_hi) cos(2 pi u_lo). */
+enum { GRINS_DIST_TABLE1 = 0, GRINS_DIST_LOGUNIFORM = 1, GRINS_DIST_NORMAL = 2, GRINS_DIST_LOGNORMAL = 3 };
 
 /* Sampling ranges, Table 1 (Sec. 2.1.2).  grins_racipe_default_ranges fills
  * the defaults: G [1,100], k [0.1,1], activating lambda [1,100], inhibiting
@@ -87,6 +98,9 @@ typedef struct {
     double thr_lo, thr_hi;
     int32_t median_samples;
     int32_t median_mode;       /* GRINS_MEDIAN_* */
+    int32_t dist_G, dist_k;            /* GRINS_DIST_* of G, k */
+    int32_t dist_lam_act, dist_lam_inh;/* and of the two fold changes (the
+                                          half-functional medians use them too) */
 } grins_racipe_ranges;
 
 /* Solver controls (Sec. 2.1.3: tolerances, start and end time, stop at

@@ -58,7 +58,9 @@ class Ranges(C.Structure):
                 ("lam_inh_min", C.c_double), ("lam_inh_max", C.c_double),
                 ("n_min", C.c_int32), ("n_max", C.c_int32),
                 ("thr_lo", C.c_double), ("thr_hi", C.c_double),
-                ("median_samples", C.c_int32), ("median_mode", C.c_int32)]
+                ("median_samples", C.c_int32), ("median_mode", C.c_int32),
+                ("dist_G", C.c_int32), ("dist_k", C.c_int32),
+                ("dist_lam_act", C.c_int32), ("dist_lam_inh", C.c_int32)]
 
 
 class Net(C.Structure):

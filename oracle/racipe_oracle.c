@@ -109,6 +109,7 @@ typedef struct {
     double thr_lo, thr_hi;         /* half-functional factors */
     int32_t median_samples;        /* samples per median estimate */
     int32_t median_mode;           /* 0 = per in-degree class, 1 = unregulated */
+    int32_t dist_G, dist_k, dist_lam_act, dist_lam_inh;   /* distribution per class, below */
 } orc_ranges;
 
 void orc_default_ranges(orc_ranges *r)
@@ -121,24 +122,54 @@ void orc_default_ranges(orc_ranges *r)
     r->thr_lo = 0.02; r->thr_hi = 1.98;
     r->median_samples = 10000;
     r->median_mode = 0;
+    r->dist_G = r->dist_k = r->dist_lam_act = r->dist_lam_inh = 0;
 }
 
 /* Affine map of a unit draw onto [lo, hi]: lo + (hi - lo) * u. */
 static double affine(double lo, double hi, double u) { return lo + (hi - lo) * u; }
 
-/* Activating fold change: uniform on [lam_act_min, lam_act_max] (Table 1). */
-static double lam_activating(const orc_ranges *r, double u)
+/* The paper's samplers besides Table 1's (Sec. 2.1.2), for one continuous */
+/* parameter over [lo, hi] from one 64-bit draw x: dist 0 uniform (Table 1),*/
+/* 1 log-uniform: exp(U[log lo, log hi]), 2 normal: mean (lo + hi) / 2,    */
+/* standard deviation (hi - lo) / 6, clamped to [lo, hi], 3 log-normal: the */
+/* same in log space, then exp.  The normal deviate is Box-Muller on the    */
+/* draw's two 32-bit halves h, l: u = (h + 1/2) 2^-32, v = (l + 1/2) 2^-32, */
+/* z = sqrt(-2 log u) cos(2 pi v).                                          */
+static double param_draw(int32_t dist, double lo, double hi, uint64_t x)
 {
-    return affine(r->lam_act_min, r->lam_act_max, u);
+    if (dist == 1) return exp(affine(log(lo), log(hi), orc_u01(x)));
+    if (dist == 2 || dist == 3) {
+        double u = ((double)(x >> 32) + 0.5) * 0x1.0p-32;
+        double v = ((double)(x & 0xffffffffULL) + 0.5) * 0x1.0p-32;
+        double z = sqrt(-2.0 * log(u)) * cos(6.283185307179586 * v);
+        double y;
+        if (dist == 2) {
+            y = (lo + hi) / 2.0 + z * ((hi - lo) / 6.0);
+        } else {
+            double a = log(lo), b = log(hi);
+            y = exp((a + b) / 2.0 + z * ((b - a) / 6.0));
+        }
+        return y < lo ? lo : (y > hi ? hi : y);
+    }
+    return affine(lo, hi, orc_u01(x));
+}
+
+/* Activating fold change: uniform on [lam_act_min, lam_act_max] (Table 1),
+ * or the class's distribution. */
+static double lam_activating(const orc_ranges *r, uint64_t x)
+{
+    return param_draw(r->dist_lam_act, r->lam_act_min, r->lam_act_max, x);
 }
 
 /* Inhibiting fold change, Sec. 2.1.2: drawn uniformly in the inverse range
- * [1/max, 1/min] and then inverted. */
-static double lam_inhibiting(const orc_ranges *r, double u)
+ * [1/max, 1/min] and then inverted (Table 1), or the class's distribution
+ * over [lam_inh_min, lam_inh_max]. */
+static double lam_inhibiting(const orc_ranges *r, uint64_t x)
 {
+    if (r->dist_lam_inh != 0) return param_draw(r->dist_lam_inh, r->lam_inh_min, r->lam_inh_max, x);
     double v_lo = 1.0 / r->lam_inh_max;
     double v_hi = 1.0 / r->lam_inh_min;
-    return 1.0 / affine(v_lo, v_hi, u);
+    return 1.0 / affine(v_lo, v_hi, orc_u01(x));
 }
 
 /* ------------------------------------------------------------------ */
@@ -244,18 +275,18 @@ void orc_median_samples(int32_t a, int32_t b, const orc_ranges *r, double M0,
     int K = r->median_samples;
     uint64_t key1 = ((uint64_t)(uint32_t)a << 32) | (uint64_t)(uint32_t)b;
     for (int s = 0; s < K; ++s) {
-        double G = affine(r->G_min, r->G_max, orc_u01(draw64(ORC_KEY_MEDIAN, key1, (uint64_t)s, 0)));
-        double k = affine(r->k_min, r->k_max, orc_u01(draw64(ORC_KEY_MEDIAN, key1, (uint64_t)s, 1)));
+        double G = param_draw(r->dist_G, r->G_min, r->G_max, draw64(ORC_KEY_MEDIAN, key1, (uint64_t)s, 0));
+        double k = param_draw(r->dist_k, r->k_min, r->k_max, draw64(ORC_KEY_MEDIAN, key1, (uint64_t)s, 1));
         double level = G / k;
         for (int m = 0; m < a + b; ++m) {
             uint64_t d = 2 + 5 * (uint64_t)m;
-            double Gs = affine(r->G_min, r->G_max, orc_u01(draw64(ORC_KEY_MEDIAN, key1, (uint64_t)s, d + 0)));
-            double ks = affine(r->k_min, r->k_max, orc_u01(draw64(ORC_KEY_MEDIAN, key1, (uint64_t)s, d + 1)));
+            double Gs = param_draw(r->dist_G, r->G_min, r->G_max, draw64(ORC_KEY_MEDIAN, key1, (uint64_t)s, d + 0));
+            double ks = param_draw(r->dist_k, r->k_min, r->k_max, draw64(ORC_KEY_MEDIAN, key1, (uint64_t)s, d + 1));
             double T = affine(r->thr_lo, r->thr_hi, orc_u01(draw64(ORC_KEY_MEDIAN, key1, (uint64_t)s, d + 2))) * M0;
-            double ul = orc_u01(draw64(ORC_KEY_MEDIAN, key1, (uint64_t)s, d + 3));
+            uint64_t xl = draw64(ORC_KEY_MEDIAN, key1, (uint64_t)s, d + 3);
             int32_t n = orc_uint_range(draw64(ORC_KEY_MEDIAN, key1, (uint64_t)s, d + 4), r->n_min, r->n_max);
             int sign = m < a ? +1 : -1;
-            double lam = sign > 0 ? lam_activating(r, ul) : lam_inhibiting(r, ul);
+            double lam = sign > 0 ? lam_activating(r, xl) : lam_inhibiting(r, xl);
             level = level * edge_factor(sign, Gs / ks, T, (double)n, lam);
         }
         out[s] = level;
@@ -307,15 +338,15 @@ void orc_sample_params(const orc_net *net, const orc_ranges *r, uint64_t seed,
         double *Gs = G + s * N, *ks = k + s * N, *Ts = T + s * E, *ls = lam + s * E;
         int32_t *ns = n + s * E;
         for (int i = 0; i < N; ++i) {
-            Gs[i] = affine(r->G_min, r->G_max, orc_u01(draw64(seed, ORC_TAG_PARAMS, c0, (uint64_t)i)));
-            ks[i] = affine(r->k_min, r->k_max, orc_u01(draw64(seed, ORC_TAG_PARAMS, c0, (uint64_t)(N + i))));
+            Gs[i] = param_draw(r->dist_G, r->G_min, r->G_max, draw64(seed, ORC_TAG_PARAMS, c0, (uint64_t)i));
+            ks[i] = param_draw(r->dist_k, r->k_min, r->k_max, draw64(seed, ORC_TAG_PARAMS, c0, (uint64_t)(N + i)));
         }
         for (int e = 0; e < E; ++e) {
             double ut = orc_u01(draw64(seed, ORC_TAG_PARAMS, c0, (uint64_t)(2 * N + e)));
-            double ul = orc_u01(draw64(seed, ORC_TAG_PARAMS, c0, (uint64_t)(2 * N + E + e)));
+            uint64_t xl = draw64(seed, ORC_TAG_PARAMS, c0, (uint64_t)(2 * N + E + e));
             uint64_t rn = draw64(seed, ORC_TAG_PARAMS, c0, (uint64_t)(2 * N + 2 * E + e));
             Ts[e] = affine(r->thr_lo, r->thr_hi, ut) * Msrc[net->src[e]];
-            ls[e] = net->sign[e] > 0 ? lam_activating(r, ul) : lam_inhibiting(r, ul);
+            ls[e] = net->sign[e] > 0 ? lam_activating(r, xl) : lam_inhibiting(r, xl);
             ns[e] = orc_uint_range(rn, r->n_min, r->n_max);
         }
     }

@@ -33,6 +33,7 @@ CONVERGED, TEND, MAXSTEPS, NONFINITE, POLISH_FAIL = range(5)
 GRINS_FP64, GRINS_FP32 = 0, 1
 GRINS_METHOD_DOPRI5, GRINS_METHOD_TSIT5 = 0, 1
 GRINS_ISING_SYNC, GRINS_ISING_ASYNC = 0, 1
+GRINS_DIST_TABLE1, GRINS_DIST_LOGUNIFORM, GRINS_DIST_NORMAL, GRINS_DIST_LOGNORMAL = 0, 1, 2, 3
 MEDIAN_PER_INDEGREE, MEDIAN_UNREGULATED = 0, 1
 GRINS_STATIC_MAX_GRID = 4096        # largest time grid of grins_racipe_integrate_static
 
@@ -44,7 +45,9 @@ class grins_racipe_ranges(C.Structure):
                 ("lam_inh_min", C.c_double), ("lam_inh_max", C.c_double),
                 ("n_min", C.c_int32), ("n_max", C.c_int32),
                 ("thr_lo", C.c_double), ("thr_hi", C.c_double),
-                ("median_samples", C.c_int32), ("median_mode", C.c_int32)]
+                ("median_samples", C.c_int32), ("median_mode", C.c_int32),
+                ("dist_G", C.c_int32), ("dist_k", C.c_int32),
+                ("dist_lam_act", C.c_int32), ("dist_lam_inh", C.c_int32)]
 
 
 class grins_solver_opts(C.Structure):

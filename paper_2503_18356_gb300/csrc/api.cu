@@ -119,6 +119,7 @@ extern "C" void grins_racipe_default_ranges(grins_racipe_ranges *r)
     r->thr_lo = 0.02; r->thr_hi = 1.98;
     r->median_samples = 10000;
     r->median_mode = GRINS_MEDIAN_PER_INDEGREE;
+    r->dist_G = r->dist_k = r->dist_lam_act = r->dist_lam_inh = GRINS_DIST_TABLE1;
 }
 
 extern "C" void grins_solver_default_opts(grins_solver_opts *o)
@@ -561,6 +562,28 @@ struct MedianStream {
 
 inline double span_map(double lo, double hi, double u) { return lo + (hi - lo) * u; }
 
+// A continuous parameter of class distribution `dist` over [lo, hi] from one
+// 64-bit draw (GRINS_DIST_*; Table 1's uniform map when dist is 0).
+double dist_draw(int dist, double lo, double hi, uint64_t r)
+{
+    if (dist == GRINS_DIST_LOGUNIFORM) return std::exp(span_map(std::log(lo), std::log(hi), unit_double(r)));
+    if (dist == GRINS_DIST_NORMAL || dist == GRINS_DIST_LOGNORMAL) {
+        const double uh = ((double)(r >> 32) + 0.5) * 0x1.0p-32, ul = ((double)(r & 0xffffffffu) + 0.5) * 0x1.0p-32;
+        const double z = std::sqrt(-2.0 * std::log(uh)) * std::cos(6.283185307179586 * ul);
+        if (dist == GRINS_DIST_NORMAL) return std::min(hi, std::max(lo, (lo + hi) / 2.0 + z * ((hi - lo) / 6.0)));
+        const double a = std::log(lo), b = std::log(hi);
+        return std::min(hi, std::max(lo, std::exp((a + b) / 2.0 + z * ((b - a) / 6.0))));
+    }
+    return span_map(lo, hi, unit_double(r));
+}
+
+// The inhibiting fold change: Table 1's inverse-range rule, or dist_draw.
+double lam_inh_draw(const grins_racipe_ranges &r, uint64_t x)
+{
+    if (r.dist_lam_inh == GRINS_DIST_TABLE1) return 1.0 / span_map(1.0 / r.lam_inh_max, 1.0 / r.lam_inh_min, unit_double(x));
+    return dist_draw(r.dist_lam_inh, r.lam_inh_min, r.lam_inh_max, x);
+}
+
 // Eq. 2 in its printed form, H = B0^n/(B0^n+B^n) + lambda B^n/(B0^n+B^n),
 // times 1/lambda for an activating input (Eq. 1).
 inline double hill_factor(bool act, double B, double B0, double n, double lam)
@@ -588,20 +611,19 @@ std::vector<double> level_samples(int na, int ni, const grins_racipe_ranges &r, 
     const MedianStream ms{((uint64_t)(uint32_t)na << 32) | (uint64_t)(uint32_t)ni};
     const int K = r.median_samples;
     std::vector<double> out((size_t)K);
-    const double v_lo = 1.0 / r.lam_inh_max, v_hi = 1.0 / r.lam_inh_min;
     for (int s = 0; s < K; ++s) {
-        const double G = span_map(r.G_min, r.G_max, unit_double(ms.draw(s, 0)));
-        const double k = span_map(r.k_min, r.k_max, unit_double(ms.draw(s, 1)));
+        const double G = dist_draw(r.dist_G, r.G_min, r.G_max, ms.draw(s, 0));
+        const double k = dist_draw(r.dist_k, r.k_min, r.k_max, ms.draw(s, 1));
         double level = G / k;
         for (int m = 0; m < na + ni; ++m) {
             const uint64_t d = 2 + 5 * (uint64_t)m;
-            const double Gs = span_map(r.G_min, r.G_max, unit_double(ms.draw(s, d)));
-            const double ks = span_map(r.k_min, r.k_max, unit_double(ms.draw(s, d + 1)));
+            const double Gs = dist_draw(r.dist_G, r.G_min, r.G_max, ms.draw(s, d));
+            const double ks = dist_draw(r.dist_k, r.k_min, r.k_max, ms.draw(s, d + 1));
             const double T = span_map(r.thr_lo, r.thr_hi, unit_double(ms.draw(s, d + 2))) * M0;
-            const double ul = unit_double(ms.draw(s, d + 3));
+            const uint64_t xl = ms.draw(s, d + 3);
             const int n = unit_int(ms.draw(s, d + 4), r.n_min, r.n_max - r.n_min + 1);
             const bool act = m < na;
-            const double lam = act ? span_map(r.lam_act_min, r.lam_act_max, ul) : 1.0 / span_map(v_lo, v_hi, ul);
+            const double lam = act ? dist_draw(r.dist_lam_act, r.lam_act_min, r.lam_act_max, xl) : lam_inh_draw(r, xl);
             level = level * hill_factor(act, Gs / ks, T, (double)n, lam);
         }
         out[(size_t)s] = level;
@@ -630,6 +652,9 @@ grins_status check_ranges(const grins_racipe_ranges &r)
         return fail(GRINS_E_INVALID_ARG, "ranges: median_samples outside [1, 1e7]");
     if (r.median_mode != GRINS_MEDIAN_PER_INDEGREE && r.median_mode != GRINS_MEDIAN_UNREGULATED)
         return fail(GRINS_E_INVALID_ARG, "ranges: unknown median_mode %d", r.median_mode);
+    for (int d : {r.dist_G, r.dist_k, r.dist_lam_act, r.dist_lam_inh})
+        if (d < GRINS_DIST_TABLE1 || d > GRINS_DIST_LOGNORMAL)
+            return fail(GRINS_E_INVALID_ARG, "ranges: unknown distribution %d", d);
     return GRINS_OK;
 }
 
@@ -735,6 +760,9 @@ extern "C" grins_status grins_racipe_sample_params(grins_racipe_t h, const grins
     a.vi_span = 1.0 / rr.lam_inh_min - 1.0 / rr.lam_inh_max;
     a.thr_lo = rr.thr_lo; a.thr_span = rr.thr_hi - rr.thr_lo;
     a.n_min = rr.n_min; a.n_count = rr.n_max - rr.n_min + 1;
+    a.dist_G = rr.dist_G; a.dist_k = rr.dist_k; a.dist_la = rr.dist_lam_act; a.dist_li = rr.dist_lam_inh;
+    a.G_hi = rr.G_max; a.k_hi = rr.k_max; a.la_hi = rr.lam_act_max;
+    a.li_min = rr.lam_inh_min; a.li_max = rr.lam_inh_max;
     a.params = static_cast<unsigned char *>(d_params);
     CUDA_TRY(launch_sample_params(a, st), "sample_params: launch");
     if (d_ic_unit && n_ics > 0) CUDA_TRY(launch_sample_ics(h->N, seed, n_ics, d_ic_unit, st), "sample_params: IC launch");

@@ -60,6 +60,9 @@ struct SampleArgs {
     double vi_min, vi_span;      // inverse inhibiting lambda
     double thr_lo, thr_span;
     int32_t n_min, n_count;
+    int32_t dist_G, dist_k, dist_la, dist_li;   // GRINS_DIST_* per class
+    double G_hi, k_hi, la_hi;                   // range ends (non-Table-1 draws)
+    double li_min, li_max;                      // inhibiting lambda range (non-Table-1 draws)
     unsigned char *params;
 };
 

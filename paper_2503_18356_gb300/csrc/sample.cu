@@ -18,6 +18,32 @@ __device__ __forceinline__ double affine_rn(double lo, double span, double u)
     return __dadd_rn(lo, __dmul_rn(span, u));
 }
 
+// A continuous parameter over [lo, hi] under a GRINS_DIST_* other than
+// Table 1's: log-uniform, or normal / log-normal around the range's middle
+// with a sixth of the range as standard deviation, clamped (Box-Muller on
+// the draw's two 32-bit halves).  The steps are those of the host's draw;
+// the log, exp and cos of the device agree with the host's to a few ulp.
+__device__ double dist_draw(int dist, double lo, double hi, uint64_t r)
+{
+    if (dist == GRINS_DIST_LOGUNIFORM) {
+        const double a = log(lo), b = log(hi);
+        return exp(affine_rn(a, __dsub_rn(b, a), unit_double(r)));
+    }
+    const double uh = __dmul_rn(__dadd_rn((double)(r >> 32), 0.5), 0x1.0p-32);
+    const double ul = __dmul_rn(__dadd_rn((double)(r & 0xffffffffull), 0.5), 0x1.0p-32);
+    const double z = __dmul_rn(__dsqrt_rn(__dmul_rn(-2.0, log(uh))), cos(__dmul_rn(6.283185307179586, ul)));
+    if (dist == GRINS_DIST_NORMAL) {
+        const double x = __dadd_rn(__ddiv_rn(__dadd_rn(lo, hi), 2.0), __dmul_rn(z, __ddiv_rn(__dsub_rn(hi, lo), 6.0)));
+        return fmin(hi, fmax(lo, x));
+    }
+    const double a = log(lo), b = log(hi);
+    const double x = exp(__dadd_rn(__ddiv_rn(__dadd_rn(a, b), 2.0), __dmul_rn(z, __ddiv_rn(__dsub_rn(b, a), 6.0))));
+    return fmin(hi, fmax(lo, x));
+}
+
+// OTHER: some class uses a distribution besides Table 1's (a separate
+// instantiation, so that the Table 1 kernel carries no log, exp or cos).
+template <bool OTHER>
 __global__ void sample_params_kernel(SampleArgs a)
 {
     const int N = a.L.N, E = a.L.E;
@@ -42,9 +68,11 @@ __global__ void sample_params_kernel(SampleArgs a)
             if (d >= n_draws) break;
             const uint64_t x = r.v[w];
             if (d < N) {
-                G[d] = affine_rn(a.G_min, a.G_span, unit_double(x));
+                G[d] = OTHER && a.dist_G ? dist_draw(a.dist_G, a.G_min, a.G_hi, x)
+                                         : affine_rn(a.G_min, a.G_span, unit_double(x));
             } else if (d < 2 * N) {
-                k[d - N] = affine_rn(a.k_min, a.k_span, unit_double(x));
+                k[d - N] = OTHER && a.dist_k ? dist_draw(a.dist_k, a.k_min, a.k_hi, x)
+                                             : affine_rn(a.k_min, a.k_span, unit_double(x));
             } else if (d < 2 * N + E) {
                 const int e = d - 2 * N;
                 T[e] = __dmul_rn(affine_rn(a.thr_lo, a.thr_span, unit_double(x)), a.edge_median[e]);
@@ -52,8 +80,10 @@ __global__ void sample_params_kernel(SampleArgs a)
                 const int e = d - 2 * N - E;
                 const double u = unit_double(x);
                 const bool act = a.edge_sign[e] > 0;
-                lam[e] = act ? affine_rn(a.la_min, a.la_span, u)
-                             : __ddiv_rn(1.0, affine_rn(a.vi_min, a.vi_span, u));
+                if (act) lam[e] = OTHER && a.dist_la ? dist_draw(a.dist_la, a.la_min, a.la_hi, x)
+                                                     : affine_rn(a.la_min, a.la_span, u);
+                else lam[e] = OTHER && a.dist_li ? dist_draw(a.dist_li, a.li_min, a.li_max, x)
+                                                 : __ddiv_rn(1.0, affine_rn(a.vi_min, a.vi_span, u));
             } else {
                 const int e = d - 2 * N - 2 * E;
                 nn[e] = (uint8_t)unit_int(x, a.n_min, a.n_count);
@@ -98,7 +128,10 @@ cudaError_t launch_sample_params(const SampleArgs &a, cudaStream_t st)
     if (a.n_sets <= 0) return cudaSuccess;
     const int n_draws = 2 * a.L.N + 3 * a.L.E;
     const int64_t work = a.n_sets * ((n_draws + 3) / 4);
-    sample_params_kernel<<<grid_for(work, 256), 256, 0, st>>>(a);
+    if (a.dist_G || a.dist_k || a.dist_la || a.dist_li)
+        sample_params_kernel<true><<<grid_for(work, 256), 256, 0, st>>>(a);
+    else
+        sample_params_kernel<false><<<grid_for(work, 256), 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -63,6 +63,25 @@ def test_sampler_unregulated_mode_and_custom_ranges():
         assert np.array_equal(getattr(p, name), getattr(ref, name)), name
 
 
+@pytest.mark.parametrize("dists", [(1, 1, 1, 1), (2, 2, 2, 2), (3, 3, 3, 3), (1, 2, 3, 0)])
+def test_sampler_other_distributions(dists):
+    """The samplers besides Table 1's: Hill coefficients and thresholds
+    (whose medians the host computes with the same distributions) stay
+    bit-exact; G, k and lambda, through the device's log, exp and cos,
+    agree with the oracle's to a few ulp."""
+    from paper_2503_18356_gb300 import api
+    w = W.net22_workload()
+    topo = w["topology"]
+    h = PT.gpu_handle(topo)
+    kw = dict(dist_G=dists[0], dist_k=dists[1], dist_lam_act=dists[2], dist_lam_inh=dists[3])
+    _, _, p, _ = PT.gpu_sample(h, 21, 64, 2, ranges=api.default_ranges(**kw))
+    ref = O.sample_params(O.Network(*topo.edges()), 21, 64, ranges=O.default_ranges(**kw))
+    assert np.array_equal(p.n, ref.n) and np.array_equal(p.T, ref.T)
+    for name, span in (("G", 99.0), ("k", 0.9), ("lam", 100.0)):
+        a, b = getattr(p, name), getattr(ref, name)
+        assert np.all(np.abs(a - b) <= 1e-14 * (np.abs(b) + span)), name
+
+
 # ----------------------------------------------------------------- dedupe
 def test_unique_states_bit_exact_on_given_states():
     topo = W.random_network(3, 4, 8, 4, 0)
