@@ -276,14 +276,16 @@ def ising_measurement(h, stream, N, n_traj=1_000_000, reps=3):
 
 def sampler_measurement(h, stream, S, reps=3):
     """The parameter sampler of the workload under each distribution of
-    every continuous class (Table 1, log-uniform, normal, log-normal):
-    CUDA-event time of one call for all S sets (the medians are cached)."""
+    every continuous class (Table 1, log-uniform, normal, log-normal) and
+    under a Latin hypercube over the S sets (Table 1 classes): CUDA-event
+    time of one call for all S sets (the medians are cached)."""
     import numpy as np
     import torch
     from paper_2503_18356_gb300 import api
     res = {}
-    for name, d in (("table1", 0), ("loguniform", 1), ("normal", 2), ("lognormal", 3)):
-        r = api.default_ranges(dist_G=d, dist_k=d, dist_lam_act=d, dist_lam_inh=d)
+    for name, d, lhs in (("table1", 0, 0), ("loguniform", 1, 0), ("normal", 2, 0), ("lognormal", 3, 0),
+                         ("lhs_table1", 0, S)):
+        r = api.default_ranges(dist_G=d, dist_k=d, dist_lam_act=d, dist_lam_inh=d, lhs_sets=lhs)
         params, _ = h.sample_params(2000, S, 1, ranges=r, stream=stream)       # medians, warm-up
         ts = []
         for _ in range(reps):
@@ -520,6 +522,7 @@ def run_native(args):
     kern_ms = per_kernel.mean(axis=0)
     # the timed step's step attempts and statuses, before later legs reuse the buffers
     attempts = int(out["n_steps"].sum().item())
+    kernel_desc = h.integrator()          # the timed step's kernels, before the Tsit5 leg
     status = out["status"].cpu().numpy()
     levels = levels_measurement(h, params, out, stream, dev, S, I) if rank == 0 else None
     tsit5 = tsit5_measurement(h, params, ic, out, stream, S, I) if rank == 0 else None
@@ -618,7 +621,7 @@ def run_native(args):
             status_hist=np.bincount(status.ravel(), minlength=5).tolist(),
             roofline=dict(bound="alu", achieved=achieved, peak=peak, unit=unit, frac=achieved / peak,
                           traffic=(INTEGRATOR_DRAM_BYTES_PER_SOLVE * S * I
-                                   if INTEGRATOR_DRAM_BYTES_PER_SOLVE else None), kernel=h.integrator(),
+                                   if INTEGRATOR_DRAM_BYTES_PER_SOLVE else None), kernel=kernel_desc,
                           peak_basis="%d SMs x %s lanes/clk x %.0f MHz (median SM clock sampled in the "
                                      "timed region); reciprocal rate measured at 16/clk/SM on this GPU"
                                      % (sms, "16 SFU" if sfu_bound else "128 FP32", f_mhz),

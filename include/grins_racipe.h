@@ -101,6 +101,19 @@ typedef struct {
     int32_t dist_G, dist_k;            /* GRINS_DIST_* of G, k */
     int32_t dist_lam_act, dist_lam_inh;/* and of the two fold changes (the
                                           half-functional medians use them too) */
+    int64_t lhs_sets;                  /* > 0: Latin hypercube over sets
+                                          [0, lhs_sets) -- draw d of set s
+                                          takes the unit (pi_d(s) + u) / lhs_sets,
+                                          u its own draw, pi_d a permutation of
+                                          the sets per draw index (a 4-round
+                                          Feistel network on 2h bits, 2^(2h) >=
+                                          lhs_sets, round function word 0 of
+                                          Philox4x64-10 with counter (d, round,
+                                          right half, 0) and key (seed,
+                                          0x5241434950454C), cycle-walked into
+                                          range); Hill coefficients n_min +
+                                          floor(unit n_count); Table 1 and
+                                          log-uniform classes only; 0 = off */
 } grins_racipe_ranges;
 
 /* Solver controls (Sec. 2.1.3: tolerances, start and end time, stop at

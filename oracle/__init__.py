@@ -60,7 +60,8 @@ class Ranges(C.Structure):
                 ("thr_lo", C.c_double), ("thr_hi", C.c_double),
                 ("median_samples", C.c_int32), ("median_mode", C.c_int32),
                 ("dist_G", C.c_int32), ("dist_k", C.c_int32),
-                ("dist_lam_act", C.c_int32), ("dist_lam_inh", C.c_int32)]
+                ("dist_lam_act", C.c_int32), ("dist_lam_inh", C.c_int32),
+                ("lhs_sets", C.c_int64)]
 
 
 class Net(C.Structure):
@@ -111,6 +112,7 @@ def lib():
             l.orc_sample_params.argtypes = [P(Net), P(Ranges), C.c_uint64, C.c_int64, C.c_int64,
                                             P(C.c_double), P(C.c_double), P(C.c_double),
                                             P(C.c_double), P(C.c_int32)]
+            l.orc_lhs_stratum.argtypes = [C.c_uint64] * 4; l.orc_lhs_stratum.restype = C.c_uint64
             l.orc_sample_ics.argtypes = [C.c_int32, C.c_uint64, C.c_int32, P(C.c_double)]
             l.orc_solve.argtypes = [P(Net), P(Params), P(C.c_double), P(Opts), P(C.c_double),
                                     P(C.c_double)]
@@ -254,6 +256,12 @@ def sample_params(net: Network, seed, n_sets, set0=0, ranges=None) -> ParamSet:
                             _p(G, C.c_double), _p(k, C.c_double), _p(T, C.c_double),
                             _p(lam, C.c_double), _p(n, C.c_int32))
     return ParamSet(G, k, T, lam, n)
+
+
+def lhs_stratum(seed, d, s, S):
+    """The Latin-hypercube stratum of draw d of set s among S sets: a keyed
+    permutation of [0, S) in s (Feistel network with cycle walking)."""
+    return int(lib().orc_lhs_stratum(C.c_uint64(seed), C.c_uint64(d), C.c_uint64(s), C.c_uint64(S)))
 
 
 def sample_ics(n_nodes, seed, n_ics):

@@ -22,6 +22,13 @@
  *     times (Sec. 2.1.3, time series).
  *   - Newton polish of a converged state (steady state = Eq. 1 equal to 0).
  *   - Per-parameter-set steady-state dedupe (Sec. 3.1, multistability).
+ *   - Tsitouras 5(4) (Tsitouras 2011), the paper's own integrator, as the
+ *     second tableau of the same stepper.
+ *   - Levels of G/k-normalised expression, level labels and the
+ *     multistability histogram (Sec. 2.1.3, Sec. 3.1).
+ *   - The Boolean Ising formalism, synchronous and asynchronous (Eq. 3).
+ *   - Log-uniform, normal and log-normal parameter distributions and the
+ *     Latin-hypercube stratification (the samplers of Sec. 2.1.2).
  *
  * Parity status: every function here is pinned by a CPU test against
  * closed forms, library routines (numpy Philox, scipy DOP853, scipy
@@ -110,6 +117,7 @@ typedef struct {
     int32_t median_samples;        /* samples per median estimate */
     int32_t median_mode;           /* 0 = per in-degree class, 1 = unregulated */
     int32_t dist_G, dist_k, dist_lam_act, dist_lam_inh;   /* distribution per class, below */
+    int64_t lhs_sets;              /* > 0: Latin hypercube over this many sets (below) */
 } orc_ranges;
 
 void orc_default_ranges(orc_ranges *r)
@@ -123,6 +131,7 @@ void orc_default_ranges(orc_ranges *r)
     r->median_samples = 10000;
     r->median_mode = 0;
     r->dist_G = r->dist_k = r->dist_lam_act = r->dist_lam_inh = 0;
+    r->lhs_sets = 0;
 }
 
 /* Affine map of a unit draw onto [lo, hi]: lo + (hi - lo) * u. */
@@ -135,9 +144,9 @@ static double affine(double lo, double hi, double u) { return lo + (hi - lo) * u
 /* same in log space, then exp.  The normal deviate is Box-Muller on the    */
 /* draw's two 32-bit halves h, l: u = (h + 1/2) 2^-32, v = (l + 1/2) 2^-32, */
 /* z = sqrt(-2 log u) cos(2 pi v).                                          */
-static double param_draw(int32_t dist, double lo, double hi, uint64_t x)
+static double param_draw_u(int32_t dist, double lo, double hi, double uu, uint64_t x)
 {
-    if (dist == 1) return exp(affine(log(lo), log(hi), orc_u01(x)));
+    if (dist == 1) return exp(affine(log(lo), log(hi), uu));
     if (dist == 2 || dist == 3) {
         double u = ((double)(x >> 32) + 0.5) * 0x1.0p-32;
         double v = ((double)(x & 0xffffffffULL) + 0.5) * 0x1.0p-32;
@@ -151,25 +160,70 @@ static double param_draw(int32_t dist, double lo, double hi, uint64_t x)
         }
         return y < lo ? lo : (y > hi ? hi : y);
     }
-    return affine(lo, hi, orc_u01(x));
+    return affine(lo, hi, uu);
+}
+
+static double param_draw(int32_t dist, double lo, double hi, uint64_t x)
+{
+    return param_draw_u(dist, lo, hi, orc_u01(x), x);
 }
 
 /* Activating fold change: uniform on [lam_act_min, lam_act_max] (Table 1),
- * or the class's distribution. */
-static double lam_activating(const orc_ranges *r, uint64_t x)
+ * or the class's distribution; uu is the draw's unit. */
+static double lam_activating_u(const orc_ranges *r, double uu, uint64_t x)
 {
-    return param_draw(r->dist_lam_act, r->lam_act_min, r->lam_act_max, x);
+    return param_draw_u(r->dist_lam_act, r->lam_act_min, r->lam_act_max, uu, x);
 }
 
 /* Inhibiting fold change, Sec. 2.1.2: drawn uniformly in the inverse range
  * [1/max, 1/min] and then inverted (Table 1), or the class's distribution
  * over [lam_inh_min, lam_inh_max]. */
-static double lam_inhibiting(const orc_ranges *r, uint64_t x)
+static double lam_inhibiting_u(const orc_ranges *r, double uu, uint64_t x)
 {
-    if (r->dist_lam_inh != 0) return param_draw(r->dist_lam_inh, r->lam_inh_min, r->lam_inh_max, x);
+    if (r->dist_lam_inh != 0) return param_draw_u(r->dist_lam_inh, r->lam_inh_min, r->lam_inh_max, uu, x);
     double v_lo = 1.0 / r->lam_inh_max;
     double v_hi = 1.0 / r->lam_inh_min;
-    return 1.0 / affine(v_lo, v_hi, orc_u01(x));
+    return 1.0 / affine(v_lo, v_hi, uu);
+}
+
+static double lam_activating(const orc_ranges *r, uint64_t x) { return lam_activating_u(r, orc_u01(x), x); }
+static double lam_inhibiting(const orc_ranges *r, uint64_t x) { return lam_inhibiting_u(r, orc_u01(x), x); }
+
+/* Latin hypercube (Sec. 2.1.2, the paper's other samplers): with       */
+/* lhs_sets = S > 0, draw d of set s < S takes the unit (p + u) / S,    */
+/* u its own draw and p = pi_d(s), pi_d a keyed permutation of [0, S):  */
+/* a balanced 4-round Feistel network on 2h bits (h = ceil(b / 2), b    */
+/* the bits of S - 1, at least 2), round function word 0 of             */
+/* Philox4x64-10 at counter (d, round, right half, 0) with key (seed,   */
+/* ORC_TAG_LHS) masked to h bits, applied again while the result is     */
+/* not below S (cycle walking, Black and Rogaway 2002).                 */
+#define ORC_TAG_LHS 0x5241434950454CULL    /* "RACIPEL" */
+
+uint64_t orc_lhs_stratum(uint64_t seed, uint64_t d, uint64_t s, uint64_t S)
+{
+    int b = 2;
+    while (b < 62 && (1ULL << b) < S) ++b;
+    int h = (b + 1) / 2;
+    uint64_t hm = (1ULL << h) - 1ULL, x = s;
+    do {
+        uint64_t L = x >> h, R = x & hm;
+        for (uint64_t rd = 0; rd < 4; ++rd) {
+            uint64_t ctr[4] = { d, rd, R, 0 }, key[2] = { seed, ORC_TAG_LHS }, out[4];
+            orc_philox4x64_10(ctr, key, out);
+            uint64_t nR = L ^ (out[0] & hm);
+            L = R;
+            R = nR;
+        }
+        x = (L << h) | R;
+    } while (x >= S);
+    return x;
+}
+
+/* The unit of draw d of set s: u01 of its draw, or the stratified one. */
+static double unit_of(const orc_ranges *r, uint64_t seed, uint64_t d, uint64_t s, uint64_t x)
+{
+    if (r->lhs_sets <= 0) return orc_u01(x);
+    return ((double)orc_lhs_stratum(seed, d, s, (uint64_t)r->lhs_sets) + orc_u01(x)) / (double)r->lhs_sets;
 }
 
 /* ------------------------------------------------------------------ */
@@ -338,16 +392,26 @@ void orc_sample_params(const orc_net *net, const orc_ranges *r, uint64_t seed,
         double *Gs = G + s * N, *ks = k + s * N, *Ts = T + s * E, *ls = lam + s * E;
         int32_t *ns = n + s * E;
         for (int i = 0; i < N; ++i) {
-            Gs[i] = param_draw(r->dist_G, r->G_min, r->G_max, draw64(seed, ORC_TAG_PARAMS, c0, (uint64_t)i));
-            ks[i] = param_draw(r->dist_k, r->k_min, r->k_max, draw64(seed, ORC_TAG_PARAMS, c0, (uint64_t)(N + i)));
+            uint64_t xg = draw64(seed, ORC_TAG_PARAMS, c0, (uint64_t)i);
+            uint64_t xk = draw64(seed, ORC_TAG_PARAMS, c0, (uint64_t)(N + i));
+            Gs[i] = param_draw_u(r->dist_G, r->G_min, r->G_max, unit_of(r, seed, (uint64_t)i, c0, xg), xg);
+            ks[i] = param_draw_u(r->dist_k, r->k_min, r->k_max, unit_of(r, seed, (uint64_t)(N + i), c0, xk), xk);
         }
         for (int e = 0; e < E; ++e) {
-            double ut = orc_u01(draw64(seed, ORC_TAG_PARAMS, c0, (uint64_t)(2 * N + e)));
-            uint64_t xl = draw64(seed, ORC_TAG_PARAMS, c0, (uint64_t)(2 * N + E + e));
-            uint64_t rn = draw64(seed, ORC_TAG_PARAMS, c0, (uint64_t)(2 * N + 2 * E + e));
-            Ts[e] = affine(r->thr_lo, r->thr_hi, ut) * Msrc[net->src[e]];
-            ls[e] = net->sign[e] > 0 ? lam_activating(r, xl) : lam_inhibiting(r, xl);
-            ns[e] = orc_uint_range(rn, r->n_min, r->n_max);
+            uint64_t dt = (uint64_t)(2 * N + e), dl = (uint64_t)(2 * N + E + e), dn = (uint64_t)(2 * N + 2 * E + e);
+            uint64_t xt = draw64(seed, ORC_TAG_PARAMS, c0, dt);
+            uint64_t xl = draw64(seed, ORC_TAG_PARAMS, c0, dl);
+            uint64_t rn = draw64(seed, ORC_TAG_PARAMS, c0, dn);
+            double ul = unit_of(r, seed, dl, c0, xl);
+            Ts[e] = affine(r->thr_lo, r->thr_hi, unit_of(r, seed, dt, c0, xt)) * Msrc[net->src[e]];
+            ls[e] = net->sign[e] > 0 ? lam_activating_u(r, ul, xl) : lam_inhibiting_u(r, ul, xl);
+            if (r->lhs_sets > 0) {
+                int cnt = r->n_max - r->n_min + 1;
+                int m = (int)(unit_of(r, seed, dn, c0, rn) * (double)cnt);
+                ns[e] = r->n_min + (m < cnt ? m : cnt - 1);
+            } else {
+                ns[e] = orc_uint_range(rn, r->n_min, r->n_max);
+            }
         }
     }
     free(Msrc);

@@ -47,7 +47,8 @@ class grins_racipe_ranges(C.Structure):
                 ("thr_lo", C.c_double), ("thr_hi", C.c_double),
                 ("median_samples", C.c_int32), ("median_mode", C.c_int32),
                 ("dist_G", C.c_int32), ("dist_k", C.c_int32),
-                ("dist_lam_act", C.c_int32), ("dist_lam_inh", C.c_int32)]
+                ("dist_lam_act", C.c_int32), ("dist_lam_inh", C.c_int32),
+                ("lhs_sets", C.c_int64)]
 
 
 class grins_solver_opts(C.Structure):

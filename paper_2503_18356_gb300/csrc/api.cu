@@ -120,6 +120,7 @@ extern "C" void grins_racipe_default_ranges(grins_racipe_ranges *r)
     r->median_samples = 10000;
     r->median_mode = GRINS_MEDIAN_PER_INDEGREE;
     r->dist_G = r->dist_k = r->dist_lam_act = r->dist_lam_inh = GRINS_DIST_TABLE1;
+    r->lhs_sets = 0;
 }
 
 extern "C" void grins_solver_default_opts(grins_solver_opts *o)
@@ -652,9 +653,13 @@ grins_status check_ranges(const grins_racipe_ranges &r)
         return fail(GRINS_E_INVALID_ARG, "ranges: median_samples outside [1, 1e7]");
     if (r.median_mode != GRINS_MEDIAN_PER_INDEGREE && r.median_mode != GRINS_MEDIAN_UNREGULATED)
         return fail(GRINS_E_INVALID_ARG, "ranges: unknown median_mode %d", r.median_mode);
-    for (int d : {r.dist_G, r.dist_k, r.dist_lam_act, r.dist_lam_inh})
+    for (int d : {r.dist_G, r.dist_k, r.dist_lam_act, r.dist_lam_inh}) {
         if (d < GRINS_DIST_TABLE1 || d > GRINS_DIST_LOGNORMAL)
             return fail(GRINS_E_INVALID_ARG, "ranges: unknown distribution %d", d);
+        if (r.lhs_sets > 0 && d > GRINS_DIST_LOGUNIFORM)
+            return fail(GRINS_E_INVALID_ARG, "ranges: the Latin hypercube takes Table 1 and log-uniform draws only");
+    }
+    if (r.lhs_sets < 0) return fail(GRINS_E_INVALID_ARG, "ranges: lhs_sets < 0");
     return GRINS_OK;
 }
 
@@ -762,6 +767,10 @@ extern "C" grins_status grins_racipe_sample_params(grins_racipe_t h, const grins
     a.n_min = rr.n_min; a.n_count = rr.n_max - rr.n_min + 1;
     a.dist_G = rr.dist_G; a.dist_k = rr.dist_k; a.dist_la = rr.dist_lam_act; a.dist_li = rr.dist_lam_inh;
     a.G_hi = rr.G_max; a.k_hi = rr.k_max; a.la_hi = rr.lam_act_max;
+    a.lhs_sets = rr.lhs_sets;
+    if (rr.lhs_sets > 0 && set0 + n_sets > rr.lhs_sets)
+        return fail(GRINS_E_INVALID_ARG, "sample_params: sets [%lld, %lld) outside the Latin hypercube's %lld",
+                    (long long)set0, (long long)(set0 + n_sets), (long long)rr.lhs_sets);
     a.li_min = rr.lam_inh_min; a.li_max = rr.lam_inh_max;
     a.params = static_cast<unsigned char *>(d_params);
     CUDA_TRY(launch_sample_params(a, st), "sample_params: launch");

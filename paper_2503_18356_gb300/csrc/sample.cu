@@ -21,13 +21,15 @@ __device__ __forceinline__ double affine_rn(double lo, double span, double u)
 // A continuous parameter over [lo, hi] under a GRINS_DIST_* other than
 // Table 1's: log-uniform, or normal / log-normal around the range's middle
 // with a sixth of the range as standard deviation, clamped (Box-Muller on
-// the draw's two 32-bit halves).  The steps are those of the host's draw;
-// the log, exp and cos of the device agree with the host's to a few ulp.
-__device__ double dist_draw(int dist, double lo, double hi, uint64_t r)
+// the draw's two 32-bit halves).  u is the draw's unit (stratified under a
+// Latin hypercube), r the raw draw.  The steps are those of the host's
+// draw; the log, exp and cos of the device agree with the host's to a few
+// ulp.
+__device__ double dist_draw(int dist, double lo, double hi, double u, uint64_t r)
 {
     if (dist == GRINS_DIST_LOGUNIFORM) {
         const double a = log(lo), b = log(hi);
-        return exp(affine_rn(a, __dsub_rn(b, a), unit_double(r)));
+        return exp(affine_rn(a, __dsub_rn(b, a), u));
     }
     const double uh = __dmul_rn(__dadd_rn((double)(r >> 32), 0.5), 0x1.0p-32);
     const double ul = __dmul_rn(__dadd_rn((double)(r & 0xffffffffull), 0.5), 0x1.0p-32);
@@ -39,6 +41,39 @@ __device__ double dist_draw(int dist, double lo, double hi, uint64_t r)
     const double a = log(lo), b = log(hi);
     const double x = exp(__dadd_rn(__ddiv_rn(__dadd_rn(a, b), 2.0), __dmul_rn(z, __ddiv_rn(__dsub_rn(b, a), 6.0))));
     return fmin(hi, fmax(lo, x));
+}
+
+// Latin hypercube stratum of set s (< S) for draw index d: a keyed
+// permutation of [0, S) -- a 4-round Feistel network on 2h bits (2^(2h) >=
+// S) whose round function is word 0 of Philox4x64-10 at counter (d, round,
+// right half, 0), key (seed, kTagLhs), walked until it lands below S.
+__device__ uint64_t lhs_stratum(uint64_t seed, uint64_t d, uint64_t s, uint64_t S)
+{
+    int nb = 2;
+    while (nb < 62 && (1ull << nb) < S) ++nb;
+    const int h = (nb + 1) / 2;
+    const uint64_t hm = (1ull << h) - 1ull;
+    uint64_t x = s;
+    do {
+        uint64_t L = x >> h, R = x & hm;
+        for (uint64_t rd = 0; rd < 4; ++rd) {
+            const uint64_t F = philox4x64_10(d, rd, R, 0, seed, kTagLhs).v[0] & hm;
+            const uint64_t t = L ^ F;
+            L = R;
+            R = t;
+        }
+        x = (L << h) | R;
+    } while (x >= S);
+    return x;
+}
+
+// The unit of draw d of set s: its own draw, or under a Latin hypercube
+// (stratum + draw) / S.
+__device__ __forceinline__ double draw_unit(const SampleArgs &a, uint64_t d, uint64_t s, uint64_t x)
+{
+    if (a.lhs_sets <= 0) return unit_double(x);
+    const uint64_t p = lhs_stratum(a.seed, d, s, (uint64_t)a.lhs_sets);
+    return __ddiv_rn(__dadd_rn((double)p, unit_double(x)), (double)a.lhs_sets);
 }
 
 // OTHER: some class uses a distribution besides Table 1's (a separate
@@ -67,26 +102,30 @@ __global__ void sample_params_kernel(SampleArgs a)
             const int d = 4 * c + w;
             if (d >= n_draws) break;
             const uint64_t x = r.v[w];
+            const double u = OTHER ? draw_unit(a, (uint64_t)d, s, x) : unit_double(x);
             if (d < N) {
-                G[d] = OTHER && a.dist_G ? dist_draw(a.dist_G, a.G_min, a.G_hi, x)
-                                         : affine_rn(a.G_min, a.G_span, unit_double(x));
+                G[d] = OTHER && a.dist_G ? dist_draw(a.dist_G, a.G_min, a.G_hi, u, x) : affine_rn(a.G_min, a.G_span, u);
             } else if (d < 2 * N) {
-                k[d - N] = OTHER && a.dist_k ? dist_draw(a.dist_k, a.k_min, a.k_hi, x)
-                                             : affine_rn(a.k_min, a.k_span, unit_double(x));
+                k[d - N] = OTHER && a.dist_k ? dist_draw(a.dist_k, a.k_min, a.k_hi, u, x)
+                                             : affine_rn(a.k_min, a.k_span, u);
             } else if (d < 2 * N + E) {
                 const int e = d - 2 * N;
-                T[e] = __dmul_rn(affine_rn(a.thr_lo, a.thr_span, unit_double(x)), a.edge_median[e]);
+                T[e] = __dmul_rn(affine_rn(a.thr_lo, a.thr_span, u), a.edge_median[e]);
             } else if (d < 2 * N + 2 * E) {
                 const int e = d - 2 * N - E;
-                const double u = unit_double(x);
                 const bool act = a.edge_sign[e] > 0;
-                if (act) lam[e] = OTHER && a.dist_la ? dist_draw(a.dist_la, a.la_min, a.la_hi, x)
+                if (act) lam[e] = OTHER && a.dist_la ? dist_draw(a.dist_la, a.la_min, a.la_hi, u, x)
                                                      : affine_rn(a.la_min, a.la_span, u);
-                else lam[e] = OTHER && a.dist_li ? dist_draw(a.dist_li, a.li_min, a.li_max, x)
+                else lam[e] = OTHER && a.dist_li ? dist_draw(a.dist_li, a.li_min, a.li_max, u, x)
                                                  : __ddiv_rn(1.0, affine_rn(a.vi_min, a.vi_span, u));
             } else {
                 const int e = d - 2 * N - 2 * E;
-                nn[e] = (uint8_t)unit_int(x, a.n_min, a.n_count);
+                if (OTHER && a.lhs_sets > 0) {
+                    const int m = (int)__dmul_rn(u, (double)a.n_count);
+                    nn[e] = (uint8_t)(a.n_min + (m < a.n_count ? m : a.n_count - 1));
+                } else {
+                    nn[e] = (uint8_t)unit_int(x, a.n_min, a.n_count);
+                }
             }
         }
         // zero the tail padding once per set
@@ -128,7 +167,7 @@ cudaError_t launch_sample_params(const SampleArgs &a, cudaStream_t st)
     if (a.n_sets <= 0) return cudaSuccess;
     const int n_draws = 2 * a.L.N + 3 * a.L.E;
     const int64_t work = a.n_sets * ((n_draws + 3) / 4);
-    if (a.dist_G || a.dist_k || a.dist_la || a.dist_li)
+    if (a.dist_G || a.dist_k || a.dist_la || a.dist_li || a.lhs_sets > 0)
         sample_params_kernel<true><<<grid_for(work, 256), 256, 0, st>>>(a);
     else
         sample_params_kernel<false><<<grid_for(work, 256), 256, 0, st>>>(a);

@@ -82,6 +82,52 @@ def test_sampler_other_distributions(dists):
         assert np.all(np.abs(a - b) <= 1e-14 * (np.abs(b) + span)), name
 
 
+@pytest.mark.parametrize("dist_G", [0, 1])
+def test_sampler_latin_hypercube(dist_G):
+    """Latin-hypercube strata (a keyed Feistel permutation per draw) agree
+    with the oracle's: Table 1 classes bit-exact; log-uniform G through the
+    device's log and exp to a few ulp.  Sets are taken from the middle of
+    the hypercube (set0 > 0), with a ragged count."""
+    from paper_2503_18356_gb300 import api
+    w = W.net22_workload()
+    topo = w["topology"]
+    h = PT.gpu_handle(topo)
+    S, set0, n = 5000, 1234, 77
+    _, _, p, _ = PT.gpu_sample(h, 31, n, 2, set0=set0,
+                               ranges=api.default_ranges(lhs_sets=S, dist_G=dist_G))
+    ref = O.sample_params(O.Network(*topo.edges()), 31, n, set0=set0,
+                          ranges=O.default_ranges(lhs_sets=S, dist_G=dist_G))
+    for f in ("k", "T", "lam", "n"):
+        assert np.array_equal(getattr(p, f), getattr(ref, f)), f
+    if dist_G == 0:
+        assert np.array_equal(p.G, ref.G)
+    else:
+        assert np.all(np.abs(p.G - ref.G) <= 1e-14 * (np.abs(ref.G) + 99.0))
+
+
+def test_sampler_latin_hypercube_whole_and_refusals():
+    """All sets of a small hypercube in one call: one value per stratum in
+    every dimension, bit-exact with the oracle; the forms the sampler
+    refuses (normal classes under a hypercube, sets beyond it)."""
+    from paper_2503_18356_gb300 import api
+    topo = W.random_network(3, 4, 8, 4, 0)
+    h = PT.gpu_handle(topo)
+    S = 257
+    _, _, p, _ = PT.gpu_sample(h, 8, S, 1, ranges=api.default_ranges(lhs_sets=S))
+    ref = O.sample_params(O.Network(*topo.edges()), 8, S, ranges=O.default_ranges(lhs_sets=S))
+    for f in ("G", "k", "T", "lam", "n"):
+        assert np.array_equal(getattr(p, f), getattr(ref, f)), f
+    r = api.default_ranges()
+    z = np.sort(p.G, axis=0)
+    z = (z - r.G_min) / (r.G_max - r.G_min) * S
+    i = np.arange(S)[:, None]
+    assert np.all((z >= i - 1e-9) & (z <= i + 1 + 1e-9))
+    with pytest.raises(api.GrinsError):
+        h.sample_params(8, 4, 1, ranges=api.default_ranges(lhs_sets=S, dist_k=2))
+    with pytest.raises(api.GrinsError):
+        h.sample_params(8, 4, 1, set0=S - 2, ranges=api.default_ranges(lhs_sets=S))
+
+
 # ----------------------------------------------------------------- dedupe
 def test_unique_states_bit_exact_on_given_states():
     topo = W.random_network(3, 4, 8, 4, 0)

@@ -64,3 +64,99 @@ def test_box_muller_halves_are_independent_normals():
     zk = (p.k.ravel() - 0.55) / (0.9 / 6)
     assert abs(zg.mean()) < 0.03 and abs(zg.std() - 0.986) < 0.03
     assert abs(np.corrcoef(zg, zk)[0, 1]) < 0.03
+
+
+# ---------------------------------------------------------------- Latin hypercube
+@pytest.mark.parametrize("S", [1, 2, 3, 5, 17, 64, 100, 1000, 4097])
+def test_lhs_stratum_is_a_permutation(S):
+    # brute force: for each draw index the map s -> stratum is a bijection
+    # of [0, S), whatever S (power of two or not, cycle walking included)
+    for d in (0, 1, 7, 123456):
+        p = [O.lhs_stratum(2002, d, s, S) for s in range(S)]
+        assert sorted(p) == list(range(S)), (S, d)
+
+
+def test_lhs_strata_differ_between_draws_and_seeds():
+    S = 1000
+    a = np.array([O.lhs_stratum(1, 0, s, S) for s in range(S)])
+    b = np.array([O.lhs_stratum(1, 1, s, S) for s in range(S)])
+    c = np.array([O.lhs_stratum(2, 0, s, S) for s in range(S)])
+    assert not np.array_equal(a, np.arange(S))
+    # independent permutations: rank correlation within a few 1 / sqrt(S)
+    for x, y in ((a, b), (a, c)):
+        assert abs(np.corrcoef(x, y)[0, 1]) < 4 / np.sqrt(S)
+
+
+def lhs_draw(S, **dist):
+    r = O.default_ranges(median_samples=2000, lhs_sets=S, **dist)
+    return O.sample_params(NET, 11, S, ranges=r), r
+
+
+def order_in_strata(v, lo, hi, S):
+    """The i-th smallest of S values lies in the i-th of S equal strata of
+    [lo, hi]: one value per stratum, the Latin-hypercube property."""
+    z = (np.sort(v) - lo) / (hi - lo) * S
+    i = np.arange(S)
+    return np.all(z >= i - 1e-9) and np.all(z <= i + 1 + 1e-9)
+
+
+@pytest.mark.parametrize("S", [1, 7, 500])
+def test_lhs_one_value_per_stratum_in_every_dimension(S):
+    p, r = lhs_draw(S)
+    for i in range(NET.n_nodes):
+        assert order_in_strata(p.G[:, i], r.G_min, r.G_max, S)
+        assert order_in_strata(p.k[:, i], r.k_min, r.k_max, S)
+    for e in range(NET.n_edges):
+        if NET.sign[e] > 0:
+            assert order_in_strata(p.lam[:, e], r.lam_act_min, r.lam_act_max, S)
+        else:
+            # Table 1's inhibiting fold change is uniform in the inverse range
+            assert order_in_strata(1 / p.lam[:, e], 1 / r.lam_inh_max, 1 / r.lam_inh_min, S)
+
+
+def test_lhs_log_uniform_strata_and_hill_coefficients():
+    S = 600
+    p, r = lhs_draw(S, dist_G=1, dist_lam_act=1)
+    for i in range(NET.n_nodes):
+        assert order_in_strata(np.log(p.G[:, i]), np.log(r.G_min), np.log(r.G_max), S)
+    act = NET.sign > 0
+    for e in np.flatnonzero(act):
+        assert order_in_strata(np.log(p.lam[:, e]), np.log(r.lam_act_min), np.log(r.lam_act_max), S)
+    # n is stratified too: S divisible by the n_max - n_min + 1 values, so
+    # every value is taken exactly S / 6 times in every edge
+    cnt = r.n_max - r.n_min + 1
+    for e in range(NET.n_edges):
+        assert np.array_equal(np.bincount(p.n[:, e] - r.n_min, minlength=cnt), np.full(cnt, S // cnt))
+
+
+def test_lhs_thresholds_stratified_before_the_source_median_scale():
+    # T = u' M(source), u' over the threshold's range and M the median of
+    # the source's in-degree class, the same for every set: T / M is
+    # stratified
+    S = 300
+    p, r = lhs_draw(S)
+    for e in range(NET.n_edges):
+        j = NET.src[e]
+        a = int(np.sum((NET.dst == j) & (NET.sign > 0)))
+        b = int(np.sum((NET.dst == j) & (NET.sign < 0)))
+        assert order_in_strata(p.T[:, e] / O.median(a, b, r), r.thr_lo, r.thr_hi, S)
+
+
+def test_lhs_sets_split_across_calls_equal_one_call():
+    # counter-based: sets [0, S) drawn in two calls (set0 = 0 and S / 2)
+    # equal one call, the permutation depends on S, not on the call
+    S = 200
+    r = O.default_ranges(median_samples=2000, lhs_sets=S)
+    whole = O.sample_params(NET, 5, S, ranges=r)
+    a = O.sample_params(NET, 5, S // 2, set0=0, ranges=r)
+    b = O.sample_params(NET, 5, S // 2, set0=S // 2, ranges=r)
+    for f in ("G", "k", "T", "lam", "n"):
+        assert np.array_equal(getattr(whole, f), np.concatenate([getattr(a, f), getattr(b, f)])), f
+
+
+def test_lhs_off_is_the_plain_sampler():
+    r0 = O.default_ranges(median_samples=2000)
+    r1 = O.default_ranges(median_samples=2000, lhs_sets=0)
+    a, b = O.sample_params(NET, 3, 50, ranges=r0), O.sample_params(NET, 3, 50, ranges=r1)
+    for f in ("G", "k", "T", "lam", "n"):
+        assert np.array_equal(getattr(a, f), getattr(b, f))
