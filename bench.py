@@ -276,16 +276,20 @@ def ising_measurement(h, stream, N, n_traj=1_000_000, reps=3):
 
 def sampler_measurement(h, stream, S, reps=3):
     """The parameter sampler of the workload under each distribution of
-    every continuous class (Table 1, log-uniform, normal, log-normal) and
-    under a Latin hypercube over the S sets (Table 1 classes): CUDA-event
-    time of one call for all S sets (the medians are cached)."""
+    every continuous class (Table 1, log-uniform, normal, log-normal), under
+    a Latin hypercube over the S sets and as scrambled Sobol points (Table 1
+    classes): CUDA-event time of one call for all S sets (the medians are
+    cached; the Sobol call includes building and uploading its table)."""
     import numpy as np
     import torch
     from paper_2503_18356_gb300 import api
     res = {}
-    for name, d, lhs in (("table1", 0, 0), ("loguniform", 1, 0), ("normal", 2, 0), ("lognormal", 3, 0),
-                         ("lhs_table1", 0, S)):
-        r = api.default_ranges(dist_G=d, dist_k=d, dist_lam_act=d, dist_lam_inh=d, lhs_sets=lhs)
+    from paper_2503_18356_gb300 import workloads as W
+    tab = W.sobol_direction_table()
+    for name, d, lhs, sob in (("table1", 0, 0, 0), ("loguniform", 1, 0, 0), ("normal", 2, 0, 0),
+                              ("lognormal", 3, 0, 0), ("lhs_table1", 0, S, 0), ("sobol_scrambled", 0, 0, 2)):
+        r = api.default_ranges(dist_G=d, dist_k=d, dist_lam_act=d, dist_lam_inh=d, lhs_sets=lhs, sobol=sob,
+                               sobol_table=tab if sob else None)
         params, _ = h.sample_params(2000, S, 1, ranges=r, stream=stream)       # medians, warm-up
         ts = []
         for _ in range(reps):

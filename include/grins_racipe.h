@@ -114,7 +114,35 @@ typedef struct {
                                           range); Hill coefficients n_min +
                                           floor(unit n_count); Table 1 and
                                           log-uniform classes only; 0 = off */
+    int32_t sobol;                     /* GRINS_SOBOL_* (below); 0 = off */
+    int32_t sobol_dims;                /* rows of the two tables, >= 2N + 3E */
+    const int64_t *sobol_poly;         /* host [sobol_dims], read during the call */
+    const int64_t *sobol_m;            /* host [sobol_dims][sobol_m_cols] */
+    int32_t sobol_m_cols;
+    int32_t reserved;                  /* set to 0 (keeps the struct free of padding) */
 } grins_racipe_ranges;
+
+/* Sobol sets (Sec. 2.1.2: the paper's default sampler).  With sobol != 0,
+ * draw d (0 <= d < 2N + 3E, the order of the layout above) of set s takes
+ * the unit x 2^-32, x the 32-bit coordinate d of point s of the Sobol
+ * sequence in Gray-code order (Antonov and Saleev 1979): x = XOR of V_d[b]
+ * over the set bits b of s ^ (s >> 1), s < 2^32.  Direction numbers
+ * (Bratley and Fox 1988): V_d[b] = m_{b+1} 2^(31-b), with m_k = 1 for
+ * dimension 0 and, for d >= 1, sobol_m[d][k-1] for k <= s_d and
+ *   m_k = m_{k-s} ^ (m_{k-s} << s) ^ XOR_{i=1}^{s-1} a_i (m_{k-i} << i)
+ * beyond, where sobol_poly[d] holds the primitive polynomial
+ * x^s + a_1 x^(s-1) + ... + a_{s-1} x + 1 with bit j the coefficient of x^j
+ * (s its highest set bit, 1 <= s <= min(sobol_m_cols, 32), each given m_k
+ * odd and below 2^k).  The table of Joe and Kuo (2008) as scipy ships it has
+ * this form.  GRINS_SOBOL_SCRAMBLED adds a linear matrix scramble and a
+ * digital shift (Matousek 1998), drawn from Philox4x64-10 with key (seed,
+ * 0x52414349504553): digit j (1 = most significant, bit 32 - j) of the
+ * scrambled coordinate is the parity of x AND M_j, M_j bit 32 - j plus the
+ * bits above it taken from the low word of the draw at counter (d, j, 0, 0);
+ * the shift is the low word at counter (d, 0, 0, 0).  Hill coefficients take
+ * n_min + floor(unit n_count); Table 1 and log-uniform classes only; not
+ * with lhs_sets. */
+enum { GRINS_SOBOL_OFF = 0, GRINS_SOBOL_PLAIN = 1, GRINS_SOBOL_SCRAMBLED = 2 };
 
 /* Solver controls (Sec. 2.1.3: tolerances, start and end time, stop at
  * steady state, optional time points).  grins_solver_default_opts fills:

@@ -61,7 +61,10 @@ class Ranges(C.Structure):
                 ("median_samples", C.c_int32), ("median_mode", C.c_int32),
                 ("dist_G", C.c_int32), ("dist_k", C.c_int32),
                 ("dist_lam_act", C.c_int32), ("dist_lam_inh", C.c_int32),
-                ("lhs_sets", C.c_int64)]
+                ("lhs_sets", C.c_int64),
+                ("sobol", C.c_int32), ("sobol_dims", C.c_int32),
+                ("sobol_poly", C.POINTER(C.c_int64)), ("sobol_m", C.POINTER(C.c_int64)),
+                ("sobol_m_cols", C.c_int32)]
 
 
 class Net(C.Structure):
@@ -113,6 +116,8 @@ def lib():
                                             P(C.c_double), P(C.c_double), P(C.c_double),
                                             P(C.c_double), P(C.c_int32)]
             l.orc_lhs_stratum.argtypes = [C.c_uint64] * 4; l.orc_lhs_stratum.restype = C.c_uint64
+            l.orc_sobol_x.argtypes = [P(Ranges), C.c_uint64, C.c_uint64, C.c_uint64]
+            l.orc_sobol_x.restype = C.c_uint32
             l.orc_sample_ics.argtypes = [C.c_int32, C.c_uint64, C.c_int32, P(C.c_double)]
             l.orc_solve.argtypes = [P(Net), P(Params), P(C.c_double), P(Opts), P(C.c_double),
                                     P(C.c_double)]
@@ -157,11 +162,20 @@ def _f64(a):
 
 
 # ---------------------------------------------------------------- helpers
-def default_ranges(**over) -> Ranges:
+def default_ranges(sobol_table=None, **over) -> Ranges:
+    """Table 1's ranges with fields overridden; `sobol_table` = (poly, m)
+    int64 arrays for the Sobol modes (kept alive with the struct)."""
     r = Ranges()
     lib().orc_default_ranges(C.byref(r))
     for k, v in over.items():
         setattr(r, k, v)
+    if sobol_table is not None:
+        poly = np.ascontiguousarray(sobol_table[0], dtype=np.int64)
+        m = np.ascontiguousarray(sobol_table[1], dtype=np.int64)
+        r._keep = (poly, m)
+        r.sobol_dims, r.sobol_m_cols = int(poly.shape[0]), int(m.shape[1])
+        r.sobol_poly = _p(poly, C.c_int64)
+        r.sobol_m = _p(m, C.c_int64)
     return r
 
 
@@ -262,6 +276,12 @@ def lhs_stratum(seed, d, s, S):
     """The Latin-hypercube stratum of draw d of set s among S sets: a keyed
     permutation of [0, S) in s (Feistel network with cycle walking)."""
     return int(lib().orc_lhs_stratum(C.c_uint64(seed), C.c_uint64(d), C.c_uint64(s), C.c_uint64(S)))
+
+
+def sobol_x(ranges, seed, d, s):
+    """Coordinate d of Sobol point s (32-bit), plain or scrambled per
+    `ranges.sobol`."""
+    return int(lib().orc_sobol_x(C.byref(ranges), C.c_uint64(seed), C.c_uint64(d), C.c_uint64(s)))
 
 
 def sample_ics(n_nodes, seed, n_ics):

@@ -118,6 +118,11 @@ typedef struct {
     int32_t median_mode;           /* 0 = per in-degree class, 1 = unregulated */
     int32_t dist_G, dist_k, dist_lam_act, dist_lam_inh;   /* distribution per class, below */
     int64_t lhs_sets;              /* > 0: Latin hypercube over this many sets (below) */
+    int32_t sobol;                 /* 0 off, 1 Sobol points, 2 scrambled (below) */
+    int32_t sobol_dims;
+    const int64_t *sobol_poly;     /* [sobol_dims] primitive polynomials, bit j = coeff. of x^j */
+    const int64_t *sobol_m;        /* [sobol_dims][sobol_m_cols] initial m_1 .. m_s */
+    int32_t sobol_m_cols;
 } orc_ranges;
 
 void orc_default_ranges(orc_ranges *r)
@@ -132,6 +137,11 @@ void orc_default_ranges(orc_ranges *r)
     r->median_mode = 0;
     r->dist_G = r->dist_k = r->dist_lam_act = r->dist_lam_inh = 0;
     r->lhs_sets = 0;
+    r->sobol = 0;
+    r->sobol_dims = 0;
+    r->sobol_poly = NULL;
+    r->sobol_m = NULL;
+    r->sobol_m_cols = 0;
 }
 
 /* Affine map of a unit draw onto [lo, hi]: lo + (hi - lo) * u. */
@@ -219,9 +229,70 @@ uint64_t orc_lhs_stratum(uint64_t seed, uint64_t d, uint64_t s, uint64_t S)
     return x;
 }
 
-/* The unit of draw d of set s: u01 of its draw, or the stratified one. */
+/* Sobol sequence (Sec. 2.1.2, the paper's default sampler).  Coordinate */
+/* d of point s, as a 32-bit integer x (the unit is x 2^-32):           */
+/*  - direction integers (Bratley and Fox 1988): dimension 0 has m_k = 1; */
+/*    dimension d >= 1, with primitive polynomial                        */
+/*    x^s + a_1 x^(s-1) + ... + a_(s-1) x + 1, takes its given m_1..m_s    */
+/*    and m_k = m_(k-s) XOR 2^s m_(k-s) XOR sum_i 2^i a_i m_(k-i) beyond;  */
+/*    direction number b (0-based) is m_(b+1) 2^(31-b);                  */
+/*  - point s in Gray-code order (Antonov and Saleev 1979): the XOR of    */
+/*    the direction numbers of the set bits of s XOR (s >> 1);           */
+/*  - scrambled (Matousek 1998): digit j of the result (j = 1 the most   */
+/*    significant) is the parity of x AND M_j, M_j = digit j plus the     */
+/*    digits above it taken from the low 32 bits of Philox4x64-10 word 0  */
+/*    at counter (d, j, 0, 0), key (seed, ORC_TAG_SOBOL); then XOR the     */
+/*    low 32 bits of word 0 at counter (d, 0, 0, 0) (digital shift).      */
+#define ORC_TAG_SOBOL 0x52414349504553ULL  /* "RACIPES" */
+
+static uint32_t low32_draw(uint64_t seed, uint64_t d, uint64_t j)
+{
+    uint64_t ctr[4] = { d, j, 0, 0 }, key[2] = { seed, ORC_TAG_SOBOL }, out[4];
+    orc_philox4x64_10(ctr, key, out);
+    return (uint32_t)(out[0] & 0xFFFFFFFFULL);
+}
+
+uint32_t orc_sobol_x(const orc_ranges *r, uint64_t seed, uint64_t d, uint64_t s)
+{
+    uint64_t m[33];
+    if (d == 0) {
+        for (int k = 1; k <= 32; ++k) m[k] = 1;
+    } else {
+        uint64_t p = (uint64_t)r->sobol_poly[d];
+        int deg = 0;
+        for (int j = 0; j < 64; ++j) if ((p >> j) & 1ULL) deg = j;
+        for (int k = 1; k <= deg; ++k) m[k] = (uint64_t)r->sobol_m[d * (uint64_t)r->sobol_m_cols + (uint64_t)(k - 1)];
+        for (int k = deg + 1; k <= 32; ++k) {
+            uint64_t v = m[k - deg] ^ (m[k - deg] << deg);
+            for (int i = 1; i <= deg - 1; ++i) {
+                uint64_t a_i = (p >> (deg - i)) & 1ULL;
+                if (a_i) v ^= m[k - i] << i;
+            }
+            m[k] = v;
+        }
+    }
+    uint64_t g = s ^ (s >> 1);
+    uint32_t x = 0;
+    for (int b = 0; b < 32; ++b)
+        if ((g >> b) & 1ULL) x ^= (uint32_t)(m[b + 1] << (31 - b));
+    if (r->sobol != 2) return x;
+    uint32_t y = 0;
+    for (int j = 1; j <= 32; ++j) {
+        int bit = 32 - j;
+        uint32_t Mj = 1U << bit;
+        if (j >= 2) Mj |= low32_draw(seed, d, (uint64_t)j) & (0xFFFFFFFFU << (bit + 1));
+        uint32_t t = x & Mj, par = 0;
+        while (t) { par ^= 1U; t &= t - 1U; }
+        y |= par << bit;
+    }
+    return y ^ low32_draw(seed, d, 0);
+}
+
+/* The unit of draw d of set s: u01 of its draw, the stratified one, or the
+ * Sobol coordinate. */
 static double unit_of(const orc_ranges *r, uint64_t seed, uint64_t d, uint64_t s, uint64_t x)
 {
+    if (r->sobol) return (double)orc_sobol_x(r, seed, d, s) * 0x1p-32;
     if (r->lhs_sets <= 0) return orc_u01(x);
     return ((double)orc_lhs_stratum(seed, d, s, (uint64_t)r->lhs_sets) + orc_u01(x)) / (double)r->lhs_sets;
 }
@@ -405,7 +476,7 @@ void orc_sample_params(const orc_net *net, const orc_ranges *r, uint64_t seed,
             double ul = unit_of(r, seed, dl, c0, xl);
             Ts[e] = affine(r->thr_lo, r->thr_hi, unit_of(r, seed, dt, c0, xt)) * Msrc[net->src[e]];
             ls[e] = net->sign[e] > 0 ? lam_activating_u(r, ul, xl) : lam_inhibiting_u(r, ul, xl);
-            if (r->lhs_sets > 0) {
+            if (r->lhs_sets > 0 || r->sobol) {
                 int cnt = r->n_max - r->n_min + 1;
                 int m = (int)(unit_of(r, seed, dn, c0, rn) * (double)cnt);
                 ns[e] = r->n_min + (m < cnt ? m : cnt - 1);

@@ -34,6 +34,7 @@ GRINS_FP64, GRINS_FP32 = 0, 1
 GRINS_METHOD_DOPRI5, GRINS_METHOD_TSIT5 = 0, 1
 GRINS_ISING_SYNC, GRINS_ISING_ASYNC = 0, 1
 GRINS_DIST_TABLE1, GRINS_DIST_LOGUNIFORM, GRINS_DIST_NORMAL, GRINS_DIST_LOGNORMAL = 0, 1, 2, 3
+GRINS_SOBOL_OFF, GRINS_SOBOL_PLAIN, GRINS_SOBOL_SCRAMBLED = 0, 1, 2
 MEDIAN_PER_INDEGREE, MEDIAN_UNREGULATED = 0, 1
 GRINS_STATIC_MAX_GRID = 4096        # largest time grid of grins_racipe_integrate_static
 
@@ -48,7 +49,10 @@ class grins_racipe_ranges(C.Structure):
                 ("median_samples", C.c_int32), ("median_mode", C.c_int32),
                 ("dist_G", C.c_int32), ("dist_k", C.c_int32),
                 ("dist_lam_act", C.c_int32), ("dist_lam_inh", C.c_int32),
-                ("lhs_sets", C.c_int64)]
+                ("lhs_sets", C.c_int64),
+                ("sobol", C.c_int32), ("sobol_dims", C.c_int32),
+                ("sobol_poly", C.POINTER(C.c_int64)), ("sobol_m", C.POINTER(C.c_int64)),
+                ("sobol_m_cols", C.c_int32), ("reserved", C.c_int32)]
 
 
 class grins_solver_opts(C.Structure):
@@ -142,11 +146,23 @@ def _check(st):
         raise GrinsError(st, _lib.grins_last_error().decode())
 
 
-def default_ranges(**over) -> grins_racipe_ranges:
+def default_ranges(sobol_table=None, **over) -> grins_racipe_ranges:
+    """Table 1's ranges with fields overridden by keyword.  `sobol_table` =
+    (poly [D], m [D, cols]) int64 arrays, e.g. workloads.sobol_direction_table(),
+    for the Sobol modes (`sobol=GRINS_SOBOL_PLAIN` or `GRINS_SOBOL_SCRAMBLED`);
+    the arrays are kept alive with the returned struct."""
     r = grins_racipe_ranges()
     _lib.grins_racipe_default_ranges(C.byref(r))
     for k, v in over.items():
         setattr(r, k, v)
+    if sobol_table is not None:
+        poly = np.ascontiguousarray(sobol_table[0], dtype=np.int64)
+        m = np.ascontiguousarray(sobol_table[1], dtype=np.int64)
+        r._keep = (poly, m)
+        r.sobol_dims = int(poly.shape[0])
+        r.sobol_m_cols = int(m.shape[1])
+        r.sobol_poly = poly.ctypes.data_as(C.POINTER(C.c_int64))
+        r.sobol_m = m.ctypes.data_as(C.POINTER(C.c_int64))
     return r
 
 

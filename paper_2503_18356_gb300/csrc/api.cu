@@ -121,6 +121,12 @@ extern "C" void grins_racipe_default_ranges(grins_racipe_ranges *r)
     r->median_mode = GRINS_MEDIAN_PER_INDEGREE;
     r->dist_G = r->dist_k = r->dist_lam_act = r->dist_lam_inh = GRINS_DIST_TABLE1;
     r->lhs_sets = 0;
+    r->sobol = GRINS_SOBOL_OFF;
+    r->sobol_dims = 0;
+    r->sobol_poly = nullptr;
+    r->sobol_m = nullptr;
+    r->sobol_m_cols = 0;
+    r->reserved = 0;
 }
 
 extern "C" void grins_solver_default_opts(grins_solver_opts *o)
@@ -632,9 +638,24 @@ std::vector<double> level_samples(int na, int ni, const grins_racipe_ranges &r, 
     return out;
 }
 
+// Equal in what the medians depend on (the set-stratification fields --
+// Latin hypercube, Sobol tables -- do not enter the median samples).
 bool same_ranges(const grins_racipe_ranges &a, const grins_racipe_ranges &b)
 {
-    return std::memcmp(&a, &b, sizeof(a)) == 0;
+    grins_racipe_ranges x, y;
+    std::memcpy(&x, &a, sizeof(x));
+    std::memcpy(&y, &b, sizeof(y));
+    for (grins_racipe_ranges *r : {&x, &y}) {
+        r->lhs_sets = 0;
+        r->sobol = 0;
+        r->sobol_dims = 0;
+        r->sobol_poly = nullptr;
+        r->sobol_m = nullptr;
+        r->sobol_m_cols = 0;
+        r->reserved = 0;
+    }
+    static_assert(sizeof(grins_racipe_ranges) == 152, "grins_racipe_ranges has no padding bytes");
+    return std::memcmp(&x, &y, sizeof(x)) == 0;
 }
 
 grins_status check_ranges(const grins_racipe_ranges &r)
@@ -658,8 +679,14 @@ grins_status check_ranges(const grins_racipe_ranges &r)
             return fail(GRINS_E_INVALID_ARG, "ranges: unknown distribution %d", d);
         if (r.lhs_sets > 0 && d > GRINS_DIST_LOGUNIFORM)
             return fail(GRINS_E_INVALID_ARG, "ranges: the Latin hypercube takes Table 1 and log-uniform draws only");
+        if (r.sobol != GRINS_SOBOL_OFF && d > GRINS_DIST_LOGUNIFORM)
+            return fail(GRINS_E_INVALID_ARG, "ranges: Sobol sets take Table 1 and log-uniform draws only");
     }
     if (r.lhs_sets < 0) return fail(GRINS_E_INVALID_ARG, "ranges: lhs_sets < 0");
+    if (r.sobol < GRINS_SOBOL_OFF || r.sobol > GRINS_SOBOL_SCRAMBLED)
+        return fail(GRINS_E_INVALID_ARG, "ranges: unknown sobol mode %d", r.sobol);
+    if (r.sobol != GRINS_SOBOL_OFF && r.lhs_sets > 0)
+        return fail(GRINS_E_INVALID_ARG, "ranges: Sobol sets and the Latin hypercube exclude each other");
     return GRINS_OK;
 }
 
@@ -726,6 +753,61 @@ extern "C" grins_status grins_racipe_node_medians(grins_racipe_t h, const grins_
     return GRINS_OK;
 }
 
+// Sobol direction numbers of the first D dimensions, scrambled when asked,
+// followed by the D digital shifts (zero unscrambled): the definitions
+// stated with GRINS_SOBOL_* in grins_racipe.h.
+static grins_status sobol_table(const grins_racipe_ranges &r, int D, uint64_t seed, std::vector<uint32_t> &out)
+{
+    if (r.sobol_dims < D || !r.sobol_poly || !r.sobol_m || r.sobol_m_cols < 1)
+        return fail(GRINS_E_INVALID_ARG, "sample_params: Sobol tables need %d dimensions (have %d) and m columns",
+                    D, r.sobol_dims);
+    out.assign((size_t)D * 33, 0u);
+    for (int d = 0; d < D; ++d) {
+        uint64_t m[33];                                 // m[k], k = 1..32
+        if (d == 0) {
+            for (int k = 1; k <= 32; ++k) m[k] = 1;
+        } else {
+            const uint64_t p = (uint64_t)r.sobol_poly[d];
+            int deg = 63;
+            while (deg >= 0 && !((p >> deg) & 1ull)) --deg;
+            if (deg < 1 || deg > 32 || deg > r.sobol_m_cols || !(p & 1ull))
+                return fail(GRINS_E_INVALID_ARG, "sample_params: Sobol polynomial of dimension %d is invalid", d);
+            for (int k = 1; k <= deg; ++k) {
+                const int64_t mk = r.sobol_m[(size_t)d * r.sobol_m_cols + (k - 1)];
+                if (mk < 1 || !(mk & 1) || mk >= (int64_t(1) << k))
+                    return fail(GRINS_E_INVALID_ARG, "sample_params: Sobol m_%d of dimension %d is invalid", k, d);
+                m[k] = (uint64_t)mk;
+            }
+            for (int k = deg + 1; k <= 32; ++k) {
+                uint64_t v = m[k - deg] ^ (m[k - deg] << deg);
+                for (int i = 1; i < deg; ++i)
+                    if ((p >> (deg - i)) & 1ull) v ^= m[k - i] << i;
+                m[k] = v;
+            }
+        }
+        uint32_t *V = out.data() + (size_t)d * 32;
+        for (int b = 0; b < 32; ++b) V[b] = (uint32_t)(m[b + 1] << (31 - b));
+        if (r.sobol != GRINS_SOBOL_SCRAMBLED) continue;
+        uint32_t M[33];                                 // row masks of the scramble, digit j = 1..32
+        for (int j = 1; j <= 32; ++j) {
+            uint64_t c[4] = {(uint64_t)d, (uint64_t)j, 0, 0};
+            philox_host(c, seed, kTagSobol);
+            const int bit = 32 - j;
+            M[j] = (1u << bit) | (j >= 2 ? ((uint32_t)c[0] & (0xFFFFFFFFu << (bit + 1))) : 0u);
+        }
+        for (int b = 0; b < 32; ++b) {
+            uint32_t y = 0;
+            for (int j = 1; j <= 32; ++j)
+                y |= (uint32_t)(__builtin_popcount(V[b] & M[j]) & 1) << (32 - j);
+            V[b] = y;
+        }
+        uint64_t c[4] = {(uint64_t)d, 0, 0, 0};
+        philox_host(c, seed, kTagSobol);
+        out[(size_t)D * 32 + d] = (uint32_t)c[0];
+    }
+    return GRINS_OK;
+}
+
 // ------------------------------------------------------------------ sample
 extern "C" grins_status grins_racipe_sample_params(grins_racipe_t h, const grins_racipe_ranges *r,
                                                    uint64_t seed, int64_t set0, int64_t n_sets,
@@ -773,7 +855,25 @@ extern "C" grins_status grins_racipe_sample_params(grins_racipe_t h, const grins
                     (long long)set0, (long long)(set0 + n_sets), (long long)rr.lhs_sets);
     a.li_min = rr.lam_inh_min; a.li_max = rr.lam_inh_max;
     a.params = static_cast<unsigned char *>(d_params);
-    CUDA_TRY(launch_sample_params(a, st), "sample_params: launch");
+    if (rr.sobol != GRINS_SOBOL_OFF && n_sets > 0) {
+        if (set0 + n_sets > (int64_t(1) << 32))
+            return fail(GRINS_E_INVALID_ARG, "sample_params: Sobol sets beyond 2^32");
+        const int D = 2 * h->N + 3 * h->E;
+        std::vector<uint32_t> tab;
+        s = sobol_table(rr, D, seed, tab);
+        if (s != GRINS_OK) return s;
+        void *d_tab = nullptr;
+        CUDA_TRY(cudaMallocAsync(&d_tab, sizeof(uint32_t) * tab.size(), st), "sample_params: Sobol table");
+        cudaError_t e = cudaMemcpyAsync(d_tab, tab.data(), sizeof(uint32_t) * tab.size(), cudaMemcpyHostToDevice, st);
+        a.sobol_v = static_cast<const uint32_t *>(d_tab);
+        a.sobol_dims = D;
+        if (e == cudaSuccess) e = launch_sample_params(a, st);
+        const cudaError_t ef = cudaFreeAsync(d_tab, st);
+        CUDA_TRY(e, "sample_params: Sobol launch");
+        CUDA_TRY(ef, "sample_params: Sobol table");
+    } else {
+        CUDA_TRY(launch_sample_params(a, st), "sample_params: launch");
+    }
     if (d_ic_unit && n_ics > 0) CUDA_TRY(launch_sample_ics(h->N, seed, n_ics, d_ic_unit, st), "sample_params: IC launch");
     return GRINS_OK;
 }

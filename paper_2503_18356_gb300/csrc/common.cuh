@@ -63,6 +63,9 @@ struct SampleArgs {
     int32_t dist_G, dist_k, dist_la, dist_li;   // GRINS_DIST_* per class
     double G_hi, k_hi, la_hi;                   // range ends (non-Table-1 draws)
     int64_t lhs_sets;                           // > 0: Latin hypercube over this many sets
+    const uint32_t *sobol_v;                    // non-null: Sobol units; [D][32] direction
+                                                // numbers (scrambled), then [D] shifts
+    int sobol_dims;                             // D = 2N + 3E
     double li_min, li_max;                      // inhibiting lambda range (non-Table-1 draws)
     unsigned char *params;
 };
@@ -264,6 +267,7 @@ __device__ __forceinline__ U64x4 philox4x64_10(uint64_t c0, uint64_t c1, uint64_
 constexpr uint64_t kTagParams = 0x52414349504550ull;  // "RACIPEP"
 constexpr uint64_t kTagIcs = 0x52414349504549ull;     // "RACIPEI"
 constexpr uint64_t kTagLhs = 0x5241434950454Cull;     // "RACIPEL": Latin hypercube permutations
+constexpr uint64_t kTagSobol = 0x52414349504553ull;   // "RACIPES": Sobol scramble
 constexpr uint64_t kKeyMedian = 0x48414C4646554E43ull; // "HALFFUNC"
 
 // [0, 1) from the top 53 bits; exact.

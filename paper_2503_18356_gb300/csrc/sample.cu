@@ -67,10 +67,21 @@ __device__ uint64_t lhs_stratum(uint64_t seed, uint64_t d, uint64_t s, uint64_t 
     return x;
 }
 
-// The unit of draw d of set s: its own draw, or under a Latin hypercube
-// (stratum + draw) / S.
+// Coordinate d of Sobol point s in Gray-code order: the shift XOR the
+// direction numbers of the set bits of s ^ (s >> 1).
+__device__ __forceinline__ double sobol_unit(const SampleArgs &a, uint64_t d, uint64_t s)
+{
+    const uint32_t *V = a.sobol_v + d * 32;
+    uint32_t x = __ldg(a.sobol_v + (size_t)a.sobol_dims * 32 + d);
+    for (uint64_t g = s ^ (s >> 1); g; g &= g - 1) x ^= __ldg(V + (__ffsll((long long)g) - 1));
+    return __dmul_rn((double)x, 0x1.0p-32);
+}
+
+// The unit of draw d of set s: its own draw, under a Latin hypercube
+// (stratum + draw) / S, or the Sobol coordinate.
 __device__ __forceinline__ double draw_unit(const SampleArgs &a, uint64_t d, uint64_t s, uint64_t x)
 {
+    if (a.sobol_v) return sobol_unit(a, d, s);
     if (a.lhs_sets <= 0) return unit_double(x);
     const uint64_t p = lhs_stratum(a.seed, d, s, (uint64_t)a.lhs_sets);
     return __ddiv_rn(__dadd_rn((double)p, unit_double(x)), (double)a.lhs_sets);
@@ -120,7 +131,7 @@ __global__ void sample_params_kernel(SampleArgs a)
                                                  : __ddiv_rn(1.0, affine_rn(a.vi_min, a.vi_span, u));
             } else {
                 const int e = d - 2 * N - 2 * E;
-                if (OTHER && a.lhs_sets > 0) {
+                if (OTHER && (a.lhs_sets > 0 || a.sobol_v)) {
                     const int m = (int)__dmul_rn(u, (double)a.n_count);
                     nn[e] = (uint8_t)(a.n_min + (m < a.n_count ? m : a.n_count - 1));
                 } else {
@@ -167,7 +178,7 @@ cudaError_t launch_sample_params(const SampleArgs &a, cudaStream_t st)
     if (a.n_sets <= 0) return cudaSuccess;
     const int n_draws = 2 * a.L.N + 3 * a.L.E;
     const int64_t work = a.n_sets * ((n_draws + 3) / 4);
-    if (a.dist_G || a.dist_k || a.dist_la || a.dist_li || a.lhs_sets > 0)
+    if (a.dist_G || a.dist_k || a.dist_la || a.dist_li || a.lhs_sets > 0 || a.sobol_v)
         sample_params_kernel<true><<<grid_for(work, 256), 256, 0, st>>>(a);
     else
         sample_params_kernel<false><<<grid_for(work, 256), 256, 0, st>>>(a);

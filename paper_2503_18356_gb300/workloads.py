@@ -149,3 +149,19 @@ def serving_stream(rate_hz: float = 20.0, duration_s: float = 60.0, seed: int = 
         reqs.append(dict(arrival_s=t, topology=topo, n_sets=S, n_ics=I,
                          param_seed=4000 + r, ic_seed=4000 + r))
     return reqs
+
+
+def sobol_direction_table():
+    """The published Sobol initialisation table of Joe and Kuo (2008), as
+    scipy ships it (21,201 dimensions): (poly int64 [D], m int64 [D, 18]),
+    poly[d] the primitive polynomial of dimension d with bit j the
+    coefficient of x^j, m[d, k-1] the initial direction integer m_k.  Data
+    only: the direction numbers are derived from it by the sampler and,
+    independently, by the oracle."""
+    import os
+
+    import scipy.stats
+    path = os.path.join(os.path.dirname(scipy.stats.__file__), "_sobol_direction_numbers.npz")
+    with np.load(path) as z:
+        return (np.ascontiguousarray(z["poly"], dtype=np.int64),
+                np.ascontiguousarray(z["vinit"], dtype=np.int64))

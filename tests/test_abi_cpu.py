@@ -75,3 +75,16 @@ def test_defaults_follow_table1(lib):
     assert (r.n_min, r.n_max, r.thr_lo, r.thr_hi) == (1, 6, 0.02, 1.98)
     o = api.default_opts()
     assert o.precision == api.GRINS_FP32 and o.polish == 1 and o.t0 == 0.0 and o.t_end == 200.0
+
+
+def test_binding_structs_match_the_header_sizes(lib):
+    # the library asserts sizeof(grins_racipe_ranges) == 152 with no padding
+    # (its median cache compares the struct bytewise); the ctypes mirror
+    # must have the same size and field order
+    from paper_2503_18356_gb300 import api
+    assert C.sizeof(api.grins_racipe_ranges) == 152
+    names = [f[0] for f in api.grins_racipe_ranges._fields_]
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    body = re.search(r"typedef struct \{(.*?)\} grins_racipe_ranges;", text, flags=re.S).group(1)
+    declared = [n for decl in body.split(";") for n in re.findall(r"(\w+)\s*(?:,|$)", decl.strip())]
+    assert names == declared

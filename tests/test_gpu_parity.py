@@ -128,6 +128,50 @@ def test_sampler_latin_hypercube_whole_and_refusals():
         h.sample_params(8, 4, 1, set0=S - 2, ranges=api.default_ranges(lhs_sets=S))
 
 
+@pytest.mark.parametrize("mode,dist_G", [(1, 0), (2, 0), (2, 1)])
+def test_sampler_sobol(mode, dist_G):
+    """Sobol sets, plain and scrambled (the host builds the direction numbers
+    and applies the scramble to them, the oracle scrambles each point): Table
+    1 classes bit-exact, log-uniform G to a few ulp; sets from an offset,
+    ragged count."""
+    from paper_2503_18356_gb300 import api
+    topo = W.net22_workload()["topology"]
+    h = PT.gpu_handle(topo)
+    tab = W.sobol_direction_table()
+    set0, n = 4093, 77
+    _, _, p, _ = PT.gpu_sample(h, 17, n, 2, set0=set0,
+                               ranges=api.default_ranges(sobol=mode, dist_G=dist_G, sobol_table=tab))
+    ref = O.sample_params(O.Network(*topo.edges()), 17, n, set0=set0,
+                          ranges=O.default_ranges(sobol=mode, dist_G=dist_G, sobol_table=tab))
+    for f in ("k", "T", "lam", "n"):
+        assert np.array_equal(getattr(p, f), getattr(ref, f)), f
+    if dist_G == 0:
+        assert np.array_equal(p.G, ref.G)
+    else:
+        assert np.all(np.abs(p.G - ref.G) <= 1e-14 * (np.abs(ref.G) + 99.0))
+
+
+def test_sampler_sobol_refusals():
+    from paper_2503_18356_gb300 import api
+    topo = W.net22_workload()["topology"]
+    h = PT.gpu_handle(topo)
+    poly, m = W.sobol_direction_table()
+    R = lambda **kw: api.default_ranges(sobol=api.GRINS_SOBOL_PLAIN, **kw)
+    bad = [R(sobol_table=(poly, m), dist_k=api.GRINS_DIST_NORMAL),      # normal class
+           R(sobol_table=(poly, m), lhs_sets=100),                       # with the hypercube
+           R(sobol_table=(poly[:100], m[:100])),                         # fewer than 2N + 3E dims
+           R()]                                                          # no table
+    for r in bad:
+        with pytest.raises(api.GrinsError):
+            h.sample_params(1, 8, 1, ranges=r)
+    bad_m = m.copy()
+    bad_m[5, 0] = 2                                                      # even m_1
+    with pytest.raises(api.GrinsError):
+        h.sample_params(1, 8, 1, ranges=R(sobol_table=(poly, bad_m)))
+    with pytest.raises(api.GrinsError):
+        h.sample_params(1, 8, 1, set0=(1 << 32) - 4, ranges=R(sobol_table=(poly, m)))
+
+
 # ----------------------------------------------------------------- dedupe
 def test_unique_states_bit_exact_on_given_states():
     topo = W.random_network(3, 4, 8, 4, 0)

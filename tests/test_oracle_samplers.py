@@ -160,3 +160,92 @@ def test_lhs_off_is_the_plain_sampler():
     a, b = O.sample_params(NET, 3, 50, ranges=r0), O.sample_params(NET, 3, 50, ranges=r1)
     for f in ("G", "k", "T", "lam", "n"):
         assert np.array_equal(getattr(a, f), getattr(b, f))
+
+
+# ---------------------------------------------------------------- Sobol
+TAB = None
+
+
+def sobol_tab():
+    global TAB
+    if TAB is None:
+        TAB = W.sobol_direction_table()
+    return TAB
+
+
+def test_sobol_points_equal_scipy_unscrambled():
+    # the plain Sobol sequence from its definition (Bratley-Fox direction
+    # integers, Gray-code order) against scipy's generator on the same
+    # Joe-Kuo table: every coordinate of 290 dimensions (the 22-node
+    # network's 2N + 3E draws) for points 0..511, and from an offset
+    qmc = pytest.importorskip("scipy.stats").qmc
+    r = O.default_ranges(sobol=1, sobol_table=sobol_tab())
+    D, n = 290, 512
+    ref = np.rint(qmc.Sobol(D, scramble=False, bits=32).random(n) * 2.0**32).astype(np.uint64)
+    mine = np.array([[O.sobol_x(r, 0, d, s) for d in range(D)] for s in range(n)], dtype=np.uint64)
+    assert np.array_equal(ref, mine)
+    g = qmc.Sobol(40, scramble=False, bits=32)
+    g.fast_forward(100_000)
+    ref = np.rint(g.random(16) * 2.0**32).astype(np.uint64)
+    mine = np.array([[O.sobol_x(r, 0, d, 100_000 + s) for d in range(40)] for s in range(16)], dtype=np.uint64)
+    assert np.array_equal(ref, mine)
+
+
+def elementary_intervals_hold_one_point(u, v, m):
+    """(0, m, 2)-net in base 2: every box [a 2^-i, (a+1) 2^-i) x
+    [b 2^-(m-i), (b+1) 2^-(m-i)) of area 2^-m holds exactly one point."""
+    for i in range(m + 1):
+        a = np.floor(u * 2**i).astype(np.int64)
+        b = np.floor(v * 2**(m - i)).astype(np.int64)
+        cnt = np.bincount(a * 2**(m - i) + b, minlength=2**m)
+        if not np.all(cnt == 1):
+            return False
+    return True
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_sobol_net_and_stratification(mode):
+    # the first 2^m points: dimensions 0 and 1 form a (0, m, 2)-net, and
+    # every one-dimensional projection holds one point per 2^-m stratum;
+    # both survive the linear scramble and the digital shift
+    m = 8
+    r = O.default_ranges(sobol=mode, sobol_table=sobol_tab())
+    X = np.array([[O.sobol_x(r, 77, d, s) for d in range(60)] for s in range(2**m)], dtype=np.float64) * 2.0**-32
+    assert elementary_intervals_hold_one_point(X[:, 0], X[:, 1], m)
+    for d in range(60):
+        assert np.array_equal(np.sort(np.floor(X[:, d] * 2**m)), np.arange(2**m)), d
+
+
+def test_sobol_scramble_depends_on_the_seed_only_when_scrambled():
+    t = sobol_tab()
+    plain = O.default_ranges(sobol=1, sobol_table=t)
+    scr = O.default_ranges(sobol=2, sobol_table=t)
+    pts = lambda r, seed: np.array([[O.sobol_x(r, seed, d, s) for d in range(20)] for s in range(256)])
+    assert np.array_equal(pts(plain, 1), pts(plain, 2))
+    a, b = pts(scr, 1), pts(scr, 2)
+    assert not np.array_equal(a, b) and not np.array_equal(a, pts(plain, 1))
+    # a randomised net: coordinates average 1/2 within 1/(2 sqrt(3) 16)-ish
+    assert np.all(np.abs(a.mean(axis=0) * 2.0**-32 - 0.5) < 0.01)
+
+
+def test_sobol_sets_one_value_per_stratum():
+    S = 256
+    r = O.default_ranges(median_samples=2000, sobol=2, sobol_table=sobol_tab())
+    p = O.sample_params(NET, 13, S, ranges=r)
+    for i in range(NET.n_nodes):
+        assert order_in_strata(p.G[:, i], r.G_min, r.G_max, S)
+        assert order_in_strata(p.k[:, i], r.k_min, r.k_max, S)
+    cnt = r.n_max - r.n_min + 1
+    for e in range(NET.n_edges):
+        if NET.sign[e] > 0:
+            assert order_in_strata(p.lam[:, e], r.lam_act_min, r.lam_act_max, S)
+        else:
+            assert order_in_strata(1 / p.lam[:, e], 1 / r.lam_inh_max, 1 / r.lam_inh_min, S)
+        # n = n_min + floor(u count): each value S / count sets, within 2
+        # for the strata that straddle the value's two boundaries
+        c = np.bincount(p.n[:, e] - r.n_min, minlength=cnt)
+        assert np.all(np.abs(c - S / cnt) <= 2)
+    # sets drawn in two calls equal one call (point index = set index)
+    a = O.sample_params(NET, 13, S // 2, set0=0, ranges=r)
+    b = O.sample_params(NET, 13, S // 2, set0=S // 2, ranges=r)
+    assert np.array_equal(p.G, np.concatenate([a.G, b.G]))
