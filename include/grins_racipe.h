@@ -84,6 +84,22 @@ enum { GRINS_MEDIAN_PER_INDEGREE = 0, GRINS_MEDIAN_UNREGULATED = 1 };
  * u_hi, u_lo = (half + 1/2) 2^-32: sqrt(-2 log u_hi) cos(2 pi u_lo). */
 enum { GRINS_DIST_TABLE1 = 0, GRINS_DIST_LOGUNIFORM = 1, GRINS_DIST_NORMAL = 2, GRINS_DIST_LOGNORMAL = 3 };
 
+/* One row of a per-parameter range table (Sec. 2.1.2: the generated
+ * parameter range file, with a distribution per parameter).  Rows follow
+ * the layout of a parameter set: G[N], k[N], T[E], lam[E], n[E].
+ *   G, k, lam: dist (GRINS_DIST_*) over [lo, hi]; an inhibiting lam needs
+ *              hi <= 1 and, under GRINS_DIST_TABLE1, is drawn in the
+ *              inverse range and inverted (Table 1); an activating lam
+ *              needs lo >= 1;
+ *   T:         the multiplier range of the source's median (Table 1:
+ *              [0.02, 1.98]), uniform; dist must be 0;
+ *   n:         integers lo..hi (1 <= lo <= hi <= 255), uniform; dist 0. */
+typedef struct {
+    int32_t dist;
+    int32_t reserved;          /* set to 0 */
+    double lo, hi;
+} grins_param_range;
+
 /* Sampling ranges, Table 1 (Sec. 2.1.2).  grins_racipe_default_ranges fills
  * the defaults: G [1,100], k [0.1,1], activating lambda [1,100], inhibiting
  * lambda [0.01,1] (drawn in the inverse range and inverted), integer n [1,6],
@@ -120,6 +136,12 @@ typedef struct {
     const int64_t *sobol_m;            /* host [sobol_dims][sobol_m_cols] */
     int32_t sobol_m_cols;
     int32_t reserved;                  /* set to 0 (keeps the struct free of padding) */
+    const grins_param_range *param_ranges; /* host [2N + 3E], read during the
+                                          call, or NULL.  Non-NULL: every
+                                          parameter takes its own row (the
+                                          class fields above are unused but
+                                          median_samples and median_mode), and
+                                          the medians are per node (below) */
 } grins_racipe_ranges;
 
 /* Sobol sets (Sec. 2.1.2: the paper's default sampler).  With sobol != 0,
@@ -211,7 +233,15 @@ int64_t grins_racipe_param_stride(grins_racipe_t h);
 /* Host copy of the per-node median levels M_j used by the half-functional
  * threshold rule for the given ranges (NULL = defaults): out[n_nodes].
  * M_j depends on node j's in-degree class (#activating, #inhibiting
- * inputs), Sec. 2.1.2 and Table 1 threshold row. */
+ * inputs), Sec. 2.1.2 and Table 1 threshold row.
+ * With a per-parameter table, node j's medians use its own rows: the
+ * unregulated median M0_j of G_j / k_j (median_samples draws of Philox
+ * key (0x48414C4646554E43, 2^63 + 2j), counter (sample, draw / 4), word draw %
+ * 4: G draw 0, k draw 1), and, when j has inputs and median_mode is
+ * per-in-degree, the median M_j of G_j / k_j times one Hill factor per
+ * in-edge e (edge order, q-th in-edge draws 2 + 5q .. 6 + 5q: G and k of
+ * the source from its rows, T = multiplier x M0_src, lam, n from e's rows)
+ * under key (0x48414C4646554E43, 2^63 + 2j + 1); else M_j = M0_j. */
 grins_status grins_racipe_node_medians(grins_racipe_t h, const grins_racipe_ranges *r,
                                        double *out);
 

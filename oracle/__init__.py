@@ -64,7 +64,12 @@ class Ranges(C.Structure):
                 ("lhs_sets", C.c_int64),
                 ("sobol", C.c_int32), ("sobol_dims", C.c_int32),
                 ("sobol_poly", C.POINTER(C.c_int64)), ("sobol_m", C.POINTER(C.c_int64)),
-                ("sobol_m_cols", C.c_int32)]
+                ("sobol_m_cols", C.c_int32),
+                ("param_ranges", C.c_void_p)]
+
+
+# one row of a per-parameter range table (dist, reserved, lo, hi)
+PARAM_ROW = np.dtype([("dist", np.int32), ("reserved", np.int32), ("lo", np.float64), ("hi", np.float64)])
 
 
 class Net(C.Structure):
@@ -118,6 +123,7 @@ def lib():
             l.orc_lhs_stratum.argtypes = [C.c_uint64] * 4; l.orc_lhs_stratum.restype = C.c_uint64
             l.orc_sobol_x.argtypes = [P(Ranges), C.c_uint64, C.c_uint64, C.c_uint64]
             l.orc_sobol_x.restype = C.c_uint32
+            l.orc_node_medians.argtypes = [P(Net), P(Ranges), P(C.c_double)]
             l.orc_sample_ics.argtypes = [C.c_int32, C.c_uint64, C.c_int32, P(C.c_double)]
             l.orc_solve.argtypes = [P(Net), P(Params), P(C.c_double), P(Opts), P(C.c_double),
                                     P(C.c_double)]
@@ -162,13 +168,18 @@ def _f64(a):
 
 
 # ---------------------------------------------------------------- helpers
-def default_ranges(sobol_table=None, **over) -> Ranges:
+def default_ranges(sobol_table=None, param_ranges=None, **over) -> Ranges:
     """Table 1's ranges with fields overridden; `sobol_table` = (poly, m)
-    int64 arrays for the Sobol modes (kept alive with the struct)."""
+    int64 arrays for the Sobol modes; `param_ranges` = a PARAM_ROW array of
+    2N + 3E rows (kept alive with the struct)."""
     r = Ranges()
     lib().orc_default_ranges(C.byref(r))
     for k, v in over.items():
         setattr(r, k, v)
+    r._rows = None
+    if param_ranges is not None:
+        r._rows = np.ascontiguousarray(param_ranges, dtype=PARAM_ROW)
+        r.param_ranges = r._rows.ctypes.data
     if sobol_table is not None:
         poly = np.ascontiguousarray(sobol_table[0], dtype=np.int64)
         m = np.ascontiguousarray(sobol_table[1], dtype=np.int64)
@@ -276,6 +287,14 @@ def lhs_stratum(seed, d, s, S):
     """The Latin-hypercube stratum of draw d of set s among S sets: a keyed
     permutation of [0, S) in s (Feistel network with cycle walking)."""
     return int(lib().orc_lhs_stratum(C.c_uint64(seed), C.c_uint64(d), C.c_uint64(s), C.c_uint64(S)))
+
+
+def node_medians(net: Network, ranges=None):
+    """The half-functional median M_j of every node."""
+    r = ranges or default_ranges()
+    M = np.zeros(net.n_nodes)
+    lib().orc_node_medians(C.byref(net.c), C.byref(r), _p(M, C.c_double))
+    return M
 
 
 def sobol_x(ranges, seed, d, s):

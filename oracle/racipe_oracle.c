@@ -123,7 +123,18 @@ typedef struct {
     const int64_t *sobol_poly;     /* [sobol_dims] primitive polynomials, bit j = coeff. of x^j */
     const int64_t *sobol_m;        /* [sobol_dims][sobol_m_cols] initial m_1 .. m_s */
     int32_t sobol_m_cols;
+    const struct orc_param_range *param_ranges;  /* [2N + 3E] rows, or NULL (below) */
 } orc_ranges;
+
+/* A per-parameter range row (Sec. 2.1.2: the parameter range file, with a */
+/* distribution per parameter), rows in the order G[N], k[N], T[E],        */
+/* lambda[E], n[E]: G, k, lambda by dist over [lo, hi] (an inhibiting      */
+/* lambda under dist 0 in Table 1's inverse range); T the multiplier range */
+/* of the source's median; n the integers lo..hi.                          */
+typedef struct orc_param_range {
+    int32_t dist, reserved;
+    double lo, hi;
+} orc_param_range;
 
 void orc_default_ranges(orc_ranges *r)
 {
@@ -142,6 +153,7 @@ void orc_default_ranges(orc_ranges *r)
     r->sobol_poly = NULL;
     r->sobol_m = NULL;
     r->sobol_m_cols = 0;
+    r->param_ranges = NULL;
 }
 
 /* Affine map of a unit draw onto [lo, hi]: lo + (hi - lo) * u. */
@@ -445,18 +457,135 @@ double orc_median(int32_t a, int32_t b, const orc_ranges *r)
 /* is u_{c,i} * G_i / k_i (Sec. 2.1.2, between a node's minimum 0 and   */
 /* maximum G/k; the same unit ICs are used for every set, Sec. 3.1).    */
 /* ------------------------------------------------------------------ */
+/* A continuous parameter from its row: G, k, activating lambda by the    */
+/* row's distribution; an inhibiting lambda under dist 0 in the inverse    */
+/* range [1/hi, 1/lo], inverted (Table 1's rule).                          */
+static double row_param(const orc_param_range *p, int inh, double uu, uint64_t x)
+{
+    if (inh && p->dist == 0) return 1.0 / affine(1.0 / p->hi, 1.0 / p->lo, uu);
+    return param_draw_u(p->dist, p->lo, p->hi, uu, x);
+}
+
+/* Sets from a per-parameter table: the class sampler's draws and units,  */
+/* each parameter taking its own row.                                      */
+static void sample_rows(const orc_net *net, const orc_ranges *r, uint64_t seed, int64_t set0, int64_t n_sets,
+                        const double *Msrc, double *G, double *k, double *T, double *lam, int32_t *n)
+{
+    int N = net->n_nodes, E = net->n_edges;
+    const orc_param_range *P = r->param_ranges;
+    int strat = r->lhs_sets > 0 || r->sobol;
+    for (int64_t s = 0; s < n_sets; ++s) {
+        uint64_t c0 = (uint64_t)(set0 + s);
+        for (int d = 0; d < 2 * N + 3 * E; ++d) {
+            uint64_t x = draw64(seed, ORC_TAG_PARAMS, c0, (uint64_t)d);
+            double uu = unit_of(r, seed, (uint64_t)d, c0, x);
+            const orc_param_range *p = &P[d];
+            if (d < N) G[s * N + d] = row_param(p, 0, uu, x);
+            else if (d < 2 * N) k[s * N + (d - N)] = row_param(p, 0, uu, x);
+            else if (d < 2 * N + E) {
+                int e = d - 2 * N;
+                T[s * E + e] = affine(p->lo, p->hi, uu) * Msrc[net->src[e]];
+            } else if (d < 2 * N + 2 * E) {
+                int e = d - 2 * N - E;
+                lam[s * E + e] = row_param(p, net->sign[e] < 0, uu, x);
+            } else {
+                int e = d - 2 * N - 2 * E;
+                int lo = (int)p->lo, hi = (int)p->hi, cnt = hi - lo + 1;
+                if (strat) {
+                    int m = (int)(uu * (double)cnt);
+                    n[s * E + e] = lo + (m < cnt ? m : cnt - 1);
+                } else {
+                    n[s * E + e] = orc_uint_range(x, lo, hi);
+                }
+            }
+        }
+    }
+}
+
+/* The half-functional medians M_j of every node (Sec. 2.1.2).  Class      */
+/* ranges: the median of node j's in-degree class (orc_median).  A         */
+/* per-parameter table: node j's own rows -- first its unregulated median  */
+/* M0_j, the median of G_j / k_j over median_samples draws (stream key     */
+/* (ORC_KEY_MEDIAN, 2^63 + 2j), draws 0 and 1); then, if j has inputs and  */
+/* the per-in-degree mode is on, the median of G_j / k_j times the Hill    */
+/* factor of each in-edge (edge order; the q-th in-edge takes draws 2 + 5q */
+/* .. 6 + 5q: G and k of its source from the source's rows, the threshold  */
+/* multiplier from the edge's T row times M0 of the source, lambda and n   */
+/* from the edge's rows), key (ORC_KEY_MEDIAN, 2^63 + 2j + 1).              */
+void orc_node_medians(const orc_net *net, const orc_ranges *r, double *M)
+{
+    int N = net->n_nodes, E = net->n_edges;
+    if (!r->param_ranges) {
+        for (int j = 0; j < N; ++j) {
+            int a = 0, b = 0;
+            for (int e = 0; e < E; ++e)
+                if (net->dst[e] == j) { if (net->sign[e] > 0) ++a; else ++b; }
+            M[j] = orc_median(a, b, r);
+        }
+        return;
+    }
+    const orc_param_range *P = r->param_ranges;
+    int K = r->median_samples;
+    double *v = (double *)malloc(sizeof(double) * (size_t)K);
+    double *M0 = (double *)malloc(sizeof(double) * (size_t)N);
+    for (int j = 0; j < N; ++j) {
+        uint64_t key1 = (1ULL << 63) + 2ULL * (uint64_t)j;
+        for (int s = 0; s < K; ++s) {
+            uint64_t xg = draw64(ORC_KEY_MEDIAN, key1, (uint64_t)s, 0);
+            uint64_t xk = draw64(ORC_KEY_MEDIAN, key1, (uint64_t)s, 1);
+            v[s] = row_param(&P[j], 0, orc_u01(xg), xg) / row_param(&P[N + j], 0, orc_u01(xk), xk);
+        }
+        M0[j] = median_of(v, K);
+        M[j] = M0[j];
+    }
+    for (int j = 0; j < N && r->median_mode == 0; ++j) {
+        int has_inputs = 0;
+        for (int e = 0; e < E; ++e) if (net->dst[e] == j) has_inputs = 1;
+        if (!has_inputs) continue;
+        uint64_t key1 = (1ULL << 63) + 2ULL * (uint64_t)j + 1ULL;
+        for (int s = 0; s < K; ++s) {
+            uint64_t xg = draw64(ORC_KEY_MEDIAN, key1, (uint64_t)s, 0);
+            uint64_t xk = draw64(ORC_KEY_MEDIAN, key1, (uint64_t)s, 1);
+            double level = row_param(&P[j], 0, orc_u01(xg), xg) / row_param(&P[N + j], 0, orc_u01(xk), xk);
+            int q = 0;
+            for (int e = 0; e < E; ++e) {
+                if (net->dst[e] != j) continue;
+                int src = net->src[e];
+                uint64_t d = 2 + 5 * (uint64_t)q;
+                uint64_t x0 = draw64(ORC_KEY_MEDIAN, key1, (uint64_t)s, d + 0);
+                uint64_t x1 = draw64(ORC_KEY_MEDIAN, key1, (uint64_t)s, d + 1);
+                uint64_t x2 = draw64(ORC_KEY_MEDIAN, key1, (uint64_t)s, d + 2);
+                uint64_t x3 = draw64(ORC_KEY_MEDIAN, key1, (uint64_t)s, d + 3);
+                uint64_t x4 = draw64(ORC_KEY_MEDIAN, key1, (uint64_t)s, d + 4);
+                double Gs = row_param(&P[src], 0, orc_u01(x0), x0);
+                double ks = row_param(&P[N + src], 0, orc_u01(x1), x1);
+                const orc_param_range *pt = &P[2 * N + e], *pl = &P[2 * N + E + e], *pn = &P[2 * N + 2 * E + e];
+                double Tq = affine(pt->lo, pt->hi, orc_u01(x2)) * M0[src];
+                double lq = row_param(pl, net->sign[e] < 0, orc_u01(x3), x3);
+                int32_t nq = orc_uint_range(x4, (int32_t)pn->lo, (int32_t)pn->hi);
+                level = level * edge_factor(net->sign[e], Gs / ks, Tq, (double)nq, lq);
+                ++q;
+            }
+            v[s] = level;
+        }
+        M[j] = median_of(v, K);
+    }
+    free(v);
+    free(M0);
+}
+
 void orc_sample_params(const orc_net *net, const orc_ranges *r, uint64_t seed,
                        int64_t set0, int64_t n_sets,
                        double *G, double *k, double *T, double *lam, int32_t *n)
 {
     int N = net->n_nodes, E = net->n_edges;
-    /* Median per source node, from its in-degree class. */
+    /* Median per source node (class or per-parameter). */
     double *Msrc = (double *)malloc(sizeof(double) * (size_t)N);
-    for (int j = 0; j < N; ++j) {
-        int a = 0, b = 0;
-        for (int e = 0; e < E; ++e)
-            if (net->dst[e] == j) { if (net->sign[e] > 0) ++a; else ++b; }
-        Msrc[j] = orc_median(a, b, r);
+    orc_node_medians(net, r, Msrc);
+    if (r->param_ranges) {
+        sample_rows(net, r, seed, set0, n_sets, Msrc, G, k, T, lam, n);
+        free(Msrc);
+        return;
     }
     for (int64_t s = 0; s < n_sets; ++s) {
         uint64_t c0 = (uint64_t)(set0 + s);

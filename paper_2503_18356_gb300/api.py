@@ -39,6 +39,14 @@ MEDIAN_PER_INDEGREE, MEDIAN_UNREGULATED = 0, 1
 GRINS_STATIC_MAX_GRID = 4096        # largest time grid of grins_racipe_integrate_static
 
 
+class grins_param_range(C.Structure):
+    _fields_ = [("dist", C.c_int32), ("reserved", C.c_int32), ("lo", C.c_double), ("hi", C.c_double)]
+
+
+# numpy mirror of grins_param_range (one row per parameter, layout order)
+PARAM_RANGE_DTYPE = np.dtype([("dist", np.int32), ("reserved", np.int32), ("lo", np.float64), ("hi", np.float64)])
+
+
 class grins_racipe_ranges(C.Structure):
     _fields_ = [("G_min", C.c_double), ("G_max", C.c_double),
                 ("k_min", C.c_double), ("k_max", C.c_double),
@@ -52,7 +60,8 @@ class grins_racipe_ranges(C.Structure):
                 ("lhs_sets", C.c_int64),
                 ("sobol", C.c_int32), ("sobol_dims", C.c_int32),
                 ("sobol_poly", C.POINTER(C.c_int64)), ("sobol_m", C.POINTER(C.c_int64)),
-                ("sobol_m_cols", C.c_int32), ("reserved", C.c_int32)]
+                ("sobol_m_cols", C.c_int32), ("reserved", C.c_int32),
+                ("param_ranges", C.POINTER(grins_param_range))]
 
 
 class grins_solver_opts(C.Structure):
@@ -146,23 +155,30 @@ def _check(st):
         raise GrinsError(st, _lib.grins_last_error().decode())
 
 
-def default_ranges(sobol_table=None, **over) -> grins_racipe_ranges:
+def default_ranges(sobol_table=None, param_ranges=None, **over) -> grins_racipe_ranges:
     """Table 1's ranges with fields overridden by keyword.  `sobol_table` =
     (poly [D], m [D, cols]) int64 arrays, e.g. workloads.sobol_direction_table(),
     for the Sobol modes (`sobol=GRINS_SOBOL_PLAIN` or `GRINS_SOBOL_SCRAMBLED`);
-    the arrays are kept alive with the returned struct."""
+    `param_ranges` = a PARAM_RANGE_DTYPE array of 2N + 3E rows (see
+    Racipe.param_range_table).  The arrays are kept alive with the struct."""
     r = grins_racipe_ranges()
     _lib.grins_racipe_default_ranges(C.byref(r))
     for k, v in over.items():
         setattr(r, k, v)
+    keep = []
+    if param_ranges is not None:
+        rows = np.ascontiguousarray(param_ranges, dtype=PARAM_RANGE_DTYPE)
+        keep.append(rows)
+        r.param_ranges = rows.ctypes.data_as(C.POINTER(grins_param_range))
     if sobol_table is not None:
         poly = np.ascontiguousarray(sobol_table[0], dtype=np.int64)
         m = np.ascontiguousarray(sobol_table[1], dtype=np.int64)
-        r._keep = (poly, m)
+        keep += [poly, m]
         r.sobol_dims = int(poly.shape[0])
         r.sobol_m_cols = int(m.shape[1])
         r.sobol_poly = poly.ctypes.data_as(C.POINTER(C.c_int64))
         r.sobol_m = m.ctypes.data_as(C.POINTER(C.c_int64))
+    r._keep = keep
     return r
 
 
@@ -204,6 +220,23 @@ class Racipe:
     @classmethod
     def from_topology(cls, topo, device=None):
         return cls(*topo.edges(), device=device)
+
+    def param_range_table(self, ranges=None):
+        """The per-parameter range table (the generated range file) that the
+        class fields of `ranges` describe: rows G[N], k[N], T[E], lam[E], n[E]
+        as a PARAM_RANGE_DTYPE array, to be edited and passed back as
+        default_ranges(param_ranges=...)."""
+        r = ranges if ranges is not None else default_ranges()
+        N, E = self.n_nodes, self.n_edges
+        t = np.zeros(2 * N + 3 * E, dtype=PARAM_RANGE_DTYPE)
+        t[:N] = (r.dist_G, 0, r.G_min, r.G_max)
+        t[N:2 * N] = (r.dist_k, 0, r.k_min, r.k_max)
+        t[2 * N:2 * N + E] = (0, 0, r.thr_lo, r.thr_hi)
+        for e in range(E):
+            t[2 * N + E + e] = ((r.dist_lam_act, 0, r.lam_act_min, r.lam_act_max) if self.sign[e] > 0
+                                else (r.dist_lam_inh, 0, r.lam_inh_min, r.lam_inh_max))
+        t[2 * N + 2 * E:] = (0, 0, float(r.n_min), float(r.n_max))
+        return t
 
     def integrator(self) -> str:
         """Which FP32 integrator kernel this handle uses (grins_racipe_integrator)."""

@@ -104,6 +104,7 @@ struct grins_racipe {
     // cached median table
     bool median_valid = false;
     grins_racipe_ranges median_ranges{};
+    std::vector<grins_param_range> median_table;   // per-parameter rows the medians were taken with
     std::vector<double> node_median;
     bool median_uploaded = false;
 };
@@ -127,6 +128,7 @@ extern "C" void grins_racipe_default_ranges(grins_racipe_ranges *r)
     r->sobol_m = nullptr;
     r->sobol_m_cols = 0;
     r->reserved = 0;
+    r->param_ranges = nullptr;
 }
 
 extern "C" void grins_solver_default_opts(grins_solver_opts *o)
@@ -653,8 +655,9 @@ bool same_ranges(const grins_racipe_ranges &a, const grins_racipe_ranges &b)
         r->sobol_m = nullptr;
         r->sobol_m_cols = 0;
         r->reserved = 0;
+        r->param_ranges = nullptr;        // its rows are compared by the caller
     }
-    static_assert(sizeof(grins_racipe_ranges) == 152, "grins_racipe_ranges has no padding bytes");
+    static_assert(sizeof(grins_racipe_ranges) == 160, "grins_racipe_ranges has no padding bytes");
     return std::memcmp(&x, &y, sizeof(x)) == 0;
 }
 
@@ -712,9 +715,102 @@ double class_median(int na, int ni, const grins_racipe_ranges &r, double m0)
     return m;
 }
 
+// Rows of a per-parameter table: the constraints stated with
+// grins_param_range in grins_racipe.h.
+grins_status check_param_table(const grins_racipe *h, const grins_racipe_ranges &r)
+{
+    const int N = h->N, E = h->E;
+    const bool strat = r.lhs_sets > 0 || r.sobol != GRINS_SOBOL_OFF;
+    for (int d = 0; d < 2 * N + 3 * E; ++d) {
+        const grins_param_range &p = r.param_ranges[d];
+        const bool cont = d < 2 * N || (d >= 2 * N + E && d < 2 * N + 2 * E);
+        if (!(std::isfinite(p.lo) && std::isfinite(p.hi) && p.lo > 0.0 && p.lo <= p.hi) || p.reserved != 0)
+            return fail(GRINS_E_INVALID_ARG, "param_ranges: row %d needs 0 < lo <= hi and reserved 0", d);
+        if (!cont && p.dist != GRINS_DIST_TABLE1)
+            return fail(GRINS_E_INVALID_ARG, "param_ranges: row %d (threshold or Hill coefficient) takes dist 0", d);
+        if (p.dist < GRINS_DIST_TABLE1 || p.dist > GRINS_DIST_LOGNORMAL)
+            return fail(GRINS_E_INVALID_ARG, "param_ranges: row %d has unknown distribution %d", d, p.dist);
+        if (strat && p.dist > GRINS_DIST_LOGUNIFORM)
+            return fail(GRINS_E_INVALID_ARG, "param_ranges: row %d: stratified sets take Table 1 and log-uniform draws only", d);
+        if (d >= 2 * N + E && d < 2 * N + 2 * E) {
+            const bool act = h->sign[d - 2 * N - E] > 0;
+            if (act ? p.lo < 1.0 : p.hi > 1.0)
+                return fail(GRINS_E_INVALID_ARG, "param_ranges: row %d: fold change on the wrong side of 1", d);
+        }
+        if (d >= 2 * N + 2 * E && (p.lo != std::floor(p.lo) || p.hi != std::floor(p.hi) || p.hi > 255.0))
+            return fail(GRINS_E_INVALID_ARG, "param_ranges: row %d: Hill coefficients are integers in [1, 255]", d);
+    }
+    return GRINS_OK;
+}
+
+// A continuous parameter from row p (G, k or an activating lambda), or an
+// inhibiting lambda (inverse range under Table 1).
+double row_draw(const grins_param_range &p, bool inh, uint64_t x)
+{
+    if (inh && p.dist == GRINS_DIST_TABLE1) return 1.0 / span_map(1.0 / p.hi, 1.0 / p.lo, unit_double(x));
+    return dist_draw(p.dist, p.lo, p.hi, x);
+}
+
+// Per-node medians of a per-parameter table (the definition stated with
+// grins_racipe_node_medians): M0_j from node j's rows, then M_j with one
+// factor per in-edge of j.
+void table_medians(const grins_racipe *h, const grins_racipe_ranges &r, std::vector<double> &M)
+{
+    const int N = h->N, E = h->E, K = r.median_samples;
+    const grins_param_range *P = r.param_ranges;
+    std::vector<double> M0((size_t)N), v((size_t)K);
+    for (int j = 0; j < N; ++j) {
+        const MedianStream ms{(1ull << 63) + 2ull * (uint64_t)j};
+        for (int s = 0; s < K; ++s)
+            v[(size_t)s] = row_draw(P[j], false, ms.draw(s, 0)) / row_draw(P[N + j], false, ms.draw(s, 1));
+        M0[(size_t)j] = median_sorted(v);
+    }
+    M = M0;
+    if (r.median_mode != GRINS_MEDIAN_PER_INDEGREE) return;
+    for (int j = 0; j < N; ++j) {
+        std::vector<int> in;
+        for (int e = 0; e < E; ++e)
+            if (h->dst[e] == j) in.push_back(e);
+        if (in.empty()) continue;
+        const MedianStream ms{(1ull << 63) + 2ull * (uint64_t)j + 1ull};
+        for (int s = 0; s < K; ++s) {
+            double level = row_draw(P[j], false, ms.draw(s, 0)) / row_draw(P[N + j], false, ms.draw(s, 1));
+            for (size_t q = 0; q < in.size(); ++q) {
+                const int e = in[q], src = h->src[e];
+                const bool act = h->sign[e] > 0;
+                const uint64_t d = 2 + 5 * (uint64_t)q;
+                const double Gs = row_draw(P[src], false, ms.draw(s, d));
+                const double ks = row_draw(P[N + src], false, ms.draw(s, d + 1));
+                const grins_param_range &pt = P[2 * N + e], &pl = P[2 * N + E + e], &pn = P[2 * N + 2 * E + e];
+                const double T = span_map(pt.lo, pt.hi, unit_double(ms.draw(s, d + 2))) * M0[(size_t)src];
+                const double lam = row_draw(pl, !act, ms.draw(s, d + 3));
+                const int n = unit_int(ms.draw(s, d + 4), (int32_t)pn.lo, (int32_t)pn.hi - (int32_t)pn.lo + 1);
+                level = level * hill_factor(act, Gs / ks, T, (double)n, lam);
+            }
+            v[(size_t)s] = level;
+        }
+        M[(size_t)j] = median_sorted(v);
+    }
+}
+
 grins_status ensure_medians(grins_racipe *h, const grins_racipe_ranges &r)
 {
-    if (h->median_valid && same_ranges(h->median_ranges, r)) return GRINS_OK;
+    if (r.param_ranges) {
+        grins_status st = check_param_table(h, r);
+        if (st != GRINS_OK) return st;
+        const size_t D = (size_t)(2 * h->N + 3 * h->E);
+        const bool same_rows = h->median_table.size() == D &&
+                               std::memcmp(h->median_table.data(), r.param_ranges, D * sizeof(grins_param_range)) == 0;
+        if (h->median_valid && same_rows && same_ranges(h->median_ranges, r)) return GRINS_OK;
+        table_medians(h, r, h->node_median);
+        h->median_table.assign(r.param_ranges, r.param_ranges + D);
+        h->median_ranges = r;
+        h->median_valid = true;
+        h->median_uploaded = false;
+        return GRINS_OK;
+    }
+    if (h->median_valid && h->median_table.empty() && same_ranges(h->median_ranges, r)) return GRINS_OK;
+    h->median_table.clear();
     const double M0 = class_median(0, 0, r, 0.0);
     h->node_median.assign(h->N, M0);
     if (r.median_mode == GRINS_MEDIAN_PER_INDEGREE) {
@@ -855,22 +951,35 @@ extern "C" grins_status grins_racipe_sample_params(grins_racipe_t h, const grins
                     (long long)set0, (long long)(set0 + n_sets), (long long)rr.lhs_sets);
     a.li_min = rr.lam_inh_min; a.li_max = rr.lam_inh_max;
     a.params = static_cast<unsigned char *>(d_params);
+    // tables the kernel reads besides the parameters: Sobol direction
+    // numbers and per-parameter rows, staged in one stream-ordered buffer
+    const int D = 2 * h->N + 3 * h->E;
+    std::vector<uint32_t> tab;
     if (rr.sobol != GRINS_SOBOL_OFF && n_sets > 0) {
         if (set0 + n_sets > (int64_t(1) << 32))
             return fail(GRINS_E_INVALID_ARG, "sample_params: Sobol sets beyond 2^32");
-        const int D = 2 * h->N + 3 * h->E;
-        std::vector<uint32_t> tab;
         s = sobol_table(rr, D, seed, tab);
         if (s != GRINS_OK) return s;
-        void *d_tab = nullptr;
-        CUDA_TRY(cudaMallocAsync(&d_tab, sizeof(uint32_t) * tab.size(), st), "sample_params: Sobol table");
-        cudaError_t e = cudaMemcpyAsync(d_tab, tab.data(), sizeof(uint32_t) * tab.size(), cudaMemcpyHostToDevice, st);
-        a.sobol_v = static_cast<const uint32_t *>(d_tab);
-        a.sobol_dims = D;
+    }
+    const size_t tab_bytes = (sizeof(uint32_t) * tab.size() + 15) / 16 * 16;
+    const size_t row_bytes = rr.param_ranges ? sizeof(grins_param_range) * (size_t)D : 0;
+    if (n_sets > 0 && tab_bytes + row_bytes > 0) {
+        std::vector<unsigned char> blob(tab_bytes + row_bytes, 0);
+        if (!tab.empty()) std::memcpy(blob.data(), tab.data(), sizeof(uint32_t) * tab.size());
+        if (row_bytes) std::memcpy(blob.data() + tab_bytes, rr.param_ranges, row_bytes);
+        void *d_blob = nullptr;
+        CUDA_TRY(cudaMallocAsync(&d_blob, blob.size(), st), "sample_params: table buffer");
+        cudaError_t e = cudaMemcpyAsync(d_blob, blob.data(), blob.size(), cudaMemcpyHostToDevice, st);
+        unsigned char *base = static_cast<unsigned char *>(d_blob);
+        if (!tab.empty()) {
+            a.sobol_v = reinterpret_cast<const uint32_t *>(base);
+            a.sobol_dims = D;
+        }
+        if (row_bytes) a.prange = reinterpret_cast<const grins_param_range *>(base + tab_bytes);
         if (e == cudaSuccess) e = launch_sample_params(a, st);
-        const cudaError_t ef = cudaFreeAsync(d_tab, st);
-        CUDA_TRY(e, "sample_params: Sobol launch");
-        CUDA_TRY(ef, "sample_params: Sobol table");
+        const cudaError_t ef = cudaFreeAsync(d_blob, st);
+        CUDA_TRY(e, "sample_params: launch");
+        CUDA_TRY(ef, "sample_params: table buffer");
     } else {
         CUDA_TRY(launch_sample_params(a, st), "sample_params: launch");
     }

@@ -66,6 +66,7 @@ struct SampleArgs {
     const uint32_t *sobol_v;                    // non-null: Sobol units; [D][32] direction
                                                 // numbers (scrambled), then [D] shifts
     int sobol_dims;                             // D = 2N + 3E
+    const grins_param_range *prange;            // non-null: per-parameter rows [2N + 3E]
     double li_min, li_max;                      // inhibiting lambda range (non-Table-1 draws)
     unsigned char *params;
 };

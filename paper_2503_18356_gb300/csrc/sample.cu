@@ -87,6 +87,41 @@ __device__ __forceinline__ double draw_unit(const SampleArgs &a, uint64_t d, uin
     return __ddiv_rn(__dadd_rn((double)p, unit_double(x)), (double)a.lhs_sets);
 }
 
+// Draw d of a set from its per-parameter row (grins_param_range): G, k and
+// lambda by the row's distribution (an inhibiting lambda under Table 1 in
+// the inverse range), T as the row's multiplier range times the source's
+// median, n uniform over the row's integers (stratified: floor(u count)).
+__device__ __forceinline__ void row_draw(const SampleArgs &a, int d, double u, uint64_t x, double *G, double *k,
+                                         double *T, double *lam, uint8_t *nn)
+{
+    const int N = a.L.N, E = a.L.E;
+    const grins_param_range p = a.prange[d];
+    if (d < 2 * N) {
+        const double v = p.dist ? dist_draw(p.dist, p.lo, p.hi, u, x) : affine_rn(p.lo, __dsub_rn(p.hi, p.lo), u);
+        if (d < N) G[d] = v; else k[d - N] = v;
+    } else if (d < 2 * N + E) {
+        const int e = d - 2 * N;
+        T[e] = __dmul_rn(affine_rn(p.lo, __dsub_rn(p.hi, p.lo), u), a.edge_median[e]);
+    } else if (d < 2 * N + 2 * E) {
+        const int e = d - 2 * N - E;
+        if (p.dist) lam[e] = dist_draw(p.dist, p.lo, p.hi, u, x);
+        else if (a.edge_sign[e] > 0) lam[e] = affine_rn(p.lo, __dsub_rn(p.hi, p.lo), u);
+        else {
+            const double vlo = __ddiv_rn(1.0, p.hi);
+            lam[e] = __ddiv_rn(1.0, affine_rn(vlo, __dsub_rn(__ddiv_rn(1.0, p.lo), vlo), u));
+        }
+    } else {
+        const int e = d - 2 * N - 2 * E;
+        const int lo = (int)p.lo, count = (int)p.hi - lo + 1;
+        if (a.lhs_sets > 0 || a.sobol_v) {
+            const int m = (int)__dmul_rn(u, (double)count);
+            nn[e] = (uint8_t)(lo + (m < count ? m : count - 1));
+        } else {
+            nn[e] = (uint8_t)unit_int(x, lo, count);
+        }
+    }
+}
+
 // OTHER: some class uses a distribution besides Table 1's (a separate
 // instantiation, so that the Table 1 kernel carries no log, exp or cos).
 template <bool OTHER>
@@ -114,6 +149,10 @@ __global__ void sample_params_kernel(SampleArgs a)
             if (d >= n_draws) break;
             const uint64_t x = r.v[w];
             const double u = OTHER ? draw_unit(a, (uint64_t)d, s, x) : unit_double(x);
+            if (OTHER && a.prange) {
+                row_draw(a, d, u, x, G, k, T, lam, nn);
+                continue;
+            }
             if (d < N) {
                 G[d] = OTHER && a.dist_G ? dist_draw(a.dist_G, a.G_min, a.G_hi, u, x) : affine_rn(a.G_min, a.G_span, u);
             } else if (d < 2 * N) {
@@ -178,7 +217,7 @@ cudaError_t launch_sample_params(const SampleArgs &a, cudaStream_t st)
     if (a.n_sets <= 0) return cudaSuccess;
     const int n_draws = 2 * a.L.N + 3 * a.L.E;
     const int64_t work = a.n_sets * ((n_draws + 3) / 4);
-    if (a.dist_G || a.dist_k || a.dist_la || a.dist_li || a.lhs_sets > 0 || a.sobol_v)
+    if (a.dist_G || a.dist_k || a.dist_la || a.dist_li || a.lhs_sets > 0 || a.sobol_v || a.prange)
         sample_params_kernel<true><<<grid_for(work, 256), 256, 0, st>>>(a);
     else
         sample_params_kernel<false><<<grid_for(work, 256), 256, 0, st>>>(a);

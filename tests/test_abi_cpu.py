@@ -78,13 +78,14 @@ def test_defaults_follow_table1(lib):
 
 
 def test_binding_structs_match_the_header_sizes(lib):
-    # the library asserts sizeof(grins_racipe_ranges) == 152 with no padding
-    # (its median cache compares the struct bytewise); the ctypes mirror
-    # must have the same size and field order
+    # the library asserts sizeof(grins_racipe_ranges) == 160 with no padding
+    # (its median cache compares the struct bytewise); the ctypes mirrors
+    # must have the same sizes and field order
     from paper_2503_18356_gb300 import api
-    assert C.sizeof(api.grins_racipe_ranges) == 152
-    names = [f[0] for f in api.grins_racipe_ranges._fields_]
+    assert C.sizeof(api.grins_racipe_ranges) == 160
+    assert C.sizeof(api.grins_param_range) == 24 == api.PARAM_RANGE_DTYPE.itemsize
     text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
-    body = re.search(r"typedef struct \{(.*?)\} grins_racipe_ranges;", text, flags=re.S).group(1)
-    declared = [n for decl in body.split(";") for n in re.findall(r"(\w+)\s*(?:,|$)", decl.strip())]
-    assert names == declared
+    for cls, name in ((api.grins_racipe_ranges, "grins_racipe_ranges"), (api.grins_param_range, "grins_param_range")):
+        body = re.search(r"typedef struct \{([^{}]*?)\} " + name + ";", text, flags=re.S).group(1)
+        declared = [n for decl in body.split(";") for n in re.findall(r"(\w+)\s*(?:,|$)", decl.strip())]
+        assert [f[0] for f in cls._fields_] == declared, name

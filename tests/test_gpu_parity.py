@@ -172,6 +172,80 @@ def test_sampler_sobol_refusals():
         h.sample_params(1, 8, 1, set0=(1 << 32) - 4, ranges=R(sobol_table=(poly, m)))
 
 
+def mixed_param_table(h, topo):
+    """The class-equivalent table of the network with rows edited: some G
+    log-uniform or normal over narrowed ranges, some k narrowed, activating
+    fold changes log-uniform, inhibiting ones log-normal, a few threshold
+    multipliers and Hill coefficient ranges changed."""
+    from paper_2503_18356_gb300 import api
+    t = h.param_range_table(api.default_ranges(median_samples=2000))
+    N, E = topo.n_nodes, topo.n_edges
+    t[0] = (api.GRINS_DIST_LOGUNIFORM, 0, 5.0, 50.0)
+    t[3] = (api.GRINS_DIST_NORMAL, 0, 10.0, 20.0)
+    t[N + 1] = (0, 0, 0.5, 0.6)
+    for e in range(0, E, 5):
+        row = 2 * N + E + e
+        t[row]["dist"] = api.GRINS_DIST_LOGUNIFORM if topo.sign[e] > 0 else api.GRINS_DIST_LOGNORMAL
+    t[2 * N + 1] = (0, 0, 0.5, 1.5)
+    t[2 * N + 2 * E + 2] = (0, 0, 2.0, 4.0)
+    return t
+
+
+def test_sampler_per_parameter_table():
+    """A per-parameter range table: per-node medians bit-exact with the
+    oracle's (host FP64 without contraction on both sides); Table 1 rows,
+    thresholds and Hill coefficients bit-exact; rows through the device's
+    log, exp and cos to a few ulp."""
+    from paper_2503_18356_gb300 import api
+    topo = W.net22_workload()["topology"]
+    h = PT.gpu_handle(topo)
+    t = mixed_param_table(h, topo)
+    rg = api.default_ranges(median_samples=2000, param_ranges=t)
+    ro = O.default_ranges(median_samples=2000, param_ranges=t)
+    net = O.Network(*topo.edges())
+    assert np.array_equal(h.node_medians(rg), O.node_medians(net, ro))
+    _, _, p, _ = PT.gpu_sample(h, 23, 300, 2, set0=77, ranges=rg)
+    ref = O.sample_params(net, 23, 300, set0=77, ranges=ro)
+    assert np.array_equal(p.n, ref.n) and np.array_equal(p.T, ref.T)
+    for name in ("G", "k", "lam"):
+        a, b = getattr(p, name), getattr(ref, name)
+        assert np.all(np.abs(a - b) <= 1e-14 * (np.abs(b) + 100.0)), name
+    N = topo.n_nodes
+    plain = [i for i in range(N) if t[i]["dist"] == 0]
+    assert np.array_equal(p.G[:, plain], ref.G[:, plain])
+    # under a Latin hypercube, Table 1 rows stay bit-exact
+    t2 = h.param_range_table(api.default_ranges(median_samples=2000))
+    t2[N + 4] = (0, 0, 0.2, 0.3)
+    _, _, p2, _ = PT.gpu_sample(h, 5, 64, 1, ranges=api.default_ranges(median_samples=2000, lhs_sets=64,
+                                                                     param_ranges=t2))
+    ref2 = O.sample_params(net, 5, 64, ranges=O.default_ranges(median_samples=2000, lhs_sets=64,
+                                                              param_ranges=t2))
+    for f in ("G", "k", "T", "lam", "n"):
+        assert np.array_equal(getattr(p2, f), getattr(ref2, f)), f
+
+
+def test_sampler_per_parameter_table_refusals():
+    from paper_2503_18356_gb300 import api
+    topo = W.net22_workload()["topology"]
+    h = PT.gpu_handle(topo)
+    N, E = topo.n_nodes, topo.n_edges
+    inh = int(np.flatnonzero(topo.sign < 0)[0])
+    edits = [(2 * N, (1, 0, 0.02, 1.98)),               # threshold row with a distribution
+             (2 * N + E + inh, (0, 0, 0.5, 2.0)),       # inhibiting fold change above 1
+             (2 * N + 2 * E, (0, 0, 1.5, 3.0)),         # non-integer Hill coefficient
+             (0, (0, 0, 50.0, 5.0)),                    # lo > hi
+             (1, (0, 7, 1.0, 2.0))]                     # reserved not 0
+    for row, val in edits:
+        t = h.param_range_table()
+        t[row] = val
+        with pytest.raises(api.GrinsError):
+            h.sample_params(1, 4, 1, ranges=api.default_ranges(param_ranges=t))
+    t = h.param_range_table()
+    t[0] = (api.GRINS_DIST_NORMAL, 0, 1.0, 100.0)
+    with pytest.raises(api.GrinsError):
+        h.sample_params(1, 4, 1, ranges=api.default_ranges(param_ranges=t, lhs_sets=10))
+
+
 # ----------------------------------------------------------------- dedupe
 def test_unique_states_bit_exact_on_given_states():
     topo = W.random_network(3, 4, 8, 4, 0)

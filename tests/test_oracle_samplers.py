@@ -249,3 +249,86 @@ def test_sobol_sets_one_value_per_stratum():
     a = O.sample_params(NET, 13, S // 2, set0=0, ranges=r)
     b = O.sample_params(NET, 13, S // 2, set0=S // 2, ranges=r)
     assert np.array_equal(p.G, np.concatenate([a.G, b.G]))
+
+
+# ---------------------------------------------------------------- per-parameter range table
+def class_table(net, r):
+    """The per-parameter rows that the class fields of r describe."""
+    N, E = net.n_nodes, net.n_edges
+    t = np.zeros(2 * N + 3 * E, dtype=O.PARAM_ROW)
+    t[:N] = (r.dist_G, 0, r.G_min, r.G_max)
+    t[N:2 * N] = (r.dist_k, 0, r.k_min, r.k_max)
+    t[2 * N:2 * N + E] = (0, 0, r.thr_lo, r.thr_hi)
+    for e in range(E):
+        t[2 * N + E + e] = ((r.dist_lam_act, 0, r.lam_act_min, r.lam_act_max) if net.sign[e] > 0
+                            else (r.dist_lam_inh, 0, r.lam_inh_min, r.lam_inh_max))
+    t[2 * N + 2 * E:] = (0, 0, r.n_min, r.n_max)
+    return t
+
+
+@pytest.mark.parametrize("lhs", [0, 64])
+def test_class_equivalent_table_reproduces_the_class_draws(lhs):
+    # same draws and units: G, k, lambda, n identical; T differs only by the
+    # per-node median replacing the class median
+    rc = O.default_ranges(median_samples=2000, lhs_sets=lhs)
+    rt = O.default_ranges(median_samples=2000, lhs_sets=lhs, param_ranges=class_table(NET, rc))
+    a, b = O.sample_params(NET, 4, 64, ranges=rc), O.sample_params(NET, 4, 64, ranges=rt)
+    for f in ("G", "k", "lam", "n"):
+        assert np.array_equal(getattr(a, f), getattr(b, f)), f
+    Mc, Mt = O.node_medians(NET, rc), O.node_medians(NET, rt)
+    ratio = b.T / a.T
+    assert np.allclose(ratio, (Mt / Mc)[NET.src][None, :], rtol=1e-14)
+
+
+def test_degenerate_rows_fix_the_per_node_medians():
+    # every row a point: M0_j = G_j / k_j exactly, and a regulated node's
+    # median is its level G_j / k_j times the Hill factor of each in-edge
+    # (Eq. 1, 2) with the source at G_s / k_s and T = multiplier x M0_s
+    net = O.Network(3, np.array([0, 1, 0]), np.array([1, 2, 2]), np.array([1, -1, -1]))
+    N, E = 3, 3
+    t = np.zeros(2 * N + 3 * E, dtype=O.PARAM_ROW)
+    G, k = [10.0, 20.0, 30.0], [0.5, 0.25, 1.0]
+    mult, lam, n = [0.5, 1.5, 1.0], [4.0, 0.1, 0.5], [2, 3, 1]
+    for i in range(N):
+        t[i] = (0, 0, G[i], G[i])
+        t[N + i] = (0, 0, k[i], k[i])
+    for e in range(E):
+        t[2 * N + e] = (0, 0, mult[e], mult[e])
+        t[2 * N + E + e] = (0, 0, lam[e], lam[e])
+        t[2 * N + 2 * E + e] = (0, 0, n[e], n[e])
+    r = O.default_ranges(median_samples=101, param_ranges=t)
+    M = O.node_medians(net, r)
+    M0 = np.array(G) / np.array(k)
+
+    def factor(e):
+        s = net.src[e]
+        B, B0 = M0[s], mult[e] * M0[s]
+        h = (B0**n[e] + lam[e] * B**n[e]) / (B0**n[e] + B**n[e])
+        return h / lam[e] if net.sign[e] > 0 else h
+    assert M[0] == M0[0]
+    assert np.isclose(M[1], M0[1] * factor(0), rtol=1e-14)
+    assert np.isclose(M[2], M0[2] * factor(1) * factor(2), rtol=1e-14)
+    # the unregulated mode keeps M0 for every node
+    r1 = O.default_ranges(median_samples=101, median_mode=1, param_ranges=t)
+    assert np.array_equal(O.node_medians(net, r1), M0)
+
+
+def test_per_parameter_distributions_mix():
+    S = 20000
+    r = O.default_ranges(median_samples=2000)
+    t = class_table(NET, r)
+    N = NET.n_nodes
+    t[0] = (1, 0, 5.0, 50.0)          # G_0 log-uniform on [5, 50]
+    t[1] = (2, 0, 10.0, 20.0)         # G_1 normal on [10, 20]
+    t[N + 2] = (0, 0, 0.5, 0.6)       # k_2 uniform on [0.5, 0.6]
+    e_n = 2 * N + 2 * NET.n_edges     # the first edge's Hill coefficient on {2, 3}
+    t[e_n] = (0, 0, 2.0, 3.0)
+    p = O.sample_params(NET, 6, S, ranges=O.default_ranges(median_samples=2000, param_ranges=t))
+    assert stats.kstest(np.log(p.G[:, 0]), stats.uniform(np.log(5), np.log(10)).cdf).pvalue > 1e-3
+    inner = p.G[:, 1][(p.G[:, 1] > 10) & (p.G[:, 1] < 20)]
+    assert stats.kstest(inner, stats.truncnorm(-3, 3, loc=15, scale=10 / 6).cdf).pvalue > 1e-3
+    assert stats.kstest(p.k[:, 2], stats.uniform(0.5, 0.1).cdf).pvalue > 1e-3
+    assert set(np.unique(p.n[:, 0])) == {2, 3}
+    # the untouched rows keep the class draws
+    q = O.sample_params(NET, 6, S, ranges=r)
+    assert np.array_equal(p.G[:, 2:], q.G[:, 2:]) and np.array_equal(p.n[:, 1:], q.n[:, 1:])
