@@ -142,6 +142,13 @@ typedef struct {
                                           class fields above are unused but
                                           median_samples and median_mode), and
                                           the medians are per node (below) */
+    const grins_param_range *ic_ranges;  /* host [N], read during the call, or
+                                          NULL: initial condition of node i as
+                                          a fraction of its maximum G_i / k_i
+                                          drawn by row i's dist over [lo, hi],
+                                          0 <= lo <= hi <= 1 (lo > 0 for the
+                                          log distributions); NULL = uniform
+                                          on [0, 1) (Sec. 2.1.2) */
 } grins_racipe_ranges;
 
 /* Sobol sets (Sec. 2.1.2: the paper's default sampler).  With sobol != 0,

@@ -125,6 +125,7 @@ def lib():
             l.orc_sobol_x.restype = C.c_uint32
             l.orc_node_medians.argtypes = [P(Net), P(Ranges), P(C.c_double)]
             l.orc_sample_ics.argtypes = [C.c_int32, C.c_uint64, C.c_int32, P(C.c_double)]
+            l.orc_sample_ics_ranges.argtypes = [C.c_int32, C.c_uint64, C.c_int32, C.c_void_p, P(C.c_double)]
             l.orc_solve.argtypes = [P(Net), P(Params), P(C.c_double), P(Opts), P(C.c_double),
                                     P(C.c_double)]
             l.orc_solve.restype = Result
@@ -303,9 +304,15 @@ def sobol_x(ranges, seed, d, s):
     return int(lib().orc_sobol_x(C.byref(ranges), C.c_uint64(seed), C.c_uint64(d), C.c_uint64(s)))
 
 
-def sample_ics(n_nodes, seed, n_ics):
+def sample_ics(n_nodes, seed, n_ics, ic_ranges=None):
+    """Unit initial conditions [n_ics, N] (fractions of G/k), uniform on
+    [0, 1) or from per-node PARAM_ROW rows."""
     u = np.zeros((n_ics, n_nodes))
-    lib().orc_sample_ics(n_nodes, C.c_uint64(seed), n_ics, _p(u, C.c_double))
+    if ic_ranges is None:
+        lib().orc_sample_ics(n_nodes, C.c_uint64(seed), n_ics, _p(u, C.c_double))
+    else:
+        rows = np.ascontiguousarray(ic_ranges, dtype=PARAM_ROW)
+        lib().orc_sample_ics_ranges(n_nodes, C.c_uint64(seed), n_ics, rows.ctypes.data, _p(u, C.c_double))
     return u
 
 

@@ -624,6 +624,19 @@ void orc_sample_ics(int32_t n_nodes, uint64_t seed, int32_t n_ics, double *u)
             u[(int64_t)c * n_nodes + i] = orc_u01(draw64(seed, ORC_TAG_ICS, (uint64_t)c, (uint64_t)i));
 }
 
+/* Initial conditions from updated ranges (Sec. 2.1.2: regenerated from the */
+/* range file, with a distribution per node): the same draw as above, the  */
+/* fraction of node i's maximum G_i / k_i taken by row i's distribution    */
+/* over [lo, hi] instead of uniformly over [0, 1).                          */
+void orc_sample_ics_ranges(int32_t n_nodes, uint64_t seed, int32_t n_ics, const orc_param_range *rows, double *u)
+{
+    for (int c = 0; c < n_ics; ++c)
+        for (int i = 0; i < n_nodes; ++i) {
+            uint64_t x = draw64(seed, ORC_TAG_ICS, (uint64_t)c, (uint64_t)i);
+            u[(int64_t)c * n_nodes + i] = param_draw(rows[i].dist, rows[i].lo, rows[i].hi, x);
+        }
+}
+
 /* ------------------------------------------------------------------ */
 /* Dormand-Prince 5(4) (Dormand & Prince 1980, "A family of embedded    */
 /* Runge-Kutta formulae"), seven stages, first-same-as-last.            */

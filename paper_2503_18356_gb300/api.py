@@ -61,7 +61,8 @@ class grins_racipe_ranges(C.Structure):
                 ("sobol", C.c_int32), ("sobol_dims", C.c_int32),
                 ("sobol_poly", C.POINTER(C.c_int64)), ("sobol_m", C.POINTER(C.c_int64)),
                 ("sobol_m_cols", C.c_int32), ("reserved", C.c_int32),
-                ("param_ranges", C.POINTER(grins_param_range))]
+                ("param_ranges", C.POINTER(grins_param_range)),
+                ("ic_ranges", C.POINTER(grins_param_range))]
 
 
 class grins_solver_opts(C.Structure):
@@ -155,12 +156,13 @@ def _check(st):
         raise GrinsError(st, _lib.grins_last_error().decode())
 
 
-def default_ranges(sobol_table=None, param_ranges=None, **over) -> grins_racipe_ranges:
+def default_ranges(sobol_table=None, param_ranges=None, ic_ranges=None, **over) -> grins_racipe_ranges:
     """Table 1's ranges with fields overridden by keyword.  `sobol_table` =
     (poly [D], m [D, cols]) int64 arrays, e.g. workloads.sobol_direction_table(),
     for the Sobol modes (`sobol=GRINS_SOBOL_PLAIN` or `GRINS_SOBOL_SCRAMBLED`);
     `param_ranges` = a PARAM_RANGE_DTYPE array of 2N + 3E rows (see
-    Racipe.param_range_table).  The arrays are kept alive with the struct."""
+    Racipe.param_range_table); `ic_ranges` = N rows for the initial
+    conditions (fractions of G/k).  The arrays are kept alive with the struct."""
     r = grins_racipe_ranges()
     _lib.grins_racipe_default_ranges(C.byref(r))
     for k, v in over.items():
@@ -170,6 +172,10 @@ def default_ranges(sobol_table=None, param_ranges=None, **over) -> grins_racipe_
         rows = np.ascontiguousarray(param_ranges, dtype=PARAM_RANGE_DTYPE)
         keep.append(rows)
         r.param_ranges = rows.ctypes.data_as(C.POINTER(grins_param_range))
+    if ic_ranges is not None:
+        icr = np.ascontiguousarray(ic_ranges, dtype=PARAM_RANGE_DTYPE)
+        keep.append(icr)
+        r.ic_ranges = icr.ctypes.data_as(C.POINTER(grins_param_range))
     if sobol_table is not None:
         poly = np.ascontiguousarray(sobol_table[0], dtype=np.int64)
         m = np.ascontiguousarray(sobol_table[1], dtype=np.int64)

@@ -129,6 +129,7 @@ extern "C" void grins_racipe_default_ranges(grins_racipe_ranges *r)
     r->sobol_m_cols = 0;
     r->reserved = 0;
     r->param_ranges = nullptr;
+    r->ic_ranges = nullptr;
 }
 
 extern "C" void grins_solver_default_opts(grins_solver_opts *o)
@@ -656,8 +657,9 @@ bool same_ranges(const grins_racipe_ranges &a, const grins_racipe_ranges &b)
         r->sobol_m_cols = 0;
         r->reserved = 0;
         r->param_ranges = nullptr;        // its rows are compared by the caller
+        r->ic_ranges = nullptr;           // initial conditions do not enter the medians
     }
-    static_assert(sizeof(grins_racipe_ranges) == 160, "grins_racipe_ranges has no padding bytes");
+    static_assert(sizeof(grins_racipe_ranges) == 168, "grins_racipe_ranges has no padding bytes");
     return std::memcmp(&x, &y, sizeof(x)) == 0;
 }
 
@@ -983,7 +985,29 @@ extern "C" grins_status grins_racipe_sample_params(grins_racipe_t h, const grins
     } else {
         CUDA_TRY(launch_sample_params(a, st), "sample_params: launch");
     }
-    if (d_ic_unit && n_ics > 0) CUDA_TRY(launch_sample_ics(h->N, seed, n_ics, d_ic_unit, st), "sample_params: IC launch");
+    if (d_ic_unit && n_ics > 0) {
+        if (!rr.ic_ranges) {
+            CUDA_TRY(launch_sample_ics(h->N, seed, n_ics, d_ic_unit, nullptr, st), "sample_params: IC launch");
+        } else {
+            for (int i = 0; i < h->N; ++i) {
+                const grins_param_range &p = rr.ic_ranges[i];
+                const bool logd = p.dist == GRINS_DIST_LOGUNIFORM || p.dist == GRINS_DIST_LOGNORMAL;
+                if (p.dist < GRINS_DIST_TABLE1 || p.dist > GRINS_DIST_LOGNORMAL || p.reserved != 0 ||
+                    !(p.lo >= 0.0 && p.lo <= p.hi && p.hi <= 1.0) || (logd && !(p.lo > 0.0)))
+                    return fail(GRINS_E_INVALID_ARG, "ic_ranges: row %d needs 0 <= lo <= hi <= 1 (lo > 0 for log "
+                                "distributions), a known dist and reserved 0", i);
+            }
+            void *d_rows = nullptr;
+            const size_t bytes = sizeof(grins_param_range) * (size_t)h->N;
+            CUDA_TRY(cudaMallocAsync(&d_rows, bytes, st), "sample_params: IC rows");
+            cudaError_t e = cudaMemcpyAsync(d_rows, rr.ic_ranges, bytes, cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess)
+                e = launch_sample_ics(h->N, seed, n_ics, d_ic_unit, static_cast<const grins_param_range *>(d_rows), st);
+            const cudaError_t ef = cudaFreeAsync(d_rows, st);
+            CUDA_TRY(e, "sample_params: IC launch");
+            CUDA_TRY(ef, "sample_params: IC rows");
+        }
+    }
     return GRINS_OK;
 }
 

@@ -73,7 +73,8 @@ struct SampleArgs {
 
 #ifndef __CUDACC_RTC__
 cudaError_t launch_sample_params(const SampleArgs &a, cudaStream_t st);
-cudaError_t launch_sample_ics(int N, uint64_t seed, int n_ics, double *u, cudaStream_t st);
+cudaError_t launch_sample_ics(int N, uint64_t seed, int n_ics, double *u, const grins_param_range *rows,
+                              cudaStream_t st);
 #endif
 
 // ------------------------------------------------------------- integrator

@@ -185,7 +185,9 @@ __global__ void sample_params_kernel(SampleArgs a)
     }
 }
 
-__global__ void sample_ics_kernel(int N, uint64_t seed, int n_ics, double *u)
+// Unit initial conditions: u in [0, 1) per (IC, node), or, with rows, the
+// fraction of G/k that row i's distribution gives over [lo, hi].
+__global__ void sample_ics_kernel(int N, uint64_t seed, int n_ics, double *u, const grins_param_range *rows)
 {
     const int blocks_per_ic = (N + 3) / 4;
     const int64_t total = (int64_t)n_ics * blocks_per_ic;
@@ -197,7 +199,15 @@ __global__ void sample_ics_kernel(int N, uint64_t seed, int n_ics, double *u)
 #pragma unroll
         for (int w = 0; w < 4; ++w) {
             const int i = 4 * c + w;
-            if (i < N) u[(int64_t)ic * N + i] = unit_double(r.v[w]);
+            if (i >= N) continue;
+            const double v = unit_double(r.v[w]);
+            if (!rows) {
+                u[(int64_t)ic * N + i] = v;
+            } else {
+                const grins_param_range p = rows[i];
+                u[(int64_t)ic * N + i] = p.dist ? dist_draw(p.dist, p.lo, p.hi, v, r.v[w])
+                                                : affine_rn(p.lo, __dsub_rn(p.hi, p.lo), v);
+            }
         }
     }
 }
@@ -224,11 +234,12 @@ cudaError_t launch_sample_params(const SampleArgs &a, cudaStream_t st)
     return cudaGetLastError();
 }
 
-cudaError_t launch_sample_ics(int N, uint64_t seed, int n_ics, double *u, cudaStream_t st)
+cudaError_t launch_sample_ics(int N, uint64_t seed, int n_ics, double *u, const grins_param_range *rows,
+                              cudaStream_t st)
 {
     if (n_ics <= 0) return cudaSuccess;
     const int64_t work = (int64_t)n_ics * ((N + 3) / 4);
-    sample_ics_kernel<<<grid_for(work, 256), 256, 0, st>>>(N, seed, n_ics, u);
+    sample_ics_kernel<<<grid_for(work, 256), 256, 0, st>>>(N, seed, n_ics, u, rows);
     return cudaGetLastError();
 }
 

@@ -78,11 +78,11 @@ def test_defaults_follow_table1(lib):
 
 
 def test_binding_structs_match_the_header_sizes(lib):
-    # the library asserts sizeof(grins_racipe_ranges) == 160 with no padding
+    # the library asserts sizeof(grins_racipe_ranges) == 168 with no padding
     # (its median cache compares the struct bytewise); the ctypes mirrors
     # must have the same sizes and field order
     from paper_2503_18356_gb300 import api
-    assert C.sizeof(api.grins_racipe_ranges) == 160
+    assert C.sizeof(api.grins_racipe_ranges) == 168
     assert C.sizeof(api.grins_param_range) == 24 == api.PARAM_RANGE_DTYPE.itemsize
     text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
     for cls, name in ((api.grins_racipe_ranges, "grins_racipe_ranges"), (api.grins_param_range, "grins_param_range")):

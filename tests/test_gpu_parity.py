@@ -246,6 +246,35 @@ def test_sampler_per_parameter_table_refusals():
         h.sample_params(1, 4, 1, ranges=api.default_ranges(param_ranges=t, lhs_sets=10))
 
 
+def test_sampler_ic_ranges():
+    """Initial conditions from per-node rows (fractions of G/k): uniform rows
+    bit-exact with the oracle's, other distributions to a few ulp; rows the
+    sampler refuses."""
+    from paper_2503_18356_gb300 import api
+    topo = W.net22_workload()["topology"]
+    h = PT.gpu_handle(topo)
+    N = topo.n_nodes
+    rows = np.zeros(N, dtype=api.PARAM_RANGE_DTYPE)
+    rows[:] = (0, 0, 0.0, 1.0)
+    rows[1] = (0, 0, 0.25, 0.5)
+    rows[2] = (api.GRINS_DIST_LOGUNIFORM, 0, 0.01, 1.0)
+    rows[3] = (api.GRINS_DIST_NORMAL, 0, 0.2, 0.8)
+    rows[4] = (api.GRINS_DIST_LOGNORMAL, 0, 0.05, 0.5)
+    _, ic = h.sample_params(12, 4, 3000, ranges=api.default_ranges(ic_ranges=rows))
+    ic = ic.cpu().numpy()
+    ref = O.sample_ics(N, 12, 3000, ic_ranges=rows)
+    plain = [i for i in range(N) if rows[i]["dist"] == 0]
+    assert np.array_equal(ic[:, plain], ref[:, plain])
+    assert np.all(np.abs(ic - ref) <= 1e-14 * (np.abs(ref) + 1.0))
+    _, ic0 = h.sample_params(12, 4, 3000)
+    assert np.array_equal(ic[:, 0], ic0.cpu().numpy()[:, 0])
+    for bad in ((0, 0, 0.5, 1.5), (api.GRINS_DIST_LOGUNIFORM, 0, 0.0, 1.0), (0, 0, 0.6, 0.4), (9, 0, 0.1, 0.2)):
+        r2 = rows.copy()
+        r2[5] = bad
+        with pytest.raises(api.GrinsError):
+            h.sample_params(12, 4, 8, ranges=api.default_ranges(ic_ranges=r2))
+
+
 # ----------------------------------------------------------------- dedupe
 def test_unique_states_bit_exact_on_given_states():
     topo = W.random_network(3, 4, 8, 4, 0)

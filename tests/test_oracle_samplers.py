@@ -332,3 +332,24 @@ def test_per_parameter_distributions_mix():
     # the untouched rows keep the class draws
     q = O.sample_params(NET, 6, S, ranges=r)
     assert np.array_equal(p.G[:, 2:], q.G[:, 2:]) and np.array_equal(p.n[:, 1:], q.n[:, 1:])
+
+
+# ---------------------------------------------------------------- initial-condition ranges
+def test_ic_ranges_map_the_same_draws():
+    # uniform rows map the default unit draw u to lo + (hi - lo) u; a
+    # log-uniform row follows its distribution; rows of [0, 1] reproduce
+    # the default
+    N, I = 5, 20000
+    u = O.sample_ics(N, 3, I)
+    rows = np.zeros(N, dtype=O.PARAM_ROW)
+    rows[:] = (0, 0, 0.0, 1.0)
+    assert np.array_equal(O.sample_ics(N, 3, I, ic_ranges=rows), u)
+    rows[1] = (0, 0, 0.25, 0.5)
+    rows[2] = (1, 0, 0.01, 1.0)
+    rows[3] = (2, 0, 0.2, 0.8)
+    v = O.sample_ics(N, 3, I, ic_ranges=rows)
+    assert np.array_equal(v[:, [0, 4]], u[:, [0, 4]])
+    assert np.array_equal(v[:, 1], 0.25 + (0.5 - 0.25) * u[:, 1])
+    assert stats.kstest(np.log(v[:, 2]), stats.uniform(np.log(0.01), -np.log(0.01)).cdf).pvalue > 1e-3
+    inner = v[:, 3][(v[:, 3] > 0.2) & (v[:, 3] < 0.8)]
+    assert stats.kstest(inner, stats.truncnorm(-3, 3, loc=0.5, scale=0.1).cdf).pvalue > 1e-3
