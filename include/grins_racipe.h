@@ -410,7 +410,9 @@ grins_status grins_racipe_server_create(const grins_server_config *c, grins_raci
 
 /* Queues a request: parameter sets 0 .. n_sets-1 of `seed` (ranges r, NULL
  * = defaults) with n_ics ICs on network `net`, integrated with o (no time
- * grid) and deduplicated with dedupe_tol.  Returns at once with its id.
+ * grid) and deduplicated with dedupe_tol.  Returns at once with its id; the
+ * tables r points to (Sobol, per-parameter and initial-condition rows) are
+ * copied, so the caller may free them on return.
  * Errors: GRINS_E_INVALID_ARG for bad arguments, GRINS_E_BUDGET when the
  * request alone needs more than the whole HBM budget. */
 grins_status grins_racipe_server_submit(grins_racipe_server_t sv, grins_racipe_t net,

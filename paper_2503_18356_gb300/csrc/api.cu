@@ -1796,6 +1796,10 @@ struct ServerRequest {
     int64_t id = 0;
     grins_racipe *net = nullptr;
     grins_racipe_ranges ranges{};
+    // the request's own copies of the tables `ranges` points to (the
+    // caller's may be gone by the time the worker samples)
+    std::vector<int64_t> sobol_poly, sobol_m;
+    std::vector<grins_param_range> param_rows, ic_rows;
     uint64_t seed = 0;
     int64_t n_sets = 0;
     int32_t n_ics = 0;
@@ -2061,6 +2065,20 @@ extern "C" grins_status grins_racipe_server_submit(grins_racipe_server_t sv, gri
     auto req = std::unique_ptr<ServerRequest>(new (std::nothrow) ServerRequest());
     if (!req) return fail(GRINS_E_NOMEM, "server_submit: host allocation failed");
     req->net = net; req->ranges = rr; req->seed = seed; req->n_sets = n_sets; req->n_ics = n_ics;
+    if (rr.sobol != GRINS_SOBOL_OFF && rr.sobol_poly && rr.sobol_m && rr.sobol_dims > 0 && rr.sobol_m_cols > 0) {
+        req->sobol_poly.assign(rr.sobol_poly, rr.sobol_poly + rr.sobol_dims);
+        req->sobol_m.assign(rr.sobol_m, rr.sobol_m + (size_t)rr.sobol_dims * (size_t)rr.sobol_m_cols);
+        req->ranges.sobol_poly = req->sobol_poly.data();
+        req->ranges.sobol_m = req->sobol_m.data();
+    }
+    if (rr.param_ranges) {
+        req->param_rows.assign(rr.param_ranges, rr.param_ranges + 2 * net->N + 3 * net->E);
+        req->ranges.param_ranges = req->param_rows.data();
+    }
+    if (rr.ic_ranges) {
+        req->ic_rows.assign(rr.ic_ranges, rr.ic_ranges + net->N);
+        req->ranges.ic_ranges = req->ic_rows.data();
+    }
     req->opts = *o; req->dedupe_tol = dedupe_tol;
     req->bytes = request_bytes(*req);
     if (req->bytes > sv->budget)

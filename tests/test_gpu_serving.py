@@ -159,3 +159,47 @@ def test_requests_on_compiled_kernels():
         diff = g["status"] != o["status"]
         seen = set(g["status"][diff].tolist()) | set(o["status"][diff].tolist())
         assert seen <= {O.CONVERGED, O.TEND, O.POLISH_FAIL}, seen
+
+
+def test_request_keeps_its_own_copy_of_the_ranges_tables():
+    """A request with Sobol sets, a per-parameter table and initial-condition
+    rows: the caller overwrites its arrays right after submitting, and the
+    served results still match the same work run directly on the handle
+    (the server may run another kernel for a request this small, so the
+    polished states agree to the polish tolerance, not bit for bit)."""
+    from paper_2503_18356_gb300 import api
+    r = _requests(1)[0]
+    net, S, I = r["net"], r["S"], r["I"]
+    poly, m = W.sobol_direction_table()
+    rows = net.param_range_table()
+    rows[0] = (api.GRINS_DIST_LOGUNIFORM, 0, 5.0, 50.0)
+    icr = np.zeros(net.n_nodes, dtype=api.PARAM_RANGE_DTYPE)
+    icr[:] = (0, 0, 0.1, 0.9)
+
+    def ranges(poly, m, rows, icr):
+        return api.default_ranges(sobol=api.GRINS_SOBOL_SCRAMBLED, sobol_table=(poly, m), param_ranges=rows,
+                                  ic_ranges=icr)
+
+    params, ic = net.sample_params(r["seed"], S, I, ranges=ranges(poly, m, rows, icr))
+    out = net.integrate(params, ic)
+    _, nu = net.unique_states(params, out["states"], out["status"])
+    direct = dict(states=out["states"].cpu().numpy(), status=out["status"].cpu().numpy(), n_unique=nu.cpu().numpy())
+
+    p2, m2, rows2, icr2 = poly.copy(), m.copy(), rows.copy(), icr.copy()
+    rr = ranges(p2, m2, rows2, icr2)
+    sv = api.Server(max_inflight=4)
+    rid = sv.submit(net, r["seed"], S, I, ranges=rr)
+    p2[:] = 0; m2[:] = 0; rows2["lo"] = -1.0; icr2["hi"] = 7.0       # the caller's arrays change at once
+    info = sv.wait(rid)
+    served = _np(sv.results(rid))
+    print("request", info)
+    both = (served["status"] == 0) & (direct["status"] == 0)
+    assert np.mean(served["status"] == direct["status"]) >= 0.97
+    G, k = (x.cpu().numpy() for x in net.unpack_params(params)[:2])
+    gk = np.broadcast_to((G / k)[:, None, :], direct["states"].shape)
+    d = np.abs(served["states"] - direct["states"])[both]
+    scale = np.maximum(np.abs(direct["states"][both]), 1e-6 * gk[both])
+    assert both.sum() > 0 and np.all(d <= 1e-6 * scale)
+    assert np.mean(served["n_unique"] == direct["n_unique"]) >= 0.95
+    sv.release(rid)
+    sv.close()
