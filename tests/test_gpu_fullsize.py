@@ -105,3 +105,74 @@ def test_net5_full_size_fp32_polish():
 def test_toggle_switch_full_size_fp64():
     """500 sets x 20 ICs of the toggle switch, plain FP64, every set."""
     check_full_size(W.ts_workload(), precision=0, polish=0, n_sample=500, rel_tol=1e-3, normalised=True)
+
+
+def test_levels_full_size_net22():
+    """The levels row on every solve of the full 22-node workload: histogram,
+    boundaries, labels, distinct level states and the multistability
+    histogram bit-exact with the oracle's over all 1,000,000 solves."""
+    from paper_2503_18356_gb300 import api
+    w = W.net22_workload()
+    topo = w["topology"]
+    S, I = w["n_sets"], w["n_ics"]
+    h = PT.gpu_handle(topo)
+    params, ic = h.sample_params(w["param_seed"], S, I)
+    out = h.integrate(params, ic)
+    counts = h.gk_histogram(params, out["states"], out["status"], n_bins=100)
+    torch.cuda.synchronize()
+    c = counts.cpu().numpy().view(np.uint64)
+    bounds = api.level_boundaries(c, half_width=4, max_boundaries=3)
+    lab, ns, mh = h.level_states(params, out["states"], out["status"], bounds, n_bins=100)
+    torch.cuda.synchronize()
+    G, k = (x.cpu().numpy() for x in h.unpack_params(params)[:2])
+    st, stat = out["states"].cpu().numpy(), out["status"].cpu().numpy()
+    assert np.array_equal(c, O.gk_histogram(st, stat, G, k, 100))
+    assert list(bounds) == list(O.level_boundaries(c, m=4, max_b=3))
+    olab, ons, omh = O.level_states(st, stat, G, k, np.asarray(bounds, np.int32), 100)
+    assert np.array_equal(lab.cpu().numpy().view(np.uint64), olab)
+    assert np.array_equal(ns.cpu().numpy(), ons)
+    assert np.array_equal(mh.cpu().numpy().view(np.uint64), omh)
+    assert int(omh.sum()) == S and int(c.sum()) == int((stat == 0).sum()) * topo.n_nodes
+
+
+def is_fixed_point(topo, final, enc01=False):
+    """No node of any state would change under Eq. 3 (ties keep the state):
+    the field J s of every node agrees in sign with the node's state."""
+    N = topo.n_nodes
+    bits = ((final[:, None] >> np.arange(N, dtype=np.uint64)[None, :]) & np.uint64(1)).astype(bool)
+    s = np.where(bits, 1.0, 0.0 if enc01 else -1.0).astype(np.float32)
+    J = np.zeros((N, N), dtype=np.float32)                 # J[src, dst]
+    np.add.at(J, (topo.src, topo.dst), topo.sign.astype(np.float32))
+    field = s @ J
+    return ~np.any((field > 0) & ~bits, axis=1) & ~np.any((field < 0) & bits, axis=1)
+
+
+def test_ising_full_size_net22():
+    """1,000,000 trajectories of the 22-node network, synchronous and
+    asynchronous: every converged final state is a fixed point of Eq. 3;
+    synchronous trajectories spread over the index range, restarted by the
+    oracle from their initial states, and the first asynchronous ones (the
+    node choices are drawn per trajectory index) are bit-exact."""
+    from paper_2503_18356_gb300 import api
+    topo = W.net22_workload()["topology"]
+    net = O.Network(*topo.edges())
+    h = PT.gpu_handle(topo)
+    n, seed = 1_000_000, 31
+    init, _, _ = O.ising_run(net, mode=0, seed=seed, n_traj=n, max_steps=0)   # the initial states
+    for mode, max_steps in ((api.GRINS_ISING_SYNC, 200), (api.GRINS_ISING_ASYNC, 2000)):
+        fin, stp, st = h.ising_run(n, mode=mode, seed=seed, max_steps=max_steps)
+        torch.cuda.synchronize()
+        fin, stp, st = fin.cpu().numpy().view(np.uint64), stp.cpu().numpy(), st.cpu().numpy()
+        conv = st == 0
+        assert conv.mean() > 0.9
+        assert np.all(is_fixed_point(topo, fin[conv])) and not np.any(is_fixed_point(topo, fin[~conv]))
+        assert np.all(stp[~conv] == max_steps)
+        if mode == api.GRINS_ISING_SYNC:
+            pick = sampled_sets(n, 20_000)
+            o = O.ising_run(net, mode=mode, seed=seed, n_traj=len(pick), init=init[pick], max_steps=max_steps)
+            got = (fin[pick], stp[pick], st[pick])
+        else:
+            o = O.ising_run(net, mode=mode, seed=seed, n_traj=3000, max_steps=max_steps)
+            got = (fin[:3000], stp[:3000], st[:3000])
+        for a, b in zip(got, o):
+            assert np.array_equal(a, b), mode
