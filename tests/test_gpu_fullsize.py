@@ -32,13 +32,13 @@ def sampled_sets(S, n):
     return np.unique(np.concatenate([np.linspace(0, S - 1, n).round().astype(np.int64), [S - 1]]))
 
 
-def check_full_size(w, precision, polish, n_sample, rel_tol, normalised):
+def check_full_size(w, precision, polish, n_sample, rel_tol, normalised, method=0):
     topo = w["topology"]
     S, I, N = w["n_sets"], w["n_ics"], topo.n_nodes
     net = O.Network(*topo.edges())
     h = PT.gpu_handle(topo)
     params, ic = h.sample_params(w["param_seed"], S, I)
-    out = h.integrate(params, ic, precision=precision, polish=polish)
+    out = h.integrate(params, ic, precision=precision, polish=polish, method=method)
     sid, nu = h.unique_states(params, out["states"], out["status"])
     torch.cuda.synchronize()
     G, k = (x.cpu().numpy() for x in h.unpack_params(params)[:2])
@@ -71,7 +71,7 @@ def check_full_size(w, precision, polish, n_sample, rel_tol, normalised):
     icn = ic.cpu().numpy()
     assert np.array_equal(icn, O.sample_ics(N, w["param_seed"], I))
     p = O.ParamSet(*(np.concatenate([getattr(r, f) for r in ref_p]) for f in ("G", "k", "T", "lam", "n")))
-    o = O.run_sets_parallel(net, p, icn, threads=PT.THREADS, polish=bool(polish))
+    o = O.run_sets_parallel(net, p, icn, threads=PT.THREADS, polish=bool(polish), method=method)
     g = dict(states=states[pick], status=status[pick])
     c = PT.compare_states(g, o, p, rel_tol, normalised=normalised)
     print(w["topology"].name, "sampled", len(pick), c)
@@ -95,6 +95,13 @@ def check_full_size(w, precision, polish, n_sample, rel_tol, normalised):
 def test_net22_full_size_fp32_polish():
     """100,000 sets x 10 ICs of the 22-node network, FP32 + FP64 polish."""
     check_full_size(W.net22_workload(), precision=1, polish=1, n_sample=120, rel_tol=1e-6, normalised=False)
+
+
+def test_net22_full_size_tsit5_polish():
+    """The same full workload with the paper's Tsitouras 5(4) pair on both
+    sides (FP32 + FP64 polish on the GPU)."""
+    check_full_size(W.net22_workload(), precision=1, polish=1, n_sample=60, rel_tol=1e-6, normalised=False,
+                    method=1)
 
 
 def test_net5_full_size_fp32_polish():

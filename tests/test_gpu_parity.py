@@ -275,6 +275,39 @@ def test_sampler_ic_ranges():
             h.sample_params(12, 4, 8, ranges=api.default_ranges(ic_ranges=r2))
 
 
+def test_sampler_edge_cases_of_the_set_stratifications():
+    """The ends of the ranges the samplers accept: Sobol points just below
+    2^32 (Gray codes with the top bit set), a one-stratum Latin hypercube,
+    point rows of a per-parameter table and of the initial-condition rows
+    (every value equal to the row's bound), and empty calls."""
+    from paper_2503_18356_gb300 import api
+    topo = W.random_network(3, 4, 8, 4, 0)
+    h = PT.gpu_handle(topo)
+    net = O.Network(*topo.edges())
+    tab = W.sobol_direction_table()
+    N, E = topo.n_nodes, topo.n_edges
+    cases = [dict(set0=(1 << 32) - 5, n=5, kw=dict(sobol=api.GRINS_SOBOL_SCRAMBLED, sobol_table=tab)),
+             dict(set0=(1 << 31) - 2, n=4, kw=dict(sobol=api.GRINS_SOBOL_PLAIN, sobol_table=tab)),
+             dict(set0=0, n=1, kw=dict(lhs_sets=1))]
+    for c in cases:
+        _, _, p, _ = PT.gpu_sample(h, 3, c["n"], 1, set0=c["set0"], ranges=api.default_ranges(**c["kw"]))
+        ref = O.sample_params(net, 3, c["n"], set0=c["set0"], ranges=O.default_ranges(**c["kw"]))
+        for f in ("G", "k", "T", "lam", "n"):
+            assert np.array_equal(getattr(p, f), getattr(ref, f)), (c["set0"], f)
+    rows = h.param_range_table()
+    rows[:N] = (0, 0, 7.0, 7.0)
+    rows[2 * N + 2 * E:] = (0, 0, 3.0, 3.0)
+    icr = np.zeros(N, dtype=api.PARAM_RANGE_DTYPE)
+    icr[:] = (0, 0, 0.5, 0.5)
+    _, ic, p, icn = PT.gpu_sample(h, 3, 50, 4, ranges=api.default_ranges(param_ranges=rows, ic_ranges=icr))
+    assert np.all(p.G == 7.0) and np.all(p.n == 3) and np.all(icn == 0.5)
+    ref = O.sample_params(net, 3, 50, ranges=O.default_ranges(param_ranges=rows))
+    for f in ("G", "k", "T", "lam", "n"):
+        assert np.array_equal(getattr(p, f), getattr(ref, f)), f
+    params = torch.empty((0, h.param_stride), dtype=torch.uint8, device="cuda")
+    h.sample_params(3, 0, 0, params=params, ranges=api.default_ranges(sobol=api.GRINS_SOBOL_PLAIN, sobol_table=tab))
+
+
 # ----------------------------------------------------------------- dedupe
 def test_unique_states_bit_exact_on_given_states():
     topo = W.random_network(3, 4, 8, 4, 0)
