@@ -106,7 +106,12 @@ struct grins_racipe {
     grins_racipe_ranges median_ranges{};
     std::vector<grins_param_range> median_table;   // per-parameter rows the medians were taken with
     std::vector<double> node_median;
-    bool median_uploaded = false;
+    // d_edge_median is written once, by the first sampling call, and then
+    // only read: calls whose medians differ stage their own copy on their
+    // stream, so no queued sampler ever sees it change
+    bool edge_median_set = false;
+    std::vector<double> edge_median_host;          // what d_edge_median holds
+    std::mutex median_mu;                          // the median cache and the fields above
 };
 
 extern "C" void grins_racipe_default_ranges(grins_racipe_ranges *r)
@@ -808,7 +813,6 @@ grins_status ensure_medians(grins_racipe *h, const grins_racipe_ranges &r)
         h->median_table.assign(r.param_ranges, r.param_ranges + D);
         h->median_ranges = r;
         h->median_valid = true;
-        h->median_uploaded = false;
         return GRINS_OK;
     }
     if (h->median_valid && h->median_table.empty() && same_ranges(h->median_ranges, r)) return GRINS_OK;
@@ -824,7 +828,6 @@ grins_status ensure_medians(grins_racipe *h, const grins_racipe_ranges &r)
     }
     h->median_ranges = r;
     h->median_valid = true;
-    h->median_uploaded = false;
     return GRINS_OK;
 }
 
@@ -845,6 +848,7 @@ extern "C" grins_status grins_racipe_node_medians(grins_racipe_t h, const grins_
     if (r) rr = *r; else grins_racipe_default_ranges(&rr);
     grins_status s = check_ranges(rr);
     if (s != GRINS_OK) return s;
+    std::lock_guard<std::mutex> lock(h->median_mu);
     s = ensure_medians(h, rr);
     if (s != GRINS_OK) return s;
     std::copy(h->node_median.begin(), h->node_median.end(), out);
@@ -922,16 +926,24 @@ extern "C" grins_status grins_racipe_sample_params(grins_racipe_t h, const grins
     if (r) rr = *r; else grins_racipe_default_ranges(&rr);
     grins_status s = check_ranges(rr);
     if (s != GRINS_OK) return s;
-    s = ensure_medians(h, rr);
-    if (s != GRINS_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
-    if (!h->median_uploaded && h->E > 0) {
-        std::vector<double> em(h->E);
-        for (int e = 0; e < h->E; ++e) em[e] = h->node_median[h->src[e]];
-        CUDA_TRY(cudaMemcpyAsync(h->d_edge_median, em.data(), sizeof(double) * h->E, cudaMemcpyHostToDevice, st),
-                 "sample_params: median upload");
-        CUDA_TRY(cudaStreamSynchronize(st), "sample_params: median upload");
-        h->median_uploaded = true;
+    // the median of each edge's source under these ranges; the handle's
+    // device copy when it holds exactly these values, else a staged copy
+    std::vector<double> em((size_t)h->E);
+    bool own_medians = false;
+    {
+        std::lock_guard<std::mutex> lock(h->median_mu);
+        s = ensure_medians(h, rr);
+        if (s != GRINS_OK) return s;
+        for (int e = 0; e < h->E; ++e) em[(size_t)e] = h->node_median[h->src[e]];
+        if (!h->edge_median_set && h->E > 0) {
+            CUDA_TRY(cudaMemcpyAsync(h->d_edge_median, em.data(), sizeof(double) * h->E, cudaMemcpyHostToDevice, st),
+                     "sample_params: median upload");
+            CUDA_TRY(cudaStreamSynchronize(st), "sample_params: median upload");
+            h->edge_median_host = em;
+            h->edge_median_set = true;
+        }
+        own_medians = h->E > 0 && std::memcmp(em.data(), h->edge_median_host.data(), sizeof(double) * h->E) != 0;
     }
     SampleArgs a{};
     a.L = h->layout;
@@ -954,7 +966,8 @@ extern "C" grins_status grins_racipe_sample_params(grins_racipe_t h, const grins
     a.li_min = rr.lam_inh_min; a.li_max = rr.lam_inh_max;
     a.params = static_cast<unsigned char *>(d_params);
     // tables the kernel reads besides the parameters: Sobol direction
-    // numbers and per-parameter rows, staged in one stream-ordered buffer
+    // numbers, per-parameter rows and, when they are not the handle's,
+    // the edge medians, staged in one stream-ordered buffer
     const int D = 2 * h->N + 3 * h->E;
     std::vector<uint32_t> tab;
     if (rr.sobol != GRINS_SOBOL_OFF && n_sets > 0) {
@@ -965,10 +978,12 @@ extern "C" grins_status grins_racipe_sample_params(grins_racipe_t h, const grins
     }
     const size_t tab_bytes = (sizeof(uint32_t) * tab.size() + 15) / 16 * 16;
     const size_t row_bytes = rr.param_ranges ? sizeof(grins_param_range) * (size_t)D : 0;
-    if (n_sets > 0 && tab_bytes + row_bytes > 0) {
-        std::vector<unsigned char> blob(tab_bytes + row_bytes, 0);
+    const size_t med_bytes = own_medians ? sizeof(double) * (size_t)h->E : 0;
+    if (n_sets > 0 && tab_bytes + row_bytes + med_bytes > 0) {
+        std::vector<unsigned char> blob(tab_bytes + row_bytes + med_bytes, 0);
         if (!tab.empty()) std::memcpy(blob.data(), tab.data(), sizeof(uint32_t) * tab.size());
         if (row_bytes) std::memcpy(blob.data() + tab_bytes, rr.param_ranges, row_bytes);
+        if (med_bytes) std::memcpy(blob.data() + tab_bytes + row_bytes, em.data(), med_bytes);
         void *d_blob = nullptr;
         CUDA_TRY(cudaMallocAsync(&d_blob, blob.size(), st), "sample_params: table buffer");
         cudaError_t e = cudaMemcpyAsync(d_blob, blob.data(), blob.size(), cudaMemcpyHostToDevice, st);
@@ -978,6 +993,7 @@ extern "C" grins_status grins_racipe_sample_params(grins_racipe_t h, const grins
             a.sobol_dims = D;
         }
         if (row_bytes) a.prange = reinterpret_cast<const grins_param_range *>(base + tab_bytes);
+        if (med_bytes) a.edge_median = reinterpret_cast<const double *>(base + tab_bytes + row_bytes);
         if (e == cudaSuccess) e = launch_sample_params(a, st);
         const cudaError_t ef = cudaFreeAsync(d_blob, st);
         CUDA_TRY(e, "sample_params: launch");
@@ -2060,7 +2076,10 @@ extern "C" grins_status grins_racipe_server_submit(grins_racipe_server_t sv, gri
     if (s != GRINS_OK) return s;
     // the half-functional median table is host work: do it here, in the
     // submitting thread, not in the worker
-    s = ensure_medians(net, rr);
+    {
+        std::lock_guard<std::mutex> lock(net->median_mu);
+        s = ensure_medians(net, rr);
+    }
     if (s != GRINS_OK) return s;
     auto req = std::unique_ptr<ServerRequest>(new (std::nothrow) ServerRequest());
     if (!req) return fail(GRINS_E_NOMEM, "server_submit: host allocation failed");

@@ -308,6 +308,33 @@ def test_sampler_edge_cases_of_the_set_stratifications():
     h.sample_params(3, 0, 0, params=params, ranges=api.default_ranges(sobol=api.GRINS_SOBOL_PLAIN, sobol_table=tab))
 
 
+def test_sampler_ranges_changing_between_streams():
+    """Calls on two streams with ranges of different medians, queued back to
+    back: each call's thresholds use its own medians (bit-exact with the
+    oracle), whichever call the handle's medians came from."""
+    from paper_2503_18356_gb300 import api
+    topo = W.net22_workload()["topology"]
+    net = O.Network(*topo.edges())
+    h = PT.gpu_handle(topo)
+    S = 20000
+    rx = dict(median_samples=3000)
+    ry = dict(median_samples=3000, G_max=30.0, lam_act_max=10.0)
+    sa, sb = torch.cuda.Stream(), torch.cuda.Stream()
+    pa = torch.empty((S, h.param_stride), dtype=torch.uint8, device="cuda")
+    pb = torch.empty_like(pa)
+    for first, second in ((rx, ry), (ry, rx)):
+        h2 = PT.gpu_handle(topo)                        # a fresh handle: its medians come from `first`
+        h2.sample_params(9, S, 0, params=pa, ranges=api.default_ranges(**first), stream=sa)
+        h2.sample_params(9, S, 0, params=pb, ranges=api.default_ranges(**second), stream=sb)
+        torch.cuda.synchronize()
+        for params, r in ((pa, first), (pb, second)):
+            T = h2.unpack_params(params)[2].cpu().numpy()
+            idx = [0, 1, S // 2, S - 1]
+            ref = np.concatenate([O.sample_params(net, 9, 1, set0=i, ranges=O.default_ranges(**r)).T for i in idx])
+            assert np.array_equal(T[idx], ref)
+        h2.close()
+
+
 # ----------------------------------------------------------------- dedupe
 def test_unique_states_bit_exact_on_given_states():
     topo = W.random_network(3, 4, 8, 4, 0)
