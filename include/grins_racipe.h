@@ -260,7 +260,15 @@ grins_status grins_racipe_node_medians(grins_racipe_t h, const grins_racipe_rang
  * GRINS_E_INVALID_ARG for bad ranges (min > max, non-positive G/k/lambda
  * bounds, activating lambda below 1, inhibiting lambda above 1, n outside
  * [1, 255], median_samples < 1), n_sets < 0, set0 < 0, n_ics < 0, or a
- * null d_params with n_sets > 0. */
+ * null d_params with n_sets > 0, and for the Sobol, table and
+ * initial-condition options the conditions stated with them.
+ * Host work and synchronisation: the half-functional medians are computed
+ * on the host once per ranges (cached on the handle, under a lock); the
+ * first call on a handle uploads its edge medians and waits for its stream;
+ * a later call whose medians differ, and any call with Sobol tables or
+ * per-parameter or initial-condition rows, stages them in a stream-ordered
+ * device buffer (cudaMallocAsync, freed after the sampler on the same
+ * stream) and does not wait. */
 grins_status grins_racipe_sample_params(grins_racipe_t h, const grins_racipe_ranges *r,
                                         uint64_t seed, int64_t set0, int64_t n_sets,
                                         int32_t n_ics, void *d_params, double *d_ic_unit,
