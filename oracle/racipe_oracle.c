@@ -27,8 +27,10 @@
  *   - Levels of G/k-normalised expression, level labels and the
  *     multistability histogram (Sec. 2.1.3, Sec. 3.1).
  *   - The Boolean Ising formalism, synchronous and asynchronous (Eq. 3).
- *   - Log-uniform, normal and log-normal parameter distributions and the
- *     Latin-hypercube stratification (the samplers of Sec. 2.1.2).
+ *   - Log-uniform, normal and log-normal parameter distributions, the
+ *     Latin-hypercube and Sobol sets, the per-parameter range table with
+ *     per-node medians, and initial conditions from per-node ranges (the
+ *     samplers and the range file of Sec. 2.1.2).
  *
  * Parity status: every function here is pinned by a CPU test against
  * closed forms, library routines (numpy Philox, scipy DOP853, scipy
