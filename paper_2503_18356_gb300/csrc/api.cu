@@ -19,7 +19,18 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "integrate_grp.cuh"
+
+// An NVTX range over one call of the C ABI, named after it (a timeline
+// marker for Nsight tools; a null-pointer check when no tool is attached).
+struct AbiRange {
+    explicit AbiRange(const char *name) { nvtxRangePushA(name); }
+    ~AbiRange() { nvtxRangePop(); }
+    AbiRange(const AbiRange &) = delete;
+    AbiRange &operator=(const AbiRange &) = delete;
+};
 
 using namespace grins;
 
@@ -434,6 +445,7 @@ extern "C" grins_status grins_racipe_create(int32_t n_nodes, int32_t n_edges, co
                                             const int32_t *dst, const int8_t *sign,
                                             grins_racipe_t *out)
 {
+    AbiRange nvtx_range_("grins_racipe_create");
     g_last_error.clear();
     if (!out) return fail(GRINS_E_INVALID_ARG, "create: out is NULL");
     *out = nullptr;
@@ -842,6 +854,7 @@ bool on_handle_device(const grins_racipe *h)
 extern "C" grins_status grins_racipe_node_medians(grins_racipe_t h, const grins_racipe_ranges *r,
                                                   double *out)
 {
+    AbiRange nvtx_range_("grins_racipe_node_medians");
     g_last_error.clear();
     if (!h || !out) return fail(GRINS_E_INVALID_ARG, "node_medians: NULL argument");
     grins_racipe_ranges rr;
@@ -916,6 +929,7 @@ extern "C" grins_status grins_racipe_sample_params(grins_racipe_t h, const grins
                                                    int32_t n_ics, void *d_params, double *d_ic_unit,
                                                    void *stream)
 {
+    AbiRange nvtx_range_("grins_racipe_sample_params");
     g_last_error.clear();
     if (!h) return fail(GRINS_E_INVALID_ARG, "sample_params: NULL handle");
     if (set0 < 0 || n_sets < 0 || n_ics < 0)
@@ -1117,6 +1131,7 @@ extern "C" grins_status grins_racipe_polish(grins_racipe_t h, const grins_solver
                                             double *d_states, uint8_t *d_status, float *d_err_est,
                                             void *stream)
 {
+    AbiRange nvtx_range_("grins_racipe_polish");
     g_last_error.clear();
     if (!h || !o) return fail(GRINS_E_INVALID_ARG, "polish: NULL handle or options");
     if (n_sets < 0 || n_ics < 1) return fail(GRINS_E_INVALID_ARG, "polish: bad sizes");
@@ -1143,6 +1158,7 @@ extern "C" grins_status grins_racipe_integrate(grins_racipe_t h, const grins_sol
                                                float *d_err_est, int32_t *d_n_steps, double *d_series,
                                                void *stream)
 {
+    AbiRange nvtx_range_("grins_racipe_integrate");
     g_last_error.clear();
     if (!h || !o) return fail(GRINS_E_INVALID_ARG, "integrate: NULL handle or options");
     if (n_sets < 0) return fail(GRINS_E_INVALID_ARG, "integrate: n_sets < 0");
@@ -1244,6 +1260,7 @@ extern "C" grins_status grins_racipe_unique_states(grins_racipe_t h, const void 
                                                    int64_t n_sets, int32_t n_ics, double tol,
                                                    int32_t *d_state_id, int32_t *d_n_unique, void *stream)
 {
+    AbiRange nvtx_range_("grins_racipe_unique_states");
     g_last_error.clear();
     if (!h) return fail(GRINS_E_INVALID_ARG, "unique_states: NULL handle");
     if (n_sets < 0 || n_ics < 1 || n_ics > 4096) return fail(GRINS_E_INVALID_ARG, "unique_states: bad sizes");
@@ -1284,6 +1301,7 @@ extern "C" grins_status grins_racipe_gk_histogram(grins_racipe_t h, const void *
                                                   const uint8_t *d_status, int64_t n_sets, int32_t n_ics,
                                                   int32_t n_bins, unsigned long long *d_counts, void *stream)
 {
+    AbiRange nvtx_range_("grins_racipe_gk_histogram");
     g_last_error.clear();
     LevelArgs a;
     const grins_status rc = level_args(h, "gk_histogram", d_params, d_states, d_status, n_sets, n_ics, n_bins, &a);
@@ -1376,6 +1394,7 @@ extern "C" grins_status grins_racipe_level_states(grins_racipe_t h, const void *
                                                   unsigned long long *d_labels, int32_t *d_n_states,
                                                   unsigned long long *d_multi_hist, void *stream)
 {
+    AbiRange nvtx_range_("grins_racipe_level_states");
     g_last_error.clear();
     LevelArgs a;
     const grins_status rc = level_args(h, "level_states", d_params, d_states, d_status, n_sets, n_ics, n_bins, &a);
@@ -1405,6 +1424,7 @@ extern "C" grins_status grins_ising_run(grins_racipe_t h, int32_t mode, int32_t 
                                         unsigned long long *d_final, int32_t *d_steps, uint8_t *d_status,
                                         void *stream)
 {
+    AbiRange nvtx_range_("grins_ising_run");
     g_last_error.clear();
     if (!h) return fail(GRINS_E_INVALID_ARG, "ising_run: NULL handle");
     if (mode != GRINS_ISING_SYNC && mode != GRINS_ISING_ASYNC) return fail(GRINS_E_INVALID_ARG, "ising_run: unknown mode %d", mode);
@@ -1615,6 +1635,7 @@ extern "C" grins_status grins_racipe_plan_create(const grins_solver_opts *o, con
                                                  int32_t n_jobs, int32_t autotune, void *stream,
                                                  grins_racipe_plan_t *out)
 {
+    AbiRange nvtx_range_("grins_racipe_plan_create");
     g_last_error.clear();
     if (!o || !out || (n_jobs > 0 && !jobs)) return fail(GRINS_E_INVALID_ARG, "plan_create: NULL argument");
     *out = nullptr;
@@ -1766,6 +1787,7 @@ extern "C" grins_status grins_racipe_plan_create(const grins_solver_opts *o, con
 
 extern "C" grins_status grins_racipe_plan_run(grins_racipe_plan_t p, void *stream)
 {
+    AbiRange nvtx_range_("grins_racipe_plan_run");
     g_last_error.clear();
     if (!p) return fail(GRINS_E_INVALID_ARG, "plan_run: NULL plan");
     int dev = -1;
@@ -2056,6 +2078,7 @@ extern "C" grins_status grins_racipe_server_submit(grins_racipe_server_t sv, gri
                                                    int32_t n_ics, const grins_solver_opts *o, double dedupe_tol,
                                                    int64_t *request_id)
 {
+    AbiRange nvtx_range_("grins_racipe_server_submit");
     g_last_error.clear();
     if (!sv || !net || !o || !request_id) return fail(GRINS_E_INVALID_ARG, "server_submit: NULL argument");
     if (n_sets < 1 || n_ics < 1 || n_ics > 4096) return fail(GRINS_E_INVALID_ARG, "server_submit: bad sizes");
@@ -2167,6 +2190,7 @@ extern "C" grins_status grins_racipe_server_copy_results(grins_racipe_server_t s
                                                          uint8_t *d_status, int32_t *d_n_unique,
                                                          int32_t *d_state_id, void *stream)
 {
+    AbiRange nvtx_range_("grins_racipe_server_copy_results");
     g_last_error.clear();
     if (!sv) return fail(GRINS_E_INVALID_ARG, "server_copy_results: NULL server");
     std::lock_guard<std::mutex> lock(sv->mu);
@@ -2282,6 +2306,7 @@ extern "C" grins_status grins_racipe_integrate_static(grins_racipe_t h, const gr
                                                       double *d_t_final, float *d_err_est,
                                                       int32_t *d_n_steps, double *d_series, void *stream)
 {
+    AbiRange nvtx_range_("grins_racipe_integrate_static");
     g_last_error.clear();
     if (!h || !o) return fail(GRINS_E_INVALID_ARG, "integrate_static: NULL handle or options");
     if (n_sets < 0) return fail(GRINS_E_INVALID_ARG, "integrate_static: n_sets < 0");
