@@ -5,6 +5,7 @@ Workload (one "step" = the whole hot path over one batch): the seeded random
 stand-in for the paper's EMT network, Sec. 3.2), 100,000 parameter sets x 10
 initial conditions = 1,000,000 solves per step:
   sample parameters + ICs -> FP32 Dormand-Prince 5(4) to steady state ->
+  FP64 re-pass of the solves whose steady-state decision fell near t_end ->
   FP64 Newton polish -> distinct steady states per set.
 Under torchrun each rank integrates its own 100,000 sets (set offset rank x
 100,000; weak scaling, no collective on the data path).
@@ -36,7 +37,7 @@ TOL = dict(rtol=1e-6, atol=1e-9, t_end=200.0, ss_tol=1e-6)
 # capture of the same kernel on a 20,000-set launch of this workload
 # (35.34 MB read + 1.28 MB written for 200,000 solves); traffic grows with
 # the solves per launch.  None while no capture of the current kernel exists.
-INTEGRATOR_DRAM_BYTES_PER_SOLVE = 36.62e6 / 200_000
+INTEGRATOR_DRAM_BYTES_PER_SOLVE = None
 
 
 def parse():
@@ -48,7 +49,10 @@ def parse():
     ap.add_argument("--sets", type=int, default=N_SETS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sets", type=int, default=1000, help="sets of the oracle sample (sets 0..n-1)")
-    ap.add_argument("--fp64-sets", type=int, default=5000, help="sets of the FP64 GPU solver sample")
+    ap.add_argument("--ref-sets", type=int, default=200,
+                    help="sets per step of the reference arm (the oracle timed on the host cores)")
+    ap.add_argument("--fp64-sets", type=int, default=N_SETS,
+                    help="sets of the plain FP64 GPU solver's timed run (default: the whole workload)")
     ap.add_argument("--serve-seconds", type=float, default=6.0,
                     help="length of the Poisson request stream of the serving measurement (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=20.0, help="requests per second of that stream")
@@ -162,41 +166,81 @@ def cpu_baseline(n_sets):
                        "Newton polish + dedupe, %.1f s" % (n_sets - 1, N_ICS, n_sets * N_ICS, dt)), out
 
 
-def parity_figures(gpu, orc, G, k):
-    """Per-result error of the GPU path against the oracle on the same sets:
-    raw FP32 states on the G/k scale, polished states relative (floor
-    1e-6 G/k), over solves converged on both sides at the same fixed point
-    (G/k-normalised distance <= 1e-2 raw, 1e-5 polished); the basin-mismatch
-    rate (both converged, different fixed points), the status agreement and
-    the share of sets with the same number of distinct steady states."""
+def parity_figures(gpu, orc, G, k, params_slice):
+    """Per-result error of the GPU path against the oracle on the same sets,
+    over solves converged on both sides at the same fixed point (G/k-
+    normalised distance <= 1e-2 raw, 1e-5 polished):
+      * raw states (the integrator's stopping point, before the polish):
+        relative error with G12's floor, |x - x*| / max(|x*|, 1e-6 G/k) --
+        the benchmark spec's scale -- with the share of solves above 1e-3, and the
+        error on the G/k scale beside it (the steady-state test bounds the
+        distance to the fixed point in units of G/k);
+      * polished states: relative, floor 1e-6 G/k;
+    the basin-mismatch rate (both converged, different fixed points) and how
+    many of those fail the oracle's residual certificate, the status
+    agreement and the share of sets with the same number of distinct steady
+    states."""
     import numpy as np
+    import oracle as O
+    from paper_2503_18356_gb300 import workloads as W
+    net = O.Network(*W.net22_workload()["topology"].edges())
     G = G[:, None, :]
     k = k[:, None, :]
     vo = orc["states"] * k / G
     res = {}
-    for name, states, status, tol in (("fp32_raw", gpu["raw_states"], gpu["raw_status"], 1e-2),
-                                      ("fp32_polish", gpu["states"], gpu["status"], 1e-5)):
+    for name, states, status, tol, cert in (("fp32_raw", gpu["raw_states"], gpu["raw_status"], 1e-2, 1e-5),
+                                            ("fp32_polish", gpu["states"], gpu["status"], 1e-5, 1e-10)):
         both = (status == 0) & (orc["status"] == 0)
         vg = states * k / G
         dist = np.abs(vg - vo).max(axis=2)
         same = both & (dist <= tol)
-        if name == "fp32_raw":
-            err = np.abs(vg - vo).max(axis=2)
-        else:
-            err = (np.abs(states - orc["states"]) / np.maximum(np.abs(orc["states"]), 1e-6 * G)).max(axis=2)
-        e = err[same]
+        rel = (np.abs(states - orc["states"]) / np.maximum(np.abs(orc["states"]), 1e-6 * G)).max(axis=2)
+        gk = np.abs(vg - vo).max(axis=2)
+        e = rel[same]
+        unc = 0
+        for s_, c_ in zip(*np.nonzero(both & ~same)):
+            if not all(O.rho(net, params_slice, x, s_) < cert for x in (states[s_, c_], orc["states"][s_, c_])):
+                unc += 1
         res[name] = dict(max=float(e.max()) if e.size else None,
                          p999=float(np.quantile(e, 0.999)) if e.size else None,
+                         share_above_1e3=float((e > 1e-3).mean()) if e.size else None,
                          compared=int(same.sum()), basin_mismatch_rate=float((both & ~same).mean()),
-                         status_agree=float((status == orc["status"]).mean()))
-    res["fp32_polish"]["error"] = "relative, floor 1e-6 G/k"
-    res["fp32_raw"]["error"] = "G/k-normalised"
+                         basin_mismatch_uncertified=unc,
+                         status_agree=float((status == orc["status"]).mean()),
+                         error="relative, floor 1e-6 G/k")
+        if name == "fp32_raw":
+            res[name]["gk_scale"] = dict(max=float(gk[same].max()) if e.size else None,
+                                         p999=float(np.quantile(gk[same], 0.999)) if e.size else None)
     res["n_unique_agree"] = float((gpu["n_unique"] == orc["n_unique"]).mean())
     if "fp64_n_unique" in gpu:
         # the same figures for the plain FP64 GPU solver at the same tolerances
         res["fp64_solver"] = dict(status_agree=float((gpu["fp64_status"] == orc["status"]).mean()),
                                   n_unique_agree=float((gpu["fp64_n_unique"] == orc["n_unique"]).mean()))
     return res
+
+
+def oracle_unpolished_share(n_sets):
+    """The oracle's own integration stopping point (rtol 1e-10, no polish)
+    against its polished fixed point on the first n_sets sets, on the same
+    relative scale: what the steady-state test alone leaves on nodes near
+    zero, whatever the arithmetic."""
+    import numpy as np
+    import oracle as O
+    from paper_2503_18356_gb300 import workloads as W
+    w = W.net22_workload()
+    net = O.Network(*w["topology"].edges())
+    p = O.sample_params(net, w["param_seed"], n_sets)
+    ic = O.sample_ics(w["topology"].n_nodes, w["ic_seed"], N_ICS)
+    raw = O.run_sets_parallel(net, p, ic, polish=False)
+    pol = O.run_sets_parallel(net, p, ic, polish=True)
+    G, k = p.G[:, None, :], p.k[:, None, :]
+    both = (raw["status"] == 0) & (pol["status"] == 0)
+    rel = (np.abs(raw["states"] - pol["states"]) / np.maximum(np.abs(pol["states"]), 1e-6 * G / k)).max(axis=2)[both]
+    gk = (np.abs(raw["states"] - pol["states"]) * k / G).max(axis=2)[both]
+    return dict(sets=n_sets, compared=int(both.sum()), share_above_1e3=float((rel > 1e-3).mean()),
+                max=float(rel.max()), gk_max=float(gk.max()),
+                note="the oracle's own unpolished states (rtol 1e-10, stopped at max|f| k/G < 1e-6) against its "
+                     "polished ones, relative with floor 1e-6 G/k")
 
 
 def levels_measurement(h, params, out, stream, dev, S, I, n_bins=100, reps=3):
@@ -329,12 +373,12 @@ def run_reference(args):
     import oracle as O
     O.build()
     for _ in range(args.warmup):
-        oracle_sample(max(2, args.cpu_sets // 4), os.cpu_count() or 1)
+        oracle_sample(max(2, args.ref_sets // 4), os.cpu_count() or 1)
     vals, times = [], []
     for _ in range(args.steps):
-        v, dt, _ = oracle_sample(args.cpu_sets, os.cpu_count() or 1)
+        v, dt, _ = oracle_sample(args.ref_sets, os.cpu_count() or 1)
         vals.append(v); times.append(dt)
-    total = args.cpu_sets * N_ICS * args.steps
+    total = args.ref_sets * N_ICS * args.steps
     value = total / sum(times)
     cores = os.cpu_count() or 1
     line = dict(impl="reference", metric=METRIC,
@@ -342,9 +386,9 @@ def run_reference(args):
                 ms_per_step=1000 * sum(times) / args.steps, higher_is_better=True, scaling="weak",
                 vs_baseline=None, dtype="f64", data="synthetic",
                 config=dict(workload="rand22x82: 22 nodes, 82 edges; %d sets x %d ICs per step "
-                                     "(bounded CPU sample of the 100000 x 10 workload)" % (args.cpu_sets, N_ICS)),
+                                     "(bounded CPU sample of the 100000 x 10 workload)" % (args.ref_sets, N_ICS)),
                 cpu_baseline=dict(value=value, unit="solves/s", cores=cores, kind="oracle",
-                                  sample="%d sets x %d ICs per step" % (args.cpu_sets, N_ICS)),
+                                  sample="sets 0..%d x %d ICs per step" % (args.ref_sets - 1, N_ICS)),
                 e2e=dict(value=value, unit="solves/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line))
 
@@ -491,15 +535,20 @@ def run_native(args):
     popts = api.default_opts()
 
     def step(ev=None):
-        if ev: ev[0].record(stream)
+        # events: 0 start, 1 sampled, 2 FP32 pass done (recorded by the
+        # library between its passes), 3 re-pass done, 4 polished, 5 deduped
+        if ev:
+            ev[0].record(stream)
+            opts.pass_event = ev[2].cuda_event
         h.sample_params(w["param_seed"], S, I, set0=set0, params=params, ic_unit=ic, stream=stream)
         if ev: ev[1].record(stream)
         h.integrate(params, ic, opts=opts, stream=stream, out=out)
-        if ev: ev[2].record(stream)
-        h.polish(params, out["states"], out["status"], out["err_est"], opts=popts, stream=stream)
+        opts.pass_event = None
         if ev: ev[3].record(stream)
-        h.unique_states(params, out["states"], out["status"], stream=stream, out=(sid, nu))
+        h.polish(params, out["states"], out["status"], out["err_est"], opts=popts, stream=stream)
         if ev: ev[4].record(stream)
+        h.unique_states(params, out["states"], out["status"], stream=stream, out=(sid, nu))
+        if ev: ev[5].record(stream)
 
     def barrier():
         torch.cuda.synchronize()
@@ -516,7 +565,9 @@ def run_native(args):
     uuid = str(getattr(props, "uuid", "") or "")
     clk = ClockSampler(("GPU-" + uuid) if uuid and not uuid.startswith("GPU-") else (uuid or str(dev.index)))
     clk.start()
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
+    for e in evs:                    # create the events the library records (torch creates them lazily)
+        e[2].record(stream)
     start = torch.cuda.Event(enable_timing=True)
     stop = torch.cuda.Event(enable_timing=True)
     barrier()
@@ -527,7 +578,9 @@ def run_native(args):
     barrier()
     clocks = clk.stop()
     elapsed_ms = shard.max_over_ranks(start.elapsed_time(stop), dev)
-    per_kernel = np.array([[e[i].elapsed_time(e[i + 1]) for i in range(4)] for e in evs])  # ms
+    per_kernel = np.array([[e[i].elapsed_time(e[i + 1]) for i in range(5)] for e in evs])  # ms
+    # the last timed step's re-pass (every step integrates the same sets)
+    n_tail, a_tail = h.tail_stats(stream)
 
     # the first sets of one more (untimed) step, raw and polished, for the
     # per-result comparison with the oracle
@@ -540,11 +593,15 @@ def run_native(args):
         h.polish(params, out["states"], out["status"], out["err_est"], opts=popts, stream=stream)
         h.unique_states(params, out["states"], out["status"], stream=stream, out=(sid, nu))
         G, k = (x[:P].cpu().numpy() for x in h.unpack_params(params[:P])[:2])
+        Tt, lt, nt = (x[:P].cpu().numpy() for x in h.unpack_params(params[:P])[2:])
         snap.update(states=out["states"][:P].cpu().numpy(), status=out["status"][:P].cpu().numpy(),
-                    n_unique=nu[:P].cpu().numpy(), G=G, k=k)
+                    n_unique=nu[:P].cpu().numpy(), G=G, k=k, T=Tt, lam=lt, n=nt,
+                    n_unique_all=nu.cpu().numpy(), status_all=out["status"].cpu().numpy())
     kern_ms = per_kernel.mean(axis=0)
-    # the timed step's step attempts and statuses, before later legs reuse the buffers
-    attempts = int(out["n_steps"].sum().item())
+    # the timed step's step attempts and statuses, before later legs reuse the
+    # buffers; d_n_steps counts both passes, the roofline the FP32 pass's
+    attempts_all = int(out["n_steps"].sum().item())
+    attempts = attempts_all - a_tail
     kernel_desc = h.integrator()          # the timed step's kernels, before the Tsit5 leg
     status = out["status"].cpu().numpy()
     levels = levels_measurement(h, params, out, stream, dev, S, I) if rank == 0 else None
@@ -604,18 +661,21 @@ def run_native(args):
     e2e_value = solves * e2e_steps / e2e_s
 
     # the plain FP64 GPU solver (FP64 Dormand-Prince end to end, no polish)
-    # on the first sets of the same workload, for the FP32 + polish ratio
+    # on the same sets as the step (the whole workload by default), for the
+    # FP32 + polish ratio
     f64_sets = max(1, min(S, args.fp64_sets))
     opts64 = api.default_opts(precision=api.GRINS_FP64, polish=0, **TOL)
     out64 = {k: (v[:f64_sets] if v is not None else None) for k, v in out.items()}
-    h.integrate(params[:f64_sets], ic, opts=opts64, stream=stream, out=out64)
+    h.integrate(params[:min(f64_sets, 2000)], ic, opts=opts64, stream=stream,
+                out={k: (v[:min(f64_sets, 2000)] if v is not None else None) for k, v in out.items()})
     e64 = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     barrier()
     e64[0].record(stream)
     h.integrate(params[:f64_sets], ic, opts=opts64, stream=stream, out=out64)
     e64[1].record(stream)
     barrier()
-    fp64_value = f64_sets * I / (e64[0].elapsed_time(e64[1]) / 1e3)
+    fp64_ms = e64[0].elapsed_time(e64[1])
+    fp64_value = f64_sets * I / (fp64_ms / 1e3)
     if snap is not None and f64_sets >= snap["n_unique"].shape[0]:
         # the plain FP64 solver's statuses and distinct-state counts on the
         # oracle's sets (polished and deduplicated as the FP32 path is)
@@ -638,9 +698,13 @@ def run_native(args):
                         l2="inputs larger than L2: parameter block %.0f MB, states %.0f MB" % (
                             S * h.param_stride / 1e6, S * I * N * 8 / 1e6),
                         parallelism="dp%d (sets sharded by rank)" % ws),
-            kernel_ms=dict(sample=kern_ms[0], integrate_fp32=kern_ms[1], polish_fp64=kern_ms[2],
-                           unique=kern_ms[3]),
+            kernel_ms=dict(sample=kern_ms[0], integrate_fp32=kern_ms[1], repass_fp64=kern_ms[2],
+                           polish_fp64=kern_ms[3], unique=kern_ms[4]),
             step_attempts_per_solve=attempts / (S * I),
+            repass=dict(solves=n_tail, share=n_tail / (S * I), fp64_attempts=a_tail, ms=kern_ms[2],
+                        what="solves whose steady-state decision fell near t_end, re-integrated in FP64 at rtol "
+                             "%g from their first state with residual below %g ss_tol (ordering kernel + FP64 "
+                             "kernel)" % (opts.tail_rtol, opts.tail_start)),
             status_hist=np.bincount(status.ravel(), minlength=5).tolist(),
             roofline=dict(bound="alu", achieved=achieved, peak=peak, unit=unit, frac=achieved / peak,
                           traffic=(INTEGRATOR_DRAM_BYTES_PER_SOLVE * S * I
@@ -650,10 +714,12 @@ def run_native(args):
                                      % (sms, "16 SFU" if sfu_bound else "128 FP32", f_mhz),
                           work_per_attempt=dict(fp32=w32, sfu=wsfu)),
             e2e=dict(value=e2e_value, unit="solves/s", h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h),
-            gpu_launches=5 * args.steps,
-            fp64_gpu_solver=dict(value=fp64_value, unit="solves/s",
-                                 sample="sets 0..%d x %d ICs, FP64 Dormand-Prince 5(4) on the GPU, same "
-                                        "tolerances, no polish" % (f64_sets - 1, I),
+            # per step: parameter and IC samplers, FP32 integrator, re-pass
+            # ordering and FP64 kernels, polish, dedupe
+            gpu_launches=(7 if n_tail >= 0 and opts.tail_rtol > 0 else 5) * args.steps,
+            fp64_gpu_solver=dict(value=fp64_value, unit="solves/s", ms=fp64_ms,
+                                 sample="sets 0..%d x %d ICs (the step's sets), FP64 Dormand-Prince 5(4) on the "
+                                        "GPU, same tolerances, no polish" % (f64_sets - 1, I),
                                  ratio=value / fp64_value),
             clocks=clocks)
         if levels is not None:
@@ -672,9 +738,24 @@ def run_native(args):
             line["cpu_baseline"], orc = cpu_baseline(args.cpu_sets)
             P = snap["G"].shape[0]
             orc = {kk: (v[:P] if hasattr(v, "shape") else v) for kk, v in orc.items()}
+            import oracle as O
+            pslice = O.ParamSet(snap["G"], snap["k"], snap["T"], snap["lam"], snap["n"].astype(np.int32))
             line["parity"] = dict(sets=P, solves=P * I, against="the oracle (FP64 CPU, rtol 1e-10, Newton "
-                                  "polish) on the same sets", **parity_figures(snap, orc, snap["G"], snap["k"]))
+                                  "polish) on the same sets", **parity_figures(snap, orc, snap["G"], snap["k"],
+                                                                               pslice))
             line["parity"]["oracle_at_solver_tolerances"] = oracle_tolerance_floor(P, orc)
+            line["parity"]["oracle_unpolished"] = oracle_unpolished_share(min(P, 200))
+            # distinct-state counts on sets 0..9999 against the oracle's,
+            # stored by tests/golden/make_net22_reference.py (which calls only
+            # the oracle; too long to recompute here)
+            from tests.golden import make_net22_reference as R
+            ref_status, ref_nu = R.load()
+            M = min(ref_nu.size, S)
+            g_nu, g_st = snap["n_unique_all"][:M], snap["status_all"][:M]
+            line["parity"]["n_unique_10k"] = dict(
+                sets=M, agree=float((g_nu == ref_nu[:M]).mean()), mismatched_sets=int((g_nu != ref_nu[:M]).sum()),
+                converged_status_agree=float(((g_st == 0) == (ref_status[:M] == 0)).mean()),
+                against="the oracle's stored counts (tests/golden/net22_oracle_sets0_9999.txt.gz)")
         print(json.dumps(line))
     h.close()
     if ws > 1:

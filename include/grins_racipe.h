@@ -177,7 +177,8 @@ enum { GRINS_SOBOL_OFF = 0, GRINS_SOBOL_PLAIN = 1, GRINS_SOBOL_SCRAMBLED = 2 };
  * steady state, optional time points).  grins_solver_default_opts fills:
  * FP32 + polish, rtol 1e-6, atol 1e-9, t0 0, t_end 200, ss_tol 1e-6,
  * max_steps 100000, no time grid, polish_tol 1e-13, polish_iters 16,
- * polish_max_move 1e-2, ss_tighten 0.3, method GRINS_METHOD_DOPRI5. */
+ * polish_max_move 1e-2, ss_tighten 0.3, method GRINS_METHOD_DOPRI5,
+ * tail_rtol 1e-9, tail_start 20, tail_rho 10, tail_late 0.2, tail_work 96. */
 typedef struct {
     int32_t precision;         /* GRINS_FP32 or GRINS_FP64 integration */
     int32_t polish;            /* 1: FP64 Newton polish of each converged state */
@@ -207,6 +208,36 @@ typedef struct {
                                   no register layout, run-time compiles off -- and
                                   plans and the server take Dormand-Prince only
                                   (GRINS_E_INVALID_ARG otherwise) */
+    /* Borderline re-pass (FP32 integrations; tail_rtol = 0 turns it off).
+     * Near t_end the steady-state decision of Sec. 2.1.3 is decided by a
+     * residual max_i |dx_i/dt| / (G_i/k_i) that has fallen to about ss_tol,
+     * and at rtol ~ ss_tol the integrated state is not accurate enough to
+     * place it on the right side: the residual can cross ss_tol early, late
+     * or, where it dips and rises again, not at all.  So the FP32 pass keeps
+     * a checkpoint -- its first accepted state with residual below
+     * tail_start * ss_tol -- and a solve whose decision is borderline
+     *   - t_end reached with a final residual below tail_rho * ss_tol, or
+     *   - converged at t with t_end - t < tail_late * (t - t_c), t_c the
+     *     checkpoint's time (the crossing could move past t_end),
+     * and that took at most tail_work attempts after its checkpoint (longer
+     * stretches -- slow oscillations that hover near ss_tol -- would hold
+     * the FP64 pass for many times the rest of its work and keep their FP32
+     * result), is integrated again in FP64 from its checkpoint to t_end at rtol
+     * tail_rtol (atol scaled by tail_rtol / rtol), no tightening, which sets
+     * its state, status and t_final; d_n_steps counts the attempts of both
+     * passes, and grins_racipe_tail_stats reports the re-pass's share.  Runs when the
+     * kernels compiled for the network are available (FP32 and FP64 register
+     * records) and there is no time grid; otherwise the call proceeds without
+     * it.  Plans, the server and grins_racipe_integrate_static do not run it. */
+    double tail_rtol;
+    double tail_start;
+    double tail_rho;
+    double tail_late;
+    int32_t tail_work;
+    void *pass_event;          /* profiling hook, NULL = none: a cudaEvent_t that
+                                  grins_racipe_integrate records on its stream after
+                                  the integration pass and before the re-pass and the
+                                  polish, so a caller can time the integrator alone */
 } grins_solver_opts;
 
 void grins_racipe_default_ranges(grins_racipe_ranges *r);
@@ -214,6 +245,12 @@ void grins_solver_default_opts(grins_solver_opts *o);
 
 /* Thread-local message of the last failing call on this thread ("" if none). */
 const char *grins_last_error(void);
+
+/* Number of device allocations (cudaMalloc, cudaMallocAsync and
+ * cudaMallocFromPoolAsync calls) the library has made in this process, over
+ * all handles, plans and servers: a diagnostic that shows whether a call
+ * allocated (compare the count before and after it).  Thread-safe. */
+int64_t grins_device_allocations(void);
 
 /* Library version string. */
 const char *grins_version(void);
@@ -449,24 +486,37 @@ grins_status grins_racipe_server_destroy(grins_racipe_server_t sv);
 /* Largest time grid (o->n_t) that grins_racipe_integrate_static accepts. */
 #define GRINS_STATIC_MAX_GRID 4096
 
-/* Same computation, arguments, outputs and errors as grins_racipe_integrate,
- * for callers that must not allocate device memory during a call: code that
- * runs inside a host framework owning every device allocation, a real-time
- * loop where cudaMalloc/cudaFree would synchronise the device or block, or a
- * sandbox whose allocation quota is already spent.  The paper has no
- * counterpart; this is an ABI convenience.
- *   - Allocates nothing: no cudaMalloc, cudaFree or allocating library call.
- *     Its scratch (work-queue counter, check words and the device copy of
- *     the time grid) is one fixed array of about 33 KB inside the library,
- *     present on every device that loads the library until the process
- *     exits.  Inputs and outputs are still the caller's buffers.
- *   - The first call on each device looks up that array's device address
- *     (cudaGetSymbolAddress) with the device current; make that first call
- *     before any stream capture.
+/* The integrate call (same arguments, outputs and errors as
+ * grins_racipe_integrate) for callers that must not allocate device memory
+ * during a call: code that runs inside a host framework owning every device
+ * allocation, a real-time loop where cudaMalloc/cudaFree would synchronise
+ * the device or block, or a sandbox whose allocation quota is already spent.
+ * The paper has no counterpart; this is an ABI convenience.
+ *   - Allocates nothing: no cudaMalloc, cudaFree or allocating library call
+ *     (grins_device_allocations does not move across a call).  Its scratch
+ *     (work-queue counter, check words and the device copy of the time
+ *     grid) is one fixed array of about 33 KB inside the library, present on
+ *     every device that loads the library until the process exits.  Inputs
+ *     and outputs are still the caller's buffers.
+ *   - Kernel: it compiles nothing.  The kernel compiled for the network is
+ *     used only when an earlier grins_racipe_integrate call in this process,
+ *     with the same precision and method, compiled and loaded it; otherwise
+ *     the FP32 run-time-layout kernel or the generic FP64 kernel runs -- the
+ *     same equations, step control and steady-state test, so states agree
+ *     within the integration tolerance, but step counts (d_n_steps) and the
+ *     last digits can differ from grins_racipe_integrate's.  The Tsitouras
+ *     pair has no such fallback: without the compiled kernel it returns
+ *     GRINS_E_INVALID_ARG.
+ *   - The first call on each device (and again after the device's context
+ *     is replaced, e.g. by cudaDeviceReset) looks up that array's device
+ *     address with cudaGetSymbolAddress, with the device current.  That
+ *     lookup can load the library's device code onto the device (lazy module
+ *     loading): make the first call before any stream capture.
  *   - Every call, from any handle or thread, shares the one array; the call
- *     clears the counters it needs before launching.  Calls whose work
- *     overlaps on the GPU (different streams, or different host threads)
- *     race on it: serialise them.
+ *     clears the counters it needs before launching, and the array keeps the
+ *     last call's contents otherwise.  Calls whose work overlaps on the GPU
+ *     (different streams, or different host threads) race on it: serialise
+ *     them.
  *   - Extra error: GRINS_E_BUDGET when o->n_t > GRINS_STATIC_MAX_GRID. */
 grins_status grins_racipe_integrate_static(grins_racipe_t h, const grins_solver_opts *o,
                                            const void *d_params, int64_t n_sets,
@@ -474,6 +524,14 @@ grins_status grins_racipe_integrate_static(grins_racipe_t h, const grins_solver_
                                            double *d_states, uint8_t *d_status,
                                            double *d_t_final, float *d_err_est,
                                            int32_t *d_n_steps, double *d_series, void *stream);
+
+/* The borderline re-pass of the last FP32 grins_racipe_integrate call on h
+ * (see grins_solver_opts.tail_rtol): *n_solves = solves it re-integrated in
+ * FP64, *n_attempts = their FP64 step attempts; both 0 when that call did
+ * not run it.  Copies two counters from the device after synchronising
+ * `stream` (the stream of that call).  Errors: GRINS_E_INVALID_ARG for null
+ * pointers. */
+grins_status grins_racipe_tail_stats(grins_racipe_t h, void *stream, int64_t *n_solves, int64_t *n_attempts);
 
 /* Newton polish of states already integrated (the step integrate runs when
  * o->polish is set; exposed so a caller can polish separately).  For every

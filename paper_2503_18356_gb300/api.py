@@ -72,7 +72,9 @@ class grins_solver_opts(C.Structure):
                 ("max_steps", C.c_int64),
                 ("t_grid", C.POINTER(C.c_double)), ("n_t", C.c_int32),
                 ("polish_tol", C.c_double), ("polish_iters", C.c_int32),
-                ("polish_max_move", C.c_double), ("ss_tighten", C.c_double), ("method", C.c_int32)]
+                ("polish_max_move", C.c_double), ("ss_tighten", C.c_double), ("method", C.c_int32),
+                ("tail_rtol", C.c_double), ("tail_start", C.c_double), ("tail_rho", C.c_double),
+                ("tail_late", C.c_double), ("tail_work", C.c_int32), ("pass_event", C.c_void_p)]
 
 
 class grins_racipe_job(C.Structure):
@@ -104,6 +106,7 @@ _sig = {
     "grins_solver_default_opts": (None, [C.POINTER(grins_solver_opts)]),
     "grins_last_error": (C.c_char_p, []),
     "grins_version": (C.c_char_p, []),
+    "grins_device_allocations": (C.c_int64, []),
     "grins_racipe_create": (_S, [C.c_int32, C.c_int32, _P, _P, _P, C.POINTER(_H)]),
     "grins_racipe_destroy": (_S, [_H]),
     "grins_racipe_param_stride": (C.c_int64, [_H]),
@@ -128,6 +131,7 @@ _sig = {
     "grins_racipe_server_copy_results": (_S, [_H, C.c_int64, _P, _P, _P, _P, _P]),
     "grins_racipe_server_release": (_S, [_H, C.c_int64]),
     "grins_racipe_server_destroy": (_S, [_H]),
+    "grins_racipe_tail_stats": (_S, [_H, _P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "grins_racipe_polish": (_S, [_H, C.POINTER(grins_solver_opts), _P, C.c_int64, C.c_int32, _P, _P, _P, _P]),
     "grins_racipe_unique_states": (_S, [_H, _P, _P, _P, C.c_int64, C.c_int32, C.c_double, _P, _P, _P]),
     "grins_racipe_gk_histogram": (_S, [_H, _P, _P, _P, C.c_int64, C.c_int32, C.c_int32, _P, _P]),
@@ -149,6 +153,11 @@ class GrinsError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__("grins status %d: %s" % (status, msg))
         self.status = status
+
+
+def device_allocations() -> int:
+    """grins_device_allocations: device allocations the library has made so far."""
+    return int(_lib.grins_device_allocations())
 
 
 def _check(st):
@@ -345,6 +354,13 @@ class Racipe:
                 _ptr(out["status"]), _ptr(out.get("t_final")), _ptr(out.get("err_est")),
                 _ptr(out.get("n_steps")), _ptr(out.get("series")), _stream(stream)))
         return out
+
+    def tail_stats(self, stream=None):
+        """(solves, FP64 attempts) of the last FP32 integrate's borderline re-pass."""
+        n, a = C.c_int64(0), C.c_int64(0)
+        with torch.cuda.device(self.device):
+            _check(_lib.grins_racipe_tail_stats(self._h, _stream(stream), C.byref(n), C.byref(a)))
+        return n.value, a.value
 
     def polish(self, params, states, status, err_est=None, opts=None, stream=None, **over):
         """FP64 Newton polish in place of converged states (see grins_racipe_polish)."""

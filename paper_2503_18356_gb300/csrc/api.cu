@@ -2,6 +2,7 @@
 // lifetime, argument validation, the incoming-edge CSR, the half-functional
 // median table and the kernel launch sequence of each entry point.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -19,6 +20,7 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>
 #include <nvtx3/nvToolsExt.h>
 
 #include "integrate_grp.cuh"
@@ -59,6 +61,38 @@ static grins_status cuda_fail(cudaError_t e, const char *what)
         cudaError_t _e = (expr);                              \
         if (_e != cudaSuccess) return cuda_fail(_e, what);    \
     } while (0)
+
+// ------------------------------------------------------- device allocations
+// Every device allocation the library makes goes through these three
+// helpers, which count the calls (grins_device_allocations reports the
+// count), so a caller can check that an entry point allocated nothing.
+static std::atomic<long long> g_device_allocations{0};
+
+template <typename T>
+static cudaError_t dev_malloc(T **p, size_t bytes)
+{
+    g_device_allocations.fetch_add(1, std::memory_order_relaxed);
+    return cudaMalloc(reinterpret_cast<void **>(p), bytes);
+}
+
+template <typename T>
+static cudaError_t dev_malloc_async(T **p, size_t bytes, cudaStream_t st)
+{
+    g_device_allocations.fetch_add(1, std::memory_order_relaxed);
+    return cudaMallocAsync(reinterpret_cast<void **>(p), bytes, st);
+}
+
+template <typename T>
+static cudaError_t dev_malloc_pool(T **p, size_t bytes, cudaMemPool_t pool, cudaStream_t st)
+{
+    g_device_allocations.fetch_add(1, std::memory_order_relaxed);
+    return cudaMallocFromPoolAsync(reinterpret_cast<void **>(p), bytes, pool, st);
+}
+
+extern "C" int64_t grins_device_allocations(void)
+{
+    return g_device_allocations.load(std::memory_order_relaxed);
+}
 
 // ------------------------------------------------------------------ handle
 // A lane-group layout on the device (host copy of the row table).
@@ -112,6 +146,12 @@ struct grins_racipe {
     int used_method = 0;                               // and its 5(4) pair
     std::string info;                                  // grins_racipe_integrator text
     int grid_cap = 0;
+    // borderline re-pass workspace: two counters (items listed, FP64
+    // attempts) then the item list, room for tail_cap solves
+    unsigned char *d_tail = nullptr;
+    int64_t tail_cap = 0;
+    bool tail_ran = false;                             // the last FP32 integrate ran the re-pass
+    std::string tail_why = "off";                      // what the last FP32 integrate did about it
     // cached median table
     bool median_valid = false;
     grins_racipe_ranges median_ranges{};
@@ -163,6 +203,12 @@ extern "C" void grins_solver_default_opts(grins_solver_opts *o)
     o->polish_max_move = 1e-2;
     o->ss_tighten = 0.3;
     o->method = GRINS_METHOD_DOPRI5;
+    o->tail_rtol = 1e-9;
+    o->tail_start = 20.0;
+    o->tail_rho = 10.0;
+    o->tail_late = 0.2;
+    o->tail_work = 96;
+    o->pass_event = nullptr;
 }
 
 extern "C" const char *grins_last_error(void) { return g_last_error.c_str(); }
@@ -172,6 +218,9 @@ static void free_device(grins_racipe *h)
 {
     cudaFree(h->d_off); cudaFree(h->d_src); cudaFree(h->d_edge); cudaFree(h->d_sign);
     cudaFree(h->d_edge_sign); cudaFree(h->d_edge_median); cudaFree(h->d_queue); cudaFree(h->d_grid);
+    cudaFree(h->d_tail);
+    h->d_tail = nullptr;
+    h->tail_cap = 0;
     h->grp.free_device();
     h->rr.free_device();
     h->d_off = h->d_src = h->d_edge = nullptr;
@@ -426,16 +475,16 @@ static cudaError_t upload_grp(const GrpHost &g, GrpDev &d)
     d.row_off = g.row_off; d.row_deg = g.row_deg; d.link_to = g.link_to;
     if (g.L <= 0) return cudaSuccess;
     const size_t np = std::max<size_t>(g.pos_edge.size(), 1), nr = g.row_node.size();
-    cudaError_t ce = cudaMalloc(&d.d_pos_edge, sizeof(int32_t) * np);
-    if (ce == cudaSuccess) ce = cudaMalloc(&d.d_pos_off, sizeof(int32_t) * np);
-    if (ce == cudaSuccess) ce = cudaMalloc(&d.d_row_node, sizeof(int32_t) * nr);
+    cudaError_t ce = dev_malloc(&d.d_pos_edge, sizeof(int32_t) * np);
+    if (ce == cudaSuccess) ce = dev_malloc(&d.d_pos_off, sizeof(int32_t) * np);
+    if (ce == cudaSuccess) ce = dev_malloc(&d.d_row_node, sizeof(int32_t) * nr);
     if (ce == cudaSuccess && !g.pos_edge.empty())
         ce = cudaMemcpy(d.d_pos_edge, g.pos_edge.data(), sizeof(int32_t) * g.pos_edge.size(), cudaMemcpyHostToDevice);
     if (ce == cudaSuccess && !g.pos_off.empty())
         ce = cudaMemcpy(d.d_pos_off, g.pos_off.data(), sizeof(int32_t) * g.pos_off.size(), cudaMemcpyHostToDevice);
     if (ce == cudaSuccess)
         ce = cudaMemcpy(d.d_row_node, g.row_node.data(), sizeof(int32_t) * nr, cudaMemcpyHostToDevice);
-    if (ce == cudaSuccess) ce = cudaMalloc(&d.d_row_link, sizeof(int32_t) * nr);
+    if (ce == cudaSuccess) ce = dev_malloc(&d.d_row_link, sizeof(int32_t) * nr);
     if (ce == cudaSuccess)
         ce = cudaMemcpy(d.d_row_link, g.row_link.data(), sizeof(int32_t) * nr, cudaMemcpyHostToDevice);
     return ce;
@@ -496,13 +545,13 @@ extern "C" grins_status grins_racipe_create(int32_t n_nodes, int32_t n_edges, co
     if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
     h->smem_optin = (size_t)optin;
     const size_t Eb = (size_t)std::max(n_edges, 1);
-    if (ce == cudaSuccess) ce = cudaMalloc(&h->d_off, sizeof(int32_t) * (n_nodes + 1));
-    if (ce == cudaSuccess) ce = cudaMalloc(&h->d_src, sizeof(int32_t) * Eb);
-    if (ce == cudaSuccess) ce = cudaMalloc(&h->d_edge, sizeof(int32_t) * Eb);
-    if (ce == cudaSuccess) ce = cudaMalloc(&h->d_sign, Eb);
-    if (ce == cudaSuccess) ce = cudaMalloc(&h->d_edge_sign, Eb);
-    if (ce == cudaSuccess) ce = cudaMalloc(&h->d_edge_median, sizeof(double) * Eb);
-    if (ce == cudaSuccess) ce = cudaMalloc(&h->d_queue, sizeof(unsigned long long) * 4);
+    if (ce == cudaSuccess) ce = dev_malloc(&h->d_off, sizeof(int32_t) * (n_nodes + 1));
+    if (ce == cudaSuccess) ce = dev_malloc(&h->d_src, sizeof(int32_t) * Eb);
+    if (ce == cudaSuccess) ce = dev_malloc(&h->d_edge, sizeof(int32_t) * Eb);
+    if (ce == cudaSuccess) ce = dev_malloc(&h->d_sign, Eb);
+    if (ce == cudaSuccess) ce = dev_malloc(&h->d_edge_sign, Eb);
+    if (ce == cudaSuccess) ce = dev_malloc(&h->d_edge_median, sizeof(double) * Eb);
+    if (ce == cudaSuccess) ce = dev_malloc(&h->d_queue, sizeof(unsigned long long) * 4);
     if (ce == cudaSuccess) ce = cudaMemset(h->d_queue, 0, sizeof(unsigned long long) * 4);
     if (ce == cudaSuccess) ce = cudaMemcpy(h->d_off, h->csr_off.data(), sizeof(int32_t) * (n_nodes + 1), cudaMemcpyHostToDevice);
     if (ce == cudaSuccess && n_edges) ce = cudaMemcpy(h->d_src, h->csr_src.data(), sizeof(int32_t) * n_edges, cudaMemcpyHostToDevice);
@@ -550,6 +599,7 @@ extern "C" const char *grins_racipe_integrator(grins_racipe_t h)
     if (h->ran64)
         h->info += h->jit_used64 ? "; FP64 solver compiled for this network at run time (" + h->jit_why64 + ")"
                                  : "; FP64 solver generic (" + h->jit_why64 + ")";
+    if (ran) h->info += "; borderline re-pass: " + h->tail_why;
     return h->info.c_str();
 }
 
@@ -999,7 +1049,7 @@ extern "C" grins_status grins_racipe_sample_params(grins_racipe_t h, const grins
         if (row_bytes) std::memcpy(blob.data() + tab_bytes, rr.param_ranges, row_bytes);
         if (med_bytes) std::memcpy(blob.data() + tab_bytes + row_bytes, em.data(), med_bytes);
         void *d_blob = nullptr;
-        CUDA_TRY(cudaMallocAsync(&d_blob, blob.size(), st), "sample_params: table buffer");
+        CUDA_TRY(dev_malloc_async(&d_blob, blob.size(), st), "sample_params: table buffer");
         cudaError_t e = cudaMemcpyAsync(d_blob, blob.data(), blob.size(), cudaMemcpyHostToDevice, st);
         unsigned char *base = static_cast<unsigned char *>(d_blob);
         if (!tab.empty()) {
@@ -1029,7 +1079,7 @@ extern "C" grins_status grins_racipe_sample_params(grins_racipe_t h, const grins
             }
             void *d_rows = nullptr;
             const size_t bytes = sizeof(grins_param_range) * (size_t)h->N;
-            CUDA_TRY(cudaMallocAsync(&d_rows, bytes, st), "sample_params: IC rows");
+            CUDA_TRY(dev_malloc_async(&d_rows, bytes, st), "sample_params: IC rows");
             cudaError_t e = cudaMemcpyAsync(d_rows, rr.ic_ranges, bytes, cudaMemcpyHostToDevice, st);
             if (e == cudaSuccess)
                 e = launch_sample_ics(h->N, seed, n_ics, d_ic_unit, static_cast<const grins_param_range *>(d_rows), st);
@@ -1101,7 +1151,7 @@ static void set_tighten(IntegrateArgs *a, const grins_solver_opts *o)
 // register layout exists, else records in shared memory (GRINS_JIT_KIND=grp
 // asks for the latter) -- or leaves the run-time-layout kernel (grp_jit
 // null).  compile = false only looks up kernels an earlier call compiled.
-static void pick_fp32_kernel(const grins_racipe *h, IntegrateArgs *a, bool compile, std::string *why)
+static bool pick_fp32_kernel(const grins_racipe *h, IntegrateArgs *a, bool compile, std::string *why)
 {
     a->grp = h->grp.topo();
     a->grp_jit = nullptr;
@@ -1112,13 +1162,14 @@ static void pick_fp32_kernel(const grins_racipe *h, IntegrateArgs *a, bool compi
         const GrpTopo g = h->rr.topo();
         const void *k = compile ? grp_jit_kernel(g, kJitRegisters, &w, a->method)
                                 : grp_jit_lookup(g, kJitRegisters, a->method);
-        if (k) { a->grp = g; a->grp_jit = k; if (why) *why = w; return; }
+        if (k) { a->grp = g; a->grp_jit = k; if (why) *why = w; return true; }
     }
     if (h->grp.L > 0 && a->method == 0) {
         const void *k = compile ? grp_jit_kernel(a->grp, kJitShared, &w) : grp_jit_lookup(a->grp, kJitShared);
         if (k) a->grp_jit = k;
     }
     if (why) *why = w;
+    return false;
 }
 
 static bool polish_opts_ok(const grins_solver_opts *o)
@@ -1143,6 +1194,14 @@ extern "C" grins_status grins_racipe_polish(grins_racipe_t h, const grins_solver
     CUDA_TRY(launch_polish(polish_args(h, o, d_params, n_sets, n_ics, d_states, d_status, d_err_est),
                            (cudaStream_t)stream, h->num_sms), "polish: launch");
     return GRINS_OK;
+}
+
+static bool tail_opts_ok(const grins_solver_opts *o)
+{
+    if (!(o->tail_rtol >= 0) || !std::isfinite(o->tail_rtol)) return false;
+    if (o->tail_rtol == 0) return true;
+    return o->tail_start >= 1 && std::isfinite(o->tail_start) && o->tail_rho >= 0 && std::isfinite(o->tail_rho) &&
+           o->tail_late >= 0 && std::isfinite(o->tail_late) && o->tail_work >= 0;
 }
 
 static int slots_for(int n_ics)
@@ -1186,6 +1245,7 @@ extern "C" grins_status grins_racipe_integrate(grins_racipe_t h, const grins_sol
     }
     if (o->polish && !polish_opts_ok(o))
         return fail(GRINS_E_INVALID_ARG, "integrate: bad polish options");
+    if (!tail_opts_ok(o)) return fail(GRINS_E_INVALID_ARG, "integrate: bad borderline re-pass options");
     if (!on_handle_device(h)) return fail(GRINS_E_INVALID_ARG, "integrate: current device is not the handle's");
     if (n_sets == 0) return GRINS_OK;
     cudaStream_t st = (cudaStream_t)stream;
@@ -1195,7 +1255,7 @@ extern "C" grins_status grins_racipe_integrate(grins_racipe_t h, const grins_sol
         cudaFree(h->d_grid);
         h->d_grid = nullptr;
         h->grid_cap = 0;
-        CUDA_TRY(cudaMalloc(&h->d_grid, sizeof(double) * o->n_t), "integrate: grid buffer");
+        CUDA_TRY(dev_malloc(&h->d_grid, sizeof(double) * o->n_t), "integrate: grid buffer");
         h->grid_cap = o->n_t;
     }
     if (o->n_t > 0) {
@@ -1222,12 +1282,61 @@ extern "C" grins_status grins_racipe_integrate(grins_racipe_t h, const grins_sol
     a.slots = slots_for(n_ics);
     a.smem_limit = (int32_t)h->smem_optin;
     a.grp = grp_topo(h);
+    IntegrateArgs a64{};             // the borderline re-pass, when it runs
+    bool tail = false;
+    IntegrateArgs::TailItem *tail_sorted = nullptr;   // its list, longest first
     if (o->precision == GRINS_FP32) {
         // grins_racipe_integrator describes the FP32 kernel: only its launches record it
-        pick_fp32_kernel(h, &a, true, &h->jit_why);
+        const bool rr = pick_fp32_kernel(h, &a, true, &h->jit_why);
         h->jit_used = a.grp_jit != nullptr;
         h->used_L = a.grp.L; h->used_R = a.grp.R; h->used_P = a.grp.P;
         h->used_method = a.method;
+        h->tail_ran = false;
+        if (o->tail_rtol <= 0) h->tail_why = "off";
+        else if (o->n_t > 0) h->tail_why = "not run (time series requested)";
+        else if (!rr) h->tail_why = "not run (no FP32 kernel compiled for the network)";
+        else {
+            a64 = a;
+            std::string w64;
+            pick_fp64_kernel(h, &a64, true, &w64);
+            if (!a64.grp_jit) h->tail_why = "not run (no FP64 kernel compiled for the network: " + w64 + ")";
+            else tail = true;
+        }
+        if (tail) {
+            const int64_t n_solves = n_sets * (int64_t)n_ics;
+            if (n_solves > h->tail_cap) {
+                CUDA_TRY(cudaStreamSynchronize(st), "integrate: re-pass buffer");
+                cudaFree(h->d_tail);
+                h->d_tail = nullptr;
+                h->tail_cap = 0;
+                CUDA_TRY(dev_malloc(&h->d_tail, 16 + 2 * sizeof(IntegrateArgs::TailItem) * (size_t)n_solves),
+                         "integrate: re-pass buffer");
+                h->tail_cap = n_solves;
+            }
+            auto *cnt = reinterpret_cast<unsigned long long *>(h->d_tail);
+            auto *items = reinterpret_cast<IntegrateArgs::TailItem *>(h->d_tail + 16);
+            tail_sorted = items + n_solves;
+            CUDA_TRY(cudaMemsetAsync(cnt, 0, 16, st), "integrate: re-pass counters");
+            a.tail_items = items;
+            a.tail_n = cnt;
+            a.f_tail_chk = (float)(o->tail_start * o->ss_tol);
+            a.f_tail_rho = (float)(o->tail_rho * o->ss_tol);
+            a.f_tail_late = (float)o->tail_late;
+            a.tail_work = o->tail_work;
+            a64.tail_items = tail_sorted;
+            a64.tail_n = cnt;
+            a64.rtol = o->tail_rtol;
+            a64.atol = o->atol * (o->tail_rtol / o->rtol);
+            a64.ss_near = 0.0;
+            a64.ss_gain = 1.0;
+            a64.f_rtol = (float)a64.rtol; a64.f_atol = (float)a64.atol;
+            a64.f_ss_near = 0.0f; a64.f_ss_gain = 1.0f;
+            h->tail_ran = true;
+            char buf[160];
+            std::snprintf(buf, sizeof(buf), "FP64 (kernel compiled for the network) from the checkpoint below %g "
+                          "ss_tol at rtol %g", o->tail_start, o->tail_rtol);
+            h->tail_why = buf;
+        }
     } else {
         pick_fp64_kernel(h, &a, true, &h->jit_why64);
         h->jit_used64 = a.grp_jit != nullptr;
@@ -1244,6 +1353,15 @@ extern "C" grins_status grins_racipe_integrate(grins_racipe_t h, const grins_sol
     if (le == cudaErrorInvalidConfiguration)
         return fail(GRINS_E_BUDGET, "integrate: the network needs more shared memory per block than the device has");
     if (le != cudaSuccess) return cuda_fail(le, "integrate: launch");
+    if (o->pass_event)
+        CUDA_TRY(cudaEventRecord(static_cast<cudaEvent_t>(o->pass_event), st), "integrate: pass event");
+    if (tail) {
+        CUDA_TRY(launch_tail_order(a.tail_items, tail_sorted, a.tail_n, n_sets * (long long)n_ics, a.tail_work, st),
+                 "integrate: re-pass order");
+        CUDA_TRY(cudaMemsetAsync(h->d_queue, 0, 2 * sizeof(unsigned long long), st), "integrate: queue reset");
+        le = launch_grp_jit(a64.grp_jit, a64, st, h->num_sms);
+        if (le != cudaSuccess) return cuda_fail(le, "integrate: re-pass launch");
+    }
 
     if (o->polish) {
         CUDA_TRY(launch_polish(polish_args(h, o, d_params, n_sets, n_ics, d_states, d_status, d_err_est), st,
@@ -1251,6 +1369,24 @@ extern "C" grins_status grins_racipe_integrate(grins_racipe_t h, const grins_sol
     } else if (d_err_est) {
         CUDA_TRY(cudaMemsetAsync(d_err_est, 0xff, sizeof(float) * n_sets * n_ics, st), "integrate: err_est");
     }
+    return GRINS_OK;
+}
+
+extern "C" grins_status grins_racipe_tail_stats(grins_racipe_t h, void *stream, int64_t *n_solves,
+                                                int64_t *n_attempts)
+{
+    g_last_error.clear();
+    if (!h || !n_solves || !n_attempts) return fail(GRINS_E_INVALID_ARG, "tail_stats: NULL argument");
+    *n_solves = 0;
+    *n_attempts = 0;
+    if (!h->tail_ran || !h->d_tail) return GRINS_OK;
+    if (!on_handle_device(h)) return fail(GRINS_E_INVALID_ARG, "tail_stats: current device is not the handle's");
+    unsigned long long w[2] = {0, 0};
+    CUDA_TRY(cudaMemcpyAsync(w, h->d_tail, sizeof(w), cudaMemcpyDeviceToHost, (cudaStream_t)stream),
+             "tail_stats: copy");
+    CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream), "tail_stats: synchronise");
+    *n_solves = (int64_t)w[0];
+    *n_attempts = (int64_t)w[1];
     return GRINS_OK;
 }
 
@@ -1682,9 +1818,9 @@ extern "C" grins_status grins_racipe_plan_create(const grins_solver_opts *o, con
     }
     for (int b = 0; b < n_jobs; ++b) cum[b] = tot > 0 ? cum[b] / tot : (b + 1.0) / n_jobs;
     cudaStream_t st = (cudaStream_t)stream;
-    cudaError_t ce = cudaMalloc(&p->d_args, sizeof(IntegrateArgs) * n_jobs);
-    if (ce == cudaSuccess) ce = cudaMalloc(&p->d_cum, sizeof(double) * n_jobs);
-    if (ce == cudaSuccess) ce = cudaMalloc(&p->d_counters, sizeof(unsigned long long) * 4 * n_jobs);
+    cudaError_t ce = dev_malloc(&p->d_args, sizeof(IntegrateArgs) * n_jobs);
+    if (ce == cudaSuccess) ce = dev_malloc(&p->d_cum, sizeof(double) * n_jobs);
+    if (ce == cudaSuccess) ce = dev_malloc(&p->d_counters, sizeof(unsigned long long) * 4 * n_jobs);
     if (ce == cudaSuccess) ce = cudaMemcpy(p->d_cum, cum.data(), sizeof(double) * n_jobs, cudaMemcpyHostToDevice);
     if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking);
     if (ce != cudaSuccess) { plan_free(p); delete p; return cuda_fail(ce, "plan_create: device buffers"); }
@@ -1901,7 +2037,7 @@ grins_status server_launch(grins_racipe_server *sv, ServerRequest &r)
 {
     cudaStream_t st = sv->streams[r.slot];
     const int64_t S = r.n_sets, I = r.n_ics, N = r.net->N;
-    CUDA_TRY(cudaMallocFromPoolAsync(reinterpret_cast<void **>(&r.mem), (size_t)r.bytes, sv->pool, st),
+    CUDA_TRY(dev_malloc_pool(reinterpret_cast<void **>(&r.mem), (size_t)r.bytes, sv->pool, st),
              "server: request buffers");
     unsigned char *q = r.mem;
     auto take = [&](int64_t b) { unsigned char *x = q; q += align256(b); return x; };
@@ -2263,13 +2399,16 @@ extern "C" int grins_debug_check_status(grins_racipe_t h, long long *info)
 // ------------------------------------------------- integrate, no allocation
 // grins_racipe_integrate_static: the integrate entry point for callers that
 // cannot allocate device memory.  Its scratch -- the work-queue counter, the
-// largest-exponent word, the check words and the device copy of the time
-// grid -- lives in the fixed array below instead of the handle's workspace,
-// and nothing is allocated per call.  Every device that loads the library
-// holds this array until the process exits.
+// check words and the device copy of the time grid -- lives in the fixed
+// array below instead of the handle's workspace, and nothing is allocated
+// per call.  Every device that loads the library holds this array until the
+// process exits.
 namespace {
 
-constexpr int kStaticWords = 4;   // queue, nmax, check code, check info
+// Words at the head of the array: 0 the work-queue counter, 1 reserved (kept
+// zero; the check words sit at a fixed offset), 2-3 the first index/alignment
+// violation of a checked build (code, offending index).
+constexpr int kStaticWords = 4;
 constexpr size_t kStaticBytes = kStaticWords * sizeof(unsigned long long) +
                                 (size_t)GRINS_STATIC_MAX_GRID * sizeof(double);
 
@@ -2277,27 +2416,82 @@ static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
 
 constexpr int kStaticMaxDevices = 64;
 std::mutex g_static_mu;
-unsigned char *g_static_addr[kStaticMaxDevices] = {};
+struct StaticAddr {
+    unsigned long long ctx_id = 0;     // the context the address belongs to (0: not looked up)
+    unsigned char *addr = nullptr;
+};
+StaticAddr g_static_addr[kStaticMaxDevices];
+
+// Unique id of the current CUDA context (cuCtxGetId through the runtime's
+// driver entry points; ids are never reused within a process), so that the
+// address looked up in a context is not used in a later one, for example
+// after cudaDeviceReset.  0 when the driver cannot say.
+unsigned long long current_context_id()
+{
+    using GetCur = CUresult (*)(CUcontext *);
+    using GetId = CUresult (*)(CUcontext, unsigned long long *);
+    static GetCur get_cur = nullptr;
+    static GetId get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_cur = reinterpret_cast<GetCur>(f);
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<GetId>(f);
+    });
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (get_cur && get_id && get_cur(&c) == CUDA_SUCCESS && c && get_id(c, &id) == CUDA_SUCCESS) return id;
+    return 0;
+}
 
 // Device address of g_static_scratch on the current device, looked up once
-// per device (host code must not use the symbol itself: it names a host-side
-// shadow, not device memory).
+// per device and context (host code must not use the symbol itself: it
+// names a host-side shadow, not device memory).  The first lookup in a
+// context may load the library's device code there (lazy module loading).
 grins_status static_scratch(int device, unsigned char **out)
 {
     if (device < 0 || device >= kStaticMaxDevices)
         return fail(GRINS_E_INVALID_ARG, "integrate_static: device %d outside [0, %d)", device, kStaticMaxDevices);
+    // the handle's allocations already made this device's context current;
+    // with no context id (0) the address is looked up again on every call
+    const unsigned long long ctx = current_context_id();
     std::lock_guard<std::mutex> lock(g_static_mu);
-    if (!g_static_addr[device]) {
+    StaticAddr &a = g_static_addr[device];
+    if (!a.addr || ctx == 0 || a.ctx_id != ctx) {
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
         if (e != cudaSuccess) return cuda_fail(e, "integrate_static: cudaGetSymbolAddress");
-        g_static_addr[device] = static_cast<unsigned char *>(p);
+        a.addr = static_cast<unsigned char *>(p);
+        a.ctx_id = ctx;
     }
-    *out = g_static_addr[device];
+    *out = a.addr;
     return GRINS_OK;
 }
 
 }  // namespace
+
+#ifdef GRINS_CHECKED
+// Checked builds only: the first index/alignment violation recorded by a
+// grins_racipe_integrate_static call on the current device (its kernels
+// write their check words into the static array, not the handle's).
+extern "C" int grins_debug_static_check_status(long long *info)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+    unsigned char *scratch = nullptr;
+    if (static_scratch(dev, &scratch) != GRINS_OK) return -1;
+    unsigned long long w[2] = {0, 0};
+    if (cudaMemcpy(w, scratch + 2 * sizeof(unsigned long long), sizeof(w), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return -1;
+    if (info) *info = (long long)w[1];
+    return (int)w[0];
+}
+#endif
 
 extern "C" grins_status grins_racipe_integrate_static(grins_racipe_t h, const grins_solver_opts *o,
                                                       const void *d_params, int64_t n_sets,

@@ -124,6 +124,20 @@ struct IntegrateArgs {
     int32_t smem_limit;          // opt-in shared memory per block, bytes
     GrpTopo grp;                 // lane-group layout (grp.L == 0: not available)
     const void *grp_jit;         // host: kernel compiled for this layout, or null
+    // Borderline re-pass (FP32 register-record kernel writes, FP64 one reads;
+    // all null / zero when off).  The FP32 pass keeps a checkpoint -- the
+    // first accepted state with residual < tail_chk -- and, for a solve whose
+    // steady-state decision falls near t_end (t_end reached with final
+    // residual < tail_rho, or converged with t_end - t < tail_late (t - t_c))
+    // and which took at most tail_work attempts after its checkpoint, leaves
+    // that state in `states`, appends (solve, t_c, those attempts) to
+    // tail_items and bumps tail_n.  The FP64 pass, given the same list,
+    // integrates each from its checkpoint to its status.
+    struct TailItem { int64_t idx; float t; int32_t work; };
+    TailItem *tail_items;        // [n_sets * n_ics] capacity
+    unsigned long long *tail_n;  // [2]: items appended, FP64 attempts spent on them
+    float f_tail_chk, f_tail_rho, f_tail_late;
+    int32_t tail_work;
 };
 
 // Jobs of one batched launch (a plan): per-job arguments as for a single
@@ -158,6 +172,11 @@ cudaError_t launch_integrate_fp32(const IntegrateArgs &a, cudaStream_t st, int n
 cudaError_t launch_integrate_batch(const BatchArgs &b, int warps, cudaStream_t st, int num_sms,
                                    int smem_limit);
 cudaError_t launch_integrate_fp64(const IntegrateArgs &a, cudaStream_t st, int num_sms);
+// The borderline re-pass list `in` (n_in[0] items) copied to `out` longest
+// first (by the FP32 pass's attempts after the checkpoint, in buckets of
+// max_work / 64), for the FP64 pass.
+cudaError_t launch_tail_order(const IntegrateArgs::TailItem *in, IntegrateArgs::TailItem *out,
+                              const unsigned long long *n_in, long long cap, int max_work, cudaStream_t st);
 #endif
 
 // ----------------------------------------------------------------- polish

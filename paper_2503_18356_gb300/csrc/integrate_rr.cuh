@@ -556,7 +556,18 @@ __device__ __forceinline__ void rr_body(const IntegrateArgs &a)
     const Real ss_tol = rr_argr<Real>(a.ss_tol, a.f_ss_tol);
     const Real t_end = rr_argr<Real>(a.t_end, a.f_t_end);
     const Real invN = (Real)1 / (Real)N;
-    const long long total = a.n_sets * (long long)a.n_ics;
+    // FP64 list mode: the solves to integrate are the borderline ones the
+    // FP32 pass listed, each from its checkpoint (state in `states`, time in
+    // the list); FP32 tail mode: keep checkpoints and list borderline solves
+    const bool from_list = F64 && a.tail_items != nullptr;
+    const bool tail_on = !F64 && a.tail_items != nullptr;
+    const long long n_solves = a.n_sets * (long long)a.n_ics;
+    const unsigned long long listed = from_list ? *a.tail_n : 0ull;
+    const long long total = from_list ? (listed < (unsigned long long)n_solves ? (long long)listed : n_solves) : n_solves;
+    const float tail_chk = tail_on ? a.f_tail_chk : -1.0f;
+    bool has_chk = false;            // this solve's checkpoint is written
+    Real t_c = 0;                    // and its time
+    int steps_c = 0;                 // and the attempts before it
 
     long long my_set = 0;
     int my_ic = 0;
@@ -582,6 +593,13 @@ __device__ __forceinline__ void rr_body(const IntegrateArgs &a)
     // item it = set * n_ics + ic -> this lane's records, rows and state
     auto start = [&](long long it) {
         if (!GRINS_OK_IDX(it >= 0 && it < total, 35, it)) it = 0;
+        Real t_start = (Real)a.t0;
+        if (from_list) {
+            const typename IntegrateArgs::TailItem ti = a.tail_items[it];
+            it = ti.idx;
+            if (!GRINS_OK_IDX(it >= 0 && it < n_solves, 36, it)) it = 0;
+            t_start = (Real)ti.t;
+        }
         my_set = it / a.n_ics;
         my_ic = (int)(it - my_set * a.n_ics);
         const unsigned char *blk = a.params + my_set * a.L.stride;
@@ -603,11 +621,12 @@ __device__ __forceinline__ void rr_body(const IntegrateArgs &a)
                 q.Gp[r] = (Real)Gp;
                 q.k[r] = (Real)k;
                 q.kg[r] = (Real)(k / G);
-                if constexpr (F64) y[r] = u0[node] * G / k;
+                if constexpr (F64) y[r] = from_list ? a.states[it * N + node] : u0[node] * G / k;
                 else y[r] = __fdividef((float)u0[node] * (float)G, (float)k);
             }
         }
-        t = (Real)a.t0;
+        t = (Real)t_start;
+        has_chk = false;
         steps = 0;
         gidx = 0;
         need_k1 = true;
@@ -683,9 +702,10 @@ __device__ __forceinline__ void rr_body(const IntegrateArgs &a)
 #pragma unroll
                 for (int r = 0; r < NPL; ++r) k1[r] = z[r];
                 h = (d0 < (Real)1e-5 || d1 < (Real)1e-5) ? (Real)1e-6 : (Real)0.01 * d0 / d1;
-                h = rr_min(h, (Real)(a.t_end - a.t0));
+                h = rr_min(h, t_end - t);
                 if (!fin) { done = true; st_code = GRINS_SS_NONFINITE; }
                 else if (res < ss_tol) { done = true; st_code = GRINS_SS_CONVERGED; }
+                else if (!(t < t_end)) { done = true; st_code = GRINS_SS_TEND; }   // a checkpoint at t_end
             }
         }
 
@@ -776,6 +796,20 @@ __device__ __forceinline__ void rr_body(const IntegrateArgs &a)
 #pragma unroll
             for (int r = 0; r < NPL; ++r) { y[r] = k2[r]; k1[r] = z[r]; }
             near = res < ss_near;
+            if constexpr (!F64) {
+                if (res < tail_chk && !has_chk && !done) {
+                    // checkpoint: the first accepted state below tail_chk
+                    has_chk = true;
+                    t_c = t;
+                    steps_c = steps;
+                    double *dst = a.states + (my_set * a.n_ics + my_ic) * N;
+#pragma unroll
+                    for (int r = 0; r < NPL; ++r) {
+                        const int node = a.grp.row_node[r * L + j];
+                        if (node >= 0) dst[node] = (double)y[r];
+                    }
+                }
+            }
             if (!done) {
                 if (res < ss_tol) { done = true; st_code = GRINS_SS_CONVERGED; }
                 else if (t >= t_end) { done = true; st_code = GRINS_SS_TEND; }
@@ -790,17 +824,41 @@ __device__ __forceinline__ void rr_body(const IntegrateArgs &a)
         if (__any_sync(FULL, done)) {
             if (done) {
                 long long idx = my_set * a.n_ics + my_ic;
-                if (!GRINS_OK_IDX(idx >= 0 && idx < total, 35, idx)) idx = 0;
-                double *dst = a.states + idx * N;
+                if (!GRINS_OK_IDX(idx >= 0 && idx < n_solves, 35, idx)) idx = 0;
+                // a borderline decision goes to the FP64 pass: t_end reached
+                // with the residual close to ss_tol, or converged so late that
+                // the time the residual took to fall from the checkpoint's
+                // level says the crossing may lie past t_end
+                bool relist = false;
+                if constexpr (!F64) {
+                    if (has_chk && steps - steps_c <= a.tail_work) {
+                        if (st_code == GRINS_SS_TEND) relist = res < a.f_tail_rho;
+                        else if (st_code == GRINS_SS_CONVERGED) relist = t_end - t < a.f_tail_late * (t - t_c);
+                    }
+                }
+                if (!relist) {
+                    double *dst = a.states + idx * N;
 #pragma unroll
-                for (int r = 0; r < NPL; ++r) {
-                    const int node = a.grp.row_node[r * L + j];
-                    if (node >= 0) dst[node] = (double)y[r];
+                    for (int r = 0; r < NPL; ++r) {
+                        const int node = a.grp.row_node[r * L + j];
+                        if (node >= 0) dst[node] = (double)y[r];
+                    }
                 }
                 if (j == 0) {
                     a.status[idx] = (uint8_t)st_code;
                     if (a.t_final) a.t_final[idx] = (double)t;
-                    if (a.n_steps) a.n_steps[idx] = steps;
+                    if (from_list) {
+                        atomicAdd(a.tail_n + 1, (unsigned long long)steps);
+                        if (a.n_steps) a.n_steps[idx] += steps;      // after the FP32 pass's attempts
+                    } else if (a.n_steps) {
+                        a.n_steps[idx] = steps;
+                    }
+                    if (relist) {
+                        const unsigned long long k = atomicAdd(a.tail_n, 1ull);
+                        // at most one entry per solve: the list holds n_sets * n_ics
+                        if (k < (unsigned long long)n_solves)
+                            a.tail_items[k] = typename IntegrateArgs::TailItem{idx, (float)t_c, steps - steps_c};
+                    }
                 }
 #pragma unroll 1
                 while (gidx < a.n_t) { write_series(gidx); ++gidx; }

@@ -46,6 +46,21 @@ def main(out_path, which):
             f.argtypes = [C.c_void_p, C.POINTER(C.c_longlong)]
             info = C.c_longlong(0)
             codes[name] = (f(h._h, C.byref(info)), info.value)
+            # the no-allocation entry point writes its check words into the
+            # library's static array, read by their own accessor
+            N = topo.n_nodes
+            buf = dict(states=torch.empty((S, I, N), dtype=torch.float64, device=params.device),
+                       status=torch.empty((S, I), dtype=torch.uint8, device=params.device),
+                       t_final=torch.empty((S, I), dtype=torch.float64, device=params.device),
+                       err_est=torch.empty((S, I), dtype=torch.float32, device=params.device),
+                       n_steps=torch.empty((S, I), dtype=torch.int32, device=params.device))
+            h.integrate_static(params, ic, buf)
+            torch.cuda.synchronize()
+            fs = api._lib.grins_debug_static_check_status
+            fs.restype = C.c_int
+            fs.argtypes = [C.POINTER(C.c_longlong)]
+            info = C.c_longlong(0)
+            codes[name + "_static"] = (fs(C.byref(info)), info.value)
         h.close()
     np.savez(out_path, **res)
     print("CHECK", codes)

@@ -61,9 +61,9 @@ def test_plan_matches_oracle_and_replays_exactly(autotune):
         p = O.ParamSet(G, k, T, lam, n.astype(np.int32))
         o = O.run_sets_parallel(O.Network(*topo.edges()), p, jb["ic_unit"].cpu().numpy(), threads=PT.THREADS)
         gs = {kk: v[:S] for kk, v in g.items()}
-        c = PT.compare_states(gs, o, p, 1e-6)
+        c = PT.compare_states(gs, o, p, 1e-6, O.Network(*topo.edges()))
         print(topo.name, topo.n_nodes, topo.n_edges, c)
-        assert c["max_rel"] <= 1e-6
+        assert c["max_err"] <= 1e-6 and c["n_uncertified"] == 0
         assert c["n_basin"] <= max(1, 0.01 * gs["status"].size)
         assert c["status_agree"] >= 0.95
         bad = np.where(gs["n_unique"] != o["n_unique"])[0]

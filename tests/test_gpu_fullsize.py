@@ -9,7 +9,8 @@ Bars (the same as the small parity tests):
   * polished states: relative 1e-6 (floor 1e-6 G/k); plain FP64: 1e-3 on the
     G/k scale;
   * distinct steady states per set: every mismatch explained by a solve
-    whose status differs, and mismatches below 2 % of the sampled sets;
+    whose status differs, and mismatches within 0.1 % of the sampled sets
+    (none at these sample sizes);
   * at full size: statuses valid, converged states finite and within
     [0, G/k] (up to 1e-4 of G/k: unpolished states stop within the
     steady-state tolerance), state ids and counts consistent; on the sampled
@@ -73,9 +74,9 @@ def check_full_size(w, precision, polish, n_sample, rel_tol, normalised, method=
     p = O.ParamSet(*(np.concatenate([getattr(r, f) for r in ref_p]) for f in ("G", "k", "T", "lam", "n")))
     o = O.run_sets_parallel(net, p, icn, threads=PT.THREADS, polish=bool(polish), method=method)
     g = dict(states=states[pick], status=status[pick])
-    c = PT.compare_states(g, o, p, rel_tol, normalised=normalised)
+    c = PT.compare_states(g, o, p, rel_tol, net, normalised=normalised)
     print(w["topology"].name, "sampled", len(pick), c)
-    assert c["max_rel"] <= rel_tol
+    assert c["max_err"] <= rel_tol and c["n_uncertified"] == 0
     assert c["n_basin"] <= 0.01 * g["status"].size
     assert c["status_agree"] >= 0.98
     if polish:
@@ -88,7 +89,8 @@ def check_full_size(w, precision, polish, n_sample, rel_tol, normalised, method=
         assert worst < 1e-11, worst
     bad = np.flatnonzero(nu[pick] != o["n_unique"])
     st_diff = np.any(g["status"] != o["status"], axis=1)
-    assert len(bad) <= 0.02 * len(pick)
+    print("n_unique mismatches on the sampled sets", [int(pick[b]) for b in bad])
+    assert len(bad) <= 0.001 * len(pick)
     assert all(st_diff[b] for b in bad), [int(pick[b]) for b in bad]
 
 

@@ -400,10 +400,10 @@ def test_toggle_switch_states(precision, polish, tol):
     params, ic, p, icn = PT.gpu_sample(h, w["param_seed"], 120, w["n_ics"])
     g = run_gpu(h, params, ic, precision=precision, polish=polish)
     o = oracle_run(w["topology"], p, icn)
-    c = PT.compare_states(g, o, p, tol, normalised=not polish)
+    c = PT.compare_states(g, o, p, tol, O.Network(*w["topology"].edges()), normalised=not polish)
     print("TS", precision, polish, c)
     assert c["n_compared"] > 0.9 * g["status"].size
-    assert c["max_rel"] <= tol
+    assert c["max_err"] <= tol and c["n_uncertified"] == 0
     assert c["n_basin"] <= 0.01 * g["status"].size
     assert c["status_agree"] >= 0.98
 
@@ -417,9 +417,9 @@ def test_random_networks_fp32_polish_and_raw(wl, S):
     o = oracle_run(w["topology"], p, icn)
     for polish, tol in [(1, 1e-6), (0, 1e-3)]:
         g = run_gpu(h, params, ic, precision=1, polish=polish)
-        c = PT.compare_states(g, o, p, tol, normalised=not polish)
+        c = PT.compare_states(g, o, p, tol, O.Network(*w["topology"].edges()), normalised=not polish)
         print(wl, polish, c, np.bincount(g["status"].ravel(), minlength=5))
-        assert c["max_rel"] <= tol
+        assert c["max_err"] <= tol and c["n_uncertified"] == 0
         assert c["n_basin"] <= max(1, 0.01 * g["status"].size)
         assert c["status_agree"] >= 0.97
         if polish:
@@ -443,10 +443,10 @@ def test_dense_network_steep_hill_extreme_fold_changes(n):
     o = O.run_sets_parallel(O.Network(*topo.edges()), p, icn, threads=PT.THREADS)
     for polish, tol in [(1, 1e-6), (0, 1e-3)]:
         g = run_gpu(h, params, ic, precision=1, polish=polish)
-        c = PT.compare_states(g, o, p, tol, normalised=not polish)
+        c = PT.compare_states(g, o, p, tol, O.Network(*topo.edges()), normalised=not polish)
         print(n, polish, h.integrator(), c, np.bincount(g["status"].ravel(), minlength=5))
         assert c["n_compared"] >= 100            # steep Hill: many solves end at t_end on both sides
-        assert c["max_rel"] <= tol
+        assert c["max_err"] <= tol and c["n_uncertified"] == 0
         assert c["n_basin"] <= max(1, 0.01 * g["status"].size)
         assert c["status_agree"] >= 0.97
         assert not np.any((g["status"] == O.NONFINITE) & (o["status"] != O.NONFINITE))
@@ -458,12 +458,17 @@ def test_fp64_random_network():
     params, ic, p, icn = PT.gpu_sample(h, w["param_seed"], 24, 10)
     g = run_gpu(h, params, ic, precision=0, polish=0)
     o = oracle_run(w["topology"], p, icn)
-    c = PT.compare_states(g, o, p, 1e-3, normalised=True)
+    c = PT.compare_states(g, o, p, 1e-3, O.Network(*w["topology"].edges()), normalised=True)
     print("fp64 net22", c)
-    assert c["max_rel"] <= 1e-3 and c["status_agree"] >= 0.97
+    assert c["max_err"] <= 1e-3 and c["status_agree"] >= 0.97 and c["n_uncertified"] == 0
 
 
-def test_n_unique_agreement_net22():
+def test_n_unique_mismatches_explained_net22():
+    """400 sets of the 22-node workload against the oracle run here: every set
+    whose distinct-state count differs has a solve whose status differs (a
+    slow solve meeting the steady-state condition near t_end on one side
+    only), and such sets stay within the 99.9 % bar (at most 0.4 here; the
+    bar itself is held on 10,000 sets by test_n_unique_bar_net22_10k_sets)."""
     w = W.net22_workload()
     h = PT.gpu_handle(w["topology"])
     S, I = 400, 10
@@ -474,9 +479,6 @@ def test_n_unique_agreement_net22():
     o = oracle_run(w["topology"], p, icn)
     nu = nu.cpu().numpy()
     bad = np.where(nu != o["n_unique"])[0]
-    # a mismatch must come from a solve whose status differs (a slowly
-    # converging solve that meets the steady-state condition near t_end on
-    # one side only) or from two states that lie at the dedupe tolerance
     st_diff = np.any(g["status"] != o["status"], axis=1)
     unexplained = [int(s) for s in bad if not st_diff[s]]
     for s in bad:
@@ -484,14 +486,44 @@ def test_n_unique_agreement_net22():
               "oracle", o["n_unique"][s], o["status"][s], o["t_final"][s].round(1))
     print("n_unique mismatches", len(bad), "of", S, "hist", np.bincount(o["n_unique"]),
           "status agreement", np.mean(g["status"] == o["status"]))
-    assert len(bad) <= 0.01 * S
+    assert len(bad) <= 0.001 * S
     assert not unexplained, unexplained
+
+
+def test_n_unique_bar_net22_10k_sets():
+    """The distinct-steady-state count per set (Sec. 3.1) matches the
+    oracle's on at least 99.9 % of sets: sets 0..9999 of the 22-node
+    workload (100,000 solves; FP32 + the FP64 borderline re-pass + FP64
+    polish + dedupe, the library's defaults) against the oracle's counts
+    stored by tests/golden/make_net22_reference.py (FP64, rtol 1e-10)."""
+    from tests.golden import make_net22_reference as R
+    ref_status, ref_nu = R.load()
+    S = ref_nu.size
+    w = W.net22_workload()
+    h = PT.gpu_handle(w["topology"])
+    params, ic = h.sample_params(w["param_seed"], S, w["n_ics"])
+    out = h.integrate(params, ic)
+    sid, nu = h.unique_states(params, out["states"], out["status"])
+    n_tail, a_tail = h.tail_stats()
+    torch.cuda.synchronize()
+    nu = nu.cpu().numpy()
+    st = out["status"].cpu().numpy()
+    bad = np.flatnonzero(nu != ref_nu)
+    conv_agree = float(np.mean((st == 0) == (ref_status == 0)))
+    print("sets", S, "n_unique mismatches", len(bad), bad[:20].tolist(), "converged-status agreement", conv_agree,
+          "re-pass", n_tail, a_tail)
+    assert n_tail > 0
+    assert 1.0 - len(bad) / S >= 0.999
+    # every mismatched set has a solve whose convergence differs
+    st_diff = np.any((st == 0) != (ref_status == 0), axis=1)
+    assert all(st_diff[b] for b in bad), [int(b) for b in bad if not st_diff[b]]
+    h.close()
 
 
 @pytest.mark.parametrize("precision", [1, 0])
 def test_time_series(precision):
     """Time series on a fixed grid (FP32 and the plain FP64 solver), relative
-    1e-3 against the oracle's."""
+    1e-3 against the oracle's (floor 1e-6 G/k, G12)."""
     w = W.net5_workload()
     h = PT.gpu_handle(w["topology"])
     params, ic, p, icn = PT.gpu_sample(h, w["param_seed"], 40, 8)
@@ -499,7 +531,7 @@ def test_time_series(precision):
     g = run_gpu(h, params, ic, precision=precision, polish=0, t_grid=grid)
     o = oracle_run(w["topology"], p, icn, series=True, t_grid=grid)
     G = p.G[:, None, None, :]; k = p.k[:, None, None, :]
-    err = PT.rel_err(g["series"], o["series"], G, k, floor=1e-3)
+    err = PT.rel_err(g["series"], o["series"], G, k, floor=1e-6)
     # grid points before both sides stopped (after a stop the final state is held)
     stop = np.minimum(g["t_final"], o["t_final"])[:, :, None] >= grid[None, None, :]
     e = err.max(axis=-1)[stop]
@@ -542,9 +574,9 @@ def test_large_network_generic_path_and_max_nodes():
         o = oracle_run(topo, p, icn)
         for prec, polish, tol in [(1, 1, 1e-6), (0, 0, 1e-3)]:
             g = run_gpu(h, params, ic, precision=prec, polish=polish)
-            c = PT.compare_states(g, o, p, tol, normalised=not polish)
+            c = PT.compare_states(g, o, p, tol, O.Network(*topo.edges()), normalised=not polish)
             print(N, prec, c)
-            assert c["max_rel"] <= tol and c["status_agree"] >= 0.9
+            assert c["max_err"] <= tol and c["status_agree"] >= 0.9 and c["n_uncertified"] == 0
 
 
 def test_self_loops_tssa():
@@ -553,8 +585,8 @@ def test_self_loops_tssa():
     params, ic, p, icn = PT.gpu_sample(h, 77, 100, 20)
     g = run_gpu(h, params, ic, precision=1, polish=1)
     o = oracle_run(topo, p, icn)
-    c = PT.compare_states(g, o, p, 1e-6)
-    assert c["max_rel"] <= 1e-6 and c["n_basin"] <= 0.01 * g["status"].size
+    c = PT.compare_states(g, o, p, 1e-6, O.Network(*topo.edges()))
+    assert c["max_err"] <= 1e-6 and c["n_basin"] <= 0.01 * g["status"].size and c["n_uncertified"] == 0
 
 
 def test_invalid_arguments_report_errors():
