@@ -53,7 +53,7 @@ def parse():
                     help="sets per step of the reference arm (the oracle timed on the host cores)")
     ap.add_argument("--fp64-sets", type=int, default=N_SETS,
                     help="sets of the plain FP64 GPU solver's timed run (default: the whole workload)")
-    ap.add_argument("--serve-seconds", type=float, default=6.0,
+    ap.add_argument("--serve-seconds", type=float, default=60.0,
                     help="length of the Poisson request stream of the serving measurement (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=20.0, help="requests per second of that stream")
     ap.add_argument("--batch-reps", type=int, default=3,
@@ -396,11 +396,11 @@ def run_reference(args):
 # ------------------------------------------------------------------ batched
 def batched_measurement(dev, reps):
     """One plan over the 64 uneven networks of the batched workload (2-40
-    nodes, density 0.1-0.3, 100-10k sets log-uniform, 10 ICs each): one
-    persistent integrator launch, then each job's polish and dedupe, captured
-    in a CUDA graph and autotuned at creation (untimed).  Timed: `reps`
-    replays of the graph after one warm-up replay, CUDA events on the
-    stream."""
+    nodes, density 0.1-0.3, 100-10k sets log-uniform, 10 ICs each), captured
+    in a CUDA graph and autotuned at creation (untimed; the autotuner's pick
+    -- normally one persistent launch of the kernel compiled for every job's
+    layout -- then each job's polish and dedupe).  Timed: `reps` replays of
+    the graph after one warm-up replay, CUDA events on the stream."""
     import torch
     from paper_2503_18356_gb300 import api, workloads as W
 
@@ -423,9 +423,24 @@ def batched_measurement(dev, reps):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / reps
     info = plan.info()
+    # the SFU work of record over the jobs (W_SFU = 6E + N per step attempt
+    # of one solve), per replay, against the SFU peak at the maximum SM clock:
+    # a lower bound on the integrator's fraction, the replay also holding the
+    # jobs' polish and dedupe
+    work = 0.0
+    for jb in plan.jobs:
+        h = jb["net"]
+        work += float(jb["out"]["n_steps"].double().sum().item()) * (6 * h.n_edges + h.n_nodes)
+    props = torch.cuda.get_device_properties(dev)
+    peak = 16 * props.multi_processor_count * 2070e6
+    achieved = work / (ms / 1e3)
     plan.close()
     return dict(networks=len(jobs), solves=solves, ms_per_replay=ms, solves_per_s=solves / (ms / 1e3),
                 plan=info, reps=reps,
+                roofline=dict(bound="alu", achieved=achieved / 1e9, peak=peak / 1e9, unit="Gop/s (MUFU, SFU pipe)",
+                              frac=achieved / peak,
+                              basis="sum over jobs of step attempts x (6E + N) per replay / replay time (polish "
+                                    "and dedupe included) / (16 x %d SMs x 2070 MHz)" % props.multi_processor_count),
                 workload="64 seeded random signed networks of 2-40 nodes, density 0.1-0.3, 100-10k sets "
                          "(log-uniform) x 10 ICs, FP32 + FP64 polish + dedupe, one CUDA-graph replay")
 
@@ -457,12 +472,16 @@ def serving_measurement(dev, seconds, rate):
     sv.release(rid)
     n = len(stream)
     ids, nets, infos, t_ret = [None] * n, [None] * n, [None] * n, [0.0] * n
+    work = [0.0] * n              # SFU work of record: step attempts x (6E + N)
     ready = th.Semaphore(0)
 
     def releaser():
         for k in range(n):
             ready.acquire()
             infos[k] = sv.wait(ids[k])
+            if infos[k]["state"] == api.REQ_DONE:
+                steps = sv.results(ids[k], keys=("n_steps",))["n_steps"]
+                work[k] = float(steps.double().sum().item()) * (6 * nets[k].n_edges + nets[k].n_nodes)
             sv.release(ids[k])
 
     t = th.Thread(target=releaser)
@@ -483,11 +502,20 @@ def serving_measurement(dev, seconds, rate):
     sv.close()
     for h in nets:
         h.close()
+    props = __import__("torch").cuda.get_device_properties(dev)
+    peak = 16 * props.multi_processor_count * 2070e6
+    offered = sum(r["n_sets"] * r["n_ics"] for r in stream) / seconds
     srv = np.array([x["latency_s"] for x in infos]) * 1e3
     lat = srv + (np.array(t_ret) - np.array([r["arrival_s"] for r in stream])) * 1e3
     que = np.array([x["queued_s"] for x in infos]) * 1e3
     return dict(requests=n, rate_hz=rate, stream_s=seconds, wall_s=wall, solves=solves,
-                solves_per_s=solves / wall, p50_ms=float(np.percentile(lat, 50)),
+                solves_per_s=solves / wall, offered_solves_per_s=offered,
+                roofline=dict(bound="alu", frac=sum(work) / wall / peak, achieved=sum(work) / wall / 1e9,
+                              peak=peak / 1e9, unit="Gop/s (MUFU, SFU pipe)",
+                              basis="sum over requests of step attempts x (6E + N) / wall time from the first "
+                                    "arrival to the last completion (sampling, polish, dedupe, compiles and idle "
+                                    "gaps included) / (16 x %d SMs x 2070 MHz)" % props.multi_processor_count),
+                p50_ms=float(np.percentile(lat, 50)),
                 p99_ms=float(np.percentile(lat, 99)), max_ms=float(lat.max()),
                 server_p50_ms=float(np.percentile(srv, 50)), server_p99_ms=float(np.percentile(srv, 99)),
                 queued_p50_ms=float(np.percentile(que, 50)), queued_p99_ms=float(np.percentile(que, 99)),

@@ -348,10 +348,10 @@ const char *grins_racipe_integrator(grins_racipe_t h);
  * Batched form of the path (the production "batching" form of the hot
  * path; the paper's simulator runs one network per call): many networks of
  * uneven node and edge counts and uneven ensemble sizes are integrated in
- * one persistent launch of the FP32 lane-group kernel -- each warp visits
- * the jobs in turn and takes parameter sets from each job's work counter --
- * followed by each job's FP64 polish (o->polish) and dedupe.  The work is
- * captured once into a CUDA graph; grins_racipe_plan_run replays it. */
+ * one persistent launch -- each warp visits the jobs in turn and takes
+ * solves from each job's work counter -- followed by each job's FP64 polish
+ * (o->polish) and dedupe.  The work is captured once into a CUDA graph;
+ * grins_racipe_plan_run replays it. */
 typedef struct grins_racipe_plan *grins_racipe_plan_t;   /* opaque, library-owned */
 
 /* One job of a plan: a network handle and its device buffers, laid out as
@@ -373,22 +373,33 @@ typedef struct {
 } grins_racipe_job;
 
 /* Builds a plan for n_jobs jobs with the solver options o (FP32, no time
- * grid).  The integration runs in one of two forms:
- *   * one persistent launch over all jobs (run-time-layout kernel);
- *   * per job the integrator compiled for its network (NVRTC, compiled at
- *     plan creation in parallel on host threads), each on one of up to 16
- *     branches of the graph, so that jobs run concurrently.
- * autotune = 0: the persistent launch with 4 warps per block and 1 extra
- * slot per scheduling domain.  autotune = 1: the block size (2 or 4 warps),
- * the slots per domain and the per-job form are each timed on the first
- * sixteenth of every job's sets and the fastest kept (this runs kernels on
- * `stream` and writes to the jobs' output buffers).  autotune = 2: the
- * per-job form without timing.  The jobs' buffers
- * must stay valid for the plan's lifetime; their contents are read when the
- * plan runs.  Errors: GRINS_E_INVALID_ARG for bad options or jobs (networks
- * on another device, missing buffers, precision other than FP32, a time
- * grid); GRINS_E_BUDGET when a network has no lane-group layout of at most
- * 8 node rows or the jobs do not fit in shared memory. */
+ * grid).  The integration runs in one of three forms:
+ *   * one persistent launch of a kernel built for the plan: every distinct
+ *     register layout among the jobs' networks gets the integrator compiled
+ *     for it as a device function (NVRTC, in parallel on host threads,
+ *     cached per layout and register cap), linked (nvJitLink) under one
+ *     dispatcher; the warps of an SM start on the same job and visit the
+ *     jobs in the same order, so they mostly run one body at a time;
+ *   * one persistent launch of the run-time-layout kernel (no compile);
+ *   * per job the integrator compiled for its network, each on one of up to
+ *     16 branches of the graph, so that jobs run concurrently.
+ * The jobs' polish and dedupe run on the graph's branches.
+ * autotune = 0: the run-time-layout launch with 4 warps per block and 1
+ * extra slot per scheduling domain.  autotune = 1: each form and its knobs
+ * -- warps per block and resident blocks per SM (the register cap of every
+ * body) of the compiled launch, block size and slots per domain of the
+ * run-time-layout launch -- is timed on the first sixteenth of every job's
+ * sets and the fastest kept (this runs kernels on `stream` and writes to the
+ * jobs' output buffers).  autotune = 2: the per-job form without timing.
+ * autotune = 3: the compiled launch, 4 warps x 3 blocks per SM, without
+ * timing.  The jobs' buffers must stay valid for the plan's lifetime; their
+ * contents are read when the plan runs.  Plans run no borderline re-pass
+ * (grins_solver_opts.tail_rtol is ignored).  Errors: GRINS_E_INVALID_ARG for
+ * bad options or jobs (networks on another device, missing buffers,
+ * precision other than FP32, a time grid); GRINS_E_BUDGET when a network has
+ * no lane-group layout of at most 8 node rows, a form needs more shared
+ * memory than the device has, or (autotune = 3) the compiled form is not
+ * available (no register layout, no NVRTC or nvJitLink). */
 grins_status grins_racipe_plan_create(const grins_solver_opts *o, const grins_racipe_job *jobs,
                                       int32_t n_jobs, int32_t autotune, void *stream,
                                       grins_racipe_plan_t *out);
@@ -472,10 +483,11 @@ grins_status grins_racipe_server_wait(grins_racipe_server_t sv, int64_t request_
 
 /* Copies a finished request's results into caller buffers (each nullable):
  * states double [n_sets][n_ics][N], status uint8 [n_sets][n_ics],
- * n_unique int32 [n_sets], state_id int32 [n_sets][n_ics]. */
+ * n_unique int32 [n_sets], state_id int32 [n_sets][n_ics], n_steps int32
+ * [n_sets][n_ics] (step attempts per solve). */
 grins_status grins_racipe_server_copy_results(grins_racipe_server_t sv, int64_t request_id,
                                               double *d_states, uint8_t *d_status, int32_t *d_n_unique,
-                                              int32_t *d_state_id, void *stream);
+                                              int32_t *d_state_id, int32_t *d_n_steps, void *stream);
 
 /* Frees a finished request's device memory and forgets it. */
 grins_status grins_racipe_server_release(grins_racipe_server_t sv, int64_t request_id);

@@ -128,7 +128,7 @@ _sig = {
     "grins_racipe_server_submit": (_S, [_H, _H, C.POINTER(grins_racipe_ranges), C.c_uint64, C.c_int64, C.c_int32,
                                         C.POINTER(grins_solver_opts), C.c_double, C.POINTER(C.c_int64)]),
     "grins_racipe_server_wait": (_S, [_H, C.c_int64, C.c_double, C.POINTER(grins_request_info)]),
-    "grins_racipe_server_copy_results": (_S, [_H, C.c_int64, _P, _P, _P, _P, _P]),
+    "grins_racipe_server_copy_results": (_S, [_H, C.c_int64, _P, _P, _P, _P, _P, _P]),
     "grins_racipe_server_release": (_S, [_H, C.c_int64]),
     "grins_racipe_server_destroy": (_S, [_H]),
     "grins_racipe_tail_stats": (_S, [_H, _P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
@@ -441,9 +441,10 @@ def level_boundaries(counts, half_width=4, max_boundaries=3):
 class Plan:
     """A batched launch over many networks (grins_racipe_plan_*).
 
-    ``autotune``: 0/False the persistent batched launch, 1/True time the
-    launch configurations and the per-network compiled kernels and keep the
-    fastest, 2 the per-network compiled kernels without timing.
+    ``autotune``: 0/False one persistent launch of the run-time-layout
+    kernel, 1/True time every form and its knobs and keep the fastest, 2 the
+    per-network compiled kernels on graph branches without timing, 3 one
+    persistent launch of a kernel compiled for every job's layout.
 
     ``jobs``: list of dicts with keys net (a Racipe), params, ic_unit and,
     optionally, out (buffers as returned by ``Racipe.integrate``; allocated
@@ -535,17 +536,18 @@ class Server:
         return dict(state=info.state, n_sets=info.n_sets, n_ics=info.n_ics, bytes=info.bytes,
                     queued_s=info.queued_s, latency_s=info.latency_s)
 
-    def results(self, rid, stream=None):
-        """Copies a finished request's states, status, n_unique, state_id into new tensors."""
+    def results(self, rid, stream=None, keys=("states", "status", "n_unique", "state_id", "n_steps")):
+        """Copies a finished request's results (the given keys of states,
+        status, n_unique, state_id, n_steps) into new tensors."""
         net, S, I = self._nets[rid]
         dev = net.device
-        out = dict(states=torch.empty((S, I, net.n_nodes), dtype=torch.float64, device=dev),
-                   status=torch.empty((S, I), dtype=torch.uint8, device=dev),
-                   n_unique=torch.empty((S,), dtype=torch.int32, device=dev),
-                   state_id=torch.empty((S, I), dtype=torch.int32, device=dev))
+        shapes = dict(states=((S, I, net.n_nodes), torch.float64), status=((S, I), torch.uint8),
+                      n_unique=((S,), torch.int32), state_id=((S, I), torch.int32), n_steps=((S, I), torch.int32))
+        out = {k: torch.empty(shapes[k][0], dtype=shapes[k][1], device=dev) for k in keys}
         with torch.cuda.device(dev):
-            _check(_lib.grins_racipe_server_copy_results(self._s, rid, _ptr(out["states"]), _ptr(out["status"]),
-                                                         _ptr(out["n_unique"]), _ptr(out["state_id"]),
+            _check(_lib.grins_racipe_server_copy_results(self._s, rid, _ptr(out.get("states")),
+                                                         _ptr(out.get("status")), _ptr(out.get("n_unique")),
+                                                         _ptr(out.get("state_id")), _ptr(out.get("n_steps")),
                                                          _stream(stream)))
         return out
 

@@ -28,7 +28,9 @@ JIT_SOURCES = [("grins_racipe.h", os.path.join(INCLUDE, "grins_racipe.h")),
                ("common.cuh", os.path.join(CSRC, "common.cuh")),
                ("integrate.cuh", os.path.join(CSRC, "integrate.cuh")),
                ("integrate_grp.cuh", os.path.join(CSRC, "integrate_grp.cuh")),
-               ("integrate_rr.cuh", os.path.join(CSRC, "integrate_rr.cuh"))]
+               ("integrate_rr.cuh", os.path.join(CSRC, "integrate_rr.cuh")),
+               ("integrate_rr_layout.inc", os.path.join(CSRC, "integrate_rr_layout.inc")),
+               ("integrate_plan.cuh", os.path.join(CSRC, "integrate_plan.cuh"))]
 
 
 def write_jit_sources(bdir):

@@ -1118,15 +1118,28 @@ static GrpTopo grp_topo(const grins_racipe *h) { return h->grp.topo(); }
 // network in FP64 (power-table edge terms) when the register layout exists,
 // else the generic FP64 kernel (grp_jit null).  compile = false only looks
 // up a kernel an earlier call compiled.
-static void pick_fp64_kernel(const grins_racipe *h, IntegrateArgs *a, bool compile, std::string *why)
+// A compiled register-record kernel for g, kind and variant if an earlier
+// call compiled it, else the same with the re-pass flag toggled (a kernel
+// compiled for the re-pass runs exactly as one without it when it is given
+// no list).
+static const void *lookup_either(const GrpTopo &g, int kind, int variant)
+{
+    const void *k = grp_jit_lookup(g, kind, variant);
+    return k ? k : grp_jit_lookup(g, kind, variant ^ kJitTail);
+}
+
+static void pick_fp64_kernel(const grins_racipe *h, IntegrateArgs *a, bool compile, std::string *why,
+                             bool tail = false)
 {
     a->grp = h->grp.topo();
     a->grp_jit = nullptr;
     std::string w = h->rr.L > 0 ? "" : "no register layout";
     if (h->rr.L > 0) {
         const GrpTopo g = h->rr.topo();
-        const void *k = compile ? grp_jit_kernel(g, kJitRegisters64, &w, a->method)
-                                : grp_jit_lookup(g, kJitRegisters64, a->method);
+        const int variant = a->method | (a->n_t > 0 ? kJitSeries : 0) | (tail ? kJitTail : 0);
+        // a lookup also takes the re-pass variant, which runs the same without a list
+        const void *k = compile ? grp_jit_kernel(g, kJitRegisters64, &w, variant)
+                                : lookup_either(g, kJitRegisters64, variant);
         if (k) { a->grp = g; a->grp_jit = k; }
     }
     if (why) *why = w;
@@ -1151,7 +1164,8 @@ static void set_tighten(IntegrateArgs *a, const grins_solver_opts *o)
 // register layout exists, else records in shared memory (GRINS_JIT_KIND=grp
 // asks for the latter) -- or leaves the run-time-layout kernel (grp_jit
 // null).  compile = false only looks up kernels an earlier call compiled.
-static bool pick_fp32_kernel(const grins_racipe *h, IntegrateArgs *a, bool compile, std::string *why)
+static bool pick_fp32_kernel(const grins_racipe *h, IntegrateArgs *a, bool compile, std::string *why,
+                             bool tail = false)
 {
     a->grp = h->grp.topo();
     a->grp_jit = nullptr;
@@ -1160,8 +1174,9 @@ static bool pick_fp32_kernel(const grins_racipe *h, IntegrateArgs *a, bool compi
     std::string w;
     if (!want_shared && h->rr.L > 0) {
         const GrpTopo g = h->rr.topo();
-        const void *k = compile ? grp_jit_kernel(g, kJitRegisters, &w, a->method)
-                                : grp_jit_lookup(g, kJitRegisters, a->method);
+        const int variant = a->method | (a->n_t > 0 ? kJitSeries : 0) | (tail ? kJitTail : 0);
+        const void *k = compile ? grp_jit_kernel(g, kJitRegisters, &w, variant)
+                                : lookup_either(g, kJitRegisters, variant);
         if (k) { a->grp = g; a->grp_jit = k; if (why) *why = w; return true; }
     }
     if (h->grp.L > 0 && a->method == 0) {
@@ -1287,7 +1302,8 @@ extern "C" grins_status grins_racipe_integrate(grins_racipe_t h, const grins_sol
     IntegrateArgs::TailItem *tail_sorted = nullptr;   // its list, longest first
     if (o->precision == GRINS_FP32) {
         // grins_racipe_integrator describes the FP32 kernel: only its launches record it
-        const bool rr = pick_fp32_kernel(h, &a, true, &h->jit_why);
+        const bool want_tail = o->tail_rtol > 0 && o->n_t == 0;
+        const bool rr = pick_fp32_kernel(h, &a, true, &h->jit_why, want_tail);
         h->jit_used = a.grp_jit != nullptr;
         h->used_L = a.grp.L; h->used_R = a.grp.R; h->used_P = a.grp.P;
         h->used_method = a.method;
@@ -1298,7 +1314,7 @@ extern "C" grins_status grins_racipe_integrate(grins_racipe_t h, const grins_sol
         else {
             a64 = a;
             std::string w64;
-            pick_fp64_kernel(h, &a64, true, &w64);
+            pick_fp64_kernel(h, &a64, true, &w64, true);
             if (!a64.grp_jit) h->tail_why = "not run (no FP64 kernel compiled for the network: " + w64 + ")";
             else tail = true;
         }
@@ -1594,7 +1610,19 @@ struct grins_racipe_plan {
     unsigned long long *d_counters = nullptr;   // per job: queue, spare, check code, check info
     BatchArgs batch{};
     int warps = 4, slot_extra = 1;
-    int mode = 0;                          // 0: one persistent launch; 1: per-job compiled kernels on branches
+    int mode = 0;                          // 0: one persistent launch (run-time layouts); 1: per-job compiled
+                                           // kernels on branches; 2: one persistent launch of a kernel compiled
+                                           // for every job's layout
+    const void *ct_kern = nullptr;         // mode 2: the plan kernel
+    int ct_warps = 4;                      // mode 2: warps per block
+    int ct_minb = 3;                       // mode 2: resident blocks per SM (register cap of every body)
+    std::vector<int32_t> body_of;          // mode 2: each job's body
+    int ct_bodies = 0;
+    IntegrateArgs *d_ct_args = nullptr;    // mode 2: per-job arguments with the register layouts
+    int32_t *d_body_of = nullptr;
+    PlanArgs ct{};
+    std::string ct_why;
+    bool prefetched = false;               // mode 1: the per-job compiles were started
     std::vector<IntegrateArgs> jargs;      // mode 1: per-job arguments (compiled kernel and its layout)
     std::vector<size_t> order;             // mode 1: jobs by decreasing work
     std::vector<cudaStream_t> side;        // mode 1: branch streams
@@ -1607,6 +1635,8 @@ struct grins_racipe_plan {
 
 static void plan_free(grins_racipe_plan *p)
 {
+    cudaFree(p->d_ct_args); cudaFree(p->d_body_of);
+    p->d_ct_args = nullptr; p->d_body_of = nullptr;
     if (p->exec) cudaGraphExecDestroy(p->exec);
     if (p->graph) cudaGraphDestroy(p->graph);
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
@@ -1699,15 +1729,25 @@ static grins_status plan_enqueue(grins_racipe_plan *p, cudaStream_t st, bool int
 {
     CUDA_TRY(cudaMemsetAsync(p->d_counters, 0, sizeof(unsigned long long) * 4 * p->jobs.size(), st),
              "plan: counter reset");
-    if (p->mode == 0) {
-        cudaError_t e = launch_integrate_batch(p->batch, p->warps, st, p->num_sms, p->smem_limit);
+    if (p->mode == 0 || p->mode == 2) {
+        const cudaError_t e = p->mode == 2 ? launch_plan_ct(p->ct_kern, p->ct, st, p->num_sms, p->smem_limit)
+                                           : launch_integrate_batch(p->batch, p->warps, st, p->num_sms, p->smem_limit);
         if (e == cudaErrorInvalidConfiguration)
-            return fail(GRINS_E_BUDGET, "plan: the jobs need more shared memory per block than the device has");
-        if (e != cudaSuccess) return cuda_fail(e, "plan: batched launch");
+            return fail(GRINS_E_BUDGET, "plan: the persistent launch needs more shared memory per block than the "
+                        "device has");
+        if (e != cudaSuccess) return cuda_fail(e, "plan: persistent launch");
         if (integrate_only) return GRINS_OK;
-        for (size_t b = 0; b < p->jobs.size(); ++b) {
-            const grins_status s = plan_job_tail(p, b, st);
+        // the jobs' polish and dedupe, dealt out to the branch streams
+        const int K = (int)p->side.size();
+        CUDA_TRY(cudaEventRecord(p->events[0], st), "plan: fork");
+        for (int k = 0; k < K; ++k) CUDA_TRY(cudaStreamWaitEvent(p->side[k], p->events[0], 0), "plan: fork");
+        for (size_t q = 0; q < p->order.size(); ++q) {
+            const grins_status s = plan_job_tail(p, p->order[q], p->side[q % K]);
             if (s != GRINS_OK) return s;
+        }
+        for (int k = 0; k < K; ++k) {
+            CUDA_TRY(cudaEventRecord(p->events[1 + k], p->side[k]), "plan: join");
+            CUDA_TRY(cudaStreamWaitEvent(st, p->events[1 + k], 0), "plan: join");
         }
         return GRINS_OK;
     }
@@ -1735,10 +1775,80 @@ static grins_status plan_enqueue(grins_racipe_plan *p, cudaStream_t st, bool int
     return GRINS_OK;
 }
 
+// Mode 2 setup (after plan_args): the distinct register layouts of the
+// jobs' networks, the plan kernel compiled for them (once), and per-job
+// arguments pointing at each network's register layout, uploaded with the
+// job -> body map.  GRINS_E_BUDGET when a network has no register layout or
+// the kernel cannot be compiled.
+static grins_status plan_setup_branches(grins_racipe_plan *p, bool prefetch);
+
+static grins_status plan_setup_ct(grins_racipe_plan *p, cudaStream_t st)
+{
+    const size_t n = p->jobs.size();
+    const grins_status sb = plan_setup_branches(p, false);
+    if (sb != GRINS_OK) return sb;
+    std::vector<GrpTopo> lays;
+    std::vector<int32_t> body(n);
+    int gather = 0;
+    for (size_t b = 0; b < n; ++b) {
+        const grins_racipe *h = p->jobs[b].net;
+        if (h->rr.L <= 0) return fail(GRINS_E_BUDGET, "plan: job %zu's network has no register layout", b);
+        const GrpTopo g = h->rr.topo();
+        int found = -1;
+        for (size_t i = 0; i < lays.size() && found < 0; ++i) {
+            const GrpTopo &x = lays[i];
+            bool same = x.L == g.L && x.R == g.R && x.P == g.P;
+            for (int r = 0; same && r < g.R; ++r)
+                same = x.row_off[r] == g.row_off[r] && x.row_deg[r] == g.row_deg[r] && x.link_to[r] == g.link_to[r];
+            if (same) found = (int)i;
+        }
+        if (found < 0) { found = (int)lays.size(); lays.push_back(g); }
+        body[b] = found;
+        gather = std::max(gather, rr_warp_bytes(g.R, 1, 4));
+    }
+    p->ct_kern = grp_jit_plan_kernel(lays.data(), (int)lays.size(), p->ct_warps, p->ct_minb, &p->ct_why);
+    if (!p->ct_kern) return fail(GRINS_E_BUDGET, "plan: no compiled plan kernel (%s)", p->ct_why.c_str());
+    p->ct_bodies = (int)lays.size();
+    std::vector<IntegrateArgs> a = p->args;
+    for (size_t b = 0; b < n; ++b) {
+        a[b].grp = p->jobs[b].net->rr.topo();
+        a[b].grp_jit = nullptr;
+    }
+    if (!p->d_ct_args) {
+        CUDA_TRY(dev_malloc(&p->d_ct_args, sizeof(IntegrateArgs) * n), "plan: arguments");
+        CUDA_TRY(dev_malloc(&p->d_body_of, sizeof(int32_t) * n), "plan: body map");
+    }
+    CUDA_TRY(cudaMemcpyAsync(p->d_ct_args, a.data(), sizeof(IntegrateArgs) * n, cudaMemcpyHostToDevice, st),
+             "plan: argument upload");
+    CUDA_TRY(cudaMemcpyAsync(p->d_body_of, body.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st),
+             "plan: body map upload");
+    CUDA_TRY(cudaStreamSynchronize(st), "plan: argument upload");
+    p->body_of = body;
+    gather = (gather + 127) / 128 * 128;
+    p->ct = PlanArgs{p->d_ct_args, p->d_cum, p->d_body_of, (int32_t)n, gather,
+                     gather + (int)((sizeof(IntegrateArgs) + 127) / 128 * 128)};
+    return GRINS_OK;
+}
+
 // Mode 1 setup: branch streams and events, the job order, and per-job
 // arguments (from p->args) with the kernel compiled for each job's network;
 // the compiles run in parallel on the host pool.
+static grins_status plan_setup_branches(grins_racipe_plan *p, bool prefetch);
+
 static grins_status plan_setup_jobs(grins_racipe_plan *p)
+{
+    const size_t n = p->jobs.size();
+    const grins_status s = plan_setup_branches(p, true);
+    if (s != GRINS_OK) return s;
+    p->jargs = p->args;
+    for (size_t b = 0; b < n; ++b) pick_fp32_kernel(p->jobs[b].net, &p->jargs[b], true, nullptr);
+    return GRINS_OK;
+}
+
+// Branch streams and events, and the jobs by decreasing work (once per
+// plan); with `prefetch` the compiles of every job's kernel are started on
+// the host pool.
+static grins_status plan_setup_branches(grins_racipe_plan *p, bool prefetch)
 {
     const size_t n = p->jobs.size();
     if (p->side.empty()) {
@@ -1756,14 +1866,15 @@ static grins_status plan_setup_jobs(grins_racipe_plan *p)
             };
             return work(x) > work(y);
         });
+    }
+    if (prefetch && !p->prefetched) {
+        p->prefetched = true;
         for (size_t b = 0; b < n; ++b) {          // start every compile before waiting for any
             const grins_racipe *h = p->jobs[b].net;
             if (h->rr.L > 0) grp_jit_prefetch(h->rr.topo(), kJitRegisters);
             else grp_jit_prefetch(h->grp.topo(), kJitShared);
         }
     }
-    p->jargs = p->args;
-    for (size_t b = 0; b < n; ++b) pick_fp32_kernel(p->jobs[b].net, &p->jargs[b], true, nullptr);
     return GRINS_OK;
 }
 
@@ -1832,7 +1943,7 @@ extern "C" grins_status grins_racipe_plan_create(const grins_solver_opts *o, con
     // each timed on the first sixteenth of every job's sets
     char buf[512];
     std::string tried;
-    if (autotune < 0 || autotune > 2) { plan_free(p); delete p; return fail(GRINS_E_INVALID_ARG, "plan_create: autotune must be 0, 1 or 2"); }
+    if (autotune < 0 || autotune > 3) { plan_free(p); delete p; return fail(GRINS_E_INVALID_ARG, "plan_create: autotune must be 0, 1, 2 or 3"); }
     if (autotune == 1) {
         float best = -1.0f;
         int bw = 4, bx = 1;
@@ -1872,11 +1983,13 @@ extern "C" grins_status grins_racipe_plan_create(const grins_solver_opts *o, con
         s = plan_enqueue(p, st, true);
         cudaEventRecord(e1, st);
         bool per_job = false;
+        float per_job_ms = -1.0f;
         if (s == GRINS_OK && cudaEventSynchronize(e1) == cudaSuccess) {
             float ms = 0.0f;
             cudaEventElapsedTime(&ms, e0, e1);
             std::snprintf(buf, sizeof(buf), "; per-network compiled kernels: %.3f ms", ms);
             tried += buf;
+            per_job_ms = ms;
             per_job = best < 0 || ms < best;
         } else if (s != GRINS_E_BUDGET) {
             cudaEventDestroy(e0); cudaEventDestroy(e1);
@@ -1884,17 +1997,55 @@ extern "C" grins_status grins_racipe_plan_create(const grins_solver_opts *o, con
             return s != GRINS_OK ? s : fail(GRINS_E_CUDA, "plan_create: autotune run failed");
         }
         g_last_error.clear();
+        // one launch of the kernel compiled for every job's layout: blocks of
+        // 4 or 2 warps, 8, 12 or 16 resident warps per SM (the register cap
+        // of every body; a block size with the same cap reuses the bodies)
+        float ct_ms = -1.0f;
+        int ct_best = 3, ct_best_w = 4;
+        plan_args(p, 1, 16);
+        const int ct_cfg[6][2] = {{4, 2}, {4, 3}, {4, 4}, {2, 4}, {2, 6}, {2, 8}};
+        for (const auto &cfg : ct_cfg) {
+            const int mb = cfg[1];
+            p->ct_warps = cfg[0];
+            p->ct_minb = mb;
+            s = plan_setup_ct(p, st);
+            if (s == GRINS_OK) {
+                p->mode = 2;
+                cudaEventRecord(e0, st);
+                s = plan_enqueue(p, st, true);
+                cudaEventRecord(e1, st);
+                float ms = -1.0f;
+                if (s == GRINS_OK && cudaEventSynchronize(e1) == cudaSuccess) {
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    std::snprintf(buf, sizeof(buf), "; one compiled launch (%d layouts, %d warps x %d blocks per SM): "
+                                  "%.3f ms", p->ct_bodies, p->ct_warps, mb, ms);
+                    tried += buf;
+                    if (ct_ms < 0 || ms < ct_ms) { ct_ms = ms; ct_best = mb; ct_best_w = cfg[0]; }
+                }
+            }
+            if (s != GRINS_OK && s != GRINS_E_BUDGET) {
+                cudaEventDestroy(e0); cudaEventDestroy(e1);
+                plan_free(p); delete p;
+                return s;
+            }
+            g_last_error.clear();
+        }
+        p->ct_minb = ct_best;
+        p->ct_warps = ct_best_w;
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
-        if (best < 0 && !per_job) { plan_free(p); delete p; return fail(GRINS_E_BUDGET, "plan_create: no configuration fits"); }
+        if (best < 0 && !per_job && ct_ms < 0) { plan_free(p); delete p; return fail(GRINS_E_BUDGET, "plan_create: no configuration fits"); }
         p->mode = per_job ? 1 : 0;
+        if (ct_ms >= 0 && (ct_ms < best || best < 0) && (!per_job || ct_ms < per_job_ms)) p->mode = 2;
         p->warps = bw;
         p->slot_extra = bx;
     }
     if (autotune == 2) p->mode = 1;
+    if (autotune == 3) p->mode = 2;
     plan_args(p, p->slot_extra, 1);
-    grins_status s = GRINS_OK;
-    if (p->mode == 1) s = plan_setup_jobs(p);
+    grins_status s = plan_setup_branches(p, false);
+    if (p->mode == 1 && s == GRINS_OK) s = plan_setup_jobs(p);
+    if (p->mode == 2 && s == GRINS_OK) s = plan_setup_ct(p, st);
     if (s == GRINS_OK) s = plan_upload(p, st);
     if (s != GRINS_OK) { plan_free(p); delete p; return s; }
 
@@ -1908,7 +2059,11 @@ extern "C" grins_status grins_racipe_plan_create(const grins_solver_opts *o, con
     if (s != GRINS_OK) { plan_free(p); delete p; return s; }
     if (ce == cudaSuccess) ce = cudaGraphInstantiate(&p->exec, p->graph, 0);
     if (ce != cudaSuccess) { plan_free(p); delete p; return cuda_fail(ce, "plan_create: graph instantiation"); }
-    if (p->mode == 1)
+    if (p->mode == 2)
+        std::snprintf(buf, sizeof(buf), "one persistent launch of a kernel compiled for the jobs' %d register "
+                      "layouts, %d jobs, %d warps per block, %d blocks per SM%s", p->ct_bodies, n_jobs, p->ct_warps,
+                      p->ct_minb, autotune == 1 ? "; autotuned: " : "");
+    else if (p->mode == 1)
         std::snprintf(buf, sizeof(buf), "per-network compiled lane-group DP5(4) kernels, %d jobs on %d graph "
                       "branches%s", n_jobs, (int)p->side.size(), autotune == 1 ? "; autotuned: " : "");
     else
@@ -2324,7 +2479,7 @@ extern "C" grins_status grins_racipe_server_wait(grins_racipe_server_t sv, int64
 
 extern "C" grins_status grins_racipe_server_copy_results(grins_racipe_server_t sv, int64_t id, double *d_states,
                                                          uint8_t *d_status, int32_t *d_n_unique,
-                                                         int32_t *d_state_id, void *stream)
+                                                         int32_t *d_state_id, int32_t *d_n_steps, void *stream)
 {
     AbiRange nvtx_range_("grins_racipe_server_copy_results");
     g_last_error.clear();
@@ -2340,6 +2495,7 @@ extern "C" grins_status grins_racipe_server_copy_results(grins_racipe_server_t s
     if (d_status) CUDA_TRY(cudaMemcpyAsync(d_status, r.status, S * I, cudaMemcpyDeviceToDevice, st), "copy");
     if (d_n_unique) CUDA_TRY(cudaMemcpyAsync(d_n_unique, r.n_unique, S * 4, cudaMemcpyDeviceToDevice, st), "copy");
     if (d_state_id) CUDA_TRY(cudaMemcpyAsync(d_state_id, r.state_id, S * I * 4, cudaMemcpyDeviceToDevice, st), "copy");
+    if (d_n_steps) CUDA_TRY(cudaMemcpyAsync(d_n_steps, r.n_steps, S * I * 4, cudaMemcpyDeviceToDevice, st), "copy");
     return GRINS_OK;
 }
 

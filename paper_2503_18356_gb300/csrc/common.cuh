@@ -150,6 +150,22 @@ struct BatchArgs {
     int32_t warp_bytes;          // max over jobs of the per-warp layout (multiple of 128)
 };
 
+// One compiled launch for a plan (grins_racipe_plan_*): every job's
+// register-record integrator, compiled for its network's layout, in one
+// kernel; job b runs body body_of[b].  Warp w starts on the job where its
+// share of the total work falls and visits every job in turn, integrating
+// its solves from the job's counter until they are all handed out.  A warp's
+// shared-memory region is region_bytes: its gather buffers (gather_bytes,
+// the largest layout's), then a copy of the job's arguments.
+struct PlanArgs {
+    const IntegrateArgs *jobs;   // [n_jobs], device
+    const double *cum_work;      // [n_jobs], device: cumulative work fraction
+    const int32_t *body_of;      // [n_jobs], device
+    int32_t n_jobs;
+    int32_t gather_bytes;
+    int32_t region_bytes;
+};
+
 // Maximum N served by the FP32 / FP64 integrator buckets.
 #ifndef __CUDACC_RTC__
 // Run-time compiled lane-group kernel for one layout (jit.cu): compiled on
@@ -158,7 +174,13 @@ struct BatchArgs {
 // memory).  The returned pointer is an opaque handle for launch_grp_jit.
 enum JitKind { kJitShared = 0, kJitRegisters = 1, kJitRegisters64 = 2 };
 // method: the 5(4) pair of a register-record kernel (0 Dormand-Prince,
-// 1 Tsitouras); the shared-record kernel runs Dormand-Prince only.
+// 1 Tsitouras) in its low bits, plus kJitSeries for a kernel that writes
+// time series (register-record kernels without it compile the grid logic
+// out) and kJitTail for one taking part in the borderline re-pass; the
+// shared-record kernel runs Dormand-Prince only and ignores both flags.
+constexpr int kJitMethodMask = 15;
+constexpr int kJitSeries = 16;
+constexpr int kJitTail = 32;      // with the borderline re-pass (checkpoints / list mode)
 const void *grp_jit_kernel(const GrpTopo &g, int kind, std::string *why, int method = 0);
 const void *grp_jit_lookup(const GrpTopo &g, int kind, int method = 0);
 // Starts (once) a background compile for layout g: 1 ready, 0 compiling, -1
@@ -172,6 +194,13 @@ cudaError_t launch_integrate_fp32(const IntegrateArgs &a, cudaStream_t st, int n
 cudaError_t launch_integrate_batch(const BatchArgs &b, int warps, cudaStream_t st, int num_sms,
                                    int smem_limit);
 cudaError_t launch_integrate_fp64(const IntegrateArgs &a, cudaStream_t st, int num_sms);
+// The plan kernel for the given layouts (body i compiled for layouts[i];
+// FP32 Dormand-Prince, no time series, no re-pass) with `minb` resident
+// blocks of `warps` warps per SM, built on first use and cached; null with
+// the reason in *why.
+const void *grp_jit_plan_kernel(const GrpTopo *layouts, int n_layouts, int warps, int minb, std::string *why);
+// Launch of a plan kernel: grid of resident blocks, smem = warps x region.
+cudaError_t launch_plan_ct(const void *kern, const PlanArgs &p, cudaStream_t st, int num_sms, int smem_limit);
 // The borderline re-pass list `in` (n_in[0] items) copied to `out` longest
 // first (by the FP32 pass's attempts after the checkpoint, in buckets of
 // max_work / 64), for the FP64 pass.

@@ -18,6 +18,7 @@
 // leaves the run-time-layout kernel in charge (GRINS_JIT=0 forces that).
 #include <dlfcn.h>
 
+#include <algorithm>
 #include <atomic>
 #include <condition_variable>
 #include <cstdio>
@@ -31,6 +32,7 @@
 #include <thread>
 #include <vector>
 
+#include <nvJitLink.h>
 #include <nvrtc.h>
 
 #include "integrate_grp.cuh"
@@ -193,6 +195,24 @@ int jit_maxnreg(int kind)
     return 0;
 }
 
+// The row layout of g as compile-time constants (kGrpCtRows, GrpRowCt<r>)
+// in the current namespace of the generated source.
+std::string layout_prelude(const GrpTopo &g, bool links)
+{
+    std::string s;
+    char buf[256];
+    std::snprintf(buf, sizeof(buf), "constexpr int kGrpCtRows = %d;\n", g.R);
+    s += buf;
+    s += "template <int r> struct GrpRowCt { static constexpr int off = 0, deg = 0, link = -1; };\n";
+    for (int r = 0; r < g.R; ++r) {
+        std::snprintf(buf, sizeof(buf),
+                      "template <> struct GrpRowCt<%d> { static constexpr int off = %d, deg = %d, link = %d; };\n",
+                      r, g.row_off[r], g.row_deg[r], links ? g.link_to[r] : -1);
+        s += buf;
+    }
+    return s;
+}
+
 // Generated prelude + kernel wrapper for one layout.
 std::string jit_main(const GrpTopo &g, int kind, int minb, int warps, int method)
 {
@@ -213,15 +233,7 @@ std::string jit_main(const GrpTopo &g, int kind, int minb, int warps, int method
 #endif
     }
     s += "#include \"common.cuh\"\nnamespace grins {\n";
-    std::snprintf(buf, sizeof(buf), "constexpr int kGrpCtRows = %d;\n", g.R);
-    s += buf;
-    s += "template <int r> struct GrpRowCt { static constexpr int off = 0, deg = 0, link = -1; };\n";
-    for (int r = 0; r < g.R; ++r) {
-        std::snprintf(buf, sizeof(buf),
-                      "template <> struct GrpRowCt<%d> { static constexpr int off = %d, deg = %d, link = %d; };\n",
-                      r, g.row_off[r], g.row_deg[r], kind == kJitShared ? -1 : g.link_to[r]);
-        s += buf;
-    }
+    s += layout_prelude(g, kind != kJitShared);
     if (kind == kJitRegisters || kind == kJitRegisters64) {
         s += "}\n#include \"integrate_rr.cuh\"\n";
         char bounds[64];
@@ -229,8 +241,9 @@ std::string jit_main(const GrpTopo &g, int kind, int minb, int warps, int method
         else std::snprintf(bounds, sizeof(bounds), "__launch_bounds__(%d, %d)", warps * kWarp, minb);
         std::snprintf(buf, sizeof(buf),
                       "extern \"C\" __global__ void %s grins_grp_ct(const grins::IntegrateArgs a)\n"
-                      "{\n    grins::rr_body<%d, %d, %d, %s, %d>(a);\n}\n",
-                      bounds, g.R, warps, g.L, kind == kJitRegisters64 ? "double" : "float", method);
+                      "{\n    grins::rr_body<%d, %d, %d, %s, %d, %s, %s>(a);\n}\n",
+                      bounds, g.R, warps, g.L, kind == kJitRegisters64 ? "double" : "float", method & kJitMethodMask,
+                      (method & kJitSeries) ? "true" : "false", (method & kJitTail) ? "true" : "false");
     } else {
         s += "}\n#include \"integrate_grp.cuh\"\n";
         std::snprintf(buf, sizeof(buf),
@@ -255,7 +268,7 @@ int log_spill_bytes(const std::string &log)
     return total;
 }
 
-JitBuild jit_compile(const std::string &src)
+JitBuild jit_compile(const std::string &src, const char *kname = "grins_grp_ct")
 {
     JitBuild b;
     NvrtcApi &api = nvrtc();
@@ -290,7 +303,7 @@ JitBuild jit_compile(const std::string &src)
     api.cubin(prog, cubin.data());
     api.destroy(&prog);
     cudaError_t ce = cudaLibraryLoadData(&b.lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
-    if (ce == cudaSuccess) ce = cudaLibraryGetKernel(&b.kern, b.lib, "grins_grp_ct");
+    if (ce == cudaSuccess) ce = cudaLibraryGetKernel(&b.kern, b.lib, kname);
     if (ce != cudaSuccess) { b.why = std::string("loading the compiled kernel: ") + cudaGetErrorString(ce); return b; }
     b.ok = true;
     return b;
@@ -398,7 +411,7 @@ bool jit_enabled(const GrpTopo &g, std::string *why)
 const void *grp_jit_kernel(const GrpTopo &g, int kind, std::string *why, int method)
 {
     if (!jit_enabled(g, why)) return nullptr;
-    if (method != 0 && kind == kJitShared) {
+    if ((method & kJitMethodMask) != 0 && kind == kJitShared) {
         if (why) *why = "the shared-record kernel runs Dormand-Prince only";
         return nullptr;
     }
@@ -414,7 +427,7 @@ const void *grp_jit_kernel(const GrpTopo &g, int kind, std::string *why, int met
 // compiles, loads or waits.
 const void *grp_jit_lookup(const GrpTopo &g, int kind, int method)
 {
-    if (!jit_enabled(g, nullptr) || (method != 0 && kind == kJitShared)) return nullptr;
+    if (!jit_enabled(g, nullptr) || ((method & kJitMethodMask) != 0 && kind == kJitShared)) return nullptr;
     std::shared_ptr<JitEntry> e = jit_get(g, kind, kLookup, method);
     if (!e || e->state.load() != 1) return nullptr;
     return e.get();
@@ -425,8 +438,281 @@ const void *grp_jit_lookup(const GrpTopo &g, int kind, int method)
 // unavailable.
 int grp_jit_prefetch(const GrpTopo &g, int kind, int method)
 {
-    if (!jit_enabled(g, nullptr) || (method != 0 && kind == kJitShared)) return -1;
+    if (!jit_enabled(g, nullptr) || ((method & kJitMethodMask) != 0 && kind == kJitShared)) return -1;
     return jit_get(g, kind, kCompileAsync, method)->state.load();
+}
+
+namespace {
+
+// nvJitLink, opened with dlopen like NVRTC: the plan kernel is linked from
+// separately compiled bodies.
+struct JitLinkApi {
+    bool ok = false;
+    std::string why;
+    decltype(&__nvJitLinkCreate_13_0) create = nullptr;
+    decltype(&__nvJitLinkAddData_13_0) add_data = nullptr;
+    decltype(&__nvJitLinkComplete_13_0) complete = nullptr;
+    decltype(&__nvJitLinkGetLinkedCubinSize_13_0) cubin_size = nullptr;
+    decltype(&__nvJitLinkGetLinkedCubin_13_0) cubin = nullptr;
+    decltype(&__nvJitLinkGetErrorLogSize_13_0) err_size = nullptr;
+    decltype(&__nvJitLinkGetErrorLog_13_0) err_log = nullptr;
+    decltype(&__nvJitLinkDestroy_13_0) destroy = nullptr;
+};
+
+JitLinkApi &jitlink()
+{
+    static JitLinkApi api;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        const char *names[] = {"libnvJitLink.so.13", "libnvJitLink.so", "/usr/local/cuda/lib64/libnvJitLink.so.13",
+                               "/usr/local/cuda/lib64/libnvJitLink.so"};
+        void *h = nullptr;
+        for (const char *n : names)
+            if ((h = dlopen(n, RTLD_NOW | RTLD_LOCAL))) break;
+        if (!h) { api.why = "libnvJitLink not found"; return; }
+        api.create = reinterpret_cast<decltype(api.create)>(dlsym(h, "nvJitLinkCreate"));
+        api.add_data = reinterpret_cast<decltype(api.add_data)>(dlsym(h, "nvJitLinkAddData"));
+        api.complete = reinterpret_cast<decltype(api.complete)>(dlsym(h, "nvJitLinkComplete"));
+        api.cubin_size = reinterpret_cast<decltype(api.cubin_size)>(dlsym(h, "nvJitLinkGetLinkedCubinSize"));
+        api.cubin = reinterpret_cast<decltype(api.cubin)>(dlsym(h, "nvJitLinkGetLinkedCubin"));
+        api.err_size = reinterpret_cast<decltype(api.err_size)>(dlsym(h, "nvJitLinkGetErrorLogSize"));
+        api.err_log = reinterpret_cast<decltype(api.err_log)>(dlsym(h, "nvJitLinkGetErrorLog"));
+        api.destroy = reinterpret_cast<decltype(api.destroy)>(dlsym(h, "nvJitLinkDestroy"));
+        api.ok = api.create && api.add_data && api.complete && api.cubin_size && api.cubin && api.err_size &&
+                 api.err_log && api.destroy;
+        if (!api.ok) api.why = "libnvJitLink lacks an expected symbol";
+    });
+    return api;
+}
+
+// NVRTC compile of relocatable device code (no load): the cubin, or empty
+// with the reason in *why.
+std::vector<char> rdc_compile(const std::string &src, int maxreg, std::string *why)
+{
+    NvrtcApi &api = nvrtc();
+    if (!api.ok) { *why = api.why; return {}; }
+    std::vector<const char *> hdr_src, hdr_name;
+    for (int i = 0; i < kJitSourceCount; ++i) {
+        hdr_src.push_back(kJitSources[i]);
+        hdr_name.push_back(kJitSourceNames[i]);
+    }
+    hdr_src.push_back(kStdintStandIn);
+    hdr_name.push_back("stdint.h");
+    nvrtcProgram prog = nullptr;
+    nvrtcResult r = api.create(&prog, src.c_str(), "grins_plan.cu", (int)hdr_src.size(), hdr_src.data(),
+                               hdr_name.data());
+    if (r != NVRTC_SUCCESS) { *why = std::string("nvrtcCreateProgram: ") + api.err(r); return {}; }
+    const std::string reg = "--maxrregcount=" + std::to_string(maxreg);
+    const char *opts[] = {"--gpu-architecture=sm_103a", "--std=c++17", "-lineinfo", "-default-device",
+                          "--relocatable-device-code=true", reg.c_str()};
+    r = api.compile(prog, 6, opts);
+    if (r != NVRTC_SUCCESS) {
+        size_t n = 0;
+        api.log_size(prog, &n);
+        std::string log(n, '\0');
+        if (n) api.log(prog, &log[0]);
+        *why = std::string("nvrtcCompileProgram: ") + api.err(r) + "\n" + log;
+        api.destroy(&prog);
+        return {};
+    }
+    size_t n = 0;
+    api.cubin_size(prog, &n);
+    std::vector<char> cubin(n);
+    api.cubin(prog, cubin.data());
+    api.destroy(&prog);
+    return cubin;
+}
+
+// One layout's integrator as a device function grins_body_<id> (FP32
+// Dormand-Prince, no time series, no re-pass), compiled apart with the
+// plan's register cap; cached per process by source and cap.
+struct PlanBody {
+    std::atomic<int> state{0};   // 0 compiling, 1 ready, -1 failed
+    std::string why, name;
+    std::vector<char> cubin;
+};
+
+struct PlanBodyCache {
+    std::mutex mu;
+    std::condition_variable cv;
+    std::map<std::string, std::shared_ptr<PlanBody>> map;
+};
+PlanBodyCache &plan_body_cache()
+{
+    static PlanBodyCache *c = new PlanBodyCache();
+    return *c;
+}
+
+std::string body_source(const GrpTopo &g, const std::string &name)
+{
+    std::string s = "#include \"common.cuh\"\n#include \"integrate_grp.cuh\"\nnamespace grins { namespace pkb {\n";
+    s += layout_prelude(g, true);
+    s += "#include \"integrate_rr_layout.inc\"\n} }\n";
+    char buf[320];
+    std::snprintf(buf, sizeof(buf),
+                  "extern \"C\" __device__ __noinline__ void %s(const grins::IntegrateArgs &a, unsigned char *w)\n"
+                  "{ grins::pkb::rr_body_at<%d, 4, %d, float, 0, false, false>(a, w); }\n",
+                  name.c_str(), g.R, g.L);
+    return s + buf;
+}
+
+// The body for layout g under register cap maxreg: from the cache, or a
+// compile queued on the host pool (the caller waits for it).
+std::shared_ptr<PlanBody> plan_body(const GrpTopo &g, int maxreg)
+{
+    const std::string lay = layout_prelude(g, true) + "L=" + std::to_string(g.L) + " R=" + std::to_string(g.R);
+    char id[64];
+    std::snprintf(id, sizeof(id), "grins_body_%016zx_%d", std::hash<std::string>()(lay), maxreg);
+    const std::string src = body_source(g, id);
+    const std::string key = src + "\nmaxreg " + std::to_string(maxreg);
+    PlanBodyCache &c = plan_body_cache();
+    std::lock_guard<std::mutex> lock(c.mu);
+    auto it = c.map.find(key);
+    if (it != c.map.end()) return it->second;
+    auto b = std::make_shared<PlanBody>();
+    b->name = id;
+    c.map.emplace(key, b);
+    jit_pool_push([b, src, maxreg] {
+        std::string why;
+        std::vector<char> cubin = rdc_compile(src, maxreg, &why);
+        PlanBodyCache &cc = plan_body_cache();
+        {
+            std::lock_guard<std::mutex> l(cc.mu);
+            b->cubin = std::move(cubin);
+            b->why = why;
+            b->state.store(b->cubin.empty() ? -1 : 1);
+        }
+        cc.cv.notify_all();
+    });
+    return b;
+}
+
+// The dispatcher: the job loop of plan_run with a switch over the bodies,
+// which it declares and calls.
+std::string plan_dispatch_source(const std::vector<std::shared_ptr<PlanBody>> &bodies, int warps, int minb)
+{
+    std::string s = "#include \"common.cuh\"\n#include \"integrate_plan.cuh\"\n";
+    char buf[320];
+    for (const auto &b : bodies) {
+        std::snprintf(buf, sizeof(buf),
+                      "extern \"C\" __device__ void %s(const grins::IntegrateArgs &a, unsigned char *w);\n",
+                      b->name.c_str());
+        s += buf;
+    }
+    std::snprintf(buf, sizeof(buf),
+                  "extern \"C\" __global__ void __launch_bounds__(%d, %d) grins_plan_ct(const grins::PlanArgs p)\n{\n"
+                  "    grins::plan_run(p, [](int body, const grins::IntegrateArgs &a, unsigned char *w) {\n"
+                  "        switch (body) {\n", warps * kWarp, minb);
+    s += buf;
+    for (size_t i = 0; i < bodies.size(); ++i) {
+        std::snprintf(buf, sizeof(buf), "        case %zu: %s(a, w); break;\n", i, bodies[i]->name.c_str());
+        s += buf;
+    }
+    s += "        default: break;\n        }\n    });\n}\n";
+    return s;
+}
+
+}  // namespace
+
+// The plan kernel for n layouts with `minb` resident blocks of `warps`
+// warps per SM (a register cap of 65536 / (32 warps minb) for every body):
+// each distinct layout's body compiled apart (in parallel on the host pool,
+// cached per layout and cap), a dispatcher compiled for this plan, linked
+// with nvJitLink and loaded.  Cached by the dispatcher's source.
+const void *grp_jit_plan_kernel(const GrpTopo *lay, int n, int warps, int minb, std::string *why)
+{
+    if (n < 1 || warps < 1 || minb < 1) { if (why) *why = "bad plan kernel request"; return nullptr; }
+    for (int i = 0; i < n; ++i)
+        if (!jit_enabled(lay[i], why)) return nullptr;
+    JitLinkApi &lk = jitlink();
+    if (!lk.ok) { if (why) *why = lk.why; return nullptr; }
+    const int maxreg = std::min(255, 65536 / (warps * kWarp * minb) / 8 * 8);
+    std::vector<std::shared_ptr<PlanBody>> bodies;
+    for (int i = 0; i < n; ++i) bodies.push_back(plan_body(lay[i], maxreg));
+    {
+        PlanBodyCache &c = plan_body_cache();
+        std::unique_lock<std::mutex> lock(c.mu);
+        for (const auto &b : bodies) {
+            c.cv.wait(lock, [&b] { return b->state.load() != 0; });
+            if (b->state.load() != 1) { if (why) *why = "body compile: " + b->why; return nullptr; }
+        }
+    }
+    const std::string key = plan_dispatch_source(bodies, warps, minb);
+    JitCache &c = jit_cache();
+    std::unique_lock<std::mutex> lock(c.mu);
+    auto it = c.map.find(key);
+    std::shared_ptr<JitEntry> e;
+    if (it == c.map.end()) {
+        e = std::make_shared<JitEntry>();
+        e->kind = kJitRegisters;
+        e->warps = warps;
+        c.map.emplace(key, e);
+        lock.unlock();
+        std::string w;
+        std::vector<char> disp = rdc_compile(key, maxreg, &w);
+        std::vector<char> linked;
+        if (!disp.empty()) {
+            nvJitLinkHandle hl = nullptr;
+            const std::string arch = "-arch=sm_103a";
+            const char *lopts[] = {arch.c_str()};
+            nvJitLinkResult lr = lk.create(&hl, 1, lopts);
+            if (lr == NVJITLINK_SUCCESS) lr = lk.add_data(hl, NVJITLINK_INPUT_CUBIN, disp.data(), disp.size(), "dispatch");
+            for (size_t i = 0; lr == NVJITLINK_SUCCESS && i < bodies.size(); ++i)
+                lr = lk.add_data(hl, NVJITLINK_INPUT_CUBIN, bodies[i]->cubin.data(), bodies[i]->cubin.size(),
+                                 bodies[i]->name.c_str());
+            if (lr == NVJITLINK_SUCCESS) lr = lk.complete(hl);
+            size_t sz = 0;
+            if (lr == NVJITLINK_SUCCESS) lr = lk.cubin_size(hl, &sz);
+            if (lr == NVJITLINK_SUCCESS) { linked.resize(sz); lr = lk.cubin(hl, linked.data()); }
+            if (lr != NVJITLINK_SUCCESS) {
+                size_t ln = 0;
+                std::string log;
+                if (hl && lk.err_size(hl, &ln) == NVJITLINK_SUCCESS && ln) { log.resize(ln); lk.err_log(hl, &log[0]); }
+                w = "nvJitLink error " + std::to_string((int)lr) + ": " + log;
+                linked.clear();
+            }
+            if (hl) lk.destroy(&hl);
+        }
+        cudaLibrary_t lib = nullptr;
+        cudaKernel_t kern = nullptr;
+        if (!linked.empty()) {
+            cudaError_t ce = cudaLibraryLoadData(&lib, linked.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+            if (ce == cudaSuccess) ce = cudaLibraryGetKernel(&kern, lib, "grins_plan_ct");
+            if (ce != cudaSuccess) { w = std::string("loading the plan kernel: ") + cudaGetErrorString(ce); kern = nullptr; }
+        }
+        lock.lock();
+        e->why = w;
+        e->lib = lib;
+        e->kern = kern;
+        e->state.store(kern ? 1 : -1);
+        c.cv.notify_all();
+    } else {
+        e = it->second;
+        c.cv.wait(lock, [&e] { return e->state.load() != 0; });
+    }
+    if (e->state.load() != 1) { if (why) *why = e->why; return nullptr; }
+    if (why) why->clear();
+    return e.get();
+}
+
+cudaError_t launch_plan_ct(const void *handle, const PlanArgs &p, cudaStream_t st, int num_sms, int smem_limit)
+{
+    const JitEntry *je = static_cast<const JitEntry *>(handle);
+    if (je->state.load() != 1) return cudaErrorInvalidValue;
+    const int smem = je->warps * p.region_bytes;
+    if (smem > smem_limit) return cudaErrorInvalidConfiguration;
+    const void *kern = reinterpret_cast<const void *>(je->kern);
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (err != cudaSuccess) return err;
+    int per_sm = 0;
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, je->warps * kWarp, smem);
+    if (err != cudaSuccess) return err;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    PlanArgs q = p;
+    void *args[] = {&q};
+    err = cudaLaunchKernel(kern, dim3((unsigned)(num_sms * per_sm)), dim3(je->warps * kWarp), args, (size_t)smem, st);
+    if (err != cudaSuccess) return err;
+    return cudaGetLastError();
 }
 
 cudaError_t launch_grp_jit(const void *handle, const IntegrateArgs &a, cudaStream_t st, int num_sms)
