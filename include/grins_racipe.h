@@ -65,8 +65,12 @@ typedef enum {
     GRINS_SS_TEND = 1,         /* reached t_end first */
     GRINS_SS_MAXSTEPS = 2,     /* spent max_steps step attempts */
     GRINS_SS_NONFINITE = 3,    /* NaN/Inf or step-size underflow */
-    GRINS_SS_POLISH_FAIL = 4   /* converged, but the FP64 polish did not certify it;
+    GRINS_SS_POLISH_FAIL = 4,  /* converged, but the FP64 polish did not certify it;
                                   the unpolished state is returned */
+    GRINS_SS_CANCELLED = 5     /* not finished: the call's cancel flag was set before
+                                  the solve started (or, in the polish, before its
+                                  converged state was polished); its state is not a
+                                  result */
 } grins_solve_status;
 
 enum { GRINS_FP64 = 0, GRINS_FP32 = 1 };                       /* precision */
@@ -238,6 +242,16 @@ typedef struct {
                                   grins_racipe_integrate records on its stream after
                                   the integration pass and before the re-pass and the
                                   polish, so a caller can time the integrator alone */
+    const volatile int32_t *cancel; /* NULL = none: an int32 the GPU can read (pinned
+                                  host memory mapped for the device, or device
+                                  memory), polled by the integrators and the polish
+                                  each time they take their next work item (a solve,
+                                  a parameter set or a polish unit).  Once it is
+                                  nonzero no further work starts: solves in flight
+                                  finish, every solve not yet started -- and every
+                                  converged solve not yet polished -- gets
+                                  GRINS_SS_CANCELLED, and the call completes as
+                                  usual (it returns GRINS_OK; the statuses tell) */
 } grins_solver_opts;
 
 void grins_racipe_default_ranges(grins_racipe_ranges *r);
@@ -444,7 +458,8 @@ typedef struct {
     double jit_max_wait_s;
 } grins_server_config;
 
-enum { GRINS_REQ_QUEUED = 0, GRINS_REQ_RUNNING = 1, GRINS_REQ_DONE = 2, GRINS_REQ_FAILED = 3 };
+enum { GRINS_REQ_QUEUED = 0, GRINS_REQ_RUNNING = 1, GRINS_REQ_DONE = 2, GRINS_REQ_FAILED = 3,
+       GRINS_REQ_CANCELLED = 4 };
 
 typedef struct {
     int32_t state;             /* GRINS_REQ_* */
@@ -480,6 +495,16 @@ grins_status grins_racipe_server_submit(grins_racipe_server_t sv, grins_racipe_t
  * reports its state and timings in *info (nullable). */
 grins_status grins_racipe_server_wait(grins_racipe_server_t sv, int64_t request_id, double timeout_s,
                                       grins_request_info *info);
+
+/* Cancels a request.  Queued: it never runs (state GRINS_REQ_CANCELLED, no
+ * results).  Running: its kernels start no further work -- solves in flight
+ * finish, the others get GRINS_SS_CANCELLED (through a per-slot flag in
+ * pinned host memory mapped for the device, grins_solver_opts.cancel) -- and
+ * it ends in GRINS_REQ_CANCELLED with error GRINS_E_CANCELLED; its results
+ * can still be copied (the statuses tell which solves finished).  Finished:
+ * no effect.  Returns at once; grins_racipe_server_wait waits for the end.
+ * Errors: GRINS_E_INVALID_ARG for an unknown request. */
+grins_status grins_racipe_server_cancel(grins_racipe_server_t sv, int64_t request_id);
 
 /* Copies a finished request's results into caller buffers (each nullable):
  * states double [n_sets][n_ics][N], status uint8 [n_sets][n_ics],

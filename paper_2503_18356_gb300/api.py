@@ -29,7 +29,7 @@ _lib = C.CDLL(LIB_PATH)
 
 GRINS_OK, GRINS_E_INVALID_ARG, GRINS_E_TOPOLOGY, GRINS_E_NOMEM, GRINS_E_CUDA, GRINS_E_BUDGET, \
     GRINS_E_CANCELLED = range(7)
-CONVERGED, TEND, MAXSTEPS, NONFINITE, POLISH_FAIL = range(5)
+CONVERGED, TEND, MAXSTEPS, NONFINITE, POLISH_FAIL, CANCELLED = range(6)
 GRINS_FP64, GRINS_FP32 = 0, 1
 GRINS_METHOD_DOPRI5, GRINS_METHOD_TSIT5 = 0, 1
 GRINS_ISING_SYNC, GRINS_ISING_ASYNC = 0, 1
@@ -74,7 +74,8 @@ class grins_solver_opts(C.Structure):
                 ("polish_tol", C.c_double), ("polish_iters", C.c_int32),
                 ("polish_max_move", C.c_double), ("ss_tighten", C.c_double), ("method", C.c_int32),
                 ("tail_rtol", C.c_double), ("tail_start", C.c_double), ("tail_rho", C.c_double),
-                ("tail_late", C.c_double), ("tail_work", C.c_int32), ("pass_event", C.c_void_p)]
+                ("tail_late", C.c_double), ("tail_work", C.c_int32), ("pass_event", C.c_void_p),
+                ("cancel", C.c_void_p)]
 
 
 class grins_racipe_job(C.Structure):
@@ -95,7 +96,7 @@ class grins_request_info(C.Structure):
                 ("bytes", C.c_int64), ("queued_s", C.c_double), ("latency_s", C.c_double)]
 
 
-REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = range(4)
+REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED, REQ_CANCELLED = range(5)
 
 _H = C.c_void_p
 _P = C.c_void_p
@@ -130,6 +131,7 @@ _sig = {
     "grins_racipe_server_wait": (_S, [_H, C.c_int64, C.c_double, C.POINTER(grins_request_info)]),
     "grins_racipe_server_copy_results": (_S, [_H, C.c_int64, _P, _P, _P, _P, _P, _P]),
     "grins_racipe_server_release": (_S, [_H, C.c_int64]),
+    "grins_racipe_server_cancel": (_S, [_H, C.c_int64]),
     "grins_racipe_server_destroy": (_S, [_H]),
     "grins_racipe_tail_stats": (_S, [_H, _P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "grins_racipe_polish": (_S, [_H, C.POINTER(grins_solver_opts), _P, C.c_int64, C.c_int32, _P, _P, _P, _P]),
@@ -533,7 +535,7 @@ class Server:
     def wait(self, rid, timeout_s=-1.0):
         info = grins_request_info()
         _check(_lib.grins_racipe_server_wait(self._s, rid, timeout_s, C.byref(info)))
-        return dict(state=info.state, n_sets=info.n_sets, n_ics=info.n_ics, bytes=info.bytes,
+        return dict(state=info.state, error=info.error, n_sets=info.n_sets, n_ics=info.n_ics, bytes=info.bytes,
                     queued_s=info.queued_s, latency_s=info.latency_s)
 
     def results(self, rid, stream=None, keys=("states", "status", "n_unique", "state_id", "n_steps")):
@@ -550,6 +552,10 @@ class Server:
                                                          _ptr(out.get("state_id")), _ptr(out.get("n_steps")),
                                                          _stream(stream)))
         return out
+
+    def cancel(self, rid):
+        """grins_racipe_server_cancel: stop a queued or running request."""
+        _check(_lib.grins_racipe_server_cancel(self._s, rid))
 
     def release(self, rid):
         _check(_lib.grins_racipe_server_release(self._s, rid))

@@ -1109,6 +1109,7 @@ static PolishArgs polish_args(const grins_racipe *h, const grins_solver_opts *o,
     p.max_move = o->polish_max_move;
     p.iters = o->polish_iters;
     p.check = h->d_queue + 2;
+    p.cancel = o->cancel;
     return p;
 }
 
@@ -1136,7 +1137,8 @@ static void pick_fp64_kernel(const grins_racipe *h, IntegrateArgs *a, bool compi
     std::string w = h->rr.L > 0 ? "" : "no register layout";
     if (h->rr.L > 0) {
         const GrpTopo g = h->rr.topo();
-        const int variant = a->method | (a->n_t > 0 ? kJitSeries : 0) | (tail ? kJitTail : 0);
+        const int variant = a->method | (a->n_t > 0 ? kJitSeries : 0) | (tail ? kJitTail : 0) |
+                            (a->cancel ? kJitCancel : 0);
         // a lookup also takes the re-pass variant, which runs the same without a list
         const void *k = compile ? grp_jit_kernel(g, kJitRegisters64, &w, variant)
                                 : lookup_either(g, kJitRegisters64, variant);
@@ -1174,7 +1176,8 @@ static bool pick_fp32_kernel(const grins_racipe *h, IntegrateArgs *a, bool compi
     std::string w;
     if (!want_shared && h->rr.L > 0) {
         const GrpTopo g = h->rr.topo();
-        const int variant = a->method | (a->n_t > 0 ? kJitSeries : 0) | (tail ? kJitTail : 0);
+        const int variant = a->method | (a->n_t > 0 ? kJitSeries : 0) | (tail ? kJitTail : 0) |
+                            (a->cancel ? kJitCancel : 0);
         const void *k = compile ? grp_jit_kernel(g, kJitRegisters, &w, variant)
                                 : lookup_either(g, kJitRegisters, variant);
         if (k) { a->grp = g; a->grp_jit = k; if (why) *why = w; return true; }
@@ -1297,6 +1300,7 @@ extern "C" grins_status grins_racipe_integrate(grins_racipe_t h, const grins_sol
     a.slots = slots_for(n_ics);
     a.smem_limit = (int32_t)h->smem_optin;
     a.grp = grp_topo(h);
+    a.cancel = o->cancel;
     IntegrateArgs a64{};             // the borderline re-pass, when it runs
     bool tail = false;
     IntegrateArgs::TailItem *tail_sorted = nullptr;   // its list, longest first
@@ -1678,6 +1682,7 @@ static void plan_args(grins_racipe_plan *p, int slot_extra, int sample)
         a.smem_limit = p->smem_limit;
         a.grp = grp_topo(h);
         a.grp_jit = nullptr;
+        a.cancel = o->cancel;
         const int ndom = grp_domains(a.grp.L);
         const int groups = kWarp / a.grp.L / ndom;
         int sd = (groups + j.n_ics - 1) / j.n_ics + slot_extra;
@@ -1806,7 +1811,8 @@ static grins_status plan_setup_ct(grins_racipe_plan *p, cudaStream_t st)
         body[b] = found;
         gather = std::max(gather, rr_warp_bytes(g.R, 1, 4));
     }
-    p->ct_kern = grp_jit_plan_kernel(lays.data(), (int)lays.size(), p->ct_warps, p->ct_minb, &p->ct_why);
+    p->ct_kern = grp_jit_plan_kernel(lays.data(), (int)lays.size(), p->ct_warps, p->ct_minb,
+                                     p->opts.cancel != nullptr, &p->ct_why);
     if (!p->ct_kern) return fail(GRINS_E_BUDGET, "plan: no compiled plan kernel (%s)", p->ct_why.c_str());
     p->ct_bodies = (int)lays.size();
     std::vector<IntegrateArgs> a = p->args;
@@ -1871,7 +1877,7 @@ static grins_status plan_setup_branches(grins_racipe_plan *p, bool prefetch)
         p->prefetched = true;
         for (size_t b = 0; b < n; ++b) {          // start every compile before waiting for any
             const grins_racipe *h = p->jobs[b].net;
-            if (h->rr.L > 0) grp_jit_prefetch(h->rr.topo(), kJitRegisters);
+            if (h->rr.L > 0) grp_jit_prefetch(h->rr.topo(), kJitRegisters, p->opts.cancel ? kJitCancel : 0);
             else grp_jit_prefetch(h->grp.topo(), kJitShared);
         }
     }
@@ -2141,6 +2147,7 @@ struct ServerRequest {
     int64_t bytes = 0;
     int slot = -1;
     bool jit_wait = false;         // admitted once its compile is done (or jit_max_wait_s passed)
+    bool cancel = false;           // grins_racipe_server_cancel was called while it ran
     GrpTopo jit_topo{};
     int jit_kind = 0;
     unsigned char *mem = nullptr;
@@ -2174,11 +2181,18 @@ struct grins_racipe_server {
     bool stop = false;
     int64_t next_id = 1;
     std::string fatal;
+    // one cancel flag per in-flight slot, in pinned host memory mapped for
+    // the device: the kernels of the slot's request poll it
+    volatile int32_t *cancel_host = nullptr;
+    const volatile int32_t *cancel_dev = nullptr;
 };
 
 namespace {
 
 // Bytes of device memory a request holds from admission to release.
+// A request's compiled register-record kernel polls its slot's cancel flag.
+int server_variant(int kind) { return kind == kJitShared ? 0 : kJitCancel; }
+
 int64_t request_bytes(const ServerRequest &r)
 {
     const int64_t S = r.n_sets, I = r.n_ics, N = r.net->N;
@@ -2226,6 +2240,8 @@ grins_status server_launch(grins_racipe_server *sv, ServerRequest &r)
     a.slots = slots_for(I);
     a.smem_limit = (int32_t)h->smem_optin;
     a.grp = grp_topo(h);
+    sv->cancel_host[r.slot] = 0;
+    a.cancel = sv->cancel_dev + r.slot;       // the slot's flag, not the submitted options' pointer
     if (o->precision == GRINS_FP32) pick_fp32_kernel(h, &a, false, nullptr);   // never compiles here
     else pick_fp64_kernel(h, &a, false, nullptr);
     CUDA_TRY(cudaMemsetAsync(r.words, 0, 32, st), "server: counter reset");
@@ -2237,6 +2253,7 @@ grins_status server_launch(grins_racipe_server *sv, ServerRequest &r)
     if (o->polish) {
         PolishArgs pa = polish_args(h, o, r.params, S, I, r.states, r.status, r.err_est);
         pa.check = r.words + 2;
+        pa.cancel = a.cancel;
         CUDA_TRY(launch_polish(pa, st, h->num_sms), "server: polish launch");
     } else {
         CUDA_TRY(cudaMemsetAsync(r.err_est, 0xff, sizeof(float) * S * I, st), "server: err_est");
@@ -2261,8 +2278,9 @@ void server_loop(grins_racipe_server *sv)
             const cudaError_t q = cudaEventQuery(r.done);
             if (q == cudaErrorNotReady) continue;
             r.t_done = now_s();
-            r.state = q == cudaSuccess ? GRINS_REQ_DONE : GRINS_REQ_FAILED;
+            r.state = q == cudaSuccess ? (r.cancel ? GRINS_REQ_CANCELLED : GRINS_REQ_DONE) : GRINS_REQ_FAILED;
             if (q != cudaSuccess) { r.err = GRINS_E_CUDA; r.msg = cudaGetErrorString(q); }
+            else if (r.cancel) { r.err = GRINS_E_CANCELLED; r.msg = "cancelled while running"; }
             sv->slot_busy[r.slot] = 0;
             sv->busy_nets.erase(r.net);
             progress = true;
@@ -2278,7 +2296,8 @@ void server_loop(grins_racipe_server *sv)
             if (slot < 0) break;
             if (sv->busy_nets.count(r.net)) { ++it; continue; }
             if (r.jit_wait) {
-                if (grp_jit_prefetch(r.jit_topo, r.jit_kind) == 0 && now_s() - r.t_submit < sv->jit_max_wait_s) {
+                if (grp_jit_prefetch(r.jit_topo, r.jit_kind, server_variant(r.jit_kind)) == 0 &&
+                    now_s() - r.t_submit < sv->jit_max_wait_s) {
                     ++it;
                     continue;
                 }
@@ -2358,6 +2377,22 @@ extern "C" grins_status grins_racipe_server_create(const grins_server_config *c,
             return cuda_fail(e, "server_create: streams");
         }
     }
+    {
+        int32_t *hf = nullptr;
+        void *df = nullptr;
+        cudaError_t e = cudaHostAlloc(reinterpret_cast<void **>(&hf), sizeof(int32_t) * sv->max_inflight,
+                                      cudaHostAllocMapped);
+        if (e == cudaSuccess) e = cudaHostGetDevicePointer(&df, hf, 0);
+        if (e != cudaSuccess) {
+            if (hf) cudaFreeHost(hf);
+            for (auto &x : sv->streams) cudaStreamDestroy(x);
+            cudaMemPoolDestroy(sv->pool);
+            return cuda_fail(e, "server_create: cancel flags");
+        }
+        for (int i = 0; i < sv->max_inflight; ++i) hf[i] = 0;
+        sv->cancel_host = hf;
+        sv->cancel_dev = static_cast<const volatile int32_t *>(df);
+    }
     grins_racipe_server *raw = sv.release();
     raw->worker = std::thread(server_loop, raw);
     *out = raw;
@@ -2431,7 +2466,7 @@ extern "C" grins_status grins_racipe_server_submit(grins_racipe_server_t sv, gri
         } else {
             req->jit_topo = net->grp.topo(); req->jit_kind = kJitShared;
         }
-        req->jit_wait = grp_jit_prefetch(req->jit_topo, req->jit_kind) == 0;
+        req->jit_wait = grp_jit_prefetch(req->jit_topo, req->jit_kind, server_variant(req->jit_kind)) == 0;
     }
     CUDA_TRY(cudaEventCreateWithFlags(&req->done, cudaEventDisableTiming), "server_submit: event");
     std::lock_guard<std::mutex> lock(sv->mu);
@@ -2452,7 +2487,8 @@ static void fill_info(const ServerRequest &r, grins_request_info *info)
     info->n_sets = r.n_sets;
     info->n_ics = r.n_ics;
     info->bytes = r.bytes;
-    info->queued_s = (r.state >= GRINS_REQ_RUNNING ? r.t_admit : now_s()) - r.t_submit;
+    const double t_out = r.t_admit > 0 ? r.t_admit : (r.state >= GRINS_REQ_DONE ? r.t_done : now_s());
+    info->queued_s = t_out - r.t_submit;
     info->latency_s = r.state >= GRINS_REQ_DONE ? r.t_done - r.t_submit : -1.0;
 }
 
@@ -2488,7 +2524,8 @@ extern "C" grins_status grins_racipe_server_copy_results(grins_racipe_server_t s
     auto it = sv->reqs.find(id);
     if (it == sv->reqs.end()) return fail(GRINS_E_INVALID_ARG, "server_copy_results: unknown request");
     ServerRequest &r = *it->second;
-    if (r.state != GRINS_REQ_DONE) return fail(GRINS_E_INVALID_ARG, "server_copy_results: request not done");
+    if (r.state != GRINS_REQ_DONE && !(r.state == GRINS_REQ_CANCELLED && r.mem))
+        return fail(GRINS_E_INVALID_ARG, "server_copy_results: request not done (or cancelled before it ran)");
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t S = r.n_sets, I = r.n_ics, N = r.net->N;
     if (d_states) CUDA_TRY(cudaMemcpyAsync(d_states, r.states, S * I * N * 8, cudaMemcpyDeviceToDevice, st), "copy");
@@ -2496,6 +2533,31 @@ extern "C" grins_status grins_racipe_server_copy_results(grins_racipe_server_t s
     if (d_n_unique) CUDA_TRY(cudaMemcpyAsync(d_n_unique, r.n_unique, S * 4, cudaMemcpyDeviceToDevice, st), "copy");
     if (d_state_id) CUDA_TRY(cudaMemcpyAsync(d_state_id, r.state_id, S * I * 4, cudaMemcpyDeviceToDevice, st), "copy");
     if (d_n_steps) CUDA_TRY(cudaMemcpyAsync(d_n_steps, r.n_steps, S * I * 4, cudaMemcpyDeviceToDevice, st), "copy");
+    return GRINS_OK;
+}
+
+extern "C" grins_status grins_racipe_server_cancel(grins_racipe_server_t sv, int64_t id)
+{
+    g_last_error.clear();
+    if (!sv) return fail(GRINS_E_INVALID_ARG, "server_cancel: NULL server");
+    std::lock_guard<std::mutex> lock(sv->mu);
+    auto it = sv->reqs.find(id);
+    if (it == sv->reqs.end()) return fail(GRINS_E_INVALID_ARG, "server_cancel: unknown request");
+    ServerRequest &r = *it->second;
+    if (r.state == GRINS_REQ_QUEUED) {
+        // never admitted: no buffers, no slot
+        for (auto p = sv->pending.begin(); p != sv->pending.end(); ++p)
+            if (*p == id) { sv->pending.erase(p); break; }
+        r.state = GRINS_REQ_CANCELLED;
+        r.err = GRINS_E_CANCELLED;
+        r.msg = "cancelled before it ran";
+        r.t_done = now_s();
+        sv->cv_done.notify_all();
+        sv->cv.notify_all();
+    } else if (r.state == GRINS_REQ_RUNNING && !r.cancel) {
+        r.cancel = true;
+        sv->cancel_host[r.slot] = 1;            // the slot's kernels stop taking work
+    }
     return GRINS_OK;
 }
 
@@ -2536,6 +2598,7 @@ extern "C" grins_status grins_racipe_server_destroy(grins_racipe_server_t sv)
     }
     for (auto &st : sv->streams) { cudaStreamSynchronize(st); cudaStreamDestroy(st); }
     cudaMemPoolDestroy(sv->pool);
+    cudaFreeHost(const_cast<int32_t *>(sv->cancel_host));
     delete sv;
     return GRINS_OK;
 }
@@ -2722,6 +2785,7 @@ extern "C" grins_status grins_racipe_integrate_static(grins_racipe_t h, const gr
     a.slots = slots_for(n_ics);
     a.smem_limit = (int32_t)h->smem_optin;
     a.grp = grp_topo(h);
+    a.cancel = o->cancel;
     if (o->precision == GRINS_FP32) pick_fp32_kernel(h, &a, false, nullptr);   // only kernels an earlier call loaded
     else pick_fp64_kernel(h, &a, false, nullptr);
     if (a.method != GRINS_METHOD_DOPRI5 && !a.grp_jit)

@@ -138,6 +138,7 @@ struct IntegrateArgs {
     unsigned long long *tail_n;  // [2]: items appended, FP64 attempts spent on them
     float f_tail_chk, f_tail_rho, f_tail_late;
     int32_t tail_work;
+    const volatile int32_t *cancel;   // nullable: nonzero stops the hand-out of work (grins_solver_opts.cancel)
 };
 
 // Jobs of one batched launch (a plan): per-job arguments as for a single
@@ -181,6 +182,7 @@ enum JitKind { kJitShared = 0, kJitRegisters = 1, kJitRegisters64 = 2 };
 constexpr int kJitMethodMask = 15;
 constexpr int kJitSeries = 16;
 constexpr int kJitTail = 32;      // with the borderline re-pass (checkpoints / list mode)
+constexpr int kJitCancel = 64;    // polling a cancel flag (grins_solver_opts.cancel)
 const void *grp_jit_kernel(const GrpTopo &g, int kind, std::string *why, int method = 0);
 const void *grp_jit_lookup(const GrpTopo &g, int kind, int method = 0);
 // Starts (once) a background compile for layout g: 1 ready, 0 compiling, -1
@@ -198,7 +200,8 @@ cudaError_t launch_integrate_fp64(const IntegrateArgs &a, cudaStream_t st, int n
 // FP32 Dormand-Prince, no time series, no re-pass) with `minb` resident
 // blocks of `warps` warps per SM, built on first use and cached; null with
 // the reason in *why.
-const void *grp_jit_plan_kernel(const GrpTopo *layouts, int n_layouts, int warps, int minb, std::string *why);
+const void *grp_jit_plan_kernel(const GrpTopo *layouts, int n_layouts, int warps, int minb, bool cancel,
+                                std::string *why);
 // Launch of a plan kernel: grid of resident blocks, smem = warps x region.
 cudaError_t launch_plan_ct(const void *kern, const PlanArgs &p, cudaStream_t st, int num_sms, int smem_limit);
 // The borderline re-pass list `in` (n_in[0] items) copied to `out` longest
@@ -221,6 +224,7 @@ struct PolishArgs {
     double tol, max_move;
     int32_t iters;
     unsigned long long *check;   // checked builds: first violation (code, info)
+    const volatile int32_t *cancel;   // nullable: nonzero marks unpolished converged solves cancelled
 };
 
 #ifndef __CUDACC_RTC__
@@ -284,6 +288,36 @@ struct IsingArgs {
 
 #ifndef __CUDACC_RTC__
 cudaError_t launch_ising(const IsingArgs &a, cudaStream_t st, int num_sms);
+#endif
+
+// ---------------------------------------------------------- cancellation
+#ifdef __CUDACC__
+// The cancel flag of a call (nullable), read by lane 0 and broadcast: the
+// same answer on every lane of the warp.
+__device__ __forceinline__ bool grins_cancelled(const volatile int32_t *flag)
+{
+    int v = 0;
+    if (flag != nullptr && (threadIdx.x & 31) == 0) v = *flag;
+    return __shfl_sync(0xffffffffu, v, 0) != 0;
+}
+
+// After a cancel: hands out every parameter set left in a set counter
+// (queue, sets of n_ics solves), 32 at a time, and marks their solves
+// GRINS_SS_CANCELLED; warp-uniform.
+__device__ __forceinline__ void grins_cancel_sets(unsigned long long *queue, long long n_sets, int n_ics,
+                                                  uint8_t *status)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll 1
+    for (;;) {
+        unsigned long long b0 = 0;
+        if (lane == 0) b0 = atomicAdd(queue, 32ull);
+        b0 = __shfl_sync(0xffffffffu, b0, 0);
+        if ((long long)b0 >= n_sets) return;
+        const long long b1 = (long long)b0 + 32 < n_sets ? (long long)b0 + 32 : n_sets;
+        for (long long i = (long long)b0 * n_ics + lane; i < b1 * n_ics; i += 32) status[i] = GRINS_SS_CANCELLED;
+    }
+}
 #endif
 
 // ------------------------------------------------------------- device RNG

@@ -156,6 +156,22 @@ dp5_generic_kernel(const IntegrateArgs a)
     };
 
     auto refill = [&]() {
+        if (a.cancel != nullptr && !exhausted && grins_cancelled(a.cancel)) {
+            // cancelled: the initial conditions still pending in this warp's
+            // slots and every set left in the counter are marked, not started
+            for (int sl = 0; sl < S; ++sl) {
+                const long long set = meta[sl].set;
+                const int first = meta[sl].next_ic;
+                if (set >= 0 && first < a.n_ics)
+                    for (int ic = first + lane; ic < a.n_ics; ic += 32) a.status[set * a.n_ics + ic] = GRINS_SS_CANCELLED;
+                __syncwarp();
+                if (lane == 0 && set >= 0 && first < a.n_ics) meta[sl].next_ic = a.n_ics;
+                __syncwarp();
+            }
+            grins_cancel_sets(a.queue, a.n_sets, a.n_ics, a.status);
+            exhausted = true;
+            return;
+        }
         for (;;) {
             const unsigned idle = __ballot_sync(FULL, my_slot < 0);
             if (idle == 0) return;

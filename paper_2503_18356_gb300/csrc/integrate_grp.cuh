@@ -356,6 +356,23 @@ __device__ __forceinline__ void grp_body(const IntegrateArgs &a, unsigned char *
     // at most four distinct 16-byte records, which two slots of a half-warp
     // of two-lane groups never exceed.
     auto refill = [&]() {
+        if (a.cancel != nullptr && !exhausted && grins_cancelled(a.cancel)) {
+            // cancelled: the initial conditions still pending in this warp's
+            // slots and every set left in the counter are marked, not started
+#pragma unroll 1
+            for (int sl = 0; sl < NDOM * SD; ++sl) {
+                const long long set = meta[sl].set;
+                const int first = meta[sl].next_ic;
+                if (set >= 0 && first < a.n_ics)
+                    for (int ic = first + lane; ic < a.n_ics; ic += kWarp) a.status[set * a.n_ics + ic] = GRINS_SS_CANCELLED;
+                __syncwarp();
+                if (lane == 0 && set >= 0 && first < a.n_ics) meta[sl].next_ic = a.n_ics;
+                __syncwarp();
+            }
+            grins_cancel_sets(a.queue, a.n_sets, a.n_ics, a.status);
+            exhausted = true;
+            return;
+        }
 #pragma unroll 1
         for (int d = 0; d < NDOM; ++d) {
             // the domain's groups are bits d*DG .. d*DG+DG-1 of the ballot

@@ -241,9 +241,10 @@ std::string jit_main(const GrpTopo &g, int kind, int minb, int warps, int method
         else std::snprintf(bounds, sizeof(bounds), "__launch_bounds__(%d, %d)", warps * kWarp, minb);
         std::snprintf(buf, sizeof(buf),
                       "extern \"C\" __global__ void %s grins_grp_ct(const grins::IntegrateArgs a)\n"
-                      "{\n    grins::rr_body<%d, %d, %d, %s, %d, %s, %s>(a);\n}\n",
+                      "{\n    grins::rr_body<%d, %d, %d, %s, %d, %s, %s, %s>(a);\n}\n",
                       bounds, g.R, warps, g.L, kind == kJitRegisters64 ? "double" : "float", method & kJitMethodMask,
-                      (method & kJitSeries) ? "true" : "false", (method & kJitTail) ? "true" : "false");
+                      (method & kJitSeries) ? "true" : "false", (method & kJitTail) ? "true" : "false",
+                      (method & kJitCancel) ? "true" : "false");
     } else {
         s += "}\n#include \"integrate_grp.cuh\"\n";
         std::snprintf(buf, sizeof(buf),
@@ -543,7 +544,7 @@ PlanBodyCache &plan_body_cache()
     return *c;
 }
 
-std::string body_source(const GrpTopo &g, const std::string &name)
+std::string body_source(const GrpTopo &g, const std::string &name, bool cancel)
 {
     std::string s = "#include \"common.cuh\"\n#include \"integrate_grp.cuh\"\nnamespace grins { namespace pkb {\n";
     s += layout_prelude(g, true);
@@ -551,19 +552,19 @@ std::string body_source(const GrpTopo &g, const std::string &name)
     char buf[320];
     std::snprintf(buf, sizeof(buf),
                   "extern \"C\" __device__ __noinline__ void %s(const grins::IntegrateArgs &a, unsigned char *w)\n"
-                  "{ grins::pkb::rr_body_at<%d, 4, %d, float, 0, false, false>(a, w); }\n",
-                  name.c_str(), g.R, g.L);
+                  "{ grins::pkb::rr_body_at<%d, 4, %d, float, 0, false, false, %s>(a, w); }\n",
+                  name.c_str(), g.R, g.L, cancel ? "true" : "false");
     return s + buf;
 }
 
 // The body for layout g under register cap maxreg: from the cache, or a
 // compile queued on the host pool (the caller waits for it).
-std::shared_ptr<PlanBody> plan_body(const GrpTopo &g, int maxreg)
+std::shared_ptr<PlanBody> plan_body(const GrpTopo &g, int maxreg, bool cancel)
 {
     const std::string lay = layout_prelude(g, true) + "L=" + std::to_string(g.L) + " R=" + std::to_string(g.R);
     char id[64];
-    std::snprintf(id, sizeof(id), "grins_body_%016zx_%d", std::hash<std::string>()(lay), maxreg);
-    const std::string src = body_source(g, id);
+    std::snprintf(id, sizeof(id), "grins_body_%016zx_%d%s", std::hash<std::string>()(lay), maxreg, cancel ? "c" : "");
+    const std::string src = body_source(g, id, cancel);
     const std::string key = src + "\nmaxreg " + std::to_string(maxreg);
     PlanBodyCache &c = plan_body_cache();
     std::lock_guard<std::mutex> lock(c.mu);
@@ -619,7 +620,7 @@ std::string plan_dispatch_source(const std::vector<std::shared_ptr<PlanBody>> &b
 // each distinct layout's body compiled apart (in parallel on the host pool,
 // cached per layout and cap), a dispatcher compiled for this plan, linked
 // with nvJitLink and loaded.  Cached by the dispatcher's source.
-const void *grp_jit_plan_kernel(const GrpTopo *lay, int n, int warps, int minb, std::string *why)
+const void *grp_jit_plan_kernel(const GrpTopo *lay, int n, int warps, int minb, bool cancel, std::string *why)
 {
     if (n < 1 || warps < 1 || minb < 1) { if (why) *why = "bad plan kernel request"; return nullptr; }
     for (int i = 0; i < n; ++i)
@@ -628,7 +629,7 @@ const void *grp_jit_plan_kernel(const GrpTopo *lay, int n, int warps, int minb, 
     if (!lk.ok) { if (why) *why = lk.why; return nullptr; }
     const int maxreg = std::min(255, 65536 / (warps * kWarp * minb) / 8 * 8);
     std::vector<std::shared_ptr<PlanBody>> bodies;
-    for (int i = 0; i < n; ++i) bodies.push_back(plan_body(lay[i], maxreg));
+    for (int i = 0; i < n; ++i) bodies.push_back(plan_body(lay[i], maxreg, cancel));
     {
         PlanBodyCache &c = plan_body_cache();
         std::unique_lock<std::mutex> lock(c.mu);

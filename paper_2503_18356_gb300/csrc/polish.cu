@@ -120,6 +120,15 @@ __global__ void __launch_bounds__(WARPS * kWarp) polish_kernel(const PolishArgs 
         const long long set = u / upc;
         const int ic0 = (int)(u - set * upc) * kUnitIcs;
         const int ic1 = min(ic0 + kUnitIcs, a.n_ics);
+        if (a.cancel != nullptr && grins_cancelled(a.cancel)) {
+            // cancelled: the unit's converged solves stay unpolished
+            for (int ic = ic0 + lane; ic < ic1; ic += kWarp) {
+                const long long idx = set * a.n_ics + ic;
+                if (a.status[idx] == GRINS_SS_CONVERGED) a.status[idx] = GRINS_SS_CANCELLED;
+                if (a.err_est) a.err_est[idx] = -1.0f;
+            }
+            continue;
+        }
         // a unit without converged solves needs no tables
         bool any = false;
         for (int ic = ic0 + lane; ic < ic1; ic += kWarp) {
