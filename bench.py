@@ -33,11 +33,20 @@ METRIC = "RACIPE steady-state solves/s (22-node network, FP32 + FP64 polish)"
 N_SETS = 100_000
 N_ICS = 10
 TOL = dict(rtol=1e-6, atol=1e-9, t_end=200.0, ss_tol=1e-6)
-# DRAM bytes (read + write) of one integrator launch per solve, from an ncu
-# capture of the same kernel on a 20,000-set launch of this workload
-# (35.34 MB read + 1.28 MB written for 200,000 solves); traffic grows with
-# the solves per launch.  None while no capture of the current kernel exists.
-INTEGRATOR_DRAM_BYTES_PER_SOLVE = None
+# DRAM bytes (read + write) of one FP32 integrator launch per solve, from an
+# ncu capture of the same kernel on a 20,000-set launch of this workload
+# (35.30 MB read + 1.21 MB written for 200,000 solves,
+# profiles/grins_grp_ct_rr_rand22x82_20k.md); traffic grows with the solves
+# per launch.  None while no capture of the current kernel exists.
+INTEGRATOR_DRAM_BYTES_PER_SOLVE = 36.51e6 / 200_000
+# Executed FP64 instructions (DADD + DMUL + DFMA, thread level) of the FP64
+# kernels per unit of work, from an ncu capture of the same 20,000-set
+# launch (profiles/fp64_kernels_rand22x82_20k.md): the polish per solve it
+# polishes (converged before the polish: 127,247), the re-pass per FP64 step
+# attempt (254,532), the dedupe per converged solve (127,243).
+POLISH_FP64_INSTR_PER_SOLVE = (37_244_518 + 142_762_810 + 128_571_916) / 127_247
+REPASS_FP64_INSTR_PER_ATTEMPT = (253_617_128 + 766_275_305 + 786_803_446) / 254_532
+UNIQUE_FP64_INSTR_PER_SOLVE = (2_580_512 + 5_598_692 + 19_595_422) / 127_243
 
 
 def parse():
@@ -588,6 +597,9 @@ def run_native(args):
     for _ in range(max(3, args.warmup)):
         step()
     barrier()
+    # issue rates of the units the kernels are bound by (per clock per SM),
+    # measured on this device before the timed region
+    rates = api.unit_rates(stream)
 
     props = torch.cuda.get_device_properties(dev)
     uuid = str(getattr(props, "uuid", "") or "")
@@ -643,15 +655,28 @@ def run_native(args):
     sms = props.multi_processor_count
     f_mhz = clocks.get("sm_mhz") or 1440.0
     t_int = kern_ms[1] / 1e3
-    sfu_bound = wsfu / 16.0 >= w32 / 128.0
+    # the SFU term at the reciprocal-class rate (rcp and lg2; ex2 runs at
+    # about twice it) against the FP32 term at the FMA rate, both measured
+    sfu_rate, fma_rate = rates["rcp"], rates["ffma"]
+    sfu_bound = wsfu / sfu_rate >= w32 / fma_rate
     if sfu_bound:
         achieved = attempts * wsfu / t_int / 1e9
-        peak = 16 * sms * f_mhz * 1e6 / 1e9
+        peak = sfu_rate * sms * f_mhz * 1e6 / 1e9
         unit = "Gop/s (MUFU, SFU pipe)"
     else:
         achieved = attempts * w32 / t_int / 1e9
-        peak = 128 * sms * f_mhz * 1e6 / 1e9
+        peak = fma_rate * sms * f_mhz * 1e6 / 1e9
         unit = "Gop/s (FP32 pipe)"
+    # the FP64 kernels against the FP64 FMA issue rate: executed FP64
+    # instructions per unit (ncu counts, constants above) x units / time
+    fp64_peak = rates["dfma"] * sms * f_mhz * 1e6 / 1e9
+    hist = np.bincount(status.ravel(), minlength=5)
+    n_conv = int(hist[0])
+
+    def fp64_roof(instr, ms, what):
+        ach = instr / (ms / 1e3) / 1e9 if ms > 0 else 0.0
+        return dict(bound="fp64", achieved=ach, peak=fp64_peak, unit="G FP64 instr/s", frac=ach / fp64_peak,
+                    basis=what)
 
     solves = S * I * ws
     value = solves * args.steps / (elapsed_ms / 1e3)
@@ -704,6 +729,7 @@ def run_native(args):
     barrier()
     fp64_ms = e64[0].elapsed_time(e64[1])
     fp64_value = f64_sets * I / (fp64_ms / 1e3)
+    a64 = int(out64["n_steps"].sum().item())        # the FP64 solver's step attempts
     if snap is not None and f64_sets >= snap["n_unique"].shape[0]:
         # the plain FP64 solver's statuses and distinct-state counts on the
         # oracle's sets (polished and deduplicated as the FP32 path is)
@@ -733,14 +759,28 @@ def run_native(args):
                         what="solves whose steady-state decision fell near t_end, re-integrated in FP64 at rtol "
                              "%g from their first state with residual below %g ss_tol (ordering kernel + FP64 "
                              "kernel)" % (opts.tail_rtol, opts.tail_start)),
-            status_hist=np.bincount(status.ravel(), minlength=5).tolist(),
+            status_hist=hist.tolist(),
             roofline=dict(bound="alu", achieved=achieved, peak=peak, unit=unit, frac=achieved / peak,
                           traffic=(INTEGRATOR_DRAM_BYTES_PER_SOLVE * S * I
                                    if INTEGRATOR_DRAM_BYTES_PER_SOLVE else None), kernel=kernel_desc,
-                          peak_basis="%d SMs x %s lanes/clk x %.0f MHz (median SM clock sampled in the "
-                                     "timed region); reciprocal rate measured at 16/clk/SM on this GPU"
-                                     % (sms, "16 SFU" if sfu_bound else "128 FP32", f_mhz),
+                          peak_basis="%d SMs x %.2f %s/clk/SM x %.0f MHz (median SM clock sampled in the "
+                                     "timed region); per-clock rates measured on this GPU by grins_unit_rates"
+                                     % (sms, sfu_rate if sfu_bound else fma_rate,
+                                        "rcp.approx" if sfu_bound else "FFMA", f_mhz),
+                          unit_rates_per_clk_per_sm=rates,
                           work_per_attempt=dict(fp32=w32, sfu=wsfu)),
+            secondary_rooflines=dict(
+                polish=fp64_roof(POLISH_FP64_INSTR_PER_SOLVE * (n_conv + int(hist[4])), kern_ms[3],
+                                 "%.0f FP64 instructions per polished solve x %d solves / the polish kernel's "
+                                 "time" % (POLISH_FP64_INSTR_PER_SOLVE, n_conv + int(hist[4]))),
+                repass=fp64_roof(REPASS_FP64_INSTR_PER_ATTEMPT * a_tail, kern_ms[2],
+                                 "%.0f FP64 instructions per FP64 step attempt x %d attempts / the re-pass "
+                                 "time (ordering + FP64 kernel)" % (REPASS_FP64_INSTR_PER_ATTEMPT, a_tail)),
+                unique=fp64_roof(UNIQUE_FP64_INSTR_PER_SOLVE * n_conv, kern_ms[4],
+                                 "%.0f FP64 instructions per converged solve x %d solves / the dedupe "
+                                 "kernel's time" % (UNIQUE_FP64_INSTR_PER_SOLVE, n_conv)),
+                peak_basis="%d SMs x %.2f DFMA/clk/SM (grins_unit_rates) x %.0f MHz" % (
+                    sms, rates["dfma"], f_mhz)),
             e2e=dict(value=e2e_value, unit="solves/s", h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h),
             # per step: parameter and IC samplers, FP32 integrator, re-pass
             # ordering and FP64 kernels, polish, dedupe
@@ -748,7 +788,11 @@ def run_native(args):
             fp64_gpu_solver=dict(value=fp64_value, unit="solves/s", ms=fp64_ms,
                                  sample="sets 0..%d x %d ICs (the step's sets), FP64 Dormand-Prince 5(4) on the "
                                         "GPU, same tolerances, no polish" % (f64_sets - 1, I),
-                                 ratio=value / fp64_value),
+                                 ratio=value / fp64_value, step_attempts_per_solve=a64 / (f64_sets * I),
+                                 roofline=fp64_roof(REPASS_FP64_INSTR_PER_ATTEMPT * a64, fp64_ms,
+                                                    "%.0f FP64 instructions per step attempt (the same FP64 "
+                                                    "kernel body as the re-pass) x %d attempts / its time"
+                                                    % (REPASS_FP64_INSTR_PER_ATTEMPT, a64))),
             clocks=clocks)
         if levels is not None:
             line["levels"] = levels

@@ -266,6 +266,21 @@ const char *grins_last_error(void);
  * allocated (compare the count before and after it).  Thread-safe. */
 int64_t grins_device_allocations(void);
 
+/* Measured issue rates of the arithmetic units that bound this library's
+ * kernels on the current device, in operations per clock per SM (host array
+ * of five doubles): rates[0] ex2.approx.f32, rates[1] lg2.approx.f32,
+ * rates[2] rcp.approx.f32 (the special-function unit: the FP32
+ * integrator's edge powers, node logarithms and divisions of Eq. 2),
+ * rates[3] FP32 fused multiply-add, rates[4] FP64 fused multiply-add (the
+ * polish, the dedupe and the FP64 re-pass).  These are the denominators of
+ * the kernels' rooflines.  One block of 1024 threads per SM runs eight
+ * independent chains of each operation for a fixed count and reads the SM
+ * clock around the loop; a rate is the median over blocks, so it does not
+ * depend on the clock frequency.  Takes a few milliseconds; allocates two
+ * small device buffers (freed before returning) and synchronises `stream`.
+ * Errors: GRINS_E_INVALID_ARG (rates NULL), GRINS_E_NOMEM, GRINS_E_CUDA. */
+grins_status grins_unit_rates(double *rates, void *stream);
+
 /* Library version string. */
 const char *grins_version(void);
 

@@ -108,6 +108,7 @@ _sig = {
     "grins_last_error": (C.c_char_p, []),
     "grins_version": (C.c_char_p, []),
     "grins_device_allocations": (C.c_int64, []),
+    "grins_unit_rates": (_S, [C.POINTER(C.c_double), _P]),
     "grins_racipe_create": (_S, [C.c_int32, C.c_int32, _P, _P, _P, C.POINTER(_H)]),
     "grins_racipe_destroy": (_S, [_H]),
     "grins_racipe_param_stride": (C.c_int64, [_H]),
@@ -165,6 +166,18 @@ def device_allocations() -> int:
 def _check(st):
     if st != GRINS_OK:
         raise GrinsError(st, _lib.grins_last_error().decode())
+
+
+UNIT_RATE_NAMES = ("ex2", "lg2", "rcp", "ffma", "dfma")
+
+
+def unit_rates(stream=None) -> dict:
+    """grins_unit_rates: measured issue rates (operations per clock per SM) of
+    ex2.approx, lg2.approx, rcp.approx, FP32 FMA and FP64 FMA on the current
+    device, keyed by those names."""
+    r = (C.c_double * 5)()
+    _check(_lib.grins_unit_rates(r, _stream(stream)))
+    return dict(zip(UNIT_RATE_NAMES, (float(x) for x in r)))
 
 
 def default_ranges(sobol_table=None, param_ranges=None, ic_ranges=None, **over) -> grins_racipe_ranges:

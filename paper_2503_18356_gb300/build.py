@@ -20,7 +20,7 @@ LIB = os.path.join(HERE, "libgrins_racipe.so")
 
 SOURCES = ["api.cu", "sample.cu", "integrate_generic.cu", "integrate_grp2.cu", "integrate_grp4.cu",
            "integrate_grp6.cu", "integrate_grp8.cu", "integrate_grp12.cu", "polish.cu", "unique.cu",
-           "jit.cu", "integrate_batch.cu", "levels.cu", "ising.cu", "tail.cu"]
+           "jit.cu", "integrate_batch.cu", "levels.cu", "ising.cu", "tail.cu", "rates.cu"]
 
 # Sources the run-time compile of the lane-group kernel needs (jit.cu embeds
 # them as string literals): (include name, path).

@@ -1410,6 +1410,30 @@ extern "C" grins_status grins_racipe_tail_stats(grins_racipe_t h, void *stream, 
     return GRINS_OK;
 }
 
+// ------------------------------------------------------------------ rates
+extern "C" grins_status grins_unit_rates(double *rates, void *stream)
+{
+    g_last_error.clear();
+    if (!rates) return fail(GRINS_E_INVALID_ARG, "unit_rates: NULL argument");
+    int dev = 0, n_sm = 0;
+    CUDA_TRY(cudaGetDevice(&dev), "unit_rates: device");
+    CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev), "unit_rates: SM count");
+    long long *d_cycles = nullptr;
+    double *d_sink = nullptr;
+    cudaError_t e = dev_malloc(&d_cycles, sizeof(long long) * n_sm);
+    if (e == cudaSuccess) e = dev_malloc(&d_sink, sizeof(double) * n_sm);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_cycles, 0, sizeof(long long) * n_sm, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = grins::measure_unit_rates(rates, (cudaStream_t)stream, d_cycles, d_sink, n_sm);
+    const cudaError_t s = cudaStreamSynchronize((cudaStream_t)stream);
+    cudaFree(d_cycles);
+    cudaFree(d_sink);
+    if (e == cudaSuccess) e = s;
+    if (e != cudaSuccess)
+        return fail(e == cudaErrorMemoryAllocation ? GRINS_E_NOMEM : GRINS_E_CUDA, "unit_rates: %s",
+                    cudaGetErrorString(e));
+    return GRINS_OK;
+}
+
 // ------------------------------------------------------------------ unique
 extern "C" grins_status grins_racipe_unique_states(grins_racipe_t h, const void *d_params,
                                                    const double *d_states, const uint8_t *d_status,
