@@ -47,6 +47,12 @@ INTEGRATOR_DRAM_BYTES_PER_SOLVE = 36.51e6 / 200_000
 POLISH_FP64_INSTR_PER_SOLVE = (37_244_518 + 142_762_810 + 128_571_916) / 127_247
 REPASS_FP64_INSTR_PER_ATTEMPT = (253_617_128 + 766_275_305 + 786_803_446) / 254_532
 UNIQUE_FP64_INSTR_PER_SOLVE = (2_580_512 + 5_598_692 + 19_595_422) / 127_243
+# Executed warp instructions of the double-float re-pass kernel per solve
+# step attempt, from an ncu capture of the same 20,000-set launch
+# (620,488,072 warp instructions for 254,533 attempts,
+# profiles/fp64_kernels_rand22x82_20k.md); None while no capture of the
+# current kernel exists.
+REPASS_DD_WARP_INSTR_PER_ATTEMPT = 620_488_072 / 254_533
 
 
 def parse():
@@ -673,6 +679,20 @@ def run_native(args):
     hist = np.bincount(status.ravel(), minlength=5)
     n_conv = int(hist[0])
 
+    def issue_roof(att, ms):
+        # the double-float re-pass runs FP32 instructions: executed warp
+        # instructions (ncu count per attempt) against one per clock per
+        # scheduler, 4 per SM
+        ipk = REPASS_DD_WARP_INSTR_PER_ATTEMPT
+        peak_i = 4 * sms * f_mhz * 1e6 / 1e9
+        if ipk is None or ms <= 0:
+            return dict(bound="issue", achieved=None, peak=peak_i, unit="G warp instr/s", frac=None,
+                        basis="no ncu count of the current double-float kernel")
+        ach = ipk * att / (ms / 1e3) / 1e9
+        return dict(bound="issue", achieved=ach, peak=peak_i, unit="G warp instr/s", frac=ach / peak_i,
+                    basis="%.0f warp instructions per step attempt x %d attempts / the re-pass time (ordering + "
+                          "double-float kernel); peak 4 warp instructions per clock per SM" % (ipk, att))
+
     def fp64_roof(instr, ms, what):
         ach = instr / (ms / 1e3) / 1e9 if ms > 0 else 0.0
         return dict(bound="fp64", achieved=ach, peak=fp64_peak, unit="G FP64 instr/s", frac=ach / fp64_peak,
@@ -752,12 +772,13 @@ def run_native(args):
                         l2="inputs larger than L2: parameter block %.0f MB, states %.0f MB" % (
                             S * h.param_stride / 1e6, S * I * N * 8 / 1e6),
                         parallelism="dp%d (sets sharded by rank)" % ws),
-            kernel_ms=dict(sample=kern_ms[0], integrate_fp32=kern_ms[1], repass_fp64=kern_ms[2],
+            kernel_ms=dict(sample=kern_ms[0], integrate_fp32=kern_ms[1], repass=kern_ms[2],
                            polish_fp64=kern_ms[3], unique=kern_ms[4]),
             step_attempts_per_solve=attempts / (S * I),
-            repass=dict(solves=n_tail, share=n_tail / (S * I), fp64_attempts=a_tail, ms=kern_ms[2],
-                        what="solves whose steady-state decision fell near t_end, re-integrated in FP64 at rtol "
-                             "%g from their first state with residual below %g ss_tol (ordering kernel + FP64 "
+            repass=dict(solves=n_tail, share=n_tail / (S * I), attempts=a_tail, ms=kern_ms[2],
+                        precision="FP64" if opts.tail_precision == api.GRINS_TAIL_FP64 else "double-float",
+                        what="solves whose steady-state decision fell near t_end, re-integrated at rtol %g from "
+                             "their first state with residual below %g ss_tol (ordering kernel + re-pass "
                              "kernel)" % (opts.tail_rtol, opts.tail_start)),
             status_hist=hist.tolist(),
             roofline=dict(bound="alu", achieved=achieved, peak=peak, unit=unit, frac=achieved / peak,
@@ -773,9 +794,10 @@ def run_native(args):
                 polish=fp64_roof(POLISH_FP64_INSTR_PER_SOLVE * (n_conv + int(hist[4])), kern_ms[3],
                                  "%.0f FP64 instructions per polished solve x %d solves / the polish kernel's "
                                  "time" % (POLISH_FP64_INSTR_PER_SOLVE, n_conv + int(hist[4]))),
-                repass=fp64_roof(REPASS_FP64_INSTR_PER_ATTEMPT * a_tail, kern_ms[2],
-                                 "%.0f FP64 instructions per FP64 step attempt x %d attempts / the re-pass "
-                                 "time (ordering + FP64 kernel)" % (REPASS_FP64_INSTR_PER_ATTEMPT, a_tail)),
+                repass=(fp64_roof(REPASS_FP64_INSTR_PER_ATTEMPT * a_tail, kern_ms[2],
+                                  "%.0f FP64 instructions per FP64 step attempt x %d attempts / the re-pass "
+                                  "time (ordering + FP64 kernel)" % (REPASS_FP64_INSTR_PER_ATTEMPT, a_tail))
+                        if opts.tail_precision == api.GRINS_TAIL_FP64 else issue_roof(a_tail, kern_ms[2])),
                 unique=fp64_roof(UNIQUE_FP64_INSTR_PER_SOLVE * n_conv, kern_ms[4],
                                  "%.0f FP64 instructions per converged solve x %d solves / the dedupe "
                                  "kernel's time" % (UNIQUE_FP64_INSTR_PER_SOLVE, n_conv)),

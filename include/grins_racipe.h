@@ -74,6 +74,7 @@ typedef enum {
 } grins_solve_status;
 
 enum { GRINS_FP64 = 0, GRINS_FP32 = 1 };                       /* precision */
+enum { GRINS_TAIL_DD = 0, GRINS_TAIL_FP64 = 1 };                 /* tail_precision */
 enum { GRINS_METHOD_DOPRI5 = 0, GRINS_METHOD_TSIT5 = 1 };        /* 5(4) pair */
 enum { GRINS_MEDIAN_PER_INDEGREE = 0, GRINS_MEDIAN_UNREGULATED = 1 };
 /* Distribution of a continuous parameter class over its [min, max] range
@@ -182,7 +183,8 @@ enum { GRINS_SOBOL_OFF = 0, GRINS_SOBOL_PLAIN = 1, GRINS_SOBOL_SCRAMBLED = 2 };
  * FP32 + polish, rtol 1e-6, atol 1e-9, t0 0, t_end 200, ss_tol 1e-6,
  * max_steps 100000, no time grid, polish_tol 1e-13, polish_iters 16,
  * polish_max_move 1e-2, ss_tighten 0.3, method GRINS_METHOD_DOPRI5,
- * tail_rtol 1e-9, tail_start 20, tail_rho 10, tail_late 0.2, tail_work 96. */
+ * tail_rtol 1e-9, tail_start 20, tail_rho 10, tail_late 0.2, tail_work 96,
+ * tail_precision GRINS_TAIL_DD. */
 typedef struct {
     int32_t precision;         /* GRINS_FP32 or GRINS_FP64 integration */
     int32_t polish;            /* 1: FP64 Newton polish of each converged state */
@@ -225,19 +227,24 @@ typedef struct {
      *     checkpoint's time (the crossing could move past t_end),
      * and that took at most tail_work attempts after its checkpoint (longer
      * stretches -- slow oscillations that hover near ss_tol -- would hold
-     * the FP64 pass for many times the rest of its work and keep their FP32
-     * result), is integrated again in FP64 from its checkpoint to t_end at rtol
+     * the re-pass for many times the rest of its work and keep their FP32
+     * result), is integrated again from its checkpoint to t_end at rtol
      * tail_rtol (atol scaled by tail_rtol / rtol), no tightening, which sets
      * its state, status and t_final; d_n_steps counts the attempts of both
-     * passes, and grins_racipe_tail_stats reports the re-pass's share.  Runs when the
-     * kernels compiled for the network are available (FP32 and FP64 register
-     * records) and there is no time grid; otherwise the call proceeds without
-     * it.  Plans, the server and grins_racipe_integrate_static do not run it. */
+     * passes, and grins_racipe_tail_stats reports the re-pass's share.  The
+     * re-pass computes in tail_precision: GRINS_TAIL_DD (default)
+     * double-float -- each value a pair of FP32 numbers, about 48 significant
+     * bits, which this GPU runs several times faster than FP64 -- or
+     * GRINS_TAIL_FP64.  Runs when the kernels compiled for the network are
+     * available (FP32 and re-pass register records) and there is no time
+     * grid; otherwise the call proceeds without it.  Plans, the server and
+     * grins_racipe_integrate_static do not run it. */
     double tail_rtol;
     double tail_start;
     double tail_rho;
     double tail_late;
     int32_t tail_work;
+    int32_t tail_precision;    /* GRINS_TAIL_DD or GRINS_TAIL_FP64 */
     void *pass_event;          /* profiling hook, NULL = none: a cudaEvent_t that
                                   grins_racipe_integrate records on its stream after
                                   the integration pass and before the re-pass and the

@@ -31,6 +31,7 @@ GRINS_OK, GRINS_E_INVALID_ARG, GRINS_E_TOPOLOGY, GRINS_E_NOMEM, GRINS_E_CUDA, GR
     GRINS_E_CANCELLED = range(7)
 CONVERGED, TEND, MAXSTEPS, NONFINITE, POLISH_FAIL, CANCELLED = range(6)
 GRINS_FP64, GRINS_FP32 = 0, 1
+GRINS_TAIL_DD, GRINS_TAIL_FP64 = 0, 1
 GRINS_METHOD_DOPRI5, GRINS_METHOD_TSIT5 = 0, 1
 GRINS_ISING_SYNC, GRINS_ISING_ASYNC = 0, 1
 GRINS_DIST_TABLE1, GRINS_DIST_LOGUNIFORM, GRINS_DIST_NORMAL, GRINS_DIST_LOGNORMAL = 0, 1, 2, 3
@@ -74,7 +75,8 @@ class grins_solver_opts(C.Structure):
                 ("polish_tol", C.c_double), ("polish_iters", C.c_int32),
                 ("polish_max_move", C.c_double), ("ss_tighten", C.c_double), ("method", C.c_int32),
                 ("tail_rtol", C.c_double), ("tail_start", C.c_double), ("tail_rho", C.c_double),
-                ("tail_late", C.c_double), ("tail_work", C.c_int32), ("pass_event", C.c_void_p),
+                ("tail_late", C.c_double), ("tail_work", C.c_int32), ("tail_precision", C.c_int32),
+                ("pass_event", C.c_void_p),
                 ("cancel", C.c_void_p)]
 
 

@@ -27,6 +27,7 @@ SOURCES = ["api.cu", "sample.cu", "integrate_generic.cu", "integrate_grp2.cu", "
 JIT_SOURCES = [("grins_racipe.h", os.path.join(INCLUDE, "grins_racipe.h")),
                ("common.cuh", os.path.join(CSRC, "common.cuh")),
                ("integrate.cuh", os.path.join(CSRC, "integrate.cuh")),
+               ("dd.cuh", os.path.join(CSRC, "dd.cuh")),
                ("integrate_grp.cuh", os.path.join(CSRC, "integrate_grp.cuh")),
                ("integrate_rr.cuh", os.path.join(CSRC, "integrate_rr.cuh")),
                ("integrate_rr_layout.inc", os.path.join(CSRC, "integrate_rr_layout.inc")),

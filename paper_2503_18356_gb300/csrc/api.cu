@@ -208,6 +208,7 @@ extern "C" void grins_solver_default_opts(grins_solver_opts *o)
     o->tail_rho = 10.0;
     o->tail_late = 0.2;
     o->tail_work = 96;
+    o->tail_precision = GRINS_TAIL_DD;
     o->pass_event = nullptr;
 }
 
@@ -1130,7 +1131,7 @@ static const void *lookup_either(const GrpTopo &g, int kind, int variant)
 }
 
 static void pick_fp64_kernel(const grins_racipe *h, IntegrateArgs *a, bool compile, std::string *why,
-                             bool tail = false)
+                             bool tail = false, int kind = kJitRegisters64)
 {
     a->grp = h->grp.topo();
     a->grp_jit = nullptr;
@@ -1140,8 +1141,7 @@ static void pick_fp64_kernel(const grins_racipe *h, IntegrateArgs *a, bool compi
         const int variant = a->method | (a->n_t > 0 ? kJitSeries : 0) | (tail ? kJitTail : 0) |
                             (a->cancel ? kJitCancel : 0);
         // a lookup also takes the re-pass variant, which runs the same without a list
-        const void *k = compile ? grp_jit_kernel(g, kJitRegisters64, &w, variant)
-                                : lookup_either(g, kJitRegisters64, variant);
+        const void *k = compile ? grp_jit_kernel(g, kind, &w, variant) : lookup_either(g, kind, variant);
         if (k) { a->grp = g; a->grp_jit = k; }
     }
     if (why) *why = w;
@@ -1218,6 +1218,7 @@ static bool tail_opts_ok(const grins_solver_opts *o)
 {
     if (!(o->tail_rtol >= 0) || !std::isfinite(o->tail_rtol)) return false;
     if (o->tail_rtol == 0) return true;
+    if (o->tail_precision != GRINS_TAIL_DD && o->tail_precision != GRINS_TAIL_FP64) return false;
     return o->tail_start >= 1 && std::isfinite(o->tail_start) && o->tail_rho >= 0 && std::isfinite(o->tail_rho) &&
            o->tail_late >= 0 && std::isfinite(o->tail_late) && o->tail_work >= 0;
 }
@@ -1318,8 +1319,9 @@ extern "C" grins_status grins_racipe_integrate(grins_racipe_t h, const grins_sol
         else {
             a64 = a;
             std::string w64;
-            pick_fp64_kernel(h, &a64, true, &w64, true);
-            if (!a64.grp_jit) h->tail_why = "not run (no FP64 kernel compiled for the network: " + w64 + ")";
+            pick_fp64_kernel(h, &a64, true, &w64, true,
+                             o->tail_precision == GRINS_TAIL_FP64 ? kJitRegisters64 : kJitRegistersDD);
+            if (!a64.grp_jit) h->tail_why = "not run (no re-pass kernel compiled for the network: " + w64 + ")";
             else tail = true;
         }
         if (tail) {
@@ -1353,8 +1355,9 @@ extern "C" grins_status grins_racipe_integrate(grins_racipe_t h, const grins_sol
             a64.f_ss_near = 0.0f; a64.f_ss_gain = 1.0f;
             h->tail_ran = true;
             char buf[160];
-            std::snprintf(buf, sizeof(buf), "FP64 (kernel compiled for the network) from the checkpoint below %g "
-                          "ss_tol at rtol %g", o->tail_start, o->tail_rtol);
+            std::snprintf(buf, sizeof(buf), "%s (kernel compiled for the network) from the checkpoint below %g "
+                          "ss_tol at rtol %g", o->tail_precision == GRINS_TAIL_FP64 ? "FP64" : "double-float",
+                          o->tail_start, o->tail_rtol);
             h->tail_why = buf;
         }
     } else {

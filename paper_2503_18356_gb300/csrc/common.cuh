@@ -173,7 +173,9 @@ struct PlanArgs {
 // first use (grp_jit_kernel) or only looked up (grp_jit_lookup); kind is
 // kJitRegisters (records in registers) or kJitShared (records in shared
 // memory).  The returned pointer is an opaque handle for launch_grp_jit.
-enum JitKind { kJitShared = 0, kJitRegisters = 1, kJitRegisters64 = 2 };
+// kJitRegisters64 / kJitRegistersDD: records in registers in FP64 or in
+// double-float (dd.cuh: the borderline re-pass).
+enum JitKind { kJitShared = 0, kJitRegisters = 1, kJitRegisters64 = 2, kJitRegistersDD = 3 };
 // method: the 5(4) pair of a register-record kernel (0 Dormand-Prince,
 // 1 Tsitouras) in its low bits, plus kJitSeries for a kernel that writes
 // time series (register-record kernels without it compile the grid logic

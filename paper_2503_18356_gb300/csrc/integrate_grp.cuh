@@ -43,6 +43,7 @@
 #pragma once
 
 #include "integrate.cuh"
+#include "dd.cuh"
 
 // Minimum resident blocks per SM the register allocation targets (4 warps
 // per block; 3 -> at most 168 registers per thread).

@@ -234,7 +234,7 @@ std::string jit_main(const GrpTopo &g, int kind, int minb, int warps, int method
     }
     s += "#include \"common.cuh\"\nnamespace grins {\n";
     s += layout_prelude(g, kind != kJitShared);
-    if (kind == kJitRegisters || kind == kJitRegisters64) {
+    if (kind != kJitShared) {
         s += "}\n#include \"integrate_rr.cuh\"\n";
         char bounds[64];
         if (const int mr = jit_maxnreg(kind)) std::snprintf(bounds, sizeof(bounds), "__maxnreg__(%d)", mr);
@@ -242,7 +242,9 @@ std::string jit_main(const GrpTopo &g, int kind, int minb, int warps, int method
         std::snprintf(buf, sizeof(buf),
                       "extern \"C\" __global__ void %s grins_grp_ct(const grins::IntegrateArgs a)\n"
                       "{\n    grins::rr_body<%d, %d, %d, %s, %d, %s, %s, %s>(a);\n}\n",
-                      bounds, g.R, warps, g.L, kind == kJitRegisters64 ? "double" : "float", method & kJitMethodMask,
+                      bounds, g.R, warps, g.L,
+                      kind == kJitRegisters64 ? "double" : (kind == kJitRegistersDD ? "grins::dd" : "float"),
+                      method & kJitMethodMask,
                       (method & kJitSeries) ? "true" : "false", (method & kJitTail) ? "true" : "false",
                       (method & kJitCancel) ? "true" : "false");
     } else {
@@ -320,7 +322,7 @@ int jit_minb(const GrpTopo &g, int kind)
 {
     const int est = 4 * g.P + 11 * g.R + 40;
     int minb = kind == kJitRegisters ? (est <= 144 ? 4 : (est <= 176 ? 3 : 2)) : GRINS_GRP_MINB;
-    if (kind == kJitRegisters64) {          // 2 registers per value, 5 per position
+    if (kind == kJitRegisters64 || kind == kJitRegistersDD) {   // 2 registers per value, 5 per position
         const int est64 = 5 * g.P + 22 * g.R + 60;
         minb = est64 <= 128 ? 4 : (est64 <= 168 ? 3 : 2);
     }
@@ -419,8 +421,10 @@ const void *grp_jit_kernel(const GrpTopo &g, int kind, std::string *why, int met
     std::shared_ptr<JitEntry> e = jit_get(g, kind, kCompileHere, method);
     if (e->state.load() != 1) { if (why) *why = e->why; return nullptr; }
     if (why)
-        *why = e->kind == kJitRegisters64 ? "FP64, records in registers"
-                                          : (e->kind == kJitRegisters ? "records in registers" : "records in shared memory");
+        *why = e->kind == kJitRegisters64   ? "FP64, records in registers"
+               : e->kind == kJitRegistersDD ? "double-float, records in registers"
+               : e->kind == kJitRegisters   ? "records in registers"
+                                            : "records in shared memory";
     return e.get();
 }
 
@@ -723,7 +727,7 @@ cudaError_t launch_grp_jit(const void *handle, const IntegrateArgs &a, cudaStrea
     IntegrateArgs b = a;
     const int W = je->warps;
     int smem = 0;
-    if (je->kind == kJitRegisters || je->kind == kJitRegisters64) {
+    if (je->kind != kJitShared) {
         smem = je->kind == kJitRegisters ? W * rr_warp_bytes(b.grp.R, 1, 4) : W * rr_warp_bytes(b.grp.R, 6, 8);
     } else {
         const int ndom = grp_domains(b.grp.L);

@@ -9,14 +9,16 @@
 // Method: one block of 1024 threads per SM (its dynamic shared memory
 // request leaves no room for a second), each thread running independent
 // chains of the operation under test for a fixed count (8 chains; 16 for the
-// FP64 FMA, whose latency is long); the block reads the SM clock (clock64)
+// FMAs: the FP64 FMA's latency is long, and the compiler issues pairs of
+// independent FP32 FMAs as one packed f32x2 instruction, so the FP32 rate
+// counts lane operations of packed code); the block reads the SM clock (clock64)
 // after a barrier before and after the loop.  A block's rate = its threads x
 // chains x iterations / its clock delta; the probe reports the median over
 // blocks.  Each chain step is one operation of the kind under test plus, for
 // the special functions, at most one FP32 add that keeps the chain's values
 // finite (the add goes to the FMA pipe, which has eight times the
 // special-function unit's throughput, so it does not bound the loop).  The
-// FP32 FMA loop is unrolled eightfold so that the loop counter and branch
+// FP32 FMA loop is unrolled fourfold so that the loop counter and branch
 // (3 instructions per pass) take under 5 % of the issue slots.
 #include <algorithm>
 #include <vector>
@@ -30,8 +32,8 @@ constexpr int kRateThreads = 1024;
 constexpr int kRateIters = 2048;
 
 template <int OP> struct RateShape {
-    static constexpr int chains = OP == 4 ? 16 : 8;
-    static constexpr int unroll = OP == 3 ? 8 : 1;
+    static constexpr int chains = OP >= 3 ? 16 : 8;
+    static constexpr int unroll = OP == 3 ? 4 : 1;
 };
 
 __device__ __forceinline__ float mufu_ex2(float x)
