@@ -505,7 +505,12 @@ grins_status grins_racipe_server_create(const grins_server_config *c, grins_raci
  * = defaults) with n_ics ICs on network `net`, integrated with o (no time
  * grid) and deduplicated with dedupe_tol.  Returns at once with its id; the
  * tables r points to (Sobol, per-parameter and initial-condition rows) are
- * copied, so the caller may free them on return.
+ * copied, so the caller may free them on return.  The half-functional
+ * medians of in-degree classes not yet computed in the process (host work,
+ * tens of milliseconds per class) are computed by the server's preparation
+ * thread, the classes of one network in parallel; the request waits in the
+ * queue for them (later requests are not held back).  A per-parameter
+ * table's medians are computed in the calling thread.
  * Errors: GRINS_E_INVALID_ARG for bad arguments, GRINS_E_BUDGET when the
  * request alone needs more than the whole HBM budget. */
 grins_status grins_racipe_server_submit(grins_racipe_server_t sv, grins_racipe_t net,

@@ -99,12 +99,9 @@ extern "C" int64_t grins_device_allocations(void)
 struct GrpDev {
     int L = 0, R = 0, P = 0;
     std::vector<int32_t> row_off, row_deg, link_to;
+    // device arrays: parts of the handle's workspace block (grins_racipe::d_block)
     int32_t *d_pos_edge = nullptr, *d_pos_off = nullptr, *d_row_node = nullptr, *d_row_link = nullptr;
-    void free_device()
-    {
-        cudaFree(d_pos_edge); cudaFree(d_pos_off); cudaFree(d_row_node); cudaFree(d_row_link);
-        d_pos_edge = d_pos_off = d_row_node = d_row_link = nullptr;
-    }
+    void free_device() { d_pos_edge = d_pos_off = d_row_node = d_row_link = nullptr; }
     GrpTopo topo() const
     {
         GrpTopo g{};
@@ -128,7 +125,9 @@ struct grins_racipe {
     std::vector<int8_t> csr_sign;
     std::vector<int32_t> n_act_in, n_inh_in;          // in-degree class per node
     ParamLayout layout{};
-    // device workspace
+    // device workspace: the topology, the layouts' tables, the median and
+    // counter arrays are parts of one allocation (d_block), filled by one copy
+    unsigned char *d_block = nullptr;
     int32_t *d_off = nullptr, *d_src = nullptr, *d_edge = nullptr;
     int8_t *d_sign = nullptr, *d_edge_sign = nullptr;
     double *d_edge_median = nullptr;
@@ -217,9 +216,8 @@ extern "C" const char *grins_version(void) { return "grins_racipe 0.1 (sm_103a)"
 
 static void free_device(grins_racipe *h)
 {
-    cudaFree(h->d_off); cudaFree(h->d_src); cudaFree(h->d_edge); cudaFree(h->d_sign);
-    cudaFree(h->d_edge_sign); cudaFree(h->d_edge_median); cudaFree(h->d_queue); cudaFree(h->d_grid);
-    cudaFree(h->d_tail);
+    cudaFree(h->d_block); cudaFree(h->d_grid); cudaFree(h->d_tail);
+    h->d_block = nullptr;
     h->d_tail = nullptr;
     h->tail_cap = 0;
     h->grp.free_device();
@@ -469,26 +467,45 @@ static GrpHost choose_grp_registers(int N, const std::vector<int32_t> &off, cons
     return GrpHost{};
 }
 
-// Copies layout g to the device into d.
-static cudaError_t upload_grp(const GrpHost &g, GrpDev &d)
+// Host staging of the handle's device block: parts placed at 256-byte
+// aligned offsets, copied to the device in one transfer.
+struct BlockStage {
+    std::vector<unsigned char> host;
+    // reserves `bytes` (zero-filled) and copies `src` (may be null) into it
+    size_t add(const void *src, size_t bytes)
+    {
+        const size_t o = host.size();
+        host.resize((o + std::max<size_t>(bytes, 1) + 255) & ~(size_t)255, 0);
+        if (src && bytes) std::memcpy(host.data() + o, src, bytes);
+        return o;
+    }
+};
+
+// Layout g's tables into the staging block; d keeps the host row table and
+// the offsets, turned into device pointers by place_grp.
+struct GrpOffsets { size_t pos_edge = 0, pos_off = 0, row_node = 0, row_link = 0; };
+
+static GrpOffsets stage_grp(const GrpHost &g, GrpDev &d, BlockStage &b)
 {
     d.L = g.L; d.R = g.R; d.P = g.P;
     d.row_off = g.row_off; d.row_deg = g.row_deg; d.link_to = g.link_to;
-    if (g.L <= 0) return cudaSuccess;
+    GrpOffsets o;
+    if (g.L <= 0) return o;
     const size_t np = std::max<size_t>(g.pos_edge.size(), 1), nr = g.row_node.size();
-    cudaError_t ce = dev_malloc(&d.d_pos_edge, sizeof(int32_t) * np);
-    if (ce == cudaSuccess) ce = dev_malloc(&d.d_pos_off, sizeof(int32_t) * np);
-    if (ce == cudaSuccess) ce = dev_malloc(&d.d_row_node, sizeof(int32_t) * nr);
-    if (ce == cudaSuccess && !g.pos_edge.empty())
-        ce = cudaMemcpy(d.d_pos_edge, g.pos_edge.data(), sizeof(int32_t) * g.pos_edge.size(), cudaMemcpyHostToDevice);
-    if (ce == cudaSuccess && !g.pos_off.empty())
-        ce = cudaMemcpy(d.d_pos_off, g.pos_off.data(), sizeof(int32_t) * g.pos_off.size(), cudaMemcpyHostToDevice);
-    if (ce == cudaSuccess)
-        ce = cudaMemcpy(d.d_row_node, g.row_node.data(), sizeof(int32_t) * nr, cudaMemcpyHostToDevice);
-    if (ce == cudaSuccess) ce = dev_malloc(&d.d_row_link, sizeof(int32_t) * nr);
-    if (ce == cudaSuccess)
-        ce = cudaMemcpy(d.d_row_link, g.row_link.data(), sizeof(int32_t) * nr, cudaMemcpyHostToDevice);
-    return ce;
+    o.pos_edge = b.add(g.pos_edge.empty() ? nullptr : g.pos_edge.data(), sizeof(int32_t) * np);
+    o.pos_off = b.add(g.pos_off.empty() ? nullptr : g.pos_off.data(), sizeof(int32_t) * np);
+    o.row_node = b.add(g.row_node.data(), sizeof(int32_t) * nr);
+    o.row_link = b.add(g.row_link.data(), sizeof(int32_t) * nr);
+    return o;
+}
+
+static void place_grp(GrpDev &d, const GrpOffsets &o, unsigned char *block)
+{
+    if (d.L <= 0) return;
+    d.d_pos_edge = reinterpret_cast<int32_t *>(block + o.pos_edge);
+    d.d_pos_off = reinterpret_cast<int32_t *>(block + o.pos_off);
+    d.d_row_node = reinterpret_cast<int32_t *>(block + o.row_node);
+    d.d_row_link = reinterpret_cast<int32_t *>(block + o.row_link);
 }
 
 extern "C" grins_status grins_racipe_create(int32_t n_nodes, int32_t n_edges, const int32_t *src,
@@ -545,22 +562,34 @@ extern "C" grins_status grins_racipe_create(int32_t n_nodes, int32_t n_edges, co
     int optin = 0;
     if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
     h->smem_optin = (size_t)optin;
+    // one device allocation and one copy for the whole workspace (each CUDA
+    // call can stall behind other threads' driver work -- module loads of
+    // run-time compiled kernels -- so creation makes as few as it can)
     const size_t Eb = (size_t)std::max(n_edges, 1);
-    if (ce == cudaSuccess) ce = dev_malloc(&h->d_off, sizeof(int32_t) * (n_nodes + 1));
-    if (ce == cudaSuccess) ce = dev_malloc(&h->d_src, sizeof(int32_t) * Eb);
-    if (ce == cudaSuccess) ce = dev_malloc(&h->d_edge, sizeof(int32_t) * Eb);
-    if (ce == cudaSuccess) ce = dev_malloc(&h->d_sign, Eb);
-    if (ce == cudaSuccess) ce = dev_malloc(&h->d_edge_sign, Eb);
-    if (ce == cudaSuccess) ce = dev_malloc(&h->d_edge_median, sizeof(double) * Eb);
-    if (ce == cudaSuccess) ce = dev_malloc(&h->d_queue, sizeof(unsigned long long) * 4);
-    if (ce == cudaSuccess) ce = cudaMemset(h->d_queue, 0, sizeof(unsigned long long) * 4);
-    if (ce == cudaSuccess) ce = cudaMemcpy(h->d_off, h->csr_off.data(), sizeof(int32_t) * (n_nodes + 1), cudaMemcpyHostToDevice);
-    if (ce == cudaSuccess && n_edges) ce = cudaMemcpy(h->d_src, h->csr_src.data(), sizeof(int32_t) * n_edges, cudaMemcpyHostToDevice);
-    if (ce == cudaSuccess && n_edges) ce = cudaMemcpy(h->d_edge, h->csr_edge.data(), sizeof(int32_t) * n_edges, cudaMemcpyHostToDevice);
-    if (ce == cudaSuccess && n_edges) ce = cudaMemcpy(h->d_sign, h->csr_sign.data(), n_edges, cudaMemcpyHostToDevice);
-    if (ce == cudaSuccess && n_edges) ce = cudaMemcpy(h->d_edge_sign, h->sign.data(), n_edges, cudaMemcpyHostToDevice);
-    if (ce == cudaSuccess) ce = upload_grp(grp, h->grp);
-    if (ce == cudaSuccess) ce = upload_grp(grr, h->rr);
+    BlockStage bs;
+    const size_t o_off = bs.add(h->csr_off.data(), sizeof(int32_t) * (n_nodes + 1));
+    const size_t o_src = bs.add(n_edges ? h->csr_src.data() : nullptr, sizeof(int32_t) * Eb);
+    const size_t o_edge = bs.add(n_edges ? h->csr_edge.data() : nullptr, sizeof(int32_t) * Eb);
+    const size_t o_sign = bs.add(n_edges ? h->csr_sign.data() : nullptr, Eb);
+    const size_t o_esign = bs.add(n_edges ? h->sign.data() : nullptr, Eb);
+    const size_t o_median = bs.add(nullptr, sizeof(double) * Eb);
+    const size_t o_queue = bs.add(nullptr, sizeof(unsigned long long) * 4);
+    const GrpOffsets og = stage_grp(grp, h->grp, bs);
+    const GrpOffsets orr = stage_grp(grr, h->rr, bs);
+    if (ce == cudaSuccess) ce = dev_malloc(&h->d_block, bs.host.size());
+    if (ce == cudaSuccess) ce = cudaMemcpy(h->d_block, bs.host.data(), bs.host.size(), cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess) {
+        unsigned char *b = h->d_block;
+        h->d_off = reinterpret_cast<int32_t *>(b + o_off);
+        h->d_src = reinterpret_cast<int32_t *>(b + o_src);
+        h->d_edge = reinterpret_cast<int32_t *>(b + o_edge);
+        h->d_sign = reinterpret_cast<int8_t *>(b + o_sign);
+        h->d_edge_sign = reinterpret_cast<int8_t *>(b + o_esign);
+        h->d_edge_median = reinterpret_cast<double *>(b + o_median);
+        h->d_queue = reinterpret_cast<unsigned long long *>(b + o_queue);
+        place_grp(h->grp, og, b);
+        place_grp(h->rr, orr, b);
+    }
     if (ce != cudaSuccess) {
         free_device(h);
         delete h;
@@ -768,21 +797,81 @@ grins_status check_ranges(const grins_racipe_ranges &r)
 // use a fixed key), so it is computed once per process and shared by every
 // network; (0, 0) is the unregulated level, m0 the median the regulated
 // classes' sources are drawn around.
+// Process-wide cache of class medians, keyed by (na, ni, ranges).
+struct ClassMedianCache {
+    struct Entry { grins_racipe_ranges r; int na, ni; double m; };
+    std::mutex mu;
+    std::vector<Entry> tab;
+    bool find(int na, int ni, const grins_racipe_ranges &r, double *m)
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        for (const Entry &e : tab)
+            if (e.na == na && e.ni == ni && same_ranges(e.r, r)) { *m = e.m; return true; }
+        return false;
+    }
+    void put(int na, int ni, const grins_racipe_ranges &r, double m)
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        for (const Entry &e : tab)
+            if (e.na == na && e.ni == ni && same_ranges(e.r, r)) return;
+        tab.push_back(Entry{r, na, ni, m});
+    }
+};
+
+ClassMedianCache &class_cache()
+{
+    static ClassMedianCache *c = new ClassMedianCache();
+    return *c;
+}
+
 double class_median(int na, int ni, const grins_racipe_ranges &r, double m0)
 {
-    struct Entry { grins_racipe_ranges r; int na, ni; double m; };
-    static std::mutex *mu = new std::mutex();
-    static std::vector<Entry> *tab = new std::vector<Entry>();
-    {
-        std::lock_guard<std::mutex> lock(*mu);
-        for (const Entry &e : *tab)
-            if (e.na == na && e.ni == ni && same_ranges(e.r, r)) return e.m;
-    }
+    double m = 0.0;
+    if (class_cache().find(na, ni, r, &m)) return m;
     std::vector<double> v = level_samples(na, ni, r, m0);
-    const double m = median_sorted(v);
-    std::lock_guard<std::mutex> lock(*mu);
-    tab->push_back(Entry{r, na, ni, m});
+    m = median_sorted(v);
+    class_cache().put(na, ni, r, m);
     return m;
+}
+
+// The in-degree classes (a activating, b inhibiting inputs) of h's regulated
+// nodes whose medians under r are not cached yet (the unregulated class
+// (0, 0) first when it is missing).
+std::vector<std::pair<int, int>> missing_classes(const grins_racipe *h, const grins_racipe_ranges &r)
+{
+    std::vector<std::pair<int, int>> out;
+    double m = 0.0;
+    if (!class_cache().find(0, 0, r, &m)) out.push_back({0, 0});
+    if (r.median_mode != GRINS_MEDIAN_PER_INDEGREE) return out;
+    for (int j = 0; j < h->N; ++j) {
+        const std::pair<int, int> c{h->n_act_in[j], h->n_inh_in[j]};
+        if (c.first == 0 && c.second == 0) continue;
+        if (std::find(out.begin(), out.end(), c) != out.end()) continue;
+        if (!class_cache().find(c.first, c.second, r, &m)) out.push_back(c);
+    }
+    return out;
+}
+
+// Computes the missing class medians of h under r, the regulated classes in
+// parallel (each class's samples come from its own Philox stream, so the
+// result does not depend on the order or the threads).
+void warm_class_medians(const grins_racipe *h, const grins_racipe_ranges &r)
+{
+    std::vector<std::pair<int, int>> miss = missing_classes(h, r);
+    if (miss.empty()) return;
+    const double M0 = class_median(0, 0, r, 0.0);
+    if (miss.front() == std::pair<int, int>{0, 0}) miss.erase(miss.begin());
+    if (miss.empty()) return;
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const size_t T = std::min<size_t>(miss.size(), std::min<unsigned>(8u, std::max(1u, hw / 2)));
+    std::atomic<size_t> next{0};
+    auto work = [&]() {
+        for (size_t i = next++; i < miss.size(); i = next++) class_median(miss[i].first, miss[i].second, r, M0);
+    };
+    std::vector<std::thread> team;
+    for (size_t t = 1; t < T; ++t) team.emplace_back(work);
+    work();
+    for (auto &t : team) t.join();
 }
 
 // Rows of a per-parameter table: the constraints stated with
@@ -880,6 +969,7 @@ grins_status ensure_medians(grins_racipe *h, const grins_racipe_ranges &r)
     }
     if (h->median_valid && h->median_table.empty() && same_ranges(h->median_ranges, r)) return GRINS_OK;
     h->median_table.clear();
+    warm_class_medians(h, r);
     const double M0 = class_median(0, 0, r, 0.0);
     h->node_median.assign(h->N, M0);
     if (r.median_mode == GRINS_MEDIAN_PER_INDEGREE) {
@@ -2174,6 +2264,7 @@ struct ServerRequest {
     int64_t bytes = 0;
     int slot = -1;
     bool jit_wait = false;         // admitted once its compile is done (or jit_max_wait_s passed)
+    bool prep = false;             // admitted once the server's prep thread has its class medians
     bool cancel = false;           // grins_racipe_server_cancel was called while it ran
     GrpTopo jit_topo{};
     int jit_kind = 0;
@@ -2205,6 +2296,11 @@ struct grins_racipe_server {
     std::map<int64_t, std::unique_ptr<ServerRequest>> reqs;
     std::set<grins_racipe *> busy_nets;
     std::thread worker;
+    // host preparation off the submitting thread: the half-functional class
+    // medians a request's network needs and the cache does not hold yet
+    std::thread prep_worker;
+    std::deque<int64_t> prep_q;
+    std::condition_variable prep_cv;
     bool stop = false;
     int64_t next_id = 1;
     std::string fatal;
@@ -2267,8 +2363,7 @@ grins_status server_launch(grins_racipe_server *sv, ServerRequest &r)
     a.slots = slots_for(I);
     a.smem_limit = (int32_t)h->smem_optin;
     a.grp = grp_topo(h);
-    sv->cancel_host[r.slot] = 0;
-    a.cancel = sv->cancel_dev + r.slot;       // the slot's flag, not the submitted options' pointer
+    a.cancel = sv->cancel_dev + r.slot;       // the slot's flag (reset at admission), not the options' pointer
     if (o->precision == GRINS_FP32) pick_fp32_kernel(h, &a, false, nullptr);   // never compiles here
     else pick_fp64_kernel(h, &a, false, nullptr);
     CUDA_TRY(cudaMemsetAsync(r.words, 0, 32, st), "server: counter reset");
@@ -2322,6 +2417,7 @@ void server_loop(grins_racipe_server *sv)
                 if (!sv->slot_busy[i]) slot = i;
             if (slot < 0) break;
             if (sv->busy_nets.count(r.net)) { ++it; continue; }
+            if (r.prep) { ++it; continue; }
             if (r.jit_wait) {
                 if (grp_jit_prefetch(r.jit_topo, r.jit_kind, server_variant(r.jit_kind)) == 0 &&
                     now_s() - r.t_submit < sv->jit_max_wait_s) {
@@ -2337,21 +2433,59 @@ void server_loop(grins_racipe_server *sv)
             sv->used += r.bytes;
             r.t_admit = now_s();
             r.state = GRINS_REQ_RUNNING;
+            sv->cancel_host[slot] = 0;                // a cancel from here on reaches the kernels
+            sv->pending.erase(it);
+            // the launch sequence runs without the lock: a CUDA call can
+            // stall behind other threads' driver work, and submissions,
+            // waits and cancels must not wait for it (a running request
+            // cannot be released, and only this thread admits or completes)
+            lock.unlock();
             cudaSetDevice(r.net->device);
-            const grins_status s = server_launch(sv, r);
+            grins_status s = GRINS_OK;
+            if (cudaEventCreateWithFlags(&r.done, cudaEventDisableTiming) != cudaSuccess)
+                s = fail(GRINS_E_CUDA, "server: completion event");
+            if (s == GRINS_OK) s = server_launch(sv, r);
+            const std::string msg = s != GRINS_OK ? std::string(grins_last_error()) : std::string();
+            lock.lock();
             if (s != GRINS_OK) {
                 r.state = GRINS_REQ_FAILED;
                 r.err = s;
-                r.msg = grins_last_error();
+                r.msg = msg;
                 r.t_done = now_s();
                 sv->slot_busy[slot] = 0;
                 sv->busy_nets.erase(r.net);
                 sv->cv_done.notify_all();
             }
-            it = sv->pending.erase(it);
             progress = true;
+            it = sv->pending.begin();                 // others may have queued meanwhile
         }
         if (!progress) sv->cv.wait_for(lock, std::chrono::microseconds(100));
+    }
+}
+
+// The prep thread: computes the missing class medians of queued requests,
+// one request at a time (the classes of one in parallel), then lets the
+// worker admit it.
+void server_prep_loop(grins_racipe_server *sv)
+{
+    std::unique_lock<std::mutex> lock(sv->mu);
+    while (!sv->stop) {
+        if (sv->prep_q.empty()) {
+            sv->prep_cv.wait(lock);
+            continue;
+        }
+        const int64_t id = sv->prep_q.front();
+        sv->prep_q.pop_front();
+        auto it = sv->reqs.find(id);
+        if (it == sv->reqs.end() || !it->second->prep) continue;
+        grins_racipe *net = it->second->net;
+        const grins_racipe_ranges rr = it->second->ranges;
+        lock.unlock();
+        warm_class_medians(net, rr);
+        lock.lock();
+        auto jt = sv->reqs.find(id);
+        if (jt != sv->reqs.end()) jt->second->prep = false;
+        sv->cv.notify_all();
     }
 }
 
@@ -2422,6 +2556,7 @@ extern "C" grins_status grins_racipe_server_create(const grins_server_config *c,
     }
     grins_racipe_server *raw = sv.release();
     raw->worker = std::thread(server_loop, raw);
+    raw->prep_worker = std::thread(server_prep_loop, raw);
     *out = raw;
     return GRINS_OK;
 }
@@ -2450,9 +2585,14 @@ extern "C" grins_status grins_racipe_server_submit(grins_racipe_server_t sv, gri
     if (r) rr = *r; else grins_racipe_default_ranges(&rr);
     grins_status s = check_ranges(rr);
     if (s != GRINS_OK) return s;
-    // the half-functional median table is host work: do it here, in the
-    // submitting thread, not in the worker
-    {
+    // the half-functional median table is host work.  Class medians the
+    // process-wide cache lacks (tens of milliseconds per class) are computed
+    // by the server's prep thread, and the request waits in the queue for
+    // them; otherwise (all cached, or a per-parameter table, whose rows are
+    // checked here) the table is filled in this thread -- in microseconds
+    // when cached
+    const bool prep = !rr.param_ranges && !missing_classes(net, rr).empty();
+    if (!prep) {
         std::lock_guard<std::mutex> lock(net->median_mu);
         s = ensure_medians(net, rr);
     }
@@ -2495,13 +2635,17 @@ extern "C" grins_status grins_racipe_server_submit(grins_racipe_server_t sv, gri
         }
         req->jit_wait = grp_jit_prefetch(req->jit_topo, req->jit_kind, server_variant(req->jit_kind)) == 0;
     }
-    CUDA_TRY(cudaEventCreateWithFlags(&req->done, cudaEventDisableTiming), "server_submit: event");
     std::lock_guard<std::mutex> lock(sv->mu);
     req->id = sv->next_id++;
     req->t_submit = now_s();
     req->state = GRINS_REQ_QUEUED;
+    req->prep = prep;
     *request_id = req->id;
     sv->pending.push_back(req->id);
+    if (prep) {
+        sv->prep_q.push_back(req->id);
+        sv->prep_cv.notify_one();
+    }
     sv->reqs.emplace(req->id, std::move(req));
     sv->cv.notify_all();
     return GRINS_OK;
@@ -2602,7 +2746,7 @@ extern "C" grins_status grins_racipe_server_release(grins_racipe_server_t sv, in
         cudaFreeAsync(r.mem, sv->streams[r.slot]);
         sv->used -= r.bytes;
     }
-    cudaEventDestroy(r.done);
+    if (r.done) cudaEventDestroy(r.done);
     sv->reqs.erase(it);
     sv->cv.notify_all();
     return GRINS_OK;
@@ -2615,13 +2759,15 @@ extern "C" grins_status grins_racipe_server_destroy(grins_racipe_server_t sv)
         std::lock_guard<std::mutex> lock(sv->mu);
         sv->stop = true;
         sv->cv.notify_all();
+        sv->prep_cv.notify_all();
     }
     sv->worker.join();
+    sv->prep_worker.join();
     cudaSetDevice(sv->device);
     for (auto &st : sv->streams) cudaStreamSynchronize(st);
     for (auto &kv : sv->reqs) {
         if (kv.second->mem) cudaFreeAsync(kv.second->mem, sv->streams[kv.second->slot]);
-        cudaEventDestroy(kv.second->done);
+        if (kv.second->done) cudaEventDestroy(kv.second->done);
     }
     for (auto &st : sv->streams) { cudaStreamSynchronize(st); cudaStreamDestroy(st); }
     cudaMemPoolDestroy(sv->pool);
