@@ -580,18 +580,27 @@ def run_native(args):
     opts.tail_precision = api.GRINS_TAIL_FP64 if args.tail_precision == "fp64" else api.GRINS_TAIL_DD
     popts = api.default_opts()
 
-    def step(ev=None):
+    # the step as a user runs it: one integrate call with the polish, which
+    # runs the polish beside the re-pass
+    opts_p = api.default_opts(precision=api.GRINS_FP32, polish=1, **TOL)
+    opts_p.tail_precision = opts.tail_precision
+
+    def step(ev=None, separate=False):
         # events: 0 start, 1 sampled, 2 FP32 pass done (recorded by the
-        # library between its passes), 3 re-pass done, 4 polished, 5 deduped
+        # library between its passes), 3 integrate done, 4 polished, 5
+        # deduped.  separate: the polish as its own call after the re-pass
+        # (per-kernel times for the secondary rooflines); else 3 = 4
+        o = opts if separate else opts_p
         if ev:
             ev[0].record(stream)
-            opts.pass_event = ev[2].cuda_event
+            o.pass_event = ev[2].cuda_event
         h.sample_params(w["param_seed"], S, I, set0=set0, params=params, ic_unit=ic, stream=stream)
         if ev: ev[1].record(stream)
-        h.integrate(params, ic, opts=opts, stream=stream, out=out)
-        opts.pass_event = None
+        h.integrate(params, ic, opts=o, stream=stream, out=out)
+        o.pass_event = None
         if ev: ev[3].record(stream)
-        h.polish(params, out["states"], out["status"], out["err_est"], opts=popts, stream=stream)
+        if separate:
+            h.polish(params, out["states"], out["status"], out["err_est"], opts=popts, stream=stream)
         if ev: ev[4].record(stream)
         h.unique_states(params, out["states"], out["status"], stream=stream, out=(sid, nu))
         if ev: ev[5].record(stream)
@@ -637,6 +646,13 @@ def run_native(args):
     per_kernel = np.array([[e[i].elapsed_time(e[i + 1]) for i in range(5)] for e in evs])  # ms
     # the last timed step's re-pass (every step integrates the same sets)
     n_tail, a_tail = h.tail_stats(stream)
+    # one more (untimed) step with the polish as its own call: the re-pass
+    # and the polish timed apart
+    sev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+    sev[2].record(stream)
+    step(sev, separate=True)
+    torch.cuda.synchronize()
+    sep_ms = [sev[i].elapsed_time(sev[i + 1]) for i in range(5)]
 
     # the first sets of one more (untimed) step, raw and polished, for the
     # per-result comparison with the oracle
@@ -723,8 +739,7 @@ def run_native(args):
     def e2e_step():
         hh = api.Racipe.from_topology(topo, device=dev)
         hh.sample_params(w["param_seed"], S, I, set0=set0, params=params, ic_unit=ic, stream=stream)
-        hh.integrate(params, ic, opts=opts, stream=stream, out=out)
-        hh.polish(params, out["states"], out["status"], out["err_est"], opts=popts, stream=stream)
+        hh.integrate(params, ic, opts=opts_p, stream=stream, out=out)           # with the polish
         hh.unique_states(params, out["states"], out["status"], stream=stream, out=(sid, nu))
         host["states"].copy_(out["states"], non_blocking=True)
         host["status"].copy_(out["status"], non_blocking=True)
@@ -782,10 +797,13 @@ def run_native(args):
                         l2="inputs larger than L2: parameter block %.0f MB, states %.0f MB" % (
                             S * h.param_stride / 1e6, S * I * N * 8 / 1e6),
                         parallelism="dp%d (sets sharded by rank)" % ws),
-            kernel_ms=dict(sample=kern_ms[0], integrate_fp32=kern_ms[1], repass=kern_ms[2],
-                           polish_fp64=kern_ms[3], unique=kern_ms[4]),
+            kernel_ms=dict(sample=kern_ms[0], integrate_fp32=kern_ms[1], repass_and_polish=kern_ms[2] + kern_ms[3],
+                           unique=kern_ms[4],
+                           apart=dict(repass=sep_ms[2], polish_fp64=sep_ms[3],
+                                      what="one more step with the polish as its own call after the re-pass "
+                                           "(in the timed steps the polish runs beside the re-pass)")),
             step_attempts_per_solve=attempts / (S * I),
-            repass=dict(solves=n_tail, share=n_tail / (S * I), attempts=a_tail, ms=kern_ms[2],
+            repass=dict(solves=n_tail, share=n_tail / (S * I), attempts=a_tail, ms=sep_ms[2],
                         precision="FP64" if opts.tail_precision == api.GRINS_TAIL_FP64 else "double-float",
                         what="solves whose steady-state decision fell near t_end, re-integrated at rtol %g from "
                              "their first state with residual below %g ss_tol (ordering kernel + re-pass "
@@ -801,13 +819,13 @@ def run_native(args):
                           unit_rates_per_clk_per_sm=rates,
                           work_per_attempt=dict(fp32=w32, sfu=wsfu)),
             secondary_rooflines=dict(
-                polish=fp64_roof(POLISH_FP64_INSTR_PER_SOLVE * (n_conv + int(hist[4])), kern_ms[3],
+                polish=fp64_roof(POLISH_FP64_INSTR_PER_SOLVE * (n_conv + int(hist[4])), sep_ms[3],
                                  "%.0f FP64 instructions per polished solve x %d solves / the polish kernel's "
                                  "time" % (POLISH_FP64_INSTR_PER_SOLVE, n_conv + int(hist[4]))),
-                repass=(fp64_roof(REPASS_FP64_INSTR_PER_ATTEMPT * a_tail, kern_ms[2],
+                repass=(fp64_roof(REPASS_FP64_INSTR_PER_ATTEMPT * a_tail, sep_ms[2],
                                   "%.0f FP64 instructions per FP64 step attempt x %d attempts / the re-pass "
                                   "time (ordering + FP64 kernel)" % (REPASS_FP64_INSTR_PER_ATTEMPT, a_tail))
-                        if opts.tail_precision == api.GRINS_TAIL_FP64 else issue_roof(a_tail, kern_ms[2])),
+                        if opts.tail_precision == api.GRINS_TAIL_FP64 else issue_roof(a_tail, sep_ms[2])),
                 unique=fp64_roof(UNIQUE_FP64_INSTR_PER_SOLVE * n_conv, kern_ms[4],
                                  "%.0f FP64 instructions per converged solve x %d solves / the dedupe "
                                  "kernel's time" % (UNIQUE_FP64_INSTR_PER_SOLVE, n_conv)),
@@ -818,9 +836,10 @@ def run_native(args):
                      note="steady state: each timed step creates its handle, but the process-wide caches "
                           "(compiled kernels, median table) are warm; first_step_s is the first step of the "
                           "process, with the median table and the run-time compiles"),
-            # per step: parameter and IC samplers, FP32 integrator, re-pass
-            # ordering and FP64 kernels, polish, dedupe
-            gpu_launches=(7 if n_tail >= 0 and opts.tail_rtol > 0 else 5) * args.steps,
+            # per step: parameter and IC samplers, FP32 pass, re-pass ordering
+            # and kernel, the polish beside it and the list-mode polish after
+            # it, dedupe
+            gpu_launches=(8 if opts.tail_rtol > 0 else 5) * args.steps,
             fp64_gpu_solver=dict(value=fp64_value, unit="solves/s", ms=fp64_ms,
                                  sample="sets 0..%d x %d ICs (the step's sets), FP64 Dormand-Prince 5(4) on the "
                                         "GPU, same tolerances, no polish" % (f64_sets - 1, I),

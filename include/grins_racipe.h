@@ -361,6 +361,12 @@ grins_status grins_racipe_sample_params(grins_racipe_t h, const grins_racipe_ran
  *   d_series  double [n_sets][n_ics][n_t][N] states at o->t_grid (required
  *                                        iff n_t > 0); grid times after
  *                                        termination hold the final state
+ * When the borderline re-pass runs (FP32, o->tail_rtol > 0) and o->polish is
+ * set, the polish of the solves the re-pass does not take runs on a second
+ * stream of the handle beside the re-pass, and the re-passed solves are
+ * polished after it; the call forks that stream from `stream` and joins it
+ * back with events, so all of its work is ordered on `stream` as usual and
+ * the results are those of the polish run after the re-pass.
  * Errors: GRINS_E_INVALID_ARG for null required pointers, n_ics < 1,
  * n_sets < 0, non-positive tolerances, t_end <= t0, a grid that is not
  * increasing inside [t0, t_end], or max_steps < 1. */

@@ -149,6 +149,11 @@ struct grins_racipe {
     // attempts) then the item list, room for tail_cap solves
     unsigned char *d_tail = nullptr;
     int64_t tail_cap = 0;
+    // a second stream for the polish that runs beside the re-pass, with the
+    // events that fork it from and join it to the caller's stream (created
+    // on first use)
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     bool tail_ran = false;                             // the last FP32 integrate ran the re-pass
     std::string tail_why = "off";                      // what the last FP32 integrate did about it
     // cached median table
@@ -217,6 +222,11 @@ extern "C" const char *grins_version(void) { return "grins_racipe 0.1 (sm_103a)"
 static void free_device(grins_racipe *h)
 {
     cudaFree(h->d_block); cudaFree(h->d_grid); cudaFree(h->d_tail);
+    if (h->side) cudaStreamDestroy(h->side);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
+    h->side = nullptr;
+    h->ev_fork = h->ev_join = nullptr;
     h->d_block = nullptr;
     h->d_tail = nullptr;
     h->tail_cap = 0;
@@ -573,7 +583,9 @@ extern "C" grins_status grins_racipe_create(int32_t n_nodes, int32_t n_edges, co
     const size_t o_sign = bs.add(n_edges ? h->csr_sign.data() : nullptr, Eb);
     const size_t o_esign = bs.add(n_edges ? h->sign.data() : nullptr, Eb);
     const size_t o_median = bs.add(nullptr, sizeof(double) * Eb);
-    const size_t o_queue = bs.add(nullptr, sizeof(unsigned long long) * 4);
+    // d_queue: [0, 1] the integrator's work counters, [2, 3] check words,
+    // [4, 5] the unit counters of the two polish launches beside the re-pass
+    const size_t o_queue = bs.add(nullptr, sizeof(unsigned long long) * 8);
     const GrpOffsets og = stage_grp(grp, h->grp, bs);
     const GrpOffsets orr = stage_grp(grr, h->rr, bs);
     if (ce == cudaSuccess) ce = dev_malloc(&h->d_block, bs.host.size());
@@ -1468,15 +1480,46 @@ extern "C" grins_status grins_racipe_integrate(grins_racipe_t h, const grins_sol
     if (le != cudaSuccess) return cuda_fail(le, "integrate: launch");
     if (o->pass_event)
         CUDA_TRY(cudaEventRecord(static_cast<cudaEvent_t>(o->pass_event), st), "integrate: pass event");
+    // With the re-pass and the polish both to run, the polish of every
+    // solve the FP32 pass did not list (their statuses are final) runs on a
+    // second stream beside the re-pass -- the re-pass is FP32 issue work, the
+    // polish FP64 work, and the re-pass's last long solves leave SMs idle --
+    // and a list-mode polish of the listed solves follows the re-pass.
+    // The re-pass is launched before the forked polish becomes ready, so that
+    // its blocks take their SM slots first; the polish's blocks fill what is
+    // left and take over as the re-pass drains, drawing units from a counter.
+    const bool overlap = tail && o->polish;
+    if (overlap && !h->side) {
+        CUDA_TRY(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking), "integrate: polish stream");
+        CUDA_TRY(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming), "integrate: polish events");
+        CUDA_TRY(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming), "integrate: polish events");
+    }
     if (tail) {
         CUDA_TRY(launch_tail_order(a.tail_items, tail_sorted, a.tail_n, n_sets * (long long)n_ics, a.tail_work, st),
                  "integrate: re-pass order");
         CUDA_TRY(cudaMemsetAsync(h->d_queue, 0, 2 * sizeof(unsigned long long), st), "integrate: queue reset");
+        if (overlap) {
+            CUDA_TRY(cudaMemsetAsync(h->d_queue + 4, 0, 2 * sizeof(unsigned long long), st),
+                     "integrate: polish counters");
+            CUDA_TRY(cudaEventRecord(h->ev_fork, st), "integrate: fork");
+        }
         le = launch_grp_jit(a64.grp_jit, a64, st, h->num_sms);
         if (le != cudaSuccess) return cuda_fail(le, "integrate: re-pass launch");
     }
 
-    if (o->polish) {
+    if (overlap) {
+        PolishArgs pm = polish_args(h, o, d_params, n_sets, n_ics, d_states, d_status, d_err_est);
+        pm.queue = h->d_queue + 4;
+        CUDA_TRY(cudaStreamWaitEvent(h->side, h->ev_fork, 0), "integrate: fork");
+        CUDA_TRY(launch_polish(pm, h->side, h->num_sms), "integrate: polish launch");
+        CUDA_TRY(cudaEventRecord(h->ev_join, h->side), "integrate: join");
+        PolishArgs pl = polish_args(h, o, d_params, n_sets, n_ics, d_states, d_status, d_err_est);
+        pl.items = tail_sorted;
+        pl.n_items = a.tail_n;
+        pl.queue = h->d_queue + 5;
+        CUDA_TRY(launch_polish(pl, st, h->num_sms), "integrate: re-pass polish launch");
+        CUDA_TRY(cudaStreamWaitEvent(st, h->ev_join, 0), "integrate: join");
+    } else if (o->polish) {
         CUDA_TRY(launch_polish(polish_args(h, o, d_params, n_sets, n_ics, d_states, d_status, d_err_est), st,
                                h->num_sms), "integrate: polish launch");
     } else if (d_err_est) {

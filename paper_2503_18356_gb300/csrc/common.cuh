@@ -232,7 +232,20 @@ struct PolishArgs {
     int32_t iters;
     unsigned long long *check;   // checked builds: first violation (code, info)
     const volatile int32_t *cancel;   // nullable: nonzero marks unpolished converged solves cancelled
+    // list mode (non-null): polish only the solves of the re-pass list
+    // (items[0 .. *n_items)), one solve per work unit
+    const IntegrateArgs::TailItem *items;
+    const unsigned long long *n_items;
+    // non-null: warps take work units from this counter (zeroed by the
+    // caller) instead of a fixed share -- for a polish whose blocks start at
+    // different times, beside another kernel
+    unsigned long long *queue;
 };
+
+// Status byte of a solve the FP32 pass listed for the borderline re-pass:
+// its FP32 status with this bit set, until the re-pass writes the final one
+// (a polish running beside the re-pass leaves such solves alone).
+constexpr uint8_t kStatusListed = 0x80;
 
 #ifndef __CUDACC_RTC__
 cudaError_t launch_polish(const PolishArgs &a, cudaStream_t st, int num_sms);

@@ -115,17 +115,38 @@ __global__ void __launch_bounds__(WARPS * kWarp) polish_kernel(const PolishArgs 
     for (int i = lane; i < N; i += kWarp)
         for (int c = a.topo.off[i]; c < a.topo.off[i + 1]; ++c) row_e[c] = i;
     const int upc = (a.n_ics + kUnitIcs - 1) / kUnitIcs;      // units per set
-    const long long n_units = a.n_ics > 0 ? a.n_solves / a.n_ics * upc : 0;
-    for (long long u = (long long)blockIdx.x * WARPS + w; u < n_units; u += (long long)gridDim.x * WARPS) {
-        const long long set = u / upc;
-        const int ic0 = (int)(u - set * upc) * kUnitIcs;
-        const int ic1 = min(ic0 + kUnitIcs, a.n_ics);
+    // list mode: one unit per listed solve
+    const bool list = a.items != nullptr;
+    long long n_units = a.n_ics > 0 ? a.n_solves / a.n_ics * upc : 0;
+    if (list) n_units = (long long)min(*a.n_items, (unsigned long long)a.n_solves);
+    const bool dyn = a.queue != nullptr;
+    auto next_unit = [&](long long u) -> long long {
+        if (!dyn) return u + (long long)gridDim.x * WARPS;
+        unsigned long long v = 0;
+        if (lane == 0) v = atomicAdd(a.queue, 1ull);
+        return (long long)__shfl_sync(FULL, v, 0);
+    };
+    for (long long u = dyn ? next_unit(0) : (long long)blockIdx.x * WARPS + w; u < n_units; u = next_unit(u)) {
+        long long set;
+        int ic0, ic1;
+        if (list) {
+            long long idx = a.items[u].idx;
+            if (!GRINS_OK_IDX(idx >= 0 && idx < a.n_solves, 24, idx)) idx = 0;
+            set = idx / a.n_ics;
+            ic0 = (int)(idx - set * a.n_ics);
+            ic1 = ic0 + 1;
+        } else {
+            set = u / upc;
+            ic0 = (int)(u - set * upc) * kUnitIcs;
+            ic1 = min(ic0 + kUnitIcs, a.n_ics);
+        }
         if (a.cancel != nullptr && grins_cancelled(a.cancel)) {
             // cancelled: the unit's converged solves stay unpolished
             for (int ic = ic0 + lane; ic < ic1; ic += kWarp) {
                 const long long idx = set * a.n_ics + ic;
-                if (a.status[idx] == GRINS_SS_CONVERGED) a.status[idx] = GRINS_SS_CANCELLED;
-                if (a.err_est) a.err_est[idx] = -1.0f;
+                const uint8_t st = a.status[idx];
+                if (st == GRINS_SS_CONVERGED) a.status[idx] = GRINS_SS_CANCELLED;
+                if (a.err_est && !(st & kStatusListed)) a.err_est[idx] = -1.0f;
             }
             continue;
         }
@@ -133,8 +154,11 @@ __global__ void __launch_bounds__(WARPS * kWarp) polish_kernel(const PolishArgs 
         bool any = false;
         for (int ic = ic0 + lane; ic < ic1; ic += kWarp) {
             const long long idx = set * a.n_ics + ic;
-            any = any || a.status[idx] == GRINS_SS_CONVERGED;
-            if (a.status[idx] != GRINS_SS_CONVERGED && a.err_est) a.err_est[idx] = -1.0f;
+            const uint8_t st = a.status[idx];
+            any = any || st == GRINS_SS_CONVERGED;
+            // a solve listed for the re-pass (running beside this polish)
+            // is left alone: the list-mode polish after it sets its outputs
+            if (st != GRINS_SS_CONVERGED && !(st & kStatusListed) && a.err_est) a.err_est[idx] = -1.0f;
         }
         if (!__any_sync(FULL, any)) continue;
         const unsigned char *blk = a.params + set * a.L.stride;

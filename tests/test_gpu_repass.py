@@ -89,6 +89,31 @@ def test_double_float_repass_matches_fp64_repass():
     h.close()
 
 
+def test_polish_beside_repass_equals_polish_after():
+    """integrate with the polish runs it beside the re-pass (the solves the
+    FP32 pass did not list) and on the listed solves after it; the results
+    are bit-identical to integrate without the polish followed by the polish
+    call, and no status carries the internal mark of a listed solve."""
+    from paper_2503_18356_gb300 import api
+    w = W.net22_workload()
+    h = PT.gpu_handle(w["topology"])
+    params, ic, _, _ = PT.gpu_sample(h, w["param_seed"], 3000, 10)
+    a = h.integrate(params, ic, polish=1)
+    torch.cuda.synchronize()
+    a = PT.to_numpy(a)
+    n_a = h.tail_stats()
+    b = h.integrate(params, ic, polish=0)
+    h.polish(params, b["states"], b["status"], b["err_est"], opts=api.default_opts())
+    torch.cuda.synchronize()
+    b = PT.to_numpy(b)
+    assert n_a == h.tail_stats() and n_a[0] > 0
+    for k in ("states", "status", "err_est", "n_steps", "t_final"):
+        assert np.array_equal(a[k], b[k], equal_nan=True), k
+    assert a["status"].max() <= api.CANCELLED
+    assert np.any(a["status"] == O.CONVERGED)
+    h.close()
+
+
 def test_repass_skipped_with_time_series_and_for_fp64():
     w = W.net5_workload()
     h = PT.gpu_handle(w["topology"])
