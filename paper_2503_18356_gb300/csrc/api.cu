@@ -1502,6 +1502,7 @@ extern "C" grins_status grins_racipe_integrate(grins_racipe_t h, const grins_sol
             CUDA_TRY(cudaMemsetAsync(h->d_queue + 4, 0, 2 * sizeof(unsigned long long), st),
                      "integrate: polish counters");
             CUDA_TRY(cudaEventRecord(h->ev_fork, st), "integrate: fork");
+            a64.tail_mark = 1;
         }
         le = launch_grp_jit(a64.grp_jit, a64, st, h->num_sms);
         if (le != cudaSuccess) return cuda_fail(le, "integrate: re-pass launch");

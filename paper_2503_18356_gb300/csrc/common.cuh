@@ -138,6 +138,10 @@ struct IntegrateArgs {
     unsigned long long *tail_n;  // [2]: items appended, FP64 attempts spent on them
     float f_tail_chk, f_tail_rho, f_tail_late;
     int32_t tail_work;
+    // list mode: the statuses the re-pass writes keep kStatusListed (a
+    // list-mode polish after it clears the mark; a polish running beside it
+    // must not take these solves even once their status is final)
+    int32_t tail_mark;
     const volatile int32_t *cancel;   // nullable: nonzero stops the hand-out of work (grins_solver_opts.cancel)
 };
 

@@ -88,6 +88,16 @@ __host__ __device__ constexpr int rr_warp_bytes(int rows, int planes, int el)
     return 2 * planes * rows * kWarp * el;
 }
 
+// The double-float kernel keeps its edge records in shared memory instead
+// of registers (its right-hand side then runs each row's positions as a
+// loop, code that fits the instruction cache): after the gather buffers,
+// [positions][32 lanes] records of 16 bytes ((1/T)^n and 1/lambda, each a
+// pair of FP32 numbers) and [positions][32 lanes] gather addresses.
+__host__ __device__ constexpr int rr_dd_warp_bytes(int rows, int positions)
+{
+    return rr_warp_bytes(rows, 6, 8) + (positions > 0 ? positions : 1) * kWarp * 20;
+}
+
 // Lanes of a group are j-major: lane = j * (32 / L) + g, so lane j of every
 // group sits in one contiguous block and a group's lanes are 32/L apart.
 // Scheduling domains of four consecutive groups: domains per warp.

@@ -322,9 +322,13 @@ int jit_minb(const GrpTopo &g, int kind)
 {
     const int est = 4 * g.P + 11 * g.R + 40;
     int minb = kind == kJitRegisters ? (est <= 144 ? 4 : (est <= 176 ? 3 : 2)) : GRINS_GRP_MINB;
-    if (kind == kJitRegisters64 || kind == kJitRegistersDD) {   // 2 registers per value, 5 per position
+    if (kind == kJitRegisters64) {          // 2 registers per value, 5 per position
         const int est64 = 5 * g.P + 22 * g.R + 60;
         minb = est64 <= 128 ? 4 : (est64 <= 168 ? 3 : 2);
+    }
+    if (kind == kJitRegistersDD) {          // records in shared memory: 2 registers per value, ~90 besides
+        const int estdd = 22 * g.R + 90;
+        minb = estdd <= 128 ? 4 : (estdd <= 168 ? 3 : 2);
     }
     const int w = jit_warps(kind);
     minb = std::max(1, minb * kJitWarps / w);
@@ -728,7 +732,9 @@ cudaError_t launch_grp_jit(const void *handle, const IntegrateArgs &a, cudaStrea
     const int W = je->warps;
     int smem = 0;
     if (je->kind != kJitShared) {
-        smem = je->kind == kJitRegisters ? W * rr_warp_bytes(b.grp.R, 1, 4) : W * rr_warp_bytes(b.grp.R, 6, 8);
+        smem = je->kind == kJitRegisters     ? W * rr_warp_bytes(b.grp.R, 1, 4)
+               : je->kind == kJitRegistersDD ? W * rr_dd_warp_bytes(b.grp.R, b.grp.P)
+                                             : W * rr_warp_bytes(b.grp.R, 6, 8);
     } else {
         const int ndom = grp_domains(b.grp.L);
         GrpLayout LY{b.grp.L, b.grp.R, b.grp.P, b.slots};

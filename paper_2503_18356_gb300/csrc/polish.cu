@@ -135,6 +135,9 @@ __global__ void __launch_bounds__(WARPS * kWarp) polish_kernel(const PolishArgs 
             set = idx / a.n_ics;
             ic0 = (int)(idx - set * a.n_ics);
             ic1 = ic0 + 1;
+            // the re-pass left its final status marked: clear the mark
+            if (lane == 0) a.status[idx] = (uint8_t)(a.status[idx] & ~kStatusListed);
+            __syncwarp();
         } else {
             set = u / upc;
             ic0 = (int)(u - set * upc) * kUnitIcs;
