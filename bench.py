@@ -49,10 +49,10 @@ REPASS_FP64_INSTR_PER_ATTEMPT = (253_617_128 + 766_275_305 + 786_803_446) / 254_
 UNIQUE_FP64_INSTR_PER_SOLVE = (2_580_512 + 5_598_692 + 19_595_422) / 127_243
 # Executed warp instructions of the double-float re-pass kernel per solve
 # step attempt, from an ncu capture of the same 20,000-set launch
-# (620,488,072 warp instructions for 254,533 attempts,
+# (801,912,638 warp instructions for 254,533 attempts,
 # profiles/fp64_kernels_rand22x82_20k.md); None while no capture of the
 # current kernel exists.
-REPASS_DD_WARP_INSTR_PER_ATTEMPT = 620_488_072 / 254_533
+REPASS_DD_WARP_INSTR_PER_ATTEMPT = 801_912_638 / 254_533
 
 
 def parse():
