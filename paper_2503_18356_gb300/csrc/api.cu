@@ -1311,8 +1311,12 @@ extern "C" grins_status grins_racipe_polish(grins_racipe_t h, const grins_solver
     if (!polish_opts_ok(o)) return fail(GRINS_E_INVALID_ARG, "polish: bad polish options");
     if (!on_handle_device(h)) return fail(GRINS_E_INVALID_ARG, "polish: current device is not the handle's");
     if (n_sets == 0) return GRINS_OK;
-    CUDA_TRY(launch_polish(polish_args(h, o, d_params, n_sets, n_ics, d_states, d_status, d_err_est),
-                           (cudaStream_t)stream, h->num_sms), "polish: launch");
+    // units handed out from a counter (work per unit varies with its
+    // converged solves: a fixed share left warps idle at the end)
+    PolishArgs pa = polish_args(h, o, d_params, n_sets, n_ics, d_states, d_status, d_err_est);
+    pa.queue = h->d_queue + 4;
+    CUDA_TRY(cudaMemsetAsync(pa.queue, 0, sizeof(unsigned long long), (cudaStream_t)stream), "polish: counter");
+    CUDA_TRY(launch_polish(pa, (cudaStream_t)stream, h->num_sms), "polish: launch");
     return GRINS_OK;
 }
 
@@ -1521,8 +1525,10 @@ extern "C" grins_status grins_racipe_integrate(grins_racipe_t h, const grins_sol
         CUDA_TRY(launch_polish(pl, st, h->num_sms), "integrate: re-pass polish launch");
         CUDA_TRY(cudaStreamWaitEvent(st, h->ev_join, 0), "integrate: join");
     } else if (o->polish) {
-        CUDA_TRY(launch_polish(polish_args(h, o, d_params, n_sets, n_ics, d_states, d_status, d_err_est), st,
-                               h->num_sms), "integrate: polish launch");
+        PolishArgs pa = polish_args(h, o, d_params, n_sets, n_ics, d_states, d_status, d_err_est);
+        pa.queue = h->d_queue + 4;
+        CUDA_TRY(cudaMemsetAsync(pa.queue, 0, sizeof(unsigned long long), st), "integrate: polish counter");
+        CUDA_TRY(launch_polish(pa, st, h->num_sms), "integrate: polish launch");
     } else if (d_err_est) {
         CUDA_TRY(cudaMemsetAsync(d_err_est, 0xff, sizeof(float) * n_sets * n_ics, st), "integrate: err_est");
     }
@@ -1871,6 +1877,8 @@ static grins_status plan_job_tail(grins_racipe_plan *p, size_t b, cudaStream_t s
         PolishArgs pa = polish_args(j.net, &p->opts, j.d_params, j.n_sets, j.n_ics, j.d_states, j.d_status,
                                     j.d_err_est);
         pa.check = p->d_counters + 4 * b + 2;
+        pa.queue = p->d_counters + 4 * b;              // the job's integrate is done with it
+        CUDA_TRY(cudaMemsetAsync(pa.queue, 0, sizeof(unsigned long long), st), "plan: polish counter");
         CUDA_TRY(launch_polish(pa, st, p->num_sms), "plan: polish launch");
     } else if (j.d_err_est) {
         CUDA_TRY(cudaMemsetAsync(j.d_err_est, 0xff, sizeof(float) * j.n_sets * j.n_ics, st), "plan: err_est");
@@ -2420,6 +2428,8 @@ grins_status server_launch(grins_racipe_server *sv, ServerRequest &r)
         PolishArgs pa = polish_args(h, o, r.params, S, I, r.states, r.status, r.err_est);
         pa.check = r.words + 2;
         pa.cancel = a.cancel;
+        pa.queue = r.words;                             // the integrate before it on this stream is done with it
+        CUDA_TRY(cudaMemsetAsync(pa.queue, 0, sizeof(unsigned long long), st), "server: polish counter");
         CUDA_TRY(launch_polish(pa, st, h->num_sms), "server: polish launch");
     } else {
         CUDA_TRY(cudaMemsetAsync(r.err_est, 0xff, sizeof(float) * S * I, st), "server: err_est");

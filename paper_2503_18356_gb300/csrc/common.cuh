@@ -241,8 +241,9 @@ struct PolishArgs {
     const IntegrateArgs::TailItem *items;
     const unsigned long long *n_items;
     // non-null: warps take work units from this counter (zeroed by the
-    // caller) instead of a fixed share -- for a polish whose blocks start at
-    // different times, beside another kernel
+    // caller) instead of a fixed share -- the work of a unit varies with its
+    // converged solves, and a polish beside another kernel starts its
+    // blocks at different times
     unsigned long long *queue;
 };
 
