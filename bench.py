@@ -5,8 +5,9 @@ Workload (one "step" = the whole hot path over one batch): the seeded random
 stand-in for the paper's EMT network, Sec. 3.2), 100,000 parameter sets x 10
 initial conditions = 1,000,000 solves per step:
   sample parameters + ICs -> FP32 Dormand-Prince 5(4) to steady state ->
-  FP64 re-pass of the solves whose steady-state decision fell near t_end ->
-  FP64 Newton polish -> distinct steady states per set.
+  double-float re-pass of the solves whose steady-state decision fell near
+  t_end, with the FP64 Newton polish of the other solves beside it, then of
+  the re-passed ones -> distinct steady states per set.
 Under torchrun each rank integrates its own 100,000 sets (set offset rank x
 100,000; weak scaling, no collective on the data path).
 

@@ -279,7 +279,7 @@ int64_t grins_device_allocations(void);
  * rates[2] rcp.approx.f32 (the special-function unit: the FP32
  * integrator's edge powers, node logarithms and divisions of Eq. 2),
  * rates[3] FP32 fused multiply-add, rates[4] FP64 fused multiply-add (the
- * polish, the dedupe and the FP64 re-pass).  These are the denominators of
+ * polish, the dedupe, the plain FP64 solver).  These are the denominators of
  * the kernels' rooflines.  One block of 1024 threads per SM runs eight
  * independent chains of each operation for a fixed count and reads the SM
  * clock around the loop; a rate is the median over blocks, so it does not
@@ -596,9 +596,9 @@ grins_status grins_racipe_integrate_static(grins_racipe_t h, const grins_solver_
                                            int32_t *d_n_steps, double *d_series, void *stream);
 
 /* The borderline re-pass of the last FP32 grins_racipe_integrate call on h
- * (see grins_solver_opts.tail_rtol): *n_solves = solves it re-integrated in
- * FP64, *n_attempts = their FP64 step attempts; both 0 when that call did
- * not run it.  Copies two counters from the device after synchronising
+ * (see grins_solver_opts.tail_rtol): *n_solves = solves it re-integrated
+ * (in tail_precision), *n_attempts = their step attempts in the re-pass;
+ * both 0 when that call did not run it.  Copies two counters from the device after synchronising
  * `stream` (the stream of that call).  Errors: GRINS_E_INVALID_ARG for null
  * pointers. */
 grins_status grins_racipe_tail_stats(grins_racipe_t h, void *stream, int64_t *n_solves, int64_t *n_attempts);

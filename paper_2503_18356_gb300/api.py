@@ -373,7 +373,7 @@ class Racipe:
         return out
 
     def tail_stats(self, stream=None):
-        """(solves, FP64 attempts) of the last FP32 integrate's borderline re-pass."""
+        """(solves, attempts) of the last FP32 integrate's borderline re-pass."""
         n, a = C.c_int64(0), C.c_int64(0)
         with torch.cuda.device(self.device):
             _check(_lib.grins_racipe_tail_stats(self._h, _stream(stream), C.byref(n), C.byref(a)))

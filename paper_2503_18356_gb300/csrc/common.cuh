@@ -131,11 +131,11 @@ struct IntegrateArgs {
     // residual < tail_rho, or converged with t_end - t < tail_late (t - t_c))
     // and which took at most tail_work attempts after its checkpoint, leaves
     // that state in `states`, appends (solve, t_c, those attempts) to
-    // tail_items and bumps tail_n.  The FP64 pass, given the same list,
+    // tail_items and bumps tail_n.  The re-pass, given the same list,
     // integrates each from its checkpoint to its status.
     struct TailItem { int64_t idx; float t; int32_t work; };
     TailItem *tail_items;        // [n_sets * n_ics] capacity
-    unsigned long long *tail_n;  // [2]: items appended, FP64 attempts spent on them
+    unsigned long long *tail_n;  // [2]: items appended, re-pass attempts spent on them
     float f_tail_chk, f_tail_rho, f_tail_late;
     int32_t tail_work;
     // list mode: the statuses the re-pass writes keep kStatusListed (a
@@ -212,7 +212,7 @@ const void *grp_jit_plan_kernel(const GrpTopo *layouts, int n_layouts, int warps
 cudaError_t launch_plan_ct(const void *kern, const PlanArgs &p, cudaStream_t st, int num_sms, int smem_limit);
 // The borderline re-pass list `in` (n_in[0] items) copied to `out` longest
 // first (by the FP32 pass's attempts after the checkpoint, in buckets of
-// max_work / 64), for the FP64 pass.
+// max_work / 64), for the re-pass.
 // Issue rates of ex2.approx, lg2.approx, rcp.approx, FP32 FMA and FP64 FMA
 // (rates[0..4], operations per clock per SM) on the current device, from one
 // block per SM of n_sm; d_cycles / d_sink: n_sm entries each (rates.cu).

@@ -2,7 +2,7 @@
 // bound by: the special-function unit (ex2.approx, lg2.approx, rcp.approx,
 // the operations of the FP32 integrator's edge terms, node logarithms and
 // divisions), the FP32 fused multiply-add and the FP64 fused multiply-add
-// (polish, dedupe, the FP64 re-pass).  The rates, in operations per clock
+// (polish, dedupe, the plain FP64 solver and the FP64 form of the re-pass).  The rates, in operations per clock
 // per SM, are the denominators of the integrator's and the FP64 kernels'
 // rooflines on the device the library runs on.
 //

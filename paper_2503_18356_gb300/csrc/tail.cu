@@ -1,9 +1,9 @@
 // Order of the borderline re-pass (see IntegrateArgs::tail_items): the
-// solves the FP32 pass listed are re-integrated in FP64 from their
+// solves the FP32 pass listed are re-integrated (double-float or FP64) from their
 // checkpoints, and their lengths differ widely -- a checkpoint taken early
 // leaves a long stretch to t_end.  Handing them out longest first
 // (longest-processing-time-first scheduling) lets the long ones start while
-// the many short ones fill the gaps, so the FP64 launch does not end on a
+// the many short ones fill the gaps, so the re-pass launch does not end on a
 // few long solves running alone.  The length is estimated by the attempts
 // the FP32 pass took after the checkpoint, in 64 buckets (a counting sort;
 // the order within a bucket is arbitrary, and each solve's result is

@@ -1,6 +1,6 @@
 """The borderline re-pass of grins_racipe_integrate (grins_solver_opts.tail_*):
 the FP32 pass keeps a checkpoint per solve and lists the solves whose
-steady-state decision falls near t_end; an FP64 pass re-integrates only
+steady-state decision falls near t_end; a wide pass (double-float by default, or FP64) re-integrates only
 those from their checkpoints.  These tests check that it touches only the
 listed solves, reports what it did, and validates its options; its effect
 on parity is held by test_n_unique_bar_net22_10k_sets and the parity tests,
@@ -24,7 +24,7 @@ def _run(h, params, ic, **opt):
 
 def test_repass_changes_only_listed_solves():
     """Solves the FP32 pass does not list come out bit-identical with and
-    without the re-pass; listed ones carry the FP64 pass's attempts on top of
+    without the re-pass; listed ones carry the re-pass's attempts on top of
     the FP32 pass's (d_n_steps counts both) and end converged or at t_end."""
     w = W.net22_workload()
     h = PT.gpu_handle(w["topology"])
@@ -42,7 +42,7 @@ def test_repass_changes_only_listed_solves():
     assert extra.sum() == a_tail
     listed = extra > 0
     assert 0 < listed.sum() <= n_tail
-    # a listed solve the FP64 pass decides without a step (its checkpoint at
+    # a listed solve the re-pass decides without a step (its checkpoint at
     # t_end, or already below ss_tol in FP64) has no extra attempts: at most
     # n_tail - listed.sum() of the others may differ
     same = ~listed
