@@ -45,9 +45,15 @@ INTEGRATOR_DRAM_BYTES_PER_SOLVE = (35.497e6 + 0.692e6) / 200_000
 # launch (profiles/fp64_kernels_rand22x82_20k.md): the polish per solve it
 # polishes (converged before the polish: 127,247), the re-pass per FP64 step
 # attempt (254,532), the dedupe per converged solve (127,243).
-POLISH_FP64_INSTR_PER_SOLVE = (37_244_518 + 142_762_810 + 128_571_916) / 127_247
-REPASS_FP64_INSTR_PER_ATTEMPT = (253_617_128 + 766_275_305 + 786_803_446) / 254_532
-UNIQUE_FP64_INSTR_PER_SOLVE = (2_580_512 + 5_598_692 + 19_595_422) / 127_243
+# (DADD, DMUL, DFMA) counts of each kernel; the per-unit figure is their sum
+# over the units, the peak the issue rate of that mix (each kind at its own
+# measured rate)
+POLISH_FP64_MIX = (37_244_518, 142_762_810, 128_571_916)
+REPASS_FP64_MIX = (253_617_128, 766_275_305, 786_803_446)
+UNIQUE_FP64_MIX = (2_580_512, 5_598_692, 19_595_422)
+POLISH_FP64_INSTR_PER_SOLVE = sum(POLISH_FP64_MIX) / 127_247
+REPASS_FP64_INSTR_PER_ATTEMPT = sum(REPASS_FP64_MIX) / 254_532
+UNIQUE_FP64_INSTR_PER_SOLVE = sum(UNIQUE_FP64_MIX) / 127_243
 # Executed warp instructions of the double-float re-pass kernel per solve
 # step attempt, from an ncu capture of the same 20,000-set launch
 # (801,912,638 warp instructions for 254,533 attempts,
@@ -702,7 +708,6 @@ def run_native(args):
         unit = "Gop/s (FP32 pipe)"
     # the FP64 kernels against the FP64 FMA issue rate: executed FP64
     # instructions per unit (ncu counts, constants above) x units / time
-    fp64_peak = rates["dfma"] * sms * f_mhz * 1e6 / 1e9
     hist = np.bincount(status.ravel(), minlength=5)
     n_conv = int(hist[0])
 
@@ -720,9 +725,18 @@ def run_native(args):
                     basis="%.0f warp instructions per step attempt x %d attempts / the re-pass time (ordering + "
                           "double-float kernel); peak 4 warp instructions per clock per SM" % (ipk, att))
 
-    def fp64_roof(instr, ms, what):
+    # the FP64 kernels against the FP64 issue rate of their instruction mix:
+    # executed FP64 instructions per unit (ncu counts, constants above) x
+    # units / time, over the rate at which the SMs issue that mix of DADD,
+    # DMUL and DFMA (each kind at its measured rate)
+    def mix_peak(mix):
+        per_clk = sum(mix) / sum(n / r for n, r in zip(mix, (rates["dadd"], rates["dmul"], rates["dfma"])))
+        return per_clk * sms * f_mhz * 1e6 / 1e9
+
+    def fp64_roof(instr, ms, what, mix):
+        peak_m = mix_peak(mix)
         ach = instr / (ms / 1e3) / 1e9 if ms > 0 else 0.0
-        return dict(bound="fp64", achieved=ach, peak=fp64_peak, unit="G FP64 instr/s", frac=ach / fp64_peak,
+        return dict(bound="fp64", achieved=ach, peak=peak_m, unit="G FP64 instr/s", frac=ach / peak_m,
                     basis=what)
 
     solves = S * I * ws
@@ -822,16 +836,18 @@ def run_native(args):
             secondary_rooflines=dict(
                 polish=fp64_roof(POLISH_FP64_INSTR_PER_SOLVE * (n_conv + int(hist[4])), sep_ms[3],
                                  "%.0f FP64 instructions per polished solve x %d solves / the polish kernel's "
-                                 "time" % (POLISH_FP64_INSTR_PER_SOLVE, n_conv + int(hist[4]))),
+                                 "time" % (POLISH_FP64_INSTR_PER_SOLVE, n_conv + int(hist[4])), POLISH_FP64_MIX),
                 repass=(fp64_roof(REPASS_FP64_INSTR_PER_ATTEMPT * a_tail, sep_ms[2],
                                   "%.0f FP64 instructions per FP64 step attempt x %d attempts / the re-pass "
-                                  "time (ordering + FP64 kernel)" % (REPASS_FP64_INSTR_PER_ATTEMPT, a_tail))
+                                  "time (ordering + FP64 kernel)" % (REPASS_FP64_INSTR_PER_ATTEMPT, a_tail),
+                                  REPASS_FP64_MIX)
                         if opts.tail_precision == api.GRINS_TAIL_FP64 else issue_roof(a_tail, sep_ms[2])),
                 unique=fp64_roof(UNIQUE_FP64_INSTR_PER_SOLVE * n_conv, kern_ms[4],
                                  "%.0f FP64 instructions per converged solve x %d solves / the dedupe "
-                                 "kernel's time" % (UNIQUE_FP64_INSTR_PER_SOLVE, n_conv)),
-                peak_basis="%d SMs x %.2f DFMA/clk/SM (grins_unit_rates) x %.0f MHz" % (
-                    sms, rates["dfma"], f_mhz)),
+                                 "kernel's time" % (UNIQUE_FP64_INSTR_PER_SOLVE, n_conv), UNIQUE_FP64_MIX),
+                peak_basis="%d SMs x the kernel's DADD/DMUL/DFMA mix at %.2f / %.2f / %.2f per clk per SM "
+                           "(grins_unit_rates) x %.0f MHz" % (sms, rates["dadd"], rates["dmul"], rates["dfma"],
+                                                             f_mhz)),
             e2e=dict(value=e2e_value, unit="solves/s", h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h,
                      first_step_s=first_step_s,
                      note="steady state: each timed step creates its handle, but the process-wide caches "
@@ -848,7 +864,7 @@ def run_native(args):
                                  roofline=fp64_roof(REPASS_FP64_INSTR_PER_ATTEMPT * a64, fp64_ms,
                                                     "%.0f FP64 instructions per step attempt (the same FP64 "
                                                     "kernel body as the re-pass) x %d attempts / its time"
-                                                    % (REPASS_FP64_INSTR_PER_ATTEMPT, a64))),
+                                                    % (REPASS_FP64_INSTR_PER_ATTEMPT, a64), REPASS_FP64_MIX)),
             clocks=clocks)
         if levels is not None:
             line["levels"] = levels

@@ -275,11 +275,12 @@ int64_t grins_device_allocations(void);
 
 /* Measured issue rates of the arithmetic units that bound this library's
  * kernels on the current device, in operations per clock per SM (host array
- * of five doubles): rates[0] ex2.approx.f32, rates[1] lg2.approx.f32,
+ * of seven doubles): rates[0] ex2.approx.f32, rates[1] lg2.approx.f32,
  * rates[2] rcp.approx.f32 (the special-function unit: the FP32
  * integrator's edge powers, node logarithms and divisions of Eq. 2),
- * rates[3] FP32 fused multiply-add, rates[4] FP64 fused multiply-add (the
- * polish, the dedupe, the plain FP64 solver).  These are the denominators of
+ * rates[3] FP32 fused multiply-add, rates[4] FP64 fused multiply-add,
+ * rates[5] FP64 multiply, rates[6] FP64 add (the polish, the dedupe, the
+ * plain FP64 solver).  These are the denominators of
  * the kernels' rooflines.  One block of 1024 threads per SM runs eight
  * independent chains of each operation for a fixed count and reads the SM
  * clock around the loop; a rate is the median over blocks, so it does not

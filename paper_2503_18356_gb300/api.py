@@ -170,14 +170,14 @@ def _check(st):
         raise GrinsError(st, _lib.grins_last_error().decode())
 
 
-UNIT_RATE_NAMES = ("ex2", "lg2", "rcp", "ffma", "dfma")
+UNIT_RATE_NAMES = ("ex2", "lg2", "rcp", "ffma", "dfma", "dmul", "dadd")
 
 
 def unit_rates(stream=None) -> dict:
     """grins_unit_rates: measured issue rates (operations per clock per SM) of
-    ex2.approx, lg2.approx, rcp.approx, FP32 FMA and FP64 FMA on the current
-    device, keyed by those names."""
-    r = (C.c_double * 5)()
+    ex2.approx, lg2.approx, rcp.approx, FP32 FMA, FP64 FMA, FP64 multiply and
+    FP64 add on the current device, keyed by those names."""
+    r = (C.c_double * len(UNIT_RATE_NAMES))()
     _check(_lib.grins_unit_rates(r, _stream(stream)))
     return dict(zip(UNIT_RATE_NAMES, (float(x) for x in r)))
 

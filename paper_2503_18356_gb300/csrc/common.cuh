@@ -213,9 +213,10 @@ cudaError_t launch_plan_ct(const void *kern, const PlanArgs &p, cudaStream_t st,
 // The borderline re-pass list `in` (n_in[0] items) copied to `out` longest
 // first (by the FP32 pass's attempts after the checkpoint, in buckets of
 // max_work / 64), for the re-pass.
-// Issue rates of ex2.approx, lg2.approx, rcp.approx, FP32 FMA and FP64 FMA
-// (rates[0..4], operations per clock per SM) on the current device, from one
-// block per SM of n_sm; d_cycles / d_sink: n_sm entries each (rates.cu).
+// Issue rates of ex2.approx, lg2.approx, rcp.approx, FP32 FMA, FP64 FMA,
+// FP64 multiply and FP64 add (rates[0..6], operations per clock per SM) on
+// the current device, from one block per SM of n_sm; d_cycles / d_sink:
+// n_sm entries each (rates.cu).
 cudaError_t measure_unit_rates(double *rates, cudaStream_t st, long long *d_cycles, double *d_sink, int n_sm);
 
 cudaError_t launch_tail_order(const IntegrateArgs::TailItem *in, IntegrateArgs::TailItem *out,

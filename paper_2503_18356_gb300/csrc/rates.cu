@@ -1,8 +1,9 @@
 // Issue-rate probe of the arithmetic units the kernels of this library are
 // bound by: the special-function unit (ex2.approx, lg2.approx, rcp.approx,
 // the operations of the FP32 integrator's edge terms, node logarithms and
-// divisions), the FP32 fused multiply-add and the FP64 fused multiply-add
-// (polish, dedupe, the plain FP64 solver and the FP64 form of the re-pass).  The rates, in operations per clock
+// divisions), the FP32 fused multiply-add and the FP64 multiply-add,
+// multiply and add (polish, dedupe, the plain FP64 solver and the FP64 form
+// of the re-pass).  The rates, in operations per clock
 // per SM, are the denominators of the integrator's and the FP64 kernels'
 // rooflines on the device the library runs on.
 //
@@ -32,7 +33,7 @@ constexpr int kRateThreads = 1024;
 constexpr int kRateIters = 2048;
 
 template <int OP> struct RateShape {
-    static constexpr int chains = OP >= 3 ? 16 : 8;
+    static constexpr int chains = OP >= 3 ? 16 : 8;   // the FMAs and the FP64 operations
     static constexpr int unroll = OP == 3 ? 4 : 1;
 };
 
@@ -57,7 +58,7 @@ __device__ __forceinline__ float mufu_rcp(float x)
     return y;
 }
 
-// OP: 0 ex2, 1 lg2, 2 rcp, 3 FP32 FMA, 4 FP64 FMA.  cycles[b] <- block b's
+// OP: 0 ex2, 1 lg2, 2 rcp, 3 FP32 FMA, 4 FP64 FMA, 5 FP64 multiply, 6 FP64 add.  cycles[b] <- block b's
 // clock delta; sink[b] <- a value depending on every chain (keeps the loop).
 template <int OP>
 __global__ void __launch_bounds__(kRateThreads) rate_kernel(long long *cycles, double *sink, int n_blocks)
@@ -81,14 +82,16 @@ __global__ void __launch_bounds__(kRateThreads) rate_kernel(long long *cycles, d
             else if constexpr (OP == 1) f[c] = mufu_lg2(f[c] + 1.5f);       // stays in (0.58, 1.6)
             else if constexpr (OP == 2) f[c] = mufu_rcp(f[c] + 1.0f);       // stays in (0.5, 1)
             else if constexpr (OP == 3) f[c] = fmaf(f[c], 0.999f, 0.001f);  // fixed point 1
-            else d[c] = fma(d[c], 0.999, 0.001);
+            else if constexpr (OP == 4) d[c] = fma(d[c], 0.999, 0.001);
+            else if constexpr (OP == 5) d[c] = __dmul_rn(d[c], 0.999999);   // decays slowly, stays normal
+            else d[c] = __dadd_rn(d[c], 1e-9);
         }
     }
     __syncthreads();
     const long long t1 = clock64();
     double s = 0.0;
 #pragma unroll
-    for (int c = 0; c < CH; ++c) s += (OP == 4) ? d[c] : (double)f[c];
+    for (int c = 0; c < CH; ++c) s += (OP >= 4) ? d[c] : (double)f[c];
     // one value per block: any thread's value keeps its chains live
     if (threadIdx.x == 0 && b < n_blocks) {
         cycles[b] = t1 - t0;
@@ -131,7 +134,9 @@ cudaError_t measure_unit_rates(double *rates, cudaStream_t st, long long *d_cycl
     if ((e = run_rate<1>(n_sm, smem, d_cycles, d_sink, st, rates[1])) != cudaSuccess) return e;
     if ((e = run_rate<2>(n_sm, smem, d_cycles, d_sink, st, rates[2])) != cudaSuccess) return e;
     if ((e = run_rate<3>(n_sm, smem, d_cycles, d_sink, st, rates[3])) != cudaSuccess) return e;
-    return run_rate<4>(n_sm, smem, d_cycles, d_sink, st, rates[4]);
+    if ((e = run_rate<4>(n_sm, smem, d_cycles, d_sink, st, rates[4])) != cudaSuccess) return e;
+    if ((e = run_rate<5>(n_sm, smem, d_cycles, d_sink, st, rates[5])) != cudaSuccess) return e;
+    return run_rate<6>(n_sm, smem, d_cycles, d_sink, st, rates[6]);
 }
 
 }  // namespace grins

@@ -23,6 +23,7 @@ def test_unit_rates_are_plausible_and_repeatable():
     # the compiler packs independent FMAs into f32x2 instructions
     assert 64.0 <= a["ffma"] <= 272.0
     assert 0.1 <= a["dfma"] <= 72.0
+    assert 0.1 <= a["dmul"] <= 72.0 and 0.1 <= a["dadd"] <= 72.0
     assert a["ffma"] > 4.0 * a["rcp"]
     for k in a:
         assert abs(a[k] - b[k]) <= 0.05 * a[k], (k, a[k], b[k])
