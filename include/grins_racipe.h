@@ -365,7 +365,7 @@ grins_status grins_racipe_sample_params(grins_racipe_t h, const grins_racipe_ran
  * When the borderline re-pass runs (FP32, o->tail_rtol > 0) and o->polish is
  * set, the polish of the solves the re-pass does not take runs on a second
  * stream of the handle beside the re-pass, and the re-passed solves are
- * polished after it; the call forks that stream from `stream` and joins it
+ * polished after both; the call forks that stream from `stream` and joins it
  * back with events, so all of its work is ordered on `stream` as usual and
  * the results are those of the polish run after the re-pass.
  * Errors: GRINS_E_INVALID_ARG for null required pointers, n_ics < 1,

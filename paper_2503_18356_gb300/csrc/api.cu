@@ -1414,6 +1414,11 @@ extern "C" grins_status grins_racipe_integrate(grins_racipe_t h, const grins_sol
     if (o->precision == GRINS_FP32) {
         // grins_racipe_integrator describes the FP32 kernel: only its launches record it
         const bool want_tail = o->tail_rtol > 0 && o->n_t == 0;
+        // the re-pass kernel's compile starts on the host pool while this
+        // thread compiles the FP32 one (a first call waits for one, not both)
+        if (want_tail && h->rr.L > 0)
+            grp_jit_prefetch(h->rr.topo(), o->tail_precision == GRINS_TAIL_FP64 ? kJitRegisters64 : kJitRegistersDD,
+                             a.method | kJitTail | (a.cancel ? kJitCancel : 0));
         const bool rr = pick_fp32_kernel(h, &a, true, &h->jit_why, want_tail);
         h->jit_used = a.grp_jit != nullptr;
         h->used_L = a.grp.L; h->used_R = a.grp.R; h->used_P = a.grp.P;
@@ -1518,12 +1523,14 @@ extern "C" grins_status grins_racipe_integrate(grins_racipe_t h, const grins_sol
         CUDA_TRY(cudaStreamWaitEvent(h->side, h->ev_fork, 0), "integrate: fork");
         CUDA_TRY(launch_polish(pm, h->side, h->num_sms), "integrate: polish launch");
         CUDA_TRY(cudaEventRecord(h->ev_join, h->side), "integrate: join");
+        // the list-mode polish clears the listed solves' marks: it waits for
+        // the polish beside the re-pass, which must not see a cleared mark
+        CUDA_TRY(cudaStreamWaitEvent(st, h->ev_join, 0), "integrate: join");
         PolishArgs pl = polish_args(h, o, d_params, n_sets, n_ics, d_states, d_status, d_err_est);
         pl.items = tail_sorted;
         pl.n_items = a.tail_n;
         pl.queue = h->d_queue + 5;
         CUDA_TRY(launch_polish(pl, st, h->num_sms), "integrate: re-pass polish launch");
-        CUDA_TRY(cudaStreamWaitEvent(st, h->ev_join, 0), "integrate: join");
     } else if (o->polish) {
         PolishArgs pa = polish_args(h, o, d_params, n_sets, n_ics, d_states, d_status, d_err_est);
         pa.queue = h->d_queue + 4;
