@@ -195,8 +195,8 @@ def parity_figures(gpu, orc, G, k, params_slice):
     over solves converged on both sides at the same fixed point (G/k-
     normalised distance <= 1e-2 raw, 1e-5 polished):
       * raw states (the integrator's stopping point, before the polish):
-        relative error with G12's floor, |x - x*| / max(|x*|, 1e-6 G/k) --
-        the benchmark spec's scale -- with the share of solves above 1e-3, and the
+        relative error with a floor, |x - x*| / max(|x*|, 1e-6 G/k) -- the
+        relative 1e-3 scale -- with the share of solves above 1e-3, and the
         error on the G/k scale beside it (the steady-state test bounds the
         distance to the fixed point in units of G/k);
       * polished states: relative, floor 1e-6 G/k;
