@@ -43,12 +43,13 @@ INTEGRATOR_DRAM_BYTES_PER_SOLVE = (35.497e6 + 0.692e6) / 200_000
 # Executed FP64 instructions (DADD + DMUL + DFMA, thread level) of the FP64
 # kernels per unit of work, from an ncu capture of the same 20,000-set
 # launch (profiles/fp64_kernels_rand22x82_20k.md): the polish per solve it
-# polishes (converged before the polish: 127,247), the re-pass per FP64 step
+# polishes (its two launches of the step, beside the re-pass and after it;
+# converged before the polish: 127,247), the re-pass per FP64 step
 # attempt (254,532), the dedupe per converged solve (127,243).
 # (DADD, DMUL, DFMA) counts of each kernel; the per-unit figure is their sum
 # over the units, the peak the issue rate of that mix (each kind at its own
 # measured rate)
-POLISH_FP64_MIX = (37_244_518, 142_762_810, 128_571_916)
+POLISH_FP64_MIX = (5_834_202, 148_052_476, 72_993_468)
 REPASS_FP64_MIX = (253_617_128, 766_275_305, 786_803_446)
 UNIQUE_FP64_MIX = (2_580_512, 5_598_692, 19_595_422)
 POLISH_FP64_INSTR_PER_SOLVE = sum(POLISH_FP64_MIX) / 127_247
