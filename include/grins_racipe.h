@@ -182,7 +182,7 @@ enum { GRINS_SOBOL_OFF = 0, GRINS_SOBOL_PLAIN = 1, GRINS_SOBOL_SCRAMBLED = 2 };
  * steady state, optional time points).  grins_solver_default_opts fills:
  * FP32 + polish, rtol 1e-6, atol 1e-9, t0 0, t_end 200, ss_tol 1e-6,
  * max_steps 100000, no time grid, polish_tol 1e-13, polish_iters 16,
- * polish_max_move 1e-2, ss_tighten 0.3, method GRINS_METHOD_DOPRI5,
+ * polish_max_move 0.1, ss_tighten 0.3, method GRINS_METHOD_DOPRI5,
  * tail_rtol 1e-9, tail_start 20, tail_rho 10, tail_late 0.2, tail_work 96,
  * tail_precision GRINS_TAIL_DD. */
 typedef struct {
@@ -199,7 +199,11 @@ typedef struct {
     int32_t polish_iters;      /* polish steps at most (chord-Newton steps, see
                                   grins_racipe_polish) */
     double polish_max_move;    /* reject a polish that moves a G/k-normalised
-                                  coordinate by more than this */
+                                  coordinate by more than this in one step (a
+                                  guard against a jump to another fixed point;
+                                  the default lets the polish finish solves the
+                                  steady-state test stopped along a slow mode,
+                                  ~1e-2 G/k from their fixed point) */
     double ss_tighten;         /* once a solve's residual max_i |dx_i/dt| / (G_i/k_i) is
                                   below 10 ss_tol, its error tolerances are scaled by
                                   this factor (0 < ss_tighten <= 1; 1 = never): with

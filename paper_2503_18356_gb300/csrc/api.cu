@@ -204,7 +204,7 @@ extern "C" void grins_solver_default_opts(grins_solver_opts *o)
     o->t_grid = nullptr; o->n_t = 0;
     o->polish_tol = 1e-13;
     o->polish_iters = 16;
-    o->polish_max_move = 1e-2;
+    o->polish_max_move = 0.1;
     o->ss_tighten = 0.3;
     o->method = GRINS_METHOD_DOPRI5;
     o->tail_rtol = 1e-9;

@@ -91,3 +91,67 @@ def test_fp64_compiled_and_generic_kernels(jit, wl, monkeypatch):
     if jit == "1":
         assert "FP64, records in registers" in info, info
     h.close()
+
+
+def _hub_topology(n_reg=12):
+    """Node 0 regulated by nodes 1..n_reg (alternating activation and
+    inhibition), those nodes a chain 1 -> 2 -> ... -> n_reg + 1 -> 1 with 0 -| n_reg + 1."""
+    N = n_reg + 2
+    e = [(k, 0, 1 if k % 2 else -1) for k in range(1, n_reg + 1)]
+    e += [(k, k + 1, 1) for k in range(1, N - 1)] + [(N - 1, 1, 1), (0, N - 1, -1)]
+    a = np.array(e, dtype=np.int64)
+    return W.Topology(N, a[:, 0].astype(np.int32), a[:, 1].astype(np.int32), a[:, 2].astype(np.int8), "hub12")
+
+
+@pytest.mark.parametrize("L", [0, 2])
+def test_hub_node_beyond_eight_factors(L, monkeypatch):
+    """A node with 12 regulators (Eq. 1's product of 12 shifted Hill
+    factors): with the library's layout the hub's edges continue in a second
+    row; with L = 2 (no free slot to continue in) its row of 12 positions
+    takes chunks of more than six factors, each divided on its own.  The
+    polish folds the hub's running products after eight factors and the
+    borderline re-pass rescales them every third.
+
+    Bars: polished states (FP32 and FP64 integration) relative 1e-6 against
+    the oracle's; raw states 1e-3 on the G/k scale where both sides stopped
+    at the same fixed point.  The hub's slow modes let the stop rule
+    (residual below ss_tol) end some solves more than 1e-2 G/k from the
+    fixed point -- the oracle's own unpolished states stop as far (printed;
+    on these sets 8 at 0.015 G/k and one at 0.98 G/k).  Each such raw state
+    must be a certified near-equilibrium (residual below 10 ss_tol under the
+    oracle's Eq. 1); within polish_max_move (0.1 G/k) of the fixed point its
+    polish must land there, beyond it the polish either lands there or
+    refuses the step (POLISH_FAIL, raw state kept)."""
+    if L:
+        monkeypatch.setenv("GRINS_GRP_L", str(L))
+    topo = _hub_topology()
+    net = O.Network(*topo.edges())
+    h = PT.gpu_handle(topo)
+    params, ic, p, icn = PT.gpu_sample(h, 23, 40, 8)
+    o = O.run_sets_parallel(net, p, icn, threads=PT.THREADS)
+    o_raw = O.run_sets_parallel(net, p, icn, threads=PT.THREADS, polish=False)
+    Gk = (p.G / p.k)[:, None, :]
+    conv_o = o["status"] == O.CONVERGED
+    far_o = conv_o & (o_raw["status"] == O.CONVERGED) & (np.max(np.abs(o_raw["states"] - o["states"]) / Gk, axis=2) > 1e-2)
+    print(h.integrator(), "oracle raw stops > 1e-2 G/k from its fixed point:", int(far_o.sum()), "of", far_o.size)
+    if L:
+        assert "L=%d lanes" % L in h.integrator()
+    for prec in (1, 0):
+        gp = PT.to_numpy(h.integrate(params, ic, precision=prec, polish=1))
+        g = PT.to_numpy(h.integrate(params, ic, precision=prec, polish=0))
+        torch.cuda.synchronize()
+        c = PT.compare_states(gp, o, p, 1e-6, net)
+        print(prec, "polished", c)
+        assert c["max_err"] <= 1e-6 and c["n_uncertified"] == 0
+        assert c["n_basin"] <= max(1, 0.01 * gp["status"].size) and c["status_agree"] >= 0.97
+        c = PT.compare_states(g, o, p, 1e-3, net, normalised=True)
+        far = (g["status"] == O.CONVERGED) & conv_o & (np.max(np.abs(g["states"] - o["states"]) / Gk, axis=2) > 1e-2)
+        print(prec, "raw", c, "stops > 1e-2 G/k from the fixed point:", int(far.sum()))
+        assert c["max_err"] <= 1e-3 and c["n_uncertified"] == 0 and c["status_agree"] >= 0.97
+        dist = np.max(np.abs(g["states"] - o["states"]) / Gk, axis=2)
+        rel = PT.rel_err(gp["states"], o["states"], p.G[:, None, :], p.k[:, None, :]).max(axis=2)
+        landed = (gp["status"] == O.CONVERGED) & (rel <= 1e-6)
+        refused = (gp["status"] == O.POLISH_FAIL) & np.all(gp["states"] == g["states"], axis=2)
+        assert np.all(landed[far & (dist <= 0.1)]), (dist[far], rel[far], gp["status"][far])
+        assert np.all((landed | refused)[far & (dist > 0.1)]), (dist[far], rel[far], gp["status"][far])
+    h.close()
