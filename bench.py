@@ -36,10 +36,10 @@ N_ICS = 10
 TOL = dict(rtol=1e-6, atol=1e-9, t_end=200.0, ss_tol=1e-6)
 # DRAM bytes (read + write) of one FP32 integrator launch per solve, from an
 # ncu capture of the same kernel on a 20,000-set launch of this workload
-# (35.50 MB read + 0.69 MB written for 200,000 solves,
+# (35.75 MB read + 0.64 MB written for 200,000 solves,
 # profiles/grins_grp_ct_rr_rand22x82_20k.md); traffic grows with the solves
 # per launch.  None while no capture of the current kernel exists.
-INTEGRATOR_DRAM_BYTES_PER_SOLVE = (35.497e6 + 0.692e6) / 200_000
+INTEGRATOR_DRAM_BYTES_PER_SOLVE = (35.753e6 + 0.639e6) / 200_000
 # Executed FP64 instructions (DADD + DMUL + DFMA, thread level) of the FP64
 # kernels per unit of work, from an ncu capture of the same 20,000-set
 # launch (profiles/fp64_kernels_rand22x82_20k.md): the polish per solve it
