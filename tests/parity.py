@@ -35,8 +35,8 @@ def compare_states(gpu, orc, p: O.ParamSet, tol, net: O.Network, basin_tol=None,
     fixed points, how many of those are not certified equilibria, and the
     status agreement rate.
 
-    `max_rel` is always the relative error with G12's floor, |x - x*| /
-    max(|x*|, 1e-6 G/k), and `max_gk` the error on the G/k scale,
+    `max_rel` is always the relative error with a floor for states near
+    zero, |x - x*| / max(|x*|, 1e-6 G/k), and `max_gk` the error on the G/k scale,
     |x - x*| k / G.  `max_err` is the one the caller's bar is stated in:
     relative for polished states; with `normalised` the G/k scale, which is
     how unpolished states are judged -- they stop at max_i |f_i| k_i / G_i <
