@@ -31,17 +31,35 @@ __global__ void __launch_bounds__(1024) tail_order_kernel(const IntegrateArgs::T
         const int b = w / width;
         return b < 0 ? 0 : (b >= kTailBuckets ? kTailBuckets - 1 : b);
     };
-    for (long long i = threadIdx.x; i < n; i += blockDim.x) atomicAdd(&cnt[bucket(in[i].work)], 1ull);
+    // warp-aggregated counting: the lanes of a warp with the same bucket
+    // (__match_any_sync) take their slots with one atomic (whole warps step
+    // through the list together, so every lane reaches the match)
+    const int lane = threadIdx.x & 31;
+    const long long wbase = threadIdx.x - lane;
+    for (long long i0 = wbase; i0 < n; i0 += blockDim.x) {
+        const long long i = i0 + lane;
+        const int b = i < n ? bucket(in[i].work) : -1;
+        const unsigned grp = __match_any_sync(0xffffffffu, b);
+        if (b >= 0 && lane == __ffs(grp) - 1) atomicAdd(&cnt[b], (unsigned long long)__popc(grp));
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned long long s = 0;
         for (int b = kTailBuckets - 1; b >= 0; --b) { pos[b] = s; s += cnt[b]; }
     }
     __syncthreads();
-    for (long long i = threadIdx.x; i < n; i += blockDim.x) {
-        const IntegrateArgs::TailItem it = in[i];
-        const unsigned long long p = atomicAdd(&pos[bucket(it.work)], 1ull);
-        if (p < (unsigned long long)n) out[p] = it;
+    for (long long i0 = wbase; i0 < n; i0 += blockDim.x) {
+        const long long i = i0 + lane;
+        IntegrateArgs::TailItem it{};
+        int b = -1;
+        if (i < n) { it = in[i]; b = bucket(it.work); }
+        const unsigned grp = __match_any_sync(0xffffffffu, b);
+        const int leader = __ffs(grp) - 1;
+        unsigned long long base = 0;
+        if (b >= 0 && lane == leader) base = atomicAdd(&pos[b], (unsigned long long)__popc(grp));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        const unsigned long long p = base + __popc(grp & ((1u << lane) - 1u));
+        if (b >= 0 && p < (unsigned long long)n) out[p] = it;
     }
 }
 
