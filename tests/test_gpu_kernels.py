@@ -108,7 +108,8 @@ def test_hub_node_beyond_eight_factors(L, monkeypatch):
     """A node with 12 regulators (Eq. 1's product of 12 shifted Hill
     factors): with the library's layout the hub's edges continue in a second
     row; with L = 2 (no free slot to continue in) its row of 12 positions
-    takes chunks of more than six factors, each divided on its own.  The
+    takes a chunk of eight factors, too many for one division (its two
+    halves are divided apart), and one of four.  The
     polish folds the hub's running products after eight factors and the
     borderline re-pass rescales them every third.
 
