@@ -54,7 +54,9 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int kPow = 6;          // x^1 .. x^6 tabulated per node
-constexpr int kUnitIcs = 4;      // initial conditions per work unit (measured: 1 / 4 / 16 -> 8.95 / 8.10 / 8.30 ms)
+constexpr int kUnitIcs = 5;      // initial conditions per work unit (22-node workload, 10 ICs per set:
+                                 // 2 / 4 / 5 / 10 -> 6.61 / 6.45 / 6.37 / 6.37 ms; with fixed shares of
+                                 // units, 1 / 4 / 16 -> 8.95 / 8.10 / 8.30 ms)
 
 __device__ __forceinline__ float warp_maxf(float v)
 {
