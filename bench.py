@@ -419,7 +419,7 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ batched
-def batched_measurement(dev, reps):
+def batched_measurement(dev, reps, rcp_rate, f_mhz):
     """One plan over the 64 uneven networks of the batched workload (2-40
     nodes, density 0.1-0.3, 100-10k sets log-uniform, 10 ICs each), captured
     in a CUDA graph and autotuned at creation (untimed; the autotuner's pick
@@ -449,7 +449,8 @@ def batched_measurement(dev, reps):
     ms = e0.elapsed_time(e1) / reps
     info = plan.info()
     # the SFU work of record over the jobs (W_SFU = 6E + N per step attempt
-    # of one solve), per replay, against the SFU peak at the maximum SM clock:
+    # of one solve), per replay, against the SFU peak (the measured reciprocal
+    # rate at the timed steps' median SM clock):
     # a lower bound on the integrator's fraction, the replay also holding the
     # jobs' polish and dedupe
     work = 0.0
@@ -457,7 +458,7 @@ def batched_measurement(dev, reps):
         h = jb["net"]
         work += float(jb["out"]["n_steps"].double().sum().item()) * (6 * h.n_edges + h.n_nodes)
     props = torch.cuda.get_device_properties(dev)
-    peak = 16 * props.multi_processor_count * 2070e6
+    peak = rcp_rate * props.multi_processor_count * f_mhz * 1e6
     achieved = work / (ms / 1e3)
     plan.close()
     return dict(networks=len(jobs), solves=solves, ms_per_replay=ms, solves_per_s=solves / (ms / 1e3),
@@ -465,13 +466,15 @@ def batched_measurement(dev, reps):
                 roofline=dict(bound="alu", achieved=achieved / 1e9, peak=peak / 1e9, unit="Gop/s (MUFU, SFU pipe)",
                               frac=achieved / peak,
                               basis="sum over jobs of step attempts x (6E + N) per replay / replay time (polish "
-                                    "and dedupe included) / (16 x %d SMs x 2070 MHz)" % props.multi_processor_count),
+                                    "and dedupe included) / (%.2f rcp.approx/clk/SM measured x %d SMs x %.0f MHz, "
+                                    "the median SM clock of the timed steps)"
+                                    % (rcp_rate, props.multi_processor_count, f_mhz)),
                 workload="64 seeded random signed networks of 2-40 nodes, density 0.1-0.3, 100-10k sets "
                          "(log-uniform) x 10 ICs, FP32 + FP64 polish + dedupe, one CUDA-graph replay")
 
 
 # ------------------------------------------------------------------ serving
-def serving_measurement(dev, seconds, rate):
+def serving_measurement(dev, seconds, rate, rcp_rate, f_mhz):
     """Request server under the Poisson stream of ensemble requests (networks
     of 2-60 nodes, density 0.05-0.3, 1k-50k sets x 1-20 ICs, FP32 + FP64
     polish + dedupe).  At each request's arrival time the submitting thread
@@ -528,7 +531,7 @@ def serving_measurement(dev, seconds, rate):
     for h in nets:
         h.close()
     props = __import__("torch").cuda.get_device_properties(dev)
-    peak = 16 * props.multi_processor_count * 2070e6
+    peak = rcp_rate * props.multi_processor_count * f_mhz * 1e6
     offered = sum(r["n_sets"] * r["n_ics"] for r in stream) / seconds
     srv = np.array([x["latency_s"] for x in infos]) * 1e3
     lat = srv + (np.array(t_ret) - np.array([r["arrival_s"] for r in stream])) * 1e3
@@ -539,7 +542,9 @@ def serving_measurement(dev, seconds, rate):
                               peak=peak / 1e9, unit="Gop/s (MUFU, SFU pipe)",
                               basis="sum over requests of step attempts x (6E + N) / wall time from the first "
                                     "arrival to the last completion (sampling, polish, dedupe, compiles and idle "
-                                    "gaps included) / (16 x %d SMs x 2070 MHz)" % props.multi_processor_count),
+                                    "gaps included) / (%.2f rcp.approx/clk/SM measured x %d SMs x %.0f MHz, the "
+                                    "median SM clock of the timed steps)"
+                                    % (rcp_rate, props.multi_processor_count, f_mhz)),
                 p50_ms=float(np.percentile(lat, 50)),
                 p99_ms=float(np.percentile(lat, 99)), max_ms=float(lat.max()),
                 server_p50_ms=float(np.percentile(srv, 50)), server_p99_ms=float(np.percentile(srv, 99)),
@@ -907,9 +912,9 @@ def run_native(args):
         if samplers is not None:
             line["samplers"] = samplers
         if args.batch_reps > 0 and ws == 1:
-            line["batched"] = batched_measurement(dev, args.batch_reps)
+            line["batched"] = batched_measurement(dev, args.batch_reps, rates["rcp"], f_mhz)
         if args.serve_seconds > 0 and ws == 1:
-            line["serving"] = serving_measurement(dev, args.serve_seconds, args.serve_rate)
+            line["serving"] = serving_measurement(dev, args.serve_seconds, args.serve_rate, rates["rcp"], f_mhz)
         if not args.no_cpu_baseline and ws == 1:
             line["cpu_baseline"], orc = cpu_baseline(args.cpu_sets)
             P = snap["G"].shape[0]
